@@ -1,0 +1,84 @@
+/*
+ * lbmd_oracle.h -- API of the FP64 CPU oracle for the coupled
+ * lattice-Boltzmann / molecular-dynamics step of Fyta, Sircar, Kaxiras,
+ * Melchionna, Bernaschi and Succi, "Parallel multiscale modeling of
+ * biopolymer dynamics with hydrodynamic correlations" (Sec. II).
+ *
+ * TEST INFRASTRUCTURE ONLY.  The oracle exists to check and to time the CUDA
+ * path.  Only the test-suite, the smoke check and the CPU-baseline leg of the
+ * benchmark may load it; the product path never does.  It shares no code,
+ * header, table or helper with the CUDA library.
+ *
+ * Units are lattice units (dx = dt = 1, bead mass m = 1, charge q = 1).
+ * Arrays are flat, x fastest: site s = x + nx*(y + ny*z).  Populations are
+ * laid out [19][nsites]; bead vectors [n_beads][3].
+ */
+#ifndef LBMD_ORACLE_H
+#define LBMD_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int nx, ny, nz;
+    double tau;               /* BGK relaxation time, omega = 1/tau */
+    double body_force[3];     /* uniform force density on every fluid site */
+    int wall_x;               /* pore-wall plane (field region, translocation); <0: none */
+    int pore_h;               /* side of the square pore */
+    int n_beads;
+    double k_bond, r0;        /* harmonic bonds */
+    double kappa_bend;        /* angular term kappa*phi^2/2 */
+    double lj_sigma, lj_eps;  /* bead-bead WCA */
+    double wall_sigma, wall_eps; /* bead-solid-node WCA */
+    double E;                 /* driving force q*E along +x inside the pore channel */
+    double gamma;             /* bead-fluid friction */
+    double kT;                /* bead noise temperature (0: off) */
+    int md_outer;             /* M: MD steps per LB step */
+    int md_inner;             /* M^b: bonded sub-steps per MD step */
+    uint64_t seed;            /* Philox key */
+    uint32_t realization;     /* realization index, xor-ed into key word 1 */
+} orc_params;
+
+typedef struct orc_sim orc_sim;
+
+/* tables and single-site helpers */
+void orc_tables(int *c /*19*3*/, double *w /*19*/, int *opp /*19*/);
+void orc_feq(double rho, const double *u, double *feq /*19*/);
+void orc_source(const double *G, double *S /*19*/);
+void orc_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out);
+void orc_gauss3(uint64_t seed, uint32_t realization, uint32_t bead, int64_t step,
+                uint32_t substep, double *z /*3*/);
+void orc_gauss3_batch(uint64_t seed, uint32_t realization, uint32_t n_beads, int64_t step,
+                      uint32_t substep, double *z /* [n_beads][3] */);
+
+/* simulation */
+orc_sim *orc_create(const orc_params *p, const uint8_t *solid /* nsites, may be NULL */);
+void orc_destroy(orc_sim *s);
+void orc_init_fluid(orc_sim *s, const double *rho /* nsites or NULL */,
+                    const double *u /* [3][nsites] or NULL */);
+void orc_set_populations(orc_sim *s, const double *f);
+void orc_get_populations(const orc_sim *s, double *f);
+void orc_set_beads(orc_sim *s, const double *r, const double *v /* may be NULL */);
+void orc_get_beads(const orc_sim *s, double *r, double *v);
+void orc_set_step(orc_sim *s, int64_t step);
+int64_t orc_get_step(const orc_sim *s);
+void orc_step(orc_sim *s, int n);
+
+/* inspection */
+void orc_moments(const orc_sim *s, double *rho /* nsites */, double *u /* [3][nsites] */);
+int orc_interp_weights(const orc_sim *s, const double *r, int *nodes /*8*/, double *w /*8*/);
+void orc_last_coupling(const orc_sim *s, double *up, double *J);
+void orc_fast_forces(const orc_sim *s, const double *r, double *F);
+void orc_fast_energies(const orc_sim *s, const double *r, double *e /* bond,bend,lj,wall */);
+void orc_field_forces(const orc_sim *s, const double *r, double *F);
+void orc_observables(const orc_sim *s, double *out /* ORC_NOBS */);
+
+#define ORC_NOBS 16
+
+#ifdef __cplusplus
+}
+#endif
+#endif
