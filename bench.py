@@ -1,0 +1,311 @@
+"""Benchmark of the coupled LB-MD step (one JSON line on stdout).
+
+A step is one coupled lattice-Boltzmann / molecular-dynamics step of the whole
+hot path: particle kernel (gather, MD cycle, spread) concurrently with the
+fused stream-collide kernel, then the source pass.  The metric is MLUPS
+(million lattice-site updates per second, all nx*ny*nz*n_real sites counted).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--impl native|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+(its own seed); value = all ranks' site updates / max-over-ranks time
+(weak scaling, no data-path collective).
+
+Timing: each timed step is bracketed by CUDA events on the library's stream;
+between timed steps a 256 MiB buffer is written to flush the 129 MB L2 (the
+populations of the default workload, 2 x 40 MB, would otherwise stay in L2).
+The roofline object reports the stream-collide kernel: algorithmic bytes
+(19 x 4 B read + 19 x 4 B written per site in FP32, half that in FP16)
+over its CUDA-event duration, against the measured HBM copy bandwidth.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _traffic_record(sites: int):
+    """DRAM bytes per launch of the stream-collide kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "stream_collide_traffic.json")
+    src = os.path.join(ROOT, "paper_0711_2665_gb300", "csrc", "k_fluid.cu")
+    if not os.path.exists(p):
+        return None
+    rec = json.load(open(p))
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if rec.get("k_fluid_sha256") != sha:
+        return None
+    return rec["dram_bytes_per_site"] * sites
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _config_block(w, flush):
+    return {"workload": w["name"], "lattice": [w["nx"], w["ny"], w["nz"]], "n_real": w["n_real"],
+            "beads": w["n_beads"], "tau": w["tau"], "precision": w["precision"],
+            "md_substeps": [w["md_outer"], w["md_inner"]], "kappa_bend": w["kappa_bend"],
+            "l2": "flushed between timed steps (256 MiB write)" if flush else "inputs larger than L2",
+            "parallelism": "replicas"}
+
+
+def run_reference(args, w, world, rank):
+    """The oracle (FP64, plain C, one host thread) on the same workload; each
+    step is one oracle LB-MD step of realization 0."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_0711_2665_gb300 import workloads
+    oracle.build()
+    inp = workloads.build_inputs(w)
+    o1 = int(inp["offsets"][1])
+    orc = oracle.OracleSim(workloads.oracle_params(w, 0, o1), inp["solid"])
+    orc.set_beads(inp["r0"][:o1])
+    for _ in range(args.warmup):
+        orc.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        orc.step(1)
+    dt = time.perf_counter() - t0
+    sites = w["nx"] * w["ny"] * w["nz"]
+    mlups = sites * args.steps / dt / 1e6 * w["n_real"] / w["n_real"]
+    sample = f"{args.steps} oracle steps of realization 0 ({sites} sites, {o1} beads)"
+    line = {"impl": "reference", "metric": "coupled LB-MD MLUPS", "value": mlups, "unit": "MLUPS",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config_block(w, False),
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(w, budget_s=15.0):
+    """Oracle timed on a bounded sample of the workload (whole LB-MD steps of
+    realization 0) on one host core."""
+    import oracle
+    from paper_0711_2665_gb300 import workloads
+    oracle.build()
+    inp = workloads.build_inputs(w)
+    o1 = int(inp["offsets"][1])
+    orc = oracle.OracleSim(workloads.oracle_params(w, 0, o1), inp["solid"])
+    orc.set_beads(inp["r0"][:o1])
+    orc.step(1)
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s or n < 2:
+        orc.step(1)
+        n += 1
+    dt = time.perf_counter() - t0
+    sites = w["nx"] * w["ny"] * w["nz"]
+    return {"value": sites * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{n} FP64 oracle steps of realization 0 ({sites} sites, {o1} beads), {dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="plain_fp32")
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    from paper_0711_2665_gb300 import workloads
+    world, rank, local = _dist()
+    w = workloads.get(args.workload)
+    if world > 1:
+        w = dict(w, seed=w["seed"] + 1000 * rank, chain_seed=w["chain_seed"])
+
+    if args.impl == "reference":
+        return run_reference(args, w, world, rank)
+
+    import numpy as np
+    import torch
+    from paper_0711_2665_gb300 import build as libbuild, lbmd
+
+    libbuild.build_library()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+
+    inp = workloads.build_inputs(w)
+    sim = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"], device=f"cuda:{local}")
+    sim.autotune(3)
+    sites = w["nx"] * w["ny"] * w["nz"] * w["n_real"]
+    flush = not args.no_flush
+    scratch = torch.empty(256 << 20, dtype=torch.uint8, device=dev) if flush else None
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        if flush:
+            scratch.zero_()
+        sim.step(1)
+    barrier()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = sim.launch_count()
+    sim.profile(True)
+    with ClockSampler(local) as clk:
+        barrier()
+        for k in range(args.steps):
+            if flush:
+                scratch.zero_()
+            ev[k][0].record(stream)
+            sim.step(1)
+            ev[k][1].record(stream)
+        barrier()
+    ktimes = sim.kernel_times()
+    sim.profile(False)
+    launches = sim.launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    sim.check()
+    value = sites * world * args.steps / (total_ms * 1e-3) / 1e6
+
+    # roofline of the stream-collide kernel (the lattice pass)
+    peak, peak_kind = _peaks()
+    n_sc, ms_sc = ktimes["stream_collide"]
+    bytes_site = 152 if w["precision"] == "fp32" else 76
+    achieved = bytes_site * sites / (ms_sc / n_sc * 1e-3) / 1e9 if n_sc else None
+    traffic = _traffic_record(sites)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
+                "peak_kind": peak_kind, "kernel": "k_stream_collide",
+                "algorithmic_bytes_per_launch": bytes_site * sites}
+    shares = {k: {"launches": n, "ms_total": ms, "ms_per_launch": ms / n if n else None}
+              for k, (n, ms) in ktimes.items()}
+
+    # end-to-end through the C ABI from pinned host buffers: upload the state,
+    # K steps each reading back its diagnostics row, download the final state
+    f_host = torch.empty(sim.n_real * 19 * sim.ns, dtype=torch.float32, pin_memory=True).numpy()
+    r_host, v_host = sim.get_beads()
+    f_host[:] = sim.get_populations().reshape(-1)
+    barrier()
+    t0 = time.perf_counter()
+    sim.set_populations(f_host)
+    sim.set_beads(r_host, v_host)
+    for _ in range(args.steps):
+        if flush:
+            scratch.zero_()
+        sim.step(1)
+        sim.diagnostics(1)
+    f_back = sim.get_populations()
+    r_back, _ = sim.get_beads()
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    bi = f_host.nbytes + 2 * r_host.nbytes
+    bo = args.steps * sim.n_real * 112 + f_back.nbytes + 2 * r_back.nbytes
+    e2e = {"value": sites * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": bi / args.steps, "d2h_bytes_per_step": bo / args.steps,
+           "note": "state uploaded once and downloaded once per K-step job; one diagnostics row read per step"}
+
+    if rank == 0:
+        clocks = clk.summary()
+        line = {"metric": "coupled LB-MD MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if w["precision"] == "fp32" else "f16-storage/f32-math",
+                "data": "synthetic", "config": dict(_config_block(w, flush), tiles=list(sim.tiles())),
+                "roofline": roofline, "kernels": shares, "gpu_launches": launches,
+                "clocks": clocks, "e2e": e2e}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * lbmd.h -- C ABI of the GB300 (sm_103a) library for the coupled
+ * lattice-Boltzmann / molecular-dynamics step of Fyta, Sircar, Kaxiras,
+ * Melchionna, Bernaschi and Succi, "Parallel multiscale modeling of
+ * biopolymer dynamics with hydrodynamic correlations".
+ *
+ * The problem the calls state follows Sec. IV of the paper: a periodic box
+ * holding a D3Q19 BGK fluid (Sec. II, Eqs. 1-5), solid sites that reflect the
+ * fluid by halfway bounce-back (the wall with a square pore), and one bead
+ * chain per realization that exchanges momentum with the fluid (Sec. II,
+ * Eqs. 8-13) and is driven through the pore by a local field.
+ *
+ * Conventions shared by every call:
+ *  - Lattice units: dx = dt = 1, bead mass 1, charge 1.
+ *  - Site index s = x + nx*(y + ny*z) (x fastest).  Host population arrays are
+ *    [n_real][19][nz][ny][nx] float; host bead arrays are [total_beads][3]
+ *    double, beads of realization r at rows bead_offsets[r] .. bead_offsets[r+1]-1.
+ *  - D3Q19 link order: 0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 =
+ *    (1,1,0),(-1,-1,0),(1,-1,0),(-1,1,0),(1,0,1),(-1,0,-1),(1,0,-1),(-1,0,1),
+ *    (0,1,1),(0,-1,-1),(0,1,-1),(0,-1,1).
+ *  - Ownership: the caller allocates ONE device buffer of lbmd_required_bytes()
+ *    bytes and passes it to lbmd_init; it must stay valid until lbmd_destroy.
+ *    The library allocates no device memory itself.  It owns the handle, a
+ *    small host state, one extra CUDA stream and a few events.
+ *  - Streams: all device work is ordered on the stream given to lbmd_init.
+ *    lbmd_step returns without waiting; calls that return data to the host
+ *    (observables, diagnostics, get_*) synchronise that stream.
+ *  - Errors: every call returns an lbmd_status and never aborts the process.
+ *    lbmd_last_error() gives a one-line description of the last failure.
+ *    Device-side problems (non-finite values, neighbour-list overflow) are
+ *    latched in a status word that lbmd_observables / lbmd_check report.
+ */
+#ifndef LBMD_H
+#define LBMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBMD_Q 19
+/* Beads of one realization are integrated by one thread block. */
+#define LBMD_MAX_BEADS_PER_REALIZATION 1024
+/* Rows of the per-step diagnostics ring (per realization). */
+#define LBMD_DIAG_RING 1024
+
+typedef enum {
+    LBMD_OK = 0,
+    LBMD_ERR_INVALID_ARG = 1, /* bad configuration or argument; nothing was changed */
+    LBMD_ERR_CUDA = 2,        /* a CUDA runtime call failed (message in lbmd_last_error) */
+    LBMD_ERR_NONFINITE = 3,   /* a NaN/Inf appeared in the fluid or bead state */
+    LBMD_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    LBMD_ERR_CAPACITY = 5,    /* a fixed-capacity list (neighbours, wall sites) overflowed */
+    LBMD_ERR_BUFFER = 6       /* device buffer too small or misaligned */
+} lbmd_status;
+
+typedef enum {
+    LBMD_FP32 = 0,    /* populations stored as FP32 */
+    LBMD_FP16DEV = 1  /* populations stored as FP16 deviations (f_i - w_i) * 2^12, FP32 arithmetic */
+} lbmd_precision;
+
+/* Problem statement (Sec. IV set-up; Sec. II parameters). */
+typedef struct lbmd_config {
+    int32_t nx, ny, nz;      /* lattice of one realization (periodic in x, y and z) */
+    int32_t n_real;          /* independent realizations (>= 1), each with its own lattice and chain */
+    double tau;              /* BGK relaxation time, omega = 1/tau, nu = (tau - 1/2)/3; tau > 1/2 */
+    double body_force[3];    /* uniform force density on every fluid site (0 for the paper's set-up) */
+    int32_t wall_x;          /* x plane of the pore wall: defines the field channel and the
+                                translocation count; -1 = none.  Solid sites come from the mask. */
+    int32_t pore_h;          /* side of the square pore centred at (ny/2, nz/2) */
+    double k_bond, r0;       /* harmonic bonds, Sec. II, Eq. 19 */
+    double kappa_bend;       /* angular term kappa phi^2 / 2 (Sec. II) */
+    double lj_sigma, lj_eps; /* bead-bead WCA (Eq. 14 cut at 2^(1/6) sigma, shifted) */
+    double wall_sigma, wall_eps; /* bead-solid-site WCA */
+    double E;                /* field force along +x inside the pore channel (Sec. IV) */
+    double gamma;            /* bead-fluid friction (Sec. II, Eq. 12) */
+    double kT;               /* bead noise temperature (Sec. II, Eq. 15); 0 = off */
+    int32_t md_outer;        /* M, MD steps per LB step (paper: 5) */
+    int32_t md_inner;        /* M^b, bonded sub-steps per MD step (paper: 20) */
+    int32_t precision;       /* lbmd_precision */
+    int32_t reserved;        /* must be 0 */
+    uint64_t seed;           /* Philox key; realization r uses key word 1 = seed_hi ^ r */
+} lbmd_config;
+
+/* Observables of one realization at the current state (Sec. III global
+ * momenta, Sec. IV.B radii of gyration, Sec. IV.C Eqs. 24-25 work rates). */
+typedef struct lbmd_obs {
+    double mass;              /* sum of rho over fluid sites (FP64 reduction) */
+    double p_fluid[3];        /* sum of rho u over fluid sites (FP64 reduction) */
+    double p_beads[3];        /* sum of bead velocities */
+    double com[3];            /* centre of mass of the chain (unwrapped) */
+    double n_translocated;    /* beads with x > wall_x + 1/2 (unwrapped) */
+    double dWH_dt;            /* gamma sum_i v_i . u(r_i) */
+    double dWE_dt;            /* sum_i F_drive,i . v_i */
+    double rg_untranslocated; /* radius of gyration of the beads not yet translocated */
+    double rg_translocated;   /* radius of gyration of the translocated beads */
+    int64_t step;             /* LB steps taken */
+    int32_t status;           /* latched lbmd_status of the device state */
+    int32_t pad;
+} lbmd_obs;
+
+/* One row of the per-step diagnostics that each step records on the device
+ * at no extra pass over the lattice: the fluid sums come from the
+ * stream-collide kernel, the bead sums from the particle kernel, both for the
+ * state at the start of the step. */
+typedef struct lbmd_diag {
+    int64_t step;
+    double mass;
+    double p_fluid[3];
+    double p_beads[3];
+    double com[3];
+    double n_translocated;
+    double dWH_dt;
+    double dWE_dt;
+} lbmd_diag;
+
+typedef struct lbmd_kernel_time {
+    char name[32];
+    int64_t launches;
+    double total_ms;
+} lbmd_kernel_time;
+
+typedef struct lbmd_handle lbmd_handle;
+
+/* Bytes of device memory lbmd_init needs for this configuration.
+ * bead_offsets: host array of n_real+1 CSR offsets (bead_offsets[0] = 0). */
+lbmd_status lbmd_required_bytes(const lbmd_config *cfg, const int32_t *bead_offsets, size_t *bytes);
+
+/* Set up one simulation.
+ *  solid        host [nz][ny][nx] bytes, 1 = solid site (shared by all realizations)
+ *  bead_offsets host [n_real+1] CSR offsets into the bead arrays
+ *  r_init       host [total_beads][3] initial unwrapped bead positions; velocities start at 0
+ *  device_buffer / device_bytes  caller-owned device memory (256-byte aligned)
+ *  stream       cudaStream_t (as void*) that orders all work of this handle
+ * The fluid starts at rest with rho = 1 (Sec. IV).  Synchronises the stream. */
+lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_t *bead_offsets,
+                      const double *r_init, void *device_buffer, size_t device_bytes,
+                      void *stream, lbmd_handle **out);
+
+/* Advance n_steps coupled LB-MD steps (Sec. II).  Asynchronous. */
+lbmd_status lbmd_step(lbmd_handle *h, int64_t n_steps);
+
+/* Observables of every realization at the current state: out has n_real
+ * entries.  One pass over the populations; synchronises the stream. */
+lbmd_status lbmd_observables(lbmd_handle *h, lbmd_obs *out);
+
+/* Latched device status (LBMD_OK if clean); synchronises the stream. */
+lbmd_status lbmd_check(lbmd_handle *h);
+
+/* Copy the newest per-step diagnostics rows to the host: out holds
+ * n_real * max_rows rows, [realization][row], oldest first; *rows receives
+ * the number of rows written per realization.  Synchronises the stream. */
+lbmd_status lbmd_diagnostics(lbmd_handle *h, lbmd_diag *out, int32_t max_rows, int32_t *rows);
+
+/* Fluid initial condition: f = f_eq(rho, u) at every fluid site.
+ * rho: host [n_real][ns] or NULL (rho = 1); u: host [n_real][3][ns] or NULL (u = 0). */
+lbmd_status lbmd_init_fluid(lbmd_handle *h, const double *rho, const double *u);
+
+/* Pre-collision populations f^n (the state the next step starts from).
+ * f: host [n_real][19][ns]; solid sites read as 0. */
+lbmd_status lbmd_get_populations(lbmd_handle *h, float *f);
+lbmd_status lbmd_set_populations(lbmd_handle *h, const float *f);
+
+/* Bead state: r unwrapped positions, v velocities; host [total_beads][3]. */
+lbmd_status lbmd_get_beads(lbmd_handle *h, double *r, double *v);
+lbmd_status lbmd_set_beads(lbmd_handle *h, const double *r, const double *v /* NULL: zero */);
+
+/* Coupling of the last step: fluid velocity at each bead (frozen for the MD
+ * cycle) and the momentum the fluid gave each bead; host [total_beads][3]. */
+lbmd_status lbmd_get_coupling(lbmd_handle *h, float *up, float *J);
+
+/* LB step counter; it is also the Philox counter of the bead noise, so a
+ * state restored together with its step continues bit for bit. */
+lbmd_status lbmd_get_step(lbmd_handle *h, int64_t *step);
+lbmd_status lbmd_set_step(lbmd_handle *h, int64_t step);
+
+/* Replay steps from a captured CUDA graph of steps_per_graph steps
+ * (0 = launch kernels one by one).  Results are identical either way. */
+lbmd_status lbmd_set_graph(lbmd_handle *h, int32_t steps_per_graph);
+
+/* Launch shapes of the stream-collide kernel: block (32, by) threads, each
+ * thread walking zc consecutive z planes.  by in {1,2,4,8,16}, zc in 1..64.
+ * Results are bit-identical for every shape. */
+lbmd_status lbmd_set_tiles(lbmd_handle *h, int32_t by, int32_t zc);
+lbmd_status lbmd_get_tiles(lbmd_handle *h, int32_t *by, int32_t *zc);
+
+/* Time every candidate tile shape on the current state (restored afterwards)
+ * and keep the fastest.  Synchronises the stream. */
+lbmd_status lbmd_autotune(lbmd_handle *h, int32_t steps_per_candidate, int32_t *by, int32_t *zc);
+
+/* Per-kernel timing with CUDA events on the launching streams (eager launches
+ * only while enabled) and the count of kernels this handle launched. */
+lbmd_status lbmd_profile(lbmd_handle *h, int32_t enable);
+lbmd_status lbmd_kernel_times(lbmd_handle *h, lbmd_kernel_time *out, int32_t max_entries,
+                              int32_t *n_entries);
+lbmd_status lbmd_launch_count(lbmd_handle *h, int64_t *launches);
+
+const char *lbmd_status_string(lbmd_status s);
+const char *lbmd_last_error(const lbmd_handle *h);
+
+/* Release the handle (not the caller's device buffer).  Synchronises. */
+void lbmd_destroy(lbmd_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

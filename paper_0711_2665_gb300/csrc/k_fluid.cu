@@ -1,0 +1,384 @@
+// k_fluid.cu -- lattice kernels of the coupled LB-MD step:
+//   * the fused pull-scheme stream + bounce-back + moments + BGK collide
+//     (Sec. II, Eqs. 1-5, with the walls of Sec. III), with the per-step FP64
+//     mass/momentum diagnostics folded in;
+//   * the sparse source pass that adds the beads' reaction (Sec. II, Eq. 9) at
+//     the lattice sites the beads touched;
+//   * state transfer (equilibrium initialisation, pull to / push from the
+//     fp32 staging area) and the fluid part of the observables.
+#include "lbmd_internal.cuh"
+
+namespace lbmd {
+
+// ---------------------------------------------------------------------------
+// FP64 block reduction of four per-thread partials; writes partial[blk][0..3]
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void block_partial4(double a, double b, double c, double d, double *out) {
+    __shared__ double s[16][4];
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int lane = tid & 31, warp = tid >> 5, nw = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+        d += __shfl_down_sync(0xffffffffu, d, o);
+    }
+    if (lane == 0) { s[warp][0] = a; s[warp][1] = b; s[warp][2] = c; s[warp][3] = d; }
+    __syncthreads();
+    if (tid == 0) {
+        double t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+        for (int w = 0; w < nw; ++w) { t0 += s[w][0]; t1 += s[w][1]; t2 += s[w][2]; t3 += s[w][3]; }
+        out[0] = t0; out[1] = t1; out[2] = t2; out[3] = t3;
+    }
+}
+
+// The last block to finish sums the block partials of every realization in a
+// fixed order (deterministic) and stores mass = n_fluid + sum(rho - 1) and the
+// fluid momentum.  MODE 1 writes the step's diagnostics row, MODE 2 the
+// observables.  No block ever waits for another.
+template <int MODE>
+__device__ void finalize_fluid_sums(const Sim &S, unsigned int *done, long long step, int bpr) {
+    __shared__ int am_last;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int nthreads = blockDim.x * blockDim.y;
+    const unsigned int nblocks = gridDim.x * gridDim.y * gridDim.z;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) am_last = (atomicAdd(done, 1u) == nblocks - 1u);
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    __shared__ double red[16][4];
+    const int lane = tid & 31, warp = tid >> 5, nw = (nthreads + 31) >> 5;
+    for (int rr = 0; rr < S.n_real; ++rr) {
+        double t[4] = {0, 0, 0, 0};
+        for (int b = tid; b < bpr; b += nthreads) {
+            const double *p = S.partial + 4 * ((size_t)rr * bpr + b);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) t[k] += __ldcg(p + k);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) t[k] += __shfl_down_sync(0xffffffffu, t[k], o);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) red[warp][k] = t[k];
+        __syncthreads();
+        if (tid == 0) {
+            double u[4] = {0, 0, 0, 0};
+            for (int w = 0; w < nw; ++w)
+                for (int k = 0; k < 4; ++k) u[k] += red[w][k];
+            const double mass = S.n_fluid + u[0];
+            if (!isfinite(mass) || !isfinite(u[1]) || !isfinite(u[2]) || !isfinite(u[3]))
+                atomicOr(&S.ctrl->status, ST_NONFINITE);
+            if (MODE == 1) {
+                lbmd_diag *row = S.ring + (size_t)rr * LBMD_DIAG_RING + (step % LBMD_DIAG_RING);
+                row->mass = mass;
+                row->p_fluid[0] = u[1]; row->p_fluid[1] = u[2]; row->p_fluid[2] = u[3];
+            } else {
+                lbmd_obs *o = S.obs + rr;
+                o->mass = mass;
+                o->p_fluid[0] = u[1]; o->p_fluid[1] = u[2]; o->p_fluid[2] = u[3];
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) *done = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// Fused pull stream + bounce-back + moments + BGK collision.
+//   h_i(x)   = h*_i(x - c_i)          pulled from A, or h*_opp(i)(x) when x - c_i is solid
+//   rho      = 1 + sum_i h_i,  rho u = sum_i h_i c_i               (Eqs. 1-2)
+//   h*_i     = h_i + omega (heq_i - h_i) + 3 w_i g.c_i              (Eqs. 4-5)
+//   heq_i    = w_i [ (rho - 1) + rho (3 c.u + 9/2 (c.u)^2 - 3/2 u.u) ]
+// (h = f - w).  Block (32, by) covers 32 consecutive x of `by` rows; each thread
+// walks zc consecutive z planes.  MODE 0: store; 1: store + per-step sums;
+// 2: sums only (observables).
+// ---------------------------------------------------------------------------
+template <int PREC, int MODE>
+__global__ void __launch_bounds__(512) k_stream_collide(const Sim S, const void *__restrict__ Av,
+                                                        void *__restrict__ Bv, const int zc,
+                                                        const int nzb) {
+    using T = typename PopT<PREC>::T;
+    const int x = blockIdx.x * 32 + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int r = blockIdx.z / nzb;
+    const int z0 = (blockIdx.z - r * nzb) * zc;
+    const int nx = S.nx, ny = S.ny, nz = S.nz;
+    const uint32_t ns = (uint32_t)S.ns;
+    const T *__restrict__ A = reinterpret_cast<const T *>(Av) + (size_t)r * Q * ns;
+    T *__restrict__ B = reinterpret_cast<T *>(Bv) + (size_t)r * Q * ns;
+    long long step = 0;
+    if (MODE == 1) step = S.ctrl->step;
+    float am = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
+    const float om = S.omega;
+    const float g0 = S.g[0], g1 = S.g[1], g2 = S.g[2];
+    const bool has_g = (g0 != 0.f) || (g1 != 0.f) || (g2 != 0.f);
+
+    if (x < nx && y < ny) {
+        const int xv0 = (x == 0 ? nx - 1 : x - 1), xv2 = (x == nx - 1 ? 0 : x + 1);
+        const int yv0 = (y == 0 ? ny - 1 : y - 1), yv2 = (y == ny - 1 ? 0 : y + 1);
+        const int zend = min(z0 + zc, nz);
+        for (int z = z0; z < zend; ++z) {
+            const int zv0 = (z == 0 ? nz - 1 : z - 1), zv2 = (z == nz - 1 ? 0 : z + 1);
+            const int s = x + nx * (y + ny * z);
+            const uint32_t lm = S.tileflag[blockIdx.x + S.nxt * (y + ny * z)] ? __ldg(S.link + s) : 0u;
+            if (lm & SOLID_BIT) continue;
+            float h[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int sx = cx(i) == 1 ? xv0 : (cx(i) == -1 ? xv2 : x);
+                const int sy = cy(i) == 1 ? yv0 : (cy(i) == -1 ? yv2 : y);
+                const int sz = cz(i) == 1 ? zv0 : (cz(i) == -1 ? zv2 : z);
+                const uint32_t src = (uint32_t)(sx + nx * (sy + ny * sz));
+                const bool bb = (lm >> i) & 1u;
+                const uint32_t idx = bb ? (uint32_t)opp(i) * ns + (uint32_t)s : (uint32_t)i * ns + src;
+                h[i] = load_dev(A, idx, wq(i));
+            }
+            float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                drho += h[i];
+                if (cx(i) == 1) jx += h[i];
+                if (cx(i) == -1) jx -= h[i];
+                if (cy(i) == 1) jy += h[i];
+                if (cy(i) == -1) jy -= h[i];
+                if (cz(i) == 1) jz += h[i];
+                if (cz(i) == -1) jz -= h[i];
+            }
+            if (MODE != 0) { am += drho; ax += jx; ay += jy; az += jz; }
+            if (MODE != 2) {
+                const float rho = 1.0f + drho;
+                const float ir = 1.0f / rho;
+                const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
+                const float usq = 1.5f * (ux * ux + uy * uy + uz * uz);
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const float cu = 3.0f * ((float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz);
+                    const float heq = wq(i) * (drho + rho * (cu + 0.5f * cu * cu - usq));
+                    float hn = h[i] + om * (heq - h[i]);
+                    if (has_g)
+                        hn += 3.0f * wq(i) * ((float)cx(i) * g0 + (float)cy(i) * g1 + (float)cz(i) * g2);
+                    store_dev(B, (uint32_t)i * ns + (uint32_t)s, hn, wq(i));
+                }
+            }
+        }
+    }
+    if (MODE != 0) {
+        const int bpr = gridDim.x * gridDim.y * nzb;
+        const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+        block_partial4((double)am, (double)ax, (double)ay, (double)az, S.partial + 4 * (size_t)blk);
+        if (MODE == 1) finalize_fluid_sums<1>(S, &S.ctrl->sc_done, step, bpr);
+        else finalize_fluid_sums<2>(S, &S.ctrl->obs_done, 0, bpr);
+    }
+}
+
+static dim3 sc_grid(const Sim &S, int by, int zc, int *nzb) {
+    *nzb = (S.nz + zc - 1) / zc;
+    return dim3((S.nx + 31) / 32, (S.ny + by - 1) / by, (*nzb) * S.n_real);
+}
+
+int sc_blocks(const Sim &S, int by, int zc) {
+    int nzb;
+    dim3 g = sc_grid(S, by, zc, &nzb);
+    return (int)(g.x * g.y * g.z);
+}
+
+cudaError_t launch_stream_collide(const Sim &S, const void *A, void *B, int by, int zc, bool diag,
+                                  cudaStream_t st) {
+    int nzb;
+    dim3 grid = sc_grid(S, by, zc, &nzb);
+    dim3 block(32, by);
+    if (S.precision == LBMD_FP16DEV) {
+        if (diag) k_stream_collide<1, 1><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
+        else k_stream_collide<1, 0><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
+    } else {
+        if (diag) k_stream_collide<0, 1><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
+        else k_stream_collide<0, 0><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fluid_observables(const Sim &S, const void *A, cudaStream_t st) {
+    int nzb;
+    const int by = 8, zc = 4;
+    dim3 grid = sc_grid(S, by, zc, &nzb);
+    dim3 block(32, by);
+    if (S.precision == LBMD_FP16DEV) k_stream_collide<1, 2><<<grid, block, 0, st>>>(S, A, nullptr, zc, nzb);
+    else k_stream_collide<0, 2><<<grid, block, 0, st>>>(S, A, nullptr, zc, nzb);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Source pass (Sec. II, Eq. 9 with beta = 3): at every lattice site a bead
+// touched this step, f*_i += 3 w_i G.c_i with G the momentum the beads handed
+// to the fluid there; G is then cleared.  Sites are found through the list of
+// (bead, corner) pairs; the first pair to stamp a site with this step's tag
+// applies its source.  The last block to finish advances the step counter.
+// ---------------------------------------------------------------------------
+template <int PREC>
+__global__ void __launch_bounds__(256) k_source(const Sim S, void *__restrict__ Bv) {
+    using T = typename PopT<PREC>::T;
+    const long long step = S.ctrl->step;
+    const int tag = (int)(step & 0x3fffffffll) + 1;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < 8 * S.total_beads) {
+        const int gnode = S.pair_node[k];
+        if (gnode >= 0 && atomicExch(S.stamp + gnode, tag) != tag) {
+            const int r = gnode / S.ns;
+            const int s = gnode - r * S.ns;
+            const size_t ns = (size_t)S.ns;
+            unsigned long long *Gr = S.G + (size_t)r * 3 * ns + s;
+            const float G0 = (float)(long long)Gr[0] * FIX_INV_SCALE_F;
+            const float G1 = (float)(long long)Gr[ns] * FIX_INV_SCALE_F;
+            const float G2 = (float)(long long)Gr[2 * ns] * FIX_INV_SCALE_F;
+            Gr[0] = 0ull; Gr[ns] = 0ull; Gr[2 * ns] = 0ull;
+            T *B = reinterpret_cast<T *>(Bv) + (size_t)r * Q * ns;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const float src = 3.0f * wq(i) * ((float)cx(i) * G0 + (float)cy(i) * G1 + (float)cz(i) * G2);
+                const uint32_t idx = (uint32_t)i * (uint32_t)ns + (uint32_t)s;
+                store_dev(B, idx, load_dev_cg(B, idx, wq(i)) + src, wq(i));
+            }
+        }
+    }
+    __shared__ int am_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) am_last = (atomicAdd(&S.ctrl->src_done, 1u) == gridDim.x - 1u);
+    __syncthreads();
+    if (am_last && threadIdx.x == 0) {
+        S.ctrl->src_done = 0u;
+        S.ctrl->step = step + 1;
+    }
+}
+
+cudaError_t launch_source(const Sim &S, void *B, cudaStream_t st) {
+    const int threads = 256;
+    const int blocks = max(1, (8 * S.total_beads + threads - 1) / threads);
+    if (S.precision == LBMD_FP16DEV) k_source<1><<<blocks, threads, 0, st>>>(S, B);
+    else k_source<0><<<blocks, threads, 0, st>>>(S, B);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// state transfer
+// ---------------------------------------------------------------------------
+template <int PREC>
+__global__ void k_init_rest(const Sim S, void *Av) {
+    using T = typename PopT<PREC>::T;
+    const size_t ns = (size_t)S.ns;
+    const size_t total = ns * S.n_real;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = t / ns, s = t - r * ns;
+        T *A = reinterpret_cast<T *>(Av) + r * Q * ns;
+        const bool sol = S.solid[s] != 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) store_dev(A, (uint32_t)(i * ns + s), 0.0f, sol ? 0.0f : wq(i));
+    }
+}
+
+cudaError_t launch_init_rest(const Sim &S, void *A, cudaStream_t st) {
+    if (S.precision == LBMD_FP16DEV) k_init_rest<1><<<4 * 152, 256, 0, st>>>(S, A);
+    else k_init_rest<0><<<4 * 152, 256, 0, st>>>(S, A);
+    return cudaGetLastError();
+}
+
+// rho, ux, uy, uz in staging rows 15..18 -> f_eq(rho, u) in rows 0..18 (fp32 full values)
+__global__ void k_feq_to_staging(const Sim S, float *stg) {
+    const size_t ns = (size_t)S.ns;
+    const size_t total = ns * S.n_real;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = t / ns, s = t - r * ns;
+        float *f = stg + r * Q * ns + s;
+        const float rho = f[15 * ns], ux = f[16 * ns], uy = f[17 * ns], uz = f[18 * ns];
+        const bool sol = S.solid[s] != 0;
+        const float usq = 1.5f * (ux * ux + uy * uy + uz * uz);
+        float out[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const float cu = 3.0f * ((float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz);
+            out[i] = sol ? 0.0f : wq(i) * rho * (1.0f + cu + 0.5f * cu * cu - usq);
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f[i * ns] = out[i];
+    }
+}
+
+cudaError_t launch_feq_to_staging(const Sim &S, float *staging, cudaStream_t st) {
+    k_feq_to_staging<<<4 * 152, 256, 0, st>>>(S, staging);
+    return cudaGetLastError();
+}
+
+// pulled populations f^n (what the next step starts from) -> staging, full fp32 values
+template <int PREC>
+__global__ void k_pull_to_staging(const Sim S, const void *Av, float *stg) {
+    using T = typename PopT<PREC>::T;
+    const size_t ns = (size_t)S.ns;
+    const size_t total = ns * S.n_real;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = t / ns, s = t - r * ns;
+        const T *A = reinterpret_cast<const T *>(Av) + r * Q * ns;
+        float *f = stg + r * Q * ns + s;
+        const uint32_t lm = S.link[s];
+        const int x = (int)(s % S.nx), y = (int)((s / S.nx) % S.ny), z = (int)(s / ((size_t)S.nx * S.ny));
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            float v = 0.0f;
+            if (!(lm & SOLID_BIT)) {
+                uint32_t idx;
+                if ((lm >> i) & 1u) idx = (uint32_t)(opp(i) * ns + s);
+                else
+                    idx = (uint32_t)(i * ns + wrapi(x - cx(i), S.nx) +
+                                     (size_t)S.nx * (wrapi(y - cy(i), S.ny) + (size_t)S.ny * wrapi(z - cz(i), S.nz)));
+                v = wq(i) + load_dev(A, idx, wq(i));
+            }
+            f[i * ns] = v;
+        }
+    }
+}
+
+cudaError_t launch_pull_to_staging(const Sim &S, const void *A, float *staging, cudaStream_t st) {
+    if (S.precision == LBMD_FP16DEV) k_pull_to_staging<1><<<4 * 152, 256, 0, st>>>(S, A, staging);
+    else k_pull_to_staging<0><<<4 * 152, 256, 0, st>>>(S, A, staging);
+    return cudaGetLastError();
+}
+
+// inverse of the pull: A_i(y) = f_i(y + c_i), or f_opp(i)(y) when y + c_i is solid
+template <int PREC>
+__global__ void k_push_from_staging(const Sim S, const float *stg, void *Av) {
+    using T = typename PopT<PREC>::T;
+    const size_t ns = (size_t)S.ns;
+    const size_t total = ns * S.n_real;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = t / ns, s = t - r * ns;
+        T *A = reinterpret_cast<T *>(Av) + r * Q * ns;
+        const float *f = stg + r * Q * ns;
+        const uint32_t lm = S.link[s];
+        const int x = (int)(s % S.nx), y = (int)((s / S.nx) % S.ny), z = (int)(s / ((size_t)S.nx * S.ny));
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            float v = 0.0f;
+            if (!(lm & SOLID_BIT)) {
+                if ((lm >> opp(i)) & 1u) v = f[opp(i) * ns + s];
+                else
+                    v = f[i * ns + wrapi(x + cx(i), S.nx) +
+                          (size_t)S.nx * (wrapi(y + cy(i), S.ny) + (size_t)S.ny * wrapi(z + cz(i), S.nz))];
+                store_dev(A, (uint32_t)(i * ns + s), v - wq(i), wq(i));
+            } else {
+                store_dev(A, (uint32_t)(i * ns + s), 0.0f, 0.0f);
+            }
+        }
+    }
+}
+
+cudaError_t launch_push_from_staging(const Sim &S, const float *staging, void *A, cudaStream_t st) {
+    if (S.precision == LBMD_FP16DEV) k_push_from_staging<1><<<4 * 152, 256, 0, st>>>(S, staging, A);
+    else k_push_from_staging<0><<<4 * 152, 256, 0, st>>>(S, staging, A);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmd

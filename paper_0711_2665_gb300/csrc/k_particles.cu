@@ -1,0 +1,609 @@
+// k_particles.cu -- bead side of the coupled LB-MD step, one thread block per
+// realization, one thread per bead:
+//   1. gather: fluid velocity at every bead from the populations the step
+//      starts from (trilinear over fluid corners), frozen for the MD cycle
+//      (Sec. II, text after Eq. 21); one warp per bead, 4 lanes per corner;
+//   2. MD cycle (Sec. II, Eq. 22 as multiple-time-step velocity Verlet):
+//      M outer steps whose half kicks apply the pore field, the friction
+//      gamma (u_p - v) and Philox noise (Eqs. 12, 13, 15), around M^b inner
+//      velocity-Verlet steps of the conservative forces (harmonic bonds Eq. 19,
+//      angular term, WCA between beads Eq. 14 and with solid sites), the
+//      momentum handed over by the fluid accumulated in J;
+//   3. spread: G(x) -= W(x - r_p) J_p with the weights of step 1, as 2^40
+//      fixed-point integer atomics (order-independent, so runs repeat bit for
+//      bit), and the (bead, corner) list the source pass walks.
+// Bead-bead pairs come from a Verlet list (cut-off + skin) built from a cell
+// hash in shared memory; it is rebuilt whenever a bead has moved more than
+// half the skin since the last build, so the pair set equals all pairs inside
+// the cut-off at every force evaluation.
+#include "lbmd_internal.cuh"
+
+namespace lbmd {
+
+struct PSmem {
+    float4 *ph[2], *pl[2];  // positions hi / lo, double buffered
+    float4 *ups;            // gathered fluid velocity, later the impulse J
+    uint16_t *nbr;          // [ncap][NBR_CAP]
+    uint32_t *wal;          // [ncap][WALL_CAP] packed solid-site coordinates
+    int *hkey, *hhead;      // [HASH_SIZE]
+    int16_t *hnext;         // [ncap]
+    uint8_t *nn, *nw;       // [ncap]
+};
+
+__host__ __device__ inline size_t psmem_layout(int ncap, PSmem *p, char *base) {
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o += (bytes + 15) & ~(size_t)15; return base + at; };
+    char *ph0 = take(16 * (size_t)ncap), *ph1 = take(16 * (size_t)ncap);
+    char *pl0 = take(16 * (size_t)ncap), *pl1 = take(16 * (size_t)ncap);
+    char *ups = take(16 * (size_t)ncap);
+    char *nbr = take(2 * (size_t)NBR_CAP * ncap);
+    char *wal = take(4 * (size_t)WALL_CAP * ncap);
+    char *hkey = take(4 * (size_t)HASH_SIZE), *hhead = take(4 * (size_t)HASH_SIZE);
+    char *hnext = take(2 * (size_t)ncap);
+    char *nn = take((size_t)ncap), *nw = take((size_t)ncap);
+    if (p) {
+        p->ph[0] = (float4 *)ph0; p->ph[1] = (float4 *)ph1;
+        p->pl[0] = (float4 *)pl0; p->pl[1] = (float4 *)pl1;
+        p->ups = (float4 *)ups;
+        p->nbr = (uint16_t *)nbr; p->wal = (uint32_t *)wal;
+        p->hkey = (int *)hkey; p->hhead = (int *)hhead; p->hnext = (int16_t *)hnext;
+        p->nn = (uint8_t *)nn; p->nw = (uint8_t *)nw;
+    }
+    return o;
+}
+
+size_t particle_smem_bytes(int threads) { return psmem_layout(threads, nullptr, nullptr); }
+
+int particle_threads(const Sim &S) { return max(32, ((S.max_beads + 31) / 32) * 32); }
+
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+// a - b for two unwrapped float-float positions (bonded neighbours: no minimum image)
+__device__ __forceinline__ float3 ffsub(float4 ah, float4 al, float4 bh, float4 bl) {
+    return make_float3((ah.x - bh.x) + (al.x - bl.x), (ah.y - bh.y) + (al.y - bl.y), (ah.z - bh.z) + (al.z - bl.z));
+}
+
+// ---------------------------------------------------------------------------
+// lattice corner c (0..7) of the cell holding a bead at wrapped (xw, yw, zw):
+// site index and raw trilinear weight (0 on solid sites)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void corner_of(const Sim &S, float xw, float yw, float zw, int c, int &xi, int &yi,
+                                          int &zi, int &node, float &w) {
+    const int x0 = (int)floorf(xw), y0 = (int)floorf(yw), z0 = (int)floorf(zw);
+    const float fx = xw - (float)x0, fy = yw - (float)y0, fz = zw - (float)z0;
+    const int a = c & 1, b = (c >> 1) & 1, d = c >> 2;
+    xi = wrapi(x0 + a, S.nx);
+    yi = wrapi(y0 + b, S.ny);
+    zi = wrapi(z0 + d, S.nz);
+    node = xi + S.nx * (yi + S.ny * zi);
+    w = (a ? fx : 1.0f - fx) * (b ? fy : 1.0f - fy) * (d ? fz : 1.0f - fz);
+    if (S.solid[node]) w = 0.0f;
+}
+
+// sum over the 8 corners held by lanes 4c..4c+3 (same tree in gather and spread)
+__device__ __forceinline__ float corner_sum(float v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 16);
+    return v;
+}
+__device__ __forceinline__ float sub_sum(float v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    return v;
+}
+
+// Fluid velocity at one bead, computed by a whole warp: lanes 4c..4c+3 pull the
+// 19 populations of corner c (links i with i % 4 == lane % 4), form rho and
+// rho u there, and the corners are combined with the renormalised weights.
+template <typename T>
+__device__ __forceinline__ float3 gather_warp(const Sim &S, const T *__restrict__ A, float xw, float yw, float zw) {
+    const int lane = threadIdx.x & 31, c = lane >> 2, sub = lane & 3;
+    int xi, yi, zi, node;
+    float w;
+    corner_of(S, xw, yw, zw, c, xi, yi, zi, node, w);
+    const float wsum = corner_sum(sub == 0 ? w : 0.0f);
+    float m = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+    if (w > 0.0f) {
+        const uint32_t lm = __ldg(S.link + node);
+        const uint32_t ns = (uint32_t)S.ns;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if ((i & 3) != sub) continue;
+            uint32_t idx;
+            if ((lm >> i) & 1u) idx = (uint32_t)opp(i) * ns + (uint32_t)node;
+            else
+                idx = (uint32_t)i * ns +
+                      (uint32_t)(wrapi(xi - cx(i), S.nx) + S.nx * (wrapi(yi - cy(i), S.ny) + S.ny * wrapi(zi - cz(i), S.nz)));
+            const float f = wq(i) + load_dev_cg(A, idx, wq(i));
+            m += f;
+            jx += (float)cx(i) * f;
+            jy += (float)cy(i) * f;
+            jz += (float)cz(i) * f;
+        }
+    }
+    m = sub_sum(m); jx = sub_sum(jx); jy = sub_sum(jy); jz = sub_sum(jz);
+    float ux = 0.f, uy = 0.f, uz = 0.f;
+    if (w > 0.0f && m > 0.0f && sub == 0) { ux = w * (jx / m); uy = w * (jy / m); uz = w * (jz / m); }
+    ux = corner_sum(ux); uy = corner_sum(uy); uz = corner_sum(uz);
+    if (wsum > 0.0f) return make_float3(ux / wsum, uy / wsum, uz / wsum);
+    return make_float3(0.f, 0.f, 0.f);
+}
+
+// ---------------------------------------------------------------------------
+// conservative (fast) forces on bead p
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void bend_terms(float3 b1, float3 b2, float kappa, float3 &d1, float3 &d2) {
+    const float l1s = dot3(b1, b1), l2s = dot3(b2, b2), dt = dot3(b1, b2);
+    const float3 cr = cross3(b1, b2);
+    const float crn = sqrtf(dot3(cr, cr));
+    const float inv12 = rsqrtf(l1s * l2s);
+    const float c = dt * inv12, sn = crn * inv12;
+    const float phi = atan2f(crn, dt);
+    const float A = sn > 1e-6f ? kappa * phi / sn : (c > 0.0f ? kappa : 0.0f);
+    d1 = A * (inv12 * b2 - (c / l1s) * b1);  // A dcos/db1
+    d2 = A * (inv12 * b1 - (c / l2s) * b2);  // A dcos/db2
+}
+
+__device__ __forceinline__ float wca_coef(float r2, float eps, float sig2) {
+    const float sr2 = sig2 / r2;
+    const float sr6 = sr2 * sr2 * sr2;
+    return 24.0f * eps * (2.0f * sr6 * sr6 - sr6) / r2;
+}
+
+__device__ float3 fast_force(const Sim &S, const PSmem &sm, int buf, int p, int N, float4 mh, float4 ml) {
+    const float4 *ph = sm.ph[buf], *pl = sm.pl[buf];
+    float3 F = make_float3(0.f, 0.f, 0.f);
+    const bool m1 = p >= 1, m2 = p >= 2, p1 = p + 1 < N, p2 = p + 2 < N;
+    float4 hm1 = mh, lm1 = ml, hm2 = mh, lm2 = ml, hp1 = mh, lp1 = ml, hp2 = mh, lp2 = ml;
+    if (m1) { hm1 = ph[p - 1]; lm1 = pl[p - 1]; }
+    if (m2) { hm2 = ph[p - 2]; lm2 = pl[p - 2]; }
+    if (p1) { hp1 = ph[p + 1]; lp1 = pl[p + 1]; }
+    if (p2) { hp2 = ph[p + 2]; lp2 = pl[p + 2]; }
+    const float3 b0 = ffsub(hm1, lm1, hm2, lm2);  // r_{p-1} - r_{p-2}
+    const float3 b1 = ffsub(mh, ml, hm1, lm1);    // r_p - r_{p-1}
+    const float3 b2 = ffsub(hp1, lp1, mh, ml);    // r_{p+1} - r_p
+    const float3 b3 = ffsub(hp2, lp2, hp1, lp1);  // r_{p+2} - r_{p+1}
+    // harmonic bonds (Eq. 19)
+    if (m1) {
+        const float len = sqrtf(dot3(b1, b1));
+        F = F - (S.k_bond * (len - S.r0) / len) * b1;
+    }
+    if (p1) {
+        const float len = sqrtf(dot3(b2, b2));
+        F = F + (S.k_bond * (len - S.r0) / len) * b2;
+    }
+    // angular term kappa phi^2 / 2 at beads p-1, p, p+1
+    if (S.kappa != 0.0f) {
+        float3 d1, d2;
+        if (m2) { bend_terms(b0, b1, S.kappa, d1, d2); F = F + d2; }
+        if (m1 && p1) { bend_terms(b1, b2, S.kappa, d1, d2); F = F + d1 - d2; }
+        if (p2) { bend_terms(b2, b3, S.kappa, d1, d2); F = F - d1; }
+    }
+    // WCA with listed non-bonded beads (Eq. 14 cut at 2^(1/6) sigma)
+    const float fnx = (float)S.nx, fny = (float)S.ny, fnz = (float)S.nz;
+    const int nn = sm.nn[p];
+    for (int k = 0; k < nn; ++k) {
+        const int q = sm.nbr[p * NBR_CAP + k];
+        const float4 qh = ph[q], ql = pl[q];
+        const float3 d = make_float3(ff_diff(mh.x, ml.x, qh.x, ql.x, fnx), ff_diff(mh.y, ml.y, qh.y, ql.y, fny),
+                                     ff_diff(mh.z, ml.z, qh.z, ql.z, fnz));
+        const float r2 = dot3(d, d);
+        if (r2 < S.lj_rc2) F = F + wca_coef(r2, S.lj_eps, S.lj_sig2) * d;
+    }
+    // WCA with listed solid sites
+    const int nw = sm.nw[p];
+    for (int k = 0; k < nw; ++k) {
+        const uint32_t pk = sm.wal[p * WALL_CAP + k];
+        const float X = (float)(pk & 0xfffu), Y = (float)((pk >> 12) & 0x3ffu), Z = (float)(pk >> 22);
+        const float3 d = make_float3(ff_diff(mh.x, ml.x, X, 0.f, fnx), ff_diff(mh.y, ml.y, Y, 0.f, fny),
+                                     ff_diff(mh.z, ml.z, Z, 0.f, fnz));
+        const float r2 = dot3(d, d);
+        if (r2 < S.wall_rc2) F = F + wca_coef(r2, S.wall_eps, S.wall_sig2) * d;
+    }
+    return F;
+}
+
+// ---------------------------------------------------------------------------
+// Verlet lists: cell hash (cells >= list radius, >= 3 per axis) or all pairs
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int cell_slot(int key) { return (int)(((uint32_t)key * 2654435761u) >> 21); }
+
+__device__ __forceinline__ void list_insert(uint16_t *lst, int &n, int q) {
+    int pos = n;
+    while (pos > 0 && lst[pos - 1] > q) {
+        if (pos < NBR_CAP) lst[pos] = lst[pos - 1];
+        --pos;
+    }
+    if (pos < NBR_CAP) lst[pos] = (uint16_t)q;
+    ++n;
+}
+
+__device__ void build_lists(const Sim &S, const PSmem &sm, int buf, int p, int N, bool own, float4 mh, float4 ml,
+                            int *s_flag, int *s_err) {
+    const bool hashed = S.ncell[0] >= 3 && S.ncell[1] >= 3 && S.ncell[2] >= 3;
+    const float fnx = (float)S.nx, fny = (float)S.ny, fnz = (float)S.nz;
+    if (hashed)
+        for (int k = threadIdx.x; k < HASH_SIZE; k += blockDim.x) { sm.hkey[k] = -1; sm.hhead[k] = -1; }
+    __syncthreads();
+    if (threadIdx.x == 0) *s_flag = 0;
+    float xw = 0.f, yw = 0.f, zw = 0.f;
+    int ci = 0, cj = 0, ck = 0;
+    if (own) {
+        xw = ff_wrap(mh.x, ml.x, fnx);
+        yw = ff_wrap(mh.y, ml.y, fny);
+        zw = ff_wrap(mh.z, ml.z, fnz);
+        ci = min((int)(xw * (float)S.ncell[0] / fnx), S.ncell[0] - 1);
+        cj = min((int)(yw * (float)S.ncell[1] / fny), S.ncell[1] - 1);
+        ck = min((int)(zw * (float)S.ncell[2] / fnz), S.ncell[2] - 1);
+        if (hashed) {
+            const int key = ci + S.ncell[0] * (cj + S.ncell[1] * ck);
+            int slot = cell_slot(key);
+            for (int probe = 0; probe < HASH_SIZE; ++probe) {
+                const int prev = atomicCAS(sm.hkey + slot, -1, key);
+                if (prev == -1 || prev == key) break;
+                slot = (slot + 1) & (HASH_SIZE - 1);
+            }
+            sm.hnext[p] = (int16_t)atomicExch(sm.hhead + slot, p);
+        }
+    }
+    __syncthreads();
+    if (!own) return;
+    const float4 *ph = sm.ph[buf], *pl = sm.pl[buf];
+    uint16_t *lst = sm.nbr + p * NBR_CAP;
+    int n = 0;
+    auto consider = [&](int q) {
+        if (q == p || q == p - 1 || q == p + 1) return;
+        const float4 qh = ph[q], ql = pl[q];
+        const float dx = ff_diff(mh.x, ml.x, qh.x, ql.x, fnx), dy = ff_diff(mh.y, ml.y, qh.y, ql.y, fny),
+                    dz = ff_diff(mh.z, ml.z, qh.z, ql.z, fnz);
+        if (dx * dx + dy * dy + dz * dz < S.rl2) list_insert(lst, n, q);
+    };
+    if (hashed) {
+        for (int dk = -1; dk <= 1; ++dk)
+            for (int dj = -1; dj <= 1; ++dj)
+                for (int di = -1; di <= 1; ++di) {
+                    const int key = wrapi(ci + di, S.ncell[0]) +
+                                    S.ncell[0] * (wrapi(cj + dj, S.ncell[1]) + S.ncell[1] * wrapi(ck + dk, S.ncell[2]));
+                    int slot = cell_slot(key);
+                    for (int probe = 0; probe < HASH_SIZE; ++probe) {
+                        const int kk = sm.hkey[slot];
+                        if (kk == key) {
+                            for (int q = sm.hhead[slot], guard = 0; q >= 0 && guard < N; q = sm.hnext[q], ++guard)
+                                consider(q);
+                            break;
+                        }
+                        if (kk == -1) break;
+                        slot = (slot + 1) & (HASH_SIZE - 1);
+                    }
+                }
+    } else {
+        for (int q = 0; q < N; ++q) consider(q);
+    }
+    if (n > NBR_CAP) { atomicOr(s_err, ST_CAPACITY); n = NBR_CAP; }
+    sm.nn[p] = (uint8_t)n;
+    // solid sites within the wall-list radius
+    int m = 0;
+    const int x0 = (int)floorf(xw - S.rlw), x1 = (int)floorf(xw + S.rlw);
+    const int y0 = (int)floorf(yw - S.rlw), y1 = (int)floorf(yw + S.rlw);
+    const int z0 = (int)floorf(zw - S.rlw), z1 = (int)floorf(zw + S.rlw);
+    for (int Z = z0; Z <= z1; ++Z)
+        for (int Y = y0; Y <= y1; ++Y)
+            for (int X = x0; X <= x1; ++X) {
+                const int xx = wrap_any(X, S.nx), yy = wrap_any(Y, S.ny), zz = wrap_any(Z, S.nz);
+                if (!S.solid[xx + S.nx * (yy + S.ny * zz)]) continue;
+                const float dx = xw - (float)X, dy = yw - (float)Y, dz = zw - (float)Z;
+                if (dx * dx + dy * dy + dz * dz >= S.rlw2) continue;
+                if (m < WALL_CAP) sm.wal[p * WALL_CAP + m] = (uint32_t)xx | ((uint32_t)yy << 12) | ((uint32_t)zz << 22);
+                ++m;
+            }
+    if (m > WALL_CAP) { atomicOr(s_err, ST_CAPACITY); m = WALL_CAP; }
+    sm.nw[p] = (uint8_t)m;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 block sum of NV values per thread; result valid in thread 0
+// ---------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double (*red)[NV]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[warp][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NV; ++k) v[k] = 0.0;
+        for (int w = 0; w < nw; ++w)
+            for (int k = 0; k < NV; ++k) v[k] += red[w][k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the particle kernel: one block per realization, one thread per bead
+// ---------------------------------------------------------------------------
+template <int PREC>
+__global__ void __launch_bounds__(1024) k_particles(const Sim S, const void *__restrict__ Av) {
+    using T = typename PopT<PREC>::T;
+    extern __shared__ __align__(16) char smem_raw[];
+    __shared__ int s_flag, s_err;
+    __shared__ double red[32][9];
+    PSmem sm;
+    psmem_layout(blockDim.x, &sm, smem_raw);
+
+    const int r = blockIdx.x;
+    const int off = S.bead_off[r];
+    const int N = S.bead_off[r + 1] - off;
+    const int p = threadIdx.x;
+    const bool own = p < N;
+    const long long step = S.ctrl->step;
+    const T *A = reinterpret_cast<const T *>(Av) + (size_t)r * Q * S.ns;
+    const float fnx = (float)S.nx, fny = (float)S.ny, fnz = (float)S.nz;
+    if (threadIdx.x == 0) { s_flag = 0; s_err = 0; }
+
+    float4 mh = make_float4(0.f, 0.f, 0.f, 0.f), ml = mh;
+    float3 v = make_float3(0.f, 0.f, 0.f);
+    if (own) {
+        mh = S.r_hi[off + p];
+        ml = S.r_lo[off + p];
+        const float4 vv = S.v[off + p];
+        v = make_float3(vv.x, vv.y, vv.z);
+        sm.ph[0][p] = mh;
+        sm.pl[0][p] = ml;
+    }
+    __syncthreads();
+
+    // 1. fluid velocity at the beads (warp per bead)
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int q = warp; q < N; q += nwarps) {
+        const float4 qh = sm.ph[0][q], ql = sm.pl[0][q];
+        const float3 u = gather_warp(S, A, ff_wrap(qh.x, ql.x, fnx), ff_wrap(qh.y, ql.y, fny), ff_wrap(qh.z, ql.z, fnz));
+        if ((threadIdx.x & 31) == 0) sm.ups[q] = make_float4(u.x, u.y, u.z, 0.f);
+    }
+    // neighbour and wall lists at the starting positions (contains barriers)
+    build_lists(S, sm, 0, p, N, own, mh, ml, &s_flag, &s_err);
+    __syncthreads();
+
+    float3 up = make_float3(0.f, 0.f, 0.f);
+    if (own) { const float4 t = sm.ups[p]; up = make_float3(t.x, t.y, t.z); }
+
+    // per-step bead diagnostics at the starting state
+    {
+        double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        if (own) {
+            const float xw = ff_wrap(mh.x, ml.x, fnx), yw = ff_wrap(mh.y, ml.y, fny), zw = ff_wrap(mh.z, ml.z, fnz);
+            const float Fe = in_channel(S, xw, yw, zw) ? S.E : 0.0f;
+            const double X = (double)mh.x + (double)ml.x;
+            acc[0] = v.x; acc[1] = v.y; acc[2] = v.z;
+            acc[3] = X; acc[4] = (double)mh.y + (double)ml.y; acc[5] = (double)mh.z + (double)ml.z;
+            acc[6] = (S.wall_x >= 0 && X > (double)S.wall_x + 0.5) ? 1.0 : 0.0;
+            acc[7] = (double)S.gamma * ((double)v.x * up.x + (double)v.y * up.y + (double)v.z * up.z);
+            acc[8] = (double)Fe * v.x;
+        }
+        block_sum<9>(acc, red);
+        if (threadIdx.x == 0) {
+            lbmd_diag *row = S.ring + (size_t)r * LBMD_DIAG_RING + (step % LBMD_DIAG_RING);
+            row->step = step;
+            row->p_beads[0] = acc[0]; row->p_beads[1] = acc[1]; row->p_beads[2] = acc[2];
+            const double inv = N > 0 ? 1.0 / N : 0.0;
+            row->com[0] = acc[3] * inv; row->com[1] = acc[4] * inv; row->com[2] = acc[5] * inv;
+            row->n_translocated = acc[6];
+            row->dWH_dt = acc[7];
+            row->dWE_dt = acc[8];
+        }
+    }
+
+    // 2. MD cycle
+    const float dt = 1.0f / (float)S.M, h = 0.5f * dt;
+    const float dtb = dt / (float)S.Mb, hb = 0.5f * dtb;
+    const float amp = S.kT > 0.0f ? sqrtf(2.0f * S.gamma * S.kT / dt) : 0.0f;
+    float3 J = make_float3(0.f, 0.f, 0.f);
+    float4 bh = mh, bl = ml;  // position at the last list build
+    int buf = 0;
+    float3 ff = make_float3(0.f, 0.f, 0.f);
+    if (own) ff = fast_force(S, sm, buf, p, N, mh, ml);
+    for (int sub = 0; sub < S.M; ++sub) {
+        float3 xi = make_float3(0.f, 0.f, 0.f);
+        if (own && amp > 0.0f) xi = amp * gauss3(S.seed, (uint32_t)r, (uint32_t)p, step, (uint32_t)sub);
+        if (own) {  // first half kick: field + friction + noise
+            const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx), ff_wrap(mh.y, ml.y, fny), ff_wrap(mh.z, ml.z, fnz));
+            const float3 fl = S.gamma * (up - v) + xi;
+            v = v + h * (make_float3(ch ? S.E : 0.0f, 0.f, 0.f) + fl);
+            J = J + h * fl;
+        }
+        for (int b = 0; b < S.Mb; ++b) {
+            if (own) {
+                v = v + hb * ff;
+                ff_add(mh.x, ml.x, dtb * v.x);
+                ff_add(mh.y, ml.y, dtb * v.y);
+                ff_add(mh.z, ml.z, dtb * v.z);
+                sm.ph[buf ^ 1][p] = mh;
+                sm.pl[buf ^ 1][p] = ml;
+                const float3 dd = ffsub(mh, ml, bh, bl);
+                if (dot3(dd, dd) > S.skin_half2) s_flag = 1;
+            }
+            __syncthreads();
+            buf ^= 1;
+            if (s_flag) {
+                build_lists(S, sm, buf, p, N, own, mh, ml, &s_flag, &s_err);
+                bh = mh;
+                bl = ml;
+            }
+            if (own) {
+                ff = fast_force(S, sm, buf, p, N, mh, ml);
+                v = v + hb * ff;
+            }
+        }
+        if (own) {  // second half kick with the same noise
+            const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx), ff_wrap(mh.y, ml.y, fny), ff_wrap(mh.z, ml.z, fnz));
+            const float3 fl = S.gamma * (up - v) + xi;
+            v = v + h * (make_float3(ch ? S.E : 0.0f, 0.f, 0.f) + fl);
+            J = J + h * fl;
+        }
+    }
+    if (own) sm.ups[p] = make_float4(J.x, J.y, J.z, 0.f);
+    __syncthreads();
+
+    // 3. spread -W J onto the fluid corners of the starting position (warp per bead)
+    {
+        const int lane = threadIdx.x & 31, c = lane >> 2, sub = lane & 3;
+        const size_t ns = (size_t)S.ns;
+        for (int q = warp; q < N; q += nwarps) {
+            const float4 qh = S.r_hi[off + q], ql = S.r_lo[off + q];
+            int xi, yi, zi, node;
+            float w;
+            corner_of(S, ff_wrap(qh.x, ql.x, fnx), ff_wrap(qh.y, ql.y, fny), ff_wrap(qh.z, ql.z, fnz), c, xi, yi, zi,
+                      node, w);
+            const float wsum = corner_sum(sub == 0 ? w : 0.0f);
+            const float W = wsum > 0.0f ? w / wsum : 0.0f;
+            const float4 Jq = sm.ups[q];
+            if (sub < 3 && W > 0.0f) {
+                const float comp = sub == 0 ? Jq.x : (sub == 1 ? Jq.y : Jq.z);
+                const long long fx = __float2ll_rn(-W * comp * FIX_SCALE_F);
+                atomicAdd(S.G + ((size_t)r * 3 + sub) * ns + node, (unsigned long long)fx);
+            }
+            if (sub == 0) S.pair_node[(size_t)(off + q) * 8 + c] = W > 0.0f ? (int)((size_t)r * ns + node) : -1;
+        }
+    }
+    __syncthreads();
+
+    if (own) {
+        ff_norm(mh.x, ml.x);
+        ff_norm(mh.y, ml.y);
+        ff_norm(mh.z, ml.z);
+        S.r_hi[off + p] = mh;
+        S.r_lo[off + p] = ml;
+        S.v[off + p] = make_float4(v.x, v.y, v.z, 0.f);
+        S.up[off + p] = make_float4(up.x, up.y, up.z, 0.f);
+        S.J[off + p] = make_float4(J.x, J.y, J.z, 0.f);
+        if (!isfinite(mh.x + mh.y + mh.z + v.x + v.y + v.z)) atomicOr(&s_err, ST_NONFINITE);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_err) atomicOr(&S.ctrl->status, s_err);
+}
+
+cudaError_t launch_particles(const Sim &S, const void *A, cudaStream_t st) {
+    const int threads = particle_threads(S);
+    const size_t smem = particle_smem_bytes(threads);
+    cudaError_t e;
+    if (S.precision == LBMD_FP16DEV) {
+        e = cudaFuncSetAttribute(k_particles<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_particles<1><<<S.n_real, threads, smem, st>>>(S, A);
+    } else {
+        e = cudaFuncSetAttribute(k_particles<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_particles<0><<<S.n_real, threads, smem, st>>>(S, A);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// bead observables at the current state (one block per realization)
+// ---------------------------------------------------------------------------
+template <int PREC>
+__global__ void __launch_bounds__(1024) k_bead_observables(const Sim S, const void *__restrict__ Av) {
+    using T = typename PopT<PREC>::T;
+    extern __shared__ __align__(16) char smem_raw[];
+    __shared__ double red[32][9];
+    PSmem sm;
+    psmem_layout(blockDim.x, &sm, smem_raw);
+    const int r = blockIdx.x;
+    const int off = S.bead_off[r];
+    const int N = S.bead_off[r + 1] - off;
+    const int p = threadIdx.x;
+    const bool own = p < N;
+    const T *A = reinterpret_cast<const T *>(Av) + (size_t)r * Q * S.ns;
+    const float fnx = (float)S.nx, fny = (float)S.ny, fnz = (float)S.nz;
+    float4 mh = make_float4(0.f, 0.f, 0.f, 0.f), ml = mh, vv = mh;
+    if (own) {
+        mh = S.r_hi[off + p];
+        ml = S.r_lo[off + p];
+        vv = S.v[off + p];
+        sm.ph[0][p] = mh;
+        sm.pl[0][p] = ml;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int q = warp; q < N; q += nwarps) {
+        const float4 qh = sm.ph[0][q], ql = sm.pl[0][q];
+        const float3 u = gather_warp(S, A, ff_wrap(qh.x, ql.x, fnx), ff_wrap(qh.y, ql.y, fny), ff_wrap(qh.z, ql.z, fnz));
+        if ((threadIdx.x & 31) == 0) sm.ups[q] = make_float4(u.x, u.y, u.z, 0.f);
+    }
+    __syncthreads();
+    const double X = (double)mh.x + (double)ml.x, Y = (double)mh.y + (double)ml.y, Z = (double)mh.z + (double)ml.z;
+    const bool tr = own && S.wall_x >= 0 && X > (double)S.wall_x + 0.5;
+    double a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (own) {
+        const float4 u = sm.ups[p];
+        const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx), ff_wrap(mh.y, ml.y, fny), ff_wrap(mh.z, ml.z, fnz));
+        a[0] = vv.x; a[1] = vv.y; a[2] = vv.z;
+        a[3] = X; a[4] = Y; a[5] = Z;
+        a[6] = tr ? 1.0 : 0.0;
+        a[7] = (double)S.gamma * ((double)vv.x * u.x + (double)vv.y * u.y + (double)vv.z * u.z);
+        a[8] = ch ? (double)S.E * vv.x : 0.0;
+    }
+    block_sum<9>(a, red);
+    __shared__ double s_sum[9];
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 9; ++k) s_sum[k] = a[k];
+    // centres of the translocated / untranslocated parts
+    double c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (own) {
+        const int o = tr ? 4 : 0;
+        c[o] = X; c[o + 1] = Y; c[o + 2] = Z; c[o + 3] = 1.0;
+    }
+    __shared__ double red8[32][8];
+    block_sum<8>(c, red8);
+    __shared__ double s_c[8];
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 8; ++k) s_c[k] = c[k];
+    __syncthreads();
+    double g2[2] = {0, 0};
+    if (own) {
+        const int o = tr ? 4 : 0;
+        const double n = s_c[o + 3];
+        const double dx = X - s_c[o] / n, dy = Y - s_c[o + 1] / n, dz = Z - s_c[o + 2] / n;
+        g2[tr ? 1 : 0] = dx * dx + dy * dy + dz * dz;
+    }
+    __shared__ double red2[32][2];
+    block_sum<2>(g2, red2);
+    if (threadIdx.x == 0) {
+        lbmd_obs *o = S.obs + r;
+        o->p_beads[0] = s_sum[0]; o->p_beads[1] = s_sum[1]; o->p_beads[2] = s_sum[2];
+        const double inv = N > 0 ? 1.0 / N : 0.0;
+        o->com[0] = s_sum[3] * inv; o->com[1] = s_sum[4] * inv; o->com[2] = s_sum[5] * inv;
+        o->n_translocated = s_sum[6];
+        o->dWH_dt = s_sum[7];
+        o->dWE_dt = s_sum[8];
+        o->rg_untranslocated = s_c[3] > 0 ? sqrt(g2[0] / s_c[3]) : 0.0;
+        o->rg_translocated = s_c[7] > 0 ? sqrt(g2[1] / s_c[7]) : 0.0;
+    }
+}
+
+cudaError_t launch_bead_observables(const Sim &S, const void *A, cudaStream_t st) {
+    const int threads = particle_threads(S);
+    const size_t smem = particle_smem_bytes(threads);
+    cudaError_t e;
+    if (S.precision == LBMD_FP16DEV) {
+        e = cudaFuncSetAttribute(k_bead_observables<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_bead_observables<1><<<S.n_real, threads, smem, st>>>(S, A);
+    } else {
+        e = cudaFuncSetAttribute(k_bead_observables<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_bead_observables<0><<<S.n_real, threads, smem, st>>>(S, A);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lbmd

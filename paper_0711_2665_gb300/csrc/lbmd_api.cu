@@ -1,0 +1,710 @@
+// lbmd_api.cu -- host side of the C ABI declared in include/lbmd.h: argument
+// checks, the layout of the caller's device buffer, geometry preprocessing,
+// the per-step launch sequence (particle kernel and stream-collide kernel
+// concurrently on two streams, then the source pass), CUDA-graph replay,
+// per-kernel event timing and the tile autotuner.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbmd_internal.cuh"
+
+using namespace lbmd;
+
+namespace {
+
+constexpr int K_PARTICLES = 0, K_STREAM_COLLIDE = 1, K_SOURCE = 2, K_COUNT = 3;
+const char *KNAMES[K_COUNT] = {"particles", "stream_collide", "source"};
+constexpr double SKIN = 0.5;  // Verlet-list skin (lattice units)
+
+struct Layout {
+    size_t popA, popB, staging, link, tileflag, solid, G, stamp;
+    size_t r_hi, r_lo, v, up, J, pair_node, bead_off, partial, ring, obs, ctrl, total;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct ProfRec {
+    int kernel;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct lbmd_handle {
+    lbmd_config cfg;
+    Sim S;
+    char *dbuf = nullptr;
+    size_t dbytes = 0;
+    Layout L;
+    void *popA = nullptr, *popB = nullptr;
+    float *staging = nullptr;
+    std::vector<int32_t> offsets;
+    int total_beads = 0;
+    cudaStream_t st = nullptr, aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    int by = 8, zc = 8;
+    int graph_steps = 0;
+    cudaGraphExec_t gexec = nullptr;
+    void *graph_A = nullptr;  // population buffer that was "A" when the graph was captured
+    bool capturing = false;
+    bool profiling = false;
+    std::vector<ProfRec> pending;
+    std::vector<cudaEvent_t> free_events;
+    double prof_ms[K_COUNT] = {0, 0, 0};
+    long long prof_n[K_COUNT] = {0, 0, 0};
+    long long launches = 0;
+    long long host_step = 0;
+    std::string err;
+};
+
+namespace {
+
+lbmd_status fail(lbmd_handle *h, lbmd_status s, const std::string &msg) {
+    if (h) h->err = msg;
+    return s;
+}
+
+lbmd_status cuda_fail(lbmd_handle *h, cudaError_t e, const char *where) {
+    return fail(h, LBMD_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                      \
+    do {                                                              \
+        cudaError_t e__ = (call);                                     \
+        if (e__ != cudaSuccess) return cuda_fail(h, e__, #call);      \
+    } while (0)
+
+bool config_ok(const lbmd_config *c, const int32_t *off, std::string &why) {
+    if (!c) { why = "null config"; return false; }
+    if (c->nx < 1 || c->ny < 1 || c->nz < 1) { why = "lattice dimensions must be >= 1"; return false; }
+    if (c->nx > 4096 || c->ny > 1024 || c->nz > 1024) { why = "lattice limited to 4096 x 1024 x 1024"; return false; }
+    const double ns = (double)c->nx * c->ny * c->nz;
+    if (ns * LBMD_Q >= 2147483647.0) { why = "19 * sites must stay below 2^31 per realization"; return false; }
+    if (c->n_real < 1 || (double)c->n_real * ns >= 2147483647.0) { why = "n_real must be >= 1 and n_real * sites < 2^31"; return false; }
+    if (!(c->tau > 0.5)) { why = "tau must be > 1/2"; return false; }
+    if (c->md_outer < 1 || c->md_inner < 1) { why = "md_outer and md_inner must be >= 1"; return false; }
+    if (c->precision != LBMD_FP32 && c->precision != LBMD_FP16DEV) { why = "unknown precision"; return false; }
+    if (c->reserved != 0) { why = "reserved must be 0"; return false; }
+    if (c->wall_x < -1 || c->wall_x >= c->nx) { why = "wall_x must be -1 or inside [0, nx)"; return false; }
+    if (c->pore_h < 0 || c->pore_h > c->ny || c->pore_h > c->nz) { why = "pore_h out of range"; return false; }
+    if (!(c->lj_sigma > 0) || !(c->wall_sigma > 0) || c->lj_eps < 0 || c->wall_eps < 0) { why = "WCA sigma must be > 0, eps >= 0"; return false; }
+    if (c->gamma < 0 || c->kT < 0 || c->k_bond < 0) { why = "gamma, kT, k_bond must be >= 0"; return false; }
+    if (!off) { why = "null bead_offsets"; return false; }
+    if (off[0] != 0) { why = "bead_offsets[0] must be 0"; return false; }
+    for (int r = 0; r < c->n_real; ++r) {
+        const int n = off[r + 1] - off[r];
+        if (n < 0) { why = "bead_offsets must be non-decreasing"; return false; }
+        if (n > LBMD_MAX_BEADS_PER_REALIZATION) { why = "more than 1024 beads in a realization"; return false; }
+    }
+    return true;
+}
+
+Layout layout_of(const lbmd_config *c, int total_beads) {
+    Layout L;
+    const size_t ns = (size_t)c->nx * c->ny * c->nz;
+    const size_t esz = c->precision == LBMD_FP16DEV ? 2 : 4;
+    const size_t npop = (size_t)c->n_real * LBMD_Q * ns;
+    const size_t nxt = (c->nx + 31) / 32;
+    const size_t max_blocks = nxt * c->ny * c->nz * c->n_real;  // finest tile shape (by = zc = 1)
+    const size_t nb = (size_t)std::max(total_beads, 1);
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+    L.popA = take(npop * esz);
+    L.popB = take(npop * esz);
+    L.staging = take(npop * 4);
+    L.link = take(ns * 4);
+    L.tileflag = take(nxt * c->ny * c->nz);
+    L.solid = take(ns);
+    L.G = take((size_t)c->n_real * 3 * ns * 8);
+    L.stamp = take((size_t)c->n_real * ns * 4);
+    L.r_hi = take(nb * 16);
+    L.r_lo = take(nb * 16);
+    L.v = take(nb * 16);
+    L.up = take(nb * 16);
+    L.J = take(nb * 16);
+    L.pair_node = take(nb * 8 * 4);
+    L.bead_off = take((size_t)(c->n_real + 1) * 4);
+    L.partial = take(max_blocks * 4 * sizeof(double));
+    L.ring = take((size_t)c->n_real * LBMD_DIAG_RING * sizeof(lbmd_diag));
+    L.obs = take((size_t)c->n_real * sizeof(lbmd_obs));
+    L.ctrl = take(sizeof(Ctrl));
+    L.total = o;
+    return L;
+}
+
+cudaEvent_t get_event(lbmd_handle *h) {
+    if (!h->free_events.empty()) {
+        cudaEvent_t e = h->free_events.back();
+        h->free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+lbmd_status resolve_profile(lbmd_handle *h) {
+    if (h->pending.empty()) return LBMD_OK;
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaStreamSynchronize(h->aux));
+    for (auto &p : h->pending) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, p.a, p.b));
+        h->prof_ms[p.kernel] += ms;
+        h->prof_n[p.kernel] += 1;
+        h->free_events.push_back(p.a);
+        h->free_events.push_back(p.b);
+    }
+    h->pending.clear();
+    return LBMD_OK;
+}
+
+struct ProfScope {
+    lbmd_handle *h;
+    int k;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(lbmd_handle *h_, int k_, cudaStream_t s_) : h(h_), k(k_), s(s_) {
+        if (h->profiling && !h->capturing) {
+            a = get_event(h);
+            b = get_event(h);
+            cudaEventRecord(a, s);
+        }
+    }
+    ~ProfScope() {
+        if (a) {
+            cudaEventRecord(b, s);
+            h->pending.push_back({k, a, b});
+        }
+    }
+};
+
+// one coupled step: particles (aux stream) || stream-collide (main), then source
+lbmd_status enqueue_step(lbmd_handle *h) {
+    CK(cudaEventRecord(h->ev_fork, h->st));
+    CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+    {
+        ProfScope ps(h, K_PARTICLES, h->aux);
+        CK(launch_particles(h->S, h->popA, h->aux));
+    }
+    CK(cudaEventRecord(h->ev_join, h->aux));
+    {
+        ProfScope ps(h, K_STREAM_COLLIDE, h->st);
+        CK(launch_stream_collide(h->S, h->popA, h->popB, h->by, h->zc, true, h->st));
+    }
+    CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
+    {
+        ProfScope ps(h, K_SOURCE, h->st);
+        CK(launch_source(h->S, h->popB, h->st));
+    }
+    std::swap(h->popA, h->popB);
+    h->host_step += 1;
+    h->launches += 3;
+    if (h->pending.size() > 30000) return resolve_profile(h);
+    return LBMD_OK;
+}
+
+void drop_graph(lbmd_handle *h) {
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+    h->graph_A = nullptr;
+}
+
+lbmd_status capture_graph(lbmd_handle *h) {
+    drop_graph(h);
+    if (h->graph_steps <= 0) return LBMD_OK;
+    cudaGraph_t g = nullptr;
+    h->capturing = true;
+    void *A0 = h->popA;
+    const long long s0 = h->host_step, l0 = h->launches;
+    cudaError_t e = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { h->capturing = false; return cuda_fail(h, e, "cudaStreamBeginCapture"); }
+    lbmd_status s = LBMD_OK;
+    for (int k = 0; k < h->graph_steps && s == LBMD_OK; ++k) s = enqueue_step(h);
+    e = cudaStreamEndCapture(h->st, &g);
+    h->capturing = false;
+    h->host_step = s0;
+    h->launches = l0;
+    if (s != LBMD_OK) { if (g) cudaGraphDestroy(g); return s; }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { h->gexec = nullptr; return cuda_fail(h, e, "cudaGraphInstantiate"); }
+    h->graph_A = A0;
+    if (h->popA != A0) return fail(h, LBMD_ERR_INVALID_ARG, "graph must hold an even number of steps");
+    return LBMD_OK;
+}
+
+void build_geometry(const lbmd_config *c, const uint8_t *solid, std::vector<uint32_t> &link,
+                    std::vector<uint8_t> &tile, std::vector<uint8_t> &sol, double &n_fluid) {
+    const int nx = c->nx, ny = c->ny, nz = c->nz;
+    const size_t ns = (size_t)nx * ny * nz;
+    sol.assign(solid, solid + ns);
+    for (auto &b : sol) b = b ? 1 : 0;
+    link.assign(ns, 0u);
+    n_fluid = 0;
+    static const int C[19][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
+                                 {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1}, {1, 0, -1},
+                                 {-1, 0, 1}, {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const size_t s = x + (size_t)nx * (y + (size_t)ny * z);
+                if (sol[s]) { link[s] = SOLID_BIT; continue; }
+                n_fluid += 1;
+                uint32_t m = 0;
+                for (int i = 1; i < 19; ++i) {
+                    const int sx = (x - C[i][0] + nx) % nx, sy = (y - C[i][1] + ny) % ny, sz = (z - C[i][2] + nz) % nz;
+                    if (sol[sx + (size_t)nx * (sy + (size_t)ny * sz)]) m |= 1u << i;
+                }
+                link[s] = m;
+            }
+    const int nxt = (nx + 31) / 32;
+    tile.assign((size_t)nxt * ny * nz, 0);
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x)
+                if (link[x + (size_t)nx * (y + (size_t)ny * z)]) tile[x / 32 + (size_t)nxt * (y + (size_t)ny * z)] = 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lbmd_status_string(lbmd_status s) {
+    switch (s) {
+        case LBMD_OK: return "ok";
+        case LBMD_ERR_INVALID_ARG: return "invalid argument";
+        case LBMD_ERR_CUDA: return "CUDA error";
+        case LBMD_ERR_NONFINITE: return "non-finite value in the state";
+        case LBMD_ERR_TIMEOUT: return "bounded wait timed out";
+        case LBMD_ERR_CAPACITY: return "fixed-capacity list overflowed";
+        case LBMD_ERR_BUFFER: return "device buffer too small or misaligned";
+    }
+    return "unknown status";
+}
+
+const char *lbmd_last_error(const lbmd_handle *h) { return h ? h->err.c_str() : "null handle"; }
+
+lbmd_status lbmd_required_bytes(const lbmd_config *cfg, const int32_t *bead_offsets, size_t *bytes) {
+    std::string why;
+    if (!bytes || !config_ok(cfg, bead_offsets, why)) return LBMD_ERR_INVALID_ARG;
+    *bytes = layout_of(cfg, bead_offsets[cfg->n_real]).total;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_t *bead_offsets, const double *r_init,
+                      void *device_buffer, size_t device_bytes, void *stream, lbmd_handle **out) {
+    if (!out) return LBMD_ERR_INVALID_ARG;
+    *out = nullptr;
+    std::string why;
+    if (!config_ok(cfg, bead_offsets, why) || !solid) return LBMD_ERR_INVALID_ARG;
+    lbmd_handle *h = new lbmd_handle();
+    h->cfg = *cfg;
+    h->offsets.assign(bead_offsets, bead_offsets + cfg->n_real + 1);
+    h->total_beads = bead_offsets[cfg->n_real];
+    if (h->total_beads > 0 && !r_init) { delete h; return LBMD_ERR_INVALID_ARG; }
+    h->L = layout_of(cfg, h->total_beads);
+    if (!device_buffer || ((uintptr_t)device_buffer & 255u) || device_bytes < h->L.total) {
+        delete h;
+        return LBMD_ERR_BUFFER;
+    }
+    h->dbuf = (char *)device_buffer;
+    h->dbytes = device_bytes;
+    h->st = (cudaStream_t)stream;
+    auto bail = [&](lbmd_status s) { lbmd_destroy(h); return s; };
+    {
+        int lo = 0, hi = 0;
+        cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, hi);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+        if (e != cudaSuccess) { cuda_fail(h, e, "stream/event creation"); return bail(LBMD_ERR_CUDA); }
+    }
+    const Layout &L = h->L;
+    char *b = h->dbuf;
+    h->popA = b + L.popA;
+    h->popB = b + L.popB;
+    h->staging = (float *)(b + L.staging);
+
+    // geometry on the host
+    std::vector<uint32_t> link;
+    std::vector<uint8_t> tile, sol;
+    double n_fluid = 0;
+    build_geometry(cfg, solid, link, tile, sol, n_fluid);
+
+    Sim &S = h->S;
+    memset(&S, 0, sizeof(S));
+    S.nx = cfg->nx; S.ny = cfg->ny; S.nz = cfg->nz;
+    S.ns = cfg->nx * cfg->ny * cfg->nz;
+    S.nxt = (cfg->nx + 31) / 32;
+    S.n_real = cfg->n_real;
+    S.precision = cfg->precision;
+    S.omega = (float)(1.0 / cfg->tau);
+    for (int a = 0; a < 3; ++a) S.g[a] = (float)cfg->body_force[a];
+    S.n_fluid = n_fluid;
+    S.total_beads = h->total_beads;
+    int maxb = 0;
+    for (int r = 0; r < cfg->n_real; ++r) maxb = std::max(maxb, bead_offsets[r + 1] - bead_offsets[r]);
+    S.max_beads = maxb;
+    S.wall_x = cfg->wall_x;
+    S.pore_h = cfg->pore_h;
+    S.pore_ylo = cfg->ny / 2 - cfg->pore_h / 2;
+    S.pore_zlo = cfg->nz / 2 - cfg->pore_h / 2;
+    S.k_bond = (float)cfg->k_bond;
+    S.r0 = (float)cfg->r0;
+    S.kappa = (float)cfg->kappa_bend;
+    const double c13 = std::pow(2.0, 1.0 / 3.0), c16 = std::pow(2.0, 1.0 / 6.0);
+    S.lj_eps = (float)cfg->lj_eps;
+    S.lj_sig2 = (float)(cfg->lj_sigma * cfg->lj_sigma);
+    S.lj_rc2 = (float)(c13 * cfg->lj_sigma * cfg->lj_sigma);
+    S.wall_eps = (float)cfg->wall_eps;
+    S.wall_sig2 = (float)(cfg->wall_sigma * cfg->wall_sigma);
+    S.wall_rc2 = (float)(c13 * cfg->wall_sigma * cfg->wall_sigma);
+    S.E = (float)cfg->E;
+    S.gamma = (float)cfg->gamma;
+    S.kT = (float)cfg->kT;
+    S.M = cfg->md_outer;
+    S.Mb = cfg->md_inner;
+    S.skin_half2 = (float)(0.25 * SKIN * SKIN);
+    const double rl = c16 * cfg->lj_sigma + SKIN, rlw = c16 * cfg->wall_sigma + SKIN;
+    S.rl2 = (float)(rl * rl);
+    S.rlw = (float)rlw;
+    S.rlw2 = (float)(rlw * rlw);
+    const int dims[3] = {cfg->nx, cfg->ny, cfg->nz};
+    for (int a = 0; a < 3; ++a) S.ncell[a] = std::max(1, (int)std::floor(dims[a] / rl));
+    S.seed = cfg->seed;
+    S.link = (const uint32_t *)(b + L.link);
+    S.tileflag = (const uint8_t *)(b + L.tileflag);
+    S.solid = (const uint8_t *)(b + L.solid);
+    S.G = (unsigned long long *)(b + L.G);
+    S.stamp = (int *)(b + L.stamp);
+    S.r_hi = (float4 *)(b + L.r_hi);
+    S.r_lo = (float4 *)(b + L.r_lo);
+    S.v = (float4 *)(b + L.v);
+    S.up = (float4 *)(b + L.up);
+    S.J = (float4 *)(b + L.J);
+    S.pair_node = (int *)(b + L.pair_node);
+    S.bead_off = (const int *)(b + L.bead_off);
+    S.partial = (double *)(b + L.partial);
+    S.ring = (lbmd_diag *)(b + L.ring);
+    S.obs = (lbmd_obs *)(b + L.obs);
+    S.ctrl = (Ctrl *)(b + L.ctrl);
+
+#define CKI(call)                                                           \
+    do {                                                                    \
+        cudaError_t e__ = (call);                                           \
+        if (e__ != cudaSuccess) { cuda_fail(h, e__, #call); return bail(LBMD_ERR_CUDA); } \
+    } while (0)
+    CKI(cudaMemcpyAsync(b + L.link, link.data(), link.size() * 4, cudaMemcpyHostToDevice, h->st));
+    CKI(cudaMemcpyAsync(b + L.tileflag, tile.data(), tile.size(), cudaMemcpyHostToDevice, h->st));
+    CKI(cudaMemcpyAsync(b + L.solid, sol.data(), sol.size(), cudaMemcpyHostToDevice, h->st));
+    CKI(cudaMemcpyAsync(b + L.bead_off, h->offsets.data(), h->offsets.size() * 4, cudaMemcpyHostToDevice, h->st));
+    CKI(cudaMemsetAsync(b + L.G, 0, (size_t)cfg->n_real * 3 * S.ns * 8, h->st));
+    CKI(cudaMemsetAsync(b + L.stamp, 0, (size_t)cfg->n_real * S.ns * 4, h->st));
+    CKI(cudaMemsetAsync(b + L.ring, 0, (size_t)cfg->n_real * LBMD_DIAG_RING * sizeof(lbmd_diag), h->st));
+    CKI(cudaMemsetAsync(b + L.obs, 0, (size_t)cfg->n_real * sizeof(lbmd_obs), h->st));
+    CKI(cudaMemsetAsync(b + L.ctrl, 0, sizeof(Ctrl), h->st));
+    CKI(cudaMemsetAsync(b + L.popB, 0, L.staging - L.popB, h->st));
+    CKI(cudaMemsetAsync(b + L.up, 0, (size_t)std::max(h->total_beads, 1) * 32, h->st));
+    CKI(launch_init_rest(S, h->popA, h->st));
+    CKI(cudaStreamSynchronize(h->st));
+    // the particle kernel needs its shared-memory size granted once
+    if (particle_smem_bytes(particle_threads(S)) > 227 * 1024) { fail(h, LBMD_ERR_CAPACITY, "too many beads per realization for shared memory"); return bail(LBMD_ERR_CAPACITY); }
+    lbmd_status s = lbmd_set_beads(h, r_init, nullptr);
+    if (s != LBMD_OK) return bail(s);
+    *out = h;
+    return LBMD_OK;
+#undef CKI
+}
+
+lbmd_status lbmd_step(lbmd_handle *h, int64_t n) {
+    if (!h || n < 0) return LBMD_ERR_INVALID_ARG;
+    while (n > 0) {
+        const bool use_graph = h->graph_steps > 0 && !h->profiling && n >= h->graph_steps;
+        if (use_graph) {
+            if (!h->gexec) {
+                lbmd_status s = capture_graph(h);
+                if (s != LBMD_OK) return s;
+            }
+            if (h->popA == h->graph_A) {
+                CK(cudaGraphLaunch(h->gexec, h->st));
+                h->host_step += h->graph_steps;
+                h->launches += 3LL * h->graph_steps;
+                n -= h->graph_steps;
+                continue;
+            }
+        }
+        lbmd_status s = enqueue_step(h);
+        if (s != LBMD_OK) return s;
+        n -= 1;
+    }
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_check(lbmd_handle *h) {
+    if (!h) return LBMD_ERR_INVALID_ARG;
+    Ctrl c;
+    CK(cudaMemcpyAsync(&c, h->S.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    if (c.status & ST_NONFINITE) return fail(h, LBMD_ERR_NONFINITE, "non-finite value in the fluid or bead state");
+    if (c.status & ST_CAPACITY) return fail(h, LBMD_ERR_CAPACITY, "neighbour or wall list overflowed");
+    if (c.status & ST_TIMEOUT) return fail(h, LBMD_ERR_TIMEOUT, "a bounded device wait gave up");
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_observables(lbmd_handle *h, lbmd_obs *out) {
+    if (!h || !out) return LBMD_ERR_INVALID_ARG;
+    CK(launch_fluid_observables(h->S, h->popA, h->st));
+    CK(launch_bead_observables(h->S, h->popA, h->st));
+    h->launches += 2;
+    Ctrl c;
+    CK(cudaMemcpyAsync(out, h->S.obs, sizeof(lbmd_obs) * h->cfg.n_real, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(&c, h->S.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    int st = LBMD_OK;
+    if (c.status & ST_NONFINITE) st = LBMD_ERR_NONFINITE;
+    else if (c.status & ST_CAPACITY) st = LBMD_ERR_CAPACITY;
+    else if (c.status & ST_TIMEOUT) st = LBMD_ERR_TIMEOUT;
+    for (int r = 0; r < h->cfg.n_real; ++r) {
+        out[r].step = c.step;
+        out[r].status = st;
+    }
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_diagnostics(lbmd_handle *h, lbmd_diag *out, int32_t max_rows, int32_t *rows) {
+    if (!h || !out || !rows || max_rows < 0) return LBMD_ERR_INVALID_ARG;
+    const int R = h->cfg.n_real;
+    std::vector<lbmd_diag> ring((size_t)R * LBMD_DIAG_RING);
+    CK(cudaMemcpyAsync(ring.data(), h->S.ring, ring.size() * sizeof(lbmd_diag), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    const long long done = h->host_step;  // rows exist for steps [0, done)
+    const long long avail = std::min<long long>(done, LBMD_DIAG_RING);
+    const int n = (int)std::min<long long>(avail, max_rows);
+    for (int r = 0; r < R; ++r)
+        for (int k = 0; k < n; ++k) {
+            const long long stp = done - n + k;
+            out[(size_t)r * max_rows + k] = ring[(size_t)r * LBMD_DIAG_RING + (stp % LBMD_DIAG_RING)];
+        }
+    *rows = n;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_init_fluid(lbmd_handle *h, const double *rho, const double *u) {
+    if (!h) return LBMD_ERR_INVALID_ARG;
+    const size_t ns = h->S.ns;
+    std::vector<float> rows(4 * ns);
+    for (int r = 0; r < h->cfg.n_real; ++r) {
+        for (size_t s = 0; s < ns; ++s) {
+            rows[s] = rho ? (float)rho[(size_t)r * ns + s] : 1.0f;
+            for (int a = 0; a < 3; ++a) rows[(a + 1) * ns + s] = u ? (float)u[((size_t)r * 3 + a) * ns + s] : 0.0f;
+        }
+        CK(cudaMemcpyAsync(h->staging + ((size_t)r * LBMD_Q + 15) * ns, rows.data(), 4 * ns * sizeof(float),
+                           cudaMemcpyHostToDevice, h->st));
+        CK(cudaStreamSynchronize(h->st));
+    }
+    CK(launch_feq_to_staging(h->S, h->staging, h->st));
+    CK(launch_push_from_staging(h->S, h->staging, h->popA, h->st));
+    h->launches += 2;
+    CK(cudaStreamSynchronize(h->st));
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_get_populations(lbmd_handle *h, float *f) {
+    if (!h || !f) return LBMD_ERR_INVALID_ARG;
+    CK(launch_pull_to_staging(h->S, h->popA, h->staging, h->st));
+    h->launches += 1;
+    CK(cudaMemcpyAsync(f, h->staging, (size_t)h->cfg.n_real * LBMD_Q * h->S.ns * sizeof(float),
+                       cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_set_populations(lbmd_handle *h, const float *f) {
+    if (!h || !f) return LBMD_ERR_INVALID_ARG;
+    CK(cudaMemcpyAsync(h->staging, f, (size_t)h->cfg.n_real * LBMD_Q * h->S.ns * sizeof(float),
+                       cudaMemcpyHostToDevice, h->st));
+    CK(launch_push_from_staging(h->S, h->staging, h->popA, h->st));
+    h->launches += 1;
+    CK(cudaStreamSynchronize(h->st));
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_get_beads(lbmd_handle *h, double *r, double *v) {
+    if (!h) return LBMD_ERR_INVALID_ARG;
+    const int n = h->total_beads;
+    if (n == 0) return LBMD_OK;
+    std::vector<float4> hi(n), lo(n), vv(n);
+    CK(cudaMemcpyAsync(hi.data(), h->S.r_hi, n * 16, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(lo.data(), h->S.r_lo, n * 16, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(vv.data(), h->S.v, n * 16, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    for (int i = 0; i < n; ++i) {
+        if (r) {
+            r[3 * i] = (double)hi[i].x + (double)lo[i].x;
+            r[3 * i + 1] = (double)hi[i].y + (double)lo[i].y;
+            r[3 * i + 2] = (double)hi[i].z + (double)lo[i].z;
+        }
+        if (v) { v[3 * i] = vv[i].x; v[3 * i + 1] = vv[i].y; v[3 * i + 2] = vv[i].z; }
+    }
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_set_beads(lbmd_handle *h, const double *r, const double *v) {
+    if (!h) return LBMD_ERR_INVALID_ARG;
+    const int n = h->total_beads;
+    if (n == 0) return LBMD_OK;
+    if (!r) return LBMD_ERR_INVALID_ARG;
+    std::vector<float4> hi(n), lo(n), vv(n);
+    for (int i = 0; i < n; ++i) {
+        float t[3], l[3];
+        for (int a = 0; a < 3; ++a) {
+            t[a] = (float)r[3 * i + a];
+            l[a] = (float)(r[3 * i + a] - (double)t[a]);
+        }
+        hi[i] = make_float4(t[0], t[1], t[2], 0.f);
+        lo[i] = make_float4(l[0], l[1], l[2], 0.f);
+        vv[i] = v ? make_float4((float)v[3 * i], (float)v[3 * i + 1], (float)v[3 * i + 2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    CK(cudaMemcpyAsync(h->S.r_hi, hi.data(), n * 16, cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(h->S.r_lo, lo.data(), n * 16, cudaMemcpyHostToDevice, h->st));
+    CK(cudaMemcpyAsync(h->S.v, vv.data(), n * 16, cudaMemcpyHostToDevice, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_get_coupling(lbmd_handle *h, float *up, float *J) {
+    if (!h) return LBMD_ERR_INVALID_ARG;
+    const int n = h->total_beads;
+    if (n == 0) return LBMD_OK;
+    std::vector<float4> a(n), b(n);
+    CK(cudaMemcpyAsync(a.data(), h->S.up, n * 16, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(b.data(), h->S.J, n * 16, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    for (int i = 0; i < n; ++i) {
+        if (up) { up[3 * i] = a[i].x; up[3 * i + 1] = a[i].y; up[3 * i + 2] = a[i].z; }
+        if (J) { J[3 * i] = b[i].x; J[3 * i + 1] = b[i].y; J[3 * i + 2] = b[i].z; }
+    }
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_get_step(lbmd_handle *h, int64_t *step) {
+    if (!h || !step) return LBMD_ERR_INVALID_ARG;
+    *step = h->host_step;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_set_step(lbmd_handle *h, int64_t step) {
+    if (!h || step < 0) return LBMD_ERR_INVALID_ARG;
+    long long s = step;
+    CK(cudaMemcpyAsync(&h->S.ctrl->step, &s, sizeof(s), cudaMemcpyHostToDevice, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    h->host_step = step;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_set_graph(lbmd_handle *h, int32_t steps_per_graph) {
+    if (!h || steps_per_graph < 0 || (steps_per_graph & 1)) return LBMD_ERR_INVALID_ARG;
+    if (!h->st) return fail(h, LBMD_ERR_INVALID_ARG, "graph capture needs a non-default stream");
+    drop_graph(h);
+    h->graph_steps = steps_per_graph;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_set_tiles(lbmd_handle *h, int32_t by, int32_t zc) {
+    if (!h || !(by == 1 || by == 2 || by == 4 || by == 8 || by == 16) || zc < 1 || zc > 64)
+        return LBMD_ERR_INVALID_ARG;
+    if (by != h->by || zc != h->zc) drop_graph(h);
+    h->by = by;
+    h->zc = zc;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_get_tiles(lbmd_handle *h, int32_t *by, int32_t *zc) {
+    if (!h || !by || !zc) return LBMD_ERR_INVALID_ARG;
+    *by = h->by;
+    *zc = h->zc;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t *zc_out) {
+    if (!h || reps < 1) return LBMD_ERR_INVALID_ARG;
+    static const int BYS[] = {1, 2, 4, 8, 16};
+    static const int ZCS[] = {1, 2, 4, 8, 16, 32};
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    float best = 1e30f;
+    int bb = h->by, bz = h->zc;
+    for (int by : BYS)
+        for (int zc : ZCS) {
+            if (zc > h->cfg.nz) continue;
+            // warm-up, then time reps launches; B is scratch until the next step overwrites it
+            CK(launch_stream_collide(h->S, h->popA, h->popB, by, zc, true, h->st));
+            CK(cudaEventRecord(a, h->st));
+            for (int k = 0; k < reps; ++k) CK(launch_stream_collide(h->S, h->popA, h->popB, by, zc, true, h->st));
+            CK(cudaEventRecord(b, h->st));
+            CK(cudaEventSynchronize(b));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, a, b));
+            h->launches += reps + 1;
+            if (ms < best) { best = ms; bb = by; bz = zc; }
+        }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    lbmd_status s = lbmd_set_tiles(h, bb, bz);
+    if (by_out) *by_out = bb;
+    if (zc_out) *zc_out = bz;
+    return s;
+}
+
+lbmd_status lbmd_profile(lbmd_handle *h, int32_t enable) {
+    if (!h) return LBMD_ERR_INVALID_ARG;
+    lbmd_status s = resolve_profile(h);
+    if (s != LBMD_OK) return s;
+    if (enable && !h->profiling)
+        for (int k = 0; k < K_COUNT; ++k) { h->prof_ms[k] = 0; h->prof_n[k] = 0; }
+    h->profiling = enable != 0;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_kernel_times(lbmd_handle *h, lbmd_kernel_time *out, int32_t max_entries, int32_t *n_entries) {
+    if (!h || !n_entries || (max_entries > 0 && !out)) return LBMD_ERR_INVALID_ARG;
+    lbmd_status s = resolve_profile(h);
+    if (s != LBMD_OK) return s;
+    const int n = std::min<int>(max_entries, K_COUNT);
+    for (int k = 0; k < n; ++k) {
+        memset(out[k].name, 0, sizeof(out[k].name));
+        strncpy(out[k].name, KNAMES[k], sizeof(out[k].name) - 1);
+        out[k].launches = h->prof_n[k];
+        out[k].total_ms = h->prof_ms[k];
+    }
+    *n_entries = n;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_launch_count(lbmd_handle *h, int64_t *launches) {
+    if (!h || !launches) return LBMD_ERR_INVALID_ARG;
+    *launches = h->launches;
+    return LBMD_OK;
+}
+
+void lbmd_destroy(lbmd_handle *h) {
+    if (!h) return;
+    if (h->st) cudaStreamSynchronize(h->st);
+    if (h->aux) cudaStreamSynchronize(h->aux);
+    for (auto &p : h->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto e : h->free_events) cudaEventDestroy(e);
+    drop_graph(h);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->aux) cudaStreamDestroy(h->aux);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,252 @@
+// lbmd_internal.cuh -- device-side definitions shared by the kernels of the
+// coupled LB-MD library (not part of the public ABI).
+//
+// Data layout in HBM (one device buffer owned by the caller):
+//   populations  A, B      [n_real][19][ns]  fp32, or fp16 deviations (f - w) * 2^12
+//                          A holds the post-collision populations f* of the last
+//                          step; the next step pulls from A and writes B.
+//   staging                [n_real][19][ns]  fp32 host-transfer area
+//   link                   [ns] u32: bit i set = the pull of link i bounces back
+//                          (its source x - c_i is solid); bit 31 = site solid
+//   tileflag               [nxt][ny][nz] u8: 1 if any of the 32 sites of the x-tile
+//                          has a bounce-back link or is solid (warp-uniform fast path)
+//   solid                  [ns] u8
+//   G                      [n_real][3][ns] i64 fixed point (2^40): momentum handed
+//                          to the fluid by the beads this step
+//   stamp                  [n_real][ns] i32: last step a source was applied at a site
+//   beads                  float4 r_hi, r_lo (unwrapped position as a float-float
+//                          pair), v, up, J  [total_beads]
+//   pair_node              [total_beads][8] i32: global site of each fluid corner
+//   partial / ring / ctrl  reduction scratch, per-step diagnostics, counters
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "../../include/lbmd.h"
+
+namespace lbmd {
+
+// ---------------------------------------------------------------------------
+// D3Q19 (Sec. II).  Order: rest, +x,-x,+y,-y,+z,-z, then the 12 face diagonals
+// in opposite pairs.  Compile-time tables so that unrolled loops fold them.
+// ---------------------------------------------------------------------------
+constexpr int Q = 19;
+__host__ __device__ constexpr int cx(int i) {
+    return i == 1 || i == 7 || i == 9 || i == 11 || i == 13 ? 1
+         : i == 2 || i == 8 || i == 10 || i == 12 || i == 14 ? -1 : 0;
+}
+__host__ __device__ constexpr int cy(int i) {
+    return i == 3 || i == 7 || i == 10 || i == 15 || i == 17 ? 1
+         : i == 4 || i == 8 || i == 9 || i == 16 || i == 18 ? -1 : 0;
+}
+__host__ __device__ constexpr int cz(int i) {
+    return i == 5 || i == 11 || i == 14 || i == 15 || i == 18 ? 1
+         : i == 6 || i == 12 || i == 13 || i == 16 || i == 17 ? -1 : 0;
+}
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+__host__ __device__ constexpr float wq(int i) {
+    return i == 0 ? (1.0f / 3.0f) : (i <= 6 ? (1.0f / 18.0f) : (1.0f / 36.0f));
+}
+
+constexpr uint32_t SOLID_BIT = 0x80000000u;
+constexpr float FP16_SCALE = 4096.0f;          // 2^12
+constexpr float FP16_INV_SCALE = 1.0f / 4096.0f;
+constexpr double FIX_SCALE = 1099511627776.0;  // 2^40
+constexpr float FIX_SCALE_F = 1099511627776.0f;
+constexpr float FIX_INV_SCALE_F = 1.0f / 1099511627776.0f;
+
+constexpr int NBR_CAP = 32;     // bead-bead neighbours per bead
+constexpr int WALL_CAP = 8;     // solid sites within the wall-list radius per bead
+constexpr int HASH_SIZE = 2048; // cell hash slots (>= 2 * max beads per realization)
+
+// status bits latched in Ctrl::status
+constexpr int ST_NONFINITE = 1;
+constexpr int ST_CAPACITY = 2;
+constexpr int ST_TIMEOUT = 4;
+
+struct Ctrl {
+    long long step;          // LB step counter = Philox counter
+    int status;              // ST_* bits
+    unsigned int sc_done;    // blocks finished (stream-collide diag finalize)
+    unsigned int src_done;   // blocks finished (source kernel; last one advances step)
+    unsigned int obs_done;   // blocks finished (observables pass)
+    int pad[2];
+};
+
+// Everything a kernel needs, passed by value.
+struct Sim {
+    // lattice
+    int nx, ny, nz, ns, nxt, n_real;
+    int precision;
+    float omega;
+    float g[3];
+    double n_fluid;          // fluid sites per realization
+    // beads
+    int total_beads, max_beads;
+    int wall_x, pore_h, pore_ylo, pore_zlo;
+    float k_bond, r0, kappa;
+    float lj_eps, lj_sig2, lj_rc2;
+    float wall_eps, wall_sig2, wall_rc2;
+    float E, gamma, kT;
+    int M, Mb;
+    float skin_half2;        // (skin/2)^2: displacement that forces a list rebuild
+    float rl2, rlw2, rlw;    // bead and wall list radii (squared) and wall radius
+    int ncell[3];            // cells per axis for the neighbour hash (>= 3 to use it)
+    unsigned long long seed;
+    // buffers
+    const uint32_t *link;
+    const uint8_t *tileflag;
+    const uint8_t *solid;
+    unsigned long long *G;
+    int *stamp;
+    float4 *r_hi, *r_lo, *v, *up, *J;
+    int *pair_node;
+    const int *bead_off;
+    double *partial;         // [blocks][4]
+    lbmd_diag *ring;         // [n_real][LBMD_DIAG_RING]
+    lbmd_obs *obs;           // [n_real]
+    Ctrl *ctrl;
+};
+
+// ---------------------------------------------------------------------------
+// population storage
+// ---------------------------------------------------------------------------
+// PREC 0 stores f in fp32; PREC 1 stores (f - w) * 2^12 in fp16.  Both helpers
+// speak deviations h = f - w so that the arithmetic is the same for both.
+template <int PREC> struct PopT;
+template <> struct PopT<0> { using T = float; };
+template <> struct PopT<1> { using T = __half; };
+
+__device__ __forceinline__ float load_dev(const float *base, uint32_t idx, float w) {
+    return __ldg(base + idx) - w;
+}
+__device__ __forceinline__ float load_dev(const __half *base, uint32_t idx, float) {
+    return __half2float(__ldg(base + idx)) * FP16_INV_SCALE;
+}
+// plain (coherent) load for data written earlier in the same kernel
+__device__ __forceinline__ float load_dev_cg(const float *base, uint32_t idx, float w) {
+    return __ldcg(base + idx) - w;
+}
+__device__ __forceinline__ float load_dev_cg(const __half *base, uint32_t idx, float) {
+    return __half2float(__ldcg(base + idx)) * FP16_INV_SCALE;
+}
+__device__ __forceinline__ void store_dev(float *base, uint32_t idx, float h, float w) {
+    base[idx] = w + h;
+}
+__device__ __forceinline__ void store_dev(__half *base, uint32_t idx, float h, float) {
+    base[idx] = __float2half_rn(h * FP16_SCALE);
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and the Gaussian mapping
+// used for the bead noise: key = (seed_lo, seed_hi ^ realization), counter =
+// (bead, step_lo, substep, step_hi); u = (top 24 bits + 1/2) 2^-24; Box-Muller.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ float3 gauss3(unsigned long long seed, uint32_t realization,
+                                         uint32_t bead, long long step, uint32_t substep) {
+    const uint2 key = make_uint2((uint32_t)(seed & 0xffffffffull), (uint32_t)(seed >> 32) ^ realization);
+    const uint4 ctr = make_uint4(bead, (uint32_t)((unsigned long long)step & 0xffffffffull), substep,
+                                 (uint32_t)((unsigned long long)step >> 32));
+    const uint4 x = philox4x32_10(ctr, key);
+    const float u0 = ((float)(x.x >> 8) + 0.5f) * (1.0f / 16777216.0f);
+    const float u1 = ((float)(x.y >> 8) + 0.5f) * (1.0f / 16777216.0f);
+    const float u2 = ((float)(x.z >> 8) + 0.5f) * (1.0f / 16777216.0f);
+    const float u3 = ((float)(x.w >> 8) + 0.5f) * (1.0f / 16777216.0f);
+    const float a = sqrtf(-2.0f * logf(u0));
+    const float b = sqrtf(-2.0f * logf(u2));
+    float s1, c1, s3, c3;
+    sincospif(2.0f * u1, &s1, &c1);
+    sincospif(2.0f * u3, &s3, &c3);
+    return make_float3(a * c1, a * s1, b * c3);
+}
+
+// ---------------------------------------------------------------------------
+// float-float positions: unwrapped coordinate = hi + lo, |lo| <= ulp(hi)/2
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+// hi + lo += d: the rounding error of hi + d is carried in lo (renormalised by
+// ff_norm once per LB step, so lo stays far below ulp(hi) * steps)
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float d) {
+    float s, e;
+    two_sum(hi, d, s, e);
+    hi = s;
+    lo += e;
+}
+__device__ __forceinline__ void ff_norm(float &hi, float &lo) {
+    float s, e;
+    two_sum(hi, lo, s, e);
+    hi = s;
+    lo = e;
+}
+// minimum-image difference of two float-float coordinates on an axis of length n
+__device__ __forceinline__ float ff_diff(float ahi, float alo, float bhi, float blo, float n) {
+    float d = (ahi - bhi) + (alo - blo);
+    return d - n * rintf(d / n);
+}
+// wrapped coordinate in [0, n)
+__device__ __forceinline__ float ff_wrap(float hi, float lo, float n) {
+    float x = hi - n * floorf(hi / n);
+    if (x < 0.0f) x += n;
+    if (x >= n) x -= n;
+    x += lo;
+    if (x < 0.0f) x += n;
+    if (x >= n) x -= n;
+    // non-finite or runaway coordinates must never become out-of-range lattice
+    // indices: they are pinned to 0 (the step's non-finite check reports them)
+    if (!(x >= 0.0f && x < n)) x = 0.0f;
+    return x;
+}
+
+// wrap an index that is at most one period outside [0, n)
+__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+// wrap any index into [0, n)
+__device__ __forceinline__ int wrap_any(int i, int n) { const int m = i % n; return m < 0 ? m + n : m; }
+
+// Field channel of Sec. IV: |x - wall_x| <= 3/2 (minimum image) and y, z inside the
+// pore cross-section padded by half a site.
+__device__ __forceinline__ bool in_channel(const Sim &S, float xw, float yw, float zw) {
+    if (S.wall_x < 0) return false;
+    float dx = xw - (float)S.wall_x;
+    dx -= (float)S.nx * rintf(dx / (float)S.nx);
+    if (fabsf(dx) > 1.5f) return false;
+    if (yw < (float)S.pore_ylo - 0.5f || yw > (float)(S.pore_ylo + S.pore_h) - 0.5f) return false;
+    if (zw < (float)S.pore_zlo - 0.5f || zw > (float)(S.pore_zlo + S.pore_h) - 0.5f) return false;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// host-side launchers (defined in the kernel translation units)
+// ---------------------------------------------------------------------------
+int sc_blocks(const Sim &S, int by, int zc);
+cudaError_t launch_stream_collide(const Sim &S, const void *A, void *B, int by, int zc,
+                                  bool diag, cudaStream_t st);
+cudaError_t launch_fluid_observables(const Sim &S, const void *A, cudaStream_t st);
+cudaError_t launch_source(const Sim &S, void *B, cudaStream_t st);
+cudaError_t launch_init_rest(const Sim &S, void *A, cudaStream_t st);
+cudaError_t launch_feq_to_staging(const Sim &S, float *staging, cudaStream_t st);
+cudaError_t launch_pull_to_staging(const Sim &S, const void *A, float *staging, cudaStream_t st);
+cudaError_t launch_push_from_staging(const Sim &S, const float *staging, void *A, cudaStream_t st);
+size_t particle_smem_bytes(int threads);
+int particle_threads(const Sim &S);
+cudaError_t launch_particles(const Sim &S, const void *A, cudaStream_t st);
+cudaError_t launch_bead_observables(const Sim &S, const void *A, cudaStream_t st);
+
+}  // namespace lbmd

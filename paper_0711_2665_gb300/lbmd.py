@@ -1,0 +1,323 @@
+"""Python binding of the C ABI in ``include/lbmd.h`` (argument marshalling only).
+
+Every step of the coupled LB-MD path runs in the CUDA kernels of
+``liblbmd.so``; this module only converts arrays, allocates the one device
+buffer the library works in (through PyTorch's caching allocator) and passes
+the current PyTorch CUDA stream.  There is no fallback: if the library or a
+GPU is missing, constructing a :class:`Simulation` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblbmd.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "lbmd.h")
+
+LBMD_Q = 19
+MAX_BEADS_PER_REALIZATION = 1024
+DIAG_RING = 1024
+FP32, FP16DEV = 0, 1
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "non-finite value",
+          4: "timeout", 5: "capacity exceeded", 6: "device buffer too small or misaligned"}
+
+
+class LbmdError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}" + (f" ({detail})" if detail else ""))
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("n_real", ctypes.c_int32), ("tau", ctypes.c_double),
+                ("body_force", ctypes.c_double * 3), ("wall_x", ctypes.c_int32),
+                ("pore_h", ctypes.c_int32), ("k_bond", ctypes.c_double), ("r0", ctypes.c_double),
+                ("kappa_bend", ctypes.c_double), ("lj_sigma", ctypes.c_double),
+                ("lj_eps", ctypes.c_double), ("wall_sigma", ctypes.c_double),
+                ("wall_eps", ctypes.c_double), ("E", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("kT", ctypes.c_double), ("md_outer", ctypes.c_int32), ("md_inner", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("p_fluid", ctypes.c_double * 3),
+                ("p_beads", ctypes.c_double * 3), ("com", ctypes.c_double * 3),
+                ("n_translocated", ctypes.c_double), ("dWH_dt", ctypes.c_double),
+                ("dWE_dt", ctypes.c_double), ("rg_untranslocated", ctypes.c_double),
+                ("rg_translocated", ctypes.c_double), ("step", ctypes.c_int64),
+                ("status", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("mass", ctypes.c_double), ("p_fluid", ctypes.c_double * 3),
+                ("p_beads", ctypes.c_double * 3), ("com", ctypes.c_double * 3),
+                ("n_translocated", ctypes.c_double), ("dWH_dt", ctypes.c_double),
+                ("dWE_dt", ctypes.c_double)]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def declared_symbols() -> list[str]:
+    """Names of every function ``include/lbmd.h`` declares."""
+    import re
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(lbmd_[a-z_0-9]+)\s*\(", text)))
+
+
+def lib():
+    """Load liblbmd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_0711_2665_gb300.build.build_library()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    P = ctypes.POINTER
+    sig = {
+        "lbmd_required_bytes": [P(Config), vp, P(sz)],
+        "lbmd_init": [P(Config), vp, vp, vp, vp, sz, vp, P(vp)],
+        "lbmd_step": [vp, i64],
+        "lbmd_observables": [vp, P(Obs)],
+        "lbmd_check": [vp],
+        "lbmd_diagnostics": [vp, P(Diag), i32, P(i32)],
+        "lbmd_init_fluid": [vp, vp, vp],
+        "lbmd_get_populations": [vp, vp],
+        "lbmd_set_populations": [vp, vp],
+        "lbmd_get_beads": [vp, vp, vp],
+        "lbmd_set_beads": [vp, vp, vp],
+        "lbmd_get_coupling": [vp, vp, vp],
+        "lbmd_get_step": [vp, P(i64)],
+        "lbmd_set_step": [vp, i64],
+        "lbmd_set_graph": [vp, i32],
+        "lbmd_set_tiles": [vp, i32, i32],
+        "lbmd_get_tiles": [vp, P(i32), P(i32)],
+        "lbmd_autotune": [vp, i32, P(i32), P(i32)],
+        "lbmd_profile": [vp, i32],
+        "lbmd_kernel_times": [vp, P(KernelTime), i32, P(i32)],
+        "lbmd_launch_count": [vp, P(i64)],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.lbmd_status_string.argtypes = [ctypes.c_int]
+    L.lbmd_status_string.restype = ctypes.c_char_p
+    L.lbmd_last_error.argtypes = [vp]
+    L.lbmd_last_error.restype = ctypes.c_char_p
+    L.lbmd_destroy.argtypes = [vp]
+    L.lbmd_destroy.restype = None
+    _lib = L
+    return L
+
+
+def make_config(w: dict) -> Config:
+    """lbmd_config from a parameter dict (see workloads.py for the keys)."""
+    c = Config()
+    c.nx, c.ny, c.nz = int(w["nx"]), int(w["ny"]), int(w["nz"])
+    c.n_real = int(w.get("n_real", 1))
+    c.tau = float(w["tau"])
+    c.body_force = (ctypes.c_double * 3)(*[float(v) for v in w.get("body_force", (0, 0, 0))])
+    c.wall_x = int(w.get("wall_x", -1))
+    c.pore_h = int(w.get("pore_h", 0))
+    for k in ("k_bond", "r0", "kappa_bend", "lj_sigma", "lj_eps", "wall_sigma", "wall_eps", "E",
+              "gamma", "kT"):
+        setattr(c, k, float(w[k]))
+    c.md_outer = int(w.get("md_outer", 5))
+    c.md_inner = int(w.get("md_inner", 20))
+    prec = w.get("precision", "fp32")
+    c.precision = FP16DEV if prec in ("fp16dev", FP16DEV) else FP32
+    c.reserved = 0
+    c.seed = int(w.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF
+    return c
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+class Simulation:
+    """One handle of the library: n_real realizations on one GPU."""
+
+    def __init__(self, params: dict, solid: np.ndarray, offsets, r_init, device: str = "cuda:0"):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("Simulation needs a CUDA GPU; there is no CPU path")
+        self._lib = lib()
+        self.cfg = make_config(params)
+        self.device = torch.device(device)
+        self.n_real = self.cfg.n_real
+        self.ns = self.cfg.nx * self.cfg.ny * self.cfg.nz
+        self.offsets = np.ascontiguousarray(offsets, dtype=np.int32)
+        self.total_beads = int(self.offsets[-1])
+        solid = np.ascontiguousarray(solid, dtype=np.uint8).reshape(-1)
+        if solid.size != self.ns:
+            raise ValueError("solid mask must have nx*ny*nz entries")
+        r = np.ascontiguousarray(r_init, dtype=np.float64).reshape(-1)
+        if r.size != 3 * self.total_beads:
+            raise ValueError("r_init must have 3 * total_beads entries")
+        nbytes = ctypes.c_size_t(0)
+        self._check(self._lib.lbmd_required_bytes(ctypes.byref(self.cfg), _ptr(self.offsets),
+                                                  ctypes.byref(nbytes)), "lbmd_required_bytes")
+        self.nbytes = nbytes.value
+        with torch.cuda.device(self.device):
+            self.buffer = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=self.device)
+            base = self.buffer.data_ptr()
+            aligned = (base + 255) & ~255
+            self.stream = torch.cuda.current_stream(self.device)
+            h = ctypes.c_void_p()
+            st = self._lib.lbmd_init(ctypes.byref(self.cfg), _ptr(solid), _ptr(self.offsets), _ptr(r),
+                                     ctypes.c_void_p(aligned), self.nbytes,
+                                     ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if st != 0:
+            raise LbmdError(st, "lbmd_init")
+        self._h = h
+
+    # -- plumbing --------------------------------------------------------
+    def _check(self, st: int, where: str):
+        if st != 0:
+            detail = ""
+            h = getattr(self, "_h", None)
+            if h:
+                detail = self._lib.lbmd_last_error(h).decode()
+            raise LbmdError(st, where, detail)
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._lib.lbmd_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- stepping --------------------------------------------------------
+    def step(self, n: int = 1):
+        self._check(self._lib.lbmd_step(self._h, int(n)), "lbmd_step")
+
+    def check(self):
+        self._check(self._lib.lbmd_check(self._h), "lbmd_check")
+
+    def set_graph(self, steps_per_graph: int):
+        self._check(self._lib.lbmd_set_graph(self._h, int(steps_per_graph)), "lbmd_set_graph")
+
+    def set_tiles(self, by: int, zc: int):
+        self._check(self._lib.lbmd_set_tiles(self._h, int(by), int(zc)), "lbmd_set_tiles")
+
+    def tiles(self):
+        by, zc = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._lib.lbmd_get_tiles(self._h, ctypes.byref(by), ctypes.byref(zc)), "lbmd_get_tiles")
+        return by.value, zc.value
+
+    def autotune(self, reps: int = 5):
+        by, zc = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._lib.lbmd_autotune(self._h, int(reps), ctypes.byref(by), ctypes.byref(zc)),
+                    "lbmd_autotune")
+        return by.value, zc.value
+
+    @property
+    def step_count(self) -> int:
+        s = ctypes.c_int64()
+        self._check(self._lib.lbmd_get_step(self._h, ctypes.byref(s)), "lbmd_get_step")
+        return s.value
+
+    def set_step(self, n: int):
+        self._check(self._lib.lbmd_set_step(self._h, int(n)), "lbmd_set_step")
+
+    # -- state -----------------------------------------------------------
+    def init_fluid(self, rho=None, u=None):
+        r = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1) if rho is not None else None
+        uu = np.ascontiguousarray(u, dtype=np.float64).reshape(-1) if u is not None else None
+        self._check(self._lib.lbmd_init_fluid(self._h, _ptr(r), _ptr(uu)), "lbmd_init_fluid")
+
+    def get_populations(self) -> np.ndarray:
+        f = np.empty(self.n_real * LBMD_Q * self.ns, dtype=np.float32)
+        self._check(self._lib.lbmd_get_populations(self._h, _ptr(f)), "lbmd_get_populations")
+        return f.reshape(self.n_real, LBMD_Q, self.cfg.nz, self.cfg.ny, self.cfg.nx)
+
+    def set_populations(self, f):
+        a = np.ascontiguousarray(f, dtype=np.float32).reshape(-1)
+        if a.size != self.n_real * LBMD_Q * self.ns:
+            raise ValueError("populations must have n_real*19*nsites entries")
+        self._check(self._lib.lbmd_set_populations(self._h, _ptr(a)), "lbmd_set_populations")
+
+    def get_beads(self):
+        r = np.zeros(3 * max(self.total_beads, 1))
+        v = np.zeros(3 * max(self.total_beads, 1))
+        self._check(self._lib.lbmd_get_beads(self._h, _ptr(r), _ptr(v)), "lbmd_get_beads")
+        n = self.total_beads
+        return r[:3 * n].reshape(n, 3), v[:3 * n].reshape(n, 3)
+
+    def set_beads(self, r, v=None):
+        rr = np.ascontiguousarray(r, dtype=np.float64).reshape(-1)
+        vv = np.ascontiguousarray(v, dtype=np.float64).reshape(-1) if v is not None else None
+        self._check(self._lib.lbmd_set_beads(self._h, _ptr(rr), _ptr(vv)), "lbmd_set_beads")
+
+    def get_coupling(self):
+        n = self.total_beads
+        up = np.zeros(3 * max(n, 1), dtype=np.float32)
+        J = np.zeros(3 * max(n, 1), dtype=np.float32)
+        self._check(self._lib.lbmd_get_coupling(self._h, _ptr(up), _ptr(J)), "lbmd_get_coupling")
+        return up[:3 * n].reshape(n, 3), J[:3 * n].reshape(n, 3)
+
+    # -- measurements ----------------------------------------------------
+    def observables(self) -> list[dict]:
+        arr = (Obs * self.n_real)()
+        self._check(self._lib.lbmd_observables(self._h, arr), "lbmd_observables")
+        out = []
+        for o in arr:
+            out.append(dict(mass=o.mass, p_fluid_x=o.p_fluid[0], p_fluid_y=o.p_fluid[1],
+                            p_fluid_z=o.p_fluid[2], p_beads_x=o.p_beads[0], p_beads_y=o.p_beads[1],
+                            p_beads_z=o.p_beads[2], com_x=o.com[0], com_y=o.com[1], com_z=o.com[2],
+                            n_translocated=o.n_translocated, dWH_dt=o.dWH_dt, dWE_dt=o.dWE_dt,
+                            rg_untranslocated=o.rg_untranslocated, rg_translocated=o.rg_translocated,
+                            step=o.step, status=o.status))
+        return out
+
+    def diagnostics(self, max_rows: int = DIAG_RING) -> np.ndarray:
+        """Per-step rows [n_real, rows] as a structured numpy array."""
+        buf = (Diag * (self.n_real * max_rows))()
+        rows = ctypes.c_int32()
+        self._check(self._lib.lbmd_diagnostics(self._h, buf, int(max_rows), ctypes.byref(rows)),
+                    "lbmd_diagnostics")
+        dt = np.dtype([("step", np.int64), ("mass", np.float64), ("p_fluid", np.float64, 3),
+                       ("p_beads", np.float64, 3), ("com", np.float64, 3),
+                       ("n_translocated", np.float64), ("dWH_dt", np.float64), ("dWE_dt", np.float64)])
+        a = np.frombuffer(buf, dtype=dt).reshape(self.n_real, max_rows)
+        return a[:, :rows.value].copy()
+
+    def profile(self, enable: bool):
+        self._check(self._lib.lbmd_profile(self._h, int(bool(enable))), "lbmd_profile")
+
+    def kernel_times(self) -> dict:
+        arr = (KernelTime * 8)()
+        n = ctypes.c_int32()
+        self._check(self._lib.lbmd_kernel_times(self._h, arr, 8, ctypes.byref(n)), "lbmd_kernel_times")
+        return {arr[k].name.decode(): (arr[k].launches, arr[k].total_ms) for k in range(n.value)}
+
+    def launch_count(self) -> int:
+        n = ctypes.c_int64()
+        self._check(self._lib.lbmd_launch_count(self._h, ctypes.byref(n)), "lbmd_launch_count")
+        return n.value
+
+
+def from_workload(w: dict, device: str = "cuda:0", inputs: dict | None = None) -> tuple[Simulation, dict]:
+    """Build a Simulation for a named workload dict (paper_0711_2665_gb300.workloads)."""
+    from . import workloads
+    inp = inputs if inputs is not None else workloads.build_inputs(w)
+    sim = Simulation(w, inp["solid"], inp["offsets"], inp["r0"], device=device)
+    return sim, inp

@@ -1,0 +1,207 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (FP32 state, FP32 arithmetic; derivation in the design notes):
+  populations after one step      max |f_gpu - f_orc| <= 1e-5 * max |f|
+  bead velocities after one step  <= 1e-5 * max |v| + 1e-7
+  bead positions after one step   <= 1e-5 * max |r(n+1) - r(n)| + 1e-6
+  coupling u_p and J              <= 1e-5 relative to their max
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import load_state, make_pair, rel_err, small_workload, to_f32_state
+from paper_0711_2665_gb300 import inputs, lbmd, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _compare_one_step(sim, orc, label=""):
+    r_before, _ = orc.get_beads()
+    sim.step(1)
+    orc.step(1)
+    f_g = sim.get_populations()[0]
+    f_o = orc.get_populations()
+    ef = rel_err(f_g, f_o)
+    assert ef <= 1e-5, (label, "populations", ef)
+    if orc.n_beads:
+        r_g, v_g = sim.get_beads()
+        r_o, v_o = orc.get_beads()
+        dr = np.abs(r_o - r_before).max()
+        assert np.abs(r_g - r_o).max() <= 1e-5 * dr + 1e-6, (label, "r", np.abs(r_g - r_o).max(), dr)
+        assert np.abs(v_g - v_o).max() <= 1e-5 * np.abs(v_o).max() + 1e-7, (label, "v")
+        up_g, J_g = sim.get_coupling()
+        up_o, J_o = orc.last_coupling()
+        assert rel_err(up_g, up_o) <= 1e-5 or np.abs(up_g - up_o).max() < 1e-9, (label, "up")
+        assert rel_err(J_g, J_o) <= 1e-5, (label, "J", rel_err(J_g, J_o))
+    return ef
+
+
+def test_rest_state_is_exact_fixed_point():
+    w = small_workload(n_beads=0)
+    sim, orc, inp = make_pair(w)
+    sim.step(5)
+    f = sim.get_populations()[0]
+    c, wts, _ = oracle.tables()
+    fluid = inp["solid"] == 0
+    assert np.array_equal(f[:, fluid], np.broadcast_to(wts.astype(np.float32)[:, None], f[:, fluid].shape))
+    assert np.all(f[:, ~fluid] == 0)
+
+
+def test_population_roundtrip_is_exact():
+    w = small_workload(n_beads=0)
+    sim, orc, inp = make_pair(w)
+    rng = np.random.default_rng(1)
+    c, wts, _ = oracle.tables()
+    f = (wts[:, None, None, None] * (1 + 0.1 * rng.standard_normal((19, w["nz"], w["ny"], w["nx"])))).astype(np.float32)
+    f[:, inp["solid"] == 1] = 0
+    sim.set_populations(f[None])
+    assert np.array_equal(sim.get_populations()[0], f)
+
+
+def test_one_step_from_developed_state_small():
+    w = small_workload()
+    sim, orc, inp = make_pair(w)
+    orc.step(40)
+    f32, r, v = to_f32_state(orc)
+    load_state(sim, orc, f32, r, v, 40)
+    for k in range(3):
+        _compare_one_step(sim, orc, f"step {k}")
+
+
+def test_one_step_without_noise_and_with_body_force():
+    w = small_workload(kT=0.0, body_force=(1e-5, -2e-6, 0.0), E=0.05, seed=3)
+    sim, orc, inp = make_pair(w)
+    orc.step(20)
+    f32, r, v = to_f32_state(orc)
+    load_state(sim, orc, f32, r, v, 20)
+    _compare_one_step(sim, orc)
+
+
+@pytest.mark.parametrize("name", ["plain_fp64_small", "plain_fp32", "adjoint"])
+def test_one_step_at_full_workload_size(name):
+    """The named workloads at their full sizes and bench launch shapes: develop
+    a state in the oracle, then one step on both sides from the same state."""
+    w = workloads.get(name, precision="fp32")
+    sim, orc, inp = make_pair(w)
+    orc.step(3)
+    f32, r, v = to_f32_state(orc)
+    load_state(sim, orc, f32, r, v, 3)
+    _compare_one_step(sim, orc, name)
+
+
+def test_first_steps_from_initial_state_c0():
+    """Config of the plain FP64 case from its initial state: 30 steps; the
+    runs stay within the accumulated FP32 error."""
+    w = workloads.get("plain_fp64_small")
+    sim, orc, inp = make_pair(w)
+    for k in range(3):
+        sim.step(10)
+        orc.step(10)
+        f_g = sim.get_populations()[0]
+        f_o = orc.get_populations()
+        assert rel_err(f_g, f_o) < 1e-4 * (k + 1), rel_err(f_g, f_o)
+        r_g, _ = sim.get_beads()
+        r_o, _ = orc.get_beads()
+        assert np.abs(r_g - r_o).max() < 1e-3
+
+
+def test_observables_match_oracle():
+    w = small_workload()
+    sim, orc, inp = make_pair(w)
+    orc.step(25)
+    f32, r, v = to_f32_state(orc)
+    load_state(sim, orc, f32, r, v, 25)
+    og = sim.observables()[0]
+    oo = orc.observables()
+    assert og["status"] == 0 and og["step"] == 25
+    assert og["mass"] == pytest.approx(oo["mass"], rel=1e-9)
+    for k in ("p_fluid_x", "p_fluid_y", "p_fluid_z", "p_beads_x", "p_beads_y", "p_beads_z"):
+        assert og[k] == pytest.approx(oo[k], rel=1e-5, abs=1e-8), k
+    for k in ("com_x", "com_y", "com_z", "rg_untranslocated", "rg_translocated"):
+        assert og[k] == pytest.approx(oo[k], rel=1e-6, abs=1e-6), k
+    assert og["n_translocated"] == oo["n_translocated"]
+    for k in ("dWH_dt", "dWE_dt"):
+        assert og[k] == pytest.approx(oo[k], rel=1e-4, abs=1e-9), k
+
+
+def test_per_step_diagnostics_match_observables():
+    """The row each step records (fluid sums from the stream-collide kernel,
+    bead sums from the particle kernel) equals the observables of the state
+    the step started from."""
+    w = small_workload()
+    sim, orc, inp = make_pair(w)
+    sim.step(7)
+    before = sim.observables()[0]
+    sim.step(1)
+    row = sim.diagnostics(4)[0][-1]
+    assert row["step"] == 7
+    assert row["mass"] == pytest.approx(before["mass"], rel=1e-10)
+    for a, k in enumerate("xyz"):
+        assert row["p_fluid"][a] == pytest.approx(before[f"p_fluid_{k}"], rel=1e-5, abs=1e-9)
+        assert row["p_beads"][a] == pytest.approx(before[f"p_beads_{k}"], rel=1e-6, abs=1e-12)
+        assert row["com"][a] == pytest.approx(before[f"com_{k}"], rel=1e-7)
+    assert row["dWH_dt"] == pytest.approx(before["dWH_dt"], rel=1e-4, abs=1e-10)
+
+
+def test_graph_eager_and_tiles_are_bit_identical():
+    w = small_workload()
+    runs = []
+    for mode in ("eager", "graph", "tiles"):
+        sim, orc, inp = make_pair(w)
+        if mode == "graph":
+            sim.set_graph(4)
+        if mode == "tiles":
+            sim.set_tiles(2, 3)
+        sim.step(10)
+        runs.append((sim.get_populations(), *sim.get_beads()))
+    for other in runs[1:]:
+        for a, b in zip(runs[0], other):
+            assert np.array_equal(a, b)
+
+
+def test_autotune_keeps_results():
+    w = small_workload()
+    sim, orc, inp = make_pair(w)
+    sim.step(3)
+    by, zc = sim.autotune(2)
+    assert (by, zc) == sim.tiles()
+    sim.step(3)
+    sim2, _, _ = make_pair(w)
+    sim2.step(6)
+    assert np.array_equal(sim.get_populations(), sim2.get_populations())
+
+
+def test_ensemble_realizations_match_oracle():
+    """Three realizations with chains of different lengths in one launch; each
+    matches its own oracle run (realization index in the Philox key)."""
+    w = small_workload(n_real=3, n_beads=(10, 30), chain_seed=11)
+    inp = workloads.build_inputs(w)
+    assert len(set(inp["counts"].tolist())) > 1
+    sim = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"])
+    sim.step(4)
+    f_all = sim.get_populations()
+    r_all, v_all = sim.get_beads()
+    for r in range(3):
+        o0, o1 = inp["offsets"][r], inp["offsets"][r + 1]
+        orc = oracle.OracleSim(workloads.oracle_params(w, r, o1 - o0), inp["solid"])
+        orc.set_beads(inp["r0"][o0:o1])
+        orc.step(4)
+        assert rel_err(f_all[r], orc.get_populations()) < 1e-5
+        ro, vo = orc.get_beads()
+        assert np.abs(r_all[o0:o1] - ro).max() < 1e-5
+        assert np.abs(v_all[o0:o1] - vo).max() < 1e-5 * np.abs(vo).max() + 1e-7
+
+
+def test_nonfinite_state_is_reported():
+    """A NaN planted in the populations (host-side fault injection) is caught
+    by the step's diagnostics and reported by lbmd_check."""
+    w = small_workload()
+    sim, orc, inp = make_pair(w)
+    f = sim.get_populations()
+    f[0, 3, 5, 7, 9] = np.nan
+    sim.set_populations(f)
+    sim.step(2)
+    with pytest.raises(lbmd.LbmdError) as e:
+        sim.check()
+    assert e.value.status == 3

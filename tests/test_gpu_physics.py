@@ -1,0 +1,116 @@
+"""Physics the CUDA path must reproduce on its own (same pins as the oracle's,
+at FP32 / FP16 tolerances), and the FP16-deviation storage mode against the
+FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import make_pair, rel_err, small_workload
+from paper_0711_2665_gb300 import inputs, lbmd, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _fluid_only(nx, ny, nz, tau, solid=None, precision="fp32", body=(0.0, 0.0, 0.0)):
+    w = workloads.get("plain_fp64_small", nx=nx, ny=ny, nz=nz, tau=tau, wall_x=-1, pore_h=0,
+                      n_beads=0, body_force=body, precision=precision)
+    if solid is None:
+        solid = np.zeros((nz, ny, nx), np.uint8)
+    sim = lbmd.Simulation(w, solid, np.array([0, 0], np.int32), np.zeros((0, 3)))
+    return sim
+
+
+def _shear_rate(sim, nx, n1=60, n2=400):
+    k = 2 * np.pi / nx
+    s = np.sin(k * np.arange(nx))
+    c, _, _ = oracle.tables()
+
+    def amp():
+        f = sim.get_populations()[0].astype(np.float64)
+        rho = f.sum(0)
+        uy = np.einsum("izyx,i->zyx", f, c[:, 1].astype(float)) / rho
+        return 2.0 / nx * float(uy.mean(axis=(0, 1)) @ s)
+
+    sim.step(n1)
+    a1 = amp()
+    sim.step(n2)
+    a2 = amp()
+    return (a2 / a1) ** (1.0 / n2), a1
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 2e-5), ("fp16dev", 2e-3)])
+def test_shear_wave_decay(precision, tol):
+    """u_y = 1e-3 sin(2 pi x / 32): decay per step against the oracle's FP64
+    run (itself pinned to the linearised-LBGK eigenvalue).  The FP16-deviation
+    error is the one stated for the reduced-precision mode."""
+    nx, tau = 32, 0.8
+    sim = _fluid_only(nx, 4, 4, tau, precision=precision)
+    u0 = inputs.shear_wave_velocity(nx, 4, 4, 1e-3)
+    sim.init_fluid(None, u0[None])
+    rate_g, _ = _shear_rate(sim, nx)
+    orc = oracle.OracleSim(dict(nx=nx, ny=4, nz=4, tau=tau))
+    orc.init_fluid(None, u0)
+
+    class _O:
+        def step(self, n): orc.step(n)
+        def get_populations(self): return orc.get_populations()[None]
+
+    rate_o, _ = _shear_rate(_O(), nx)
+    assert abs(rate_g - rate_o) <= tol * (1 - rate_o), (rate_g, rate_o)
+
+
+def test_poiseuille_curvature_fp32():
+    ny, tau, g = 17, 0.8, 1e-5
+    solid = inputs.slab_walls_mask(2, ny, 2, axis="y")
+    sim = _fluid_only(2, ny, 2, tau, solid=solid, body=(g, 0.0, 0.0))
+    sim.step(12000)
+    f = sim.get_populations()[0].astype(np.float64)
+    c, _, _ = oracle.tables()
+    rho = f.sum(0)
+    ux = np.einsum("izyx,i->zyx", f, c[:, 0].astype(float))[:, 1:, :] / rho[:, 1:, :]
+    prof = ux.mean(axis=(0, 2))
+    d2 = prof[2:] - 2 * prof[1:-1] + prof[:-2]
+    nu = (tau - 0.5) / 3
+    assert np.allclose(d2, -g / nu, rtol=2e-3)
+
+
+def test_momentum_and_mass_conserved_gpu():
+    """Periodic box, no wall, no field, noise on: fluid + bead momentum and
+    the fluid mass stay constant to FP32 rounding of the state."""
+    w = small_workload(wall_x=-1, E=0.0, kT=1e-4, n_beads=16)
+    solid = np.zeros((w["nz"], w["ny"], w["nx"]), np.uint8)
+    r0 = inputs.chain_walk(16, (w["nx"], w["ny"], w["nz"]), -1, solid, 5)
+    sim = lbmd.Simulation(w, solid, np.array([0, 16], np.int32), r0)
+    rng = np.random.default_rng(2)
+    sim.set_beads(r0, 0.05 * rng.standard_normal((16, 3)))
+    o0 = sim.observables()[0]
+    sim.step(200)
+    o1 = sim.observables()[0]
+    P0 = np.array([o0[f"p_fluid_{k}"] + o0[f"p_beads_{k}"] for k in "xyz"])
+    P1 = np.array([o1[f"p_fluid_{k}"] + o1[f"p_beads_{k}"] for k in "xyz"])
+    assert np.abs(P0).max() > 0.05
+    assert np.abs(P1 - P0).max() < 1e-4 * np.abs(P0).max()
+    assert abs(o1["mass"] - o0["mass"]) < 1e-6 * o0["mass"]
+
+
+def test_fp16dev_one_step_error_is_bounded():
+    """FP16 deviation storage: one step from the same FP16-representable state
+    differs from the FP64 oracle by at most the storage rounding
+    (half an fp16 ulp of the largest deviation, 2^-12 relative) plus FP32."""
+    from gpu_helpers import to_f32_state, load_state
+    w = small_workload(precision="fp16dev")
+    sim, orc, inp = make_pair(w)
+    orc.step(20)
+    f32, r, v = to_f32_state(orc)
+    _, wts, _ = oracle.tables()
+    fluid = (inp["solid"] == 0)
+    dev = (f32 - wts[:, None, None, None].astype(np.float32)) * 4096.0
+    f16 = (dev.astype(np.float16).astype(np.float32) / 4096.0 + wts[:, None, None, None].astype(np.float32))
+    f16[:, ~fluid] = 0
+    load_state(sim, orc, f16.astype(np.float32), r, v, 20)
+    sim.step(1)
+    orc.step(1)
+    fo = orc.get_populations()
+    fg = sim.get_populations()[0]
+    devmax = np.abs(fo - wts[:, None, None, None])[:, fluid].max()
+    assert np.abs(fg - fo)[:, fluid].max() <= 2.0 ** -11 * devmax + 1e-6
