@@ -57,7 +57,7 @@ typedef enum {
 } lbmd_status;
 
 typedef enum {
-    LBMD_FP32 = 0,    /* populations stored as FP32 */
+    LBMD_FP32 = 0,    /* populations stored as FP32 deviations f_i - w_i */
     LBMD_FP16DEV = 1  /* populations stored as FP16 deviations (f_i - w_i) * 2^12, FP32 arithmetic */
 } lbmd_precision;
 
@@ -162,6 +162,9 @@ lbmd_status lbmd_init_fluid(lbmd_handle *h, const double *rho, const double *u);
  * f: host [n_real][19][ns]; solid sites read as 0. */
 lbmd_status lbmd_get_populations(lbmd_handle *h, float *f);
 lbmd_status lbmd_set_populations(lbmd_handle *h, const float *f);
+/* The same state as deviations from rest, h = f - w_i (what the library
+ * stores), in FP32: accurate where the flow is weak.  Host [n_real][19][ns]. */
+lbmd_status lbmd_get_deviations(lbmd_handle *h, float *dev);
 
 /* Bead state: r unwrapped positions, v velocities; host [total_beads][3]. */
 lbmd_status lbmd_get_beads(lbmd_handle *h, double *r, double *v);
@@ -182,7 +185,9 @@ lbmd_status lbmd_set_graph(lbmd_handle *h, int32_t steps_per_graph);
 
 /* Launch shapes of the stream-collide kernel: block (32, by) threads, each
  * thread walking zc consecutive z planes.  by in {1,2,4,8,16}, zc in 1..64.
- * Results are bit-identical for every shape. */
+ * The state (populations, beads) is bit-identical for every shape; the FP64
+ * diagnostics sums group their FP32 per-thread partials by shape and so agree
+ * to rounding only. */
 lbmd_status lbmd_set_tiles(lbmd_handle *h, int32_t by, int32_t zc);
 lbmd_status lbmd_get_tiles(lbmd_handle *h, int32_t *by, int32_t *zc);
 
@@ -191,7 +196,10 @@ lbmd_status lbmd_get_tiles(lbmd_handle *h, int32_t *by, int32_t *zc);
 lbmd_status lbmd_autotune(lbmd_handle *h, int32_t steps_per_candidate, int32_t *by, int32_t *zc);
 
 /* Per-kernel timing with CUDA events on the launching streams (eager launches
- * only while enabled) and the count of kernels this handle launched. */
+ * only while enabled) and the count of kernels this handle launched.  While
+ * enabled, the particle kernel of realization 0 also records the SM-clock
+ * cycles of its phases (gather, lists, md, spread), reported as extra entries
+ * "particles.<phase>" converted to ms at the device's nominal SM clock. */
 lbmd_status lbmd_profile(lbmd_handle *h, int32_t enable);
 lbmd_status lbmd_kernel_times(lbmd_handle *h, lbmd_kernel_time *out, int32_t max_entries,
                               int32_t *n_entries);

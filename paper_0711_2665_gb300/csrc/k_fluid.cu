@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(512) k_stream_collide(const Sim S, const void 
                 const uint32_t src = (uint32_t)(sx + nx * (sy + ny * sz));
                 const bool bb = (lm >> i) & 1u;
                 const uint32_t idx = bb ? (uint32_t)opp(i) * ns + (uint32_t)s : (uint32_t)i * ns + src;
-                h[i] = load_dev(A, idx, wq(i));
+                h[i] = load_dev(A, idx);
             }
             float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(512) k_stream_collide(const Sim S, const void 
                     float hn = h[i] + om * (heq - h[i]);
                     if (has_g)
                         hn += 3.0f * wq(i) * ((float)cx(i) * g0 + (float)cy(i) * g1 + (float)cz(i) * g2);
-                    store_dev(B, (uint32_t)i * ns + (uint32_t)s, hn, wq(i));
+                    store_dev(B, (uint32_t)i * ns + (uint32_t)s, hn);
                 }
             }
         }
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(256) k_source(const Sim S, void *__restrict__ 
             for (int i = 0; i < Q; ++i) {
                 const float src = 3.0f * wq(i) * ((float)cx(i) * G0 + (float)cy(i) * G1 + (float)cz(i) * G2);
                 const uint32_t idx = (uint32_t)i * (uint32_t)ns + (uint32_t)s;
-                store_dev(B, idx, load_dev_cg(B, idx, wq(i)) + src, wq(i));
+                store_dev(B, idx, load_dev_cg(B, idx) + src);
             }
         }
     }
@@ -265,7 +265,9 @@ cudaError_t launch_source(const Sim &S, void *B, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// state transfer
+// state transfer.  The fp32 staging area holds either full populations f
+// (host-visible format) or deviations h = f - w (DEV); conversions between the
+// two use the exact weights in double precision.
 // ---------------------------------------------------------------------------
 template <int PREC>
 __global__ void k_init_rest(const Sim S, void *Av) {
@@ -275,9 +277,8 @@ __global__ void k_init_rest(const Sim S, void *Av) {
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
         const size_t r = t / ns, s = t - r * ns;
         T *A = reinterpret_cast<T *>(Av) + r * Q * ns;
-        const bool sol = S.solid[s] != 0;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) store_dev(A, (uint32_t)(i * ns + s), 0.0f, sol ? 0.0f : wq(i));
+        for (int i = 0; i < Q; ++i) store_dev(A, (uint32_t)(i * ns + s), 0.0f);
     }
 }
 
@@ -287,21 +288,22 @@ cudaError_t launch_init_rest(const Sim &S, void *A, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// rho, ux, uy, uz in staging rows 15..18 -> f_eq(rho, u) in rows 0..18 (fp32 full values)
+// rho, ux, uy, uz in staging rows 15..18 -> deviations of f_eq(rho, u) (Eq. 5)
+// in rows 0..18
 __global__ void k_feq_to_staging(const Sim S, float *stg) {
     const size_t ns = (size_t)S.ns;
     const size_t total = ns * S.n_real;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
         const size_t r = t / ns, s = t - r * ns;
         float *f = stg + r * Q * ns + s;
-        const float rho = f[15 * ns], ux = f[16 * ns], uy = f[17 * ns], uz = f[18 * ns];
+        const double rho = f[15 * ns], ux = f[16 * ns], uy = f[17 * ns], uz = f[18 * ns];
         const bool sol = S.solid[s] != 0;
-        const float usq = 1.5f * (ux * ux + uy * uy + uz * uz);
+        const double usq = 1.5 * (ux * ux + uy * uy + uz * uz);
         float out[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const float cu = 3.0f * ((float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz);
-            out[i] = sol ? 0.0f : wq(i) * rho * (1.0f + cu + 0.5f * cu * cu - usq);
+            const double cu = 3.0 * (cx(i) * ux + cy(i) * uy + cz(i) * uz);
+            out[i] = sol ? 0.0f : (float)(wq_exact(i) * ((rho - 1.0) + rho * (cu + 0.5 * cu * cu - usq)));
         }
 #pragma unroll
         for (int i = 0; i < Q; ++i) f[i * ns] = out[i];
@@ -313,8 +315,8 @@ cudaError_t launch_feq_to_staging(const Sim &S, float *staging, cudaStream_t st)
     return cudaGetLastError();
 }
 
-// pulled populations f^n (what the next step starts from) -> staging, full fp32 values
-template <int PREC>
+// pulled populations f^n (what the next step starts from) -> staging
+template <int PREC, bool DEV>
 __global__ void k_pull_to_staging(const Sim S, const void *Av, float *stg) {
     using T = typename PopT<PREC>::T;
     const size_t ns = (size_t)S.ns;
@@ -334,21 +336,27 @@ __global__ void k_pull_to_staging(const Sim S, const void *Av, float *stg) {
                 else
                     idx = (uint32_t)(i * ns + wrapi(x - cx(i), S.nx) +
                                      (size_t)S.nx * (wrapi(y - cy(i), S.ny) + (size_t)S.ny * wrapi(z - cz(i), S.nz)));
-                v = wq(i) + load_dev(A, idx, wq(i));
+                const float h = load_dev(A, idx);
+                v = DEV ? h : (float)(wq_exact(i) + (double)h);
             }
             f[i * ns] = v;
         }
     }
 }
 
-cudaError_t launch_pull_to_staging(const Sim &S, const void *A, float *staging, cudaStream_t st) {
-    if (S.precision == LBMD_FP16DEV) k_pull_to_staging<1><<<4 * 152, 256, 0, st>>>(S, A, staging);
-    else k_pull_to_staging<0><<<4 * 152, 256, 0, st>>>(S, A, staging);
+cudaError_t launch_pull_to_staging(const Sim &S, const void *A, float *staging, bool dev, cudaStream_t st) {
+    if (S.precision == LBMD_FP16DEV) {
+        if (dev) k_pull_to_staging<1, true><<<4 * 152, 256, 0, st>>>(S, A, staging);
+        else k_pull_to_staging<1, false><<<4 * 152, 256, 0, st>>>(S, A, staging);
+    } else {
+        if (dev) k_pull_to_staging<0, true><<<4 * 152, 256, 0, st>>>(S, A, staging);
+        else k_pull_to_staging<0, false><<<4 * 152, 256, 0, st>>>(S, A, staging);
+    }
     return cudaGetLastError();
 }
 
 // inverse of the pull: A_i(y) = f_i(y + c_i), or f_opp(i)(y) when y + c_i is solid
-template <int PREC>
+template <int PREC, bool DEV>
 __global__ void k_push_from_staging(const Sim S, const float *stg, void *Av) {
     using T = typename PopT<PREC>::T;
     const size_t ns = (size_t)S.ns;
@@ -361,23 +369,31 @@ __global__ void k_push_from_staging(const Sim S, const float *stg, void *Av) {
         const int x = (int)(s % S.nx), y = (int)((s / S.nx) % S.ny), z = (int)(s / ((size_t)S.nx * S.ny));
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            float v = 0.0f;
+            float h = 0.0f;
             if (!(lm & SOLID_BIT)) {
-                if ((lm >> opp(i)) & 1u) v = f[opp(i) * ns + s];
-                else
-                    v = f[i * ns + wrapi(x + cx(i), S.nx) +
-                          (size_t)S.nx * (wrapi(y + cy(i), S.ny) + (size_t)S.ny * wrapi(z + cz(i), S.nz))];
-                store_dev(A, (uint32_t)(i * ns + s), v - wq(i), wq(i));
-            } else {
-                store_dev(A, (uint32_t)(i * ns + s), 0.0f, 0.0f);
+                int k;
+                size_t src;
+                if ((lm >> opp(i)) & 1u) { k = opp(i); src = s; }
+                else {
+                    k = i;
+                    src = wrapi(x + cx(i), S.nx) + (size_t)S.nx * (wrapi(y + cy(i), S.ny) + (size_t)S.ny * wrapi(z + cz(i), S.nz));
+                }
+                const float v = f[k * ns + src];
+                h = DEV ? v : (float)((double)v - wq_exact(i));
             }
+            store_dev(A, (uint32_t)(i * ns + s), h);
         }
     }
 }
 
-cudaError_t launch_push_from_staging(const Sim &S, const float *staging, void *A, cudaStream_t st) {
-    if (S.precision == LBMD_FP16DEV) k_push_from_staging<1><<<4 * 152, 256, 0, st>>>(S, staging, A);
-    else k_push_from_staging<0><<<4 * 152, 256, 0, st>>>(S, staging, A);
+cudaError_t launch_push_from_staging(const Sim &S, const float *staging, void *A, bool dev, cudaStream_t st) {
+    if (S.precision == LBMD_FP16DEV) {
+        if (dev) k_push_from_staging<1, true><<<4 * 152, 256, 0, st>>>(S, staging, A);
+        else k_push_from_staging<1, false><<<4 * 152, 256, 0, st>>>(S, staging, A);
+    } else {
+        if (dev) k_push_from_staging<0, true><<<4 * 152, 256, 0, st>>>(S, staging, A);
+        else k_push_from_staging<0, false><<<4 * 152, 256, 0, st>>>(S, staging, A);
+    }
     return cudaGetLastError();
 }
 

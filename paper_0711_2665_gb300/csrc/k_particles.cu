@@ -85,7 +85,10 @@ __device__ __forceinline__ void corner_of(const Sim &S, float xw, float yw, floa
     if (S.solid[node]) w = 0.0f;
 }
 
-// sum over the 8 corners held by lanes 4c..4c+3 (same tree in gather and spread)
+// Sum over the 8 corners: lane l holds corner l >> 2, and the xor tree over
+// 4, 8, 16 visits the 8 lanes l ^ m that share l's sub-lane, one per corner,
+// so every lane gets the full sum as long as all 4 sub-lanes of a corner hold
+// the same value.  Same tree in gather and spread.
 __device__ __forceinline__ float corner_sum(float v) {
     v += __shfl_xor_sync(0xffffffffu, v, 4);
     v += __shfl_xor_sync(0xffffffffu, v, 8);
@@ -107,8 +110,8 @@ __device__ __forceinline__ float3 gather_warp(const Sim &S, const T *__restrict_
     int xi, yi, zi, node;
     float w;
     corner_of(S, xw, yw, zw, c, xi, yi, zi, node, w);
-    const float wsum = corner_sum(sub == 0 ? w : 0.0f);
-    float m = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+    const float wsum = corner_sum(w);
+    float m = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;  // rho - 1 and rho u at the corner
     if (w > 0.0f) {
         const uint32_t lm = __ldg(S.link + node);
         const uint32_t ns = (uint32_t)S.ns;
@@ -120,16 +123,17 @@ __device__ __forceinline__ float3 gather_warp(const Sim &S, const T *__restrict_
             else
                 idx = (uint32_t)i * ns +
                       (uint32_t)(wrapi(xi - cx(i), S.nx) + S.nx * (wrapi(yi - cy(i), S.ny) + S.ny * wrapi(zi - cz(i), S.nz)));
-            const float f = wq(i) + load_dev_cg(A, idx, wq(i));
-            m += f;
-            jx += (float)cx(i) * f;
-            jy += (float)cy(i) * f;
-            jz += (float)cz(i) * f;
+            const float h = load_dev_cg(A, idx);
+            m += h;
+            jx += (float)cx(i) * h;
+            jy += (float)cy(i) * h;
+            jz += (float)cz(i) * h;
         }
     }
     m = sub_sum(m); jx = sub_sum(jx); jy = sub_sum(jy); jz = sub_sum(jz);
     float ux = 0.f, uy = 0.f, uz = 0.f;
-    if (w > 0.0f && m > 0.0f && sub == 0) { ux = w * (jx / m); uy = w * (jy / m); uz = w * (jz / m); }
+    const float rho = 1.0f + m;
+    if (w > 0.0f && rho > 0.0f) { ux = w * (jx / rho); uy = w * (jy / rho); uz = w * (jz / rho); }
     ux = corner_sum(ux); uy = corner_sum(uy); uz = corner_sum(uz);
     if (wsum > 0.0f) return make_float3(ux / wsum, uy / wsum, uz / wsum);
     return make_float3(0.f, 0.f, 0.f);
@@ -306,6 +310,15 @@ __device__ void build_lists(const Sim &S, const PSmem &sm, int buf, int p, int N
     sm.nw[p] = (uint8_t)m;
 }
 
+// SM cycles spent in phase k of realization 0 (only while profiling)
+__device__ __forceinline__ void phase_mark(const Sim &S, int k, unsigned long long &t) {
+    if (S.phase && blockIdx.x == 0 && threadIdx.x == 0) {
+        const unsigned long long now = clock64();
+        atomicAdd(S.phase + k, now - t);
+        t = now;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // FP64 block sum of NV values per thread; result valid in thread 0
 // ---------------------------------------------------------------------------
@@ -362,6 +375,7 @@ __global__ void __launch_bounds__(1024) k_particles(const Sim S, const void *__r
     }
     __syncthreads();
 
+    unsigned long long tclk = clock64();
     // 1. fluid velocity at the beads (warp per bead)
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int q = warp; q < N; q += nwarps) {
@@ -369,9 +383,12 @@ __global__ void __launch_bounds__(1024) k_particles(const Sim S, const void *__r
         const float3 u = gather_warp(S, A, ff_wrap(qh.x, ql.x, fnx), ff_wrap(qh.y, ql.y, fny), ff_wrap(qh.z, ql.z, fnz));
         if ((threadIdx.x & 31) == 0) sm.ups[q] = make_float4(u.x, u.y, u.z, 0.f);
     }
+    __syncthreads();
+    phase_mark(S, 0, tclk);
     // neighbour and wall lists at the starting positions (contains barriers)
     build_lists(S, sm, 0, p, N, own, mh, ml, &s_flag, &s_err);
     __syncthreads();
+    phase_mark(S, 1, tclk);
 
     float3 up = make_float3(0.f, 0.f, 0.f);
     if (own) { const float4 t = sm.ups[p]; up = make_float3(t.x, t.y, t.z); }
@@ -452,6 +469,7 @@ __global__ void __launch_bounds__(1024) k_particles(const Sim S, const void *__r
     }
     if (own) sm.ups[p] = make_float4(J.x, J.y, J.z, 0.f);
     __syncthreads();
+    phase_mark(S, 2, tclk);
 
     // 3. spread -W J onto the fluid corners of the starting position (warp per bead)
     {
@@ -463,7 +481,7 @@ __global__ void __launch_bounds__(1024) k_particles(const Sim S, const void *__r
             float w;
             corner_of(S, ff_wrap(qh.x, ql.x, fnx), ff_wrap(qh.y, ql.y, fny), ff_wrap(qh.z, ql.z, fnz), c, xi, yi, zi,
                       node, w);
-            const float wsum = corner_sum(sub == 0 ? w : 0.0f);
+            const float wsum = corner_sum(w);
             const float W = wsum > 0.0f ? w / wsum : 0.0f;
             const float4 Jq = sm.ups[q];
             if (sub < 3 && W > 0.0f) {
@@ -475,6 +493,7 @@ __global__ void __launch_bounds__(1024) k_particles(const Sim S, const void *__r
         }
     }
     __syncthreads();
+    phase_mark(S, 3, tclk);
 
     if (own) {
         ff_norm(mh.x, ml.x);

@@ -22,7 +22,7 @@ constexpr double SKIN = 0.5;  // Verlet-list skin (lattice units)
 
 struct Layout {
     size_t popA, popB, staging, link, tileflag, solid, G, stamp;
-    size_t r_hi, r_lo, v, up, J, pair_node, bead_off, partial, ring, obs, ctrl, total;
+    size_t r_hi, r_lo, v, up, J, pair_node, bead_off, partial, ring, obs, ctrl, phase, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -132,6 +132,7 @@ Layout layout_of(const lbmd_config *c, int total_beads) {
     L.ring = take((size_t)c->n_real * LBMD_DIAG_RING * sizeof(lbmd_diag));
     L.obs = take((size_t)c->n_real * sizeof(lbmd_obs));
     L.ctrl = take(sizeof(Ctrl));
+    L.phase = take(PHASES * sizeof(unsigned long long));
     L.total = o;
     return L;
 }
@@ -394,6 +395,7 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
     S.ring = (lbmd_diag *)(b + L.ring);
     S.obs = (lbmd_obs *)(b + L.obs);
     S.ctrl = (Ctrl *)(b + L.ctrl);
+    S.phase = nullptr;
 
 #define CKI(call)                                                           \
     do {                                                                    \
@@ -509,15 +511,15 @@ lbmd_status lbmd_init_fluid(lbmd_handle *h, const double *rho, const double *u) 
         CK(cudaStreamSynchronize(h->st));
     }
     CK(launch_feq_to_staging(h->S, h->staging, h->st));
-    CK(launch_push_from_staging(h->S, h->staging, h->popA, h->st));
+    CK(launch_push_from_staging(h->S, h->staging, h->popA, true, h->st));
     h->launches += 2;
     CK(cudaStreamSynchronize(h->st));
     return LBMD_OK;
 }
 
-lbmd_status lbmd_get_populations(lbmd_handle *h, float *f) {
+static lbmd_status pull_out(lbmd_handle *h, float *f, bool dev) {
     if (!h || !f) return LBMD_ERR_INVALID_ARG;
-    CK(launch_pull_to_staging(h->S, h->popA, h->staging, h->st));
+    CK(launch_pull_to_staging(h->S, h->popA, h->staging, dev, h->st));
     h->launches += 1;
     CK(cudaMemcpyAsync(f, h->staging, (size_t)h->cfg.n_real * LBMD_Q * h->S.ns * sizeof(float),
                        cudaMemcpyDeviceToHost, h->st));
@@ -525,11 +527,15 @@ lbmd_status lbmd_get_populations(lbmd_handle *h, float *f) {
     return LBMD_OK;
 }
 
+lbmd_status lbmd_get_populations(lbmd_handle *h, float *f) { return pull_out(h, f, false); }
+
+lbmd_status lbmd_get_deviations(lbmd_handle *h, float *dev) { return pull_out(h, dev, true); }
+
 lbmd_status lbmd_set_populations(lbmd_handle *h, const float *f) {
     if (!h || !f) return LBMD_ERR_INVALID_ARG;
     CK(cudaMemcpyAsync(h->staging, f, (size_t)h->cfg.n_real * LBMD_Q * h->S.ns * sizeof(float),
                        cudaMemcpyHostToDevice, h->st));
-    CK(launch_push_from_staging(h->S, h->staging, h->popA, h->st));
+    CK(launch_push_from_staging(h->S, h->staging, h->popA, false, h->st));
     h->launches += 1;
     CK(cudaStreamSynchronize(h->st));
     return LBMD_OK;
@@ -667,9 +673,13 @@ lbmd_status lbmd_profile(lbmd_handle *h, int32_t enable) {
     if (!h) return LBMD_ERR_INVALID_ARG;
     lbmd_status s = resolve_profile(h);
     if (s != LBMD_OK) return s;
-    if (enable && !h->profiling)
+    if (enable && !h->profiling) {
         for (int k = 0; k < K_COUNT; ++k) { h->prof_ms[k] = 0; h->prof_n[k] = 0; }
+        CK(cudaMemsetAsync(h->dbuf + h->L.phase, 0, PHASES * sizeof(unsigned long long), h->st));
+    }
     h->profiling = enable != 0;
+    h->S.phase = h->profiling ? (unsigned long long *)(h->dbuf + h->L.phase) : nullptr;
+    drop_graph(h);
     return LBMD_OK;
 }
 
@@ -677,13 +687,25 @@ lbmd_status lbmd_kernel_times(lbmd_handle *h, lbmd_kernel_time *out, int32_t max
     if (!h || !n_entries || (max_entries > 0 && !out)) return LBMD_ERR_INVALID_ARG;
     lbmd_status s = resolve_profile(h);
     if (s != LBMD_OK) return s;
-    const int n = std::min<int>(max_entries, K_COUNT);
-    for (int k = 0; k < n; ++k) {
-        memset(out[k].name, 0, sizeof(out[k].name));
-        strncpy(out[k].name, KNAMES[k], sizeof(out[k].name) - 1);
-        out[k].launches = h->prof_n[k];
-        out[k].total_ms = h->prof_ms[k];
-    }
+    static const char *PNAMES[PHASES] = {"particles.gather", "particles.lists", "particles.md", "particles.spread"};
+    unsigned long long cyc[PHASES] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(cyc, h->dbuf + h->L.phase, sizeof(cyc), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    int dev = 0, khz = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+    int n = 0;
+    auto put = [&](const char *name, long long launches, double ms) {
+        if (n >= max_entries) return;
+        memset(out[n].name, 0, sizeof(out[n].name));
+        strncpy(out[n].name, name, sizeof(out[n].name) - 1);
+        out[n].launches = launches;
+        out[n].total_ms = ms;
+        ++n;
+    };
+    for (int k = 0; k < K_COUNT; ++k) put(KNAMES[k], h->prof_n[k], h->prof_ms[k]);
+    for (int k = 0; k < PHASES; ++k)
+        put(PNAMES[k], h->prof_n[K_PARTICLES], khz > 0 ? (double)cyc[k] / (double)khz : 0.0);
     *n_entries = n;
     return LBMD_OK;
 }

@@ -108,34 +108,37 @@ struct Sim {
     lbmd_diag *ring;         // [n_real][LBMD_DIAG_RING]
     lbmd_obs *obs;           // [n_real]
     Ctrl *ctrl;
+    unsigned long long *phase;  // [PHASES] SM cycles per particle-kernel phase, or null
 };
+
+constexpr int PHASES = 4;   // gather, lists, md, spread
 
 // ---------------------------------------------------------------------------
 // population storage
 // ---------------------------------------------------------------------------
-// PREC 0 stores f in fp32; PREC 1 stores (f - w) * 2^12 in fp16.  Both helpers
-// speak deviations h = f - w so that the arithmetic is the same for both.
+// Both precisions store deviations from the rest state, h = f - w (PREC 0:
+// fp32 h; PREC 1: fp16 h * 2^12), so the constant w_i is exact by definition
+// and rounding is relative to the (small) deviation, not to w_i.
 template <int PREC> struct PopT;
 template <> struct PopT<0> { using T = float; };
 template <> struct PopT<1> { using T = __half; };
 
-__device__ __forceinline__ float load_dev(const float *base, uint32_t idx, float w) {
-    return __ldg(base + idx) - w;
+// exact weights for host-visible conversions f <-> h
+__host__ __device__ constexpr double wq_exact(int i) {
+    return i == 0 ? (1.0 / 3.0) : (i <= 6 ? (1.0 / 18.0) : (1.0 / 36.0));
 }
-__device__ __forceinline__ float load_dev(const __half *base, uint32_t idx, float) {
+
+__device__ __forceinline__ float load_dev(const float *base, uint32_t idx) { return __ldg(base + idx); }
+__device__ __forceinline__ float load_dev(const __half *base, uint32_t idx) {
     return __half2float(__ldg(base + idx)) * FP16_INV_SCALE;
 }
-// plain (coherent) load for data written earlier in the same kernel
-__device__ __forceinline__ float load_dev_cg(const float *base, uint32_t idx, float w) {
-    return __ldcg(base + idx) - w;
-}
-__device__ __forceinline__ float load_dev_cg(const __half *base, uint32_t idx, float) {
+// coherent load for data another kernel of the same step may have written
+__device__ __forceinline__ float load_dev_cg(const float *base, uint32_t idx) { return __ldcg(base + idx); }
+__device__ __forceinline__ float load_dev_cg(const __half *base, uint32_t idx) {
     return __half2float(__ldcg(base + idx)) * FP16_INV_SCALE;
 }
-__device__ __forceinline__ void store_dev(float *base, uint32_t idx, float h, float w) {
-    base[idx] = w + h;
-}
-__device__ __forceinline__ void store_dev(__half *base, uint32_t idx, float h, float) {
+__device__ __forceinline__ void store_dev(float *base, uint32_t idx, float h) { base[idx] = h; }
+__device__ __forceinline__ void store_dev(__half *base, uint32_t idx, float h) {
     base[idx] = __float2half_rn(h * FP16_SCALE);
 }
 
@@ -242,8 +245,8 @@ cudaError_t launch_fluid_observables(const Sim &S, const void *A, cudaStream_t s
 cudaError_t launch_source(const Sim &S, void *B, cudaStream_t st);
 cudaError_t launch_init_rest(const Sim &S, void *A, cudaStream_t st);
 cudaError_t launch_feq_to_staging(const Sim &S, float *staging, cudaStream_t st);
-cudaError_t launch_pull_to_staging(const Sim &S, const void *A, float *staging, cudaStream_t st);
-cudaError_t launch_push_from_staging(const Sim &S, const float *staging, void *A, cudaStream_t st);
+cudaError_t launch_pull_to_staging(const Sim &S, const void *A, float *staging, bool dev, cudaStream_t st);
+cudaError_t launch_push_from_staging(const Sim &S, const float *staging, void *A, bool dev, cudaStream_t st);
 size_t particle_smem_bytes(int threads);
 int particle_threads(const Sim &S);
 cudaError_t launch_particles(const Sim &S, const void *A, cudaStream_t st);

@@ -94,6 +94,7 @@ def lib():
         "lbmd_diagnostics": [vp, P(Diag), i32, P(i32)],
         "lbmd_init_fluid": [vp, vp, vp],
         "lbmd_get_populations": [vp, vp],
+        "lbmd_get_deviations": [vp, vp],
         "lbmd_set_populations": [vp, vp],
         "lbmd_get_beads": [vp, vp, vp],
         "lbmd_set_beads": [vp, vp, vp],
@@ -175,7 +176,13 @@ class Simulation:
             self.buffer = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=self.device)
             base = self.buffer.data_ptr()
             aligned = (base + 255) & ~255
+            # the library orders its work on the caller's current stream; the
+            # legacy default stream cannot be captured into a CUDA graph, so a
+            # simulation created there gets a stream of its own
             self.stream = torch.cuda.current_stream(self.device)
+            if self.stream.cuda_stream == 0:
+                self.stream = torch.cuda.Stream(device=self.device)
+                self.stream.wait_stream(torch.cuda.current_stream(self.device))
             h = ctypes.c_void_p()
             st = self._lib.lbmd_init(ctypes.byref(self.cfg), _ptr(solid), _ptr(self.offsets), _ptr(r),
                                      ctypes.c_void_p(aligned), self.nbytes,
@@ -249,6 +256,12 @@ class Simulation:
         self._check(self._lib.lbmd_get_populations(self._h, _ptr(f)), "lbmd_get_populations")
         return f.reshape(self.n_real, LBMD_Q, self.cfg.nz, self.cfg.ny, self.cfg.nx)
 
+    def get_deviations(self) -> np.ndarray:
+        """f - w_i as stored (FP32), shape (n_real, 19, nz, ny, nx)."""
+        f = np.empty(self.n_real * LBMD_Q * self.ns, dtype=np.float32)
+        self._check(self._lib.lbmd_get_deviations(self._h, _ptr(f)), "lbmd_get_deviations")
+        return f.reshape(self.n_real, LBMD_Q, self.cfg.nz, self.cfg.ny, self.cfg.nx)
+
     def set_populations(self, f):
         a = np.ascontiguousarray(f, dtype=np.float32).reshape(-1)
         if a.size != self.n_real * LBMD_Q * self.ns:
@@ -304,9 +317,9 @@ class Simulation:
         self._check(self._lib.lbmd_profile(self._h, int(bool(enable))), "lbmd_profile")
 
     def kernel_times(self) -> dict:
-        arr = (KernelTime * 8)()
+        arr = (KernelTime * 16)()
         n = ctypes.c_int32()
-        self._check(self._lib.lbmd_kernel_times(self._h, arr, 8, ctypes.byref(n)), "lbmd_kernel_times")
+        self._check(self._lib.lbmd_kernel_times(self._h, arr, 16, ctypes.byref(n)), "lbmd_kernel_times")
         return {arr[k].name.decode(): (arr[k].launches, arr[k].total_ms) for k in range(n.value)}
 
     def launch_count(self) -> int:
