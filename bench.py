@@ -215,7 +215,15 @@ def main():
     sim.autotune(3)
     sites = w["nx"] * w["ny"] * w["nz"] * w["n_real"]
     flush = not args.no_flush
-    scratch = torch.empty(256 << 20, dtype=torch.uint8, device=dev) if flush else None
+    # L2 flush between timed steps: write 256 MiB, then read another 256 MiB so
+    # that the L2 ends up holding clean lines (the written lines' write-backs
+    # happen during the read, not inside the next timed step)
+    scratch_w = torch.empty(64 << 20, dtype=torch.float32, device=dev) if flush else None
+    scratch_r = torch.ones(64 << 20, dtype=torch.float32, device=dev) if flush else None
+
+    def flush_l2():
+        scratch_w.zero_()
+        scratch_r.sum()
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -225,7 +233,7 @@ def main():
 
     for _ in range(args.warmup):
         if flush:
-            scratch.zero_()
+            flush_l2()
         sim.step(1)
     barrier()
 
@@ -236,7 +244,7 @@ def main():
         barrier()
         for k in range(args.steps):
             if flush:
-                scratch.zero_()
+                flush_l2()
             ev[k][0].record(stream)
             sim.step(1)
             ev[k][1].record(stream)
@@ -277,7 +285,7 @@ def main():
     sim.set_beads(r_host, v_host)
     for _ in range(args.steps):
         if flush:
-            scratch.zero_()
+            flush_l2()
         sim.step(1)
         sim.diagnostics(1)
     f_back = sim.get_populations()

@@ -98,7 +98,7 @@ __device__ void finalize_fluid_sums(const Sim &S, unsigned int *done, long long 
 // walks zc consecutive z planes.  MODE 0: store; 1: store + per-step sums;
 // 2: sums only (observables).
 // ---------------------------------------------------------------------------
-template <int PREC, int MODE>
+template <int PREC, int MODE, int U>
 __global__ void __launch_bounds__(512) k_stream_collide(const Sim S, const void *__restrict__ Av,
                                                         void *__restrict__ Bv, const int zc,
                                                         const int nzb) {
@@ -122,12 +122,24 @@ __global__ void __launch_bounds__(512) k_stream_collide(const Sim S, const void 
         const int xv0 = (x == 0 ? nx - 1 : x - 1), xv2 = (x == nx - 1 ? 0 : x + 1);
         const int yv0 = (y == 0 ? ny - 1 : y - 1), yv2 = (y == ny - 1 ? 0 : y + 1);
         const int zend = min(z0 + zc, nz);
-        for (int z = z0; z < zend; ++z) {
+        for (int zb = z0; zb < zend; zb += U) {
+          // issue the loads of U consecutive sites before any arithmetic, so
+          // that 19 * U loads per thread are in flight together
+          float hh[U][Q];
+          uint32_t lmu[U];
+          int su[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int z = zb + u;
+            lmu[u] = SOLID_BIT;
+            su[u] = 0;
+            if (z >= zend) continue;
             const int zv0 = (z == 0 ? nz - 1 : z - 1), zv2 = (z == nz - 1 ? 0 : z + 1);
             const int s = x + nx * (y + ny * z);
             const uint32_t lm = S.tileflag[blockIdx.x + S.nxt * (y + ny * z)] ? __ldg(S.link + s) : 0u;
+            lmu[u] = lm;
+            su[u] = s;
             if (lm & SOLID_BIT) continue;
-            float h[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const int sx = cx(i) == 1 ? xv0 : (cx(i) == -1 ? xv2 : x);
@@ -136,8 +148,14 @@ __global__ void __launch_bounds__(512) k_stream_collide(const Sim S, const void 
                 const uint32_t src = (uint32_t)(sx + nx * (sy + ny * sz));
                 const bool bb = (lm >> i) & 1u;
                 const uint32_t idx = bb ? (uint32_t)opp(i) * ns + (uint32_t)s : (uint32_t)i * ns + src;
-                h[i] = load_dev(A, idx);
+                hh[u][i] = load_dev(A, idx);
             }
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            if (lmu[u] & SOLID_BIT) continue;
+            const int s = su[u];
+            const float *h = hh[u];
             float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
@@ -165,6 +183,7 @@ __global__ void __launch_bounds__(512) k_stream_collide(const Sim S, const void 
                     store_dev(B, (uint32_t)i * ns + (uint32_t)s, hn);
                 }
             }
+          }
         }
     }
     if (MODE != 0) {
@@ -192,12 +211,26 @@ cudaError_t launch_stream_collide(const Sim &S, const void *A, void *B, int by, 
     int nzb;
     dim3 grid = sc_grid(S, by, zc, &nzb);
     dim3 block(32, by);
+    // Walking two z sites at a time (U = 2) doubles the loads in flight per
+    // thread but needs ~128 registers with the diagnostics; on GB300 it lost
+    // to the one-site walk at every tile shape, so it is kept off.
+    const bool two = false;
     if (S.precision == LBMD_FP16DEV) {
-        if (diag) k_stream_collide<1, 1><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
-        else k_stream_collide<1, 0><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
+        if (diag) {
+            if (two) k_stream_collide<1, 1, 2><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
+            else k_stream_collide<1, 1, 1><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
+        } else {
+            if (two) k_stream_collide<1, 0, 2><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
+            else k_stream_collide<1, 0, 1><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
+        }
     } else {
-        if (diag) k_stream_collide<0, 1><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
-        else k_stream_collide<0, 0><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
+        if (diag) {
+            if (two) k_stream_collide<0, 1, 2><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
+            else k_stream_collide<0, 1, 1><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
+        } else {
+            if (two) k_stream_collide<0, 0, 2><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
+            else k_stream_collide<0, 0, 1><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
+        }
     }
     return cudaGetLastError();
 }
@@ -207,8 +240,8 @@ cudaError_t launch_fluid_observables(const Sim &S, const void *A, cudaStream_t s
     const int by = 8, zc = 4;
     dim3 grid = sc_grid(S, by, zc, &nzb);
     dim3 block(32, by);
-    if (S.precision == LBMD_FP16DEV) k_stream_collide<1, 2><<<grid, block, 0, st>>>(S, A, nullptr, zc, nzb);
-    else k_stream_collide<0, 2><<<grid, block, 0, st>>>(S, A, nullptr, zc, nzb);
+    if (S.precision == LBMD_FP16DEV) k_stream_collide<1, 2, 2><<<grid, block, 0, st>>>(S, A, nullptr, zc, nzb);
+    else k_stream_collide<0, 2, 2><<<grid, block, 0, st>>>(S, A, nullptr, zc, nzb);
     return cudaGetLastError();
 }
 

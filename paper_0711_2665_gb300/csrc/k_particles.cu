@@ -1,8 +1,9 @@
-// k_particles.cu -- bead side of the coupled LB-MD step, one thread block per
-// realization, one thread per bead:
-//   1. gather: fluid velocity at every bead from the populations the step
-//      starts from (trilinear over fluid corners), frozen for the MD cycle
-//      (Sec. II, text after Eq. 21); one warp per bead, 4 lanes per corner;
+// k_particles.cu -- bead side of the coupled LB-MD step:
+//   1. gather kernel (one warp per bead across the GPU, 4 lanes per corner):
+//      fluid velocity at every bead from the populations the step starts from
+//      (trilinear over fluid corners), frozen for the MD cycle (Sec. II, text
+//      after Eq. 21), plus the corner sites and weights the spread reuses;
+//   particle kernel, one thread block per realization, one thread per bead:
 //   2. MD cycle (Sec. II, Eq. 22 as multiple-time-step velocity Verlet):
 //      M outer steps whose half kicks apply the pore field, the friction
 //      gamma (u_p - v) and Philox noise (Eqs. 12, 13, 15), around M^b inner
@@ -70,7 +71,8 @@ __device__ __forceinline__ float3 ffsub(float4 ah, float4 al, float4 bh, float4 
 
 // ---------------------------------------------------------------------------
 // lattice corner c (0..7) of the cell holding a bead at wrapped (xw, yw, zw):
-// site index and raw trilinear weight (0 on solid sites)
+// site index and raw trilinear weight (solid corners are zeroed by the caller
+// from the site's link word)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void corner_of(const Sim &S, float xw, float yw, float zw, int c, int &xi, int &yi,
                                           int &zi, int &node, float &w) {
@@ -82,7 +84,6 @@ __device__ __forceinline__ void corner_of(const Sim &S, float xw, float yw, floa
     zi = wrapi(z0 + d, S.nz);
     node = xi + S.nx * (yi + S.ny * zi);
     w = (a ? fx : 1.0f - fx) * (b ? fy : 1.0f - fy) * (d ? fz : 1.0f - fz);
-    if (S.solid[node]) w = 0.0f;
 }
 
 // Sum over the 8 corners: lane l holds corner l >> 2, and the xor tree over
@@ -104,31 +105,38 @@ __device__ __forceinline__ float sub_sum(float v) {
 // Fluid velocity at one bead, computed by a whole warp: lanes 4c..4c+3 pull the
 // 19 populations of corner c (links i with i % 4 == lane % 4), form rho and
 // rho u there, and the corners are combined with the renormalised weights.
+// The pulled value and its bounce-back alternative are both loaded up front,
+// so every load of the warp is in flight at once (no dependent chain through
+// the link word).  Each lane returns its corner's site and normalised weight.
 template <typename T>
-__device__ __forceinline__ float3 gather_warp(const Sim &S, const T *__restrict__ A, float xw, float yw, float zw) {
+__device__ __forceinline__ float3 gather_warp(const Sim &S, const T *__restrict__ A, float xw, float yw, float zw,
+                                              int &node, float &W) {
     const int lane = threadIdx.x & 31, c = lane >> 2, sub = lane & 3;
-    int xi, yi, zi, node;
+    int xi, yi, zi;
     float w;
     corner_of(S, xw, yw, zw, c, xi, yi, zi, node, w);
-    const float wsum = corner_sum(w);
-    float m = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;  // rho - 1 and rho u at the corner
-    if (w > 0.0f) {
-        const uint32_t lm = __ldg(S.link + node);
-        const uint32_t ns = (uint32_t)S.ns;
+    const uint32_t ns = (uint32_t)S.ns;
+    const uint32_t lm = __ldg(S.link + node);
+    float hp[5], hb[5];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            if ((i & 3) != sub) continue;
-            uint32_t idx;
-            if ((lm >> i) & 1u) idx = (uint32_t)opp(i) * ns + (uint32_t)node;
-            else
-                idx = (uint32_t)i * ns +
-                      (uint32_t)(wrapi(xi - cx(i), S.nx) + S.nx * (wrapi(yi - cy(i), S.ny) + S.ny * wrapi(zi - cz(i), S.nz)));
-            const float h = load_dev_cg(A, idx);
-            m += h;
-            jx += (float)cx(i) * h;
-            jy += (float)cy(i) * h;
-            jz += (float)cz(i) * h;
-        }
+    for (int i = 0; i < Q; ++i) {
+        if ((i & 3) != sub) continue;
+        const uint32_t src = (uint32_t)(wrapi(xi - cx(i), S.nx) + S.nx * (wrapi(yi - cy(i), S.ny) + S.ny * wrapi(zi - cz(i), S.nz)));
+        hp[i >> 2] = load_dev_cg(A, (uint32_t)i * ns + src);
+        hb[i >> 2] = load_dev_cg(A, (uint32_t)opp(i) * ns + (uint32_t)node);
+    }
+    if (lm & SOLID_BIT) w = 0.0f;
+    const float wsum = corner_sum(w);
+    W = wsum > 0.0f ? w / wsum : 0.0f;
+    float m = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;  // rho - 1 and rho u at the corner
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if ((i & 3) != sub) continue;
+        const float h = ((lm >> i) & 1u) ? hb[i >> 2] : hp[i >> 2];
+        m += h;
+        jx += (float)cx(i) * h;
+        jy += (float)cy(i) * h;
+        jz += (float)cz(i) * h;
     }
     m = sub_sum(m); jx = sub_sum(jx); jy = sub_sum(jy); jz = sub_sum(jz);
     float ux = 0.f, uy = 0.f, uz = 0.f;
@@ -137,6 +145,41 @@ __device__ __forceinline__ float3 gather_warp(const Sim &S, const T *__restrict_
     ux = corner_sum(ux); uy = corner_sum(uy); uz = corner_sum(uz);
     if (wsum > 0.0f) return make_float3(ux / wsum, uy / wsum, uz / wsum);
     return make_float3(0.f, 0.f, 0.f);
+}
+
+// ---------------------------------------------------------------------------
+// gather kernel: one warp per bead over the whole GPU.  Writes the frozen fluid
+// velocity u_p and the (site, weight) of the bead's 8 corners, which the
+// spread of the same step reuses (adjoint pair: same weights both ways).
+// ---------------------------------------------------------------------------
+template <int PREC>
+__global__ void __launch_bounds__(256) k_gather(const Sim S, const void *__restrict__ Av) {
+    using T = typename PopT<PREC>::T;
+    const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // global bead index
+    if (g >= S.total_beads) return;
+    const int r = S.bead_real[g];
+    const T *A = reinterpret_cast<const T *>(Av) + (size_t)r * Q * S.ns;
+    const float4 qh = S.r_hi[g], ql = S.r_lo[g];
+    int node;
+    float W;
+    const float3 u = gather_warp(S, A, ff_wrap(qh.x, ql.x, (float)S.nx, S.inx), ff_wrap(qh.y, ql.y, (float)S.ny, S.iny),
+                                 ff_wrap(qh.z, ql.z, (float)S.nz, S.inz), node, W);
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) S.up[g] = make_float4(u.x, u.y, u.z, 0.f);
+    if ((lane & 3) == 0) {
+        const int c = lane >> 2;
+        S.pair_node[(size_t)g * 8 + c] = W > 0.0f ? (int)((size_t)r * S.ns + node) : -1;
+        S.pair_w[(size_t)g * 8 + c] = W;
+    }
+}
+
+cudaError_t launch_gather(const Sim &S, const void *A, cudaStream_t st) {
+    if (S.total_beads == 0) return cudaSuccess;
+    const int threads = 256;
+    const int blocks = (S.total_beads * 32 + threads - 1) / threads;
+    if (S.precision == LBMD_FP16DEV) k_gather<1><<<blocks, threads, 0, st>>>(S, A);
+    else k_gather<0><<<blocks, threads, 0, st>>>(S, A);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -149,15 +192,15 @@ __device__ __forceinline__ void bend_terms(float3 b1, float3 b2, float kappa, fl
     const float inv12 = rsqrtf(l1s * l2s);
     const float c = dt * inv12, sn = crn * inv12;
     const float phi = atan2f(crn, dt);
-    const float A = sn > 1e-6f ? kappa * phi / sn : (c > 0.0f ? kappa : 0.0f);
-    d1 = A * (inv12 * b2 - (c / l1s) * b1);  // A dcos/db1
-    d2 = A * (inv12 * b1 - (c / l2s) * b2);  // A dcos/db2
+    const float A = sn > 1e-6f ? __fdividef(kappa * phi, sn) : (c > 0.0f ? kappa : 0.0f);
+    d1 = A * (inv12 * b2 - __fdividef(c, l1s) * b1);  // A dcos/db1
+    d2 = A * (inv12 * b1 - __fdividef(c, l2s) * b2);  // A dcos/db2
 }
 
 __device__ __forceinline__ float wca_coef(float r2, float eps, float sig2) {
-    const float sr2 = sig2 / r2;
+    const float ir2 = __frcp_rn(r2), sr2 = sig2 * ir2;
     const float sr6 = sr2 * sr2 * sr2;
-    return 24.0f * eps * (2.0f * sr6 * sr6 - sr6) / r2;
+    return 24.0f * eps * (2.0f * sr6 * sr6 - sr6) * ir2;
 }
 
 __device__ float3 fast_force(const Sim &S, const PSmem &sm, int buf, int p, int N, float4 mh, float4 ml) {
@@ -174,13 +217,15 @@ __device__ float3 fast_force(const Sim &S, const PSmem &sm, int buf, int p, int 
     const float3 b2 = ffsub(hp1, lp1, mh, ml);    // r_{p+1} - r_p
     const float3 b3 = ffsub(hp2, lp2, hp1, lp1);  // r_{p+2} - r_{p+1}
     // harmonic bonds (Eq. 19)
+    // k (|b| - r0) b / |b|; |b| from the correctly rounded sqrt, because
+    // |b| - r0 cancels and keeps only the absolute error of |b|
     if (m1) {
         const float len = sqrtf(dot3(b1, b1));
-        F = F - (S.k_bond * (len - S.r0) / len) * b1;
+        F = F - __fdividef(S.k_bond * (len - S.r0), len) * b1;
     }
     if (p1) {
         const float len = sqrtf(dot3(b2, b2));
-        F = F + (S.k_bond * (len - S.r0) / len) * b2;
+        F = F + __fdividef(S.k_bond * (len - S.r0), len) * b2;
     }
     // angular term kappa phi^2 / 2 at beads p-1, p, p+1
     if (S.kappa != 0.0f) {
@@ -195,8 +240,8 @@ __device__ float3 fast_force(const Sim &S, const PSmem &sm, int buf, int p, int 
     for (int k = 0; k < nn; ++k) {
         const int q = sm.nbr[p * NBR_CAP + k];
         const float4 qh = ph[q], ql = pl[q];
-        const float3 d = make_float3(ff_diff(mh.x, ml.x, qh.x, ql.x, fnx), ff_diff(mh.y, ml.y, qh.y, ql.y, fny),
-                                     ff_diff(mh.z, ml.z, qh.z, ql.z, fnz));
+        const float3 d = make_float3(ff_diff(mh.x, ml.x, qh.x, ql.x, fnx, S.inx), ff_diff(mh.y, ml.y, qh.y, ql.y, fny, S.iny),
+                                     ff_diff(mh.z, ml.z, qh.z, ql.z, fnz, S.inz));
         const float r2 = dot3(d, d);
         if (r2 < S.lj_rc2) F = F + wca_coef(r2, S.lj_eps, S.lj_sig2) * d;
     }
@@ -205,8 +250,8 @@ __device__ float3 fast_force(const Sim &S, const PSmem &sm, int buf, int p, int 
     for (int k = 0; k < nw; ++k) {
         const uint32_t pk = sm.wal[p * WALL_CAP + k];
         const float X = (float)(pk & 0xfffu), Y = (float)((pk >> 12) & 0x3ffu), Z = (float)(pk >> 22);
-        const float3 d = make_float3(ff_diff(mh.x, ml.x, X, 0.f, fnx), ff_diff(mh.y, ml.y, Y, 0.f, fny),
-                                     ff_diff(mh.z, ml.z, Z, 0.f, fnz));
+        const float3 d = make_float3(ff_diff(mh.x, ml.x, X, 0.f, fnx, S.inx), ff_diff(mh.y, ml.y, Y, 0.f, fny, S.iny),
+                                     ff_diff(mh.z, ml.z, Z, 0.f, fnz, S.inz));
         const float r2 = dot3(d, d);
         if (r2 < S.wall_rc2) F = F + wca_coef(r2, S.wall_eps, S.wall_sig2) * d;
     }
@@ -239,12 +284,12 @@ __device__ void build_lists(const Sim &S, const PSmem &sm, int buf, int p, int N
     float xw = 0.f, yw = 0.f, zw = 0.f;
     int ci = 0, cj = 0, ck = 0;
     if (own) {
-        xw = ff_wrap(mh.x, ml.x, fnx);
-        yw = ff_wrap(mh.y, ml.y, fny);
-        zw = ff_wrap(mh.z, ml.z, fnz);
-        ci = min((int)(xw * (float)S.ncell[0] / fnx), S.ncell[0] - 1);
-        cj = min((int)(yw * (float)S.ncell[1] / fny), S.ncell[1] - 1);
-        ck = min((int)(zw * (float)S.ncell[2] / fnz), S.ncell[2] - 1);
+        xw = ff_wrap(mh.x, ml.x, fnx, S.inx);
+        yw = ff_wrap(mh.y, ml.y, fny, S.iny);
+        zw = ff_wrap(mh.z, ml.z, fnz, S.inz);
+        ci = min((int)(xw * S.cell_per_site[0]), S.ncell[0] - 1);
+        cj = min((int)(yw * S.cell_per_site[1]), S.ncell[1] - 1);
+        ck = min((int)(zw * S.cell_per_site[2]), S.ncell[2] - 1);
         if (hashed) {
             const int key = ci + S.ncell[0] * (cj + S.ncell[1] * ck);
             int slot = cell_slot(key);
@@ -264,8 +309,8 @@ __device__ void build_lists(const Sim &S, const PSmem &sm, int buf, int p, int N
     auto consider = [&](int q) {
         if (q == p || q == p - 1 || q == p + 1) return;
         const float4 qh = ph[q], ql = pl[q];
-        const float dx = ff_diff(mh.x, ml.x, qh.x, ql.x, fnx), dy = ff_diff(mh.y, ml.y, qh.y, ql.y, fny),
-                    dz = ff_diff(mh.z, ml.z, qh.z, ql.z, fnz);
+        const float dx = ff_diff(mh.x, ml.x, qh.x, ql.x, fnx, S.inx), dy = ff_diff(mh.y, ml.y, qh.y, ql.y, fny, S.iny),
+                    dz = ff_diff(mh.z, ml.z, qh.z, ql.z, fnz, S.inz);
         if (dx * dx + dy * dy + dz * dz < S.rl2) list_insert(lst, n, q);
     };
     if (hashed) {
@@ -291,21 +336,39 @@ __device__ void build_lists(const Sim &S, const PSmem &sm, int buf, int p, int N
     }
     if (n > NBR_CAP) { atomicOr(s_err, ST_CAPACITY); n = NBR_CAP; }
     sm.nn[p] = (uint8_t)n;
-    // solid sites within the wall-list radius
+    // solid sites within the wall-list radius; the link word of the bead's cell
+    // corner says whether any solid site lies within the scanned box at all
     int m = 0;
-    const int x0 = (int)floorf(xw - S.rlw), x1 = (int)floorf(xw + S.rlw);
-    const int y0 = (int)floorf(yw - S.rlw), y1 = (int)floorf(yw + S.rlw);
-    const int z0 = (int)floorf(zw - S.rlw), z1 = (int)floorf(zw + S.rlw);
-    for (int Z = z0; Z <= z1; ++Z)
-        for (int Y = y0; Y <= y1; ++Y)
-            for (int X = x0; X <= x1; ++X) {
-                const int xx = wrap_any(X, S.nx), yy = wrap_any(Y, S.ny), zz = wrap_any(Z, S.nz);
-                if (!S.solid[xx + S.nx * (yy + S.ny * zz)]) continue;
-                const float dx = xw - (float)X, dy = yw - (float)Y, dz = zw - (float)Z;
-                if (dx * dx + dy * dy + dz * dz >= S.rlw2) continue;
-                if (m < WALL_CAP) sm.wal[p * WALL_CAP + m] = (uint32_t)xx | ((uint32_t)yy << 12) | ((uint32_t)zz << 22);
-                ++m;
-            }
+    const int cx0 = (int)floorf(xw), cy0 = (int)floorf(yw), cz0 = (int)floorf(zw);
+    if (S.rlw < 2.0f) {
+        // every site within rlw < 2 of the bead lies in the 4x4x4 box starting
+        // one site below its cell corner; its solid sites are one bit mask
+        unsigned long long mm = __ldg(S.wallmask + cx0 + S.nx * (cy0 + S.ny * cz0));
+        while (mm) {
+            const int bit = __ffsll((long long)mm) - 1;
+            mm &= mm - 1;
+            const int X = cx0 + (bit & 3) - 1, Y = cy0 + ((bit >> 2) & 3) - 1, Z = cz0 + (bit >> 4) - 1;
+            const float dx = xw - (float)X, dy = yw - (float)Y, dz = zw - (float)Z;
+            if (dx * dx + dy * dy + dz * dz >= S.rlw2) continue;
+            const int xx = wrapi(X, S.nx), yy = wrapi(Y, S.ny), zz = wrapi(Z, S.nz);
+            if (m < WALL_CAP) sm.wal[p * WALL_CAP + m] = (uint32_t)xx | ((uint32_t)yy << 12) | ((uint32_t)zz << 22);
+            ++m;
+        }
+    } else if (__ldg(S.link + cx0 + S.nx * (cy0 + S.ny * cz0)) & NEAR_SOLID_BIT) {
+        const int x0 = (int)floorf(xw - S.rlw), x1 = (int)floorf(xw + S.rlw);
+        const int y0 = (int)floorf(yw - S.rlw), y1 = (int)floorf(yw + S.rlw);
+        const int z0 = (int)floorf(zw - S.rlw), z1 = (int)floorf(zw + S.rlw);
+        for (int Z = z0; Z <= z1; ++Z)
+            for (int Y = y0; Y <= y1; ++Y)
+                for (int X = x0; X <= x1; ++X) {
+                    const int xx = wrap_any(X, S.nx), yy = wrap_any(Y, S.ny), zz = wrap_any(Z, S.nz);
+                    if (!(__ldg(S.link + xx + S.nx * (yy + S.ny * zz)) & SOLID_BIT)) continue;
+                    const float dx = xw - (float)X, dy = yw - (float)Y, dz = zw - (float)Z;
+                    if (dx * dx + dy * dy + dz * dz >= S.rlw2) continue;
+                    if (m < WALL_CAP) sm.wal[p * WALL_CAP + m] = (uint32_t)xx | ((uint32_t)yy << 12) | ((uint32_t)zz << 22);
+                    ++m;
+                }
+    }
     if (m > WALL_CAP) { atomicOr(s_err, ST_CAPACITY); m = WALL_CAP; }
     sm.nw[p] = (uint8_t)m;
 }
@@ -344,9 +407,8 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (*red)[NV]) {
 // ---------------------------------------------------------------------------
 // the particle kernel: one block per realization, one thread per bead
 // ---------------------------------------------------------------------------
-template <int PREC>
-__global__ void __launch_bounds__(1024) k_particles(const Sim S, const void *__restrict__ Av) {
-    using T = typename PopT<PREC>::T;
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_particles(const Sim S) {
     extern __shared__ __align__(16) char smem_raw[];
     __shared__ int s_flag, s_err;
     __shared__ double red[32][9];
@@ -359,29 +421,22 @@ __global__ void __launch_bounds__(1024) k_particles(const Sim S, const void *__r
     const int p = threadIdx.x;
     const bool own = p < N;
     const long long step = S.ctrl->step;
-    const T *A = reinterpret_cast<const T *>(Av) + (size_t)r * Q * S.ns;
     const float fnx = (float)S.nx, fny = (float)S.ny, fnz = (float)S.nz;
     if (threadIdx.x == 0) { s_flag = 0; s_err = 0; }
 
+    unsigned long long tclk = clock64();
+    // 1. state and the fluid velocity the gather kernel froze for this step
     float4 mh = make_float4(0.f, 0.f, 0.f, 0.f), ml = mh;
-    float3 v = make_float3(0.f, 0.f, 0.f);
+    float3 v = make_float3(0.f, 0.f, 0.f), up = v;
     if (own) {
         mh = S.r_hi[off + p];
         ml = S.r_lo[off + p];
         const float4 vv = S.v[off + p];
         v = make_float3(vv.x, vv.y, vv.z);
+        const float4 uu = S.up[off + p];
+        up = make_float3(uu.x, uu.y, uu.z);
         sm.ph[0][p] = mh;
         sm.pl[0][p] = ml;
-    }
-    __syncthreads();
-
-    unsigned long long tclk = clock64();
-    // 1. fluid velocity at the beads (warp per bead)
-    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int q = warp; q < N; q += nwarps) {
-        const float4 qh = sm.ph[0][q], ql = sm.pl[0][q];
-        const float3 u = gather_warp(S, A, ff_wrap(qh.x, ql.x, fnx), ff_wrap(qh.y, ql.y, fny), ff_wrap(qh.z, ql.z, fnz));
-        if ((threadIdx.x & 31) == 0) sm.ups[q] = make_float4(u.x, u.y, u.z, 0.f);
     }
     __syncthreads();
     phase_mark(S, 0, tclk);
@@ -390,14 +445,11 @@ __global__ void __launch_bounds__(1024) k_particles(const Sim S, const void *__r
     __syncthreads();
     phase_mark(S, 1, tclk);
 
-    float3 up = make_float3(0.f, 0.f, 0.f);
-    if (own) { const float4 t = sm.ups[p]; up = make_float3(t.x, t.y, t.z); }
-
     // per-step bead diagnostics at the starting state
     {
         double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         if (own) {
-            const float xw = ff_wrap(mh.x, ml.x, fnx), yw = ff_wrap(mh.y, ml.y, fny), zw = ff_wrap(mh.z, ml.z, fnz);
+            const float xw = ff_wrap(mh.x, ml.x, fnx, S.inx), yw = ff_wrap(mh.y, ml.y, fny, S.iny), zw = ff_wrap(mh.z, ml.z, fnz, S.inz);
             const float Fe = in_channel(S, xw, yw, zw) ? S.E : 0.0f;
             const double X = (double)mh.x + (double)ml.x;
             acc[0] = v.x; acc[1] = v.y; acc[2] = v.z;
@@ -432,7 +484,7 @@ __global__ void __launch_bounds__(1024) k_particles(const Sim S, const void *__r
         float3 xi = make_float3(0.f, 0.f, 0.f);
         if (own && amp > 0.0f) xi = amp * gauss3(S.seed, (uint32_t)r, (uint32_t)p, step, (uint32_t)sub);
         if (own) {  // first half kick: field + friction + noise
-            const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx), ff_wrap(mh.y, ml.y, fny), ff_wrap(mh.z, ml.z, fnz));
+            const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx, S.inx), ff_wrap(mh.y, ml.y, fny, S.iny), ff_wrap(mh.z, ml.z, fnz, S.inz));
             const float3 fl = S.gamma * (up - v) + xi;
             v = v + h * (make_float3(ch ? S.E : 0.0f, 0.f, 0.f) + fl);
             J = J + h * fl;
@@ -461,7 +513,7 @@ __global__ void __launch_bounds__(1024) k_particles(const Sim S, const void *__r
             }
         }
         if (own) {  // second half kick with the same noise
-            const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx), ff_wrap(mh.y, ml.y, fny), ff_wrap(mh.z, ml.z, fnz));
+            const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx, S.inx), ff_wrap(mh.y, ml.y, fny, S.iny), ff_wrap(mh.z, ml.z, fnz, S.inz));
             const float3 fl = S.gamma * (up - v) + xi;
             v = v + h * (make_float3(ch ? S.E : 0.0f, 0.f, 0.f) + fl);
             J = J + h * fl;
@@ -471,25 +523,19 @@ __global__ void __launch_bounds__(1024) k_particles(const Sim S, const void *__r
     __syncthreads();
     phase_mark(S, 2, tclk);
 
-    // 3. spread -W J onto the fluid corners of the starting position (warp per bead)
+    // 3. spread -W J onto the fluid corners of the starting position, with the
+    //    (site, weight) pairs the gather kernel recorded: one thread per pair
     {
-        const int lane = threadIdx.x & 31, c = lane >> 2, sub = lane & 3;
         const size_t ns = (size_t)S.ns;
-        for (int q = warp; q < N; q += nwarps) {
-            const float4 qh = S.r_hi[off + q], ql = S.r_lo[off + q];
-            int xi, yi, zi, node;
-            float w;
-            corner_of(S, ff_wrap(qh.x, ql.x, fnx), ff_wrap(qh.y, ql.y, fny), ff_wrap(qh.z, ql.z, fnz), c, xi, yi, zi,
-                      node, w);
-            const float wsum = corner_sum(w);
-            const float W = wsum > 0.0f ? w / wsum : 0.0f;
-            const float4 Jq = sm.ups[q];
-            if (sub < 3 && W > 0.0f) {
-                const float comp = sub == 0 ? Jq.x : (sub == 1 ? Jq.y : Jq.z);
-                const long long fx = __float2ll_rn(-W * comp * FIX_SCALE_F);
-                atomicAdd(S.G + ((size_t)r * 3 + sub) * ns + node, (unsigned long long)fx);
-            }
-            if (sub == 0) S.pair_node[(size_t)(off + q) * 8 + c] = W > 0.0f ? (int)((size_t)r * ns + node) : -1;
+        for (int k = threadIdx.x; k < 8 * N; k += blockDim.x) {
+            const int gnode = S.pair_node[(size_t)off * 8 + k];
+            if (gnode < 0) continue;
+            const float W = S.pair_w[(size_t)off * 8 + k];
+            const float4 Jq = sm.ups[k >> 3];
+            const size_t base = (size_t)r * 2 * ns + (size_t)gnode;  // = (r*3 + 0)*ns + site
+            atomicAdd(S.G + base, (unsigned long long)__float2ll_rn(-W * Jq.x * FIX_SCALE_F));
+            atomicAdd(S.G + base + ns, (unsigned long long)__float2ll_rn(-W * Jq.y * FIX_SCALE_F));
+            atomicAdd(S.G + base + 2 * ns, (unsigned long long)__float2ll_rn(-W * Jq.z * FIX_SCALE_F));
         }
     }
     __syncthreads();
@@ -510,20 +556,22 @@ __global__ void __launch_bounds__(1024) k_particles(const Sim S, const void *__r
     if (threadIdx.x == 0 && s_err) atomicOr(&S.ctrl->status, s_err);
 }
 
-cudaError_t launch_particles(const Sim &S, const void *A, cudaStream_t st) {
+template <int MAXT>
+static cudaError_t launch_particles_t(const Sim &S, int threads, size_t smem, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_particles<MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_particles<MAXT><<<S.n_real, threads, smem, st>>>(S);
+    return cudaGetLastError();
+}
+
+// the launch bound follows the largest chain so that short chains get more
+// registers per thread
+cudaError_t launch_particles(const Sim &S, const void *, cudaStream_t st) {
     const int threads = particle_threads(S);
     const size_t smem = particle_smem_bytes(threads);
-    cudaError_t e;
-    if (S.precision == LBMD_FP16DEV) {
-        e = cudaFuncSetAttribute(k_particles<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_particles<1><<<S.n_real, threads, smem, st>>>(S, A);
-    } else {
-        e = cudaFuncSetAttribute(k_particles<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_particles<0><<<S.n_real, threads, smem, st>>>(S, A);
-    }
-    return cudaGetLastError();
+    if (threads <= 256) return launch_particles_t<256>(S, threads, smem, st);
+    if (threads <= 512) return launch_particles_t<512>(S, threads, smem, st);
+    return launch_particles_t<1024>(S, threads, smem, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -555,7 +603,10 @@ __global__ void __launch_bounds__(1024) k_bead_observables(const Sim S, const vo
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int q = warp; q < N; q += nwarps) {
         const float4 qh = sm.ph[0][q], ql = sm.pl[0][q];
-        const float3 u = gather_warp(S, A, ff_wrap(qh.x, ql.x, fnx), ff_wrap(qh.y, ql.y, fny), ff_wrap(qh.z, ql.z, fnz));
+        int node;
+        float W;
+        const float3 u = gather_warp(S, A, ff_wrap(qh.x, ql.x, fnx, S.inx), ff_wrap(qh.y, ql.y, fny, S.iny), ff_wrap(qh.z, ql.z, fnz, S.inz),
+                                     node, W);
         if ((threadIdx.x & 31) == 0) sm.ups[q] = make_float4(u.x, u.y, u.z, 0.f);
     }
     __syncthreads();
@@ -564,7 +615,7 @@ __global__ void __launch_bounds__(1024) k_bead_observables(const Sim S, const vo
     double a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (own) {
         const float4 u = sm.ups[p];
-        const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx), ff_wrap(mh.y, ml.y, fny), ff_wrap(mh.z, ml.z, fnz));
+        const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx, S.inx), ff_wrap(mh.y, ml.y, fny, S.iny), ff_wrap(mh.z, ml.z, fnz, S.inz));
         a[0] = vv.x; a[1] = vv.y; a[2] = vv.z;
         a[3] = X; a[4] = Y; a[5] = Z;
         a[6] = tr ? 1.0 : 0.0;

@@ -16,13 +16,13 @@ using namespace lbmd;
 
 namespace {
 
-constexpr int K_PARTICLES = 0, K_STREAM_COLLIDE = 1, K_SOURCE = 2, K_COUNT = 3;
-const char *KNAMES[K_COUNT] = {"particles", "stream_collide", "source"};
-constexpr double SKIN = 0.5;  // Verlet-list skin (lattice units)
+constexpr int K_GATHER = 0, K_PARTICLES = 1, K_STREAM_COLLIDE = 2, K_SOURCE = 3, K_COUNT = 4;
+const char *KNAMES[K_COUNT] = {"gather", "particles", "stream_collide", "source"};
+constexpr double SKIN = 0.8;  // Verlet-list skin (lattice units)
 
 struct Layout {
-    size_t popA, popB, staging, link, tileflag, solid, G, stamp;
-    size_t r_hi, r_lo, v, up, J, pair_node, bead_off, partial, ring, obs, ctrl, phase, total;
+    size_t popA, popB, staging, link, wallmask, tileflag, solid, G, stamp;
+    size_t r_hi, r_lo, v, up, J, pair_node, pair_w, bead_real, bead_off, partial, ring, obs, ctrl, phase, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -54,8 +54,8 @@ struct lbmd_handle {
     bool profiling = false;
     std::vector<ProfRec> pending;
     std::vector<cudaEvent_t> free_events;
-    double prof_ms[K_COUNT] = {0, 0, 0};
-    long long prof_n[K_COUNT] = {0, 0, 0};
+    double prof_ms[K_COUNT] = {0, 0, 0, 0};
+    long long prof_n[K_COUNT] = {0, 0, 0, 0};
     long long launches = 0;
     long long host_step = 0;
     std::string err;
@@ -95,6 +95,10 @@ bool config_ok(const lbmd_config *c, const int32_t *off, std::string &why) {
     if (c->gamma < 0 || c->kT < 0 || c->k_bond < 0) { why = "gamma, kT, k_bond must be >= 0"; return false; }
     if (!off) { why = "null bead_offsets"; return false; }
     if (off[0] != 0) { why = "bead_offsets[0] must be 0"; return false; }
+    if (off[c->n_real] > 0 && (c->nx < 4 || c->ny < 4 || c->nz < 4)) {
+        why = "a lattice holding beads needs at least 4 sites per axis";
+        return false;
+    }
     for (int r = 0; r < c->n_real; ++r) {
         const int n = off[r + 1] - off[r];
         if (n < 0) { why = "bead_offsets must be non-decreasing"; return false; }
@@ -117,6 +121,7 @@ Layout layout_of(const lbmd_config *c, int total_beads) {
     L.popB = take(npop * esz);
     L.staging = take(npop * 4);
     L.link = take(ns * 4);
+    L.wallmask = take(ns * 8);
     L.tileflag = take(nxt * c->ny * c->nz);
     L.solid = take(ns);
     L.G = take((size_t)c->n_real * 3 * ns * 8);
@@ -127,6 +132,8 @@ Layout layout_of(const lbmd_config *c, int total_beads) {
     L.up = take(nb * 16);
     L.J = take(nb * 16);
     L.pair_node = take(nb * 8 * 4);
+    L.pair_w = take(nb * 8 * 4);
+    L.bead_real = take(nb * 4);
     L.bead_off = take((size_t)(c->n_real + 1) * 4);
     L.partial = take(max_blocks * 4 * sizeof(double));
     L.ring = take((size_t)c->n_real * LBMD_DIAG_RING * sizeof(lbmd_diag));
@@ -188,6 +195,10 @@ struct ProfScope {
 lbmd_status enqueue_step(lbmd_handle *h) {
     CK(cudaEventRecord(h->ev_fork, h->st));
     CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+    if (h->total_beads > 0) {
+        ProfScope ps(h, K_GATHER, h->aux);
+        CK(launch_gather(h->S, h->popA, h->aux));
+    }
     {
         ProfScope ps(h, K_PARTICLES, h->aux);
         CK(launch_particles(h->S, h->popA, h->aux));
@@ -204,7 +215,7 @@ lbmd_status enqueue_step(lbmd_handle *h) {
     }
     std::swap(h->popA, h->popB);
     h->host_step += 1;
-    h->launches += 3;
+    h->launches += h->total_beads > 0 ? 4 : 3;
     if (h->pending.size() > 30000) return resolve_profile(h);
     return LBMD_OK;
 }
@@ -240,8 +251,9 @@ lbmd_status capture_graph(lbmd_handle *h) {
     return LBMD_OK;
 }
 
-void build_geometry(const lbmd_config *c, const uint8_t *solid, std::vector<uint32_t> &link,
-                    std::vector<uint8_t> &tile, std::vector<uint8_t> &sol, double &n_fluid) {
+void build_geometry(const lbmd_config *c, const uint8_t *solid, int near_radius, std::vector<uint32_t> &link,
+                    std::vector<unsigned long long> &wallmask, std::vector<uint8_t> &tile,
+                    std::vector<uint8_t> &sol, double &n_fluid) {
     const int nx = c->nx, ny = c->ny, nz = c->nz;
     const size_t ns = (size_t)nx * ny * nz;
     sol.assign(solid, solid + ns);
@@ -264,12 +276,53 @@ void build_geometry(const lbmd_config *c, const uint8_t *solid, std::vector<uint
                 }
                 link[s] = m;
             }
+    // near-solid bit: the solid mask dilated by near_radius in the Chebyshev
+    // metric, as three separable 1-D maximum filters
+    std::vector<uint8_t> a(sol), t(ns);
+    const int dims[3] = {nx, ny, nz};
+    const size_t stride[3] = {1, (size_t)nx, (size_t)nx * ny};
+    for (int ax = 0; ax < 3; ++ax) {
+        const int n = dims[ax];
+        for (size_t s = 0; s < ns; ++s) {
+            const int coord = (int)((s / stride[ax]) % n);
+            uint8_t v = 0;
+            for (int d = -near_radius; d <= near_radius && !v; ++d) {
+                const int q = ((coord + d) % n + n) % n;
+                v = a[s + (size_t)(q - coord) * stride[ax]];
+            }
+            t[s] = v;
+        }
+        a.swap(t);
+    }
+    for (size_t s = 0; s < ns; ++s)
+        if (a[s]) link[s] |= NEAR_SOLID_BIT;
+    // solid sites of the 4x4x4 box [x-1, x+2] x [y-1, y+2] x [z-1, z+2]
+    wallmask.assign(ns, 0ull);
+    std::vector<int> wx(4 * (size_t)nx), wy(4 * (size_t)ny), wz(4 * (size_t)nz);
+    for (int d = 0; d < 4; ++d) {
+        for (int i = 0; i < nx; ++i) wx[d * (size_t)nx + i] = ((i + d - 1) % nx + nx) % nx;
+        for (int i = 0; i < ny; ++i) wy[d * (size_t)ny + i] = ((i + d - 1) % ny + ny) % ny;
+        for (int i = 0; i < nz; ++i) wz[d * (size_t)nz + i] = ((i + d - 1) % nz + nz) % nz;
+    }
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                unsigned long long m = 0;
+                for (int dz = 0; dz < 4; ++dz)
+                    for (int dy = 0; dy < 4; ++dy) {
+                        const size_t row = (size_t)nx * (wy[dy * (size_t)ny + y] + (size_t)ny * wz[dz * (size_t)nz + z]);
+                        for (int dx = 0; dx < 4; ++dx)
+                            if (sol[row + wx[dx * (size_t)nx + x]]) m |= 1ull << (dx + 4 * dy + 16 * dz);
+                    }
+                wallmask[x + (size_t)nx * (y + (size_t)ny * z)] = m;
+            }
     const int nxt = (nx + 31) / 32;
     tile.assign((size_t)nxt * ny * nz, 0);
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x)
-                if (link[x + (size_t)nx * (y + (size_t)ny * z)]) tile[x / 32 + (size_t)nxt * (y + (size_t)ny * z)] = 1;
+                if (link[x + (size_t)nx * (y + (size_t)ny * z)] & ~NEAR_SOLID_BIT)
+                    tile[x / 32 + (size_t)nxt * (y + (size_t)ny * z)] = 1;
 }
 
 }  // namespace
@@ -334,15 +387,21 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
 
     // geometry on the host
     std::vector<uint32_t> link;
+    std::vector<unsigned long long> wallmask;
     std::vector<uint8_t> tile, sol;
     double n_fluid = 0;
-    build_geometry(cfg, solid, link, tile, sol, n_fluid);
+    // a bead's wall-list box reaches floor(rlw) + 1 sites from its cell corner
+    const int near_radius = (int)std::floor(std::pow(2.0, 1.0 / 6.0) * cfg->wall_sigma + 0.5 * SKIN) + 1;
+    build_geometry(cfg, solid, near_radius, link, wallmask, tile, sol, n_fluid);
 
     Sim &S = h->S;
     memset(&S, 0, sizeof(S));
     S.nx = cfg->nx; S.ny = cfg->ny; S.nz = cfg->nz;
     S.ns = cfg->nx * cfg->ny * cfg->nz;
     S.nxt = (cfg->nx + 31) / 32;
+    S.inx = 1.0f / (float)cfg->nx;
+    S.iny = 1.0f / (float)cfg->ny;
+    S.inz = 1.0f / (float)cfg->nz;
     S.n_real = cfg->n_real;
     S.precision = cfg->precision;
     S.omega = (float)(1.0 / cfg->tau);
@@ -372,12 +431,18 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
     S.M = cfg->md_outer;
     S.Mb = cfg->md_inner;
     S.skin_half2 = (float)(0.25 * SKIN * SKIN);
-    const double rl = c16 * cfg->lj_sigma + SKIN, rlw = c16 * cfg->wall_sigma + SKIN;
+    // bead pairs: both beads may move skin/2; solid sites do not move, so the
+    // wall list needs only the cut-off plus the bead's own skin/2
+    const double rl = c16 * cfg->lj_sigma + SKIN, rlw = c16 * cfg->wall_sigma + 0.5 * SKIN;
     S.rl2 = (float)(rl * rl);
     S.rlw = (float)rlw;
     S.rlw2 = (float)(rlw * rlw);
     const int dims[3] = {cfg->nx, cfg->ny, cfg->nz};
-    for (int a = 0; a < 3; ++a) S.ncell[a] = std::max(1, (int)std::floor(dims[a] / rl));
+    for (int a = 0; a < 3; ++a) {
+        S.ncell[a] = std::max(1, (int)std::floor(dims[a] / rl));
+        S.cell_per_site[a] = (float)S.ncell[a] / (float)dims[a];
+    }
+    S.wallmask = (const unsigned long long *)(b + L.wallmask);
     S.seed = cfg->seed;
     S.link = (const uint32_t *)(b + L.link);
     S.tileflag = (const uint8_t *)(b + L.tileflag);
@@ -390,6 +455,8 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
     S.up = (float4 *)(b + L.up);
     S.J = (float4 *)(b + L.J);
     S.pair_node = (int *)(b + L.pair_node);
+    S.pair_w = (float *)(b + L.pair_w);
+    S.bead_real = (const int *)(b + L.bead_real);
     S.bead_off = (const int *)(b + L.bead_off);
     S.partial = (double *)(b + L.partial);
     S.ring = (lbmd_diag *)(b + L.ring);
@@ -403,9 +470,15 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
         if (e__ != cudaSuccess) { cuda_fail(h, e__, #call); return bail(LBMD_ERR_CUDA); } \
     } while (0)
     CKI(cudaMemcpyAsync(b + L.link, link.data(), link.size() * 4, cudaMemcpyHostToDevice, h->st));
+    CKI(cudaMemcpyAsync(b + L.wallmask, wallmask.data(), wallmask.size() * 8, cudaMemcpyHostToDevice, h->st));
     CKI(cudaMemcpyAsync(b + L.tileflag, tile.data(), tile.size(), cudaMemcpyHostToDevice, h->st));
     CKI(cudaMemcpyAsync(b + L.solid, sol.data(), sol.size(), cudaMemcpyHostToDevice, h->st));
     CKI(cudaMemcpyAsync(b + L.bead_off, h->offsets.data(), h->offsets.size() * 4, cudaMemcpyHostToDevice, h->st));
+    std::vector<int32_t> breal((size_t)std::max(h->total_beads, 1), 0);
+    for (int r = 0; r < cfg->n_real; ++r)
+        for (int i = bead_offsets[r]; i < bead_offsets[r + 1]; ++i) breal[i] = r;
+    CKI(cudaMemcpyAsync(b + L.bead_real, breal.data(), breal.size() * 4, cudaMemcpyHostToDevice, h->st));
+    CKI(cudaStreamSynchronize(h->st));
     CKI(cudaMemsetAsync(b + L.G, 0, (size_t)cfg->n_real * 3 * S.ns * 8, h->st));
     CKI(cudaMemsetAsync(b + L.stamp, 0, (size_t)cfg->n_real * S.ns * 4, h->st));
     CKI(cudaMemsetAsync(b + L.ring, 0, (size_t)cfg->n_real * LBMD_DIAG_RING * sizeof(lbmd_diag), h->st));
@@ -436,7 +509,7 @@ lbmd_status lbmd_step(lbmd_handle *h, int64_t n) {
             if (h->popA == h->graph_A) {
                 CK(cudaGraphLaunch(h->gexec, h->st));
                 h->host_step += h->graph_steps;
-                h->launches += 3LL * h->graph_steps;
+                h->launches += (h->total_beads > 0 ? 4LL : 3LL) * h->graph_steps;
                 n -= h->graph_steps;
                 continue;
             }

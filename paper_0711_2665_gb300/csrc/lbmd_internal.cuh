@@ -51,6 +51,10 @@ __host__ __device__ constexpr float wq(int i) {
 }
 
 constexpr uint32_t SOLID_BIT = 0x80000000u;
+// set on a site when a solid site lies within Chebyshev distance
+// near_solid_radius (computed on the host from the wall-list radius): a bead
+// whose cell corner lacks it has no solid site in its wall-list box
+constexpr uint32_t NEAR_SOLID_BIT = 0x40000000u;
 constexpr float FP16_SCALE = 4096.0f;          // 2^12
 constexpr float FP16_INV_SCALE = 1.0f / 4096.0f;
 constexpr double FIX_SCALE = 1099511627776.0;  // 2^40
@@ -58,7 +62,7 @@ constexpr float FIX_SCALE_F = 1099511627776.0f;
 constexpr float FIX_INV_SCALE_F = 1.0f / 1099511627776.0f;
 
 constexpr int NBR_CAP = 32;     // bead-bead neighbours per bead
-constexpr int WALL_CAP = 8;     // solid sites within the wall-list radius per bead
+constexpr int WALL_CAP = 12;    // solid sites within the wall-list radius per bead
 constexpr int HASH_SIZE = 2048; // cell hash slots (>= 2 * max beads per realization)
 
 // status bits latched in Ctrl::status
@@ -79,6 +83,7 @@ struct Ctrl {
 struct Sim {
     // lattice
     int nx, ny, nz, ns, nxt, n_real;
+    float inx, iny, inz;     // 1/nx, 1/ny, 1/nz
     int precision;
     float omega;
     float g[3];
@@ -94,15 +99,19 @@ struct Sim {
     float skin_half2;        // (skin/2)^2: displacement that forces a list rebuild
     float rl2, rlw2, rlw;    // bead and wall list radii (squared) and wall radius
     int ncell[3];            // cells per axis for the neighbour hash (>= 3 to use it)
+    float cell_per_site[3];  // ncell / n per axis
     unsigned long long seed;
     // buffers
     const uint32_t *link;
+    const unsigned long long *wallmask;  // [ns] solid sites of the 4x4x4 box from (x-1, y-1, z-1)
     const uint8_t *tileflag;
     const uint8_t *solid;
     unsigned long long *G;
     int *stamp;
     float4 *r_hi, *r_lo, *v, *up, *J;
-    int *pair_node;
+    int *pair_node;          // [total_beads][8] global site of each fluid corner, -1 if none
+    float *pair_w;           // [total_beads][8] normalised trilinear weight
+    const int *bead_real;    // [total_beads] realization of each bead
     const int *bead_off;
     double *partial;         // [blocks][4]
     lbmd_diag *ring;         // [n_real][LBMD_DIAG_RING]
@@ -199,14 +208,16 @@ __device__ __forceinline__ void ff_norm(float &hi, float &lo) {
     hi = s;
     lo = e;
 }
-// minimum-image difference of two float-float coordinates on an axis of length n
-__device__ __forceinline__ float ff_diff(float ahi, float alo, float bhi, float blo, float n) {
+// minimum-image difference of two float-float coordinates on an axis of length
+// n (inv = 1/n; a rounding of d * inv can only matter at separations of n/2,
+// far beyond every cut-off)
+__device__ __forceinline__ float ff_diff(float ahi, float alo, float bhi, float blo, float n, float inv) {
     float d = (ahi - bhi) + (alo - blo);
-    return d - n * rintf(d / n);
+    return d - n * rintf(d * inv);
 }
 // wrapped coordinate in [0, n)
-__device__ __forceinline__ float ff_wrap(float hi, float lo, float n) {
-    float x = hi - n * floorf(hi / n);
+__device__ __forceinline__ float ff_wrap(float hi, float lo, float n, float inv) {
+    float x = hi - n * floorf(hi * inv);
     if (x < 0.0f) x += n;
     if (x >= n) x -= n;
     x += lo;
@@ -228,7 +239,7 @@ __device__ __forceinline__ int wrap_any(int i, int n) { const int m = i % n; ret
 __device__ __forceinline__ bool in_channel(const Sim &S, float xw, float yw, float zw) {
     if (S.wall_x < 0) return false;
     float dx = xw - (float)S.wall_x;
-    dx -= (float)S.nx * rintf(dx / (float)S.nx);
+    dx -= (float)S.nx * rintf(dx * S.inx);
     if (fabsf(dx) > 1.5f) return false;
     if (yw < (float)S.pore_ylo - 0.5f || yw > (float)(S.pore_ylo + S.pore_h) - 0.5f) return false;
     if (zw < (float)S.pore_zlo - 0.5f || zw > (float)(S.pore_zlo + S.pore_h) - 0.5f) return false;
@@ -249,6 +260,7 @@ cudaError_t launch_pull_to_staging(const Sim &S, const void *A, float *staging, 
 cudaError_t launch_push_from_staging(const Sim &S, const float *staging, void *A, bool dev, cudaStream_t st);
 size_t particle_smem_bytes(int threads);
 int particle_threads(const Sim &S);
+cudaError_t launch_gather(const Sim &S, const void *A, cudaStream_t st);
 cudaError_t launch_particles(const Sim &S, const void *A, cudaStream_t st);
 cudaError_t launch_bead_observables(const Sim &S, const void *A, cudaStream_t st);
 
