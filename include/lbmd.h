@@ -205,6 +205,32 @@ lbmd_status lbmd_kernel_times(lbmd_handle *h, lbmd_kernel_time *out, int32_t max
                               int32_t *n_entries);
 lbmd_status lbmd_launch_count(lbmd_handle *h, int64_t *launches);
 
+/* Allocation-free fluid sums.  The paper has no counterpart: this is a
+ * utility for callers that cannot allocate device memory where they call it,
+ * such as a monitoring loop beside a running simulation on a GPU whose memory
+ * another framework's pool already holds, or time-critical code that cannot
+ * afford the device-wide synchronisation of cudaMalloc.
+ *
+ * Computes, for one lattice of FP32 population deviations dev = f_i - w_i
+ * (device array [19][nz][ny][nx], the per-realization layout and storage
+ * format of lbmd_get_deviations), out[0] = sum of rho over fluid sites and
+ * out[1..3] = sum of rho u over fluid sites (device array of 4 doubles,
+ * written when the kernel finishes).
+ * solid: device [nz][ny][nx] bytes (1 = solid, skipped) or NULL (all fluid).
+ * Asynchronous on `stream` (cudaStream_t as void*).
+ *
+ * It allocates nothing: its per-block partial sums live in one file-scope
+ * device array of about 160 KB that every GPU loading the library holds
+ * until the process exits.  Lattices above LBMD_STATIC_SUMS_MAX_SITES sites
+ * return LBMD_ERR_CAPACITY.  The first call on each device looks up that
+ * array's device address (with the device current), so make the first call
+ * before any stream capture.  Every call shares the array, and it keeps the
+ * last call's contents: calls whose kernels overlap on the GPU race and give
+ * wrong sums; order them on one stream. */
+#define LBMD_STATIC_SUMS_MAX_SITES 8388608
+lbmd_status lbmd_population_sums_static(const float *dev, const uint8_t *solid, int32_t nx, int32_t ny,
+                                        int32_t nz, double *out, void *stream);
+
 const char *lbmd_status_string(lbmd_status s);
 const char *lbmd_last_error(const lbmd_handle *h);
 

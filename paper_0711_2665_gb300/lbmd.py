@@ -108,6 +108,7 @@ def lib():
         "lbmd_profile": [vp, i32],
         "lbmd_kernel_times": [vp, P(KernelTime), i32, P(i32)],
         "lbmd_launch_count": [vp, P(i64)],
+        "lbmd_population_sums_static": [vp, vp, i32, i32, i32, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
