@@ -191,6 +191,24 @@ lbmd_status lbmd_set_graph(lbmd_handle *h, int32_t steps_per_graph);
 lbmd_status lbmd_set_tiles(lbmd_handle *h, int32_t by, int32_t zc);
 lbmd_status lbmd_get_tiles(lbmd_handle *h, int32_t *by, int32_t *zc);
 
+/* Shape of the particle kernel: threads_per_bead in {1,2,4,8} split each
+ * bead's force terms; blocks_per_chain in 1..8 is the thread-block cluster
+ * that shares one chain (positions replicated through distributed shared
+ * memory).  0 = automatic.  A block may hold at most 512 threads
+ * (ceil(beads / blocks_per_chain) * threads_per_bead); LBMD_ERR_INVALID_ARG
+ * otherwise.  Results agree with every shape to rounding (the force terms are
+ * summed in a different order). */
+lbmd_status lbmd_set_md_shape(lbmd_handle *h, int32_t threads_per_bead, int32_t blocks_per_chain);
+lbmd_status lbmd_get_md_shape(lbmd_handle *h, int32_t *threads_per_bead, int32_t *blocks_per_chain);
+
+/* overlap = 1 (default): the particle kernel runs concurrently with the
+ * stream-collide kernel of the same step (both only read the populations the
+ * step starts from); 0: one after the other.  Concurrency shares SMs between
+ * a latency-bound and a bandwidth-bound kernel, which can slow both; results
+ * are bit-identical either way. */
+lbmd_status lbmd_set_overlap(lbmd_handle *h, int32_t overlap);
+lbmd_status lbmd_get_overlap(lbmd_handle *h, int32_t *overlap);
+
 /* Time every candidate tile shape on the current state (restored afterwards)
  * and keep the fastest.  Synchronises the stream. */
 lbmd_status lbmd_autotune(lbmd_handle *h, int32_t steps_per_candidate, int32_t *by, int32_t *zc);
@@ -198,7 +216,8 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t steps_per_candidate, int32_t *
 /* Per-kernel timing with CUDA events on the launching streams (eager launches
  * only while enabled) and the count of kernels this handle launched.  While
  * enabled, the particle kernel of realization 0 also records the SM-clock
- * cycles of its phases (gather, lists, md, spread), reported as extra entries
+ * cycles of its phases (load, lists, md, spread, and the list rebuilds inside
+ * md, whose entry counts rebuilds as launches), reported as extra entries
  * "particles.<phase>" converted to ms at the device's nominal SM clock. */
 lbmd_status lbmd_profile(lbmd_handle *h, int32_t enable);
 lbmd_status lbmd_kernel_times(lbmd_handle *h, lbmd_kernel_time *out, int32_t max_entries,

@@ -3,59 +3,33 @@
 //      fluid velocity at every bead from the populations the step starts from
 //      (trilinear over fluid corners), frozen for the MD cycle (Sec. II, text
 //      after Eq. 21), plus the corner sites and weights the spread reuses;
-//   particle kernel, one thread block per realization, one thread per bead:
-//   2. MD cycle (Sec. II, Eq. 22 as multiple-time-step velocity Verlet):
-//      M outer steps whose half kicks apply the pore field, the friction
-//      gamma (u_p - v) and Philox noise (Eqs. 12, 13, 15), around M^b inner
-//      velocity-Verlet steps of the conservative forces (harmonic bonds Eq. 19,
-//      angular term, WCA between beads Eq. 14 and with solid sites), the
-//      momentum handed over by the fluid accumulated in J;
-//   3. spread: G(x) -= W(x - r_p) J_p with the weights of step 1, as 2^40
-//      fixed-point integer atomics (order-independent, so runs repeat bit for
-//      bit), and the (bead, corner) list the source pass walks.
-// Bead-bead pairs come from a Verlet list (cut-off + skin) built from a cell
-// hash in shared memory; it is rebuilt whenever a bead has moved more than
-// half the skin since the last build, so the pair set equals all pairs inside
-// the cut-off at every force evaluation.
+//   2. particle kernel: the MD cycle (Sec. II, Eq. 22 as multiple-time-step
+//      velocity Verlet): M outer steps whose half kicks apply the pore field,
+//      the friction gamma (u_p - v) and Philox noise (Eqs. 12, 13, 15), around
+//      M^b velocity-Verlet sub-steps of the conservative forces (harmonic bonds
+//      Eq. 19, angular term, WCA between beads Eq. 14 and with solid sites),
+//      accumulating the momentum J the fluid handed over; then the spread
+//      G(x) -= W(x - r_p) J_p with the gather's weights, as 2^40 fixed-point
+//      integer atomics (order-independent, so runs repeat bit for bit).
+//
+// Layout of the particle kernel.  Each realization is one thread-block
+// cluster of C blocks (C = 1 for short chains).  Block c owns Nc consecutive
+// beads, and each bead is worked on by T consecutive threads that split its
+// force terms (bonds, the three angles that involve it, its bead and wall
+// pair lists) and add them with a butterfly of shuffles.  Every block keeps a
+// replica of the whole chain's positions in shared memory; a bead's new
+// position is written to all C replicas through distributed shared memory
+// before the cluster barrier of each sub-step.  Bead-bead pairs come from a
+// Verlet list (cut-off + skin) built from a cell hash in shared memory, rebuilt
+// whenever any bead has moved more than half the skin since the last build,
+// so the pair set equals all pairs inside the cut-off at every evaluation.
+#include <cooperative_groups.h>
+
 #include "lbmd_internal.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace lbmd {
-
-struct PSmem {
-    float4 *ph[2], *pl[2];  // positions hi / lo, double buffered
-    float4 *ups;            // gathered fluid velocity, later the impulse J
-    uint16_t *nbr;          // [ncap][NBR_CAP]
-    uint32_t *wal;          // [ncap][WALL_CAP] packed solid-site coordinates
-    int *hkey, *hhead;      // [HASH_SIZE]
-    int16_t *hnext;         // [ncap]
-    uint8_t *nn, *nw;       // [ncap]
-};
-
-__host__ __device__ inline size_t psmem_layout(int ncap, PSmem *p, char *base) {
-    size_t o = 0;
-    auto take = [&](size_t bytes) { size_t at = o; o += (bytes + 15) & ~(size_t)15; return base + at; };
-    char *ph0 = take(16 * (size_t)ncap), *ph1 = take(16 * (size_t)ncap);
-    char *pl0 = take(16 * (size_t)ncap), *pl1 = take(16 * (size_t)ncap);
-    char *ups = take(16 * (size_t)ncap);
-    char *nbr = take(2 * (size_t)NBR_CAP * ncap);
-    char *wal = take(4 * (size_t)WALL_CAP * ncap);
-    char *hkey = take(4 * (size_t)HASH_SIZE), *hhead = take(4 * (size_t)HASH_SIZE);
-    char *hnext = take(2 * (size_t)ncap);
-    char *nn = take((size_t)ncap), *nw = take((size_t)ncap);
-    if (p) {
-        p->ph[0] = (float4 *)ph0; p->ph[1] = (float4 *)ph1;
-        p->pl[0] = (float4 *)pl0; p->pl[1] = (float4 *)pl1;
-        p->ups = (float4 *)ups;
-        p->nbr = (uint16_t *)nbr; p->wal = (uint32_t *)wal;
-        p->hkey = (int *)hkey; p->hhead = (int *)hhead; p->hnext = (int16_t *)hnext;
-        p->nn = (uint8_t *)nn; p->nw = (uint8_t *)nw;
-    }
-    return o;
-}
-
-size_t particle_smem_bytes(int threads) { return psmem_layout(threads, nullptr, nullptr); }
-
-int particle_threads(const Sim &S) { return max(32, ((S.max_beads + 31) / 32) * 32); }
 
 __device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
 __device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
@@ -89,7 +63,7 @@ __device__ __forceinline__ void corner_of(const Sim &S, float xw, float yw, floa
 // Sum over the 8 corners: lane l holds corner l >> 2, and the xor tree over
 // 4, 8, 16 visits the 8 lanes l ^ m that share l's sub-lane, one per corner,
 // so every lane gets the full sum as long as all 4 sub-lanes of a corner hold
-// the same value.  Same tree in gather and spread.
+// the same value.
 __device__ __forceinline__ float corner_sum(float v) {
     v += __shfl_xor_sync(0xffffffffu, v, 4);
     v += __shfl_xor_sync(0xffffffffu, v, 8);
@@ -183,77 +157,191 @@ cudaError_t launch_gather(const Sim &S, const void *A, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// conservative (fast) forces on bead p
+// conservative (fast) force terms
 // ---------------------------------------------------------------------------
+// atan2(y, x) for y >= 0, branch-free: reduce to t = min/max in [0, 1], then
+// atan(t) = t P(t^2) with P the degree-8 fit of atan(t)/t made by
+// csrc/fit_atan.py (relative error < 1.1e-7 in fp32), then reflect.
+__device__ __forceinline__ float atan_pos(float y, float x) {
+    const float ax = fabsf(x);
+    const float mx = fmaxf(y, ax), mn = fminf(y, ax);
+    const float t = mx > 0.0f ? __fdividef(mn, mx) : 0.0f;
+    const float s = t * t;
+    float p = 2.903541317e-03f;
+    p = fmaf(p, s, -1.628293283e-02f);
+    p = fmaf(p, s, 4.303918779e-02f);
+    p = fmaf(p, s, -7.533655316e-02f);
+    p = fmaf(p, s, 1.065466478e-01f);
+    p = fmaf(p, s, -1.420712918e-01f);
+    p = fmaf(p, s, 1.999305338e-01f);
+    p = fmaf(p, s, -3.333309293e-01f);
+    p = fmaf(p, s, 1.0f);
+    float a = t * p;
+    a = y > ax ? 1.5707963268f - a : a;
+    return x < 0.0f ? 3.1415926536f - a : a;
+}
+
+// angle between b1 and b2 (phi = atan2(|b1 x b2|, b1.b2)), V = kappa phi^2 / 2:
+// d1 = A dcos/db1, d2 = A dcos/db2 with A = kappa phi / sin(phi)
 __device__ __forceinline__ void bend_terms(float3 b1, float3 b2, float kappa, float3 &d1, float3 &d2) {
     const float l1s = dot3(b1, b1), l2s = dot3(b2, b2), dt = dot3(b1, b2);
     const float3 cr = cross3(b1, b2);
-    const float crn = sqrtf(dot3(cr, cr));
+    const float cr2 = dot3(cr, cr);
+    const float crn = cr2 > 0.0f ? cr2 * rsqrtf(cr2) : 0.0f;
     const float inv12 = rsqrtf(l1s * l2s);
     const float c = dt * inv12, sn = crn * inv12;
-    const float phi = atan2f(crn, dt);
+    const float phi = atan_pos(crn, dt);
     const float A = sn > 1e-6f ? __fdividef(kappa * phi, sn) : (c > 0.0f ? kappa : 0.0f);
-    d1 = A * (inv12 * b2 - __fdividef(c, l1s) * b1);  // A dcos/db1
-    d2 = A * (inv12 * b1 - __fdividef(c, l2s) * b2);  // A dcos/db2
+    d1 = A * (inv12 * b2 - __fdividef(c, l1s) * b1);
+    d2 = A * (inv12 * b1 - __fdividef(c, l2s) * b2);
 }
 
+// WCA (Eq. 14 cut at its minimum, shifted): -dV/dd = coef * d
 __device__ __forceinline__ float wca_coef(float r2, float eps, float sig2) {
     const float ir2 = __frcp_rn(r2), sr2 = sig2 * ir2;
     const float sr6 = sr2 * sr2 * sr2;
     return 24.0f * eps * (2.0f * sr6 * sr6 - sr6) * ir2;
 }
 
-__device__ float3 fast_force(const Sim &S, const PSmem &sm, int buf, int p, int N, float4 mh, float4 ml) {
-    const float4 *ph = sm.ph[buf], *pl = sm.pl[buf];
+struct PSmem {
+    float4 *ph[2], *pl[2];  // replica of the whole chain: positions hi / lo, double buffered
+    float4 *jbuf;           // [Nc] impulse J of the block's beads, for the spread
+    uint16_t *nbr;          // [Nc][NBR_CAP] bead-pair lists of the block's beads
+    uint32_t *wal;          // [Nc][WALL_CAP] packed solid-site coordinates
+    int *hkey, *hhead;      // [HASH_SIZE] cell hash
+    int16_t *hnext;         // [Nmax] cell lists
+    uint8_t *nn, *nw;       // [Nc] list lengths
+};
+
+__host__ __device__ inline size_t psmem_layout(int nmax, int nc, PSmem *p, char *base) {
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o += (bytes + 15) & ~(size_t)15; return base + at; };
+    char *ph0 = take(16 * (size_t)nmax), *ph1 = take(16 * (size_t)nmax);
+    char *pl0 = take(16 * (size_t)nmax), *pl1 = take(16 * (size_t)nmax);
+    char *jb = take(16 * (size_t)nc);
+    char *nbr = take(2 * (size_t)NBR_CAP * nc);
+    char *wal = take(4 * (size_t)WALL_CAP * nc);
+    char *hkey = take(4 * (size_t)HASH_SIZE), *hhead = take(4 * (size_t)HASH_SIZE);
+    char *hnext = take(2 * (size_t)nmax);
+    char *nn = take((size_t)nc), *nw = take((size_t)nc);
+    if (p) {
+        p->ph[0] = (float4 *)ph0; p->ph[1] = (float4 *)ph1;
+        p->pl[0] = (float4 *)pl0; p->pl[1] = (float4 *)pl1;
+        p->jbuf = (float4 *)jb;
+        p->nbr = (uint16_t *)nbr; p->wal = (uint32_t *)wal;
+        p->hkey = (int *)hkey; p->hhead = (int *)hhead; p->hnext = (int16_t *)hnext;
+        p->nn = (uint8_t *)nn; p->nw = (uint8_t *)nw;
+    }
+    return o;
+}
+
+// Automatic shape: 4 lanes per bead.  A single chain is spread over up to 8
+// blocks (about 50 beads per block: the sub-step is latency-bound, so fewer
+// beads per SM shorten it); an ensemble keeps each chain in as few blocks as
+// fit (<= 512 threads per block), since its realizations already fill the
+// GPU.  A shape set through lbmd_set_md_shape (S.md_T, S.md_C) takes precedence.
+MdShape md_shape(const Sim &S) {
+    MdShape m;
+    const int N = S.max_beads;
+    m.T = S.md_T > 0 ? S.md_T : 4;
+    const int per_block = 512 / m.T;
+    const int fit = max(1, (N + per_block - 1) / per_block);
+    const int spread = S.n_real == 1 ? min(8, max(fit, (N + 49) / 50)) : fit;
+    m.C = S.md_C > 0 ? S.md_C : spread;
+    m.Nc = N > 0 ? (N + m.C - 1) / m.C : 1;
+    m.threads = max(32, ((m.Nc * m.T + 31) / 32) * 32);
+    m.smem = psmem_layout(max(N, 1), m.Nc, nullptr, nullptr);
+    return m;
+}
+
+// Part of the conservative force on bead p computed by task lane lt of its
+// T lanes.  Terms: harmonic bonds (Eq. 19); the angular term of the angles at
+// p-1, p, p+1; WCA with the listed beads and solid sites.  The lanes' parts
+// add up to the full force.
+template <int T>
+__device__ float3 force_part(const Sim &S, const PSmem &sm, int buf, bool own, int p, int pl, int N, float4 mh,
+                             float4 ml, int lt) {
     float3 F = make_float3(0.f, 0.f, 0.f);
+    if (!own) return F;
+    // Every lane runs the same instructions on different data (lanes of a
+    // warp in different branches would run one after another): lane lt takes
+    // bond slot lt, angle slot lt and every T-th list entry from lt.
+    const float4 *ph = sm.ph[buf], *plo = sm.pl[buf];
     const bool m1 = p >= 1, m2 = p >= 2, p1 = p + 1 < N, p2 = p + 2 < N;
-    float4 hm1 = mh, lm1 = ml, hm2 = mh, lm2 = ml, hp1 = mh, lp1 = ml, hp2 = mh, lp2 = ml;
-    if (m1) { hm1 = ph[p - 1]; lm1 = pl[p - 1]; }
-    if (m2) { hm2 = ph[p - 2]; lm2 = pl[p - 2]; }
-    if (p1) { hp1 = ph[p + 1]; lp1 = pl[p + 1]; }
-    if (p2) { hp2 = ph[p + 2]; lp2 = pl[p + 2]; }
-    const float3 b0 = ffsub(hm1, lm1, hm2, lm2);  // r_{p-1} - r_{p-2}
-    const float3 b1 = ffsub(mh, ml, hm1, lm1);    // r_p - r_{p-1}
-    const float3 b2 = ffsub(hp1, lp1, mh, ml);    // r_{p+1} - r_p
-    const float3 b3 = ffsub(hp2, lp2, hp1, lp1);  // r_{p+2} - r_{p+1}
-    // harmonic bonds (Eq. 19)
-    // k (|b| - r0) b / |b|; |b| from the correctly rounded sqrt, because
-    // |b| - r0 cancels and keeps only the absolute error of |b|
-    if (m1) {
-        const float len = sqrtf(dot3(b1, b1));
-        F = F - __fdividef(S.k_bond * (len - S.r0), len) * b1;
+    if (lt < 3) {
+        float4 hm1 = mh, lm1 = ml, hm2 = mh, lm2 = ml, hp1 = mh, lp1 = ml, hp2 = mh, lp2 = ml;
+        if (m1) { hm1 = ph[p - 1]; lm1 = plo[p - 1]; }
+        if (m2) { hm2 = ph[p - 2]; lm2 = plo[p - 2]; }
+        if (p1) { hp1 = ph[p + 1]; lp1 = plo[p + 1]; }
+        if (p2) { hp2 = ph[p + 2]; lp2 = plo[p + 2]; }
+        const float3 b0 = ffsub(hm1, lm1, hm2, lm2);  // r_{p-1} - r_{p-2}
+        const float3 b1 = ffsub(mh, ml, hm1, lm1);    // r_p - r_{p-1}
+        const float3 b2 = ffsub(hp1, lp1, mh, ml);    // r_{p+1} - r_p
+        const float3 b3 = ffsub(hp2, lp2, hp1, lp1);  // r_{p+2} - r_{p+1}
+        // bond slots: 0 = bond to p-1 (force -k(|b1| - r0) b1/|b1|), 1 = bond to p+1.
+        // |b| comes from the correctly rounded sqrt, because |b| - r0 cancels
+        // and keeps only the absolute error of |b|.
+        for (int s = lt; s < 2; s += T) {
+            const float3 b = s == 0 ? b1 : b2;
+            if (s == 0 ? m1 : p1) {
+                const float len = sqrtf(dot3(b, b));
+                const float coef = __fdividef(S.k_bond * (len - S.r0), len);
+                F = F + (s == 0 ? -coef : coef) * b;
+            }
+        }
+        // angle slots: the angles at p-1, p, p+1 with their share of the force
+        // on p: +A dcos/db2, A (dcos/db1 - dcos/db2), -A dcos/db1
+        if (S.kappa != 0.0f) {
+            for (int s = lt; s < 3; s += T) {
+                const float3 u = s == 0 ? b0 : (s == 1 ? b1 : b2);
+                const float3 w = s == 0 ? b1 : (s == 1 ? b2 : b3);
+                if (s == 0 ? m2 : (s == 1 ? (m1 && p1) : p2)) {
+                    float3 d1, d2;
+                    bend_terms(u, w, S.kappa, d1, d2);
+                    const float al = s == 0 ? 0.0f : (s == 1 ? 1.0f : -1.0f);
+                    const float be = s == 0 ? 1.0f : (s == 1 ? -1.0f : 0.0f);
+                    F = F + al * d1 + be * d2;
+                }
+            }
+        }
     }
-    if (p1) {
-        const float len = sqrtf(dot3(b2, b2));
-        F = F + __fdividef(S.k_bond * (len - S.r0), len) * b2;
-    }
-    // angular term kappa phi^2 / 2 at beads p-1, p, p+1
-    if (S.kappa != 0.0f) {
-        float3 d1, d2;
-        if (m2) { bend_terms(b0, b1, S.kappa, d1, d2); F = F + d2; }
-        if (m1 && p1) { bend_terms(b1, b2, S.kappa, d1, d2); F = F + d1 - d2; }
-        if (p2) { bend_terms(b2, b3, S.kappa, d1, d2); F = F - d1; }
-    }
-    // WCA with listed non-bonded beads (Eq. 14 cut at 2^(1/6) sigma)
     const float fnx = (float)S.nx, fny = (float)S.ny, fnz = (float)S.nz;
-    const int nn = sm.nn[p];
-    for (int k = 0; k < nn; ++k) {
-        const int q = sm.nbr[p * NBR_CAP + k];
-        const float4 qh = ph[q], ql = pl[q];
-        const float3 d = make_float3(ff_diff(mh.x, ml.x, qh.x, ql.x, fnx, S.inx), ff_diff(mh.y, ml.y, qh.y, ql.y, fny, S.iny),
-                                     ff_diff(mh.z, ml.z, qh.z, ql.z, fnz, S.inz));
-        const float r2 = dot3(d, d);
-        if (r2 < S.lj_rc2) F = F + wca_coef(r2, S.lj_eps, S.lj_sig2) * d;
+    const int lj0 = lt, ljs = T;
+    const bool t_wall = true;
+    {
+        const int nn = sm.nn[pl];
+        for (int k = lj0; k < nn; k += ljs) {
+            const int q = sm.nbr[pl * NBR_CAP + k];
+            const float4 qh = ph[q], ql = plo[q];
+            const float3 d = make_float3(ff_diff(mh.x, ml.x, qh.x, ql.x, fnx, S.inx),
+                                         ff_diff(mh.y, ml.y, qh.y, ql.y, fny, S.iny),
+                                         ff_diff(mh.z, ml.z, qh.z, ql.z, fnz, S.inz));
+            const float r2 = dot3(d, d);
+            if (r2 < S.lj_rc2) F = F + wca_coef(r2, S.lj_eps, S.lj_sig2) * d;
+        }
     }
-    // WCA with listed solid sites
-    const int nw = sm.nw[p];
-    for (int k = 0; k < nw; ++k) {
-        const uint32_t pk = sm.wal[p * WALL_CAP + k];
-        const float X = (float)(pk & 0xfffu), Y = (float)((pk >> 12) & 0x3ffu), Z = (float)(pk >> 22);
-        const float3 d = make_float3(ff_diff(mh.x, ml.x, X, 0.f, fnx, S.inx), ff_diff(mh.y, ml.y, Y, 0.f, fny, S.iny),
-                                     ff_diff(mh.z, ml.z, Z, 0.f, fnz, S.inz));
-        const float r2 = dot3(d, d);
-        if (r2 < S.wall_rc2) F = F + wca_coef(r2, S.wall_eps, S.wall_sig2) * d;
+    if (t_wall) {
+        const int nw = sm.nw[pl];
+        for (int k = lt; k < nw; k += T) {
+            const uint32_t pk = sm.wal[pl * WALL_CAP + k];
+            const float X = (float)(pk & 0xfffu), Y = (float)((pk >> 12) & 0x3ffu), Z = (float)(pk >> 22);
+            const float3 d = make_float3(ff_diff(mh.x, ml.x, X, 0.f, fnx, S.inx), ff_diff(mh.y, ml.y, Y, 0.f, fny, S.iny),
+                                         ff_diff(mh.z, ml.z, Z, 0.f, fnz, S.inz));
+            const float r2 = dot3(d, d);
+            if (r2 < S.wall_rc2) F = F + wca_coef(r2, S.wall_eps, S.wall_sig2) * d;
+        }
+    }
+    return F;
+}
+
+// sum over the T consecutive lanes of a bead (fixed butterfly: deterministic)
+template <int T>
+__device__ __forceinline__ float3 group_sum(float3 F) {
+#pragma unroll
+    for (int o = 1; o < T; o <<= 1) {
+        F.x += __shfl_xor_sync(0xffffffffu, F.x, o);
+        F.y += __shfl_xor_sync(0xffffffffu, F.y, o);
+        F.z += __shfl_xor_sync(0xffffffffu, F.z, o);
     }
     return F;
 }
@@ -273,24 +361,30 @@ __device__ __forceinline__ void list_insert(uint16_t *lst, int &n, int q) {
     ++n;
 }
 
-__device__ void build_lists(const Sim &S, const PSmem &sm, int buf, int p, int N, bool own, float4 mh, float4 ml,
-                            int *s_flag, int *s_err) {
+__device__ __forceinline__ void cell_of(const Sim &S, float xw, float yw, float zw, int &ci, int &cj, int &ck) {
+    ci = min((int)(xw * S.cell_per_site[0]), S.ncell[0] - 1);
+    cj = min((int)(yw * S.cell_per_site[1]), S.ncell[1] - 1);
+    ck = min((int)(zw * S.cell_per_site[2]), S.ncell[2] - 1);
+}
+
+// Rebuild the lists of the block's beads from the block's replica (buffer
+// buf).  Called by every thread of the block; clear_flag (if not null) is
+// reset once every thread has read it.
+__device__ void build_lists(const Sim &S, const PSmem &sm, int buf, int N, int p, int pl, bool owner,
+                            int *clear_flag, int *s_err) {
     const bool hashed = S.ncell[0] >= 3 && S.ncell[1] >= 3 && S.ncell[2] >= 3;
     const float fnx = (float)S.nx, fny = (float)S.ny, fnz = (float)S.nz;
+    const float4 *ph = sm.ph[buf], *plo = sm.pl[buf];
     if (hashed)
         for (int k = threadIdx.x; k < HASH_SIZE; k += blockDim.x) { sm.hkey[k] = -1; sm.hhead[k] = -1; }
     __syncthreads();
-    if (threadIdx.x == 0) *s_flag = 0;
-    float xw = 0.f, yw = 0.f, zw = 0.f;
-    int ci = 0, cj = 0, ck = 0;
-    if (own) {
-        xw = ff_wrap(mh.x, ml.x, fnx, S.inx);
-        yw = ff_wrap(mh.y, ml.y, fny, S.iny);
-        zw = ff_wrap(mh.z, ml.z, fnz, S.inz);
-        ci = min((int)(xw * S.cell_per_site[0]), S.ncell[0] - 1);
-        cj = min((int)(yw * S.cell_per_site[1]), S.ncell[1] - 1);
-        ck = min((int)(zw * S.cell_per_site[2]), S.ncell[2] - 1);
-        if (hashed) {
+    if (clear_flag && threadIdx.x == 0) *clear_flag = 0;
+    if (hashed) {
+        for (int q = threadIdx.x; q < N; q += blockDim.x) {
+            const float4 qh = ph[q], ql = plo[q];
+            int ci, cj, ck;
+            cell_of(S, ff_wrap(qh.x, ql.x, fnx, S.inx), ff_wrap(qh.y, ql.y, fny, S.iny), ff_wrap(qh.z, ql.z, fnz, S.inz),
+                    ci, cj, ck);
             const int key = ci + S.ncell[0] * (cj + S.ncell[1] * ck);
             int slot = cell_slot(key);
             for (int probe = 0; probe < HASH_SIZE; ++probe) {
@@ -298,79 +392,84 @@ __device__ void build_lists(const Sim &S, const PSmem &sm, int buf, int p, int N
                 if (prev == -1 || prev == key) break;
                 slot = (slot + 1) & (HASH_SIZE - 1);
             }
-            sm.hnext[p] = (int16_t)atomicExch(sm.hhead + slot, p);
+            sm.hnext[q] = (int16_t)atomicExch(sm.hhead + slot, q);
         }
     }
     __syncthreads();
-    if (!own) return;
-    const float4 *ph = sm.ph[buf], *pl = sm.pl[buf];
-    uint16_t *lst = sm.nbr + p * NBR_CAP;
-    int n = 0;
-    auto consider = [&](int q) {
-        if (q == p || q == p - 1 || q == p + 1) return;
-        const float4 qh = ph[q], ql = pl[q];
-        const float dx = ff_diff(mh.x, ml.x, qh.x, ql.x, fnx, S.inx), dy = ff_diff(mh.y, ml.y, qh.y, ql.y, fny, S.iny),
-                    dz = ff_diff(mh.z, ml.z, qh.z, ql.z, fnz, S.inz);
-        if (dx * dx + dy * dy + dz * dz < S.rl2) list_insert(lst, n, q);
-    };
-    if (hashed) {
-        for (int dk = -1; dk <= 1; ++dk)
-            for (int dj = -1; dj <= 1; ++dj)
-                for (int di = -1; di <= 1; ++di) {
-                    const int key = wrapi(ci + di, S.ncell[0]) +
-                                    S.ncell[0] * (wrapi(cj + dj, S.ncell[1]) + S.ncell[1] * wrapi(ck + dk, S.ncell[2]));
-                    int slot = cell_slot(key);
-                    for (int probe = 0; probe < HASH_SIZE; ++probe) {
-                        const int kk = sm.hkey[slot];
-                        if (kk == key) {
-                            for (int q = sm.hhead[slot], guard = 0; q >= 0 && guard < N; q = sm.hnext[q], ++guard)
-                                consider(q);
-                            break;
+    if (owner) {
+        const float4 mh = ph[p], ml = plo[p];
+        const float xw = ff_wrap(mh.x, ml.x, fnx, S.inx), yw = ff_wrap(mh.y, ml.y, fny, S.iny),
+                    zw = ff_wrap(mh.z, ml.z, fnz, S.inz);
+        uint16_t *lst = sm.nbr + pl * NBR_CAP;
+        int n = 0;
+        auto consider = [&](int q) {
+            if (q == p || q == p - 1 || q == p + 1) return;
+            const float4 qh = ph[q], ql = plo[q];
+            const float dx = ff_diff(mh.x, ml.x, qh.x, ql.x, fnx, S.inx), dy = ff_diff(mh.y, ml.y, qh.y, ql.y, fny, S.iny),
+                        dz = ff_diff(mh.z, ml.z, qh.z, ql.z, fnz, S.inz);
+            if (dx * dx + dy * dy + dz * dz < S.rl2) list_insert(lst, n, q);
+        };
+        if (hashed) {
+            int ci, cj, ck;
+            cell_of(S, xw, yw, zw, ci, cj, ck);
+            for (int dk = -1; dk <= 1; ++dk)
+                for (int dj = -1; dj <= 1; ++dj)
+                    for (int di = -1; di <= 1; ++di) {
+                        const int key = wrapi(ci + di, S.ncell[0]) +
+                                        S.ncell[0] * (wrapi(cj + dj, S.ncell[1]) + S.ncell[1] * wrapi(ck + dk, S.ncell[2]));
+                        int slot = cell_slot(key);
+                        for (int probe = 0; probe < HASH_SIZE; ++probe) {
+                            const int kk = sm.hkey[slot];
+                            if (kk == key) {
+                                for (int q = sm.hhead[slot], guard = 0; q >= 0 && guard < N; q = sm.hnext[q], ++guard)
+                                    consider(q);
+                                break;
+                            }
+                            if (kk == -1) break;
+                            slot = (slot + 1) & (HASH_SIZE - 1);
                         }
-                        if (kk == -1) break;
-                        slot = (slot + 1) & (HASH_SIZE - 1);
                     }
-                }
-    } else {
-        for (int q = 0; q < N; ++q) consider(q);
-    }
-    if (n > NBR_CAP) { atomicOr(s_err, ST_CAPACITY); n = NBR_CAP; }
-    sm.nn[p] = (uint8_t)n;
-    // solid sites within the wall-list radius; the link word of the bead's cell
-    // corner says whether any solid site lies within the scanned box at all
-    int m = 0;
-    const int cx0 = (int)floorf(xw), cy0 = (int)floorf(yw), cz0 = (int)floorf(zw);
-    if (S.rlw < 2.0f) {
-        // every site within rlw < 2 of the bead lies in the 4x4x4 box starting
-        // one site below its cell corner; its solid sites are one bit mask
-        unsigned long long mm = __ldg(S.wallmask + cx0 + S.nx * (cy0 + S.ny * cz0));
-        while (mm) {
-            const int bit = __ffsll((long long)mm) - 1;
-            mm &= mm - 1;
-            const int X = cx0 + (bit & 3) - 1, Y = cy0 + ((bit >> 2) & 3) - 1, Z = cz0 + (bit >> 4) - 1;
-            const float dx = xw - (float)X, dy = yw - (float)Y, dz = zw - (float)Z;
-            if (dx * dx + dy * dy + dz * dz >= S.rlw2) continue;
-            const int xx = wrapi(X, S.nx), yy = wrapi(Y, S.ny), zz = wrapi(Z, S.nz);
-            if (m < WALL_CAP) sm.wal[p * WALL_CAP + m] = (uint32_t)xx | ((uint32_t)yy << 12) | ((uint32_t)zz << 22);
-            ++m;
+        } else {
+            for (int q = 0; q < N; ++q) consider(q);
         }
-    } else if (__ldg(S.link + cx0 + S.nx * (cy0 + S.ny * cz0)) & NEAR_SOLID_BIT) {
-        const int x0 = (int)floorf(xw - S.rlw), x1 = (int)floorf(xw + S.rlw);
-        const int y0 = (int)floorf(yw - S.rlw), y1 = (int)floorf(yw + S.rlw);
-        const int z0 = (int)floorf(zw - S.rlw), z1 = (int)floorf(zw + S.rlw);
-        for (int Z = z0; Z <= z1; ++Z)
-            for (int Y = y0; Y <= y1; ++Y)
-                for (int X = x0; X <= x1; ++X) {
-                    const int xx = wrap_any(X, S.nx), yy = wrap_any(Y, S.ny), zz = wrap_any(Z, S.nz);
-                    if (!(__ldg(S.link + xx + S.nx * (yy + S.ny * zz)) & SOLID_BIT)) continue;
-                    const float dx = xw - (float)X, dy = yw - (float)Y, dz = zw - (float)Z;
-                    if (dx * dx + dy * dy + dz * dz >= S.rlw2) continue;
-                    if (m < WALL_CAP) sm.wal[p * WALL_CAP + m] = (uint32_t)xx | ((uint32_t)yy << 12) | ((uint32_t)zz << 22);
-                    ++m;
-                }
+        if (n > NBR_CAP) { atomicOr(s_err, ST_CAPACITY); n = NBR_CAP; }
+        sm.nn[pl] = (uint8_t)n;
+        // solid sites within the wall-list radius
+        int m = 0;
+        const int cx0 = (int)floorf(xw), cy0 = (int)floorf(yw), cz0 = (int)floorf(zw);
+        if (S.rlw < 2.0f) {
+            // every site within rlw < 2 of the bead lies in the 4x4x4 box starting
+            // one site below its cell corner; its solid sites are one bit mask
+            unsigned long long mm = __ldg(S.wallmask + cx0 + S.nx * (cy0 + S.ny * cz0));
+            while (mm) {
+                const int bit = __ffsll((long long)mm) - 1;
+                mm &= mm - 1;
+                const int X = cx0 + (bit & 3) - 1, Y = cy0 + ((bit >> 2) & 3) - 1, Z = cz0 + (bit >> 4) - 1;
+                const float dx = xw - (float)X, dy = yw - (float)Y, dz = zw - (float)Z;
+                if (dx * dx + dy * dy + dz * dz >= S.rlw2) continue;
+                const int xx = wrapi(X, S.nx), yy = wrapi(Y, S.ny), zz = wrapi(Z, S.nz);
+                if (m < WALL_CAP) sm.wal[pl * WALL_CAP + m] = (uint32_t)xx | ((uint32_t)yy << 12) | ((uint32_t)zz << 22);
+                ++m;
+            }
+        } else if (__ldg(S.link + cx0 + S.nx * (cy0 + S.ny * cz0)) & NEAR_SOLID_BIT) {
+            const int x0 = (int)floorf(xw - S.rlw), x1 = (int)floorf(xw + S.rlw);
+            const int y0 = (int)floorf(yw - S.rlw), y1 = (int)floorf(yw + S.rlw);
+            const int z0 = (int)floorf(zw - S.rlw), z1 = (int)floorf(zw + S.rlw);
+            for (int Z = z0; Z <= z1; ++Z)
+                for (int Y = y0; Y <= y1; ++Y)
+                    for (int X = x0; X <= x1; ++X) {
+                        const int xx = wrap_any(X, S.nx), yy = wrap_any(Y, S.ny), zz = wrap_any(Z, S.nz);
+                        if (!(__ldg(S.link + xx + S.nx * (yy + S.ny * zz)) & SOLID_BIT)) continue;
+                        const float dx = xw - (float)X, dy = yw - (float)Y, dz = zw - (float)Z;
+                        if (dx * dx + dy * dy + dz * dz >= S.rlw2) continue;
+                        if (m < WALL_CAP) sm.wal[pl * WALL_CAP + m] = (uint32_t)xx | ((uint32_t)yy << 12) | ((uint32_t)zz << 22);
+                        ++m;
+                    }
+        }
+        if (m > WALL_CAP) { atomicOr(s_err, ST_CAPACITY); m = WALL_CAP; }
+        sm.nw[pl] = (uint8_t)m;
     }
-    if (m > WALL_CAP) { atomicOr(s_err, ST_CAPACITY); m = WALL_CAP; }
-    sm.nw[p] = (uint8_t)m;
+    __syncthreads();
 }
 
 // SM cycles spent in phase k of realization 0 (only while profiling)
@@ -404,28 +503,41 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (*red)[NV]) {
     }
 }
 
-// ---------------------------------------------------------------------------
-// the particle kernel: one block per realization, one thread per bead
-// ---------------------------------------------------------------------------
-template <int MAXT>
-__global__ void __launch_bounds__(MAXT, 1) k_particles(const Sim S) {
-    extern __shared__ __align__(16) char smem_raw[];
-    __shared__ int s_flag, s_err;
-    __shared__ double red[32][9];
-    PSmem sm;
-    psmem_layout(blockDim.x, &sm, smem_raw);
+__device__ __forceinline__ void sync_all(cg::cluster_group &cl, int C) {
+    if (C > 1) cl.sync();
+    else __syncthreads();
+}
 
-    const int r = blockIdx.x;
+// ---------------------------------------------------------------------------
+// the particle kernel (one cluster of C blocks per realization)
+// ---------------------------------------------------------------------------
+template <int T>
+__global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, const int Nmax, const int Nc) {
+    extern __shared__ __align__(16) char smem_raw[];
+    __shared__ int s_flag[2], s_err;
+    __shared__ double red[16][9];
+    __shared__ double cpart[8][9];
+    PSmem sm;
+    psmem_layout(Nmax, Nc, &sm, smem_raw);
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = C > 1 ? (int)cl.block_rank() : 0;
+    const int r = blockIdx.x / C;
     const int off = S.bead_off[r];
     const int N = S.bead_off[r + 1] - off;
-    const int p = threadIdx.x;
-    const bool own = p < N;
+    const int lt = threadIdx.x % T, pl = threadIdx.x / T;
+    const int p = rank * Nc + pl;
+    const bool own = pl < Nc && p < N;
+    const bool owner = own && lt == 0;  // the lane that publishes the bead
     const long long step = S.ctrl->step;
     const float fnx = (float)S.nx, fny = (float)S.ny, fnz = (float)S.nz;
-    if (threadIdx.x == 0) { s_flag = 0; s_err = 0; }
-
     unsigned long long tclk = clock64();
-    // 1. state and the fluid velocity the gather kernel froze for this step
+    if (threadIdx.x == 0) { s_flag[0] = 0; s_flag[1] = 0; s_err = 0; }
+
+    // replica of the whole chain and the state of this lane's bead
+    for (int q = threadIdx.x; q < N; q += blockDim.x) {
+        sm.ph[0][q] = S.r_hi[off + q];
+        sm.pl[0][q] = S.r_lo[off + q];
+    }
     float4 mh = make_float4(0.f, 0.f, 0.f, 0.f), ml = mh;
     float3 v = make_float3(0.f, 0.f, 0.f), up = v;
     if (own) {
@@ -435,21 +547,20 @@ __global__ void __launch_bounds__(MAXT, 1) k_particles(const Sim S) {
         v = make_float3(vv.x, vv.y, vv.z);
         const float4 uu = S.up[off + p];
         up = make_float3(uu.x, uu.y, uu.z);
-        sm.ph[0][p] = mh;
-        sm.pl[0][p] = ml;
     }
-    __syncthreads();
+    // every block of the cluster is running and initialised before any
+    // block writes into another's shared memory
+    sync_all(cl, C);
     phase_mark(S, 0, tclk);
-    // neighbour and wall lists at the starting positions (contains barriers)
-    build_lists(S, sm, 0, p, N, own, mh, ml, &s_flag, &s_err);
-    __syncthreads();
+    build_lists(S, sm, 0, N, p, pl, owner, nullptr, &s_err);
     phase_mark(S, 1, tclk);
 
-    // per-step bead diagnostics at the starting state
+    // per-step bead diagnostics at the starting state: block partial -> block 0
     {
         double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        if (own) {
-            const float xw = ff_wrap(mh.x, ml.x, fnx, S.inx), yw = ff_wrap(mh.y, ml.y, fny, S.iny), zw = ff_wrap(mh.z, ml.z, fnz, S.inz);
+        if (owner) {
+            const float xw = ff_wrap(mh.x, ml.x, fnx, S.inx), yw = ff_wrap(mh.y, ml.y, fny, S.iny),
+                        zw = ff_wrap(mh.z, ml.z, fnz, S.inz);
             const float Fe = in_channel(S, xw, yw, zw) ? S.E : 0.0f;
             const double X = (double)mh.x + (double)ml.x;
             acc[0] = v.x; acc[1] = v.y; acc[2] = v.z;
@@ -460,118 +571,158 @@ __global__ void __launch_bounds__(MAXT, 1) k_particles(const Sim S) {
         }
         block_sum<9>(acc, red);
         if (threadIdx.x == 0) {
-            lbmd_diag *row = S.ring + (size_t)r * LBMD_DIAG_RING + (step % LBMD_DIAG_RING);
-            row->step = step;
-            row->p_beads[0] = acc[0]; row->p_beads[1] = acc[1]; row->p_beads[2] = acc[2];
-            const double inv = N > 0 ? 1.0 / N : 0.0;
-            row->com[0] = acc[3] * inv; row->com[1] = acc[4] * inv; row->com[2] = acc[5] * inv;
-            row->n_translocated = acc[6];
-            row->dWH_dt = acc[7];
-            row->dWE_dt = acc[8];
+            double *dst = C > 1 ? cl.map_shared_rank(&cpart[rank][0], 0) : &cpart[0][0];
+            for (int k = 0; k < 9; ++k) dst[k] = acc[k];
         }
     }
 
-    // 2. MD cycle
+    // MD cycle
     const float dt = 1.0f / (float)S.M, h = 0.5f * dt;
     const float dtb = dt / (float)S.Mb, hb = 0.5f * dtb;
     const float amp = S.kT > 0.0f ? sqrtf(2.0f * S.gamma * S.kT / dt) : 0.0f;
     float3 J = make_float3(0.f, 0.f, 0.f);
     float4 bh = mh, bl = ml;  // position at the last list build
-    int buf = 0;
-    float3 ff = make_float3(0.f, 0.f, 0.f);
-    if (own) ff = fast_force(S, sm, buf, p, N, mh, ml);
+    int buf = 0, t = 0;
+    float3 ff = group_sum<T>(force_part<T>(S, sm, buf, own, p, pl, N, mh, ml, lt));
+    if (!own) ff = make_float3(0.f, 0.f, 0.f);
     for (int sub = 0; sub < S.M; ++sub) {
         float3 xi = make_float3(0.f, 0.f, 0.f);
         if (own && amp > 0.0f) xi = amp * gauss3(S.seed, (uint32_t)r, (uint32_t)p, step, (uint32_t)sub);
         if (own) {  // first half kick: field + friction + noise
-            const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx, S.inx), ff_wrap(mh.y, ml.y, fny, S.iny), ff_wrap(mh.z, ml.z, fnz, S.inz));
+            const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx, S.inx), ff_wrap(mh.y, ml.y, fny, S.iny),
+                                       ff_wrap(mh.z, ml.z, fnz, S.inz));
             const float3 fl = S.gamma * (up - v) + xi;
             v = v + h * (make_float3(ch ? S.E : 0.0f, 0.f, 0.f) + fl);
             J = J + h * fl;
         }
-        for (int b = 0; b < S.Mb; ++b) {
+        for (int b = 0; b < S.Mb; ++b, ++t) {
+            const int nb = buf ^ 1;
             if (own) {
                 v = v + hb * ff;
                 ff_add(mh.x, ml.x, dtb * v.x);
                 ff_add(mh.y, ml.y, dtb * v.y);
                 ff_add(mh.z, ml.z, dtb * v.z);
-                sm.ph[buf ^ 1][p] = mh;
-                sm.pl[buf ^ 1][p] = ml;
                 const float3 dd = ffsub(mh, ml, bh, bl);
-                if (dot3(dd, dd) > S.skin_half2) s_flag = 1;
+                const bool moved = dot3(dd, dd) > S.skin_half2;
+                if (lt == 0) {
+                    if (C > 1) {
+                        for (int c = 0; c < C; ++c) {
+                            *cl.map_shared_rank(sm.ph[nb] + p, c) = mh;
+                            *cl.map_shared_rank(sm.pl[nb] + p, c) = ml;
+                            if (moved) *cl.map_shared_rank(&s_flag[t & 1], c) = 1;
+                        }
+                    } else {
+                        sm.ph[nb][p] = mh;
+                        sm.pl[nb][p] = ml;
+                        if (moved) s_flag[t & 1] = 1;
+                    }
+                }
             }
-            __syncthreads();
-            buf ^= 1;
-            if (s_flag) {
-                build_lists(S, sm, buf, p, N, own, mh, ml, &s_flag, &s_err);
+            sync_all(cl, C);
+            buf = nb;
+            if (s_flag[t & 1]) {
+                const unsigned long long t0 = clock64();
+                build_lists(S, sm, buf, N, p, pl, owner, &s_flag[t & 1], &s_err);
                 bh = mh;
                 bl = ml;
+                if (S.phase && blockIdx.x == 0 && threadIdx.x == 0) {
+                    atomicAdd(S.phase + 4, clock64() - t0);  // cycles in rebuilds
+                    atomicAdd(S.phase + 5, 1ull);            // rebuilds
+                }
             }
+            const float3 F = group_sum<T>(force_part<T>(S, sm, buf, own, p, pl, N, mh, ml, lt));
             if (own) {
-                ff = fast_force(S, sm, buf, p, N, mh, ml);
+                ff = F;
                 v = v + hb * ff;
             }
         }
         if (own) {  // second half kick with the same noise
-            const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx, S.inx), ff_wrap(mh.y, ml.y, fny, S.iny), ff_wrap(mh.z, ml.z, fnz, S.inz));
+            const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx, S.inx), ff_wrap(mh.y, ml.y, fny, S.iny),
+                                       ff_wrap(mh.z, ml.z, fnz, S.inz));
             const float3 fl = S.gamma * (up - v) + xi;
             v = v + h * (make_float3(ch ? S.E : 0.0f, 0.f, 0.f) + fl);
             J = J + h * fl;
         }
     }
-    if (own) sm.ups[p] = make_float4(J.x, J.y, J.z, 0.f);
+    if (owner) sm.jbuf[pl] = make_float4(J.x, J.y, J.z, 0.f);
     __syncthreads();
     phase_mark(S, 2, tclk);
 
-    // 3. spread -W J onto the fluid corners of the starting position, with the
-    //    (site, weight) pairs the gather kernel recorded: one thread per pair
+    // spread -W J onto the fluid corners of the starting position, with the
+    // (site, weight) pairs the gather kernel recorded: one thread per pair
     {
         const size_t ns = (size_t)S.ns;
-        for (int k = threadIdx.x; k < 8 * N; k += blockDim.x) {
-            const int gnode = S.pair_node[(size_t)off * 8 + k];
+        const int nown = max(0, min(Nc, N - rank * Nc));
+        for (int k = threadIdx.x; k < 8 * nown; k += blockDim.x) {
+            const size_t pair = (size_t)(off + rank * Nc) * 8 + k;
+            const int gnode = S.pair_node[pair];
             if (gnode < 0) continue;
-            const float W = S.pair_w[(size_t)off * 8 + k];
-            const float4 Jq = sm.ups[k >> 3];
+            const float W = S.pair_w[pair];
+            const float4 Jq = sm.jbuf[k >> 3];
             const size_t base = (size_t)r * 2 * ns + (size_t)gnode;  // = (r*3 + 0)*ns + site
             atomicAdd(S.G + base, (unsigned long long)__float2ll_rn(-W * Jq.x * FIX_SCALE_F));
             atomicAdd(S.G + base + ns, (unsigned long long)__float2ll_rn(-W * Jq.y * FIX_SCALE_F));
             atomicAdd(S.G + base + 2 * ns, (unsigned long long)__float2ll_rn(-W * Jq.z * FIX_SCALE_F));
         }
     }
-    __syncthreads();
-    phase_mark(S, 3, tclk);
-
-    if (own) {
+    if (owner) {
         ff_norm(mh.x, ml.x);
         ff_norm(mh.y, ml.y);
         ff_norm(mh.z, ml.z);
         S.r_hi[off + p] = mh;
         S.r_lo[off + p] = ml;
         S.v[off + p] = make_float4(v.x, v.y, v.z, 0.f);
-        S.up[off + p] = make_float4(up.x, up.y, up.z, 0.f);
         S.J[off + p] = make_float4(J.x, J.y, J.z, 0.f);
         if (!isfinite(mh.x + mh.y + mh.z + v.x + v.y + v.z)) atomicOr(&s_err, ST_NONFINITE);
     }
-    __syncthreads();
+    // no block leaves while another may still write into its shared memory;
+    // after this barrier block 0 holds every block's diagnostics partial
+    sync_all(cl, C);
+    phase_mark(S, 3, tclk);
     if (threadIdx.x == 0 && s_err) atomicOr(&S.ctrl->status, s_err);
+    if (rank == 0 && threadIdx.x == 0) {
+        double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int c = 0; c < C; ++c)
+            for (int k = 0; k < 9; ++k) acc[k] += cpart[c][k];
+        lbmd_diag *row = S.ring + (size_t)r * LBMD_DIAG_RING + (step % LBMD_DIAG_RING);
+        row->step = step;
+        row->p_beads[0] = acc[0]; row->p_beads[1] = acc[1]; row->p_beads[2] = acc[2];
+        const double inv = N > 0 ? 1.0 / N : 0.0;
+        row->com[0] = acc[3] * inv; row->com[1] = acc[4] * inv; row->com[2] = acc[5] * inv;
+        row->n_translocated = acc[6];
+        row->dWH_dt = acc[7];
+        row->dWE_dt = acc[8];
+    }
 }
 
-template <int MAXT>
-static cudaError_t launch_particles_t(const Sim &S, int threads, size_t smem, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(k_particles<MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int T>
+static cudaError_t launch_particles_t(const Sim &S, const MdShape &m, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_particles<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m.smem);
     if (e != cudaSuccess) return e;
-    k_particles<MAXT><<<S.n_real, threads, smem, st>>>(S);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(S.n_real * m.C);
+    cfg.blockDim = dim3(m.threads);
+    cfg.dynamicSmemBytes = m.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = m.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_particles<T>, S, m.C, max(S.max_beads, 1), m.Nc);
 }
 
-// the launch bound follows the largest chain so that short chains get more
-// registers per thread
 cudaError_t launch_particles(const Sim &S, const void *, cudaStream_t st) {
-    const int threads = particle_threads(S);
-    const size_t smem = particle_smem_bytes(threads);
-    if (threads <= 256) return launch_particles_t<256>(S, threads, smem, st);
-    if (threads <= 512) return launch_particles_t<512>(S, threads, smem, st);
-    return launch_particles_t<1024>(S, threads, smem, st);
+    if (S.total_beads == 0) return cudaSuccess;
+    const MdShape m = md_shape(S);
+    switch (m.T) {
+        case 1: return launch_particles_t<1>(S, m, st);
+        case 2: return launch_particles_t<2>(S, m, st);
+        case 8: return launch_particles_t<8>(S, m, st);
+        default: return launch_particles_t<4>(S, m, st);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -582,8 +733,9 @@ __global__ void __launch_bounds__(1024) k_bead_observables(const Sim S, const vo
     using T = typename PopT<PREC>::T;
     extern __shared__ __align__(16) char smem_raw[];
     __shared__ double red[32][9];
-    PSmem sm;
-    psmem_layout(blockDim.x, &sm, smem_raw);
+    float4 *ph = reinterpret_cast<float4 *>(smem_raw);
+    float4 *plo = ph + blockDim.x;
+    float4 *ups = plo + blockDim.x;
     const int r = blockIdx.x;
     const int off = S.bead_off[r];
     const int N = S.bead_off[r + 1] - off;
@@ -596,26 +748,27 @@ __global__ void __launch_bounds__(1024) k_bead_observables(const Sim S, const vo
         mh = S.r_hi[off + p];
         ml = S.r_lo[off + p];
         vv = S.v[off + p];
-        sm.ph[0][p] = mh;
-        sm.pl[0][p] = ml;
+        ph[p] = mh;
+        plo[p] = ml;
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int q = warp; q < N; q += nwarps) {
-        const float4 qh = sm.ph[0][q], ql = sm.pl[0][q];
+        const float4 qh = ph[q], ql = plo[q];
         int node;
         float W;
-        const float3 u = gather_warp(S, A, ff_wrap(qh.x, ql.x, fnx, S.inx), ff_wrap(qh.y, ql.y, fny, S.iny), ff_wrap(qh.z, ql.z, fnz, S.inz),
-                                     node, W);
-        if ((threadIdx.x & 31) == 0) sm.ups[q] = make_float4(u.x, u.y, u.z, 0.f);
+        const float3 u = gather_warp(S, A, ff_wrap(qh.x, ql.x, fnx, S.inx), ff_wrap(qh.y, ql.y, fny, S.iny),
+                                     ff_wrap(qh.z, ql.z, fnz, S.inz), node, W);
+        if ((threadIdx.x & 31) == 0) ups[q] = make_float4(u.x, u.y, u.z, 0.f);
     }
     __syncthreads();
     const double X = (double)mh.x + (double)ml.x, Y = (double)mh.y + (double)ml.y, Z = (double)mh.z + (double)ml.z;
     const bool tr = own && S.wall_x >= 0 && X > (double)S.wall_x + 0.5;
     double a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (own) {
-        const float4 u = sm.ups[p];
-        const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx, S.inx), ff_wrap(mh.y, ml.y, fny, S.iny), ff_wrap(mh.z, ml.z, fnz, S.inz));
+        const float4 u = ups[p];
+        const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx, S.inx), ff_wrap(mh.y, ml.y, fny, S.iny),
+                                   ff_wrap(mh.z, ml.z, fnz, S.inz));
         a[0] = vv.x; a[1] = vv.y; a[2] = vv.z;
         a[3] = X; a[4] = Y; a[5] = Z;
         a[6] = tr ? 1.0 : 0.0;
@@ -661,18 +814,10 @@ __global__ void __launch_bounds__(1024) k_bead_observables(const Sim S, const vo
 }
 
 cudaError_t launch_bead_observables(const Sim &S, const void *A, cudaStream_t st) {
-    const int threads = particle_threads(S);
-    const size_t smem = particle_smem_bytes(threads);
-    cudaError_t e;
-    if (S.precision == LBMD_FP16DEV) {
-        e = cudaFuncSetAttribute(k_bead_observables<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_bead_observables<1><<<S.n_real, threads, smem, st>>>(S, A);
-    } else {
-        e = cudaFuncSetAttribute(k_bead_observables<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_bead_observables<0><<<S.n_real, threads, smem, st>>>(S, A);
-    }
+    const int threads = max(32, ((S.max_beads + 31) / 32) * 32);
+    const size_t smem = 48 * (size_t)threads;
+    if (S.precision == LBMD_FP16DEV) k_bead_observables<1><<<S.n_real, threads, smem, st>>>(S, A);
+    else k_bead_observables<0><<<S.n_real, threads, smem, st>>>(S, A);
     return cudaGetLastError();
 }
 

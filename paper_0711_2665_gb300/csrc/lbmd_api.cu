@@ -47,6 +47,7 @@ struct lbmd_handle {
     cudaStream_t st = nullptr, aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int by = 8, zc = 8;
+    bool overlap = true;  // particle kernel concurrent with the lattice pass
     int graph_steps = 0;
     cudaGraphExec_t gexec = nullptr;
     void *graph_A = nullptr;  // population buffer that was "A" when the graph was captured
@@ -191,19 +192,22 @@ struct ProfScope {
     }
 };
 
-// one coupled step: particles (aux stream) || stream-collide (main), then source
+// One coupled step: the gather runs alone (its latency-bound loads would queue
+// behind the lattice pass's traffic), then the particle kernel (aux stream)
+// runs concurrently with the stream-collide kernel (main), then the source.
 lbmd_status enqueue_step(lbmd_handle *h) {
+    if (h->total_beads > 0) {
+        ProfScope ps(h, K_GATHER, h->st);
+        CK(launch_gather(h->S, h->popA, h->st));
+    }
     CK(cudaEventRecord(h->ev_fork, h->st));
     CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
-    if (h->total_beads > 0) {
-        ProfScope ps(h, K_GATHER, h->aux);
-        CK(launch_gather(h->S, h->popA, h->aux));
-    }
     {
         ProfScope ps(h, K_PARTICLES, h->aux);
         CK(launch_particles(h->S, h->popA, h->aux));
     }
     CK(cudaEventRecord(h->ev_join, h->aux));
+    if (!h->overlap) CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
     {
         ProfScope ps(h, K_STREAM_COLLIDE, h->st);
         CK(launch_stream_collide(h->S, h->popA, h->popB, h->by, h->zc, true, h->st));
@@ -489,7 +493,7 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
     CKI(launch_init_rest(S, h->popA, h->st));
     CKI(cudaStreamSynchronize(h->st));
     // the particle kernel needs its shared-memory size granted once
-    if (particle_smem_bytes(particle_threads(S)) > 227 * 1024) { fail(h, LBMD_ERR_CAPACITY, "too many beads per realization for shared memory"); return bail(LBMD_ERR_CAPACITY); }
+    if (md_shape(S).smem > 200 * 1024) { fail(h, LBMD_ERR_CAPACITY, "too many beads per realization for shared memory"); return bail(LBMD_ERR_CAPACITY); }
     lbmd_status s = lbmd_set_beads(h, r_init, nullptr);
     if (s != LBMD_OK) return bail(s);
     *out = h;
@@ -704,6 +708,41 @@ lbmd_status lbmd_set_tiles(lbmd_handle *h, int32_t by, int32_t zc) {
     return LBMD_OK;
 }
 
+lbmd_status lbmd_set_md_shape(lbmd_handle *h, int32_t T, int32_t C) {
+    if (!h || !(T == 0 || T == 1 || T == 2 || T == 4 || T == 8) || C < 0 || C > 8) return LBMD_ERR_INVALID_ARG;
+    Sim trial = h->S;
+    trial.md_T = T;
+    trial.md_C = C;
+    const MdShape m = md_shape(trial);
+    if (m.threads > 512 || m.C < 1 || m.C > 8 || m.smem > 200 * 1024)
+        return fail(h, LBMD_ERR_INVALID_ARG, "particle-kernel shape needs more than 512 threads per block");
+    if (T != h->S.md_T || C != h->S.md_C) drop_graph(h);
+    h->S.md_T = T;
+    h->S.md_C = C;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_set_overlap(lbmd_handle *h, int32_t overlap) {
+    if (!h || overlap < 0 || overlap > 1) return LBMD_ERR_INVALID_ARG;
+    if ((overlap != 0) != h->overlap) drop_graph(h);
+    h->overlap = overlap != 0;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_get_overlap(lbmd_handle *h, int32_t *overlap) {
+    if (!h || !overlap) return LBMD_ERR_INVALID_ARG;
+    *overlap = h->overlap ? 1 : 0;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_get_md_shape(lbmd_handle *h, int32_t *T, int32_t *C) {
+    if (!h || !T || !C) return LBMD_ERR_INVALID_ARG;
+    const MdShape m = md_shape(h->S);
+    *T = m.T;
+    *C = m.C;
+    return LBMD_OK;
+}
+
 lbmd_status lbmd_get_tiles(lbmd_handle *h, int32_t *by, int32_t *zc) {
     if (!h || !by || !zc) return LBMD_ERR_INVALID_ARG;
     *by = h->by;
@@ -760,8 +799,9 @@ lbmd_status lbmd_kernel_times(lbmd_handle *h, lbmd_kernel_time *out, int32_t max
     if (!h || !n_entries || (max_entries > 0 && !out)) return LBMD_ERR_INVALID_ARG;
     lbmd_status s = resolve_profile(h);
     if (s != LBMD_OK) return s;
-    static const char *PNAMES[PHASES] = {"particles.gather", "particles.lists", "particles.md", "particles.spread"};
-    unsigned long long cyc[PHASES] = {0, 0, 0, 0};
+    static const char *PNAMES[PHASES - 1] = {"particles.load", "particles.lists", "particles.md", "particles.spread",
+                                             "particles.rebuilds"};
+    unsigned long long cyc[PHASES] = {0, 0, 0, 0, 0, 0};
     CK(cudaMemcpyAsync(cyc, h->dbuf + h->L.phase, sizeof(cyc), cudaMemcpyDeviceToHost, h->st));
     CK(cudaStreamSynchronize(h->st));
     int dev = 0, khz = 0;
@@ -777,8 +817,11 @@ lbmd_status lbmd_kernel_times(lbmd_handle *h, lbmd_kernel_time *out, int32_t max
         ++n;
     };
     for (int k = 0; k < K_COUNT; ++k) put(KNAMES[k], h->prof_n[k], h->prof_ms[k]);
-    for (int k = 0; k < PHASES; ++k)
-        put(PNAMES[k], h->prof_n[K_PARTICLES], khz > 0 ? (double)cyc[k] / (double)khz : 0.0);
+    // phases 0..4 are SM cycles; slot 5 counts the list rebuilds (reported as
+    // the "launches" of particles.rebuilds)
+    for (int k = 0; k < PHASES - 1; ++k)
+        put(PNAMES[k], k == 4 ? (long long)cyc[5] : h->prof_n[K_PARTICLES],
+            khz > 0 ? (double)cyc[k] / (double)khz : 0.0);
     *n_entries = n;
     return LBMD_OK;
 }

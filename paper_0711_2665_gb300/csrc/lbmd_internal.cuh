@@ -96,7 +96,8 @@ struct Sim {
     float wall_eps, wall_sig2, wall_rc2;
     float E, gamma, kT;
     int M, Mb;
-    float skin_half2;        // (skin/2)^2: displacement that forces a list rebuild
+    int md_T, md_C;          // particle-kernel shape override (0 = automatic)
+    float skin_half2;       // (skin/2)^2: displacement that forces a list rebuild
     float rl2, rlw2, rlw;    // bead and wall list radii (squared) and wall radius
     int ncell[3];            // cells per axis for the neighbour hash (>= 3 to use it)
     float cell_per_site[3];  // ncell / n per axis
@@ -120,7 +121,8 @@ struct Sim {
     unsigned long long *phase;  // [PHASES] SM cycles per particle-kernel phase, or null
 };
 
-constexpr int PHASES = 4;   // gather, lists, md, spread
+// load, lists, md, spread, rebuild cycles inside md, number of rebuilds
+constexpr int PHASES = 6;
 
 // ---------------------------------------------------------------------------
 // population storage
@@ -258,8 +260,13 @@ cudaError_t launch_init_rest(const Sim &S, void *A, cudaStream_t st);
 cudaError_t launch_feq_to_staging(const Sim &S, float *staging, cudaStream_t st);
 cudaError_t launch_pull_to_staging(const Sim &S, const void *A, float *staging, bool dev, cudaStream_t st);
 cudaError_t launch_push_from_staging(const Sim &S, const float *staging, void *A, bool dev, cudaStream_t st);
-size_t particle_smem_bytes(int threads);
-int particle_threads(const Sim &S);
+// launch shape of the particle kernel: T threads per bead, clusters of C
+// blocks per realization, Nc beads per block
+struct MdShape {
+    int T, C, Nc, threads;
+    size_t smem;
+};
+MdShape md_shape(const Sim &S);
 cudaError_t launch_gather(const Sim &S, const void *A, cudaStream_t st);
 cudaError_t launch_particles(const Sim &S, const void *A, cudaStream_t st);
 cudaError_t launch_bead_observables(const Sim &S, const void *A, cudaStream_t st);

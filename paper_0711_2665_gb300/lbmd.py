@@ -109,6 +109,10 @@ def lib():
         "lbmd_kernel_times": [vp, P(KernelTime), i32, P(i32)],
         "lbmd_launch_count": [vp, P(i64)],
         "lbmd_population_sums_static": [vp, vp, i32, i32, i32, vp, vp],
+        "lbmd_set_md_shape": [vp, i32, i32],
+        "lbmd_set_overlap": [vp, i32],
+        "lbmd_get_overlap": [vp, P(i32)],
+        "lbmd_get_md_shape": [vp, P(i32), P(i32)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -230,6 +234,18 @@ class Simulation:
         by, zc = ctypes.c_int32(), ctypes.c_int32()
         self._check(self._lib.lbmd_get_tiles(self._h, ctypes.byref(by), ctypes.byref(zc)), "lbmd_get_tiles")
         return by.value, zc.value
+
+    def set_md_shape(self, threads_per_bead: int = 0, blocks_per_chain: int = 0):
+        self._check(self._lib.lbmd_set_md_shape(self._h, int(threads_per_bead), int(blocks_per_chain)),
+                    "lbmd_set_md_shape")
+
+    def set_overlap(self, overlap: bool):
+        self._check(self._lib.lbmd_set_overlap(self._h, int(bool(overlap))), "lbmd_set_overlap")
+
+    def md_shape(self):
+        t, c = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._lib.lbmd_get_md_shape(self._h, ctypes.byref(t), ctypes.byref(c)), "lbmd_get_md_shape")
+        return t.value, c.value
 
     def autotune(self, reps: int = 5):
         by, zc = ctypes.c_int32(), ctypes.c_int32()
