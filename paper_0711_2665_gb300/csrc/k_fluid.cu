@@ -33,59 +33,57 @@ __device__ __forceinline__ void block_partial4(double a, double b, double c, dou
     }
 }
 
-// The last block to finish sums the block partials of every realization in a
-// fixed order (deterministic) and stores mass = n_fluid + sum(rho - 1) and the
-// fluid momentum.  MODE 1 writes the step's diagnostics row, MODE 2 the
-// observables.  No block ever waits for another.
+// Each realization has its own completion counter: the last of its bpr blocks
+// to finish sums that realization's block partials in a fixed order
+// (deterministic) and stores mass = n_fluid + sum(rho - 1) and the fluid
+// momentum.  MODE 1 writes the step's diagnostics row, MODE 2 the
+// observables.  No block ever waits for another, and the realizations of an
+// ensemble are finalised in parallel by different blocks.
 template <int MODE>
-__device__ void finalize_fluid_sums(const Sim &S, unsigned int *done, long long step, int bpr) {
+__device__ void finalize_fluid_sums(const Sim &S, unsigned int *done, long long step, int bpr, int rr) {
     __shared__ int am_last;
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     const int nthreads = blockDim.x * blockDim.y;
-    const unsigned int nblocks = gridDim.x * gridDim.y * gridDim.z;
     __threadfence();
     __syncthreads();
-    if (tid == 0) am_last = (atomicAdd(done, 1u) == nblocks - 1u);
+    if (tid == 0) am_last = (atomicAdd(done, 1u) == (unsigned int)bpr - 1u);
     __syncthreads();
     if (!am_last) return;
     __threadfence();
     __shared__ double red[16][4];
     const int lane = tid & 31, warp = tid >> 5, nw = (nthreads + 31) >> 5;
-    for (int rr = 0; rr < S.n_real; ++rr) {
-        double t[4] = {0, 0, 0, 0};
-        for (int b = tid; b < bpr; b += nthreads) {
-            const double *p = S.partial + 4 * ((size_t)rr * bpr + b);
+    double t[4] = {0, 0, 0, 0};
+    for (int b = tid; b < bpr; b += nthreads) {
+        const double *p = S.partial + 4 * ((size_t)rr * bpr + b);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) t[k] += __ldcg(p + k);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) t[k] += __shfl_down_sync(0xffffffffu, t[k], o);
-        if (lane == 0)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) red[warp][k] = t[k];
-        __syncthreads();
-        if (tid == 0) {
-            double u[4] = {0, 0, 0, 0};
-            for (int w = 0; w < nw; ++w)
-                for (int k = 0; k < 4; ++k) u[k] += red[w][k];
-            const double mass = S.n_fluid + u[0];
-            if (!isfinite(mass) || !isfinite(u[1]) || !isfinite(u[2]) || !isfinite(u[3]))
-                atomicOr(&S.ctrl->status, ST_NONFINITE);
-            if (MODE == 1) {
-                lbmd_diag *row = S.ring + (size_t)rr * LBMD_DIAG_RING + (step % LBMD_DIAG_RING);
-                row->mass = mass;
-                row->p_fluid[0] = u[1]; row->p_fluid[1] = u[2]; row->p_fluid[2] = u[3];
-            } else {
-                lbmd_obs *o = S.obs + rr;
-                o->mass = mass;
-                o->p_fluid[0] = u[1]; o->p_fluid[1] = u[2]; o->p_fluid[2] = u[3];
-            }
-        }
-        __syncthreads();
+        for (int k = 0; k < 4; ++k) t[k] += __ldcg(p + k);
     }
-    if (tid == 0) *done = 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t[k] += __shfl_down_sync(0xffffffffu, t[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) red[warp][k] = t[k];
+    __syncthreads();
+    if (tid == 0) {
+        double u[4] = {0, 0, 0, 0};
+        for (int w = 0; w < nw; ++w)
+            for (int k = 0; k < 4; ++k) u[k] += red[w][k];
+        const double mass = S.n_fluid + u[0];
+        if (!isfinite(mass) || !isfinite(u[1]) || !isfinite(u[2]) || !isfinite(u[3]))
+            atomicOr(&S.ctrl->status, ST_NONFINITE);
+        if (MODE == 1) {
+            lbmd_diag *row = S.ring + (size_t)rr * LBMD_DIAG_RING + (step % LBMD_DIAG_RING);
+            row->mass = mass;
+            row->p_fluid[0] = u[1]; row->p_fluid[1] = u[2]; row->p_fluid[2] = u[3];
+        } else {
+            lbmd_obs *o = S.obs + rr;
+            o->mass = mass;
+            o->p_fluid[0] = u[1]; o->p_fluid[1] = u[2]; o->p_fluid[2] = u[3];
+        }
+        *done = 0u;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -108,7 +106,7 @@ __global__ void __launch_bounds__(512) k_stream_collide(const Sim S, const void 
     const int r = blockIdx.z / nzb;
     const int z0 = (blockIdx.z - r * nzb) * zc;
     const int nx = S.nx, ny = S.ny, nz = S.nz;
-    const uint32_t ns = (uint32_t)S.ns;
+    const uint32_t ns = (uint32_t)S.ps;  // population stride (padded site count)
     const T *__restrict__ A = reinterpret_cast<const T *>(Av) + (size_t)r * Q * ns;
     T *__restrict__ B = reinterpret_cast<T *>(Bv) + (size_t)r * Q * ns;
     long long step = 0;
@@ -190,8 +188,8 @@ __global__ void __launch_bounds__(512) k_stream_collide(const Sim S, const void 
         const int bpr = gridDim.x * gridDim.y * nzb;
         const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
         block_partial4((double)am, (double)ax, (double)ay, (double)az, S.partial + 4 * (size_t)blk);
-        if (MODE == 1) finalize_fluid_sums<1>(S, &S.ctrl->sc_done, step, bpr);
-        else finalize_fluid_sums<2>(S, &S.ctrl->obs_done, 0, bpr);
+        if (MODE == 1) finalize_fluid_sums<1>(S, S.rdone + r, step, bpr, r);
+        else finalize_fluid_sums<2>(S, S.rdone + S.n_real + r, 0, bpr, r);
     }
 }
 
@@ -269,11 +267,11 @@ __global__ void __launch_bounds__(256) k_source(const Sim S, void *__restrict__ 
             const float G1 = (float)(long long)Gr[ns] * FIX_INV_SCALE_F;
             const float G2 = (float)(long long)Gr[2 * ns] * FIX_INV_SCALE_F;
             Gr[0] = 0ull; Gr[ns] = 0ull; Gr[2 * ns] = 0ull;
-            T *B = reinterpret_cast<T *>(Bv) + (size_t)r * Q * ns;
+            T *B = reinterpret_cast<T *>(Bv) + (size_t)r * Q * S.ps;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const float src = 3.0f * wq(i) * ((float)cx(i) * G0 + (float)cy(i) * G1 + (float)cz(i) * G2);
-                const uint32_t idx = (uint32_t)i * (uint32_t)ns + (uint32_t)s;
+                const uint32_t idx = (uint32_t)i * (uint32_t)S.ps + (uint32_t)s;
                 store_dev(B, idx, load_dev_cg(B, idx) + src);
             }
         }
@@ -309,9 +307,9 @@ __global__ void k_init_rest(const Sim S, void *Av) {
     const size_t total = ns * S.n_real;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
         const size_t r = t / ns, s = t - r * ns;
-        T *A = reinterpret_cast<T *>(Av) + r * Q * ns;
+        T *A = reinterpret_cast<T *>(Av) + r * Q * (size_t)S.ps;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) store_dev(A, (uint32_t)(i * ns + s), 0.0f);
+        for (int i = 0; i < Q; ++i) store_dev(A, (uint32_t)(i * (size_t)S.ps + s), 0.0f);
     }
 }
 
@@ -356,7 +354,7 @@ __global__ void k_pull_to_staging(const Sim S, const void *Av, float *stg) {
     const size_t total = ns * S.n_real;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
         const size_t r = t / ns, s = t - r * ns;
-        const T *A = reinterpret_cast<const T *>(Av) + r * Q * ns;
+        const T *A = reinterpret_cast<const T *>(Av) + r * Q * (size_t)S.ps;
         float *f = stg + r * Q * ns + s;
         const uint32_t lm = S.link[s];
         const int x = (int)(s % S.nx), y = (int)((s / S.nx) % S.ny), z = (int)(s / ((size_t)S.nx * S.ny));
@@ -365,9 +363,9 @@ __global__ void k_pull_to_staging(const Sim S, const void *Av, float *stg) {
             float v = 0.0f;
             if (!(lm & SOLID_BIT)) {
                 uint32_t idx;
-                if ((lm >> i) & 1u) idx = (uint32_t)(opp(i) * ns + s);
+                if ((lm >> i) & 1u) idx = (uint32_t)(opp(i) * (size_t)S.ps + s);
                 else
-                    idx = (uint32_t)(i * ns + wrapi(x - cx(i), S.nx) +
+                    idx = (uint32_t)(i * (size_t)S.ps + wrapi(x - cx(i), S.nx) +
                                      (size_t)S.nx * (wrapi(y - cy(i), S.ny) + (size_t)S.ny * wrapi(z - cz(i), S.nz)));
                 const float h = load_dev(A, idx);
                 v = DEV ? h : (float)(wq_exact(i) + (double)h);
@@ -396,7 +394,7 @@ __global__ void k_push_from_staging(const Sim S, const float *stg, void *Av) {
     const size_t total = ns * S.n_real;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
         const size_t r = t / ns, s = t - r * ns;
-        T *A = reinterpret_cast<T *>(Av) + r * Q * ns;
+        T *A = reinterpret_cast<T *>(Av) + r * Q * (size_t)S.ps;
         const float *f = stg + r * Q * ns;
         const uint32_t lm = S.link[s];
         const int x = (int)(s % S.nx), y = (int)((s / S.nx) % S.ny), z = (int)(s / ((size_t)S.nx * S.ny));
@@ -414,7 +412,7 @@ __global__ void k_push_from_staging(const Sim S, const float *stg, void *Av) {
                 const float v = f[k * ns + src];
                 h = DEV ? v : (float)((double)v - wq_exact(i));
             }
-            store_dev(A, (uint32_t)(i * ns + s), h);
+            store_dev(A, (uint32_t)(i * (size_t)S.ps + s), h);
         }
     }
 }

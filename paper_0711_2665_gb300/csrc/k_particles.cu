@@ -89,7 +89,7 @@ __device__ __forceinline__ float3 gather_warp(const Sim &S, const T *__restrict_
     int xi, yi, zi;
     float w;
     corner_of(S, xw, yw, zw, c, xi, yi, zi, node, w);
-    const uint32_t ns = (uint32_t)S.ns;
+    const uint32_t ns = (uint32_t)S.ps;  // population stride
     const uint32_t lm = __ldg(S.link + node);
     float hp[5], hb[5];
 #pragma unroll
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(256) k_gather(const Sim S, const void *__restr
     const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // global bead index
     if (g >= S.total_beads) return;
     const int r = S.bead_real[g];
-    const T *A = reinterpret_cast<const T *>(Av) + (size_t)r * Q * S.ns;
+    const T *A = reinterpret_cast<const T *>(Av) + (size_t)r * Q * S.ps;
     const float4 qh = S.r_hi[g], ql = S.r_lo[g];
     int node;
     float W;
@@ -741,7 +741,7 @@ __global__ void __launch_bounds__(1024) k_bead_observables(const Sim S, const vo
     const int N = S.bead_off[r + 1] - off;
     const int p = threadIdx.x;
     const bool own = p < N;
-    const T *A = reinterpret_cast<const T *>(Av) + (size_t)r * Q * S.ns;
+    const T *A = reinterpret_cast<const T *>(Av) + (size_t)r * Q * S.ps;
     const float fnx = (float)S.nx, fny = (float)S.ny, fnz = (float)S.nz;
     float4 mh = make_float4(0.f, 0.f, 0.f, 0.f), ml = mh, vv = mh;
     if (own) {

@@ -22,7 +22,7 @@ constexpr double SKIN = 0.8;  // Verlet-list skin (lattice units)
 
 struct Layout {
     size_t popA, popB, staging, link, wallmask, tileflag, solid, G, stamp;
-    size_t r_hi, r_lo, v, up, J, pair_node, pair_w, bead_real, bead_off, partial, ring, obs, ctrl, phase, total;
+    size_t r_hi, r_lo, v, up, J, pair_node, pair_w, bead_real, bead_off, partial, ring, obs, ctrl, rdone, phase, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -84,7 +84,7 @@ bool config_ok(const lbmd_config *c, const int32_t *off, std::string &why) {
     if (c->nx < 1 || c->ny < 1 || c->nz < 1) { why = "lattice dimensions must be >= 1"; return false; }
     if (c->nx > 4096 || c->ny > 1024 || c->nz > 1024) { why = "lattice limited to 4096 x 1024 x 1024"; return false; }
     const double ns = (double)c->nx * c->ny * c->nz;
-    if (ns * LBMD_Q >= 2147483647.0) { why = "19 * sites must stay below 2^31 per realization"; return false; }
+    if ((ns + 128.0) * LBMD_Q >= 2147483647.0) { why = "19 * sites must stay below 2^31 per realization"; return false; }
     if (c->n_real < 1 || (double)c->n_real * ns >= 2147483647.0) { why = "n_real must be >= 1 and n_real * sites < 2^31"; return false; }
     if (!(c->tau > 0.5)) { why = "tau must be > 1/2"; return false; }
     if (c->md_outer < 1 || c->md_inner < 1) { why = "md_outer and md_inner must be >= 1"; return false; }
@@ -108,11 +108,16 @@ bool config_ok(const lbmd_config *c, const int32_t *off, std::string &why) {
     return true;
 }
 
+// Stride between the 19 population arrays of a lattice: the site count
+// rounded up to 64, so that every array starts on a 128-byte boundary in
+// both precisions.
+size_t pop_stride(size_t ns) { return (ns + 63) / 64 * 64; }
+
 Layout layout_of(const lbmd_config *c, int total_beads) {
     Layout L;
     const size_t ns = (size_t)c->nx * c->ny * c->nz;
     const size_t esz = c->precision == LBMD_FP16DEV ? 2 : 4;
-    const size_t npop = (size_t)c->n_real * LBMD_Q * ns;
+    const size_t npop = (size_t)c->n_real * LBMD_Q * pop_stride(ns);
     const size_t nxt = (c->nx + 31) / 32;
     const size_t max_blocks = nxt * c->ny * c->nz * c->n_real;  // finest tile shape (by = zc = 1)
     const size_t nb = (size_t)std::max(total_beads, 1);
@@ -120,7 +125,7 @@ Layout layout_of(const lbmd_config *c, int total_beads) {
     auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
     L.popA = take(npop * esz);
     L.popB = take(npop * esz);
-    L.staging = take(npop * 4);
+    L.staging = take((size_t)c->n_real * LBMD_Q * ns * 4);
     L.link = take(ns * 4);
     L.wallmask = take(ns * 8);
     L.tileflag = take(nxt * c->ny * c->nz);
@@ -140,6 +145,7 @@ Layout layout_of(const lbmd_config *c, int total_beads) {
     L.ring = take((size_t)c->n_real * LBMD_DIAG_RING * sizeof(lbmd_diag));
     L.obs = take((size_t)c->n_real * sizeof(lbmd_obs));
     L.ctrl = take(sizeof(Ctrl));
+    L.rdone = take((size_t)c->n_real * 2 * sizeof(unsigned int));
     L.phase = take(PHASES * sizeof(unsigned long long));
     L.total = o;
     return L;
@@ -402,6 +408,7 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
     memset(&S, 0, sizeof(S));
     S.nx = cfg->nx; S.ny = cfg->ny; S.nz = cfg->nz;
     S.ns = cfg->nx * cfg->ny * cfg->nz;
+    S.ps = (int)pop_stride((size_t)S.ns);
     S.nxt = (cfg->nx + 31) / 32;
     S.inx = 1.0f / (float)cfg->nx;
     S.iny = 1.0f / (float)cfg->ny;
@@ -466,6 +473,7 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
     S.ring = (lbmd_diag *)(b + L.ring);
     S.obs = (lbmd_obs *)(b + L.obs);
     S.ctrl = (Ctrl *)(b + L.ctrl);
+    S.rdone = (unsigned int *)(b + L.rdone);
     S.phase = nullptr;
 
 #define CKI(call)                                                           \
@@ -488,6 +496,7 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
     CKI(cudaMemsetAsync(b + L.ring, 0, (size_t)cfg->n_real * LBMD_DIAG_RING * sizeof(lbmd_diag), h->st));
     CKI(cudaMemsetAsync(b + L.obs, 0, (size_t)cfg->n_real * sizeof(lbmd_obs), h->st));
     CKI(cudaMemsetAsync(b + L.ctrl, 0, sizeof(Ctrl), h->st));
+    CKI(cudaMemsetAsync(b + L.rdone, 0, (size_t)cfg->n_real * 2 * sizeof(unsigned int), h->st));
     CKI(cudaMemsetAsync(b + L.popB, 0, L.staging - L.popB, h->st));
     CKI(cudaMemsetAsync(b + L.up, 0, (size_t)std::max(h->total_beads, 1) * 32, h->st));
     CKI(launch_init_rest(S, h->popA, h->st));

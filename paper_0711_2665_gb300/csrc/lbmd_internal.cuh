@@ -2,7 +2,7 @@
 // coupled LB-MD library (not part of the public ABI).
 //
 // Data layout in HBM (one device buffer owned by the caller):
-//   populations  A, B      [n_real][19][ns]  fp32, or fp16 deviations (f - w) * 2^12
+//   populations  A, B      [n_real][19][ps]  fp32, or fp16 deviations (f - w) * 2^12
 //                          A holds the post-collision populations f* of the last
 //                          step; the next step pulls from A and writes B.
 //   staging                [n_real][19][ns]  fp32 host-transfer area
@@ -73,9 +73,7 @@ constexpr int ST_TIMEOUT = 4;
 struct Ctrl {
     long long step;          // LB step counter = Philox counter
     int status;              // ST_* bits
-    unsigned int sc_done;    // blocks finished (stream-collide diag finalize)
     unsigned int src_done;   // blocks finished (source kernel; last one advances step)
-    unsigned int obs_done;   // blocks finished (observables pass)
     int pad[2];
 };
 
@@ -83,6 +81,7 @@ struct Ctrl {
 struct Sim {
     // lattice
     int nx, ny, nz, ns, nxt, n_real;
+    int ps;  // stride between population arrays: ns rounded up to 64
     float inx, iny, inz;     // 1/nx, 1/ny, 1/nz
     int precision;
     float omega;
@@ -118,6 +117,7 @@ struct Sim {
     lbmd_diag *ring;         // [n_real][LBMD_DIAG_RING]
     lbmd_obs *obs;           // [n_real]
     Ctrl *ctrl;
+    unsigned int *rdone;        // [2][n_real] blocks finished per realization (diag pass, observables pass)
     unsigned long long *phase;  // [PHASES] SM cycles per particle-kernel phase, or null
 };
 
