@@ -84,6 +84,11 @@ def lib():
         _lib.orc_feq.argtypes = [ctypes.c_double, d, d]
         _lib.orc_gauss3_batch.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                           ctypes.c_int64, ctypes.c_uint32, d]
+        _lib.orc_adjoint.restype = ctypes.c_int
+        _lib.orc_adjoint.argtypes = [ctypes.POINTER(_Params), P, P, P, P, ctypes.c_int64, ctypes.c_int,
+                                     P, P, P, P]
+        _lib.orc_step_adjoint.argtypes = [P, P, P, P, P]
+        _lib.orc_event_counts.argtypes = [P, P]
     return _lib
 
 
@@ -143,6 +148,47 @@ def gauss3_batch(seed: int, realization: int, n_beads: int, step: int, substep: 
     z = np.zeros(3 * n_beads)
     lib().orc_gauss3_batch(seed, realization, n_beads, step, substep, _dp(z))
     return z.reshape(n_beads, 3)
+
+
+def _params_struct(params: dict) -> "_Params":
+    p = dict(DEFAULTS)
+    p.update(params)
+    st = _Params()
+    for name, _ in _Params._fields_:
+        if name == "body_force":
+            st.body_force = (ctypes.c_double * 3)(*[float(v) for v in p["body_force"]])
+        else:
+            setattr(st, name, p[name])
+    return st
+
+
+def _vp(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def adjoint(params: dict, solid, r0, K: int, v0=None, f0=None, step0: int = 0, want_df0: bool = False) -> dict:
+    """Reverse-mode gradient of L = mean x(K) - mean x(0) over K coupled steps
+    (all states kept in memory): {'loss', 'dgamma', 'dE', 'dr0', 'dv0'[, 'df0']}."""
+    st = _params_struct(params)
+    N = int(st.n_beads)
+    ns = int(st.nx) * int(st.ny) * int(st.nz)
+    sol = np.ascontiguousarray(solid, dtype=np.uint8).reshape(-1) if solid is not None else None
+    rr = _f64(r0).reshape(-1)
+    vv = _f64(v0).reshape(-1) if v0 is not None else None
+    ff = _f64(f0).reshape(-1) if f0 is not None else None
+    out = np.zeros(3)
+    dr0 = np.zeros(3 * N)
+    dv0 = np.zeros(3 * N)
+    df0 = np.zeros(19 * ns) if want_df0 else None
+    rc = lib().orc_adjoint(ctypes.byref(st), _vp(sol), _vp(ff), _vp(rr), _vp(vv), int(step0), int(K),
+                           _vp(out), _vp(dr0), _vp(dv0), _vp(df0))
+    if rc != 0:
+        raise RuntimeError(f"orc_adjoint failed ({rc})")
+    res = dict(loss=float(out[0]), dgamma=float(out[1]), dE=float(out[2]), dr0=dr0.reshape(N, 3),
+               dv0=dv0.reshape(N, 3))
+    if want_df0:
+        res["df0"] = df0.reshape(19, int(st.nz), int(st.ny), int(st.nx))
+    return res
 
 
 class OracleSim:
@@ -251,6 +297,25 @@ class OracleSim:
         F = np.zeros(3 * self.n_beads + 3)
         lib().orc_field_forces(self._h, _dp(rr), _dp(F))
         return F[:3 * self.n_beads].reshape(-1, 3)
+
+    def event_counts(self) -> tuple:
+        """(half kicks inside the pore channel, sum of the beads' cell indices over steps)"""
+        out = np.zeros(2)
+        lib().orc_event_counts(self._h, _vp(out))
+        return float(out[0]), float(out[1])
+
+    def step_adjoint(self, lam_f, lam_r, lam_v):
+        """Adjoint of one step at the current state; returns (lam_f, lam_r, lam_v,
+        dpar) for the state before the step, and advances the state by one step."""
+        lf = _f64(lam_f).reshape(-1).copy()
+        lr = np.zeros(3 * self.n_beads + 3)
+        lv = np.zeros(3 * self.n_beads + 3)
+        lr[:3 * self.n_beads] = _f64(lam_r).reshape(-1)
+        lv[:3 * self.n_beads] = _f64(lam_v).reshape(-1)
+        dpar = np.zeros(2)
+        lib().orc_step_adjoint(self._h, _vp(lf), _vp(lr), _vp(lv), _vp(dpar))
+        return (lf.reshape(19, self.nz, self.ny, self.nx), lr[:3 * self.n_beads].reshape(-1, 3),
+                lv[:3 * self.n_beads].reshape(-1, 3), dpar)
 
     def observables(self) -> dict:
         out = np.zeros(NOBS)

@@ -159,6 +159,10 @@ struct orc_sim {
     double *r, *v;    /* [N][3] unwrapped positions, velocities */
     double *up, *J;   /* [N][3] last step's interpolated fluid velocity and impulse */
     int64_t step;
+    /* events that make the loss non-differentiable, for finite-difference
+     * checks: half kicks taken inside the pore channel, and the sum over steps
+     * and beads of the index of the lattice cell holding the bead */
+    double field_kicks, cell_sum;
 };
 
 static int wrap_index(int i, int n)
@@ -494,6 +498,7 @@ static void slow_half_kick(orc_sim *s, const double *xi, double h)
     double *Fe = (double *)malloc(sizeof(double) * 3 * N);
     orc_field_forces(s, s->r, Fe);
     for (int i = 0; i < N; i++) {
+        if (in_pore_channel(s, s->r + 3 * i)) s->field_kicks += 1.0;
         for (int a = 0; a < 3; a++) {
             double drag = p->gamma * (s->up[3 * i + a] - s->v[3 * i + a]); /* Eq. 12 */
             double fluid = drag + xi[3 * i + a];                            /* Eqs. 12 + 13 */
@@ -504,7 +509,22 @@ static void slow_half_kick(orc_sim *s, const double *xi, double h)
     free(Fe);
 }
 
-static void md_cycle(orc_sim *s)
+/* What one MD cycle passed through, kept for the adjoint sweep. */
+typedef struct {
+    double *rt; /* [M*Mb + 1][3N] positions at the boundaries of the inner sub-steps */
+    double *vk; /* [2M][3N] velocity just before each half kick */
+    int *ch;    /* [2M][N] 1 where the bead sat in the pore channel at that kick */
+    double *xi; /* [M][3N] noise of each MD step */
+} md_record;
+
+static void record_kick(const orc_sim *s, md_record *rec, int k)
+{
+    int N = s->p.n_beads;
+    memcpy(rec->vk + (size_t)k * 3 * N, s->v, sizeof(double) * 3 * N);
+    for (int i = 0; i < N; i++) rec->ch[(size_t)k * N + i] = in_pore_channel(s, s->r + 3 * i);
+}
+
+static void md_cycle(orc_sim *s, md_record *rec)
 {
     const orc_params *p = &s->p;
     int N = p->n_beads;
@@ -516,20 +536,27 @@ static void md_cycle(orc_sim *s)
      * length dt, each component has variance 2 gamma kT / dt. */
     double amp = (p->kT > 0.0) ? sqrt(2.0 * p->gamma * p->kT / dt) : 0.0;
     memset(s->J, 0, sizeof(double) * 3 * N);
+    if (rec) memcpy(rec->rt, s->r, sizeof(double) * 3 * N);
     for (int sub = 0; sub < p->md_outer; sub++) {
         for (int i = 0; i < N; i++) {
             double z[3] = {0, 0, 0};
             if (amp > 0.0) orc_gauss3(p->seed, p->realization, (uint32_t)i, s->step, (uint32_t)sub, z);
             for (int a = 0; a < 3; a++) xi[3 * i + a] = amp * z[a];
         }
+        if (rec) {
+            memcpy(rec->xi + (size_t)sub * 3 * N, xi, sizeof(double) * 3 * N);
+            record_kick(s, rec, 2 * sub);
+        }
         slow_half_kick(s, xi, 0.5 * dt);
         for (int b = 0; b < p->md_inner; b++) {
             orc_fast_forces(s, s->r, F);
             for (int k = 0; k < 3 * N; k++) s->v[k] += 0.5 * dtb * F[k];
             for (int k = 0; k < 3 * N; k++) s->r[k] += dtb * s->v[k];
+            if (rec) memcpy(rec->rt + ((size_t)sub * p->md_inner + b + 1) * 3 * N, s->r, sizeof(double) * 3 * N);
             orc_fast_forces(s, s->r, F);
             for (int k = 0; k < 3 * N; k++) s->v[k] += 0.5 * dtb * F[k];
         }
+        if (rec) record_kick(s, rec, 2 * sub + 1);
         slow_half_kick(s, xi, 0.5 * dt);
     }
     free(xi);
@@ -551,10 +578,16 @@ static void one_step(orc_sim *s)
     /* 2. fluid velocity at the beads, frozen for the MD cycle */
     double *r_start = (double *)malloc(sizeof(double) * 3 * (N + 1));
     memcpy(r_start, s->r, sizeof(double) * 3 * N);
-    for (int i = 0; i < N; i++) gather_velocity(s, s->r + 3 * i, s->up + 3 * i);
+    for (int i = 0; i < N; i++) {
+        gather_velocity(s, s->r + 3 * i, s->up + 3 * i);
+        int nodes[8];
+        double w[8];
+        orc_interp_weights(s, s->r + 3 * i, nodes, w);
+        s->cell_sum += nodes[0];
+    }
 
     /* 3. MD cycle; J_i = momentum the fluid gave bead i */
-    if (N > 0) md_cycle(s);
+    if (N > 0) md_cycle(s, NULL);
 
     /* 4. reaction: G(x) = - sum_i W(x - r_i) J_i, with the weights of step 2 */
     memset(s->G, 0, sizeof(double) * 3 * ns);
@@ -668,4 +701,346 @@ void orc_observables(const orc_sim *s, double *out)
     out[14] = radius_of_gyration(s->r, trans, N);
     out[15] = (double)s->step;
     free(rho); free(u); free(Fe); free(trans); free(untrans);
+}
+
+void orc_event_counts(const orc_sim *s, double *out)
+{
+    out[0] = s->field_kicks;
+    out[1] = s->cell_sum;
+}
+
+/* ======================================================================== */
+/* Discrete adjoint (reverse mode) of the coupled step, in FP64.             */
+/*                                                                          */
+/* The step above maps (f^n, r^n, v^n) to (f^{n+1}, r^{n+1}, v^{n+1}) with   */
+/* the parameters gamma (friction, and the noise amplitude sqrt(2 gamma kT / */
+/* dt)) and E (pore field).  Given the adjoints lam_f, lam_r, lam_v of the    */
+/* outputs, the adjoint step returns those of the inputs and adds the       */
+/* parameter sensitivities, walking the forward stages in reverse:          */
+/*   6' streaming with bounce-back (a permutation: its transpose)           */
+/*   5' collision + source, through f_eq(rho(f), u(f)) and S(G)             */
+/*   4' spread G(x) = -sum_p W(x - r_p) J_p (through J_p and the weights)   */
+/*   3' the MD cycle, kick by kick and sub-step by sub-step                  */
+/*   2' the gather u_p = sum_k W_k u(x_k) (through u(f) and the weights)     */
+/* The pore-field indicator is piecewise constant in r, so its derivative   */
+/* is taken as 0 (the loss jumps where a bead crosses the channel boundary  */
+/* at a kick; orc_event_counts lets a finite-difference check spot that).   */
+/* ======================================================================== */
+
+/* Renormalised trilinear weights of orc_interp_weights and their gradient
+ * with respect to the bead position, dW[k][a] = dW_k / dr_a, from the
+ * product form w_k = prod_a (fa or 1 - fa) and the quotient rule for
+ * W_k = m_k w_k / sum_j m_j w_j (m = 1 on fluid corners, 0 on solid). */
+static void weights_and_gradient(const orc_sim *s, const double *r, int *nodes, double *W, double dW[8][3])
+{
+    const orc_params *p = &s->p;
+    double wr[3] = {wrap_coord(r[0], p->nx), wrap_coord(r[1], p->ny), wrap_coord(r[2], p->nz)};
+    int c0[3];
+    double fr[3];
+    for (int a = 0; a < 3; a++) { c0[a] = (int)floor(wr[a]); fr[a] = wr[a] - c0[a]; }
+    double raw[8], draw[8][3], sum = 0.0, dsum[3] = {0, 0, 0};
+    for (int k = 0; k < 8; k++) {
+        int bit[3] = {k & 1, (k >> 1) & 1, (k >> 2) & 1};
+        nodes[k] = site_of(s, c0[0] + bit[0], c0[1] + bit[1], c0[2] + bit[2]);
+        double m = s->solid[nodes[k]] ? 0.0 : 1.0;
+        double fac[3];
+        for (int a = 0; a < 3; a++) fac[a] = bit[a] ? fr[a] : 1.0 - fr[a];
+        raw[k] = m * fac[0] * fac[1] * fac[2];
+        sum += raw[k];
+        for (int a = 0; a < 3; a++) {
+            double d = bit[a] ? 1.0 : -1.0;
+            for (int b = 0; b < 3; b++)
+                if (b != a) d *= fac[b];
+            draw[k][a] = m * d;
+            dsum[a] += draw[k][a];
+        }
+    }
+    for (int k = 0; k < 8; k++) {
+        W[k] = sum > 0.0 ? raw[k] / sum : 0.0;
+        for (int a = 0; a < 3; a++) dW[k][a] = sum > 0.0 ? (draw[k][a] - W[k] * dsum[a]) / sum : 0.0;
+    }
+}
+
+/* d f_eq_i / d f_k at a site, by the chain rule through rho = sum f and
+ * u = sum f c / rho:  d f_eq_i/d rho |_u + sum_a d f_eq_i/d u_a (c_ka - u_a) / rho */
+static double dfeq_df(int i, int k, double rho, const double *u)
+{
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    double cu = CI[i][0] * u[0] + CI[i][1] * u[1] + CI[i][2] * u[2];
+    double w = weight_of(i);
+    double d_rho = w * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+    double acc = d_rho;
+    for (int a = 0; a < 3; a++) {
+        double d_ua = w * rho * (3.0 * CI[i][a] + 9.0 * cu * CI[i][a] - 3.0 * u[a]);
+        acc += d_ua * (CI[k][a] - u[a]) / rho;
+    }
+    return acc;
+}
+
+/* (dF/dr) w for the fast forces, by a central difference of orc_fast_forces
+ * along w (step 1e-6 / max|w|; the forces are smooth between the rare
+ * instants a pair crosses the cut-off). */
+static void force_jacobian_times(const orc_sim *s, const double *r, const double *w, double *out)
+{
+    int n = 3 * s->p.n_beads;
+    double wmax = 0.0;
+    for (int k = 0; k < n; k++) wmax = fmax(wmax, fabs(w[k]));
+    if (wmax == 0.0) {
+        for (int k = 0; k < n; k++) out[k] = 0.0;
+        return;
+    }
+    double eps = 1e-6 / wmax;
+    double *rp = (double *)malloc(sizeof(double) * (n + 3));
+    double *Fp = (double *)malloc(sizeof(double) * (n + 3));
+    double *Fm = (double *)malloc(sizeof(double) * (n + 3));
+    for (int k = 0; k < n; k++) rp[k] = r[k] + eps * w[k];
+    orc_fast_forces(s, rp, Fp);
+    for (int k = 0; k < n; k++) rp[k] = r[k] - eps * w[k];
+    orc_fast_forces(s, rp, Fm);
+    for (int k = 0; k < n; k++) out[k] = (Fp[k] - Fm[k]) / (2.0 * eps);
+    free(rp); free(Fp); free(Fm);
+}
+
+/* Reverse of one half kick  v' = v + h (E chi x^ + gamma (u_p - v) + xi),
+ * J' = J + h (gamma (u_p - v) + xi), with xi = sqrt(2 gamma kT / dt) z.
+ * lam_v holds the adjoint of v' on entry and of v on return; lam_J is the
+ * adjoint of J (constant through the cycle, J only accumulates). */
+static void kick_adjoint(const orc_sim *s, const md_record *rec, int k, int sub, const double *up,
+                         const double *lam_J, double *lam_v, double *lam_up, double *dpar)
+{
+    const orc_params *p = &s->p;
+    int N = p->n_beads;
+    double dt = 1.0 / p->md_outer, h = 0.5 * dt;
+    int noisy = p->kT > 0.0 && p->gamma > 0.0;
+    for (int i = 0; i < N; i++) {
+        for (int a = 0; a < 3; a++) {
+            size_t q = 3 * (size_t)i + a;
+            double lv = lam_v[q], lj = lam_J[q];
+            double vb = rec->vk[(size_t)k * 3 * N + q];
+            double xi = rec->xi[(size_t)sub * 3 * N + q];
+            double dxi_dgamma = noisy ? xi / (2.0 * p->gamma) : 0.0;
+            dpar[0] += h * ((up[q] - vb) + dxi_dgamma) * (lv + lj);
+            if (a == 0) dpar[1] += h * rec->ch[(size_t)k * N + i] * lv;
+            lam_up[q] += h * p->gamma * (lv + lj);
+            lam_v[q] = lv * (1.0 - h * p->gamma) - h * p->gamma * lj;
+        }
+    }
+}
+
+/* Reverse of md_cycle: lam_r, lam_v hold the adjoints of the end positions
+ * and velocities on entry and of the start ones on return.  Velocity Verlet
+ * sub-step t -> t+1:  v_h = v + hb F(r_t); r_{t+1} = r_t + dtb v_h;
+ * v' = v_h + hb F(r_{t+1}). */
+static void md_cycle_adjoint(const orc_sim *s, const md_record *rec, const double *up, const double *lam_J,
+                             double *lam_r, double *lam_v, double *lam_up, double *dpar)
+{
+    const orc_params *p = &s->p;
+    int N = p->n_beads, M = p->md_outer, Mb = p->md_inner;
+    double dtb = 1.0 / M / Mb, hb = 0.5 * dtb;
+    double *jw = (double *)malloc(sizeof(double) * (3 * N + 3));
+    for (int sub = M - 1; sub >= 0; sub--) {
+        kick_adjoint(s, rec, 2 * sub + 1, sub, up, lam_J, lam_v, lam_up, dpar);
+        for (int b = Mb - 1; b >= 0; b--) {
+            size_t t = (size_t)sub * Mb + b;
+            force_jacobian_times(s, rec->rt + (t + 1) * 3 * N, lam_v, jw);
+            for (int q = 0; q < 3 * N; q++) lam_r[q] += hb * jw[q];
+            for (int q = 0; q < 3 * N; q++) lam_v[q] += dtb * lam_r[q];
+            force_jacobian_times(s, rec->rt + t * 3 * N, lam_v, jw);
+            for (int q = 0; q < 3 * N; q++) lam_r[q] += hb * jw[q];
+        }
+        kick_adjoint(s, rec, 2 * sub, sub, up, lam_J, lam_v, lam_up, dpar);
+    }
+    free(jw);
+}
+
+void orc_step_adjoint(orc_sim *s, double *lam_f, double *lam_r, double *lam_v, double *dpar)
+{
+    const orc_params *p = &s->p;
+    int ns = s->ns, N = p->n_beads, M = p->md_outer, Mb = p->md_inner;
+    double omega = 1.0 / p->tau;
+
+    /* recompute the forward step's intermediates from (f^n, r^n, v^n) */
+    orc_moments(s, s->rho, s->u);
+    double *r_start = (double *)malloc(sizeof(double) * (3 * N + 3));
+    memcpy(r_start, s->r, sizeof(double) * 3 * N);
+    for (int i = 0; i < N; i++) gather_velocity(s, r_start + 3 * i, s->up + 3 * i);
+    md_record rec;
+    rec.rt = (double *)malloc(sizeof(double) * ((size_t)M * Mb + 1) * (3 * N + 3));
+    rec.vk = (double *)malloc(sizeof(double) * 2 * M * (3 * N + 3));
+    rec.ch = (int *)malloc(sizeof(int) * 2 * M * (N + 1));
+    rec.xi = (double *)malloc(sizeof(double) * M * (3 * N + 3));
+    if (N > 0) md_cycle(s, &rec);
+
+    /* 6'. streaming: f^{n+1}_i(x + c_i) = f*_i(x), or f^{n+1}_opp(i)(x) = f*_i(x)
+     *     when x + c_i is solid */
+    double *lam_star = (double *)calloc((size_t)19 * ns, sizeof(double));
+    for (int z = 0; z < p->nz; z++)
+        for (int y = 0; y < p->ny; y++)
+            for (int x = 0; x < p->nx; x++) {
+                int site = site_of(s, x, y, z);
+                if (s->solid[site]) continue;
+                for (int i = 0; i < 19; i++) {
+                    int dest = site_of(s, x + CI[i][0], y + CI[i][1], z + CI[i][2]);
+                    lam_star[(size_t)i * ns + site] = s->solid[dest] ? lam_f[(size_t)opposite_of(i) * ns + site]
+                                                                     : lam_f[(size_t)i * ns + dest];
+                }
+            }
+
+    /* 5'. f*_i = f_i - omega (f_i - f_eq_i(f)) + S_i(G + g) at fluid sites */
+    double *lam_new = (double *)calloc((size_t)19 * ns, sizeof(double));
+    double *lam_G = (double *)calloc((size_t)3 * ns, sizeof(double));
+    double dS[3][19];
+    for (int a = 0; a < 3; a++) {
+        double e[3] = {0, 0, 0};
+        e[a] = 1.0;
+        orc_source(e, dS[a]); /* S is linear in G: dS_i/dG_a */
+    }
+    for (int site = 0; site < ns; site++) {
+        if (s->solid[site]) continue;
+        double rho = s->rho[site];
+        double uu[3] = {s->u[site], s->u[ns + site], s->u[2 * ns + site]};
+        for (int k = 0; k < 19; k++) {
+            double acc = (1.0 - omega) * lam_star[(size_t)k * ns + site];
+            for (int i = 0; i < 19; i++) acc += omega * lam_star[(size_t)i * ns + site] * dfeq_df(i, k, rho, uu);
+            lam_new[(size_t)k * ns + site] = acc;
+        }
+        for (int a = 0; a < 3; a++) {
+            double acc = 0.0;
+            for (int i = 0; i < 19; i++) acc += lam_star[(size_t)i * ns + site] * dS[a][i];
+            lam_G[(size_t)a * ns + site] = acc;
+        }
+    }
+
+    /* 4'. spread: G(x_k) -= W_k(r^n) J_p */
+    double *lam_J = (double *)calloc((size_t)3 * N + 3, sizeof(double));
+    double *lam_rw = (double *)calloc((size_t)3 * N + 3, sizeof(double));
+    for (int i = 0; i < N; i++) {
+        int nodes[8];
+        double W[8], dW[8][3];
+        weights_and_gradient(s, r_start + 3 * i, nodes, W, dW);
+        for (int k = 0; k < 8; k++) {
+            double jg = 0.0;
+            for (int a = 0; a < 3; a++) {
+                double lg = lam_G[(size_t)a * ns + nodes[k]];
+                lam_J[3 * i + a] -= W[k] * lg;
+                jg += s->J[3 * i + a] * lg;
+            }
+            for (int b = 0; b < 3; b++) lam_rw[3 * i + b] -= dW[k][b] * jg;
+        }
+    }
+
+    /* 3'. the MD cycle */
+    double *lam_up = (double *)calloc((size_t)3 * N + 3, sizeof(double));
+    if (N > 0) md_cycle_adjoint(s, &rec, s->up, lam_J, lam_r, lam_v, lam_up, dpar);
+
+    /* 2'. gather: u_p = sum_k W_k(r^n) u(x_k), u = sum_i f_i c_i / rho */
+    for (int i = 0; i < N; i++) {
+        int nodes[8];
+        double W[8], dW[8][3];
+        weights_and_gradient(s, r_start + 3 * i, nodes, W, dW);
+        for (int k = 0; k < 8; k++) {
+            int nd = nodes[k];
+            double ug = 0.0;
+            for (int a = 0; a < 3; a++) ug += s->u[(size_t)a * ns + nd] * lam_up[3 * i + a];
+            for (int b = 0; b < 3; b++) lam_r[3 * i + b] += dW[k][b] * ug;
+            if (W[k] == 0.0 || s->rho[nd] <= 0.0) continue;
+            for (int q = 0; q < 19; q++) {
+                double acc = 0.0;
+                for (int a = 0; a < 3; a++)
+                    acc += lam_up[3 * i + a] * (CI[q][a] - s->u[(size_t)a * ns + nd]) / s->rho[nd];
+                lam_new[(size_t)q * ns + nd] += W[k] * acc;
+            }
+        }
+    }
+    for (int q = 0; q < 3 * N; q++) lam_r[q] += lam_rw[q];
+    memcpy(lam_f, lam_new, sizeof(double) * 19 * (size_t)ns);
+
+    /* leave s at the state after the step, like orc_step */
+    memset(s->G, 0, sizeof(double) * 3 * ns);
+    for (int i = 0; i < N; i++) {
+        int nodes[8];
+        double w[8];
+        orc_interp_weights(s, r_start + 3 * i, nodes, w);
+        for (int k = 0; k < 8; k++)
+            for (int a = 0; a < 3; a++) s->G[(size_t)a * ns + nodes[k]] -= w[k] * s->J[3 * i + a];
+    }
+    for (int site = 0; site < ns; site++) {
+        if (s->solid[site]) continue;
+        double uu[3] = {s->u[site], s->u[ns + site], s->u[2 * ns + site]};
+        double feq[19], S[19];
+        orc_feq(s->rho[site], uu, feq);
+        double Gs[3] = {s->G[site] + p->body_force[0], s->G[ns + site] + p->body_force[1],
+                        s->G[2 * ns + site] + p->body_force[2]};
+        orc_source(Gs, S);
+        for (int i = 0; i < 19; i++) {
+            double fi = s->f[(size_t)i * ns + site];
+            s->fstar[(size_t)i * ns + site] = fi - omega * (fi - feq[i]) + S[i];
+        }
+    }
+    for (size_t k = 0; k < (size_t)19 * ns; k++) s->f[k] = 0.0;
+    for (int z = 0; z < p->nz; z++)
+        for (int y = 0; y < p->ny; y++)
+            for (int x = 0; x < p->nx; x++) {
+                int site = site_of(s, x, y, z);
+                if (s->solid[site]) continue;
+                for (int i = 0; i < 19; i++) {
+                    int dest = site_of(s, x + CI[i][0], y + CI[i][1], z + CI[i][2]);
+                    double val = s->fstar[(size_t)i * ns + site];
+                    if (s->solid[dest]) s->f[(size_t)opposite_of(i) * ns + site] = val;
+                    else s->f[(size_t)i * ns + dest] = val;
+                }
+            }
+    s->step += 1;
+
+    free(r_start); free(rec.rt); free(rec.vk); free(rec.ch); free(rec.xi);
+    free(lam_star); free(lam_new); free(lam_G); free(lam_J); free(lam_rw); free(lam_up);
+}
+
+int orc_adjoint(const orc_params *p, const uint8_t *solid, const double *f0, const double *r0, const double *v0,
+                int64_t step0, int K, double *out, double *dr0, double *dv0, double *df0)
+{
+    int N = p->n_beads;
+    if (N < 1 || K < 0) return -1;
+    orc_sim *s = orc_create(p, solid);
+    size_t nf = (size_t)19 * s->ns, nb = (size_t)3 * N;
+    if (f0) orc_set_populations(s, f0);
+    orc_set_beads(s, r0, v0);
+    orc_set_step(s, step0);
+    double *fs = (double *)malloc(sizeof(double) * nf * (size_t)(K > 0 ? K : 1));
+    double *rs = (double *)malloc(sizeof(double) * nb * (size_t)(K > 0 ? K : 1));
+    double *vs = (double *)malloc(sizeof(double) * nb * (size_t)(K > 0 ? K : 1));
+    if (!fs || !rs || !vs) { free(fs); free(rs); free(vs); orc_destroy(s); return -2; }
+    double x0 = 0.0, xK = 0.0;
+    for (int i = 0; i < N; i++) x0 += s->r[3 * i] / N;
+    for (int n = 0; n < K; n++) {
+        memcpy(fs + (size_t)n * nf, s->f, sizeof(double) * nf);
+        memcpy(rs + (size_t)n * nb, s->r, sizeof(double) * nb);
+        memcpy(vs + (size_t)n * nb, s->v, sizeof(double) * nb);
+        one_step(s);
+    }
+    for (int i = 0; i < N; i++) xK += s->r[3 * i] / N;
+
+    /* L = mean_p x_p(K) - mean_p x_p(0) */
+    double *lam_f = (double *)calloc(nf, sizeof(double));
+    double *lam_r = (double *)calloc(nb + 3, sizeof(double));
+    double *lam_v = (double *)calloc(nb + 3, sizeof(double));
+    double dpar[2] = {0.0, 0.0};
+    for (int i = 0; i < N; i++) lam_r[3 * i] = 1.0 / N;
+    for (int n = K - 1; n >= 0; n--) {
+        memcpy(s->f, fs + (size_t)n * nf, sizeof(double) * nf);
+        memcpy(s->r, rs + (size_t)n * nb, sizeof(double) * nb);
+        memcpy(s->v, vs + (size_t)n * nb, sizeof(double) * nb);
+        s->step = step0 + n;
+        orc_step_adjoint(s, lam_f, lam_r, lam_v, dpar);
+    }
+    for (int i = 0; i < N; i++) lam_r[3 * i] -= 1.0 / N;
+    out[0] = xK - x0;
+    out[1] = dpar[0];
+    out[2] = dpar[1];
+    if (dr0) memcpy(dr0, lam_r, sizeof(double) * nb);
+    if (dv0) memcpy(dv0, lam_v, sizeof(double) * nb);
+    if (df0) memcpy(df0, lam_f, sizeof(double) * nf);
+    free(fs); free(rs); free(vs); free(lam_f); free(lam_r); free(lam_v);
+    orc_destroy(s);
+    return 0;
 }

@@ -78,6 +78,28 @@ void orc_observables(const orc_sim *s, double *out /* ORC_NOBS */);
 
 #define ORC_NOBS 16
 
+/* events that make a loss non-differentiable (for finite-difference checks):
+ * out[0] = half kicks taken inside the pore channel, out[1] = sum over steps
+ * and beads of the index of the lattice cell holding the bead */
+void orc_event_counts(const orc_sim *s, double *out /*2*/);
+
+/* Discrete adjoint (reverse mode) of one coupled step.  s holds the state
+ * (f^n, r^n, v^n, step n).  On entry lam_f [19][nsites], lam_r, lam_v [N][3]
+ * are the adjoints of f^{n+1}, r^{n+1}, v^{n+1}; on return those of f^n, r^n,
+ * v^n.  dpar[0] += dL/dgamma and dpar[1] += dL/dE of this step.  s is left at
+ * the state after the step, as orc_step(s, 1) would leave it. */
+void orc_step_adjoint(orc_sim *s, double *lam_f, double *lam_r, double *lam_v, double *dpar /*2*/);
+
+/* Gradient of L = mean_p x_p(K) - mean_p x_p(0) (unwrapped bead x) over K
+ * coupled steps from pre-collision populations f0 (NULL: fluid at rest),
+ * bead positions r0 and velocities v0 (NULL: at rest) at step step0.
+ * out = {L, dL/dgamma, dL/dE}; dr0, dv0 [N][3] and df0 [19][nsites] (each may
+ * be NULL) receive dL/dr0, dL/dv0, dL/df0.  Keeps all K states in memory.
+ * Returns 0, or < 0 for N < 1, K < 0 or an allocation failure. */
+int orc_adjoint(const orc_params *p, const uint8_t *solid, const double *f0, const double *r0,
+                const double *v0, int64_t step0, int K, double *out /*3*/, double *dr0,
+                double *dv0, double *df0);
+
 #ifdef __cplusplus
 }
 #endif
