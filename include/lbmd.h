@@ -224,6 +224,48 @@ lbmd_status lbmd_kernel_times(lbmd_handle *h, lbmd_kernel_time *out, int32_t max
                               int32_t *n_entries);
 lbmd_status lbmd_launch_count(lbmd_handle *h, int64_t *launches);
 
+/* Friction gamma (Sec. II, Eq. 12; it also sets the noise amplitude
+ * sqrt(2 gamma kT / dt) of Eq. 15) and pore field E (Sec. IV) of every
+ * realization, replacing the values the handle was created with.  A captured
+ * step graph is dropped (it is captured again at the next lbmd_step).
+ * gamma >= 0, finite E; LBMD_ERR_INVALID_ARG otherwise. */
+lbmd_status lbmd_set_drive(lbmd_handle *h, double gamma, double E);
+
+/* ---- reverse mode -------------------------------------------------------
+ * Gradient of the centre-of-mass displacement of each chain along the field,
+ *   L_r = mean_p x_p(K) - mean_p x_p(0)   (unwrapped x, realization r),
+ * over the next K coupled steps (Sec. II, Eqs. 1-22; Sec. IV), with respect
+ * to the friction gamma, the pore field E and the initial bead positions.
+ * This is the exact derivative of the discrete FP32 step (discrete adjoint):
+ * the pore-field indicator is piecewise constant in r and is differentiated
+ * as 0; the trilinear weights have kinks on cell faces.
+ *
+ * Scheme: the K forward steps run from the handle's state, storing the
+ * populations and bead state every checkpoint_every steps in `scratch`; then,
+ * segment by segment from the last, the steps are replayed from their
+ * checkpoint while the particle kernel records its trajectory, and the
+ * adjoint kernels run backwards through the segment: the lattice adjoint
+ * (BGK Jacobian-transpose and transposed pull with bounce-back), the bead
+ * adjoint (spread, MD cycle with force Jacobian-vector products, gather; one
+ * block per chain) and a fix-up of the lattice adjoint at the beads' corner
+ * sites.  dL/dgamma and dL/dE are summed in FP64.
+ *
+ * scratch: caller-owned device memory, 256-byte aligned, at least the size
+ * lbmd_adjoint_required_bytes reports (for K = 200, checkpoint_every = 20 on
+ * 96x48x48: about 0.6 GB).  Outputs (host): loss, dgamma, dE [n_real];
+ * dr0 [total_beads][3] (dL_r/dr0 of realization r's beads); any may be NULL.
+ * On return the handle holds the state after the K steps, as lbmd_step(h, K)
+ * would leave it.  Synchronises.
+ *
+ * Requirements (LBMD_ERR_INVALID_ARG otherwise): FP32 populations; K >= 1;
+ * 1 <= checkpoint_every; every realization holds at least one bead; the
+ * bead-wall cut-off 2^(1/6) wall_sigma below 2; gamma > 0 when kT > 0 (the
+ * noise amplitude has no derivative at gamma = 0). */
+lbmd_status lbmd_adjoint_required_bytes(const lbmd_handle *h, int32_t K, int32_t checkpoint_every,
+                                        size_t *bytes);
+lbmd_status lbmd_adjoint(lbmd_handle *h, int32_t K, int32_t checkpoint_every, void *scratch,
+                         size_t scratch_bytes, double *loss, double *dgamma, double *dE, double *dr0);
+
 /* Allocation-free fluid sums.  The paper has no counterpart: this is a
  * utility for callers that cannot allocate device memory where they call it,
  * such as a monitoring loop beside a running simulation on a GPU whose memory

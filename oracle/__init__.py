@@ -89,6 +89,7 @@ def lib():
                                      P, P, P, P]
         _lib.orc_step_adjoint.argtypes = [P, P, P, P, P]
         _lib.orc_event_counts.argtypes = [P, P]
+        _lib.orc_channel_trace.argtypes = [P, ctypes.c_int, P, ctypes.c_int64]
     return _lib
 
 
@@ -303,6 +304,15 @@ class OracleSim:
         out = np.zeros(2)
         lib().orc_event_counts(self._h, _vp(out))
         return float(out[0]), float(out[1])
+
+    def channel_trace(self, mode: int, buf: np.ndarray | None = None):
+        """Record (mode 1) or replay (mode 2) the pore-channel indicator of
+        every half kick through buf (int32, len >= steps * 2 M * N); mode 0
+        switches the trace off."""
+        if buf is not None:
+            assert buf.dtype == np.int32 and buf.flags["C_CONTIGUOUS"]
+        self._trace = buf  # kept alive while the library holds the pointer
+        lib().orc_channel_trace(self._h, int(mode), _vp(buf), int(buf.size) if buf is not None else 0)
 
     def step_adjoint(self, lam_f, lam_r, lam_v):
         """Adjoint of one step at the current state; returns (lam_f, lam_r, lam_v,

@@ -163,6 +163,12 @@ struct orc_sim {
      * checks: half kicks taken inside the pore channel, and the sum over steps
      * and beads of the index of the lattice cell holding the bead */
     double field_kicks, cell_sum;
+    /* channel trace: 0 off; 1 record the pore-channel indicator of every
+     * (step, half kick, bead) into chan; 2 replay it from chan instead of
+     * testing the position (finite differences with the field events held) */
+    int chan_mode;
+    int *chan;
+    int64_t chan_len, chan_pos;
 };
 
 static int wrap_index(int i, int n)
@@ -491,22 +497,33 @@ void orc_field_forces(const orc_sim *s, const double *r, double *F)
 /* ------------------------------------------------------------------------ */
 /* one MD cycle (Sec. II, Eq. 22, as a multiple-time-step velocity Verlet)   */
 /* ------------------------------------------------------------------------ */
+/* pore-channel indicator of bead i at a half kick, through the trace */
+static int kick_channel(orc_sim *s, int i)
+{
+    int ch;
+    if (s->chan_mode == 2 && s->chan_pos < s->chan_len) ch = s->chan[s->chan_pos++];
+    else {
+        ch = in_pore_channel(s, s->r + 3 * i);
+        if (s->chan_mode == 1 && s->chan_pos < s->chan_len) s->chan[s->chan_pos++] = ch;
+    }
+    return ch;
+}
+
 static void slow_half_kick(orc_sim *s, const double *xi, double h)
 {
     const orc_params *p = &s->p;
     int N = p->n_beads;
-    double *Fe = (double *)malloc(sizeof(double) * 3 * N);
-    orc_field_forces(s, s->r, Fe);
     for (int i = 0; i < N; i++) {
-        if (in_pore_channel(s, s->r + 3 * i)) s->field_kicks += 1.0;
+        int ch = kick_channel(s, i);
+        if (ch) s->field_kicks += 1.0;
+        double Fe[3] = {ch ? p->E : 0.0, 0.0, 0.0}; /* q E x^ in the channel, q = 1 */
         for (int a = 0; a < 3; a++) {
             double drag = p->gamma * (s->up[3 * i + a] - s->v[3 * i + a]); /* Eq. 12 */
             double fluid = drag + xi[3 * i + a];                            /* Eqs. 12 + 13 */
-            s->v[3 * i + a] += h * (Fe[3 * i + a] + fluid);
+            s->v[3 * i + a] += h * (Fe[a] + fluid);
             s->J[3 * i + a] += h * fluid;
         }
     }
-    free(Fe);
 }
 
 /* What one MD cycle passed through, kept for the adjoint sweep. */
@@ -521,7 +538,11 @@ static void record_kick(const orc_sim *s, md_record *rec, int k)
 {
     int N = s->p.n_beads;
     memcpy(rec->vk + (size_t)k * 3 * N, s->v, sizeof(double) * 3 * N);
-    for (int i = 0; i < N; i++) rec->ch[(size_t)k * N + i] = in_pore_channel(s, s->r + 3 * i);
+    for (int i = 0; i < N; i++) {
+        int ch = in_pore_channel(s, s->r + 3 * i);
+        if (s->chan_mode == 2 && s->chan_pos + i < s->chan_len) ch = s->chan[s->chan_pos + i];
+        rec->ch[(size_t)k * N + i] = ch;
+    }
 }
 
 static void md_cycle(orc_sim *s, md_record *rec)
@@ -761,20 +782,15 @@ static void weights_and_gradient(const orc_sim *s, const double *r, int *nodes, 
     }
 }
 
-/* d f_eq_i / d f_k at a site, by the chain rule through rho = sum f and
- * u = sum f c / rho:  d f_eq_i/d rho |_u + sum_a d f_eq_i/d u_a (c_ka - u_a) / rho */
-static double dfeq_df(int i, int k, double rho, const double *u)
+/* partial derivatives of f_eq_i = w_i rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u)
+ * with respect to rho (u held) and to u_a (rho held) */
+static void feq_partials(int i, double rho, const double *u, double *d_rho, double *d_u)
 {
     double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     double cu = CI[i][0] * u[0] + CI[i][1] * u[1] + CI[i][2] * u[2];
     double w = weight_of(i);
-    double d_rho = w * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-    double acc = d_rho;
-    for (int a = 0; a < 3; a++) {
-        double d_ua = w * rho * (3.0 * CI[i][a] + 9.0 * cu * CI[i][a] - 3.0 * u[a]);
-        acc += d_ua * (CI[k][a] - u[a]) / rho;
-    }
-    return acc;
+    *d_rho = w * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+    for (int a = 0; a < 3; a++) d_u[a] = w * rho * (3.0 * CI[i][a] + 9.0 * cu * CI[i][a] - 3.0 * u[a]);
 }
 
 /* (dF/dr) w for the fast forces, by a central difference of orc_fast_forces
@@ -899,9 +915,19 @@ void orc_step_adjoint(orc_sim *s, double *lam_f, double *lam_r, double *lam_v, d
         if (s->solid[site]) continue;
         double rho = s->rho[site];
         double uu[3] = {s->u[site], s->u[ns + site], s->u[2 * ns + site]};
+        /* reverse through f_eq(rho, u): lam_rho = sum_i lam*_i d f_eq_i/d rho,
+         * lam_u = sum_i lam*_i d f_eq_i/d u; then rho = sum f, u = sum f c / rho */
+        double lam_rho = 0.0, lam_u[3] = {0, 0, 0};
+        for (int i = 0; i < 19; i++) {
+            double li = omega * lam_star[(size_t)i * ns + site];
+            double d_rho, d_u[3];
+            feq_partials(i, rho, uu, &d_rho, d_u);
+            lam_rho += li * d_rho;
+            for (int a = 0; a < 3; a++) lam_u[a] += li * d_u[a];
+        }
         for (int k = 0; k < 19; k++) {
-            double acc = (1.0 - omega) * lam_star[(size_t)k * ns + site];
-            for (int i = 0; i < 19; i++) acc += omega * lam_star[(size_t)i * ns + site] * dfeq_df(i, k, rho, uu);
+            double acc = (1.0 - omega) * lam_star[(size_t)k * ns + site] + lam_rho;
+            for (int a = 0; a < 3; a++) acc += lam_u[a] * (CI[k][a] - uu[a]) / rho;
             lam_new[(size_t)k * ns + site] = acc;
         }
         for (int a = 0; a < 3; a++) {
@@ -1043,4 +1069,12 @@ int orc_adjoint(const orc_params *p, const uint8_t *solid, const double *f0, con
     free(fs); free(rs); free(vs); free(lam_f); free(lam_r); free(lam_v);
     orc_destroy(s);
     return 0;
+}
+
+void orc_channel_trace(orc_sim *s, int mode, int *buf, int64_t len)
+{
+    s->chan_mode = buf ? mode : 0;
+    s->chan = buf;
+    s->chan_len = buf ? len : 0;
+    s->chan_pos = 0;
 }

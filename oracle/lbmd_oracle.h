@@ -83,6 +83,14 @@ void orc_observables(const orc_sim *s, double *out /* ORC_NOBS */);
  * and beads of the index of the lattice cell holding the bead */
 void orc_event_counts(const orc_sim *s, double *out /*2*/);
 
+/* Pore-channel indicator trace, for finite differences of a loss with the
+ * field events held: mode 1 records the indicator of every (step, half kick,
+ * bead) into buf[len] in the order the kicks happen; mode 2 replays it
+ * instead of testing the bead positions; mode 0 (or buf NULL) switches the
+ * trace off.  The buffer stays owned by the caller and must outlive the
+ * steps that use it. */
+void orc_channel_trace(orc_sim *s, int mode, int *buf, int64_t len);
+
 /* Discrete adjoint (reverse mode) of one coupled step.  s holds the state
  * (f^n, r^n, v^n, step n).  On entry lam_f [19][nsites], lam_r, lam_v [N][3]
  * are the adjoints of f^{n+1}, r^{n+1}, v^{n+1}; on return those of f^n, r^n,

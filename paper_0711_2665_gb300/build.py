@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblbmd.so")
-SOURCES = ["lbmd_api.cu", "k_fluid.cu", "k_particles.cu", "lbmd_static.cu"]
+SOURCES = ["lbmd_api.cu", "k_fluid.cu", "k_particles.cu", "k_adjoint.cu", "lbmd_static.cu"]
 HEADERS = [os.path.join(CSRC, "lbmd_internal.cuh"), os.path.join(ROOT, "include", "lbmd.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]

@@ -548,6 +548,13 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
         const float4 uu = S.up[off + p];
         up = make_float3(uu.x, uu.y, uu.z);
     }
+    float4 *const trj = S.traj;  // trajectory record for the adjoint (usually null)
+    const int TB = S.total_beads;
+    if (trj && owner) {
+        trj[(size_t)traj_slot_hi(S.M, S.Mb, 0) * TB + off + p] = mh;
+        trj[(size_t)traj_slot_lo(S.M, S.Mb, 0) * TB + off + p] = ml;
+        trj[(size_t)traj_slot_up(S.M, S.Mb) * TB + off + p] = make_float4(up.x, up.y, up.z, 0.f);
+    }
     // every block of the cluster is running and initialised before any
     // block writes into another's shared memory
     sync_all(cl, C);
@@ -591,6 +598,8 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
         if (own) {  // first half kick: field + friction + noise
             const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx, S.inx), ff_wrap(mh.y, ml.y, fny, S.iny),
                                        ff_wrap(mh.z, ml.z, fnz, S.inz));
+            if (trj && lt == 0)
+                trj[(size_t)traj_slot_kick(S.M, S.Mb, 2 * sub) * TB + off + p] = make_float4(v.x, v.y, v.z, ch ? 1.f : 0.f);
             const float3 fl = S.gamma * (up - v) + xi;
             v = v + h * (make_float3(ch ? S.E : 0.0f, 0.f, 0.f) + fl);
             J = J + h * fl;
@@ -602,6 +611,10 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
                 ff_add(mh.x, ml.x, dtb * v.x);
                 ff_add(mh.y, ml.y, dtb * v.y);
                 ff_add(mh.z, ml.z, dtb * v.z);
+                if (trj && lt == 0) {
+                    trj[(size_t)traj_slot_hi(S.M, S.Mb, t + 1) * TB + off + p] = mh;
+                    trj[(size_t)traj_slot_lo(S.M, S.Mb, t + 1) * TB + off + p] = ml;
+                }
                 const float3 dd = ffsub(mh, ml, bh, bl);
                 const bool moved = dot3(dd, dd) > S.skin_half2;
                 if (lt == 0) {
@@ -639,6 +652,8 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
         if (own) {  // second half kick with the same noise
             const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx, S.inx), ff_wrap(mh.y, ml.y, fny, S.iny),
                                        ff_wrap(mh.z, ml.z, fnz, S.inz));
+            if (trj && lt == 0)
+                trj[(size_t)traj_slot_kick(S.M, S.Mb, 2 * sub + 1) * TB + off + p] = make_float4(v.x, v.y, v.z, ch ? 1.f : 0.f);
             const float3 fl = S.gamma * (up - v) + xi;
             v = v + h * (make_float3(ch ? S.E : 0.0f, 0.f, 0.f) + fl);
             J = J + h * fl;
@@ -673,6 +688,7 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
         S.r_lo[off + p] = ml;
         S.v[off + p] = make_float4(v.x, v.y, v.z, 0.f);
         S.J[off + p] = make_float4(J.x, J.y, J.z, 0.f);
+        if (trj) trj[(size_t)traj_slot_J(S.M, S.Mb) * TB + off + p] = make_float4(J.x, J.y, J.z, 0.f);
         if (!isfinite(mh.x + mh.y + mh.z + v.x + v.y + v.z)) atomicOr(&s_err, ST_NONFINITE);
     }
     // no block leaves while another may still write into its shared memory;

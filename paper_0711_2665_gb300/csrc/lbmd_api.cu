@@ -16,8 +16,10 @@ using namespace lbmd;
 
 namespace {
 
-constexpr int K_GATHER = 0, K_PARTICLES = 1, K_STREAM_COLLIDE = 2, K_SOURCE = 3, K_COUNT = 4;
-const char *KNAMES[K_COUNT] = {"gather", "particles", "stream_collide", "source"};
+constexpr int K_GATHER = 0, K_PARTICLES = 1, K_STREAM_COLLIDE = 2, K_SOURCE = 3, K_SC_ADJOINT = 4,
+              K_BEAD_ADJOINT = 5, K_ADJ_FIXUP = 6, K_COUNT = 7;
+const char *KNAMES[K_COUNT] = {"gather", "particles", "stream_collide", "source", "sc_adjoint", "bead_adjoint",
+                               "adj_fixup"};
 constexpr double SKIN = 0.8;  // Verlet-list skin (lattice units)
 
 struct Layout {
@@ -55,8 +57,8 @@ struct lbmd_handle {
     bool profiling = false;
     std::vector<ProfRec> pending;
     std::vector<cudaEvent_t> free_events;
-    double prof_ms[K_COUNT] = {0, 0, 0, 0};
-    long long prof_n[K_COUNT] = {0, 0, 0, 0};
+    double prof_ms[K_COUNT] = {};
+    long long prof_n[K_COUNT] = {};
     long long launches = 0;
     long long host_step = 0;
     std::string err;
@@ -695,9 +697,215 @@ lbmd_status lbmd_set_step(lbmd_handle *h, int64_t step) {
     if (!h || step < 0) return LBMD_ERR_INVALID_ARG;
     long long s = step;
     CK(cudaMemcpyAsync(&h->S.ctrl->step, &s, sizeof(s), cudaMemcpyHostToDevice, h->st));
+    // the source marks the sites it has served with a tag made from the step
+    // number; after a jump of the counter an old mark could carry the tag of
+    // a coming step, so the marks are cleared
+    CK(cudaMemsetAsync(h->S.stamp, 0, (size_t)h->cfg.n_real * h->S.ns * sizeof(int), h->st));
     CK(cudaStreamSynchronize(h->st));
     h->host_step = step;
     return LBMD_OK;
+}
+
+lbmd_status lbmd_set_drive(lbmd_handle *h, double gamma, double E) {
+    if (!h || !(gamma >= 0.0) || !std::isfinite(gamma) || !std::isfinite(E))
+        return fail(h, LBMD_ERR_INVALID_ARG, "gamma must be finite and >= 0, E finite");
+    h->cfg.gamma = gamma;
+    h->cfg.E = E;
+    h->S.gamma = (float)gamma;
+    h->S.E = (float)E;
+    drop_graph(h);  // the graph holds the old parameters in its kernel arguments
+    return LBMD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// reverse mode
+// ---------------------------------------------------------------------------
+namespace {
+
+struct AdjLayout {
+    size_t pop, bead, traj;      // bytes of one population set, bead state (hi, lo, v), trajectory record
+    size_t ck_rec, seg_rec;      // bytes of one checkpoint, one replayed step
+    int nck, nseg;               // checkpoints (+ the final state), steps per segment
+    size_t ck, seg, lamA, lamB, lam_r, lam_v, LU, adj_node, dpar, total;
+};
+
+AdjLayout adj_layout(const lbmd_handle *h, int K, int C) {
+    AdjLayout a;
+    const Sim &S = h->S;
+    const size_t TB = (size_t)std::max(h->total_beads, 1);
+    a.pop = (size_t)h->cfg.n_real * LBMD_Q * S.ps * sizeof(float);
+    a.bead = 3 * TB * 16;
+    a.traj = (size_t)traj_slots(S.M, S.Mb) * TB * 16;
+    a.ck_rec = align256(a.pop) + align256(a.bead);
+    a.seg_rec = align256(a.pop) + align256(a.traj);
+    a.nck = (K + C - 1) / C + 1;
+    a.nseg = std::min(C, K);
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+    a.ck = take(a.ck_rec * a.nck);
+    a.seg = take(a.seg_rec * a.nseg);
+    a.lamA = take(a.pop);
+    a.lamB = take(a.pop);
+    a.lam_r = take(TB * 16);
+    a.lam_v = take(TB * 16);
+    a.LU = take((size_t)h->cfg.n_real * 3 * S.ns * 8);
+    a.adj_node = take(TB * 8 * 4);
+    a.dpar = take((size_t)h->cfg.n_real * 2 * sizeof(double));
+    a.total = o;
+    return a;
+}
+
+bool adjoint_ok(const lbmd_handle *h, int K, int C, std::string &why) {
+    if (h->cfg.precision != LBMD_FP32) { why = "the adjoint needs FP32 populations"; return false; }
+    if (K < 1 || C < 1) { why = "K and checkpoint_every must be >= 1"; return false; }
+    for (int r = 0; r < h->cfg.n_real; ++r)
+        if (h->offsets[r + 1] <= h->offsets[r]) { why = "every realization needs at least one bead"; return false; }
+    if (std::pow(2.0, 1.0 / 6.0) * h->cfg.wall_sigma >= 2.0) { why = "bead-wall cut-off must be below 2"; return false; }
+    if (h->cfg.kT > 0.0 && !(h->cfg.gamma > 0.0)) { why = "gamma must be > 0 when kT > 0"; return false; }
+    return true;
+}
+
+lbmd_status chain_com_x(lbmd_handle *h, std::vector<double> &com) {
+    std::vector<double> r(3 * (size_t)h->total_beads);
+    lbmd_status s = lbmd_get_beads(h, r.data(), nullptr);
+    if (s != LBMD_OK) return s;
+    com.assign(h->cfg.n_real, 0.0);
+    for (int q = 0; q < h->cfg.n_real; ++q) {
+        const int a = h->offsets[q], b = h->offsets[q + 1];
+        double acc = 0.0;
+        for (int i = a; i < b; ++i) acc += r[3 * (size_t)i];
+        com[q] = acc / (double)(b - a);
+    }
+    return LBMD_OK;
+}
+
+}  // namespace
+
+lbmd_status lbmd_adjoint_required_bytes(const lbmd_handle *h, int32_t K, int32_t checkpoint_every, size_t *bytes) {
+    if (!h || !bytes) return LBMD_ERR_INVALID_ARG;
+    std::string why;
+    if (!adjoint_ok(h, K, checkpoint_every, why)) return fail(const_cast<lbmd_handle *>(h), LBMD_ERR_INVALID_ARG, why);
+    *bytes = adj_layout(h, K, checkpoint_every).total;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_adjoint(lbmd_handle *h, int32_t K, int32_t C, void *scratch, size_t scratch_bytes, double *loss,
+                         double *dgamma, double *dE, double *dr0) {
+    if (!h) return LBMD_ERR_INVALID_ARG;
+    std::string why;
+    if (!adjoint_ok(h, K, C, why)) return fail(h, LBMD_ERR_INVALID_ARG, why);
+    const AdjLayout a = adj_layout(h, K, C);
+    if (!scratch || scratch_bytes < a.total || ((uintptr_t)scratch & 255))
+        return fail(h, LBMD_ERR_BUFFER, "adjoint scratch missing, too small or not 256-byte aligned");
+    char *b = (char *)scratch;
+    Sim &S = h->S;
+    const int n_real = h->cfg.n_real, TB = h->total_beads;
+    const long long step0 = h->host_step;
+    lbmd_status st = LBMD_OK;
+
+    auto save = [&](int j) -> lbmd_status {
+        char *c = b + a.ck + (size_t)j * a.ck_rec;
+        char *cb = c + align256(a.pop);
+        CK(cudaMemcpyAsync(c, h->popA, a.pop, cudaMemcpyDeviceToDevice, h->st));
+        CK(cudaMemcpyAsync(cb, S.r_hi, (size_t)TB * 16, cudaMemcpyDeviceToDevice, h->st));
+        CK(cudaMemcpyAsync(cb + (size_t)TB * 16, S.r_lo, (size_t)TB * 16, cudaMemcpyDeviceToDevice, h->st));
+        CK(cudaMemcpyAsync(cb + (size_t)TB * 32, S.v, (size_t)TB * 16, cudaMemcpyDeviceToDevice, h->st));
+        return LBMD_OK;
+    };
+    auto restore = [&](int j, long long step) -> lbmd_status {
+        const char *c = b + a.ck + (size_t)j * a.ck_rec;
+        const char *cb = c + align256(a.pop);
+        CK(cudaMemcpyAsync(h->popA, c, a.pop, cudaMemcpyDeviceToDevice, h->st));
+        CK(cudaMemcpyAsync(S.r_hi, cb, (size_t)TB * 16, cudaMemcpyDeviceToDevice, h->st));
+        CK(cudaMemcpyAsync(S.r_lo, cb + (size_t)TB * 16, (size_t)TB * 16, cudaMemcpyDeviceToDevice, h->st));
+        CK(cudaMemcpyAsync(S.v, cb + (size_t)TB * 32, (size_t)TB * 16, cudaMemcpyDeviceToDevice, h->st));
+        return lbmd_set_step(h, step);
+    };
+
+    // forward sweep with checkpoints
+    std::vector<double> com0, comK;
+    if ((st = chain_com_x(h, com0)) != LBMD_OK) return st;
+    for (int n = 0; n < K; ++n) {
+        if (n % C == 0 && (st = save(n / C)) != LBMD_OK) return st;
+        if ((st = enqueue_step(h)) != LBMD_OK) return st;
+    }
+    if ((st = save(a.nck - 1)) != LBMD_OK) return st;
+    if ((st = chain_com_x(h, comK)) != LBMD_OK) return st;
+
+    // adjoint of the loss: lam_r = x^ / N_r, lam_v = 0, lam_A = 0
+    float *Lin = (float *)(b + a.lamA), *Lout = (float *)(b + a.lamB);
+    float4 *lam_r = (float4 *)(b + a.lam_r), *lam_v = (float4 *)(b + a.lam_v);
+    unsigned long long *LU = (unsigned long long *)(b + a.LU);
+    int *adj_node = (int *)(b + a.adj_node);
+    double *dpar = (double *)(b + a.dpar);
+    std::vector<float4> lr0(TB);
+    for (int q = 0; q < n_real; ++q)
+        for (int i = h->offsets[q]; i < h->offsets[q + 1]; ++i)
+            lr0[i] = make_float4((float)(1.0 / (h->offsets[q + 1] - h->offsets[q])), 0.f, 0.f, 0.f);
+    CK(cudaMemsetAsync(Lin, 0, a.pop, h->st));
+    CK(cudaMemsetAsync(Lout, 0, a.pop, h->st));
+    CK(cudaMemsetAsync(LU, 0, (size_t)n_real * 3 * S.ns * 8, h->st));
+    CK(cudaMemsetAsync(dpar, 0, (size_t)n_real * 2 * sizeof(double), h->st));
+    CK(cudaMemsetAsync(lam_v, 0, (size_t)TB * 16, h->st));
+    CK(cudaMemcpyAsync(lam_r, lr0.data(), (size_t)TB * 16, cudaMemcpyHostToDevice, h->st));
+
+    // backward sweep, segment by segment from the last
+    for (int j = (K - 1) / C; j >= 0; --j) {
+        const int n0 = j * C, n1 = std::min(K, n0 + C);
+        if ((st = restore(j, step0 + n0)) != LBMD_OK) return st;
+        for (int n = n0; n < n1; ++n) {
+            char *rec = b + a.seg + (size_t)(n - n0) * a.seg_rec;
+            CK(cudaMemcpyAsync(rec, h->popA, a.pop, cudaMemcpyDeviceToDevice, h->st));
+            S.traj = (float4 *)(rec + align256(a.pop));
+            st = enqueue_step(h);
+            S.traj = nullptr;
+            if (st != LBMD_OK) return st;
+        }
+        for (int n = n1 - 1; n >= n0; --n) {
+            const char *rec = b + a.seg + (size_t)(n - n0) * a.seg_rec;
+            const void *An = rec;
+            const float4 *trj = (const float4 *)(rec + align256(a.pop));
+            CK(cudaEventRecord(h->ev_fork, h->st));
+            CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+            {
+                ProfScope ps(h, K_BEAD_ADJOINT, h->aux);
+                CK(launch_bead_adjoint(S, An, Lin, trj, lam_r, lam_v, LU, adj_node, dpar, step0 + n, h->aux));
+            }
+            CK(cudaEventRecord(h->ev_join, h->aux));
+            {
+                ProfScope ps(h, K_SC_ADJOINT, h->st);
+                CK(launch_sc_adjoint(S, An, Lin, Lout, h->by, h->zc, h->st));
+            }
+            CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
+            {
+                ProfScope ps(h, K_ADJ_FIXUP, h->st);
+                CK(launch_adj_fixup(S, An, Lout, adj_node, LU, -1 - (int)((step0 + n) & 0x3fffffffll), h->st));
+            }
+            std::swap(Lin, Lout);
+            h->launches += 3;
+        }
+    }
+
+    // outputs, and the state after the K steps
+    std::vector<float4> lr(TB);
+    std::vector<double> dp(2 * (size_t)n_real);
+    CK(cudaMemcpyAsync(lr.data(), lam_r, (size_t)TB * 16, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(dp.data(), dpar, dp.size() * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    if ((st = restore(a.nck - 1, step0 + K)) != LBMD_OK) return st;
+    CK(cudaStreamSynchronize(h->st));
+    for (int q = 0; q < n_real; ++q) {
+        if (loss) loss[q] = comK[q] - com0[q];
+        if (dgamma) dgamma[q] = dp[2 * q];
+        if (dE) dE[q] = dp[2 * q + 1];
+        const double invN = 1.0 / (h->offsets[q + 1] - h->offsets[q]);
+        for (int i = h->offsets[q]; i < h->offsets[q + 1]; ++i) {
+            if (!dr0) break;
+            dr0[3 * (size_t)i] = (double)lr[i].x - invN;
+            dr0[3 * (size_t)i + 1] = lr[i].y;
+            dr0[3 * (size_t)i + 2] = lr[i].z;
+        }
+    }
+    return lbmd_check(h);
 }
 
 lbmd_status lbmd_set_graph(lbmd_handle *h, int32_t steps_per_graph) {

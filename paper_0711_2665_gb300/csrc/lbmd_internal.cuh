@@ -119,7 +119,22 @@ struct Sim {
     Ctrl *ctrl;
     unsigned int *rdone;        // [2][n_real] blocks finished per realization (diag pass, observables pass)
     unsigned long long *phase;  // [PHASES] SM cycles per particle-kernel phase, or null
+    // Trajectory record of the MD cycle for the adjoint, or null:
+    // traj[slot * total_beads + bead] with the slots of traj_slot_* below
+    float4 *traj;
 };
+
+// Slots of the MD trajectory record: positions (hi, lo) at the M*Mb + 1
+// sub-step boundaries, the velocity before each of the 2M half kicks (w = 1
+// when the bead sat in the pore channel), the frozen fluid velocity u_p and
+// the impulse J.
+__host__ __device__ inline int traj_npos(int M, int Mb) { return M * Mb + 1; }
+__host__ __device__ inline int traj_slot_hi(int M, int Mb, int t) { return t; }
+__host__ __device__ inline int traj_slot_lo(int M, int Mb, int t) { return traj_npos(M, Mb) + t; }
+__host__ __device__ inline int traj_slot_kick(int M, int Mb, int k) { return 2 * traj_npos(M, Mb) + k; }
+__host__ __device__ inline int traj_slot_up(int M, int Mb) { return 2 * traj_npos(M, Mb) + 2 * M; }
+__host__ __device__ inline int traj_slot_J(int M, int Mb) { return 2 * traj_npos(M, Mb) + 2 * M + 1; }
+__host__ __device__ inline int traj_slots(int M, int Mb) { return 2 * traj_npos(M, Mb) + 2 * M + 2; }
 
 // load, lists, md, spread, rebuild cycles inside md, number of rebuilds
 constexpr int PHASES = 6;
@@ -270,5 +285,12 @@ MdShape md_shape(const Sim &S);
 cudaError_t launch_gather(const Sim &S, const void *A, cudaStream_t st);
 cudaError_t launch_particles(const Sim &S, const void *A, cudaStream_t st);
 cudaError_t launch_bead_observables(const Sim &S, const void *A, cudaStream_t st);
+// reverse mode (FP32 populations only)
+cudaError_t launch_sc_adjoint(const Sim &S, const void *A, const float *Lin, float *Lout, int by, int zc, cudaStream_t st);
+size_t bead_adjoint_smem(const Sim &S);
+cudaError_t launch_bead_adjoint(const Sim &S, const void *A, const float *Lin, const float4 *trj, float4 *lam_r, float4 *lam_v,
+                                unsigned long long *LU, int *adj_node, double *dpar, long long step, cudaStream_t st);
+cudaError_t launch_adj_fixup(const Sim &S, const void *A, float *Lout, const int *adj_node, unsigned long long *LU, int tag,
+                             cudaStream_t st);
 
 }  // namespace lbmd

@@ -113,6 +113,9 @@ def lib():
         "lbmd_set_overlap": [vp, i32],
         "lbmd_get_overlap": [vp, P(i32)],
         "lbmd_get_md_shape": [vp, P(i32), P(i32)],
+        "lbmd_set_drive": [vp, ctypes.c_double, ctypes.c_double],
+        "lbmd_adjoint_required_bytes": [vp, i32, i32, P(sz)],
+        "lbmd_adjoint": [vp, i32, i32, vp, sz, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -343,6 +346,73 @@ class Simulation:
         n = ctypes.c_int64()
         self._check(self._lib.lbmd_launch_count(self._h, ctypes.byref(n)), "lbmd_launch_count")
         return n.value
+
+    # -- reverse mode ----------------------------------------------------
+    def set_drive(self, gamma: float, E: float):
+        self._check(self._lib.lbmd_set_drive(self._h, float(gamma), float(E)), "lbmd_set_drive")
+
+    def adjoint_bytes(self, K: int, checkpoint_every: int) -> int:
+        n = ctypes.c_size_t(0)
+        self._check(self._lib.lbmd_adjoint_required_bytes(self._h, int(K), int(checkpoint_every), ctypes.byref(n)),
+                    "lbmd_adjoint_required_bytes")
+        return n.value
+
+    def adjoint(self, K: int, checkpoint_every: int) -> dict:
+        """Loss L_r = mean x(K) - mean x(0) of every chain over the next K steps
+        and its gradient w.r.t. gamma, E and the initial bead positions
+        (lbmd_adjoint); the simulation ends K steps later."""
+        import torch
+        nbytes = self.adjoint_bytes(K, checkpoint_every)
+        with torch.cuda.device(self.device):
+            scratch = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        aligned = (scratch.data_ptr() + 255) & ~255
+        loss = np.zeros(self.n_real)
+        dg = np.zeros(self.n_real)
+        dE = np.zeros(self.n_real)
+        dr0 = np.zeros(3 * max(self.total_beads, 1))
+        self._check(self._lib.lbmd_adjoint(self._h, int(K), int(checkpoint_every), ctypes.c_void_p(aligned), nbytes,
+                                           _ptr(loss), _ptr(dg), _ptr(dE), _ptr(dr0)), "lbmd_adjoint")
+        del scratch
+        return dict(loss=loss, dgamma=dg, dE=dE, dr0=dr0[:3 * self.total_beads].reshape(self.total_beads, 3))
+
+
+def com_displacement(sim: Simulation, r0, gamma, E, K: int, checkpoint_every: int = 20, fluid=None):
+    """Differentiable centre-of-mass displacement of every chain along the
+    field over K coupled steps, as a function of the initial bead positions
+    r0 [total_beads, 3], the friction gamma and the pore field E (0-d
+    tensors).  The forward and the reverse sweep both run in the library
+    (lbmd_adjoint): the forward call computes the gradient too and keeps it
+    for backward.  The simulation restarts from fluid (populations as
+    get_populations returns them; None = fluid at rest) at step 0 and ends K
+    steps later."""
+    import torch
+
+    class _ComDisplacement(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, r0_t, gamma_t, E_t):
+            sim.set_drive(float(gamma_t), float(E_t))
+            if fluid is None:
+                sim.init_fluid()
+            else:
+                sim.set_populations(fluid)
+            sim.set_step(0)
+            sim.set_beads(r0_t.detach().cpu().double().numpy())
+            out = sim.adjoint(K, checkpoint_every)
+            dev = r0_t.device
+            ctx.save_for_backward(torch.as_tensor(out["dr0"], dtype=r0_t.dtype, device=dev),
+                                  torch.as_tensor(out["dgamma"], dtype=r0_t.dtype, device=dev),
+                                  torch.as_tensor(out["dE"], dtype=r0_t.dtype, device=dev))
+            ctx.offsets = sim.offsets
+            return torch.as_tensor(out["loss"], dtype=r0_t.dtype, device=dev)
+
+        @staticmethod
+        def backward(ctx, gl):
+            dr0, dg, dE = ctx.saved_tensors
+            counts = torch.as_tensor(np.diff(ctx.offsets), device=gl.device)
+            per_bead = torch.repeat_interleave(gl, counts)
+            return dr0 * per_bead[:, None], (dg * gl).sum(), (dE * gl).sum()
+
+    return _ComDisplacement.apply(r0, gamma, E)
 
 
 def from_workload(w: dict, device: str = "cuda:0", inputs: dict | None = None) -> tuple[Simulation, dict]:
