@@ -176,6 +176,85 @@ def cpu_baseline(w, budget_s=15.0):
             "sample": f"{n} FP64 oracle steps of realization 0 ({sites} sites, {o1} beads), {dt:.1f} s"}
 
 
+def _sc_roofline(sim, w, peak, peak_kind, steps=10):
+    """Stream-collide roofline from per-launch CUDA events over a few eager steps."""
+    sim.profile(True)
+    sim.step(steps)
+    kt = sim.kernel_times()
+    sim.profile(False)
+    n, ms = kt["stream_collide"]
+    sites = w["nx"] * w["ny"] * w["nz"] * w["n_real"]
+    b = (152 if w["precision"] == "fp32" else 76) * sites
+    achieved = b / (ms / n * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_kind": peak_kind, "kernel": "k_stream_collide", "algorithmic_bytes_per_launch": b,
+            "us_per_launch": 1e3 * ms / n}
+
+
+def extra_measurements(dev, stream, peak, peak_kind):
+    """The other forms of the step, each timed on its own workload with CUDA
+    events on the library's stream (inputs larger than L2, no flush needed):
+    the batched ensemble and the FP16-deviation storage, each run of K steps
+    one launch of the device-side step-loop graph, and the reverse sweep
+    (forward + checkpointed adjoint of 200 steps)."""
+    import numpy as np
+    import torch
+    from paper_0711_2665_gb300 import lbmd, workloads
+    out = {}
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) * 1e-3
+
+    for name, K in (("ensemble_fp32", 100), ("fp16dev", 60)):
+        w = workloads.get(name)
+        inp = workloads.build_inputs(w)
+        sim = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"], device=str(dev))
+        by, zc = sim.autotune(3)
+        sim.step_loop(20)  # captures the device-side loop graph
+        t = timed(lambda: sim.step_loop(K))
+        sites = w["nx"] * w["ny"] * w["nz"] * w["n_real"]
+        rf = _sc_roofline(sim, w, peak, peak_kind)
+        sim.check()
+        out[name] = {"value": sites * K / t / 1e6, "unit": "MLUPS", "ms_per_step": 1e3 * t / K,
+                     "steps_per_s": K / t, "realization_steps_per_s": K * w["n_real"] / t, "steps": K,
+                     "lattice": [w["nx"], w["ny"], w["nz"]], "n_real": w["n_real"], "beads": int(inp["offsets"][-1]),
+                     "precision": w["precision"], "tiles": [by, zc], "md_shape": list(sim.md_shape()),
+                     "launch": "one CUDA-graph launch per run (device-side loop of two-step bodies)",
+                     "roofline": rf}
+        sim.close()
+    w = workloads.get("adjoint")
+    inp = workloads.build_inputs(w)
+    K, C = w["steps"], w["checkpoint_every"]
+    sim = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"], device=str(dev))
+    sim.autotune(3)
+    sim.step(4)
+    t_fwd = timed(lambda: sim.step(K))
+    sim2 = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"], device=str(dev))
+    sim2.set_tiles(*sim.tiles())
+    sim2.adjoint(K, C)  # warm-up: first launches, and the scratch block the timed call reuses
+    sim3 = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"], device=str(dev))
+    sim3.set_tiles(*sim.tiles())
+    res = {}
+    t_adj = timed(lambda: res.update(sim3.adjoint(K, C)))
+    sites = w["nx"] * w["ny"] * w["nz"]
+    out["adjoint"] = {"value": K / t_adj, "unit": "steps/s", "forward_steps_per_s": K / t_fwd,
+                      "ratio_to_forward": t_adj / t_fwd, "K": K, "checkpoint_every": C,
+                      "lattice": [w["nx"], w["ny"], w["nz"]], "beads": int(inp["offsets"][-1]),
+                      "mlups_equivalent": sites * K / t_adj / 1e6,
+                      "grad_finite": bool(np.all(np.isfinite(res["dr0"]))),
+                      "note": "forward sweep with checkpoints, segment replay recording the MD trajectory, and the "
+                              "adjoint kernels; gradients of the centre-of-mass displacement w.r.t. gamma, E, r0"}
+    for s_ in (sim, sim2, sim3):
+        s_.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -185,6 +264,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the ensemble, FP16 and adjoint measurements")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -307,6 +388,8 @@ def main():
                 "data": "synthetic", "config": dict(_config_block(w, flush), tiles=list(sim.tiles())),
                 "roofline": roofline, "kernels": shares, "gpu_launches": launches,
                 "clocks": clocks, "e2e": e2e}
+        if not args.no_extras and world == 1:
+            line["forms"] = extra_measurements(dev, stream, peak, peak_kind)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line), flush=True)

@@ -183,6 +183,16 @@ lbmd_status lbmd_set_step(lbmd_handle *h, int64_t step);
  * (0 = launch kernels one by one).  Results are identical either way. */
 lbmd_status lbmd_set_graph(lbmd_handle *h, int32_t steps_per_graph);
 
+/* Advance n steps with one launch of a CUDA graph whose conditional WHILE
+ * node repeats a body of two coupled steps on the device, counting the
+ * bodies down in device memory: the host issues two operations for any n.
+ * The graph is captured on first use and dropped with the other graphs
+ * (parameter, tile, shape or overlap changes).  An odd n ends with one
+ * ordinary step.  Results are identical to lbmd_step(h, n).  Needs a
+ * non-default stream (LBMD_ERR_INVALID_ARG otherwise); while profiling is on
+ * it runs as lbmd_step. */
+lbmd_status lbmd_step_loop(lbmd_handle *h, int64_t n);
+
 /* Launch shapes of the stream-collide kernel: block (32, by) threads, each
  * thread walking zc consecutive z planes.  by in {1,2,4,8,16}, zc in 1..64.
  * The state (populations, beads) is bit-identical for every shape; the FP64

@@ -120,7 +120,7 @@ __device__ __forceinline__ float3 wca_tangent(float3 d, float3 dd, float eps, fl
 constexpr int ADJ_NBR_CAP = 48;
 constexpr int ADJ_ALL_PAIRS = 0xffff;
 
-__device__ float3 force_tangent(const Sim &S, const float4 *__restrict__ sh, const float4 *__restrict__ sl,
+__device__ __forceinline__ float3 force_tangent(const Sim &S, const float4 *__restrict__ sh, const float4 *__restrict__ sl,
                                 const float4 *__restrict__ sw, int p, int N, const uint16_t *__restrict__ lst,
                                 int nl) {
     const float4 mh = sh[p], ml = sl[p];

@@ -259,7 +259,7 @@ MdShape md_shape(const Sim &S) {
 // p-1, p, p+1; WCA with the listed beads and solid sites.  The lanes' parts
 // add up to the full force.
 template <int T>
-__device__ float3 force_part(const Sim &S, const PSmem &sm, int buf, bool own, int p, int pl, int N, float4 mh,
+__device__ __forceinline__ float3 force_part(const Sim &S, const PSmem &sm, int buf, bool own, int p, int pl, int N, float4 mh,
                              float4 ml, int lt) {
     float3 F = make_float3(0.f, 0.f, 0.f);
     if (!own) return F;
@@ -306,29 +306,44 @@ __device__ float3 force_part(const Sim &S, const PSmem &sm, int buf, bool own, i
         }
     }
     const float fnx = (float)S.nx, fny = (float)S.ny, fnz = (float)S.nz;
-    const int lj0 = lt, ljs = T;
-    const bool t_wall = true;
+    // Pair and wall lists, two entries per iteration: both entries' shared-
+    // memory loads are issued before either is used, since the loop is bound
+    // by load latency, not by arithmetic.
     {
         const int nn = sm.nn[pl];
-        for (int k = lj0; k < nn; k += ljs) {
-            const int q = sm.nbr[pl * NBR_CAP + k];
-            const float4 qh = ph[q], ql = plo[q];
-            const float3 d = make_float3(ff_diff(mh.x, ml.x, qh.x, ql.x, fnx, S.inx),
-                                         ff_diff(mh.y, ml.y, qh.y, ql.y, fny, S.iny),
-                                         ff_diff(mh.z, ml.z, qh.z, ql.z, fnz, S.inz));
-            const float r2 = dot3(d, d);
-            if (r2 < S.lj_rc2) F = F + wca_coef(r2, S.lj_eps, S.lj_sig2) * d;
+        const uint16_t *lst = sm.nbr + pl * NBR_CAP;
+        for (int k = lt; k < nn; k += 2 * T) {
+            const bool two = k + T < nn;
+            const int q0 = lst[k];
+            const int q1 = two ? (int)lst[k + T] : q0;
+            const float4 h0 = ph[q0], l0 = plo[q0], h1 = ph[q1], l1 = plo[q1];
+            const float3 d0 = make_float3(ff_diff(mh.x, ml.x, h0.x, l0.x, fnx, S.inx), ff_diff(mh.y, ml.y, h0.y, l0.y, fny, S.iny),
+                                          ff_diff(mh.z, ml.z, h0.z, l0.z, fnz, S.inz));
+            const float3 d1 = make_float3(ff_diff(mh.x, ml.x, h1.x, l1.x, fnx, S.inx), ff_diff(mh.y, ml.y, h1.y, l1.y, fny, S.iny),
+                                          ff_diff(mh.z, ml.z, h1.z, l1.z, fnz, S.inz));
+            const float r20 = dot3(d0, d0), r21 = dot3(d1, d1);
+            const float c0 = r20 < S.lj_rc2 ? wca_coef(r20, S.lj_eps, S.lj_sig2) : 0.0f;
+            const float c1 = (two && r21 < S.lj_rc2) ? wca_coef(r21, S.lj_eps, S.lj_sig2) : 0.0f;
+            F = F + c0 * d0 + c1 * d1;
         }
     }
-    if (t_wall) {
+    {
         const int nw = sm.nw[pl];
-        for (int k = lt; k < nw; k += T) {
-            const uint32_t pk = sm.wal[pl * WALL_CAP + k];
-            const float X = (float)(pk & 0xfffu), Y = (float)((pk >> 12) & 0x3ffu), Z = (float)(pk >> 22);
-            const float3 d = make_float3(ff_diff(mh.x, ml.x, X, 0.f, fnx, S.inx), ff_diff(mh.y, ml.y, Y, 0.f, fny, S.iny),
-                                         ff_diff(mh.z, ml.z, Z, 0.f, fnz, S.inz));
-            const float r2 = dot3(d, d);
-            if (r2 < S.wall_rc2) F = F + wca_coef(r2, S.wall_eps, S.wall_sig2) * d;
+        const uint32_t *wl = sm.wal + pl * WALL_CAP;
+        for (int k = lt; k < nw; k += 2 * T) {
+            const bool two = k + T < nw;
+            const uint32_t p0 = wl[k];
+            const uint32_t p1 = two ? wl[k + T] : p0;
+            const float3 d0 = make_float3(ff_diff(mh.x, ml.x, (float)(p0 & 0xfffu), 0.f, fnx, S.inx),
+                                          ff_diff(mh.y, ml.y, (float)((p0 >> 12) & 0x3ffu), 0.f, fny, S.iny),
+                                          ff_diff(mh.z, ml.z, (float)(p0 >> 22), 0.f, fnz, S.inz));
+            const float3 d1 = make_float3(ff_diff(mh.x, ml.x, (float)(p1 & 0xfffu), 0.f, fnx, S.inx),
+                                          ff_diff(mh.y, ml.y, (float)((p1 >> 12) & 0x3ffu), 0.f, fny, S.iny),
+                                          ff_diff(mh.z, ml.z, (float)(p1 >> 22), 0.f, fnz, S.inz));
+            const float r20 = dot3(d0, d0), r21 = dot3(d1, d1);
+            const float c0 = r20 < S.wall_rc2 ? wca_coef(r20, S.wall_eps, S.wall_sig2) : 0.0f;
+            const float c1 = (two && r21 < S.wall_rc2) ? wca_coef(r21, S.wall_eps, S.wall_sig2) : 0.0f;
+            F = F + c0 * d0 + c1 * d1;
         }
     }
     return F;
@@ -617,18 +632,18 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
                 }
                 const float3 dd = ffsub(mh, ml, bh, bl);
                 const bool moved = dot3(dd, dd) > S.skin_half2;
-                if (lt == 0) {
-                    if (C > 1) {
-                        for (int c = 0; c < C; ++c) {
-                            *cl.map_shared_rank(sm.ph[nb] + p, c) = mh;
-                            *cl.map_shared_rank(sm.pl[nb] + p, c) = ml;
-                            if (moved) *cl.map_shared_rank(&s_flag[t & 1], c) = 1;
-                        }
-                    } else {
-                        sm.ph[nb][p] = mh;
-                        sm.pl[nb][p] = ml;
-                        if (moved) s_flag[t & 1] = 1;
+                // the T lanes of a bead hold the same position; they share
+                // the writes to the C replicas of the cluster
+                if (C > 1) {
+                    for (int c = lt; c < C; c += T) {
+                        *cl.map_shared_rank(sm.ph[nb] + p, c) = mh;
+                        *cl.map_shared_rank(sm.pl[nb] + p, c) = ml;
+                        if (moved) *cl.map_shared_rank(&s_flag[t & 1], c) = 1;
                     }
+                } else if (lt == 0) {
+                    sm.ph[nb][p] = mh;
+                    sm.pl[nb][p] = ml;
+                    if (moved) s_flag[t & 1] = 1;
                 }
             }
             sync_all(cl, C);

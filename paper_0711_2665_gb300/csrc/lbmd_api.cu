@@ -24,7 +24,7 @@ constexpr double SKIN = 0.8;  // Verlet-list skin (lattice units)
 
 struct Layout {
     size_t popA, popB, staging, link, wallmask, tileflag, solid, G, stamp;
-    size_t r_hi, r_lo, v, up, J, pair_node, pair_w, bead_real, bead_off, partial, ring, obs, ctrl, rdone, phase, total;
+    size_t r_hi, r_lo, v, up, J, pair_node, pair_w, bead_real, bead_off, partial, ring, obs, ctrl, rdone, loopc, phase, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -53,6 +53,8 @@ struct lbmd_handle {
     int graph_steps = 0;
     cudaGraphExec_t gexec = nullptr;
     void *graph_A = nullptr;  // population buffer that was "A" when the graph was captured
+    cudaGraphExec_t lexec = nullptr;  // device-side loop of two-step bodies (lbmd_step_loop)
+    void *loop_A = nullptr;
     bool capturing = false;
     bool profiling = false;
     std::vector<ProfRec> pending;
@@ -148,6 +150,7 @@ Layout layout_of(const lbmd_config *c, int total_beads) {
     L.obs = take((size_t)c->n_real * sizeof(lbmd_obs));
     L.ctrl = take(sizeof(Ctrl));
     L.rdone = take((size_t)c->n_real * 2 * sizeof(unsigned int));
+    L.loopc = take(sizeof(unsigned int));
     L.phase = take(PHASES * sizeof(unsigned long long));
     L.total = o;
     return L;
@@ -236,6 +239,68 @@ void drop_graph(lbmd_handle *h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     h->gexec = nullptr;
     h->graph_A = nullptr;
+    if (h->lexec) cudaGraphExecDestroy(h->lexec);
+    h->lexec = nullptr;
+    h->loop_A = nullptr;
+}
+
+// One tick of the device-side step loop: the body of two steps has run once
+// more; the loop goes on while bodies remain.
+__global__ void k_loop_tick(cudaGraphConditionalHandle hdl, unsigned int *remaining) {
+    const unsigned int r = *remaining - 1u;
+    *remaining = r;
+    cudaGraphSetConditional(hdl, r > 0u ? 1u : 0u);
+}
+
+__global__ void k_set_u32(unsigned int *p, unsigned int v) { *p = v; }
+
+// Graph holding one conditional WHILE node whose body is two coupled steps
+// (A -> B -> A, so the buffers line up again) followed by the tick kernel.
+// The condition starts at 1 on every launch, so one launch runs
+// 2 * (*loopc) steps for *loopc >= 1.
+lbmd_status capture_loop(lbmd_handle *h) {
+    if (h->lexec) cudaGraphExecDestroy(h->lexec);
+    h->lexec = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphCreate");
+    cudaGraphConditionalHandle hdl;
+    e = cudaGraphConditionalHandleCreate(&hdl, g, 1u, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(h, e, "cudaGraphConditionalHandleCreate"); }
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hdl;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(h, e, "cudaGraphAddNode(conditional)"); }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    void *A0 = h->popA;
+    const long long s0 = h->host_step, l0 = h->launches;
+    h->capturing = true;
+    e = cudaStreamBeginCaptureToGraph(h->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { h->capturing = false; cudaGraphDestroy(g); return cuda_fail(h, e, "cudaStreamBeginCaptureToGraph"); }
+    lbmd_status s = enqueue_step(h);
+    if (s == LBMD_OK) s = enqueue_step(h);
+    if (s == LBMD_OK) {
+        k_loop_tick<<<1, 1, 0, h->st>>>(hdl, (unsigned int *)(h->dbuf + h->L.loopc));
+        if (cudaGetLastError() != cudaSuccess) s = LBMD_ERR_CUDA;
+    }
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(h->st, &captured);
+    h->capturing = false;
+    h->host_step = s0;
+    h->launches = l0;
+    if (s != LBMD_OK || e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return s != LBMD_OK ? s : cuda_fail(h, e, "cudaStreamEndCapture");
+    }
+    e = cudaGraphInstantiate(&h->lexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { h->lexec = nullptr; return cuda_fail(h, e, "cudaGraphInstantiate(loop)"); }
+    h->loop_A = A0;
+    return LBMD_OK;
 }
 
 lbmd_status capture_graph(lbmd_handle *h) {
@@ -533,6 +598,32 @@ lbmd_status lbmd_step(lbmd_handle *h, int64_t n) {
         if (s != LBMD_OK) return s;
         n -= 1;
     }
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_step_loop(lbmd_handle *h, int64_t n) {
+    if (!h || n < 0) return LBMD_ERR_INVALID_ARG;
+    if (!h->st) return fail(h, LBMD_ERR_INVALID_ARG, "graph capture needs a non-default stream");
+    if (h->profiling) return lbmd_step(h, n);
+    if (h->lexec && h->popA != h->loop_A && n > 0) {  // realign A with the captured body
+        lbmd_status s = enqueue_step(h);
+        if (s != LBMD_OK) return s;
+        n -= 1;
+    }
+    const int64_t pairs = n / 2;
+    if (pairs >= 1) {
+        if (pairs > 0xffffffffll) return fail(h, LBMD_ERR_INVALID_ARG, "too many steps for one loop launch");
+        if (!h->lexec) {
+            lbmd_status s = capture_loop(h);
+            if (s != LBMD_OK) return s;
+        }
+        k_set_u32<<<1, 1, 0, h->st>>>((unsigned int *)(h->dbuf + h->L.loopc), (unsigned int)pairs);
+        CK(cudaGetLastError());
+        CK(cudaGraphLaunch(h->lexec, h->st));
+        h->host_step += 2 * pairs;
+        h->launches += 1 + (2LL * (h->total_beads > 0 ? 4 : 3) + 1) * pairs;
+    }
+    if (n & 1) return enqueue_step(h);
     return LBMD_OK;
 }
 

@@ -114,6 +114,7 @@ def lib():
         "lbmd_get_overlap": [vp, P(i32)],
         "lbmd_get_md_shape": [vp, P(i32), P(i32)],
         "lbmd_set_drive": [vp, ctypes.c_double, ctypes.c_double],
+        "lbmd_step_loop": [vp, i64],
         "lbmd_adjoint_required_bytes": [vp, i32, i32, P(sz)],
         "lbmd_adjoint": [vp, i32, i32, vp, sz, vp, vp, vp, vp],
     }
@@ -223,6 +224,10 @@ class Simulation:
     # -- stepping --------------------------------------------------------
     def step(self, n: int = 1):
         self._check(self._lib.lbmd_step(self._h, int(n)), "lbmd_step")
+
+    def step_loop(self, n: int):
+        """n steps in one launch of the device-side step loop (lbmd_step_loop)."""
+        self._check(self._lib.lbmd_step_loop(self._h, int(n)), "lbmd_step_loop")
 
     def check(self):
         self._check(self._lib.lbmd_check(self._h), "lbmd_check")
