@@ -191,7 +191,7 @@ def _sc_roofline(sim, w, peak, peak_kind, steps=10):
             "us_per_launch": 1e3 * ms / n}
 
 
-def extra_measurements(dev, stream, peak, peak_kind):
+def extra_measurements(dev, stream, peak, peak_kind, forms, tiles=None):
     """The other forms of the step, each timed on its own workload with CUDA
     events on the library's stream (inputs larger than L2, no flush needed):
     the batched ensemble and the FP16-deviation storage, each run of K steps
@@ -212,10 +212,16 @@ def extra_measurements(dev, stream, peak, peak_kind):
         return a.elapsed_time(b) * 1e-3
 
     for name, K in (("ensemble_fp32", 100), ("fp16dev", 60)):
+        if name not in forms:
+            continue
         w = workloads.get(name)
         inp = workloads.build_inputs(w)
         sim = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"], device=str(dev))
-        by, zc = sim.autotune(3)
+        if tiles:
+            sim.set_tiles(*tiles)
+            by, zc = tiles
+        else:
+            by, zc = sim.autotune(3)
         sim.step_loop(20)  # captures the device-side loop graph
         t = timed(lambda: sim.step_loop(K))
         sites = w["nx"] * w["ny"] * w["nz"] * w["n_real"]
@@ -228,11 +234,16 @@ def extra_measurements(dev, stream, peak, peak_kind):
                      "launch": "one CUDA-graph launch per run (device-side loop of two-step bodies)",
                      "roofline": rf}
         sim.close()
+    if "adjoint" not in forms:
+        return out
     w = workloads.get("adjoint")
     inp = workloads.build_inputs(w)
     K, C = w["steps"], w["checkpoint_every"]
     sim = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"], device=str(dev))
-    sim.autotune(3)
+    if tiles:
+        sim.set_tiles(*tiles)
+    else:
+        sim.autotune(3)
     sim.step(4)
     t_fwd = timed(lambda: sim.step(K))
     sim2 = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"], device=str(dev))
@@ -264,8 +275,10 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true",
-                    help="skip the ensemble, FP16 and adjoint measurements")
+    ap.add_argument("--forms", default="ensemble_fp32,fp16dev,adjoint",
+                    help="comma list of the other forms to measure (ensemble_fp32, fp16dev, adjoint), or none")
+    ap.add_argument("--tiles", type=int, nargs=2, metavar=("BY", "ZC"), default=None,
+                    help="fixed stream-collide tile shape instead of the autotuner (for profiling runs)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -293,7 +306,10 @@ def main():
 
     inp = workloads.build_inputs(w)
     sim = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"], device=f"cuda:{local}")
-    sim.autotune(3)
+    if args.tiles:
+        sim.set_tiles(*args.tiles)
+    else:
+        sim.autotune(3)
     sites = w["nx"] * w["ny"] * w["nz"] * w["n_real"]
     flush = not args.no_flush
     # L2 flush between timed steps: write 256 MiB, then read another 256 MiB so
@@ -388,8 +404,9 @@ def main():
                 "data": "synthetic", "config": dict(_config_block(w, flush), tiles=list(sim.tiles())),
                 "roofline": roofline, "kernels": shares, "gpu_launches": launches,
                 "clocks": clocks, "e2e": e2e}
-        if not args.no_extras and world == 1:
-            line["forms"] = extra_measurements(dev, stream, peak, peak_kind)
+        forms = [f for f in args.forms.split(",") if f and f != "none"]
+        if forms and world == 1:
+            line["forms"] = extra_measurements(dev, stream, peak, peak_kind, forms, args.tiles)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line), flush=True)
