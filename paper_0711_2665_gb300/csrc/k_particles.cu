@@ -257,95 +257,123 @@ MdShape md_shape(const Sim &S) {
 // Part of the conservative force on bead p computed by task lane lt of its
 // T lanes.  Terms: harmonic bonds (Eq. 19); the angular term of the angles at
 // p-1, p, p+1; WCA with the listed beads and solid sites.  The lanes' parts
-// add up to the full force.
+// add up to the full force.  Every lane of the warp must call this (own or
+// not): the list loops run to a warp-uniform trip count.
 template <int T>
 __device__ __forceinline__ float3 force_part(const Sim &S, const PSmem &sm, int buf, bool own, int p, int pl, int N, float4 mh,
-                             float4 ml, int lt) {
+                                             float4 ml, int lt) {
     float3 F = make_float3(0.f, 0.f, 0.f);
-    if (!own) return F;
-    // Every lane runs the same instructions on different data (lanes of a
-    // warp in different branches would run one after another): lane lt takes
-    // bond slot lt, angle slot lt and every T-th list entry from lt.
     const float4 *ph = sm.ph[buf], *plo = sm.pl[buf];
-    const bool m1 = p >= 1, m2 = p >= 2, p1 = p + 1 < N, p2 = p + 2 < N;
-    if (lt < 3) {
-        float4 hm1 = mh, lm1 = ml, hm2 = mh, lm2 = ml, hp1 = mh, lp1 = ml, hp2 = mh, lp2 = ml;
-        if (m1) { hm1 = ph[p - 1]; lm1 = plo[p - 1]; }
-        if (m2) { hm2 = ph[p - 2]; lm2 = plo[p - 2]; }
-        if (p1) { hp1 = ph[p + 1]; lp1 = plo[p + 1]; }
-        if (p2) { hp2 = ph[p + 2]; lp2 = plo[p + 2]; }
-        const float3 b0 = ffsub(hm1, lm1, hm2, lm2);  // r_{p-1} - r_{p-2}
-        const float3 b1 = ffsub(mh, ml, hm1, lm1);    // r_p - r_{p-1}
-        const float3 b2 = ffsub(hp1, lp1, mh, ml);    // r_{p+1} - r_p
-        const float3 b3 = ffsub(hp2, lp2, hp1, lp1);  // r_{p+2} - r_{p+1}
-        // bond slots: 0 = bond to p-1 (force -k(|b1| - r0) b1/|b1|), 1 = bond to p+1.
-        // |b| comes from the correctly rounded sqrt, because |b| - r0 cancels
-        // and keeps only the absolute error of |b|.
-        for (int s = lt; s < 2; s += T) {
-            const float3 b = s == 0 ? b1 : b2;
-            if (s == 0 ? m1 : p1) {
-                const float len = sqrtf(dot3(b, b));
-                const float coef = __fdividef(S.k_bond * (len - S.r0), len);
-                F = F + (s == 0 ? -coef : coef) * b;
+    const int nn = own ? (int)sm.nn[pl] : 0, nw = own ? (int)sm.nw[pl] : 0;
+    const int nn_w = __reduce_max_sync(0xffffffffu, nn), nw_w = __reduce_max_sync(0xffffffffu, nw);
+    if (own) {
+        if constexpr (T >= 3) {
+            // Lane lt (< 3) takes the angle whose beads are a = p+lt-2,
+            // b = p+lt-1, c = p+lt, with u = r_b - r_a and w = r_c - r_b.  Its
+            // share of the force on p (p = c, b, a for lt = 0, 1, 2) is
+            // +A dcos/dw, A (dcos/du - dcos/dw), -A dcos/du.  Lanes 0 and 1 also
+            // take the bond along w (p = c: -k(|w| - r0) w/|w|; p = b: +...).
+            // Straight-line code with selects: the bond and angle chains of a
+            // lane are independent and overlap.
+            const int ia = p + lt - 2, ib = p + lt - 1, ic = p + lt;
+            const bool va = ia >= 0 && ia < N, vb = ib >= 0 && ib < N, vc = ic >= 0 && ic < N;
+            const int ja = va ? ia : p, jb = vb ? ib : p, jc = vc ? ic : p;
+            const float4 ha = ph[ja], la = plo[ja], hb = ph[jb], lb = plo[jb], hc = ph[jc], lc = plo[jc];
+            const float3 u = ffsub(hb, lb, ha, la), w = ffsub(hc, lc, hb, lb);
+            const bool bond_ok = lt < 2 && vb && vc;
+            const bool ang_ok = lt < 3 && va && vb && vc && S.kappa != 0.0f;
+            // |w| from the correctly rounded sqrt: |w| - r0 cancels and keeps
+            // only the absolute error of |w|
+            const float w2 = bond_ok ? dot3(w, w) : 1.0f;
+            const float len = sqrtf(w2);
+            const float bc = __fdividef(S.k_bond * (len - S.r0), len);
+            const float bsign = lt == 0 ? -1.0f : 1.0f;
+            const float3 uu = ang_ok ? u : make_float3(1.f, 0.f, 0.f);
+            const float3 ww = ang_ok ? w : make_float3(0.f, 1.f, 0.f);
+            float3 d1, d2;
+            bend_terms(uu, ww, S.kappa, d1, d2);
+            const float al = lt == 0 ? 0.0f : (lt == 1 ? 1.0f : -1.0f);
+            const float be = lt == 0 ? 1.0f : (lt == 1 ? -1.0f : 0.0f);
+            if (bond_ok) F = F + (bsign * bc) * w;
+            if (ang_ok) F = F + al * d1 + be * d2;
+        } else {
+            const bool m1 = p >= 1, m2 = p >= 2, p1 = p + 1 < N, p2 = p + 2 < N;
+            float4 hm1 = mh, lm1 = ml, hm2 = mh, lm2 = ml, hp1 = mh, lp1 = ml, hp2 = mh, lp2 = ml;
+            if (m1) { hm1 = ph[p - 1]; lm1 = plo[p - 1]; }
+            if (m2) { hm2 = ph[p - 2]; lm2 = plo[p - 2]; }
+            if (p1) { hp1 = ph[p + 1]; lp1 = plo[p + 1]; }
+            if (p2) { hp2 = ph[p + 2]; lp2 = plo[p + 2]; }
+            const float3 b0 = ffsub(hm1, lm1, hm2, lm2);  // r_{p-1} - r_{p-2}
+            const float3 b1 = ffsub(mh, ml, hm1, lm1);    // r_p - r_{p-1}
+            const float3 b2 = ffsub(hp1, lp1, mh, ml);    // r_{p+1} - r_p
+            const float3 b3 = ffsub(hp2, lp2, hp1, lp1);  // r_{p+2} - r_{p+1}
+            // bond slots: 0 = bond to p-1, 1 = bond to p+1
+            for (int s = lt; s < 2; s += T) {
+                const float3 b = s == 0 ? b1 : b2;
+                if (s == 0 ? m1 : p1) {
+                    const float len = sqrtf(dot3(b, b));
+                    const float coef = __fdividef(S.k_bond * (len - S.r0), len);
+                    F = F + (s == 0 ? -coef : coef) * b;
+                }
             }
-        }
-        // angle slots: the angles at p-1, p, p+1 with their share of the force
-        // on p: +A dcos/db2, A (dcos/db1 - dcos/db2), -A dcos/db1
-        if (S.kappa != 0.0f) {
-            for (int s = lt; s < 3; s += T) {
-                const float3 u = s == 0 ? b0 : (s == 1 ? b1 : b2);
-                const float3 w = s == 0 ? b1 : (s == 1 ? b2 : b3);
-                if (s == 0 ? m2 : (s == 1 ? (m1 && p1) : p2)) {
-                    float3 d1, d2;
-                    bend_terms(u, w, S.kappa, d1, d2);
-                    const float al = s == 0 ? 0.0f : (s == 1 ? 1.0f : -1.0f);
-                    const float be = s == 0 ? 1.0f : (s == 1 ? -1.0f : 0.0f);
-                    F = F + al * d1 + be * d2;
+            // angle slots: the angles at p-1, p, p+1
+            if (S.kappa != 0.0f) {
+                for (int s = lt; s < 3; s += T) {
+                    const float3 u = s == 0 ? b0 : (s == 1 ? b1 : b2);
+                    const float3 w = s == 0 ? b1 : (s == 1 ? b2 : b3);
+                    if (s == 0 ? m2 : (s == 1 ? (m1 && p1) : p2)) {
+                        float3 d1, d2;
+                        bend_terms(u, w, S.kappa, d1, d2);
+                        const float al = s == 0 ? 0.0f : (s == 1 ? 1.0f : -1.0f);
+                        const float be = s == 0 ? 1.0f : (s == 1 ? -1.0f : 0.0f);
+                        F = F + al * d1 + be * d2;
+                    }
                 }
             }
         }
     }
     const float fnx = (float)S.nx, fny = (float)S.ny, fnz = (float)S.nz;
-    // Pair and wall lists, two entries per iteration: both entries' shared-
-    // memory loads are issued before either is used, since the loop is bound
-    // by load latency, not by arithmetic.
+    // Pair and wall lists, two entries per iteration, to the warp's longest
+    // list: both entries' shared-memory loads are issued before either is
+    // used, and no lane branches away (entries past a lane's own list point
+    // at the bead itself and are selected out).
     {
-        const int nn = sm.nn[pl];
-        const uint16_t *lst = sm.nbr + pl * NBR_CAP;
-        for (int k = lt; k < nn; k += 2 * T) {
-            const bool two = k + T < nn;
-            const int q0 = lst[k];
-            const int q1 = two ? (int)lst[k + T] : q0;
+        const uint16_t *lst = sm.nbr + (own ? pl : 0) * NBR_CAP;
+        const int pself = own ? p : 0;  // a bead of the replica for lanes without one
+        for (int k = lt; k < nn_w; k += 2 * T) {
+            const bool v0 = k < nn, v1 = k + T < nn;
+            const int q0 = v0 ? (int)lst[k] : pself;
+            const int q1 = v1 ? (int)lst[k + T] : pself;
             const float4 h0 = ph[q0], l0 = plo[q0], h1 = ph[q1], l1 = plo[q1];
             const float3 d0 = make_float3(ff_diff(mh.x, ml.x, h0.x, l0.x, fnx, S.inx), ff_diff(mh.y, ml.y, h0.y, l0.y, fny, S.iny),
                                           ff_diff(mh.z, ml.z, h0.z, l0.z, fnz, S.inz));
             const float3 d1 = make_float3(ff_diff(mh.x, ml.x, h1.x, l1.x, fnx, S.inx), ff_diff(mh.y, ml.y, h1.y, l1.y, fny, S.iny),
                                           ff_diff(mh.z, ml.z, h1.z, l1.z, fnz, S.inz));
-            const float r20 = dot3(d0, d0), r21 = dot3(d1, d1);
+            const float r20 = v0 ? dot3(d0, d0) : 1e30f, r21 = v1 ? dot3(d1, d1) : 1e30f;
             const float c0 = r20 < S.lj_rc2 ? wca_coef(r20, S.lj_eps, S.lj_sig2) : 0.0f;
-            const float c1 = (two && r21 < S.lj_rc2) ? wca_coef(r21, S.lj_eps, S.lj_sig2) : 0.0f;
+            const float c1 = r21 < S.lj_rc2 ? wca_coef(r21, S.lj_eps, S.lj_sig2) : 0.0f;
             F = F + c0 * d0 + c1 * d1;
         }
     }
     {
-        const int nw = sm.nw[pl];
-        const uint32_t *wl = sm.wal + pl * WALL_CAP;
-        for (int k = lt; k < nw; k += 2 * T) {
-            const bool two = k + T < nw;
-            const uint32_t p0 = wl[k];
-            const uint32_t p1 = two ? wl[k + T] : p0;
+        const uint32_t *wl = sm.wal + (own ? pl : 0) * WALL_CAP;
+        for (int k = lt; k < nw_w; k += 2 * T) {
+            const bool v0 = k < nw, v1 = k + T < nw;
+            const uint32_t p0 = v0 ? wl[k] : 0u;
+            const uint32_t p1 = v1 ? wl[k + T] : 0u;
             const float3 d0 = make_float3(ff_diff(mh.x, ml.x, (float)(p0 & 0xfffu), 0.f, fnx, S.inx),
                                           ff_diff(mh.y, ml.y, (float)((p0 >> 12) & 0x3ffu), 0.f, fny, S.iny),
                                           ff_diff(mh.z, ml.z, (float)(p0 >> 22), 0.f, fnz, S.inz));
             const float3 d1 = make_float3(ff_diff(mh.x, ml.x, (float)(p1 & 0xfffu), 0.f, fnx, S.inx),
                                           ff_diff(mh.y, ml.y, (float)((p1 >> 12) & 0x3ffu), 0.f, fny, S.iny),
                                           ff_diff(mh.z, ml.z, (float)(p1 >> 22), 0.f, fnz, S.inz));
-            const float r20 = dot3(d0, d0), r21 = dot3(d1, d1);
+            const float r20 = v0 ? dot3(d0, d0) : 1e30f, r21 = v1 ? dot3(d1, d1) : 1e30f;
             const float c0 = r20 < S.wall_rc2 ? wca_coef(r20, S.wall_eps, S.wall_sig2) : 0.0f;
-            const float c1 = (two && r21 < S.wall_rc2) ? wca_coef(r21, S.wall_eps, S.wall_sig2) : 0.0f;
+            const float c1 = r21 < S.wall_rc2 ? wca_coef(r21, S.wall_eps, S.wall_sig2) : 0.0f;
             F = F + c0 * d0 + c1 * d1;
         }
     }
+    if (!own) F = make_float3(0.f, 0.f, 0.f);
     return F;
 }
 
@@ -531,7 +559,7 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
     extern __shared__ __align__(16) char smem_raw[];
     __shared__ int s_flag[2], s_err;
     __shared__ double red[16][9];
-    __shared__ double cpart[8][9];
+    __shared__ double cpart[MAX_CLUSTER][9];
     PSmem sm;
     psmem_layout(Nmax, Nc, &sm, smem_raw);
     cg::cluster_group cl = cg::this_cluster();
@@ -730,6 +758,10 @@ template <int T>
 static cudaError_t launch_particles_t(const Sim &S, const MdShape &m, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(k_particles<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m.smem);
     if (e != cudaSuccess) return e;
+    if (m.C > 8) {  // clusters above the portable size of 8 are opt-in
+        e = cudaFuncSetAttribute(k_particles<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(S.n_real * m.C);
     cfg.blockDim = dim3(m.threads);

@@ -1017,12 +1017,12 @@ lbmd_status lbmd_set_tiles(lbmd_handle *h, int32_t by, int32_t zc) {
 }
 
 lbmd_status lbmd_set_md_shape(lbmd_handle *h, int32_t T, int32_t C) {
-    if (!h || !(T == 0 || T == 1 || T == 2 || T == 4 || T == 8) || C < 0 || C > 8) return LBMD_ERR_INVALID_ARG;
+    if (!h || !(T == 0 || T == 1 || T == 2 || T == 4 || T == 8) || C < 0 || C > MAX_CLUSTER) return LBMD_ERR_INVALID_ARG;
     Sim trial = h->S;
     trial.md_T = T;
     trial.md_C = C;
     const MdShape m = md_shape(trial);
-    if (m.threads > 512 || m.C < 1 || m.C > 8 || m.smem > 200 * 1024)
+    if (m.threads > 512 || m.C < 1 || m.C > MAX_CLUSTER || m.smem > 200 * 1024)
         return fail(h, LBMD_ERR_INVALID_ARG, "particle-kernel shape needs more than 512 threads per block");
     if (T != h->S.md_T || C != h->S.md_C) drop_graph(h);
     h->S.md_T = T;

@@ -61,6 +61,7 @@ constexpr double FIX_SCALE = 1099511627776.0;  // 2^40
 constexpr float FIX_SCALE_F = 1099511627776.0f;
 constexpr float FIX_INV_SCALE_F = 1.0f / 1099511627776.0f;
 
+constexpr int MAX_CLUSTER = 16;  // blocks per chain (above 8: non-portable cluster size)
 constexpr int NBR_CAP = 32;     // bead-bead neighbours per bead
 constexpr int WALL_CAP = 12;    // solid sites within the wall-list radius per bead
 constexpr int HASH_SIZE = 2048; // cell hash slots (>= 2 * max beads per realization)
