@@ -588,12 +588,18 @@ __global__ void __launch_bounds__(256) k_adj_fixup(const Sim S, const float *__r
     const float lu_u = dot3f(lu, u);
     const int x = s % S.nx, y = (s / S.nx) % S.ny, z = s / (S.nx * S.ny);
     const uint32_t lm = __ldg(S.link + s);
+    uint32_t idx[Q];
+    float old[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {  // all loads before any store (one L2 round trip)
+        const uint32_t src = (uint32_t)(wrapi(x - cx(i), S.nx) + S.nx * (wrapi(y - cy(i), S.ny) + S.ny * wrapi(z - cz(i), S.nz)));
+        idx[i] = ((lm >> i) & 1u) ? (uint32_t)opp(i) * S.ps + (uint32_t)s : (uint32_t)i * S.ps + src;
+        old[i] = __ldcg(Lo + idx[i]);
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const float dl = ((float)cx(i) * lu.x + (float)cy(i) * lu.y + (float)cz(i) * lu.z - lu_u) * ir;
-        const uint32_t src = (uint32_t)(wrapi(x - cx(i), S.nx) + S.nx * (wrapi(y - cy(i), S.ny) + S.ny * wrapi(z - cz(i), S.nz)));
-        const uint32_t idx = ((lm >> i) & 1u) ? (uint32_t)opp(i) * S.ps + (uint32_t)s : (uint32_t)i * S.ps + src;
-        Lo[idx] += dl;
+        Lo[idx[i]] = old[i] + dl;
     }
 }
 

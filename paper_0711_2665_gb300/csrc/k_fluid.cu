@@ -268,11 +268,15 @@ __global__ void __launch_bounds__(256) k_source(const Sim S, void *__restrict__ 
             const float G2 = (float)(long long)Gr[2 * ns] * FIX_INV_SCALE_F;
             Gr[0] = 0ull; Gr[ns] = 0ull; Gr[2 * ns] = 0ull;
             T *B = reinterpret_cast<T *>(Bv) + (size_t)r * Q * S.ps;
+            // all 19 loads first: loads and stores through one pointer would
+            // otherwise run one L2 round trip after another
+            float h[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) h[i] = load_dev_cg(B, (uint32_t)i * (uint32_t)S.ps + (uint32_t)s);
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const float src = 3.0f * wq(i) * ((float)cx(i) * G0 + (float)cy(i) * G1 + (float)cz(i) * G2);
-                const uint32_t idx = (uint32_t)i * (uint32_t)S.ps + (uint32_t)s;
-                store_dev(B, idx, load_dev_cg(B, idx) + src);
+                store_dev(B, (uint32_t)i * (uint32_t)S.ps + (uint32_t)s, h[i] + src);
             }
         }
     }
