@@ -38,21 +38,26 @@ __device__ __forceinline__ Du operator+(Du a, Du b) { return Du{a.v + b.v, a.d +
 __device__ __forceinline__ Du operator-(Du a, Du b) { return Du{a.v - b.v, a.d - b.d}; }
 __device__ __forceinline__ Du operator*(Du a, Du b) { return Du{a.v * b.v, a.d * b.v + a.v * b.d}; }
 __device__ __forceinline__ Du operator*(float s, Du a) { return Du{s * a.v, s * a.d}; }
+// The tangents feed a first-order sensitivity; fast reciprocals and square
+// roots (relative error ~1e-7) are ample for it.
 __device__ __forceinline__ Du operator/(Du a, Du b) {
-    const float q = a.v / b.v;
-    return Du{q, (a.d - q * b.d) / b.v};
+    const float ib = __frcp_rn(b.v);
+    const float q = a.v * ib;
+    return Du{q, (a.d - q * b.d) * ib};
 }
 __device__ __forceinline__ Du dsqrt(Du a) {
-    const float s = sqrtf(a.v);
-    return Du{s, 0.5f * a.d / s};
+    const float r = rsqrtf(a.v);
+    const float s = a.v * r;
+    return Du{s, 0.5f * a.d * r};
 }
 __device__ __forceinline__ Du drsqrt(Du a) {
     const float r = rsqrtf(a.v);
     return Du{r, -0.5f * a.d * r * r * r};
 }
-// atan2(y, x): d = (x dy - y dx) / (x^2 + y^2)
+// atan2(y, x) for y >= 0 (the angle of the angular term): value from the
+// forward kernel's polynomial, d = (x dy - y dx) / (x^2 + y^2)
 __device__ __forceinline__ Du datan2(Du y, Du x) {
-    return Du{atan2f(y.v, x.v), (x.v * y.d - y.v * x.d) / (x.v * x.v + y.v * y.v)};
+    return Du{atan_pos(y.v, x.v), (x.v * y.d - y.v * x.d) * __frcp_rn(x.v * x.v + y.v * y.v)};
 }
 
 struct Du3 {
@@ -108,80 +113,111 @@ __device__ __forceinline__ void bend_dual(Du3 b1, Du3 b2, float kappa, Du3 &D1, 
 // tangent of coef(r2) d for the WCA force coef(r2) d, coef = 24 eps (2 s^12/r^14 - s^6/r^8)
 __device__ __forceinline__ float3 wca_tangent(float3 d, float3 dd, float eps, float sig2) {
     const float r2 = dot3f(d, d);
-    const float ir2 = 1.0f / r2, sr2 = sig2 * ir2;
+    const float ir2 = __frcp_rn(r2), sr2 = sig2 * ir2;
     const float sr6 = sr2 * sr2 * sr2;
     const float coef = 24.0f * eps * (2.0f * sr6 * sr6 - sr6) * ir2;
     const float dcoef = 24.0f * eps * (-14.0f * sr6 * sr6 + 4.0f * sr6) * ir2 * ir2 * (2.0f * dot3f(d, dd));
     return add3(mul3(dcoef, d), mul3(coef, dd));
 }
 
-// Pair list of bead p for one outer MD step (ADJ_NBR_CAP entries; a count of
-// ADJ_ALL_PAIRS means the list overflowed and every bead is a candidate).
-constexpr int ADJ_NBR_CAP = 48;
+// Pair list of one lane of bead p for one outer MD step: the beads q with
+// q % T == lt within the list radius (ADJ_LANE_CAP entries; a count of
+// ADJ_ALL_PAIRS means the list overflowed and every bead of the lane's
+// residue class is a candidate).
+constexpr int ADJ_LANE_CAP = 16;
 constexpr int ADJ_ALL_PAIRS = 0xffff;
+// Wall list of one lane: packed solid-site coordinates x | y << 12 | z << 22
+// (ADJ_WALL_CAP entries; ADJ_ALL_PAIRS: take the lane's share of the 4x4x4
+// box mask at every evaluation).
+constexpr int ADJ_WALL_CAP = 8;
 
-__device__ __forceinline__ float3 force_tangent(const Sim &S, const float4 *__restrict__ sh, const float4 *__restrict__ sl,
-                                const float4 *__restrict__ sw, int p, int N, const uint16_t *__restrict__ lst,
-                                int nl) {
+// Lane lt's part of the tangent of the conservative force on bead p along the
+// displacement field w (positions hi/lo and w of the chain in shared memory):
+// sum over its terms of dF_p/dr_q w_q.  Terms as in the forward kernel: the
+// bonded triples (a, b, c) = (p+s-2, p+s-1, p+s) for s = lt, lt+T, .. < 3 with
+// the angle at b and, for s < 2, the bond b-c (Eq. 19); WCA with the lane's
+// listed beads (|p - q| >= 2, minimum image) and with every T-th solid site of
+// the 4x4x4 box around the bead's cell (Eq. 14).
+template <int T>
+__device__ __forceinline__ float3 force_tangent_part(const Sim &S, const float4 *__restrict__ sh, const float4 *__restrict__ sl,
+                                                     const float4 *__restrict__ sw, int p, int N, int lt,
+                                                     const uint16_t *__restrict__ lst, int nl,
+                                                     const uint32_t *__restrict__ wlst, int nwl) {
     const float4 mh = sh[p], ml = sl[p];
     const float3 wp = f3(sw[p]);
-    float3 T = make_float3(0.f, 0.f, 0.f);
-    const bool m1 = p >= 1, m2 = p >= 2, p1 = p + 1 < N, p2 = p + 2 < N;
-    // bonded neighbours p-2 .. p+2 (unused ones alias p and are never read)
-    auto rel = [&](int q) { return du3(ffsub3(sh[q], sl[q], mh, ml), sub3(f3(sw[q]), wp)); };  // r_q - r_p
-    const Du3 zero = Du3{du(0.f), du(0.f), du(0.f)};
-    const Du3 dm1 = m1 ? rel(p - 1) : zero, dm2 = m2 ? rel(p - 2) : zero;
-    const Du3 dp1 = p1 ? rel(p + 1) : zero, dp2 = p2 ? rel(p + 2) : zero;
-    const Du3 b1 = zero - dm1;  // r_p - r_{p-1}
-    const Du3 b2 = dp1;         // r_{p+1} - r_p
-    const Du3 b0 = dm1 - dm2;   // r_{p-1} - r_{p-2}
-    const Du3 b3 = dp2 - dp1;   // r_{p+2} - r_{p+1}
-    // bonds: F_p += -k (|b1| - r0) b1 / |b1| + k (|b2| - r0) b2 / |b2|
-    if (m1) {
-        const Du len = dsqrt(ddot(b1, b1));
-        const Du coef = du(S.k_bond) - (S.k_bond * S.r0) * (du(1.f) / len);
-        T = sub3(T, tangent(coef * b1));
+    float3 Tn = make_float3(0.f, 0.f, 0.f);
+    for (int s = lt; s < 3; s += T) {
+        const int ia = p + s - 2, ib = p + s - 1, ic = p + s;
+        const bool bond_ok = s < 2 && ib >= 0 && ic < N;
+        const bool ang_ok = ia >= 0 && ic < N && S.kappa != 0.0f;
+        if (!bond_ok && !ang_ok) continue;
+        const int ja = ia >= 0 ? ia : ib;  // ia < 0 only when the angle is unused
+        const Du3 u = du3(ffsub3(sh[ib], sl[ib], sh[ja], sl[ja]), sub3(f3(sw[ib]), f3(sw[ja])));  // r_b - r_a
+        const Du3 w = du3(ffsub3(sh[ic], sl[ic], sh[ib], sl[ib]), sub3(f3(sw[ic]), f3(sw[ib])));  // r_c - r_b
+        if (bond_ok) {  // p = c (s = 0): -k(|w| - r0) w/|w|;  p = b (s = 1): +...
+            const Du len = dsqrt(ddot(w, w));
+            const Du coef = du(S.k_bond) - (S.k_bond * S.r0) * (du(1.f) / len);
+            const float3 t = tangent(coef * w);
+            Tn = s == 0 ? sub3(Tn, t) : add3(Tn, t);
+        }
+        if (ang_ok) {  // share of the angle at b on p = c, b, a: +D2, D1 - D2, -D1
+            Du3 D1, D2;
+            bend_dual(u, w, S.kappa, D1, D2);
+            if (s == 0) Tn = add3(Tn, tangent(D2));
+            else if (s == 1) Tn = add3(Tn, tangent(D1 - D2));
+            else Tn = sub3(Tn, tangent(D1));
+        }
     }
-    if (p1) {
-        const Du len = dsqrt(ddot(b2, b2));
-        const Du coef = du(S.k_bond) - (S.k_bond * S.r0) * (du(1.f) / len);
-        T = add3(T, tangent(coef * b2));
-    }
-    // angular term: angle (b0, b1) at p-1 adds D2; (b1, b2) at p adds D1 - D2;
-    // (b2, b3) at p+1 adds -D1
-    if (S.kappa != 0.0f) {
-        Du3 D1, D2;
-        if (m2) { bend_dual(b0, b1, S.kappa, D1, D2); T = add3(T, tangent(D2)); }
-        if (m1 && p1) { bend_dual(b1, b2, S.kappa, D1, D2); T = add3(T, tangent(D1 - D2)); }
-        if (p2) { bend_dual(b2, b3, S.kappa, D1, D2); T = sub3(T, tangent(D1)); }
-    }
-    // WCA with the non-bonded beads of the list (or all of them)
     const float fnx = (float)S.nx, fny = (float)S.ny, fnz = (float)S.nz;
     const bool all = nl == ADJ_ALL_PAIRS;
-    const int nq = all ? N : nl;
+    const int nq = all ? (N - lt + T - 1) / T : nl;
     for (int k = 0; k < nq; ++k) {
-        const int q = all ? k : (int)lst[k];
+        const int q = all ? lt + k * T : (int)lst[k];
         if (q >= p - 1 && q <= p + 1) continue;
         const float4 qh = sh[q], ql = sl[q];
         const float3 d = make_float3(ff_diff(mh.x, ml.x, qh.x, ql.x, fnx, S.inx), ff_diff(mh.y, ml.y, qh.y, ql.y, fny, S.iny),
                                      ff_diff(mh.z, ml.z, qh.z, ql.z, fnz, S.inz));
-        if (dot3f(d, d) < S.lj_rc2) T = add3(T, wca_tangent(d, sub3(wp, f3(sw[q])), S.lj_eps, S.lj_sig2));
+        if (dot3f(d, d) < S.lj_rc2) Tn = add3(Tn, wca_tangent(d, sub3(wp, f3(sw[q])), S.lj_eps, S.lj_sig2));
     }
-    // WCA with the solid sites of the 4x4x4 box around the bead's cell (it
-    // holds every site within the cut-off, which is below 2)
+    if (nwl != ADJ_ALL_PAIRS) {  // the lane's listed solid sites
+        for (int k = 0; k < nwl; ++k) {
+            const uint32_t pk = wlst[k];
+            const float3 d = make_float3(ff_diff(mh.x, ml.x, (float)(pk & 0xfffu), 0.f, fnx, S.inx),
+                                         ff_diff(mh.y, ml.y, (float)((pk >> 12) & 0x3ffu), 0.f, fny, S.iny),
+                                         ff_diff(mh.z, ml.z, (float)(pk >> 22), 0.f, fnz, S.inz));
+            if (dot3f(d, d) < S.wall_rc2) Tn = add3(Tn, wca_tangent(d, wp, S.wall_eps, S.wall_sig2));
+        }
+        return Tn;
+    }
+    // solid sites of the 4x4x4 box around the bead's cell (it holds every
+    // site within the cut-off, which is below 2); lane lt takes every T-th
     const float xw = ff_wrap(mh.x, ml.x, fnx, S.inx), yw = ff_wrap(mh.y, ml.y, fny, S.iny), zw = ff_wrap(mh.z, ml.z, fnz, S.inz);
     const int cx0 = (int)floorf(xw), cy0 = (int)floorf(yw), cz0 = (int)floorf(zw);
     unsigned long long mm = __ldg(S.wallmask + cx0 + S.nx * (cy0 + S.ny * cz0));
-    while (mm) {
+    for (int j = 0; mm; ++j) {
         const int bit = __ffsll((long long)mm) - 1;
         mm &= mm - 1;
+        if (j % T != lt) continue;
         const int X = wrap_any(cx0 + (bit & 3) - 1, S.nx), Y = wrap_any(cy0 + ((bit >> 2) & 3) - 1, S.ny),
                   Z = wrap_any(cz0 + (bit >> 4) - 1, S.nz);
         const float3 d = make_float3(ff_diff(mh.x, ml.x, (float)X, 0.f, fnx, S.inx), ff_diff(mh.y, ml.y, (float)Y, 0.f, fny, S.iny),
                                      ff_diff(mh.z, ml.z, (float)Z, 0.f, fnz, S.inz));
-        if (dot3f(d, d) < S.wall_rc2) T = add3(T, wca_tangent(d, wp, S.wall_eps, S.wall_sig2));
+        if (dot3f(d, d) < S.wall_rc2) Tn = add3(Tn, wca_tangent(d, wp, S.wall_eps, S.wall_sig2));
     }
-    return T;
+    return Tn;
+}
+
+// sum over the T consecutive lanes of a bead (fixed butterfly: every lane
+// gets the same, deterministic sum)
+template <int T>
+__device__ __forceinline__ float3 lane_sum(float3 v) {
+#pragma unroll
+    for (int o = 1; o < T; o <<= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+        v.z += __shfl_xor_sync(0xffffffffu, v.z, o);
+    }
+    return v;
 }
 
 // ---------------------------------------------------------------------------
@@ -344,7 +380,10 @@ __device__ __forceinline__ void block_sum_d(double (&v)[NV], double (*red)[NV]) 
     }
 }
 
-template <int MAXT>
+// One block per chain; T lanes per bead split the corner terms, the bonded
+// triples, the pair list and the wall sites, and hold the bead's adjoint
+// state identically (lane_sum gives every lane the same sums).
+template <int T, int MAXT>
 __global__ void __launch_bounds__(MAXT) k_bead_adjoint(const Sim S, const float *__restrict__ Av, const float *__restrict__ Lin,
                                                        const float4 *__restrict__ trj, float4 *__restrict__ lam_r,
                                                        float4 *__restrict__ lam_v, unsigned long long *__restrict__ LU,
@@ -352,14 +391,17 @@ __global__ void __launch_bounds__(MAXT) k_bead_adjoint(const Sim S, const float 
                                                        const long long step, const int Nmax) {
     extern __shared__ __align__(16) float4 smq[];
     __shared__ double red[32][2];
-    __shared__ float s_dmax;
     float4 *sh = smq, *sl = smq + Nmax, *sw = smq + 2 * Nmax;
-    uint16_t *nbr = reinterpret_cast<uint16_t *>(smq + 3 * Nmax);  // [Nmax][ADJ_NBR_CAP]
+    float *sd = reinterpret_cast<float *>(smq + 3 * Nmax);                 // [Nmax] displacement bound
+    uint32_t *wal = reinterpret_cast<uint32_t *>(sd + ((Nmax + 3) & ~3));  // [Nmax][T][ADJ_WALL_CAP]
+    uint16_t *nbr = reinterpret_cast<uint16_t *>(wal + (size_t)Nmax * T * ADJ_WALL_CAP);  // [Nmax][T][ADJ_LANE_CAP]
     const int r = blockIdx.x;
     const int off = S.bead_off[r];
     const int N = S.bead_off[r + 1] - off;
-    const int p = threadIdx.x;
+    const int lt = threadIdx.x % T;
+    const int p = threadIdx.x / T;
     const bool own = p < N;
+    const bool lead = own && lt == 0;  // the lane that writes the bead's results
     const int g = off + (own ? p : 0);
     const int TB = S.total_beads, M = S.M, Mb = S.Mb;
     const size_t ns = (size_t)S.ns;
@@ -383,14 +425,15 @@ __global__ void __launch_bounds__(MAXT) k_bead_adjoint(const Sim S, const float 
     };
 
     // spread: G(x_k) -= W_k J  =>  lam_J -= W_k lam_G(x_k), lam_r -= dW_k (J . lam_G(x_k)),
-    // with lam_G(x) = sum_i 3 w_i c_i lam_A_i(x) (source of Eq. 9)
+    // with lam_G(x) = sum_i 3 w_i c_i lam_A_i(x) (source of Eq. 9); lane lt
+    // takes the corners k = lt, lt + T, ...
     float3 lJ = make_float3(0.f, 0.f, 0.f), lrw = lJ;
     if (own) {
         Corners cn;
         corners(cn);
         const float3 J = f3(trj[(size_t)traj_slot_J(M, Mb) * TB + g]);
 #pragma unroll 1
-        for (int k = 0; k < 8; ++k) {
+        for (int k = lt; k < 8; k += T) {
             if (cn.W[k] == 0.0f && cn.dW[k].x == 0.0f && cn.dW[k].y == 0.0f && cn.dW[k].z == 0.0f) continue;
             float gx = 0.f, gy = 0.f, gz = 0.f;
 #pragma unroll
@@ -405,6 +448,8 @@ __global__ void __launch_bounds__(MAXT) k_bead_adjoint(const Sim S, const float 
             lrw = sub3(lrw, mul3(dot3f(J, lg), cn.dW[k]));
         }
     }
+    lJ = lane_sum<T>(lJ);
+    lrw = lane_sum<T>(lrw);
 
     // the MD cycle in reverse
     const float dt = 1.0f / (float)M, h = 0.5f * dt;
@@ -431,46 +476,80 @@ __global__ void __launch_bounds__(MAXT) k_bead_adjoint(const Sim S, const float 
         lup = add3(lup, mul3(h * gam, s));
         lv = sub3(mul3(1.0f - h * gam, lv), mul3(h * gam, lJ));
     };
-    // Pair list for the sub-steps of one outer step, from the recorded
-    // positions: every pair closer than the cut-off at any of its sub-steps
-    // is closer than rc + 2 D at its start, D the largest displacement of
-    // any bead during the outer step.
-    int nl = 0;
-    uint16_t *my = nbr + (size_t)(own ? p : 0) * ADJ_NBR_CAP;
+    // Pair lists for the sub-steps of one outer step, from the recorded
+    // positions: a pair closer than the cut-off at any of its sub-steps is
+    // closer than rc + D_p + D_q at its start, D the bead's largest
+    // displacement during the outer step.
+    int nl = 0, nwl = 0;
+    uint16_t *my = nbr + ((size_t)(own ? p : 0) * T + lt) * ADJ_LANE_CAP;
+    uint32_t *myw = wal + ((size_t)(own ? p : 0) * T + lt) * ADJ_WALL_CAP;
+    const float rc = sqrtf(S.lj_rc2);
     auto build_list = [&](int sub) {
-        if (threadIdx.x == 0) s_dmax = 0.0f;
-        __syncthreads();
         float dm = 0.0f;
         const int t0 = sub * Mb;
         if (own) {
             const float4 ah = trj[(size_t)traj_slot_hi(M, Mb, t0) * TB + g], al = trj[(size_t)traj_slot_lo(M, Mb, t0) * TB + g];
-            for (int t = t0 + 1; t <= t0 + Mb; ++t) {
+            for (int t = t0 + 1 + lt; t <= t0 + Mb; t += T) {
                 const float3 d = ffsub3(trj[(size_t)traj_slot_hi(M, Mb, t) * TB + g], trj[(size_t)traj_slot_lo(M, Mb, t) * TB + g], ah, al);
                 dm = fmaxf(dm, dot3f(d, d));
             }
         }
-        // non-negative floats order like their bit patterns
-        atomicMax(reinterpret_cast<int *>(&s_dmax), __float_as_int(sqrtf(dm)));
+#pragma unroll
+        for (int o = 1; o < T; o <<= 1) dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));  // over the bead's lanes
+        if (own && lt == 0) sd[p] = sqrtf(dm) * 1.0001f + 1e-6f;
         load_positions(t0);
         __syncthreads();
-        const float rl = sqrtf(S.lj_rc2) + 2.0f * s_dmax * 1.0001f + 1e-5f;
-        const float rl2 = rl * rl;
         nl = 0;
         if (own) {
             const float4 mh = sh[p], ml = sl[p];
-            for (int q = 0; q < N; ++q) {
+            const float dp = sd[p];
+            for (int q = lt; q < N; q += T) {
                 if (q >= p - 1 && q <= p + 1) continue;
                 const float4 qh = sh[q], ql = sl[q];
                 const float3 d = make_float3(ff_diff(mh.x, ml.x, qh.x, ql.x, fnx, S.inx), ff_diff(mh.y, ml.y, qh.y, ql.y, fny, S.iny),
                                              ff_diff(mh.z, ml.z, qh.z, ql.z, fnz, S.inz));
-                if (dot3f(d, d) < rl2) {
-                    if (nl < ADJ_NBR_CAP) my[nl] = (uint16_t)q;
+                const float rl = rc + dp + sd[q];
+                if (dot3f(d, d) < rl * rl) {
+                    if (nl < ADJ_LANE_CAP) my[nl] = (uint16_t)q;
                     ++nl;
                 }
             }
-            if (nl > ADJ_NBR_CAP) nl = ADJ_ALL_PAIRS;
+            if (nl > ADJ_LANE_CAP) nl = ADJ_ALL_PAIRS;
+            // solid sites closer than rc_w + D_p at the start: the 4x4x4 box of
+            // the start cell holds every site within rc_w of the later
+            // positions while D_p < 0.85 (rc_w < 1.15); else the mask is
+            // walked at every evaluation
+            nwl = 0;
+            if (dp < 0.85f && S.wall_rc2 < 1.3225f) {
+                const float xw = ff_wrap(mh.x, ml.x, fnx, S.inx), yw = ff_wrap(mh.y, ml.y, fny, S.iny),
+                            zw = ff_wrap(mh.z, ml.z, fnz, S.inz);
+                const int cx0 = (int)floorf(xw), cy0 = (int)floorf(yw), cz0 = (int)floorf(zw);
+                unsigned long long mm = __ldg(S.wallmask + cx0 + S.nx * (cy0 + S.ny * cz0));
+                const float rw = sqrtf(S.wall_rc2) + dp;
+                for (int j = 0; mm; ++j) {
+                    const int bit = __ffsll((long long)mm) - 1;
+                    mm &= mm - 1;
+                    if (j % T != lt) continue;
+                    const int X = wrap_any(cx0 + (bit & 3) - 1, S.nx), Y = wrap_any(cy0 + ((bit >> 2) & 3) - 1, S.ny),
+                              Z = wrap_any(cz0 + (bit >> 4) - 1, S.nz);
+                    const float3 d = make_float3(ff_diff(mh.x, ml.x, (float)X, 0.f, fnx, S.inx),
+                                                 ff_diff(mh.y, ml.y, (float)Y, 0.f, fny, S.iny),
+                                                 ff_diff(mh.z, ml.z, (float)Z, 0.f, fnz, S.inz));
+                    if (dot3f(d, d) < rw * rw) {
+                        if (nwl < ADJ_WALL_CAP) myw[nwl] = (uint32_t)X | ((uint32_t)Y << 12) | ((uint32_t)Z << 22);
+                        ++nwl;
+                    }
+                }
+                if (nwl > ADJ_WALL_CAP) nwl = ADJ_ALL_PAIRS;
+            } else {
+                nwl = ADJ_ALL_PAIRS;
+            }
         }
         __syncthreads();
+    };
+    auto tangent_all = [&]() {
+        const float3 part = own ? force_tangent_part<T>(S, sh, sl, sw, p, N, lt, my, nl, myw, nwl) : make_float3(0.f, 0.f, 0.f);
+        return lane_sum<T>(part);
     };
     for (int sub = M - 1; sub >= 0; --sub) {
         build_list(sub);
@@ -481,18 +560,18 @@ __global__ void __launch_bounds__(MAXT) k_bead_adjoint(const Sim S, const float 
         for (int b = Mb - 1; b >= 0; --b) {
             const int t = sub * Mb + b;
             // v' = v_h + hb F(r_{t+1})
-            if (own) sw[p] = make_float4(lv.x, lv.y, lv.z, 0.f);
+            if (lead) sw[p] = make_float4(lv.x, lv.y, lv.z, 0.f);
             __syncthreads();
-            float3 jw = own ? force_tangent(S, sh, sl, sw, p, N, my, nl) : make_float3(0.f, 0.f, 0.f);
+            float3 jw = tangent_all();
             __syncthreads();
             lr = add3(lr, mul3(hb, jw));
             // r_{t+1} = r_t + dtb v_h
             lv = add3(lv, mul3(dtb, lr));
             // v_h = v + hb F(r_t)
             load_positions(t);
-            if (own) sw[p] = make_float4(lv.x, lv.y, lv.z, 0.f);
+            if (lead) sw[p] = make_float4(lv.x, lv.y, lv.z, 0.f);
             __syncthreads();
-            jw = own ? force_tangent(S, sh, sl, sw, p, N, my, nl) : make_float3(0.f, 0.f, 0.f);
+            jw = tangent_all();
             __syncthreads();
             lr = add3(lr, mul3(hb, jw));
         }
@@ -500,17 +579,18 @@ __global__ void __launch_bounds__(MAXT) k_bead_adjoint(const Sim S, const float 
     }
 
     // gather: u_p = sum_k W_k u(x_k)  =>  lam_r += dW_k (u(x_k) . lam_up); lam_u(x_k) += W_k lam_up
+    float3 lrg = make_float3(0.f, 0.f, 0.f);
     if (own) {
         Corners cn;
         corners(cn);
 #pragma unroll 1
-        for (int k = 0; k < 8; ++k) {
+        for (int k = lt; k < 8; k += T) {
             int gnode = -1;
             if (cn.W[k] > 0.0f || cn.dW[k].x != 0.0f || cn.dW[k].y != 0.0f || cn.dW[k].z != 0.0f) {
                 float rho;
                 float3 u;
                 pulled_moments(S, A, cn.node[k], rho, u);
-                lr = add3(lr, mul3(dot3f(u, lup), cn.dW[k]));
+                lrg = add3(lrg, mul3(dot3f(u, lup), cn.dW[k]));
                 if (cn.W[k] > 0.0f) {
                     const size_t b0 = (size_t)r * 3 * ns + (size_t)cn.node[k];
                     atomicAdd(LU + b0, (unsigned long long)__float2ll_rn(cn.W[k] * lup.x * FIX_SCALE_F));
@@ -521,11 +601,14 @@ __global__ void __launch_bounds__(MAXT) k_bead_adjoint(const Sim S, const float 
             }
             adj_node[(size_t)g * 8 + k] = gnode;
         }
-        lr = add3(lr, lrw);
+    }
+    lrg = lane_sum<T>(lrg);
+    if (lead) {
+        lr = add3(add3(lr, lrg), lrw);
         lam_r[g] = make_float4(lr.x, lr.y, lr.z, 0.f);
         lam_v[g] = make_float4(lv.x, lv.y, lv.z, 0.f);
     }
-    double acc[2] = {dg, de};
+    double acc[2] = {lead ? dg : 0.0, lead ? de : 0.0};
     block_sum_d<2>(acc, red);
     if (threadIdx.x == 0) {
         dpar[2 * r] += acc[0];
@@ -533,29 +616,39 @@ __global__ void __launch_bounds__(MAXT) k_bead_adjoint(const Sim S, const float 
     }
 }
 
+// lanes per bead: 4 up to 128 beads, 2 up to 256, 1 above (at most 512
+// threads per block, 128 registers; chains above 512 beads take 1024)
+static int adj_lanes(int nmax) { return nmax <= 128 ? 4 : (nmax <= 256 ? 2 : 1); }
+
 size_t bead_adjoint_smem(const Sim &S) {
     const size_t n = (size_t)max(S.max_beads, 1);
-    return 3 * 16 * n + ((2 * ADJ_NBR_CAP * n + 15) & ~(size_t)15);
+    const size_t T = (size_t)adj_lanes(S.max_beads);
+    return 3 * 16 * n + 4 * ((n + 3) & ~(size_t)3) + 4 * ADJ_WALL_CAP * T * n + ((2 * ADJ_LANE_CAP * T * n + 15) & ~(size_t)15);
 }
 
-template <int MAXT>
+template <int T, int MAXT>
 static cudaError_t launch_bead_adjoint_t(const Sim &S, const float *A, const float *Lin, const float4 *trj, float4 *lam_r,
                                          float4 *lam_v, unsigned long long *LU, int *adj_node, double *dpar, long long step,
                                          cudaStream_t st) {
-    const int threads = max(32, ((S.max_beads + 31) / 32) * 32);
+    const int threads = max(32, ((S.max_beads * T + 31) / 32) * 32);
     const size_t smem = bead_adjoint_smem(S);
-    cudaError_t e = cudaFuncSetAttribute(k_bead_adjoint<MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_bead_adjoint<T, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_bead_adjoint<MAXT><<<S.n_real, threads, smem, st>>>(S, A, Lin, trj, lam_r, lam_v, LU, adj_node, dpar, step,
-                                                          max(S.max_beads, 1));
+    k_bead_adjoint<T, MAXT><<<S.n_real, threads, smem, st>>>(S, A, Lin, trj, lam_r, lam_v, LU, adj_node, dpar, step,
+                                                             max(S.max_beads, 1));
     return cudaGetLastError();
 }
 
 cudaError_t launch_bead_adjoint(const Sim &S, const void *A, const float *Lin, const float4 *trj, float4 *lam_r, float4 *lam_v,
                                 unsigned long long *LU, int *adj_node, double *dpar, long long step, cudaStream_t st) {
     const float *Af = reinterpret_cast<const float *>(A);
-    if (S.max_beads <= 512) return launch_bead_adjoint_t<512>(S, Af, Lin, trj, lam_r, lam_v, LU, adj_node, dpar, step, st);
-    return launch_bead_adjoint_t<1024>(S, Af, Lin, trj, lam_r, lam_v, LU, adj_node, dpar, step, st);
+    switch (adj_lanes(S.max_beads)) {
+    case 4: return launch_bead_adjoint_t<4, 512>(S, Af, Lin, trj, lam_r, lam_v, LU, adj_node, dpar, step, st);
+    case 2: return launch_bead_adjoint_t<2, 512>(S, Af, Lin, trj, lam_r, lam_v, LU, adj_node, dpar, step, st);
+    default:
+        if (S.max_beads <= 512) return launch_bead_adjoint_t<1, 512>(S, Af, Lin, trj, lam_r, lam_v, LU, adj_node, dpar, step, st);
+        return launch_bead_adjoint_t<1, 1024>(S, Af, Lin, trj, lam_r, lam_v, LU, adj_node, dpar, step, st);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -159,28 +159,6 @@ cudaError_t launch_gather(const Sim &S, const void *A, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // conservative (fast) force terms
 // ---------------------------------------------------------------------------
-// atan2(y, x) for y >= 0, branch-free: reduce to t = min/max in [0, 1], then
-// atan(t) = t P(t^2) with P the degree-8 fit of atan(t)/t made by
-// csrc/fit_atan.py (relative error < 1.1e-7 in fp32), then reflect.
-__device__ __forceinline__ float atan_pos(float y, float x) {
-    const float ax = fabsf(x);
-    const float mx = fmaxf(y, ax), mn = fminf(y, ax);
-    const float t = mx > 0.0f ? __fdividef(mn, mx) : 0.0f;
-    const float s = t * t;
-    float p = 2.903541317e-03f;
-    p = fmaf(p, s, -1.628293283e-02f);
-    p = fmaf(p, s, 4.303918779e-02f);
-    p = fmaf(p, s, -7.533655316e-02f);
-    p = fmaf(p, s, 1.065466478e-01f);
-    p = fmaf(p, s, -1.420712918e-01f);
-    p = fmaf(p, s, 1.999305338e-01f);
-    p = fmaf(p, s, -3.333309293e-01f);
-    p = fmaf(p, s, 1.0f);
-    float a = t * p;
-    a = y > ax ? 1.5707963268f - a : a;
-    return x < 0.0f ? 3.1415926536f - a : a;
-}
-
 // angle between b1 and b2 (phi = atan2(|b1 x b2|, b1.b2)), V = kappa phi^2 / 2:
 // d1 = A dcos/db1, d2 = A dcos/db2 with A = kappa phi / sin(phi)
 __device__ __forceinline__ void bend_terms(float3 b1, float3 b2, float kappa, float3 &d1, float3 &d2) {
