@@ -134,30 +134,46 @@ __global__ void __launch_bounds__(512) k_stream_collide(const Sim S, const void 
             if (z >= zend) continue;
             const int zv0 = (z == 0 ? nz - 1 : z - 1), zv2 = (z == nz - 1 ? 0 : z + 1);
             const int s = x + nx * (y + ny * z);
-            const uint32_t lm = S.tileflag[blockIdx.x + S.nxt * (y + ny * z)] ? __ldg(S.link + s) : 0u;
-            lmu[u] = lm;
             su[u] = s;
-            if (lm & SOLID_BIT) continue;
+            // warp-uniform: a flagged tile holds a bounce-back link somewhere
+            if (S.tileflag[blockIdx.x + S.nxt * (y + ny * z)]) {
+                const uint32_t lm = __ldg(S.link + s);
+                lmu[u] = lm;
+                if (lm & SOLID_BIT) continue;
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const int sx = cx(i) == 1 ? xv0 : (cx(i) == -1 ? xv2 : x);
-                const int sy = cy(i) == 1 ? yv0 : (cy(i) == -1 ? yv2 : y);
-                const int sz = cz(i) == 1 ? zv0 : (cz(i) == -1 ? zv2 : z);
-                const uint32_t src = (uint32_t)(sx + nx * (sy + ny * sz));
-                const bool bb = (lm >> i) & 1u;
-                const uint32_t idx = bb ? (uint32_t)opp(i) * ns + (uint32_t)s : (uint32_t)i * ns + src;
-                hh[u][i] = load_dev(A, idx);
+                for (int i = 0; i < Q; ++i) {
+                    const int sx = cx(i) == 1 ? xv0 : (cx(i) == -1 ? xv2 : x);
+                    const int sy = cy(i) == 1 ? yv0 : (cy(i) == -1 ? yv2 : y);
+                    const int sz = cz(i) == 1 ? zv0 : (cz(i) == -1 ? zv2 : z);
+                    const uint32_t src = (uint32_t)(sx + nx * (sy + ny * sz));
+                    const bool bb = (lm >> i) & 1u;
+                    const uint32_t idx = bb ? (uint32_t)opp(i) * ns + (uint32_t)s : (uint32_t)i * ns + src;
+                    hh[u][i] = load_raw(A, idx);
+                }
+            } else {  // no bounce-back in the tile: plain pull
+                lmu[u] = 0u;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const int sx = cx(i) == 1 ? xv0 : (cx(i) == -1 ? xv2 : x);
+                    const int sy = cy(i) == 1 ? yv0 : (cy(i) == -1 ? yv2 : y);
+                    const int sz = cz(i) == 1 ? zv0 : (cz(i) == -1 ? zv2 : z);
+                    hh[u][i] = load_raw(A, (uint32_t)i * ns + (uint32_t)(sx + nx * (sy + ny * sz)));
+                }
             }
           }
+          // arithmetic in stored units (h, or h * 2^12 for FP16): the moments
+          // are scaled once, so no population is (the scale is a power of two:
+          // the results are those of the unscaled formulas)
+          constexpr float up = PopScale<PREC>::up, down = PopScale<PREC>::down;
 #pragma unroll
           for (int u = 0; u < U; ++u) {
             if (lmu[u] & SOLID_BIT) continue;
             const int s = su[u];
             const float *h = hh[u];
-            float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+            float drho_s = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                drho += h[i];
+                drho_s += h[i];
                 if (cx(i) == 1) jx += h[i];
                 if (cx(i) == -1) jx -= h[i];
                 if (cy(i) == 1) jy += h[i];
@@ -165,20 +181,23 @@ __global__ void __launch_bounds__(512) k_stream_collide(const Sim S, const void 
                 if (cz(i) == 1) jz += h[i];
                 if (cz(i) == -1) jz -= h[i];
             }
+            const float drho = drho_s * down;
+            jx *= down; jy *= down; jz *= down;
             if (MODE != 0) { am += drho; ax += jx; ay += jy; az += jz; }
             if (MODE != 2) {
                 const float rho = 1.0f + drho;
                 const float ir = 1.0f / rho;
                 const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
                 const float usq = 1.5f * (ux * ux + uy * uy + uz * uz);
+                const float rho_s = rho * up;
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
                     const float cu = 3.0f * ((float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz);
-                    const float heq = wq(i) * (drho + rho * (cu + 0.5f * cu * cu - usq));
+                    const float heq = wq(i) * (drho_s + rho_s * (cu + 0.5f * cu * cu - usq));
                     float hn = h[i] + om * (heq - h[i]);
                     if (has_g)
-                        hn += 3.0f * wq(i) * ((float)cx(i) * g0 + (float)cy(i) * g1 + (float)cz(i) * g2);
-                    store_dev(B, (uint32_t)i * ns + (uint32_t)s, hn);
+                        hn += up * (3.0f * wq(i) * ((float)cx(i) * g0 + (float)cy(i) * g1 + (float)cz(i) * g2));
+                    store_raw(B, (uint32_t)i * ns + (uint32_t)s, hn);
                 }
             }
           }

@@ -165,6 +165,15 @@ __device__ __forceinline__ float load_dev_cg(const __half *base, uint32_t idx) {
     return __half2float(__ldcg(base + idx)) * FP16_INV_SCALE;
 }
 __device__ __forceinline__ void store_dev(float *base, uint32_t idx, float h) { base[idx] = h; }
+// stored units: h for FP32, h * 2^12 for FP16 (the lattice kernels compute in
+// stored units and scale the moments, so no load or store is multiplied)
+template <int PREC> struct PopScale;
+template <> struct PopScale<0> { static constexpr float up = 1.0f, down = 1.0f; };
+template <> struct PopScale<1> { static constexpr float up = FP16_SCALE, down = FP16_INV_SCALE; };
+__device__ __forceinline__ float load_raw(const float *base, uint32_t idx) { return __ldg(base + idx); }
+__device__ __forceinline__ float load_raw(const __half *base, uint32_t idx) { return __half2float(__ldg(base + idx)); }
+__device__ __forceinline__ void store_raw(float *base, uint32_t idx, float v) { base[idx] = v; }
+__device__ __forceinline__ void store_raw(__half *base, uint32_t idx, float v) { base[idx] = __float2half_rn(v); }
 __device__ __forceinline__ void store_dev(__half *base, uint32_t idx, float h) {
     base[idx] = __float2half_rn(h * FP16_SCALE);
 }
