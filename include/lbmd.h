@@ -80,8 +80,10 @@ typedef struct lbmd_config {
     int32_t md_outer;        /* M, MD steps per LB step (paper: 5) */
     int32_t md_inner;        /* M^b, bonded sub-steps per MD step (paper: 20) */
     int32_t precision;       /* lbmd_precision */
-    int32_t reserved;        /* must be 0 */
-    uint64_t seed;           /* Philox key; realization r uses key word 1 = seed_hi ^ r */
+    int32_t real_base;       /* global index of this handle's first realization (>= 0): realization r
+                                draws its noise as realization real_base + r, so an ensemble split
+                                over several handles (or GPUs) reproduces the unsplit one */
+    uint64_t seed;           /* Philox key; global realization g uses key word 1 = seed_hi ^ g */
 } lbmd_config;
 
 /* Observables of one realization at the current state (Sec. III global

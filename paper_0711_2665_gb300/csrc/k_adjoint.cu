@@ -555,7 +555,7 @@ __global__ void __launch_bounds__(MAXT) k_bead_adjoint(const Sim S, const float 
         build_list(sub);
         load_positions((sub + 1) * Mb);
         float3 xi = make_float3(0.f, 0.f, 0.f);
-        if (own && noisy) xi = mul3(amp, gauss3(S.seed, (uint32_t)r, (uint32_t)p, step, (uint32_t)sub));
+        if (own && noisy) xi = mul3(amp, gauss3(S.seed, S.real_base + (uint32_t)r, (uint32_t)p, step, (uint32_t)sub));
         if (own) kick(2 * sub + 1, xi);
         for (int b = Mb - 1; b >= 0; --b) {
             const int t = sub * Mb + b;

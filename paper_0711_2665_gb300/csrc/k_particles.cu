@@ -615,7 +615,7 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
     if (!own) ff = make_float3(0.f, 0.f, 0.f);
     for (int sub = 0; sub < S.M; ++sub) {
         float3 xi = make_float3(0.f, 0.f, 0.f);
-        if (own && amp > 0.0f) xi = amp * gauss3(S.seed, (uint32_t)r, (uint32_t)p, step, (uint32_t)sub);
+        if (own && amp > 0.0f) xi = amp * gauss3(S.seed, S.real_base + (uint32_t)r, (uint32_t)p, step, (uint32_t)sub);
         if (own) {  // first half kick: field + friction + noise
             const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx, S.inx), ff_wrap(mh.y, ml.y, fny, S.iny),
                                        ff_wrap(mh.z, ml.z, fnz, S.inz));

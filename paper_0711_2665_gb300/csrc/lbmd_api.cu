@@ -93,7 +93,7 @@ bool config_ok(const lbmd_config *c, const int32_t *off, std::string &why) {
     if (!(c->tau > 0.5)) { why = "tau must be > 1/2"; return false; }
     if (c->md_outer < 1 || c->md_inner < 1) { why = "md_outer and md_inner must be >= 1"; return false; }
     if (c->precision != LBMD_FP32 && c->precision != LBMD_FP16DEV) { why = "unknown precision"; return false; }
-    if (c->reserved != 0) { why = "reserved must be 0"; return false; }
+    if (c->real_base < 0 || (double)c->real_base + c->n_real > 4294967295.0) { why = "real_base out of range"; return false; }
     if (c->wall_x < -1 || c->wall_x >= c->nx) { why = "wall_x must be -1 or inside [0, nx)"; return false; }
     if (c->pore_h < 0 || c->pore_h > c->ny || c->pore_h > c->nz) { why = "pore_h out of range"; return false; }
     if (!(c->lj_sigma > 0) || !(c->wall_sigma > 0) || c->lj_eps < 0 || c->wall_eps < 0) { why = "WCA sigma must be > 0, eps >= 0"; return false; }
@@ -481,6 +481,7 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
     S.iny = 1.0f / (float)cfg->ny;
     S.inz = 1.0f / (float)cfg->nz;
     S.n_real = cfg->n_real;
+    S.real_base = (uint32_t)cfg->real_base;
     S.precision = cfg->precision;
     S.omega = (float)(1.0 / cfg->tau);
     for (int a = 0; a < 3; ++a) S.g[a] = (float)cfg->body_force[a];

@@ -83,6 +83,7 @@ struct Sim {
     // lattice
     int nx, ny, nz, ns, nxt, n_real;
     int ps;  // stride between population arrays: ns rounded up to 64
+    uint32_t real_base;  // global index of realization 0 (noise key)
     float inx, iny, inz;     // 1/nx, 1/ny, 1/nz
     int precision;
     float omega;

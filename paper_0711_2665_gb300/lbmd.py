@@ -41,7 +41,7 @@ class Config(ctypes.Structure):
                 ("lj_eps", ctypes.c_double), ("wall_sigma", ctypes.c_double),
                 ("wall_eps", ctypes.c_double), ("E", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("kT", ctypes.c_double), ("md_outer", ctypes.c_int32), ("md_inner", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("real_base", ctypes.c_int32),
                 ("seed", ctypes.c_uint64)]
 
 
@@ -148,7 +148,7 @@ def make_config(w: dict) -> Config:
     c.md_inner = int(w.get("md_inner", 20))
     prec = w.get("precision", "fp32")
     c.precision = FP16DEV if prec in ("fp16dev", FP16DEV) else FP32
-    c.reserved = 0
+    c.real_base = int(w.get("real_base", 0))
     c.seed = int(w.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF
     return c
 
