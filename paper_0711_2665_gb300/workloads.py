@@ -56,7 +56,10 @@ def get(name: str, **overrides) -> dict:
 
 
 def bead_counts(w: dict) -> np.ndarray:
-    """Beads per realization."""
+    """Beads per realization (explicit "bead_counts", a (lo, hi) range drawn
+    per realization, or one count for all)."""
+    if w.get("bead_counts") is not None:
+        return np.asarray(w["bead_counts"], dtype=np.int32)
     nb = w["n_beads"]
     if isinstance(nb, (tuple, list)):
         return inputs.chain_lengths(w["n_real"], nb[0], nb[1], w["chain_seed"])
