@@ -223,8 +223,13 @@ lbmd_status lbmd_get_md_shape(lbmd_handle *h, int32_t *threads_per_bead, int32_t
 lbmd_status lbmd_set_overlap(lbmd_handle *h, int32_t overlap);
 lbmd_status lbmd_get_overlap(lbmd_handle *h, int32_t *overlap);
 
-/* Time every candidate tile shape on the current state (restored afterwards)
- * and keep the fastest.  Synchronises the stream. */
+/* Time every candidate tile shape of the stream-collide kernel on the
+ * current state and keep the fastest; then, unless the caller fixed the
+ * particle-kernel shape with lbmd_set_md_shape, time pseudo-steps (gather,
+ * particle kernel concurrent with the lattice pass) for every admissible
+ * (lanes per bead in {2,4,8}, blocks per chain in {1,2,4,8}) and keep the
+ * fastest.  The state (populations, beads, G, step) is restored afterwards.
+ * Synchronises the stream. */
 lbmd_status lbmd_autotune(lbmd_handle *h, int32_t steps_per_candidate, int32_t *by, int32_t *zc);
 
 /* Per-kernel timing with CUDA events on the launching streams (eager launches

@@ -24,7 +24,7 @@ constexpr double SKIN = 0.8;  // Verlet-list skin (lattice units)
 
 struct Layout {
     size_t popA, popB, staging, link, wallmask, tileflag, solid, G, stamp;
-    size_t r_hi, r_lo, v, up, J, pair_node, pair_w, bead_real, bead_off, partial, ring, obs, ctrl, rdone, loopc, phase, total;
+    size_t r_hi, r_lo, v, up, J, pair_node, pair_w, bead_real, bead_off, partial, ring, obs, ctrl, rdone, loopc, snap, phase, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -50,6 +50,7 @@ struct lbmd_handle {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int by = 8, zc = 8;
     bool overlap = true;  // particle kernel concurrent with the lattice pass
+    bool md_fixed = false;  // particle-kernel shape set by the caller (the autotuner leaves it)
     int graph_steps = 0;
     cudaGraphExec_t gexec = nullptr;
     void *graph_A = nullptr;  // population buffer that was "A" when the graph was captured
@@ -151,6 +152,7 @@ Layout layout_of(const lbmd_config *c, int total_beads) {
     L.ctrl = take(sizeof(Ctrl));
     L.rdone = take((size_t)c->n_real * 2 * sizeof(unsigned int));
     L.loopc = take(sizeof(unsigned int));
+    L.snap = take(nb * 48);  // bead state saved while the autotuner times particle shapes
     L.phase = take(PHASES * sizeof(unsigned long long));
     L.total = o;
     return L;
@@ -1028,6 +1030,7 @@ lbmd_status lbmd_set_md_shape(lbmd_handle *h, int32_t T, int32_t C) {
     if (T != h->S.md_T || C != h->S.md_C) drop_graph(h);
     h->S.md_T = T;
     h->S.md_C = C;
+    h->md_fixed = T != 0 || C != 0;
     return LBMD_OK;
 }
 
@@ -1082,12 +1085,69 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
             h->launches += reps + 1;
             if (ms < best) { best = ms; bb = by; bz = zc; }
         }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
     lbmd_status s = lbmd_set_tiles(h, bb, bz);
+    if (s != LBMD_OK) { cudaEventDestroy(a); cudaEventDestroy(b); return s; }
     if (by_out) *by_out = bb;
     if (zc_out) *zc_out = bz;
-    return s;
+    if (h->total_beads == 0 || h->md_fixed) {  // no chain, or a shape the caller fixed
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        return LBMD_OK;
+    }
+    // Particle-kernel shape: time pseudo-steps (gather, then the particle
+    // kernel concurrent with the lattice pass, as in a step) for every
+    // admissible (lanes per bead, blocks per chain); the bead state is saved
+    // and restored and G cleared, so the state is unchanged.
+    const size_t bb16 = (size_t)h->total_beads * 16;
+    char *snap = h->dbuf + h->L.snap;
+    CK(cudaMemcpyAsync(snap, h->S.r_hi, bb16, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(snap + bb16, h->S.r_lo, bb16, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(snap + 2 * bb16, h->S.v, bb16, cudaMemcpyDeviceToDevice, h->st));
+    static const int TS[] = {2, 4, 8};
+    static const int CS[] = {1, 2, 4, 8};
+    float best_md = 1e30f;
+    int bt = 0, bc = 0;
+    for (int T : TS)
+        for (int C : CS) {
+            Sim trial = h->S;
+            trial.md_T = T;
+            trial.md_C = C;
+            const MdShape m = md_shape(trial);
+            if (m.threads > 512 || m.C != C || m.smem > 200 * 1024) continue;
+            if (C > 1 && C > (h->S.max_beads + 15) / 16) continue;  // blocks of a few beads: barrier-bound
+            float ms = 0.f;
+            for (int pass = 0; pass < 2; ++pass) {  // warm-up pass, then the timed one
+                CK(cudaEventRecord(a, h->st));
+                for (int k = 0; k < reps; ++k) {
+                    CK(launch_gather(trial, h->popA, h->st));
+                    CK(cudaEventRecord(h->ev_fork, h->st));
+                    CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+                    CK(launch_particles(trial, h->popA, h->aux));
+                    CK(cudaEventRecord(h->ev_join, h->aux));
+                    if (!h->overlap) CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
+                    CK(launch_stream_collide(trial, h->popA, h->popB, h->by, h->zc, false, h->st));
+                    CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
+                }
+                CK(cudaEventRecord(b, h->st));
+                CK(cudaEventSynchronize(b));
+                CK(cudaEventElapsedTime(&ms, a, b));
+                h->launches += 3LL * reps;
+            }
+            if (ms < best_md) { best_md = ms; bt = T; bc = C; }
+        }
+    CK(cudaMemcpyAsync(h->S.r_hi, snap, bb16, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(h->S.r_lo, snap + bb16, bb16, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(h->S.v, snap + 2 * bb16, bb16, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemsetAsync(h->S.G, 0, (size_t)h->cfg.n_real * 3 * h->S.ns * 8, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (bt > 0 && (bt != h->S.md_T || bc != h->S.md_C)) {
+        h->S.md_T = bt;
+        h->S.md_C = bc;
+        drop_graph(h);
+    }
+    return LBMD_OK;
 }
 
 lbmd_status lbmd_profile(lbmd_handle *h, int32_t enable) {

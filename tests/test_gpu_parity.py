@@ -165,15 +165,27 @@ def test_graph_eager_and_tiles_are_bit_identical():
 
 
 def test_autotune_keeps_results():
+    """The autotuner (tiles, then particle-kernel shape) leaves the state as it
+    found it, and a run with the tuned shapes equals a run given the same
+    shapes explicitly, bit for bit; a shape fixed by the caller is kept."""
     w = small_workload()
     sim, orc, inp = make_pair(w)
     sim.step(3)
+    before = (sim.get_deviations(), *sim.get_beads(), sim.step_count)
     by, zc = sim.autotune(2)
+    after = (sim.get_deviations(), *sim.get_beads(), sim.step_count)
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
     assert (by, zc) == sim.tiles()
+    shape = sim.md_shape()
     sim.step(3)
     sim2, _, _ = make_pair(w)
+    sim2.set_tiles(by, zc)
+    sim2.set_md_shape(*shape)
     sim2.step(6)
     assert np.array_equal(sim.get_populations(), sim2.get_populations())
+    sim2.autotune(2)
+    assert sim2.md_shape() == shape
 
 
 def test_ensemble_realizations_match_oracle():
