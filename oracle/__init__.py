@@ -58,7 +58,8 @@ class _Params(ctypes.Structure):
                 ("wall_eps", ctypes.c_double), ("E", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("kT", ctypes.c_double),
                 ("md_outer", ctypes.c_int), ("md_inner", ctypes.c_int),
-                ("seed", ctypes.c_uint64), ("realization", ctypes.c_uint32)]
+                ("seed", ctypes.c_uint64), ("realization", ctypes.c_uint32),
+                ("interp", ctypes.c_int), ("integrator", ctypes.c_int), ("lb_kT", ctypes.c_double)]
 
 
 _lib = None
@@ -90,6 +91,7 @@ def lib():
         _lib.orc_step_adjoint.argtypes = [P, P, P, P, P]
         _lib.orc_event_counts.argtypes = [P, P]
         _lib.orc_channel_trace.argtypes = [P, ctypes.c_int, P, ctypes.c_int64]
+        _lib.orc_md_only.argtypes = [P, P, ctypes.c_int]
     return _lib
 
 
@@ -104,7 +106,7 @@ def _f64(a) -> np.ndarray:
 DEFAULTS = dict(tau=1.0, body_force=(0.0, 0.0, 0.0), wall_x=-1, pore_h=3, n_beads=0,
                 k_bond=100.0, r0=1.0, kappa_bend=1.0, lj_sigma=1.0, lj_eps=1.0,
                 wall_sigma=1.0, wall_eps=1.0, E=0.0, gamma=0.1, kT=0.0, md_outer=5,
-                md_inner=20, seed=0, realization=0)
+                md_inner=20, seed=0, realization=0, interp=0, integrator=0, lb_kT=0.0)
 
 
 def tables():
@@ -304,6 +306,12 @@ class OracleSim:
         out = np.zeros(2)
         lib().orc_event_counts(self._h, _vp(out))
         return float(out[0]), float(out[1])
+
+    def md_only(self, up, n: int = 1):
+        """n MD cycles with the fluid velocity at the beads held at up [N, 3]."""
+        uu = np.zeros(3 * self.n_beads + 3)
+        uu[:3 * self.n_beads] = _f64(up).reshape(-1)
+        lib().orc_md_only(self._h, _vp(uu), int(n))
 
     def channel_trace(self, mode: int, buf: np.ndarray | None = None):
         """Record (mode 1) or replay (mode 2) the pore-channel indicator of

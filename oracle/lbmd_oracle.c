@@ -299,6 +299,8 @@ int orc_interp_weights(const orc_sim *s, const double *r, int *nodes, double *w)
         int a = k & 1, b = (k >> 1) & 1, c = (k >> 2) & 1;
         nodes[k] = site_of(s, x0 + a, y0 + b, z0 + c);
         double wk = (a ? fx : 1.0 - fx) * (b ? fy : 1.0 - fy) * (c ? fz : 1.0 - fz);
+        if (p->interp == 1) /* nearest grid point (Sec. II): the corner on the bead's side of each mid-plane */
+            wk = (a == (fx >= 0.5) && b == (fy >= 0.5) && c == (fz >= 0.5)) ? 1.0 : 0.0;
         if (s->solid[nodes[k]]) wk = 0.0;
         else nfluid++;
         w[k] = wk;
@@ -545,9 +547,67 @@ static void record_kick(const orc_sim *s, md_record *rec, int k)
     }
 }
 
+/* Stochastic position Verlet (Sec. II, Eq. SPValgo) nested as the
+ * multiple-time-step scheme that follows it in the paper.  Per outer step
+ * (dt = 1/M): a half kick with the slow force (the pore field); M^b inner
+ * steps of length h = dt/M^b, each a half drift, the exact Ornstein-Uhlenbeck
+ * velocity update over h with the fast (conservative) forces evaluated at the
+ * half-drifted positions, and a half drift; a half kick.  With c = exp(-gamma h)
+ * and m = 1:
+ *   v' = c v + (1 - c) u_p + (1 - c)/gamma F + sqrt(kT (1 - c^2)) z,
+ * a fresh normal vector z per bead and inner step (Philox counter word 2 =
+ * the inner-step index).  The momentum the fluid gives the bead over the step
+ * is what the velocity gains beyond the conservative impulse: v' - v - h F. */
+/* half kick of the stochastic position Verlet cycle: the field only */
+static void field_half_kick(orc_sim *s, double dt)
+{
+    for (int i = 0; i < s->p.n_beads; i++) {
+        int ch = kick_channel(s, i);
+        if (ch) s->field_kicks += 1.0;
+        s->v[3 * i] += 0.5 * dt * (ch ? s->p.E : 0.0);
+    }
+}
+
+static void md_cycle_spv(orc_sim *s)
+{
+    const orc_params *p = &s->p;
+    int N = p->n_beads;
+    double dt = 1.0 / p->md_outer, h = dt / p->md_inner;
+    double c = exp(-p->gamma * h);
+    double g1 = p->gamma > 0.0 ? (1.0 - c) / p->gamma : h;
+    double sig = p->kT > 0.0 ? sqrt(p->kT * (1.0 - c * c)) : 0.0;
+    double *F = (double *)malloc(sizeof(double) * (3 * N + 3));
+    memset(s->J, 0, sizeof(double) * 3 * N);
+    for (int sub = 0; sub < p->md_outer; sub++) {
+        field_half_kick(s, dt);
+        for (int b = 0; b < p->md_inner; b++) {
+            int t = sub * p->md_inner + b;
+            for (int k = 0; k < 3 * N; k++) s->r[k] += 0.5 * h * s->v[k];
+            orc_fast_forces(s, s->r, F);
+            for (int i = 0; i < N; i++) {
+                double z[3] = {0, 0, 0};
+                if (sig > 0.0) orc_gauss3(p->seed, p->realization, (uint32_t)i, s->step, (uint32_t)t, z);
+                for (int a = 0; a < 3; a++) {
+                    size_t q = 3 * (size_t)i + a;
+                    double vn = c * s->v[q] + (1.0 - c) * s->up[q] + g1 * F[q] + sig * z[a];
+                    s->J[q] += vn - s->v[q] - h * F[q];
+                    s->v[q] = vn;
+                }
+            }
+            for (int k = 0; k < 3 * N; k++) s->r[k] += 0.5 * h * s->v[k];
+        }
+        field_half_kick(s, dt);
+    }
+    free(F);
+}
+
 static void md_cycle(orc_sim *s, md_record *rec)
 {
     const orc_params *p = &s->p;
+    if (p->integrator == 1) {
+        md_cycle_spv(s);
+        return;
+    }
     int N = p->n_beads;
     double dt = 1.0 / p->md_outer;
     double dtb = dt / p->md_inner;
@@ -604,7 +664,13 @@ static void one_step(orc_sim *s)
         int nodes[8];
         double w[8];
         orc_interp_weights(s, s->r + 3 * i, nodes, w);
-        s->cell_sum += nodes[0];
+        double id = nodes[0]; /* the cell (trilinear) or the chosen node (nearest grid point) */
+        if (p->interp == 1) {
+            id = -1.0;
+            for (int k = 0; k < 8; k++)
+                if (w[k] > 0.0) id = nodes[k];
+        }
+        s->cell_sum += id;
     }
 
     /* 3. MD cycle; J_i = momentum the fluid gave bead i */
@@ -767,14 +833,18 @@ static void weights_and_gradient(const orc_sim *s, const double *r, int *nodes, 
         double fac[3];
         for (int a = 0; a < 3; a++) fac[a] = bit[a] ? fr[a] : 1.0 - fr[a];
         raw[k] = m * fac[0] * fac[1] * fac[2];
-        sum += raw[k];
         for (int a = 0; a < 3; a++) {
             double d = bit[a] ? 1.0 : -1.0;
             for (int b = 0; b < 3; b++)
                 if (b != a) d *= fac[b];
             draw[k][a] = m * d;
-            dsum[a] += draw[k][a];
         }
+        if (s->p.interp == 1) { /* nearest grid point: piecewise constant, gradient 0 */
+            raw[k] = m * ((bit[0] == (fr[0] >= 0.5) && bit[1] == (fr[1] >= 0.5) && bit[2] == (fr[2] >= 0.5)) ? 1.0 : 0.0);
+            for (int a = 0; a < 3; a++) draw[k][a] = 0.0;
+        }
+        sum += raw[k];
+        for (int a = 0; a < 3; a++) dsum[a] += draw[k][a];
     }
     for (int k = 0; k < 8; k++) {
         W[k] = sum > 0.0 ? raw[k] / sum : 0.0;
@@ -1027,6 +1097,7 @@ int orc_adjoint(const orc_params *p, const uint8_t *solid, const double *f0, con
 {
     int N = p->n_beads;
     if (N < 1 || K < 0) return -1;
+    if (p->integrator != 0) return -3; /* the reverse sweep follows the velocity-Verlet cycle */
     orc_sim *s = orc_create(p, solid);
     size_t nf = (size_t)19 * s->ns, nb = (size_t)3 * N;
     if (f0) orc_set_populations(s, f0);
@@ -1077,4 +1148,13 @@ void orc_channel_trace(orc_sim *s, int mode, int *buf, int64_t len)
     s->chan = buf;
     s->chan_len = buf ? len : 0;
     s->chan_pos = 0;
+}
+
+void orc_md_only(orc_sim *s, const double *up, int n)
+{
+    memcpy(s->up, up, sizeof(double) * 3 * s->p.n_beads);
+    for (int k = 0; k < n; k++) {
+        if (s->p.n_beads > 0) md_cycle(s, NULL);
+        s->step += 1;
+    }
 }

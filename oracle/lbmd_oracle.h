@@ -40,6 +40,10 @@ typedef struct {
     int md_inner;             /* M^b: bonded sub-steps per MD step */
     uint64_t seed;            /* Philox key */
     uint32_t realization;     /* realization index, xor-ed into key word 1 */
+    int interp;               /* bead-lattice weights: 0 trilinear, 1 nearest grid point (Sec. II) */
+    int integrator;           /* 0: multiple-time-step velocity Verlet with explicit friction;
+                                 1: stochastic position Verlet (Sec. II, Eq. SPValgo), nested */
+    double lb_kT;             /* fluctuating-LB temperature (0: off) */
 } orc_params;
 
 typedef struct orc_sim orc_sim;
@@ -82,6 +86,11 @@ void orc_observables(const orc_sim *s, double *out /* ORC_NOBS */);
  * out[0] = half kicks taken inside the pore channel, out[1] = sum over steps
  * and beads of the index of the lattice cell holding the bead */
 void orc_event_counts(const orc_sim *s, double *out /*2*/);
+
+/* MD cycles alone, with the fluid velocity at the beads held at up [N][3]
+ * (no lattice update, no spread): the MD part of n coupled steps, for pins of
+ * the integrators.  The step counter advances as in orc_step. */
+void orc_md_only(orc_sim *s, const double *up, int n);
 
 /* Pore-channel indicator trace, for finite differences of a loss with the
  * field events held: mode 1 records the indicator of every (step, half kick,

@@ -90,6 +90,8 @@ def oracle_params(w: dict, realization: int = 0, n_beads: int | None = None) -> 
             "kappa_bend", "lj_sigma", "lj_eps", "wall_sigma", "wall_eps", "E", "gamma", "kT",
             "md_outer", "md_inner", "seed")
     p = {k: w[k] for k in keys}
-    p["realization"] = realization
+    p["realization"] = int(w.get("real_base", 0)) + realization
+    for k, d in (("interp", 0), ("integrator", 0), ("lb_kT", 0.0)):
+        p[k] = w.get(k, d)
     p["n_beads"] = int(n_beads if n_beads is not None else bead_counts(w)[realization])
     return p
