@@ -84,6 +84,14 @@ typedef struct lbmd_config {
                                 draws its noise as realization real_base + r, so an ensemble split
                                 over several handles (or GPUs) reproduces the unsplit one */
     uint64_t seed;           /* Philox key; global realization g uses key word 1 = seed_hi ^ g */
+    int32_t interp;          /* bead-lattice transfer: 0 trilinear over the fluid corners of the
+                                bead's cell; 1 nearest grid point, the paper's scheme (Sec. II) */
+    int32_t integrator;      /* MD cycle: 0 multiple-time-step velocity Verlet with explicit
+                                friction and noise at the half kicks; 1 stochastic position
+                                Verlet (Sec. II, Eq. SPValgo) nested over the M^b sub-steps, with
+                                the exact Ornstein-Uhlenbeck velocity update and fresh noise per
+                                sub-step.  lbmd_adjoint needs 0 */
+    double lb_kT;            /* fluctuating-LB temperature; must be 0 (not built) */
 } lbmd_config;
 
 /* Observables of one realization at the current state (Sec. III global

@@ -246,6 +246,10 @@ __device__ __forceinline__ void corners_with_gradient(const Sim &S, float xw, fl
         const float sx = a ? 1.0f : -1.0f, sy = b ? 1.0f : -1.0f, sz = d ? 1.0f : -1.0f;
         raw[k] = m * fx * fy * fz;
         c.dW[k] = make_float3(m * sx * fy * fz, m * fx * sy * fz, m * fx * fy * sz);
+        if (S.interp == 1) {  // nearest grid point: piecewise constant, gradient 0
+            raw[k] = m * ((a == (f[0] >= 0.5f) && b == (f[1] >= 0.5f) && d == (f[2] >= 0.5f)) ? 1.0f : 0.0f);
+            c.dW[k] = make_float3(0.f, 0.f, 0.f);
+        }
         sum += raw[k];
         dsum = add3(dsum, c.dW[k]);
     }

@@ -58,6 +58,8 @@ __device__ __forceinline__ void corner_of(const Sim &S, float xw, float yw, floa
     zi = wrapi(z0 + d, S.nz);
     node = xi + S.nx * (yi + S.ny * zi);
     w = (a ? fx : 1.0f - fx) * (b ? fy : 1.0f - fy) * (d ? fz : 1.0f - fz);
+    if (S.interp == 1)  // nearest grid point: the corner on the bead's side of each mid-plane
+        w = (a == (fx >= 0.5f) && b == (fy >= 0.5f) && d == (fz >= 0.5f)) ? 1.0f : 0.0f;
 }
 
 // Sum over the 8 corners: lane l holds corner l >> 2, and the xor tree over
@@ -613,25 +615,37 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
     int buf = 0, t = 0;
     float3 ff = group_sum<T>(force_part<T>(S, sm, buf, own, p, pl, N, mh, ml, lt));
     if (!own) ff = make_float3(0.f, 0.f, 0.f);
+    // Stochastic position Verlet (integrator 1): the half kicks carry the
+    // field only; each sub-step drifts to its mid-point (h/2 for the first,
+    // then h: the second half of one sub-step and the first of the next),
+    // evaluates the forces there and updates v with the exact
+    // Ornstein-Uhlenbeck step v' = c v + (1 - c) u_p + g1 F + sig z; the
+    // fluid's impulse is v' - v - h F; a last half drift closes the cycle.
+    const bool spv = S.integrator == 1;
     for (int sub = 0; sub < S.M; ++sub) {
         float3 xi = make_float3(0.f, 0.f, 0.f);
-        if (own && amp > 0.0f) xi = amp * gauss3(S.seed, S.real_base + (uint32_t)r, (uint32_t)p, step, (uint32_t)sub);
-        if (own) {  // first half kick: field + friction + noise
+        if (own && amp > 0.0f && !spv) xi = amp * gauss3(S.seed, S.real_base + (uint32_t)r, (uint32_t)p, step, (uint32_t)sub);
+        if (own) {  // first half kick: field + friction + noise (field only for SPV)
             const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx, S.inx), ff_wrap(mh.y, ml.y, fny, S.iny),
                                        ff_wrap(mh.z, ml.z, fnz, S.inz));
             if (trj && lt == 0)
                 trj[(size_t)traj_slot_kick(S.M, S.Mb, 2 * sub) * TB + off + p] = make_float4(v.x, v.y, v.z, ch ? 1.f : 0.f);
-            const float3 fl = S.gamma * (up - v) + xi;
-            v = v + h * (make_float3(ch ? S.E : 0.0f, 0.f, 0.f) + fl);
-            J = J + h * fl;
+            if (spv) {
+                v.x += h * (ch ? S.E : 0.0f);
+            } else {
+                const float3 fl = S.gamma * (up - v) + xi;
+                v = v + h * (make_float3(ch ? S.E : 0.0f, 0.f, 0.f) + fl);
+                J = J + h * fl;
+            }
         }
         for (int b = 0; b < S.Mb; ++b, ++t) {
             const int nb = buf ^ 1;
             if (own) {
-                v = v + hb * ff;
-                ff_add(mh.x, ml.x, dtb * v.x);
-                ff_add(mh.y, ml.y, dtb * v.y);
-                ff_add(mh.z, ml.z, dtb * v.z);
+                if (!spv) v = v + hb * ff;
+                const float dr = (spv && b == 0) ? hb : dtb;
+                ff_add(mh.x, ml.x, dr * v.x);
+                ff_add(mh.y, ml.y, dr * v.y);
+                ff_add(mh.z, ml.z, dr * v.z);
                 if (trj && lt == 0) {
                     trj[(size_t)traj_slot_hi(S.M, S.Mb, t + 1) * TB + off + p] = mh;
                     trj[(size_t)traj_slot_lo(S.M, S.Mb, t + 1) * TB + off + p] = ml;
@@ -666,18 +680,36 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
             }
             const float3 F = group_sum<T>(force_part<T>(S, sm, buf, own, p, pl, N, mh, ml, lt));
             if (own) {
-                ff = F;
-                v = v + hb * ff;
+                if (spv) {
+                    float3 z = make_float3(0.f, 0.f, 0.f);
+                    if (S.spv_sig > 0.0f) z = gauss3(S.seed, S.real_base + (uint32_t)r, (uint32_t)p, step, (uint32_t)t);
+                    const float3 vn = S.spv_c * v + (1.0f - S.spv_c) * up + S.spv_g1 * F + S.spv_sig * z;
+                    J = J + (vn - v - dtb * F);
+                    v = vn;
+                } else {
+                    ff = F;
+                    v = v + hb * ff;
+                }
             }
         }
-        if (own) {  // second half kick with the same noise
+        if (own) {
+            if (spv) {  // the last half drift of the cycle
+                ff_add(mh.x, ml.x, hb * v.x);
+                ff_add(mh.y, ml.y, hb * v.y);
+                ff_add(mh.z, ml.z, hb * v.z);
+            }
+            // second half kick with the same noise (field only for SPV)
             const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx, S.inx), ff_wrap(mh.y, ml.y, fny, S.iny),
                                        ff_wrap(mh.z, ml.z, fnz, S.inz));
             if (trj && lt == 0)
                 trj[(size_t)traj_slot_kick(S.M, S.Mb, 2 * sub + 1) * TB + off + p] = make_float4(v.x, v.y, v.z, ch ? 1.f : 0.f);
-            const float3 fl = S.gamma * (up - v) + xi;
-            v = v + h * (make_float3(ch ? S.E : 0.0f, 0.f, 0.f) + fl);
-            J = J + h * fl;
+            if (spv) {
+                v.x += h * (ch ? S.E : 0.0f);
+            } else {
+                const float3 fl = S.gamma * (up - v) + xi;
+                v = v + h * (make_float3(ch ? S.E : 0.0f, 0.f, 0.f) + fl);
+                J = J + h * fl;
+            }
         }
     }
     if (owner) sm.jbuf[pl] = make_float4(J.x, J.y, J.z, 0.f);

@@ -95,6 +95,9 @@ bool config_ok(const lbmd_config *c, const int32_t *off, std::string &why) {
     if (c->md_outer < 1 || c->md_inner < 1) { why = "md_outer and md_inner must be >= 1"; return false; }
     if (c->precision != LBMD_FP32 && c->precision != LBMD_FP16DEV) { why = "unknown precision"; return false; }
     if (c->real_base < 0 || (double)c->real_base + c->n_real > 4294967295.0) { why = "real_base out of range"; return false; }
+    if (c->interp != 0 && c->interp != 1) { why = "interp must be 0 (trilinear) or 1 (nearest grid point)"; return false; }
+    if (c->integrator != 0 && c->integrator != 1) { why = "integrator must be 0 (velocity Verlet) or 1 (SPV)"; return false; }
+    if (c->lb_kT != 0.0) { why = "fluctuating LB (lb_kT > 0) is not built"; return false; }
     if (c->wall_x < -1 || c->wall_x >= c->nx) { why = "wall_x must be -1 or inside [0, nx)"; return false; }
     if (c->pore_h < 0 || c->pore_h > c->ny || c->pore_h > c->nz) { why = "pore_h out of range"; return false; }
     if (!(c->lj_sigma > 0) || !(c->wall_sigma > 0) || c->lj_eps < 0 || c->wall_eps < 0) { why = "WCA sigma must be > 0, eps >= 0"; return false; }
@@ -484,6 +487,15 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
     S.inz = 1.0f / (float)cfg->nz;
     S.n_real = cfg->n_real;
     S.real_base = (uint32_t)cfg->real_base;
+    S.interp = cfg->interp;
+    S.integrator = cfg->integrator;
+    {   // stochastic position Verlet constants over one sub-step h (double, then stored)
+        const double hsub = 1.0 / cfg->md_outer / cfg->md_inner;
+        const double c1 = std::exp(-cfg->gamma * hsub);
+        S.spv_c = (float)c1;
+        S.spv_g1 = (float)(cfg->gamma > 0.0 ? (1.0 - c1) / cfg->gamma : hsub);
+        S.spv_sig = (float)(cfg->kT > 0.0 ? std::sqrt(cfg->kT * (1.0 - c1 * c1)) : 0.0);
+    }
     S.precision = cfg->precision;
     S.omega = (float)(1.0 / cfg->tau);
     for (int a = 0; a < 3; ++a) S.g[a] = (float)cfg->body_force[a];
@@ -807,6 +819,11 @@ lbmd_status lbmd_set_drive(lbmd_handle *h, double gamma, double E) {
     h->cfg.E = E;
     h->S.gamma = (float)gamma;
     h->S.E = (float)E;
+    const double hsub = 1.0 / h->cfg.md_outer / h->cfg.md_inner;
+    const double c1 = std::exp(-gamma * hsub);
+    h->S.spv_c = (float)c1;
+    h->S.spv_g1 = (float)(gamma > 0.0 ? (1.0 - c1) / gamma : hsub);
+    h->S.spv_sig = (float)(h->cfg.kT > 0.0 ? std::sqrt(h->cfg.kT * (1.0 - c1 * c1)) : 0.0);
     drop_graph(h);  // the graph holds the old parameters in its kernel arguments
     return LBMD_OK;
 }
@@ -851,6 +868,7 @@ AdjLayout adj_layout(const lbmd_handle *h, int K, int C) {
 
 bool adjoint_ok(const lbmd_handle *h, int K, int C, std::string &why) {
     if (h->cfg.precision != LBMD_FP32) { why = "the adjoint needs FP32 populations"; return false; }
+    if (h->cfg.integrator != 0) { why = "the adjoint follows the velocity-Verlet cycle (integrator 0)"; return false; }
     if (K < 1 || C < 1) { why = "K and checkpoint_every must be >= 1"; return false; }
     for (int r = 0; r < h->cfg.n_real; ++r)
         if (h->offsets[r + 1] <= h->offsets[r]) { why = "every realization needs at least one bead"; return false; }

@@ -84,6 +84,9 @@ struct Sim {
     int nx, ny, nz, ns, nxt, n_real;
     int ps;  // stride between population arrays: ns rounded up to 64
     uint32_t real_base;  // global index of realization 0 (noise key)
+    int interp;          // 0 trilinear, 1 nearest grid point
+    int integrator;      // 0 velocity Verlet (explicit friction), 1 stochastic position Verlet
+    float spv_c, spv_g1, spv_sig;  // exp(-gamma h), (1 - c)/gamma, sqrt(kT (1 - c^2)) over a sub-step h
     float inx, iny, inz;     // 1/nx, 1/ny, 1/nz
     int precision;
     float omega;

@@ -42,7 +42,7 @@ class Config(ctypes.Structure):
                 ("wall_eps", ctypes.c_double), ("E", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("kT", ctypes.c_double), ("md_outer", ctypes.c_int32), ("md_inner", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("real_base", ctypes.c_int32),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("interp", ctypes.c_int32), ("integrator", ctypes.c_int32), ("lb_kT", ctypes.c_double)]
 
 
 class Obs(ctypes.Structure):
@@ -149,6 +149,9 @@ def make_config(w: dict) -> Config:
     prec = w.get("precision", "fp32")
     c.precision = FP16DEV if prec in ("fp16dev", FP16DEV) else FP32
     c.real_base = int(w.get("real_base", 0))
+    c.interp = int(w.get("interp", 0))
+    c.integrator = int(w.get("integrator", 0))
+    c.lb_kT = float(w.get("lb_kT", 0.0))
     c.seed = int(w.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF
     return c
 
