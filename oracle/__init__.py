@@ -92,6 +92,9 @@ def lib():
         _lib.orc_event_counts.argtypes = [P, P]
         _lib.orc_channel_trace.argtypes = [P, ctypes.c_int, P, ctypes.c_int64]
         _lib.orc_md_only.argtypes = [P, P, ctypes.c_int]
+        _lib.orc_mode.restype = ctypes.c_double
+        _lib.orc_mode.argtypes = [ctypes.c_int, P]
+        _lib.orc_fluid_noise.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64, P]
     return _lib
 
 
@@ -192,6 +195,18 @@ def adjoint(params: dict, solid, r0, K: int, v0=None, f0=None, step0: int = 0, w
     if want_df0:
         res["df0"] = df0.reshape(19, int(st.nz), int(st.ny), int(st.nx))
     return res
+
+
+def mode(k: int, c) -> float:
+    """Mode k of the D3Q19 moment basis evaluated on velocity c."""
+    cc = np.ascontiguousarray(c, dtype=np.int32)
+    return float(lib().orc_mode(int(k), cc.ctypes.data_as(ctypes.c_void_p)))
+
+
+def fluid_noise(seed: int, realization: int, site: int, step: int) -> np.ndarray:
+    z = np.zeros(16)
+    lib().orc_fluid_noise(seed, realization, site, step, _vp(z))
+    return z
 
 
 class OracleSim:

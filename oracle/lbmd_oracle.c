@@ -645,6 +645,90 @@ static void md_cycle(orc_sim *s, md_record *rec)
 }
 
 /* ------------------------------------------------------------------------ */
+/* fluctuating LB (Sec. II, the stochastic term F_i of Eq. 4, after the     */
+/* moment-space scheme of the cited work of Adhikari et al.)                 */
+/* ------------------------------------------------------------------------ */
+
+/* Mode k of the D3Q19 moment basis evaluated on the velocity c: density,
+ * momentum (k = 1..3), the six stress modes (4..9: bulk, two normal-stress
+ * differences, three shear), and nine ghost modes (10..18).  The modes are
+ * orthogonal under the lattice weights: sum_i w_i e_k(c_i) e_l(c_i) = b_k delta_kl. */
+double orc_mode(int k, const int *c)
+{
+    double x = c[0], y = c[1], z = c[2], q = x * x + y * y + z * z;
+    switch (k) {
+    case 0: return 1.0;
+    case 1: return x;
+    case 2: return y;
+    case 3: return z;
+    case 4: return q - 1.0;
+    case 5: return 3.0 * x * x - q;
+    case 6: return y * y - z * z;
+    case 7: return x * y;
+    case 8: return y * z;
+    case 9: return z * x;
+    case 10: return (3.0 * q - 5.0) * x;
+    case 11: return (3.0 * q - 5.0) * y;
+    case 12: return (3.0 * q - 5.0) * z;
+    case 13: return (y * y - z * z) * x;
+    case 14: return (z * z - x * x) * y;
+    case 15: return (x * x - y * y) * z;
+    case 16: return 3.0 * q * q - 6.0 * q + 1.0;
+    case 17: return (2.0 * q - 3.0) * (3.0 * x * x - q);
+    case 18: return (2.0 * q - 3.0) * (y * y - z * z);
+    }
+    return 0.0;
+}
+
+/* Sixteen standard normals for the fluctuations of one site and step:
+ * Philox4x32-10 with the bead key (seed_lo, seed_hi ^ realization) and the
+ * counters (site, step_lo, 0xF0000000 + j, step_hi), j = 0..3; each word ->
+ * u = (top 24 bits + 1/2) 2^-24; Box-Muller on (u0, u1) and (u2, u3). */
+void orc_fluid_noise(uint64_t seed, uint32_t realization, uint32_t site, int64_t step, double *z)
+{
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32) ^ realization};
+    const double two_pi = 6.283185307179586476925286766559;
+    for (uint32_t j = 0; j < 4; j++) {
+        uint32_t ctr[4] = {site, (uint32_t)((uint64_t)step & 0xffffffffu), 0xF0000000u + j,
+                           (uint32_t)((uint64_t)step >> 32)};
+        uint32_t x[4];
+        orc_philox4x32_10(ctr, key, x);
+        double u[4];
+        for (int k = 0; k < 4; k++) u[k] = ((double)(x[k] >> 8) + 0.5) / 16777216.0;
+        double a = sqrt(-2.0 * log(u[0])), b = sqrt(-2.0 * log(u[2]));
+        z[4 * j + 0] = a * cos(two_pi * u[1]);
+        z[4 * j + 1] = a * sin(two_pi * u[1]);
+        z[4 * j + 2] = b * cos(two_pi * u[3]);
+        z[4 * j + 3] = b * sin(two_pi * u[3]);
+    }
+}
+
+/* Fluctuation added to the post-collision populations of one site: every
+ * non-conserved mode k (4..18) relaxes with gamma_k = 1 - omega (BGK) and
+ * receives a kick of variance mu b_k (1 - gamma_k^2), mu = rho kT / c_s^2;
+ * back in population space
+ *   dF_i = w_i sum_k e_k(c_i) sqrt(mu (1 - gamma_k^2) / b_k) r_k.
+ * The conserved modes get none, so mass and momentum are untouched. */
+static void fluid_fluctuation(const orc_sim *s, int site, double rho, double *dF)
+{
+    const orc_params *p = &s->p;
+    double gam = 1.0 - 1.0 / p->tau;
+    double mu = 3.0 * rho * p->lb_kT;
+    double z[16];
+    orc_fluid_noise(p->seed, p->realization, (uint32_t)site, s->step, z);
+    for (int i = 0; i < 19; i++) dF[i] = 0.0;
+    for (int k = 4; k < 19; k++) {
+        double b = 0.0;
+        for (int i = 0; i < 19; i++) {
+            double e = orc_mode(k, CI[i]);
+            b += weight_of(i) * e * e;
+        }
+        double amp = sqrt(mu * (1.0 - gam * gam) / b) * z[k - 4];
+        for (int i = 0; i < 19; i++) dF[i] += weight_of(i) * orc_mode(k, CI[i]) * amp;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* one coupled LB-MD step                                                    */
 /* ------------------------------------------------------------------------ */
 static void one_step(orc_sim *s)
@@ -697,9 +781,11 @@ static void one_step(orc_sim *s)
         double Gs[3] = {s->G[site] + p->body_force[0], s->G[ns + site] + p->body_force[1],
                         s->G[2 * ns + site] + p->body_force[2]};
         orc_source(Gs, S);
+        double dF[19] = {0};
+        if (p->lb_kT > 0.0) fluid_fluctuation(s, site, s->rho[site], dF);
         for (int i = 0; i < 19; i++) {
             double fi = s->f[(size_t)i * ns + site];
-            s->fstar[(size_t)i * ns + site] = fi - omega * (fi - feq[i]) + S[i];
+            s->fstar[(size_t)i * ns + site] = fi - omega * (fi - feq[i]) + S[i] + dF[i];
         }
     }
 
@@ -1098,6 +1184,7 @@ int orc_adjoint(const orc_params *p, const uint8_t *solid, const double *f0, con
     int N = p->n_beads;
     if (N < 1 || K < 0) return -1;
     if (p->integrator != 0) return -3; /* the reverse sweep follows the velocity-Verlet cycle */
+    if (p->lb_kT != 0.0) return -4;     /* and a deterministic fluid */
     orc_sim *s = orc_create(p, solid);
     size_t nf = (size_t)19 * s->ns, nb = (size_t)3 * N;
     if (f0) orc_set_populations(s, f0);

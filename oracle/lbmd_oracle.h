@@ -92,6 +92,12 @@ void orc_event_counts(const orc_sim *s, double *out /*2*/);
  * the integrators.  The step counter advances as in orc_step. */
 void orc_md_only(orc_sim *s, const double *up, int n);
 
+/* fluctuating LB: mode k of the D3Q19 moment basis on velocity c, and the
+ * sixteen standard normals of one site and step (Philox4x32-10, counters
+ * (site, step_lo, 0xF0000000 + j, step_hi), j = 0..3; Box-Muller) */
+double orc_mode(int k, const int *c /*3*/);
+void orc_fluid_noise(uint64_t seed, uint32_t realization, uint32_t site, int64_t step, double *z /*16*/);
+
 /* Pore-channel indicator trace, for finite differences of a loss with the
  * field events held: mode 1 records the indicator of every (step, half kick,
  * bead) into buf[len] in the order the kicks happen; mode 2 replays it
