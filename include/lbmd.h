@@ -91,7 +91,10 @@ typedef struct lbmd_config {
                                 Verlet (Sec. II, Eq. SPValgo) nested over the M^b sub-steps, with
                                 the exact Ornstein-Uhlenbeck velocity update and fresh noise per
                                 sub-step.  lbmd_adjoint needs 0 */
-    double lb_kT;            /* fluctuating-LB temperature; must be 0 (not built) */
+    double lb_kT;            /* fluctuating-LB temperature (Sec. II, the term F_i of Eq. 4): every
+                                non-conserved mode of an orthogonal D3Q19 basis gets Philox noise of
+                                variance 3 rho lb_kT b_k (1 - (1 - omega)^2) per site and step; 0 = off.
+                                lbmd_adjoint needs 0 */
 } lbmd_config;
 
 /* Observables of one realization at the current state (Sec. III global

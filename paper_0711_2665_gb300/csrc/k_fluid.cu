@@ -96,7 +96,7 @@ __device__ void finalize_fluid_sums(const Sim &S, unsigned int *done, long long 
 // walks zc consecutive z planes.  MODE 0: store; 1: store + per-step sums;
 // 2: sums only (observables).
 // ---------------------------------------------------------------------------
-template <int PREC, int MODE, int U>
+template <int PREC, int MODE, int U, bool FL>
 __global__ void __launch_bounds__(512) k_stream_collide(const Sim S, const void *__restrict__ Av,
                                                         void *__restrict__ Bv, const int zc,
                                                         const int nzb) {
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(512) k_stream_collide(const Sim S, const void 
     const T *__restrict__ A = reinterpret_cast<const T *>(Av) + (size_t)r * Q * ns;
     T *__restrict__ B = reinterpret_cast<T *>(Bv) + (size_t)r * Q * ns;
     long long step = 0;
-    if (MODE == 1) step = S.ctrl->step;
+    if (MODE == 1 || FL) step = S.ctrl->step;
     float am = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
     const float om = S.omega;
     const float g0 = S.g[0], g1 = S.g[1], g2 = S.g[2];
@@ -190,11 +190,27 @@ __global__ void __launch_bounds__(512) k_stream_collide(const Sim S, const void 
                 const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
                 const float usq = 1.5f * (ux * ux + uy * uy + uz * uz);
                 const float rho_s = rho * up;
+                // fluctuating LB: mode k (4..18) gets amplitude sqrt(rho) fl_amp[k-4] r_k
+                float am_[15];
+                if (FL) {
+                    float z[16];
+                    fluid_noise16(S.seed, S.real_base + (uint32_t)r, (uint32_t)s, step, z);
+                    const float sr = sqrtf(fmaxf(rho, 0.0f)) * up;
+#pragma unroll
+                    for (int k = 0; k < 15; ++k) am_[k] = sr * S.fl_amp[k] * z[k];
+                }
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
                     const float cu = 3.0f * ((float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz);
                     const float heq = wq(i) * (drho_s + rho_s * (cu + 0.5f * cu * cu - usq));
                     float hn = h[i] + om * (heq - h[i]);
+                    if (FL) {
+                        float d = 0.0f;
+#pragma unroll
+                        for (int k = 4; k < Q; ++k)
+                            if (mode_e(k, i) != 0.0f) d += mode_e(k, i) * am_[k - 4];
+                        hn += wq(i) * d;
+                    }
                     if (has_g)
                         hn += up * (3.0f * wq(i) * ((float)cx(i) * g0 + (float)cy(i) * g1 + (float)cz(i) * g2));
                     store_raw(B, (uint32_t)i * ns + (uint32_t)s, hn);
@@ -228,27 +244,19 @@ cudaError_t launch_stream_collide(const Sim &S, const void *A, void *B, int by, 
     int nzb;
     dim3 grid = sc_grid(S, by, zc, &nzb);
     dim3 block(32, by);
-    // Walking two z sites at a time (U = 2) doubles the loads in flight per
-    // thread but needs ~128 registers with the diagnostics; on GB300 it lost
-    // to the one-site walk at every tile shape, so it is kept off.
-    const bool two = false;
+    // One site per thread and z-iteration: walking two z sites at a time
+    // doubled the loads in flight but needed ~128 registers and lost at
+    // every tile shape on GB300.
+#define SC_LAUNCH(P, M, F) k_stream_collide<P, M, 1, F><<<grid, block, 0, st>>>(S, A, B, zc, nzb)
+    const bool fl = S.fluct != 0;
     if (S.precision == LBMD_FP16DEV) {
-        if (diag) {
-            if (two) k_stream_collide<1, 1, 2><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
-            else k_stream_collide<1, 1, 1><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
-        } else {
-            if (two) k_stream_collide<1, 0, 2><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
-            else k_stream_collide<1, 0, 1><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
-        }
+        if (diag) { if (fl) SC_LAUNCH(1, 1, true); else SC_LAUNCH(1, 1, false); }
+        else { if (fl) SC_LAUNCH(1, 0, true); else SC_LAUNCH(1, 0, false); }
     } else {
-        if (diag) {
-            if (two) k_stream_collide<0, 1, 2><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
-            else k_stream_collide<0, 1, 1><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
-        } else {
-            if (two) k_stream_collide<0, 0, 2><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
-            else k_stream_collide<0, 0, 1><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
-        }
+        if (diag) { if (fl) SC_LAUNCH(0, 1, true); else SC_LAUNCH(0, 1, false); }
+        else { if (fl) SC_LAUNCH(0, 0, true); else SC_LAUNCH(0, 0, false); }
     }
+#undef SC_LAUNCH
     return cudaGetLastError();
 }
 
@@ -257,8 +265,8 @@ cudaError_t launch_fluid_observables(const Sim &S, const void *A, cudaStream_t s
     const int by = 8, zc = 4;
     dim3 grid = sc_grid(S, by, zc, &nzb);
     dim3 block(32, by);
-    if (S.precision == LBMD_FP16DEV) k_stream_collide<1, 2, 2><<<grid, block, 0, st>>>(S, A, nullptr, zc, nzb);
-    else k_stream_collide<0, 2, 2><<<grid, block, 0, st>>>(S, A, nullptr, zc, nzb);
+    if (S.precision == LBMD_FP16DEV) k_stream_collide<1, 2, 2, false><<<grid, block, 0, st>>>(S, A, nullptr, zc, nzb);
+    else k_stream_collide<0, 2, 2, false><<<grid, block, 0, st>>>(S, A, nullptr, zc, nzb);
     return cudaGetLastError();
 }
 

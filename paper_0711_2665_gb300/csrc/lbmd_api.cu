@@ -97,7 +97,7 @@ bool config_ok(const lbmd_config *c, const int32_t *off, std::string &why) {
     if (c->real_base < 0 || (double)c->real_base + c->n_real > 4294967295.0) { why = "real_base out of range"; return false; }
     if (c->interp != 0 && c->interp != 1) { why = "interp must be 0 (trilinear) or 1 (nearest grid point)"; return false; }
     if (c->integrator != 0 && c->integrator != 1) { why = "integrator must be 0 (velocity Verlet) or 1 (SPV)"; return false; }
-    if (c->lb_kT != 0.0) { why = "fluctuating LB (lb_kT > 0) is not built"; return false; }
+    if (!(c->lb_kT >= 0.0) || !std::isfinite(c->lb_kT)) { why = "lb_kT must be finite and >= 0"; return false; }
     if (c->wall_x < -1 || c->wall_x >= c->nx) { why = "wall_x must be -1 or inside [0, nx)"; return false; }
     if (c->pore_h < 0 || c->pore_h > c->ny || c->pore_h > c->nz) { why = "pore_h out of range"; return false; }
     if (!(c->lj_sigma > 0) || !(c->wall_sigma > 0) || c->lj_eps < 0 || c->wall_eps < 0) { why = "WCA sigma must be > 0, eps >= 0"; return false; }
@@ -489,6 +489,16 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
     S.real_base = (uint32_t)cfg->real_base;
     S.interp = cfg->interp;
     S.integrator = cfg->integrator;
+    S.fluct = cfg->lb_kT > 0.0;
+    {   // fluctuating LB: mode k gets variance mu b_k (1 - gamma^2), mu = rho kT / c_s^2,
+        // gamma = 1 - omega; per unit sqrt(rho) and weight: sqrt(3 kT (1 - gamma^2) / b_k)
+        const double gam = 1.0 - 1.0 / cfg->tau;
+        for (int k = 4; k < LBMD_Q; ++k) {
+            double b = 0.0;
+            for (int i = 0; i < LBMD_Q; ++i) b += wq_exact(i) * (double)mode_e(k, i) * (double)mode_e(k, i);
+            S.fl_amp[k - 4] = (float)std::sqrt(3.0 * cfg->lb_kT * (1.0 - gam * gam) / b);
+        }
+    }
     {   // stochastic position Verlet constants over one sub-step h (double, then stored)
         const double hsub = 1.0 / cfg->md_outer / cfg->md_inner;
         const double c1 = std::exp(-cfg->gamma * hsub);
@@ -869,6 +879,7 @@ AdjLayout adj_layout(const lbmd_handle *h, int K, int C) {
 bool adjoint_ok(const lbmd_handle *h, int K, int C, std::string &why) {
     if (h->cfg.precision != LBMD_FP32) { why = "the adjoint needs FP32 populations"; return false; }
     if (h->cfg.integrator != 0) { why = "the adjoint follows the velocity-Verlet cycle (integrator 0)"; return false; }
+    if (h->cfg.lb_kT != 0.0) { why = "the adjoint needs a deterministic fluid (lb_kT = 0)"; return false; }
     if (K < 1 || C < 1) { why = "K and checkpoint_every must be >= 1"; return false; }
     for (int r = 0; r < h->cfg.n_real; ++r)
         if (h->offsets[r + 1] <= h->offsets[r]) { why = "every realization needs at least one bead"; return false; }

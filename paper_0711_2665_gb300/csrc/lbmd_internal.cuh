@@ -50,6 +50,34 @@ __host__ __device__ constexpr float wq(int i) {
     return i == 0 ? (1.0f / 3.0f) : (i <= 6 ? (1.0f / 18.0f) : (1.0f / 36.0f));
 }
 
+// Mode k of the D3Q19 moment basis on velocity c_i (orthogonal under the
+// weights): 0 density, 1-3 momentum, 4-9 stress (bulk, two normal-stress
+// differences, three shear), 10-18 ghost modes.  Used by the fluctuating LB.
+__host__ __device__ constexpr float mode_e(int k, int i) {
+    return k == 0 ? 1.0f
+         : k == 1 ? (float)cx(i)
+         : k == 2 ? (float)cy(i)
+         : k == 3 ? (float)cz(i)
+         : k == 4 ? (float)(cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i) - 1)
+         : k == 5 ? (float)(3 * cx(i) * cx(i) - (cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i)))
+         : k == 6 ? (float)(cy(i) * cy(i) - cz(i) * cz(i))
+         : k == 7 ? (float)(cx(i) * cy(i))
+         : k == 8 ? (float)(cy(i) * cz(i))
+         : k == 9 ? (float)(cz(i) * cx(i))
+         : k == 10 ? (float)((3 * (cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i)) - 5) * cx(i))
+         : k == 11 ? (float)((3 * (cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i)) - 5) * cy(i))
+         : k == 12 ? (float)((3 * (cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i)) - 5) * cz(i))
+         : k == 13 ? (float)((cy(i) * cy(i) - cz(i) * cz(i)) * cx(i))
+         : k == 14 ? (float)((cz(i) * cz(i) - cx(i) * cx(i)) * cy(i))
+         : k == 15 ? (float)((cx(i) * cx(i) - cy(i) * cy(i)) * cz(i))
+         : k == 16 ? (float)(3 * (cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i)) * (cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i))
+                             - 6 * (cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i)) + 1)
+         : k == 17 ? (float)((2 * (cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i)) - 3) *
+                             (3 * cx(i) * cx(i) - (cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i))))
+         : k == 18 ? (float)((2 * (cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i)) - 3) * (cy(i) * cy(i) - cz(i) * cz(i)))
+         : 0.0f;
+}
+
 constexpr uint32_t SOLID_BIT = 0x80000000u;
 // set on a site when a solid site lies within Chebyshev distance
 // near_solid_radius (computed on the host from the wall-list radius): a bead
@@ -87,6 +115,8 @@ struct Sim {
     int interp;          // 0 trilinear, 1 nearest grid point
     int integrator;      // 0 velocity Verlet (explicit friction), 1 stochastic position Verlet
     float spv_c, spv_g1, spv_sig;  // exp(-gamma h), (1 - c)/gamma, sqrt(kT (1 - c^2)) over a sub-step h
+    int fluct;           // fluctuating LB on
+    float fl_amp[15];    // sqrt(3 kT_lb (1 - (1 - omega)^2) / b_k), modes k = 4..18 (times sqrt(rho))
     float inx, iny, inz;     // 1/nx, 1/ny, 1/nz
     int precision;
     float omega;
@@ -215,6 +245,32 @@ __device__ __forceinline__ float3 gauss3(unsigned long long seed, uint32_t reali
     sincospif(2.0f * u1, &s1, &c1);
     sincospif(2.0f * u3, &s3, &c3);
     return make_float3(a * c1, a * s1, b * c3);
+}
+
+// Sixteen standard normals for the fluctuations of one site and step:
+// counters (site, step_lo, 0xF0000000 + j, step_hi), j = 0..3, same key as the
+// bead noise; Box-Muller on (u0, u1) and (u2, u3) of each call.
+__device__ __forceinline__ void fluid_noise16(unsigned long long seed, uint32_t realization, uint32_t site, long long step,
+                                              float (&z)[16]) {
+    const uint2 key = make_uint2((uint32_t)(seed & 0xffffffffull), (uint32_t)(seed >> 32) ^ realization);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint4 ctr = make_uint4(site, (uint32_t)((unsigned long long)step & 0xffffffffull), 0xF0000000u + (uint32_t)j,
+                                     (uint32_t)((unsigned long long)step >> 32));
+        const uint4 x = philox4x32_10(ctr, key);
+        const float u0 = ((float)(x.x >> 8) + 0.5f) * (1.0f / 16777216.0f);
+        const float u1 = ((float)(x.y >> 8) + 0.5f) * (1.0f / 16777216.0f);
+        const float u2 = ((float)(x.z >> 8) + 0.5f) * (1.0f / 16777216.0f);
+        const float u3 = ((float)(x.w >> 8) + 0.5f) * (1.0f / 16777216.0f);
+        const float a = sqrtf(-2.0f * logf(u0)), b = sqrtf(-2.0f * logf(u2));
+        float s1, c1, s3, c3;
+        sincospif(2.0f * u1, &s1, &c1);
+        sincospif(2.0f * u3, &s3, &c3);
+        z[4 * j + 0] = a * c1;
+        z[4 * j + 1] = a * s1;
+        z[4 * j + 2] = b * c3;
+        z[4 * j + 3] = b * s3;
+    }
 }
 
 // ---------------------------------------------------------------------------

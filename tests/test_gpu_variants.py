@@ -77,3 +77,56 @@ def test_adjoint_refuses_spv():
     with pytest.raises(lbmd.LbmdError) as e:
         sim.adjoint_bytes(4, 2)
     assert e.value.status == 1
+
+
+# ---------------------------------------------------------------------------
+# fluctuating lattice Boltzmann (lb_kT > 0)
+# ---------------------------------------------------------------------------
+LB_KT = 1e-4
+
+
+def test_fluctuating_one_step_matches_oracle():
+    """Same Philox normals per site and step on both sides: one coupled step
+    from a developed state within the parity tolerance."""
+    w = small_workload(lb_kT=LB_KT)
+    sim, orc, inp = make_pair(w)
+    orc.step(5)
+    f32, r, v = to_f32_state(orc)
+    load_state(sim, orc, f32, r, v, 5)
+    sim.step(1)
+    orc.step(1)
+    assert rel_err(sim.get_populations()[0], orc.get_populations()) <= 1e-5
+    r_g, _ = sim.get_beads()
+    r_o, _ = orc.get_beads()
+    assert np.abs(r_g - r_o).max() <= 1e-5
+
+
+def test_fluctuating_equipartition_and_conservation():
+    w = small_workload(nx=32, ny=32, nz=32, wall_x=-1, n_beads=0, tau=0.8, lb_kT=LB_KT)
+    inp = workloads.build_inputs(w)
+    sim = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"])
+    o0 = sim.observables()[0]
+    sim.step(200)
+    c, wts, _ = oracle.tables()
+    acc = np.zeros(4)
+    n = 40
+    for _ in range(n):
+        sim.step(1)
+        d = sim.get_deviations()[0].astype(np.float64)
+        j = np.tensordot(c.T.astype(float), d, 1)
+        acc += [np.mean(j[0] ** 2), np.mean(j[1] ** 2), np.mean(j[2] ** 2), np.mean(d.sum(0) ** 2)]
+    acc /= n
+    assert np.allclose(acc[:3] / LB_KT, 1.0, atol=0.03), acc[:3] / LB_KT
+    assert acc[3] / (3 * LB_KT) == pytest.approx(1.0, abs=0.03)
+    o1 = sim.observables()[0]
+    assert abs(o1["mass"] - o0["mass"]) < 1e-9 * o0["mass"]
+    for a in ("x", "y", "z"):
+        assert abs(o1["p_fluid_" + a]) < 1e-4  # 32768 sites of rounding-level momentum
+
+
+def test_adjoint_refuses_fluctuating_fluid():
+    w = small_workload(lb_kT=LB_KT)
+    inp = workloads.build_inputs(w)
+    sim = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"])
+    with pytest.raises(lbmd.LbmdError):
+        sim.adjoint_bytes(4, 2)
