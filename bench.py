@@ -364,10 +364,22 @@ def main():
     bytes_site = 152 if w["precision"] == "fp32" else 76
     achieved = bytes_site * sites / (ms_sc / n_sc * 1e-3) / 1e9 if n_sc else None
     traffic = _traffic_record(sites)
+    # the step's own kernels: the particle kernel dominates a single chain's
+    # step; it is latency-bound (100 cluster barriers per LB step) and has no
+    # byte or flop roofline, so the roofline is the lattice kernel's and the
+    # dominant kernel is named beside it with its share
+    kern_ms = {k: ktimes[k][1] for k in ("gather", "particles", "stream_collide", "source") if k in ktimes}
+    n_p = ktimes["particles"][0] if "particles" in ktimes else 0
+    dominant = None
+    if n_p:
+        dominant = {"kernel": "k_particles", "bound": "latency",
+                    "share_of_step_kernels": kern_ms["particles"] / sum(kern_ms.values()),
+                    "us_per_launch": 1e3 * kern_ms["particles"] / n_p,
+                    "us_per_md_substep": 1e3 * kern_ms["particles"] / n_p / (w["md_outer"] * w["md_inner"])}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "peak_kind": peak_kind, "kernel": "k_stream_collide",
-                "algorithmic_bytes_per_launch": bytes_site * sites}
+                "algorithmic_bytes_per_launch": bytes_site * sites, "dominant_kernel": dominant}
     shares = {k: {"launches": n, "ms_total": ms, "ms_per_launch": ms / n if n else None}
               for k, (n, ms) in ktimes.items()}
 

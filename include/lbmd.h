@@ -127,7 +127,23 @@ typedef struct lbmd_diag {
     double n_translocated;
     double dWH_dt;
     double dWE_dt;
+    double rg_untranslocated; /* as in lbmd_obs, from one-pass FP64 moments about the pore centre */
+    double rg_translocated;
 } lbmd_diag;
+
+/* Translocation record of one realization (Sec. IV.A durations, Sec. IV.B
+ * lambda_R = R_T(t_X) / R_U(0)).  A bead counts as translocated when its
+ * unwrapped x exceeds wall_x + 1/2; "at step n" means the state step n starts
+ * from (the state after n steps).  The particle kernel updates the record
+ * every step, after the origin, at no extra launch. */
+typedef struct lbmd_transloc {
+    int64_t t_origin;        /* step at which the record was last reset */
+    int64_t t_first;         /* first step >= t_origin with at least one bead translocated; -1 = none yet */
+    int64_t t_x;             /* first step >= t_origin with every bead translocated; -1 = none yet */
+    double rg_u_origin;      /* R_U at t_origin (-1 until that step has run) */
+    double rg_t_x;           /* R_T at t_x (-1 until then) */
+    double max_translocated; /* largest number of translocated beads seen at a step >= t_origin */
+} lbmd_transloc;
 
 typedef struct lbmd_kernel_time {
     char name[32];
@@ -166,6 +182,15 @@ lbmd_status lbmd_check(lbmd_handle *h);
  * n_real * max_rows rows, [realization][row], oldest first; *rows receives
  * the number of rows written per realization.  Synchronises the stream. */
 lbmd_status lbmd_diagnostics(lbmd_handle *h, lbmd_diag *out, int32_t max_rows, int32_t *rows);
+
+/* Translocation records of every realization (out: n_real entries; the
+ * duration of a completed event is t_x - t_origin).  Synchronises the stream. */
+lbmd_status lbmd_translocation(lbmd_handle *h, lbmd_transloc *out);
+
+/* Restart every realization's translocation record at the current step
+ * (t_origin = that step, everything else "none yet").  lbmd_init does this
+ * at step 0; setting beads or the step does not.  Asynchronous. */
+lbmd_status lbmd_reset_translocation(lbmd_handle *h);
 
 /* Fluid initial condition: f = f_eq(rho, u) at every fluid site.
  * rho: host [n_real][ns] or NULL (rho = 1); u: host [n_real][3][ns] or NULL (u = 0). */

@@ -531,6 +531,17 @@ __device__ __forceinline__ void sync_all(cg::cluster_group &cl, int C) {
     else __syncthreads();
 }
 
+// entries of the per-step bead diagnostics partial: 9 sums, then the
+// (first, second) moments of the untranslocated and translocated parts
+constexpr int NDIAG = 17;
+
+// radius of gyration of n beads from their moments m = (sum d, sum |d|^2)
+__device__ __forceinline__ double part_rg(const double *m, double n) {
+    if (n <= 0.0) return 0.0;
+    const double cx = m[0] / n, cy = m[1] / n, cz = m[2] / n;
+    return sqrt(fmax(0.0, m[3] / n - (cx * cx + cy * cy + cz * cz)));
+}
+
 // ---------------------------------------------------------------------------
 // the particle kernel (one cluster of C blocks per realization)
 // ---------------------------------------------------------------------------
@@ -538,8 +549,8 @@ template <int T>
 __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, const int Nmax, const int Nc) {
     extern __shared__ __align__(16) char smem_raw[];
     __shared__ int s_flag[2], s_err;
-    __shared__ double red[16][9];
-    __shared__ double cpart[MAX_CLUSTER][9];
+    __shared__ double red[16][NDIAG];
+    __shared__ double cpart[MAX_CLUSTER][NDIAG];
     PSmem sm;
     psmem_layout(Nmax, Nc, &sm, smem_raw);
     cg::cluster_group cl = cg::this_cluster();
@@ -585,24 +596,34 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
     build_lists(S, sm, 0, N, p, pl, owner, nullptr, &s_err);
     phase_mark(S, 1, tclk);
 
-    // per-step bead diagnostics at the starting state: block partial -> block 0
+    // per-step bead diagnostics at the starting state: block partial -> block 0.
+    // Entries 9..16 are the first and second moments of the untranslocated
+    // and translocated parts about the pore centre, for their radii of gyration.
     {
-        double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        double acc[NDIAG];
+#pragma unroll
+        for (int k = 0; k < NDIAG; ++k) acc[k] = 0.0;
         if (owner) {
             const float xw = ff_wrap(mh.x, ml.x, fnx, S.inx), yw = ff_wrap(mh.y, ml.y, fny, S.iny),
                         zw = ff_wrap(mh.z, ml.z, fnz, S.inz);
             const float Fe = in_channel(S, xw, yw, zw) ? S.E : 0.0f;
-            const double X = (double)mh.x + (double)ml.x;
+            const double X = (double)mh.x + (double)ml.x, Y = (double)mh.y + (double)ml.y,
+                         Z = (double)mh.z + (double)ml.z;
+            const bool tr = S.wall_x >= 0 && X > (double)S.wall_x + 0.5;
             acc[0] = v.x; acc[1] = v.y; acc[2] = v.z;
-            acc[3] = X; acc[4] = (double)mh.y + (double)ml.y; acc[5] = (double)mh.z + (double)ml.z;
-            acc[6] = (S.wall_x >= 0 && X > (double)S.wall_x + 0.5) ? 1.0 : 0.0;
+            acc[3] = X; acc[4] = Y; acc[5] = Z;
+            acc[6] = tr ? 1.0 : 0.0;
             acc[7] = (double)S.gamma * ((double)v.x * up.x + (double)v.y * up.y + (double)v.z * up.z);
             acc[8] = (double)Fe * v.x;
+            const double dx = X - (double)max(S.wall_x, 0), dy = Y - 0.5 * S.ny, dz = Z - 0.5 * S.nz;
+            const double d2 = dx * dx + dy * dy + dz * dz;
+            acc[9] = tr ? 0.0 : dx; acc[10] = tr ? 0.0 : dy; acc[11] = tr ? 0.0 : dz; acc[12] = tr ? 0.0 : d2;
+            acc[13] = tr ? dx : 0.0; acc[14] = tr ? dy : 0.0; acc[15] = tr ? dz : 0.0; acc[16] = tr ? d2 : 0.0;
         }
-        block_sum<9>(acc, red);
+        block_sum<NDIAG>(acc, red);
         if (threadIdx.x == 0) {
             double *dst = C > 1 ? cl.map_shared_rank(&cpart[rank][0], 0) : &cpart[0][0];
-            for (int k = 0; k < 9; ++k) dst[k] = acc[k];
+            for (int k = 0; k < NDIAG; ++k) dst[k] = acc[k];
         }
     }
 
@@ -750,17 +771,30 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
     phase_mark(S, 3, tclk);
     if (threadIdx.x == 0 && s_err) atomicOr(&S.ctrl->status, s_err);
     if (rank == 0 && threadIdx.x == 0) {
-        double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        double acc[NDIAG];
+        for (int k = 0; k < NDIAG; ++k) acc[k] = 0.0;
         for (int c = 0; c < C; ++c)
-            for (int k = 0; k < 9; ++k) acc[k] += cpart[c][k];
+            for (int k = 0; k < NDIAG; ++k) acc[k] += cpart[c][k];
         lbmd_diag *row = S.ring + (size_t)r * LBMD_DIAG_RING + (step % LBMD_DIAG_RING);
         row->step = step;
         row->p_beads[0] = acc[0]; row->p_beads[1] = acc[1]; row->p_beads[2] = acc[2];
         const double inv = N > 0 ? 1.0 / N : 0.0;
         row->com[0] = acc[3] * inv; row->com[1] = acc[4] * inv; row->com[2] = acc[5] * inv;
-        row->n_translocated = acc[6];
+        const double nT = acc[6], nU = (double)N - nT;
+        row->n_translocated = nT;
         row->dWH_dt = acc[7];
         row->dWE_dt = acc[8];
+        const double rgU = part_rg(acc + 9, nU), rgT = part_rg(acc + 13, nT);
+        row->rg_untranslocated = rgU;
+        row->rg_translocated = rgT;
+        // translocation record (Sec. IV.A first passage of the whole chain)
+        lbmd_transloc *ev = S.tl + r;
+        if (N > 0 && step >= ev->t_origin) {
+            if (step == ev->t_origin) ev->rg_u_origin = rgU;
+            if (nT > ev->max_translocated) ev->max_translocated = nT;
+            if (ev->t_first < 0 && nT > 0.0) ev->t_first = step;
+            if (ev->t_x < 0 && nT >= (double)N) { ev->t_x = step; ev->rg_t_x = rgT; }
+        }
     }
 }
 

@@ -24,7 +24,7 @@ constexpr double SKIN = 0.8;  // Verlet-list skin (lattice units)
 
 struct Layout {
     size_t popA, popB, staging, link, wallmask, tileflag, solid, G, stamp;
-    size_t r_hi, r_lo, v, up, J, pair_node, pair_w, bead_real, bead_off, partial, ring, obs, ctrl, rdone, loopc, snap, phase, total;
+    size_t r_hi, r_lo, v, up, J, pair_node, pair_w, bead_real, bead_off, partial, ring, obs, tl, ctrl, rdone, loopc, snap, phase, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -152,10 +152,12 @@ Layout layout_of(const lbmd_config *c, int total_beads) {
     L.partial = take(max_blocks * 4 * sizeof(double));
     L.ring = take((size_t)c->n_real * LBMD_DIAG_RING * sizeof(lbmd_diag));
     L.obs = take((size_t)c->n_real * sizeof(lbmd_obs));
+    L.tl = take((size_t)c->n_real * sizeof(lbmd_transloc));
     L.ctrl = take(sizeof(Ctrl));
     L.rdone = take((size_t)c->n_real * 2 * sizeof(unsigned int));
     L.loopc = take(sizeof(unsigned int));
-    L.snap = take(nb * 48);  // bead state saved while the autotuner times particle shapes
+    // bead state and translocation records saved while the autotuner times particle shapes
+    L.snap = take(nb * 48 + (size_t)c->n_real * sizeof(lbmd_transloc));
     L.phase = take(PHASES * sizeof(unsigned long long));
     L.total = o;
     return L;
@@ -258,6 +260,20 @@ __global__ void k_loop_tick(cudaGraphConditionalHandle hdl, unsigned int *remain
 }
 
 __global__ void k_set_u32(unsigned int *p, unsigned int v) { *p = v; }
+
+// restart every realization's translocation record at step origin
+__global__ void k_reset_transloc(lbmd_transloc *tl, int n_real, long long origin) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_real) return;
+    lbmd_transloc e;
+    e.t_origin = origin;
+    e.t_first = -1;
+    e.t_x = -1;
+    e.rg_u_origin = -1.0;
+    e.rg_t_x = -1.0;
+    e.max_translocated = 0.0;
+    tl[r] = e;
+}
 
 // Graph holding one conditional WHILE node whose body is two coupled steps
 // (A -> B -> A, so the buffers line up again) followed by the tick kernel.
@@ -564,6 +580,7 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
     S.partial = (double *)(b + L.partial);
     S.ring = (lbmd_diag *)(b + L.ring);
     S.obs = (lbmd_obs *)(b + L.obs);
+    S.tl = (lbmd_transloc *)(b + L.tl);
     S.ctrl = (Ctrl *)(b + L.ctrl);
     S.rdone = (unsigned int *)(b + L.rdone);
     S.phase = nullptr;
@@ -596,6 +613,7 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
     // the particle kernel needs its shared-memory size granted once
     if (md_shape(S).smem > 200 * 1024) { fail(h, LBMD_ERR_CAPACITY, "too many beads per realization for shared memory"); return bail(LBMD_ERR_CAPACITY); }
     lbmd_status s = lbmd_set_beads(h, r_init, nullptr);
+    if (s == LBMD_OK) s = lbmd_reset_translocation(h);
     if (s != LBMD_OK) return bail(s);
     *out = h;
     return LBMD_OK;
@@ -698,6 +716,22 @@ lbmd_status lbmd_diagnostics(lbmd_handle *h, lbmd_diag *out, int32_t max_rows, i
             out[(size_t)r * max_rows + k] = ring[(size_t)r * LBMD_DIAG_RING + (stp % LBMD_DIAG_RING)];
         }
     *rows = n;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_translocation(lbmd_handle *h, lbmd_transloc *out) {
+    if (!h || !out) return LBMD_ERR_INVALID_ARG;
+    CK(cudaMemcpyAsync(out, h->S.tl, (size_t)h->cfg.n_real * sizeof(lbmd_transloc), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_reset_translocation(lbmd_handle *h) {
+    if (!h) return LBMD_ERR_INVALID_ARG;
+    const int R = h->cfg.n_real;
+    k_reset_transloc<<<(R + 127) / 128, 128, 0, h->st>>>(h->S.tl, R, (long long)h->host_step);
+    CK(cudaGetLastError());
+    h->launches += 1;
     return LBMD_OK;
 }
 
@@ -1132,6 +1166,8 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
     CK(cudaMemcpyAsync(snap, h->S.r_hi, bb16, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(snap + bb16, h->S.r_lo, bb16, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(snap + 2 * bb16, h->S.v, bb16, cudaMemcpyDeviceToDevice, h->st));
+    const size_t tlb = (size_t)h->cfg.n_real * sizeof(lbmd_transloc);
+    CK(cudaMemcpyAsync(snap + 3 * bb16, h->S.tl, tlb, cudaMemcpyDeviceToDevice, h->st));
     static const int TS[] = {2, 4, 8};
     static const int CS[] = {1, 2, 4, 8};
     float best_md = 1e30f;
@@ -1167,6 +1203,7 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
     CK(cudaMemcpyAsync(h->S.r_hi, snap, bb16, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(h->S.r_lo, snap + bb16, bb16, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(h->S.v, snap + 2 * bb16, bb16, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(h->S.tl, snap + 3 * bb16, tlb, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemsetAsync(h->S.G, 0, (size_t)h->cfg.n_real * 3 * h->S.ns * 8, h->st));
     CK(cudaStreamSynchronize(h->st));
     cudaEventDestroy(a);

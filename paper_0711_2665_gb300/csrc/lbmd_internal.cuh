@@ -151,6 +151,7 @@ struct Sim {
     double *partial;         // [blocks][4]
     lbmd_diag *ring;         // [n_real][LBMD_DIAG_RING]
     lbmd_obs *obs;           // [n_real]
+    lbmd_transloc *tl;       // [n_real] translocation records
     Ctrl *ctrl;
     unsigned int *rdone;        // [2][n_real] blocks finished per realization (diag pass, observables pass)
     unsigned long long *phase;  // [PHASES] SM cycles per particle-kernel phase, or null

@@ -58,7 +58,14 @@ class Diag(ctypes.Structure):
     _fields_ = [("step", ctypes.c_int64), ("mass", ctypes.c_double), ("p_fluid", ctypes.c_double * 3),
                 ("p_beads", ctypes.c_double * 3), ("com", ctypes.c_double * 3),
                 ("n_translocated", ctypes.c_double), ("dWH_dt", ctypes.c_double),
-                ("dWE_dt", ctypes.c_double)]
+                ("dWE_dt", ctypes.c_double), ("rg_untranslocated", ctypes.c_double),
+                ("rg_translocated", ctypes.c_double)]
+
+
+class Transloc(ctypes.Structure):
+    _fields_ = [("t_origin", ctypes.c_int64), ("t_first", ctypes.c_int64), ("t_x", ctypes.c_int64),
+                ("rg_u_origin", ctypes.c_double), ("rg_t_x", ctypes.c_double),
+                ("max_translocated", ctypes.c_double)]
 
 
 class KernelTime(ctypes.Structure):
@@ -92,6 +99,8 @@ def lib():
         "lbmd_observables": [vp, P(Obs)],
         "lbmd_check": [vp],
         "lbmd_diagnostics": [vp, P(Diag), i32, P(i32)],
+        "lbmd_translocation": [vp, P(Transloc)],
+        "lbmd_reset_translocation": [vp],
         "lbmd_init_fluid": [vp, vp, vp],
         "lbmd_get_populations": [vp, vp],
         "lbmd_get_deviations": [vp, vp],
@@ -337,9 +346,24 @@ class Simulation:
                     "lbmd_diagnostics")
         dt = np.dtype([("step", np.int64), ("mass", np.float64), ("p_fluid", np.float64, 3),
                        ("p_beads", np.float64, 3), ("com", np.float64, 3),
-                       ("n_translocated", np.float64), ("dWH_dt", np.float64), ("dWE_dt", np.float64)])
+                       ("n_translocated", np.float64), ("dWH_dt", np.float64), ("dWE_dt", np.float64),
+                       ("rg_untranslocated", np.float64), ("rg_translocated", np.float64)])
         a = np.frombuffer(buf, dtype=dt).reshape(self.n_real, max_rows)
         return a[:, :rows.value].copy()
+
+    def translocation(self) -> np.ndarray:
+        """Translocation record of every realization (Sec. IV.A) as a structured
+        array: t_origin, t_first, t_x (-1 = not yet), rg_u_origin, rg_t_x,
+        max_translocated."""
+        arr = (Transloc * self.n_real)()
+        self._check(self._lib.lbmd_translocation(self._h, arr), "lbmd_translocation")
+        dt = np.dtype([("t_origin", np.int64), ("t_first", np.int64), ("t_x", np.int64),
+                       ("rg_u_origin", np.float64), ("rg_t_x", np.float64), ("max_translocated", np.float64)])
+        return np.frombuffer(arr, dtype=dt).copy()
+
+    def reset_translocation(self):
+        """Restart every translocation record at the current step."""
+        self._check(self._lib.lbmd_reset_translocation(self._h), "lbmd_reset_translocation")
 
     def profile(self, enable: bool):
         self._check(self._lib.lbmd_profile(self._h, int(bool(enable))), "lbmd_profile")

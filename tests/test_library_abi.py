@@ -24,16 +24,18 @@ def test_structs_match_header_layout(lbmd_lib, tmp_path):
     src = tmp_path / "sizes.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "lbmd.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(lbmd_config), sizeof(lbmd_obs),"
-        " sizeof(lbmd_diag), sizeof(lbmd_kernel_time), offsetof(lbmd_config, seed),"
-        " offsetof(lbmd_obs, step), offsetof(lbmd_config, precision)); return 0;}\n")
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(lbmd_config),"
+        " sizeof(lbmd_obs), sizeof(lbmd_diag), sizeof(lbmd_kernel_time), offsetof(lbmd_config, seed),"
+        " offsetof(lbmd_obs, step), offsetof(lbmd_config, precision), sizeof(lbmd_transloc),"
+        " offsetof(lbmd_transloc, rg_u_origin), offsetof(lbmd_diag, rg_translocated)); return 0;}\n")
     exe = tmp_path / "sizes"
     subprocess.check_call(["gcc", "-I", lbmd_lib.HEADER.rsplit("/", 1)[0], "-o", str(exe), str(src)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     assert got == [ctypes.sizeof(lbmd_lib.Config), ctypes.sizeof(lbmd_lib.Obs),
                    ctypes.sizeof(lbmd_lib.Diag), ctypes.sizeof(lbmd_lib.KernelTime),
                    lbmd_lib.Config.seed.offset, lbmd_lib.Obs.step.offset,
-                   lbmd_lib.Config.precision.offset]
+                   lbmd_lib.Config.precision.offset, ctypes.sizeof(lbmd_lib.Transloc),
+                   lbmd_lib.Transloc.rg_u_origin.offset, lbmd_lib.Diag.rg_translocated.offset]
 
 
 def _cfg(lbmd_lib, **kw):
