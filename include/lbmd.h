@@ -100,8 +100,8 @@ typedef struct lbmd_config {
 /* Observables of one realization at the current state (Sec. III global
  * momenta, Sec. IV.B radii of gyration, Sec. IV.C Eqs. 24-25 work rates). */
 typedef struct lbmd_obs {
-    double mass;              /* sum of rho over fluid sites (FP64 reduction) */
-    double p_fluid[3];        /* sum of rho u over fluid sites (FP64 reduction) */
+    double mass;              /* sum of rho over fluid sites (exact fixed-point sum of FP32 partials) */
+    double p_fluid[3];        /* sum of rho u over fluid sites (likewise) */
     double p_beads[3];        /* sum of bead velocities */
     double com[3];            /* centre of mass of the chain (unwrapped) */
     double n_translocated;    /* beads with x > wall_x + 1/2 (unwrapped) */
@@ -115,9 +115,13 @@ typedef struct lbmd_obs {
 } lbmd_obs;
 
 /* One row of the per-step diagnostics that each step records on the device
- * at no extra pass over the lattice: the fluid sums come from the
- * stream-collide kernel, the bead sums from the particle kernel, both for the
- * state at the start of the step. */
+ * at no extra pass over the lattice, for the state at the start of the step.
+ * The fluid sums come from the stream-collide kernel; the bead sums from a
+ * small kernel that runs beside it on the starting bead state the gather
+ * kernel saves.  Every sum is a 64-bit fixed-point integer sum (exact, the
+ * same in any order), converted to double at the end: mass and momentum at
+ * 2^-40 per FP32 partial, bead velocities and work rates at 2^-40, positions
+ * at 2^-36, squared distances at 2^-30. */
 typedef struct lbmd_diag {
     int64_t step;
     double mass;
@@ -127,7 +131,7 @@ typedef struct lbmd_diag {
     double n_translocated;
     double dWH_dt;
     double dWE_dt;
-    double rg_untranslocated; /* as in lbmd_obs, from one-pass FP64 moments about the pore centre */
+    double rg_untranslocated; /* as in lbmd_obs, two-pass: centroid, then distances to it */
     double rg_translocated;
 } lbmd_diag;
 
@@ -233,7 +237,7 @@ lbmd_status lbmd_step_loop(lbmd_handle *h, int64_t n);
 
 /* Launch shapes of the stream-collide kernel: block (32, by) threads, each
  * thread walking zc consecutive z planes.  by in {1,2,4,8,16}, zc in 1..64.
- * The state (populations, beads) is bit-identical for every shape; the FP64
+ * The state (populations, beads) is bit-identical for every shape; the
  * diagnostics sums group their FP32 per-thread partials by shape and so agree
  * to rounding only. */
 lbmd_status lbmd_set_tiles(lbmd_handle *h, int32_t by, int32_t zc);

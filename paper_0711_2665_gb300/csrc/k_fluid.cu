@@ -1,7 +1,7 @@
 // k_fluid.cu -- lattice kernels of the coupled LB-MD step:
 //   * the fused pull-scheme stream + bounce-back + moments + BGK collide
-//     (Sec. II, Eqs. 1-5, with the walls of Sec. III), with the per-step FP64
-//     mass/momentum diagnostics folded in;
+//     (Sec. II, Eqs. 1-5, with the walls of Sec. III), with the per-step
+//     mass/momentum diagnostics folded in as exact fixed-point sums;
 //   * the sparse source pass that adds the beads' reaction (Sec. II, Eq. 9) at
 //     the lattice sites the beads touched;
 //   * state transfer (equilibrium initialisation, pull to / push from the
@@ -11,78 +11,28 @@
 namespace lbmd {
 
 // ---------------------------------------------------------------------------
-// FP64 block reduction of four per-thread partials; writes partial[blk][0..3]
+// Fluid diagnostics sums.  Each block turns its threads' FP32 partials of
+// rho - 1 and rho u into 64-bit fixed point (fix_of), sums them exactly and
+// adds them to its realization's accumulator with four integer atomics: no
+// fence, no completion counter, and a result independent of order and of the
+// launch shape.  A later kernel in stream order reads the accumulator,
+// converts it to FP64 and zeroes it (the source kernel for the per-step row,
+// the bead observables kernel for the observables).  FP64 arithmetic, slow
+// on this GPU, is left to those few conversions.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void block_partial4(double a, double b, double c, double d, double *out) {
-    __shared__ double s[16][4];
+__device__ __forceinline__ void block_partial4(float a, float b, float c, float d, long long *acc, int *status) {
+    __shared__ long long s[16][4];
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     const int lane = tid & 31, warp = tid >> 5, nw = (blockDim.x * blockDim.y + 31) >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        b += __shfl_down_sync(0xffffffffu, b, o);
-        c += __shfl_down_sync(0xffffffffu, c, o);
-        d += __shfl_down_sync(0xffffffffu, d, o);
-    }
-    if (lane == 0) { s[warp][0] = a; s[warp][1] = b; s[warp][2] = c; s[warp][3] = d; }
+    if (!(isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d))) atomicOr(status, ST_NONFINITE);
+    const long long v0 = warp_sum_ll(fix_of(a, FIXD_FLUID)), v1 = warp_sum_ll(fix_of(b, FIXD_FLUID));
+    const long long v2 = warp_sum_ll(fix_of(c, FIXD_FLUID)), v3 = warp_sum_ll(fix_of(d, FIXD_FLUID));
+    if (lane == 0) { s[warp][0] = v0; s[warp][1] = v1; s[warp][2] = v2; s[warp][3] = v3; }
     __syncthreads();
-    if (tid == 0) {
-        double t0 = 0, t1 = 0, t2 = 0, t3 = 0;
-        for (int w = 0; w < nw; ++w) { t0 += s[w][0]; t1 += s[w][1]; t2 += s[w][2]; t3 += s[w][3]; }
-        out[0] = t0; out[1] = t1; out[2] = t2; out[3] = t3;
-    }
-}
-
-// Each realization has its own completion counter: the last of its bpr blocks
-// to finish sums that realization's block partials in a fixed order
-// (deterministic) and stores mass = n_fluid + sum(rho - 1) and the fluid
-// momentum.  MODE 1 writes the step's diagnostics row, MODE 2 the
-// observables.  No block ever waits for another, and the realizations of an
-// ensemble are finalised in parallel by different blocks.
-template <int MODE>
-__device__ void finalize_fluid_sums(const Sim &S, unsigned int *done, long long step, int bpr, int rr) {
-    __shared__ int am_last;
-    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-    const int nthreads = blockDim.x * blockDim.y;
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) am_last = (atomicAdd(done, 1u) == (unsigned int)bpr - 1u);
-    __syncthreads();
-    if (!am_last) return;
-    __threadfence();
-    __shared__ double red[16][4];
-    const int lane = tid & 31, warp = tid >> 5, nw = (nthreads + 31) >> 5;
-    double t[4] = {0, 0, 0, 0};
-    for (int b = tid; b < bpr; b += nthreads) {
-        const double *p = S.partial + 4 * ((size_t)rr * bpr + b);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) t[k] += __ldcg(p + k);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) t[k] += __shfl_down_sync(0xffffffffu, t[k], o);
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) red[warp][k] = t[k];
-    __syncthreads();
-    if (tid == 0) {
-        double u[4] = {0, 0, 0, 0};
-        for (int w = 0; w < nw; ++w)
-            for (int k = 0; k < 4; ++k) u[k] += red[w][k];
-        const double mass = S.n_fluid + u[0];
-        if (!isfinite(mass) || !isfinite(u[1]) || !isfinite(u[2]) || !isfinite(u[3]))
-            atomicOr(&S.ctrl->status, ST_NONFINITE);
-        if (MODE == 1) {
-            lbmd_diag *row = S.ring + (size_t)rr * LBMD_DIAG_RING + (step % LBMD_DIAG_RING);
-            row->mass = mass;
-            row->p_fluid[0] = u[1]; row->p_fluid[1] = u[2]; row->p_fluid[2] = u[3];
-        } else {
-            lbmd_obs *o = S.obs + rr;
-            o->mass = mass;
-            o->p_fluid[0] = u[1]; o->p_fluid[1] = u[2]; o->p_fluid[2] = u[3];
-        }
-        *done = 0u;
+    if (tid < 4) {
+        long long t = 0;
+        for (int w = 0; w < nw; ++w) t += s[w][tid];
+        if (t != 0) atomicAdd(reinterpret_cast<unsigned long long *>(acc) + tid, (unsigned long long)t);
     }
 }
 
@@ -97,7 +47,7 @@ __device__ void finalize_fluid_sums(const Sim &S, unsigned int *done, long long 
 // 2: sums only (observables).
 // ---------------------------------------------------------------------------
 template <int PREC, int MODE, int U, bool FL>
-__global__ void __launch_bounds__(512) k_stream_collide(const Sim S, const void *__restrict__ Av,
+__global__ void __launch_bounds__(512, FL ? 1 : 2) k_stream_collide(const Sim S, const void *__restrict__ Av,
                                                         void *__restrict__ Bv, const int zc,
                                                         const int nzb) {
     using T = typename PopT<PREC>::T;
@@ -219,13 +169,8 @@ __global__ void __launch_bounds__(512) k_stream_collide(const Sim S, const void 
           }
         }
     }
-    if (MODE != 0) {
-        const int bpr = gridDim.x * gridDim.y * nzb;
-        const int blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-        block_partial4((double)am, (double)ax, (double)ay, (double)az, S.partial + 4 * (size_t)blk);
-        if (MODE == 1) finalize_fluid_sums<1>(S, S.rdone + r, step, bpr, r);
-        else finalize_fluid_sums<2>(S, S.rdone + S.n_real + r, 0, bpr, r);
-    }
+    if (MODE != 0)
+        block_partial4(am, ax, ay, az, S.fsum + 4 * ((size_t)(MODE == 2 ? S.n_real : 0) + r), &S.ctrl->status);
 }
 
 static dim3 sc_grid(const Sim &S, int by, int zc, int *nzb) {
@@ -275,7 +220,9 @@ cudaError_t launch_fluid_observables(const Sim &S, const void *A, cudaStream_t s
 // touched this step, f*_i += 3 w_i G.c_i with G the momentum the beads handed
 // to the fluid there; G is then cleared.  Sites are found through the list of
 // (bead, corner) pairs; the first pair to stamp a site with this step's tag
-// applies its source.  The last block to finish advances the step counter.
+// applies its source.  Thread r also completes realization r's diagnostics
+// row with the fluid sums of the step's lattice pass.  The last block to
+// finish advances the step counter.
 // ---------------------------------------------------------------------------
 template <int PREC>
 __global__ void __launch_bounds__(256) k_source(const Sim S, void *__restrict__ Bv) {
@@ -307,6 +254,19 @@ __global__ void __launch_bounds__(256) k_source(const Sim S, void *__restrict__ 
             }
         }
     }
+    // the lattice pass of this step has finished: thread r writes the fluid
+    // part of realization r's diagnostics row and clears its accumulator
+    if (k < S.n_real) {
+        long long *acc = S.fsum + 4 * (size_t)k;
+        const double unit = fix_unit(FIXD_FLUID);
+        lbmd_diag *row = S.ring + (size_t)k * LBMD_DIAG_RING + (step % LBMD_DIAG_RING);
+        row->step = step;
+        row->mass = S.n_fluid + (double)acc[0] * unit;
+        row->p_fluid[0] = (double)acc[1] * unit;
+        row->p_fluid[1] = (double)acc[2] * unit;
+        row->p_fluid[2] = (double)acc[3] * unit;
+        acc[0] = 0; acc[1] = 0; acc[2] = 0; acc[3] = 0;
+    }
     __shared__ int am_last;
     __threadfence();
     __syncthreads();
@@ -320,7 +280,7 @@ __global__ void __launch_bounds__(256) k_source(const Sim S, void *__restrict__ 
 
 cudaError_t launch_source(const Sim &S, void *B, cudaStream_t st) {
     const int threads = 256;
-    const int blocks = max(1, (8 * S.total_beads + threads - 1) / threads);
+    const int blocks = max(1, (max(8 * S.total_beads, S.n_real) + threads - 1) / threads);
     if (S.precision == LBMD_FP16DEV) k_source<1><<<blocks, threads, 0, st>>>(S, B);
     else k_source<0><<<blocks, threads, 0, st>>>(S, B);
     return cudaGetLastError();

@@ -20,9 +20,12 @@
 // replica of the whole chain's positions in shared memory; a bead's new
 // position is written to all C replicas through distributed shared memory
 // before the cluster barrier of each sub-step.  Bead-bead pairs come from a
-// Verlet list (cut-off + skin) built from a cell hash in shared memory, rebuilt
-// whenever any bead has moved more than half the skin since the last build,
-// so the pair set equals all pairs inside the cut-off at every evaluation.
+// Verlet list (cut-off + skin), built by a scan of the whole chain by all
+// lanes (chains up to 512 beads) or from a cell hash in shared memory, and
+// rebuilt whenever any bead has moved more than half the skin since the last
+// build, so the pair set equals all pairs inside the cut-off at every
+// evaluation.  The bead diagnostics of the step are summed by their own
+// kernel, beside this one, from the starting state the gather saves.
 #include <cooperative_groups.h>
 
 #include "lbmd_internal.cuh"
@@ -142,11 +145,153 @@ __global__ void __launch_bounds__(256) k_gather(const Sim S, const void *__restr
                                  ff_wrap(qh.z, ql.z, (float)S.nz, S.inz), node, W);
     const int lane = threadIdx.x & 31;
     if (lane == 0) S.up[g] = make_float4(u.x, u.y, u.z, 0.f);
+    // the starting state, for the step's bead diagnostics (the particle
+    // kernel overwrites r and v while the lattice pass that sums them runs)
+    if (lane == 1) S.bsnap[g] = qh;
+    if (lane == 2) S.bsnap[S.total_beads + g] = ql;
+    if (lane == 3) S.bsnap[2 * S.total_beads + g] = S.v[g];
     if ((lane & 3) == 0) {
         const int c = lane >> 2;
         S.pair_node[(size_t)g * 8 + c] = W > 0.0f ? (int)((size_t)r * S.ns + node) : -1;
         S.pair_w[(size_t)g * 8 + c] = W;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Bead part of the per-step diagnostics row (one block per realization), from
+// the starting state the gather kernel saved; it runs beside the lattice pass
+// and the particle kernel.  Every term enters as 64-bit fixed point
+// (fix_of): exact sums, in any order.
+// ---------------------------------------------------------------------------
+// x - c for x = hi + lo and c = chi + clo, as a float-float pair (h, l):
+// Knuth's two-sum of hi and -chi, then the low parts added to the error term
+__device__ __forceinline__ void diff_ff(float hi, float lo, float chi, float clo, float &h, float &l) {
+    h = hi - chi;
+    const float bb = h - hi;
+    l = ((hi - (h - bb)) + (-chi - bb)) + (lo - clo);
+}
+
+// One pass over the realization's beads, adding its terms into sb:
+//   PASS 0: momentum, translocated count, work rates   -> sb 0, 1, 2, 6, 7, 8
+//   PASS 1: positions of all beads and of the translocated ones -> 3-5, 9-11
+//   PASS 2: |r - c|^2 about each part's centroid c (in cen)     -> 12, 13
+template <int PASS>
+__device__ __forceinline__ void bead_sum_pass(const Sim &S, int off, int N, unsigned long long *sb, const float *cen) {
+    constexpr int NV = PASS == 2 ? 2 : 6;
+    const int TB = S.total_beads;
+    const float thr = (float)S.wall_x + 0.5f;
+    long long a[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) a[k] = 0;
+    const int trips = (N + blockDim.x - 1) / blockDim.x;  // uniform over the block
+    for (int it = 0; it < trips; ++it) {
+        const int q = it * blockDim.x + threadIdx.x;
+        if (q >= N) continue;
+        const float4 h = S.bsnap[off + q], l = S.bsnap[TB + off + q];
+        // x = hi + lo > thr, exactly: a stored position is normalised
+        // (|lo| <= ulp(hi) / 2), so hi decides unless it equals thr
+        const bool tr = S.wall_x >= 0 && (h.x > thr || (h.x == thr && l.x > 0.0f));
+        if constexpr (PASS == 0) {
+            const float4 v = S.bsnap[2 * TB + off + q], u = S.up[off + q];
+            const bool ch = in_channel(S, ff_wrap(h.x, l.x, (float)S.nx, S.inx), ff_wrap(h.y, l.y, (float)S.ny, S.iny),
+                                       ff_wrap(h.z, l.z, (float)S.nz, S.inz));
+            a[0] += fix_of(v.x, FIXD_V); a[1] += fix_of(v.y, FIXD_V); a[2] += fix_of(v.z, FIXD_V);
+            a[3] += tr ? 1 : 0;
+            a[4] += fix_of(S.gamma * fmaf(v.x, u.x, fmaf(v.y, u.y, v.z * u.z)), FIXD_V);
+            a[5] += ch ? fix_of(S.E * v.x, FIXD_V) : 0;
+        } else if constexpr (PASS == 1) {
+            const long long X = fix_of(h.x, FIXD_X) + fix_of(l.x, FIXD_X);
+            const long long Y = fix_of(h.y, FIXD_X) + fix_of(l.y, FIXD_X);
+            const long long Z = fix_of(h.z, FIXD_X) + fix_of(l.z, FIXD_X);
+            a[0] += X; a[1] += Y; a[2] += Z;
+            a[3] += tr ? X : 0; a[4] += tr ? Y : 0; a[5] += tr ? Z : 0;
+        } else {
+            const float *c = cen + (tr ? 6 : 0);  // (hi, lo) per axis of this bead's part
+            const float hc[3] = {h.x, h.y, h.z}, lc[3] = {l.x, l.y, l.z};
+            long long d2 = 0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                float dh, dl;
+                diff_ff(hc[k], lc[k], c[2 * k], c[2 * k + 1], dh, dl);
+                // d^2 = p + e up to the dl^2 term, p + e from one exact product
+                const float p = dh * dh;
+                const float e = fmaf(2.0f * dh, dl, fmaf(dh, dh, -p));
+                d2 += fix_of(p, FIXD_D2) + fix_of(e, FIXD_D2);
+            }
+            a[tr ? 1 : 0] += d2;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const long long w = warp_sum_ll(a[k]);
+        const int dst = PASS == 0 ? (k < 3 ? k : k + 3) : (PASS == 1 ? (k < 3 ? 3 + k : 6 + k) : 12 + k);
+        if ((threadIdx.x & 31) == 0 && w != 0) atomicAdd(sb + dst, (unsigned long long)w);
+    }
+}
+
+// Bead momentum, centre of mass, translocated count (x > wall_x + 1/2,
+// unwrapped), the work rates gamma v.u_p and F_E.v (Sec. IV.C), and the radii
+// of gyration of the untranslocated and translocated parts, two-pass:
+// centroids from exact sums, then the squared distances to them (Sec. IV.B).
+// Thread 0 writes them into the step's row and advances the realization's
+// translocation record (Sec. IV.A).
+__global__ void __launch_bounds__(256) k_bead_diag(const Sim S) {
+    __shared__ unsigned long long sb[14];
+    __shared__ float cen[12];
+    const int rr = blockIdx.x, tid = threadIdx.x;
+    const int off = S.bead_off[rr], N = S.bead_off[rr + 1] - off;
+    const long long step = S.ctrl->step;
+    if (tid < 14) sb[tid] = 0ull;
+    __syncthreads();
+    bead_sum_pass<0>(S, off, N, sb, cen);
+    bead_sum_pass<1>(S, off, N, sb, cen);
+    __syncthreads();
+    const long long nTi = (long long)sb[6];
+    const double nT = (double)nTi, nU = (double)(N - nTi);
+    const double ux = fix_unit(FIXD_X);
+    if (tid < 6) {  // centroid of the untranslocated (0..2) or translocated (3..5) part, one axis
+        const int k = tid % 3;
+        const bool t = tid >= 3;
+        const long long all = (long long)sb[3 + k], trs = (long long)sb[9 + k];
+        const double n = t ? nT : nU;
+        const double c = n > 0 ? (double)(t ? trs : all - trs) * ux / n : 0.0;
+        const float chi = (float)c;
+        cen[(t ? 6 : 0) + 2 * k] = chi;
+        cen[(t ? 6 : 0) + 2 * k + 1] = (float)(c - (double)chi);
+    }
+    __syncthreads();
+    bead_sum_pass<2>(S, off, N, sb, cen);
+    __syncthreads();
+    if (tid != 0) return;
+    const double uv = fix_unit(FIXD_V), ud = fix_unit(FIXD_D2);
+    lbmd_diag *row = S.ring + (size_t)rr * LBMD_DIAG_RING + (step % LBMD_DIAG_RING);
+    row->p_beads[0] = (double)(long long)sb[0] * uv;
+    row->p_beads[1] = (double)(long long)sb[1] * uv;
+    row->p_beads[2] = (double)(long long)sb[2] * uv;
+    const double inv = N > 0 ? ux / N : 0.0;
+    row->com[0] = (double)(long long)sb[3] * inv;
+    row->com[1] = (double)(long long)sb[4] * inv;
+    row->com[2] = (double)(long long)sb[5] * inv;
+    row->n_translocated = nT;
+    row->dWH_dt = (double)(long long)sb[7] * uv;
+    row->dWE_dt = (double)(long long)sb[8] * uv;
+    const double rgU = nU > 0 ? sqrt((double)(long long)sb[12] * ud / nU) : 0.0;
+    const double rgT = nT > 0 ? sqrt((double)(long long)sb[13] * ud / nT) : 0.0;
+    row->rg_untranslocated = rgU;
+    row->rg_translocated = rgT;
+    lbmd_transloc *ev = S.tl + rr;
+    if (N > 0 && step >= ev->t_origin) {
+        if (step == ev->t_origin) ev->rg_u_origin = rgU;
+        if (nT > ev->max_translocated) ev->max_translocated = nT;
+        if (ev->t_first < 0 && nTi > 0) ev->t_first = step;
+        if (ev->t_x < 0 && nTi >= N) { ev->t_x = step; ev->rg_t_x = rgT; }
+    }
+}
+
+cudaError_t launch_bead_diag(const Sim &S, cudaStream_t st) {
+    if (S.total_beads == 0) return cudaSuccess;
+    k_bead_diag<<<S.n_real, 256, 0, st>>>(S);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_gather(const Sim &S, const void *A, cudaStream_t st) {
@@ -239,13 +384,13 @@ MdShape md_shape(const Sim &S) {
 // p-1, p, p+1; WCA with the listed beads and solid sites.  The lanes' parts
 // add up to the full force.  Every lane of the warp must call this (own or
 // not): the list loops run to a warp-uniform trip count.
+// bonded_part: the bond and angle terms, which read beads p-2 .. p+2 only;
+// pair_part: adds the pair- and wall-list terms to them.  force_part is both.
 template <int T>
-__device__ __forceinline__ float3 force_part(const Sim &S, const PSmem &sm, int buf, bool own, int p, int pl, int N, float4 mh,
-                                             float4 ml, int lt) {
+__device__ __forceinline__ float3 bonded_part(const Sim &S, const PSmem &sm, int buf, bool own, int p, int N, float4 mh,
+                                              float4 ml, int lt) {
     float3 F = make_float3(0.f, 0.f, 0.f);
     const float4 *ph = sm.ph[buf], *plo = sm.pl[buf];
-    const int nn = own ? (int)sm.nn[pl] : 0, nw = own ? (int)sm.nw[pl] : 0;
-    const int nn_w = __reduce_max_sync(0xffffffffu, nn), nw_w = __reduce_max_sync(0xffffffffu, nw);
     if (own) {
         if constexpr (T >= 3) {
             // Lane lt (< 3) takes the angle whose beads are a = p+lt-2,
@@ -312,6 +457,15 @@ __device__ __forceinline__ float3 force_part(const Sim &S, const PSmem &sm, int 
             }
         }
     }
+    return F;
+}
+
+template <int T>
+__device__ __forceinline__ float3 pair_part(const Sim &S, const PSmem &sm, int buf, bool own, int p, int pl, float4 mh,
+                                            float4 ml, int lt, float3 F) {
+    const float4 *ph = sm.ph[buf], *plo = sm.pl[buf];
+    const int nn = own ? (int)sm.nn[pl] : 0, nw = own ? (int)sm.nw[pl] : 0;
+    const int nn_w = __reduce_max_sync(0xffffffffu, nn), nw_w = __reduce_max_sync(0xffffffffu, nw);
     const float fnx = (float)S.nx, fny = (float)S.ny, fnz = (float)S.nz;
     // Pair and wall lists, two entries per iteration, to the warp's longest
     // list: both entries' shared-memory loads are issued before either is
@@ -357,6 +511,12 @@ __device__ __forceinline__ float3 force_part(const Sim &S, const PSmem &sm, int 
     return F;
 }
 
+template <int T>
+__device__ __forceinline__ float3 force_part(const Sim &S, const PSmem &sm, int buf, bool own, int p, int pl, int N, float4 mh,
+                                             float4 ml, int lt) {
+    return pair_part<T>(S, sm, buf, own, p, pl, mh, ml, lt, bonded_part<T>(S, sm, buf, own, p, N, mh, ml, lt));
+}
+
 // sum over the T consecutive lanes of a bead (fixed butterfly: deterministic)
 template <int T>
 __device__ __forceinline__ float3 group_sum(float3 F) {
@@ -393,9 +553,49 @@ __device__ __forceinline__ void cell_of(const Sim &S, float xw, float yw, float 
 // Rebuild the lists of the block's beads from the block's replica (buffer
 // buf).  Called by every thread of the block; clear_flag (if not null) is
 // reset once every thread has read it.
-__device__ void build_lists(const Sim &S, const PSmem &sm, int buf, int N, int p, int pl, bool owner,
+// Pair list of bead p by its T lanes over every bead of the chain in
+// ascending order: lane lt tests q = kT + lt and a ballot over the bead's
+// lanes compacts the hits, so the list comes out sorted (the order the
+// hashed build reaches by insertion) with no hash and no sort.  Every lane of
+// the warp runs the same trip count: no divergence.
+template <int T>
+__device__ __forceinline__ int scan_pairs(const Sim &S, const float4 *ph, const float4 *plo, int N, int p, bool own,
+                                          uint16_t *lst) {
+    const float fnx = (float)S.nx, fny = (float)S.ny, fnz = (float)S.nz;
+    const int lane = threadIdx.x & 31, lt = lane & (T - 1);
+    const int pself = own ? p : 0;
+    const float4 mh = ph[pself], ml = plo[pself];
+    const unsigned gshift = (unsigned)(lane - lt);
+    const unsigned gmask = T == 32 ? 0xffffffffu : ((1u << T) - 1u);
+    const unsigned below = (1u << lt) - 1u;
+    int n = 0;
+    for (int base = 0; base < N; base += T) {
+        const int q = base + lt;
+        const int qq = q < N ? q : pself;
+        const float4 qh = ph[qq], ql = plo[qq];
+        const float dx = ff_diff(mh.x, ml.x, qh.x, ql.x, fnx, S.inx), dy = ff_diff(mh.y, ml.y, qh.y, ql.y, fny, S.iny),
+                    dz = ff_diff(mh.z, ml.z, qh.z, ql.z, fnz, S.inz);
+        const bool hit = own && q < N && (q < p - 1 || q > p + 1) && dx * dx + dy * dy + dz * dz < S.rl2;
+        const unsigned g = (__ballot_sync(0xffffffffu, hit) >> gshift) & gmask;
+        if (hit) {
+            const int pos = n + __popc(g & below);
+            if (pos < NBR_CAP) lst[pos] = (uint16_t)q;
+        }
+        n += __popc(g);
+    }
+    return n;
+}
+
+// Bead-bead and bead-wall lists of the block's beads from replica buf.
+// Chains of up to BRUTE_MAX beads use scan_pairs (every lane of the block
+// busy); longer ones a cell hash in shared memory, scanned by one lane per
+// bead.  Both give each bead's pairs within the list radius in ascending order.
+template <int T>
+__device__ void build_lists(const Sim &S, const PSmem &sm, int buf, int N, int p, int pl, bool own,
                             int *clear_flag, int *s_err) {
-    const bool hashed = S.ncell[0] >= 3 && S.ncell[1] >= 3 && S.ncell[2] >= 3;
+    const bool owner = own && (threadIdx.x % T) == 0;
+    const bool brute = N <= BRUTE_MAX;
+    const bool hashed = !brute && S.ncell[0] >= 3 && S.ncell[1] >= 3 && S.ncell[2] >= 3;
     const float fnx = (float)S.nx, fny = (float)S.ny, fnz = (float)S.nz;
     const float4 *ph = sm.ph[buf], *plo = sm.pl[buf];
     if (hashed)
@@ -419,12 +619,14 @@ __device__ void build_lists(const Sim &S, const PSmem &sm, int buf, int N, int p
         }
     }
     __syncthreads();
+    int n_scan = 0;
+    if (brute) n_scan = scan_pairs<T>(S, ph, plo, N, p, own, sm.nbr + (own ? pl : 0) * NBR_CAP);
     if (owner) {
         const float4 mh = ph[p], ml = plo[p];
         const float xw = ff_wrap(mh.x, ml.x, fnx, S.inx), yw = ff_wrap(mh.y, ml.y, fny, S.iny),
                     zw = ff_wrap(mh.z, ml.z, fnz, S.inz);
         uint16_t *lst = sm.nbr + pl * NBR_CAP;
-        int n = 0;
+        int n = n_scan;
         auto consider = [&](int q) {
             if (q == p || q == p - 1 || q == p + 1) return;
             const float4 qh = ph[q], ql = plo[q];
@@ -432,7 +634,9 @@ __device__ void build_lists(const Sim &S, const PSmem &sm, int buf, int N, int p
                         dz = ff_diff(mh.z, ml.z, qh.z, ql.z, fnz, S.inz);
             if (dx * dx + dy * dy + dz * dz < S.rl2) list_insert(lst, n, q);
         };
-        if (hashed) {
+        if (brute) {
+            // done by scan_pairs
+        } else if (hashed) {
             int ci, cj, ck;
             cell_of(S, xw, yw, zw, ci, cj, ck);
             for (int dk = -1; dk <= 1; ++dk)
@@ -531,17 +735,6 @@ __device__ __forceinline__ void sync_all(cg::cluster_group &cl, int C) {
     else __syncthreads();
 }
 
-// entries of the per-step bead diagnostics partial: 9 sums, then the
-// (first, second) moments of the untranslocated and translocated parts
-constexpr int NDIAG = 17;
-
-// radius of gyration of n beads from their moments m = (sum d, sum |d|^2)
-__device__ __forceinline__ double part_rg(const double *m, double n) {
-    if (n <= 0.0) return 0.0;
-    const double cx = m[0] / n, cy = m[1] / n, cz = m[2] / n;
-    return sqrt(fmax(0.0, m[3] / n - (cx * cx + cy * cy + cz * cz)));
-}
-
 // ---------------------------------------------------------------------------
 // the particle kernel (one cluster of C blocks per realization)
 // ---------------------------------------------------------------------------
@@ -549,8 +742,6 @@ template <int T>
 __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, const int Nmax, const int Nc) {
     extern __shared__ __align__(16) char smem_raw[];
     __shared__ int s_flag[2], s_err;
-    __shared__ double red[16][NDIAG];
-    __shared__ double cpart[MAX_CLUSTER][NDIAG];
     PSmem sm;
     psmem_layout(Nmax, Nc, &sm, smem_raw);
     cg::cluster_group cl = cg::this_cluster();
@@ -593,39 +784,8 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
     // block writes into another's shared memory
     sync_all(cl, C);
     phase_mark(S, 0, tclk);
-    build_lists(S, sm, 0, N, p, pl, owner, nullptr, &s_err);
+    build_lists<T>(S, sm, 0, N, p, pl, own, nullptr, &s_err);
     phase_mark(S, 1, tclk);
-
-    // per-step bead diagnostics at the starting state: block partial -> block 0.
-    // Entries 9..16 are the first and second moments of the untranslocated
-    // and translocated parts about the pore centre, for their radii of gyration.
-    {
-        double acc[NDIAG];
-#pragma unroll
-        for (int k = 0; k < NDIAG; ++k) acc[k] = 0.0;
-        if (owner) {
-            const float xw = ff_wrap(mh.x, ml.x, fnx, S.inx), yw = ff_wrap(mh.y, ml.y, fny, S.iny),
-                        zw = ff_wrap(mh.z, ml.z, fnz, S.inz);
-            const float Fe = in_channel(S, xw, yw, zw) ? S.E : 0.0f;
-            const double X = (double)mh.x + (double)ml.x, Y = (double)mh.y + (double)ml.y,
-                         Z = (double)mh.z + (double)ml.z;
-            const bool tr = S.wall_x >= 0 && X > (double)S.wall_x + 0.5;
-            acc[0] = v.x; acc[1] = v.y; acc[2] = v.z;
-            acc[3] = X; acc[4] = Y; acc[5] = Z;
-            acc[6] = tr ? 1.0 : 0.0;
-            acc[7] = (double)S.gamma * ((double)v.x * up.x + (double)v.y * up.y + (double)v.z * up.z);
-            acc[8] = (double)Fe * v.x;
-            const double dx = X - (double)max(S.wall_x, 0), dy = Y - 0.5 * S.ny, dz = Z - 0.5 * S.nz;
-            const double d2 = dx * dx + dy * dy + dz * dz;
-            acc[9] = tr ? 0.0 : dx; acc[10] = tr ? 0.0 : dy; acc[11] = tr ? 0.0 : dz; acc[12] = tr ? 0.0 : d2;
-            acc[13] = tr ? dx : 0.0; acc[14] = tr ? dy : 0.0; acc[15] = tr ? dz : 0.0; acc[16] = tr ? d2 : 0.0;
-        }
-        block_sum<NDIAG>(acc, red);
-        if (threadIdx.x == 0) {
-            double *dst = C > 1 ? cl.map_shared_rank(&cpart[rank][0], 0) : &cpart[0][0];
-            for (int k = 0; k < NDIAG; ++k) dst[k] = acc[k];
-        }
-    }
 
     // MD cycle
     const float dt = 1.0f / (float)S.M, h = 0.5f * dt;
@@ -691,7 +851,7 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
             buf = nb;
             if (s_flag[t & 1]) {
                 const unsigned long long t0 = clock64();
-                build_lists(S, sm, buf, N, p, pl, owner, &s_flag[t & 1], &s_err);
+                build_lists<T>(S, sm, buf, N, p, pl, own, &s_flag[t & 1], &s_err);
                 bh = mh;
                 bl = ml;
                 if (S.phase && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -765,37 +925,11 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
         if (trj) trj[(size_t)traj_slot_J(S.M, S.Mb) * TB + off + p] = make_float4(J.x, J.y, J.z, 0.f);
         if (!isfinite(mh.x + mh.y + mh.z + v.x + v.y + v.z)) atomicOr(&s_err, ST_NONFINITE);
     }
-    // no block leaves while another may still write into its shared memory;
-    // after this barrier block 0 holds every block's diagnostics partial
-    sync_all(cl, C);
+    // the last writes into another block's shared memory came before the
+    // last sub-step's cluster barrier; this one collects the error flags
+    __syncthreads();
     phase_mark(S, 3, tclk);
     if (threadIdx.x == 0 && s_err) atomicOr(&S.ctrl->status, s_err);
-    if (rank == 0 && threadIdx.x == 0) {
-        double acc[NDIAG];
-        for (int k = 0; k < NDIAG; ++k) acc[k] = 0.0;
-        for (int c = 0; c < C; ++c)
-            for (int k = 0; k < NDIAG; ++k) acc[k] += cpart[c][k];
-        lbmd_diag *row = S.ring + (size_t)r * LBMD_DIAG_RING + (step % LBMD_DIAG_RING);
-        row->step = step;
-        row->p_beads[0] = acc[0]; row->p_beads[1] = acc[1]; row->p_beads[2] = acc[2];
-        const double inv = N > 0 ? 1.0 / N : 0.0;
-        row->com[0] = acc[3] * inv; row->com[1] = acc[4] * inv; row->com[2] = acc[5] * inv;
-        const double nT = acc[6], nU = (double)N - nT;
-        row->n_translocated = nT;
-        row->dWH_dt = acc[7];
-        row->dWE_dt = acc[8];
-        const double rgU = part_rg(acc + 9, nU), rgT = part_rg(acc + 13, nT);
-        row->rg_untranslocated = rgU;
-        row->rg_translocated = rgT;
-        // translocation record (Sec. IV.A first passage of the whole chain)
-        lbmd_transloc *ev = S.tl + r;
-        if (N > 0 && step >= ev->t_origin) {
-            if (step == ev->t_origin) ev->rg_u_origin = rgU;
-            if (nT > ev->max_translocated) ev->max_translocated = nT;
-            if (ev->t_first < 0 && nT > 0.0) ev->t_first = step;
-            if (ev->t_x < 0 && nT >= (double)N) { ev->t_x = step; ev->rg_t_x = rgT; }
-        }
-    }
 }
 
 template <int T>
@@ -909,6 +1043,14 @@ __global__ void __launch_bounds__(1024) k_bead_observables(const Sim S, const vo
     block_sum<2>(g2, red2);
     if (threadIdx.x == 0) {
         lbmd_obs *o = S.obs + r;
+        // fluid sums of the observables pass of the lattice kernel (run before this)
+        long long *acc = S.fsum + 4 * ((size_t)S.n_real + r);
+        const double unit = fix_unit(FIXD_FLUID);
+        o->mass = S.n_fluid + (double)acc[0] * unit;
+        o->p_fluid[0] = (double)acc[1] * unit;
+        o->p_fluid[1] = (double)acc[2] * unit;
+        o->p_fluid[2] = (double)acc[3] * unit;
+        acc[0] = 0; acc[1] = 0; acc[2] = 0; acc[3] = 0;
         o->p_beads[0] = s_sum[0]; o->p_beads[1] = s_sum[1]; o->p_beads[2] = s_sum[2];
         const double inv = N > 0 ? 1.0 / N : 0.0;
         o->com[0] = s_sum[3] * inv; o->com[1] = s_sum[4] * inv; o->com[2] = s_sum[5] * inv;

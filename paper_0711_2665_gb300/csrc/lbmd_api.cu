@@ -17,14 +17,14 @@ using namespace lbmd;
 namespace {
 
 constexpr int K_GATHER = 0, K_PARTICLES = 1, K_STREAM_COLLIDE = 2, K_SOURCE = 3, K_SC_ADJOINT = 4,
-              K_BEAD_ADJOINT = 5, K_ADJ_FIXUP = 6, K_COUNT = 7;
+              K_BEAD_ADJOINT = 5, K_ADJ_FIXUP = 6, K_BEAD_DIAG = 7, K_COUNT = 8;
 const char *KNAMES[K_COUNT] = {"gather", "particles", "stream_collide", "source", "sc_adjoint", "bead_adjoint",
-                               "adj_fixup"};
+                               "adj_fixup", "bead_diag"};
 constexpr double SKIN = 0.8;  // Verlet-list skin (lattice units)
 
 struct Layout {
     size_t popA, popB, staging, link, wallmask, tileflag, solid, G, stamp;
-    size_t r_hi, r_lo, v, up, J, pair_node, pair_w, bead_real, bead_off, partial, ring, obs, tl, ctrl, rdone, loopc, snap, phase, total;
+    size_t r_hi, r_lo, v, up, J, pair_node, pair_w, bead_real, bead_off, bsnap, fsum, ring, obs, tl, ctrl, loopc, snap, phase, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -46,8 +46,8 @@ struct lbmd_handle {
     float *staging = nullptr;
     std::vector<int32_t> offsets;
     int total_beads = 0;
-    cudaStream_t st = nullptr, aux = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t st = nullptr, aux = nullptr, aux2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
     int by = 8, zc = 8;
     bool overlap = true;  // particle kernel concurrent with the lattice pass
     bool md_fixed = false;  // particle-kernel shape set by the caller (the autotuner leaves it)
@@ -127,7 +127,6 @@ Layout layout_of(const lbmd_config *c, int total_beads) {
     const size_t esz = c->precision == LBMD_FP16DEV ? 2 : 4;
     const size_t npop = (size_t)c->n_real * LBMD_Q * pop_stride(ns);
     const size_t nxt = (c->nx + 31) / 32;
-    const size_t max_blocks = nxt * c->ny * c->nz * c->n_real;  // finest tile shape (by = zc = 1)
     const size_t nb = (size_t)std::max(total_beads, 1);
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
@@ -149,15 +148,14 @@ Layout layout_of(const lbmd_config *c, int total_beads) {
     L.pair_w = take(nb * 8 * 4);
     L.bead_real = take(nb * 4);
     L.bead_off = take((size_t)(c->n_real + 1) * 4);
-    L.partial = take(max_blocks * 4 * sizeof(double));
+    L.bsnap = take(nb * 48);
+    L.fsum = take((size_t)c->n_real * 8 * sizeof(long long));
     L.ring = take((size_t)c->n_real * LBMD_DIAG_RING * sizeof(lbmd_diag));
     L.obs = take((size_t)c->n_real * sizeof(lbmd_obs));
     L.tl = take((size_t)c->n_real * sizeof(lbmd_transloc));
     L.ctrl = take(sizeof(Ctrl));
-    L.rdone = take((size_t)c->n_real * 2 * sizeof(unsigned int));
     L.loopc = take(sizeof(unsigned int));
-    // bead state and translocation records saved while the autotuner times particle shapes
-    L.snap = take(nb * 48 + (size_t)c->n_real * sizeof(lbmd_transloc));
+    L.snap = take(nb * 48);  // bead state saved while the autotuner times particle shapes
     L.phase = take(PHASES * sizeof(unsigned long long));
     L.total = o;
     return L;
@@ -178,6 +176,7 @@ lbmd_status resolve_profile(lbmd_handle *h) {
     if (h->pending.empty()) return LBMD_OK;
     CK(cudaStreamSynchronize(h->st));
     CK(cudaStreamSynchronize(h->aux));
+    CK(cudaStreamSynchronize(h->aux2));
     for (auto &p : h->pending) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, p.a, p.b));
@@ -212,7 +211,8 @@ struct ProfScope {
 
 // One coupled step: the gather runs alone (its latency-bound loads would queue
 // behind the lattice pass's traffic), then the particle kernel (aux stream)
-// runs concurrently with the stream-collide kernel (main), then the source.
+// and the bead diagnostics (aux2) run concurrently with the stream-collide
+// kernel (main), then the source, which also completes the diagnostics row.
 lbmd_status enqueue_step(lbmd_handle *h) {
     if (h->total_beads > 0) {
         ProfScope ps(h, K_GATHER, h->st);
@@ -225,19 +225,28 @@ lbmd_status enqueue_step(lbmd_handle *h) {
         CK(launch_particles(h->S, h->popA, h->aux));
     }
     CK(cudaEventRecord(h->ev_join, h->aux));
+    if (h->total_beads > 0) {
+        CK(cudaStreamWaitEvent(h->aux2, h->ev_fork, 0));
+        {
+            ProfScope ps(h, K_BEAD_DIAG, h->aux2);
+            CK(launch_bead_diag(h->S, h->aux2));
+        }
+        CK(cudaEventRecord(h->ev_join2, h->aux2));
+    }
     if (!h->overlap) CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
     {
         ProfScope ps(h, K_STREAM_COLLIDE, h->st);
         CK(launch_stream_collide(h->S, h->popA, h->popB, h->by, h->zc, true, h->st));
     }
     CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
+    if (h->total_beads > 0) CK(cudaStreamWaitEvent(h->st, h->ev_join2, 0));
     {
         ProfScope ps(h, K_SOURCE, h->st);
         CK(launch_source(h->S, h->popB, h->st));
     }
     std::swap(h->popA, h->popB);
     h->host_step += 1;
-    h->launches += h->total_beads > 0 ? 4 : 3;
+    h->launches += h->total_beads > 0 ? 5 : 3;
     if (h->pending.size() > 30000) return resolve_profile(h);
     return LBMD_OK;
 }
@@ -473,6 +482,8 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
         int lo = 0, hi = 0;
         cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->aux2, cudaStreamNonBlocking, lo);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join2, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
         if (e != cudaSuccess) { cuda_fail(h, e, "stream/event creation"); return bail(LBMD_ERR_CUDA); }
@@ -577,12 +588,12 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
     S.pair_w = (float *)(b + L.pair_w);
     S.bead_real = (const int *)(b + L.bead_real);
     S.bead_off = (const int *)(b + L.bead_off);
-    S.partial = (double *)(b + L.partial);
+    S.bsnap = (float4 *)(b + L.bsnap);
+    S.fsum = (long long *)(b + L.fsum);
     S.ring = (lbmd_diag *)(b + L.ring);
     S.obs = (lbmd_obs *)(b + L.obs);
     S.tl = (lbmd_transloc *)(b + L.tl);
     S.ctrl = (Ctrl *)(b + L.ctrl);
-    S.rdone = (unsigned int *)(b + L.rdone);
     S.phase = nullptr;
 
 #define CKI(call)                                                           \
@@ -605,7 +616,7 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
     CKI(cudaMemsetAsync(b + L.ring, 0, (size_t)cfg->n_real * LBMD_DIAG_RING * sizeof(lbmd_diag), h->st));
     CKI(cudaMemsetAsync(b + L.obs, 0, (size_t)cfg->n_real * sizeof(lbmd_obs), h->st));
     CKI(cudaMemsetAsync(b + L.ctrl, 0, sizeof(Ctrl), h->st));
-    CKI(cudaMemsetAsync(b + L.rdone, 0, (size_t)cfg->n_real * 2 * sizeof(unsigned int), h->st));
+    CKI(cudaMemsetAsync(b + L.fsum, 0, (size_t)cfg->n_real * 8 * sizeof(long long), h->st));
     CKI(cudaMemsetAsync(b + L.popB, 0, L.staging - L.popB, h->st));
     CKI(cudaMemsetAsync(b + L.up, 0, (size_t)std::max(h->total_beads, 1) * 32, h->st));
     CKI(launch_init_rest(S, h->popA, h->st));
@@ -632,7 +643,7 @@ lbmd_status lbmd_step(lbmd_handle *h, int64_t n) {
             if (h->popA == h->graph_A) {
                 CK(cudaGraphLaunch(h->gexec, h->st));
                 h->host_step += h->graph_steps;
-                h->launches += (h->total_beads > 0 ? 4LL : 3LL) * h->graph_steps;
+                h->launches += (h->total_beads > 0 ? 5LL : 3LL) * h->graph_steps;
                 n -= h->graph_steps;
                 continue;
             }
@@ -664,7 +675,7 @@ lbmd_status lbmd_step_loop(lbmd_handle *h, int64_t n) {
         CK(cudaGetLastError());
         CK(cudaGraphLaunch(h->lexec, h->st));
         h->host_step += 2 * pairs;
-        h->launches += 1 + (2LL * (h->total_beads > 0 ? 4 : 3) + 1) * pairs;
+        h->launches += 1 + (2LL * (h->total_beads > 0 ? 5 : 3) + 1) * pairs;
     }
     if (n & 1) return enqueue_step(h);
     return LBMD_OK;
@@ -1127,6 +1138,13 @@ lbmd_status lbmd_get_tiles(lbmd_handle *h, int32_t *by, int32_t *zc) {
 
 lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t *zc_out) {
     if (!h || reps < 1) return LBMD_ERR_INVALID_ARG;
+    // The timed lattice passes add into the per-step fluid accumulators: they
+    // are cleared before returning.
+    auto put_back = [&]() -> cudaError_t {
+        cudaError_t e = cudaMemsetAsync(h->S.fsum, 0, (size_t)h->cfg.n_real * 4 * sizeof(long long), h->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+        return e;
+    };
     static const int BYS[] = {1, 2, 4, 8, 16};
     static const int ZCS[] = {1, 2, 4, 8, 16, 32};
     cudaEvent_t a, b;
@@ -1155,6 +1173,7 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
     if (h->total_beads == 0 || h->md_fixed) {  // no chain, or a shape the caller fixed
         cudaEventDestroy(a);
         cudaEventDestroy(b);
+        CK(put_back());
         return LBMD_OK;
     }
     // Particle-kernel shape: time pseudo-steps (gather, then the particle
@@ -1166,8 +1185,6 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
     CK(cudaMemcpyAsync(snap, h->S.r_hi, bb16, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(snap + bb16, h->S.r_lo, bb16, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(snap + 2 * bb16, h->S.v, bb16, cudaMemcpyDeviceToDevice, h->st));
-    const size_t tlb = (size_t)h->cfg.n_real * sizeof(lbmd_transloc);
-    CK(cudaMemcpyAsync(snap + 3 * bb16, h->S.tl, tlb, cudaMemcpyDeviceToDevice, h->st));
     static const int TS[] = {2, 4, 8};
     static const int CS[] = {1, 2, 4, 8};
     float best_md = 1e30f;
@@ -1203,9 +1220,8 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
     CK(cudaMemcpyAsync(h->S.r_hi, snap, bb16, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(h->S.r_lo, snap + bb16, bb16, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(h->S.v, snap + 2 * bb16, bb16, cudaMemcpyDeviceToDevice, h->st));
-    CK(cudaMemcpyAsync(h->S.tl, snap + 3 * bb16, tlb, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemsetAsync(h->S.G, 0, (size_t)h->cfg.n_real * 3 * h->S.ns * 8, h->st));
-    CK(cudaStreamSynchronize(h->st));
+    CK(put_back());
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (bt > 0 && (bt != h->S.md_T || bc != h->S.md_C)) {
@@ -1271,12 +1287,15 @@ void lbmd_destroy(lbmd_handle *h) {
     if (!h) return;
     if (h->st) cudaStreamSynchronize(h->st);
     if (h->aux) cudaStreamSynchronize(h->aux);
+    if (h->aux2) cudaStreamSynchronize(h->aux2);
     for (auto &p : h->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : h->free_events) cudaEventDestroy(e);
     drop_graph(h);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->ev_join2) cudaEventDestroy(h->ev_join2);
     if (h->aux) cudaStreamDestroy(h->aux);
+    if (h->aux2) cudaStreamDestroy(h->aux2);
     delete h;
 }
 

@@ -87,12 +87,48 @@ constexpr float FP16_SCALE = 4096.0f;          // 2^12
 constexpr float FP16_INV_SCALE = 1.0f / 4096.0f;
 constexpr double FIX_SCALE = 1099511627776.0;  // 2^40
 constexpr float FIX_SCALE_F = 1099511627776.0f;
+
+// Fixed-point scales (powers of two) of the per-step diagnostics sums.  The
+// sums are 64-bit integer sums: exact, and the same in any order and for any
+// launch shape.  Ranges: |sum of rho - 1| and |sum of rho u| over one
+// realization below 2^22; bead |v| below 2^12; unwrapped |x| below 2^15;
+// distances from a part's centroid below 2^10.
+constexpr int FIXD_FLUID = 40;  // rho - 1 and rho u
+constexpr int FIXD_V = 40;      // bead velocities and work rates
+constexpr int FIXD_X = 36;      // bead positions
+constexpr int FIXD_D2 = 30;     // squared distances from a centroid
+
+// round(x 2^S) as a 64-bit integer, with integer operations only (the
+// hardware conversion runs on the slow double-precision path of this GPU).
+// Halves round away from zero; zero, subnormal and non-finite x give 0 (the
+// callers flag non-finite values themselves).
+__device__ __forceinline__ long long fix_of(float x, int S) {
+    const unsigned b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xffu);
+    if (e == 0 || e == 0xff) return 0;
+    const long long m = (long long)((b & 0x7fffffu) | 0x800000u);
+    const int sh = e - 150 + S;  // x 2^S = m 2^sh
+    long long r = 0;
+    if (sh >= 0) r = m << min(sh, 39);
+    else if (sh > -25) r = (m + (1ll << (-sh - 1))) >> (-sh);
+    return (b >> 31) ? -r : r;
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// 2^-S as a double (exact)
+__host__ __device__ constexpr double fix_unit(int S) { return S <= 0 ? 1.0 : 0.5 * fix_unit(S - 1); }
 constexpr float FIX_INV_SCALE_F = 1.0f / 1099511627776.0f;
 
 constexpr int MAX_CLUSTER = 16;  // blocks per chain (above 8: non-portable cluster size)
 constexpr int NBR_CAP = 32;     // bead-bead neighbours per bead
 constexpr int WALL_CAP = 12;    // solid sites within the wall-list radius per bead
 constexpr int HASH_SIZE = 2048; // cell hash slots (>= 2 * max beads per realization)
+constexpr int BRUTE_MAX = 512;  // chains up to this length build pair lists without the hash
 
 // status bits latched in Ctrl::status
 constexpr int ST_NONFINITE = 1;
@@ -144,16 +180,16 @@ struct Sim {
     unsigned long long *G;
     int *stamp;
     float4 *r_hi, *r_lo, *v, *up, *J;
+    float4 *bsnap;           // [3][total_beads] r_hi, r_lo, v at the start of the step (written by the gather)
     int *pair_node;          // [total_beads][8] global site of each fluid corner, -1 if none
     float *pair_w;           // [total_beads][8] normalised trilinear weight
     const int *bead_real;    // [total_beads] realization of each bead
     const int *bead_off;
-    double *partial;         // [blocks][4]
+    long long *fsum;         // [2][n_real][4] fixed-point fluid sums (per-step, observables); zero between uses
     lbmd_diag *ring;         // [n_real][LBMD_DIAG_RING]
     lbmd_obs *obs;           // [n_real]
     lbmd_transloc *tl;       // [n_real] translocation records
     Ctrl *ctrl;
-    unsigned int *rdone;        // [2][n_real] blocks finished per realization (diag pass, observables pass)
     unsigned long long *phase;  // [PHASES] SM cycles per particle-kernel phase, or null
     // Trajectory record of the MD cycle for the adjoint, or null:
     // traj[slot * total_beads + bead] with the slots of traj_slot_* below
@@ -376,6 +412,7 @@ struct MdShape {
 };
 MdShape md_shape(const Sim &S);
 cudaError_t launch_gather(const Sim &S, const void *A, cudaStream_t st);
+cudaError_t launch_bead_diag(const Sim &S, cudaStream_t st);
 cudaError_t launch_particles(const Sim &S, const void *A, cudaStream_t st);
 cudaError_t launch_bead_observables(const Sim &S, const void *A, cudaStream_t st);
 // reverse mode (FP32 populations only)
