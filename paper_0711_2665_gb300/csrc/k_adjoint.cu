@@ -563,6 +563,15 @@ __global__ void __launch_bounds__(MAXT) k_bead_adjoint(const Sim S, const float 
         if (own) kick(2 * sub + 1, xi);
         for (int b = Mb - 1; b >= 0; --b) {
             const int t = sub * Mb + b;
+            // the positions r_t of the second evaluation, fetched now so that
+            // their latency passes during the first (one bead per thread:
+            // the block has at least N threads)
+            const int q = threadIdx.x;
+            float4 ph = make_float4(0.f, 0.f, 0.f, 0.f), pl = ph;
+            if (q < N) {
+                ph = trj[(size_t)traj_slot_hi(M, Mb, t) * TB + off + q];
+                pl = trj[(size_t)traj_slot_lo(M, Mb, t) * TB + off + q];
+            }
             // v' = v_h + hb F(r_{t+1})
             if (lead) sw[p] = make_float4(lv.x, lv.y, lv.z, 0.f);
             __syncthreads();
@@ -572,7 +581,10 @@ __global__ void __launch_bounds__(MAXT) k_bead_adjoint(const Sim S, const float 
             // r_{t+1} = r_t + dtb v_h
             lv = add3(lv, mul3(dtb, lr));
             // v_h = v + hb F(r_t)
-            load_positions(t);
+            if (q < N) {
+                sh[q] = ph;
+                sl[q] = pl;
+            }
             if (lead) sw[p] = make_float4(lv.x, lv.y, lv.z, 0.f);
             __syncthreads();
             jw = tangent_all();
