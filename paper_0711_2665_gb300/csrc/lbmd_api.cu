@@ -715,17 +715,22 @@ lbmd_status lbmd_observables(lbmd_handle *h, lbmd_obs *out) {
 lbmd_status lbmd_diagnostics(lbmd_handle *h, lbmd_diag *out, int32_t max_rows, int32_t *rows) {
     if (!h || !out || !rows || max_rows < 0) return LBMD_ERR_INVALID_ARG;
     const int R = h->cfg.n_real;
-    std::vector<lbmd_diag> ring((size_t)R * LBMD_DIAG_RING);
-    CK(cudaMemcpyAsync(ring.data(), h->S.ring, ring.size() * sizeof(lbmd_diag), cudaMemcpyDeviceToHost, h->st));
-    CK(cudaStreamSynchronize(h->st));
     const long long done = h->host_step;  // rows exist for steps [0, done)
     const long long avail = std::min<long long>(done, LBMD_DIAG_RING);
     const int n = (int)std::min<long long>(avail, max_rows);
-    for (int r = 0; r < R; ++r)
-        for (int k = 0; k < n; ++k) {
-            const long long stp = done - n + k;
-            out[(size_t)r * max_rows + k] = ring[(size_t)r * LBMD_DIAG_RING + (stp % LBMD_DIAG_RING)];
-        }
+    // only the rows returned cross to the host: the ring slots of steps
+    // [done - n, done), at most two runs per realization (the ring wraps),
+    // each one strided copy over the realizations
+    const size_t row = sizeof(lbmd_diag);
+    const int s0 = (int)((done - n) % LBMD_DIAG_RING);
+    const int first = std::min(n, LBMD_DIAG_RING - s0);
+    if (first > 0)
+        CK(cudaMemcpy2DAsync(out, (size_t)max_rows * row, h->S.ring + s0, (size_t)LBMD_DIAG_RING * row, (size_t)first * row, R,
+                             cudaMemcpyDeviceToHost, h->st));
+    if (n > first)
+        CK(cudaMemcpy2DAsync(out + first, (size_t)max_rows * row, h->S.ring, (size_t)LBMD_DIAG_RING * row,
+                             (size_t)(n - first) * row, R, cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
     *rows = n;
     return LBMD_OK;
 }
