@@ -244,14 +244,16 @@ lbmd_status lbmd_set_tiles(lbmd_handle *h, int32_t by, int32_t zc);
 lbmd_status lbmd_get_tiles(lbmd_handle *h, int32_t *by, int32_t *zc);
 
 /* Shape of the particle kernel: threads_per_bead in {1,2,4,8} split each
- * bead's force terms; blocks_per_chain in 1..16 is the thread-block cluster
- * that shares one chain (positions replicated through distributed shared
- * memory).  0 = automatic.  A block may hold at most 512 threads
- * (ceil(beads / blocks_per_chain) * threads_per_bead); LBMD_ERR_INVALID_ARG
- * otherwise.  Clusters above 8 blocks are a non-portable size: where the
- * device cannot schedule one, the next step returns LBMD_ERR_CUDA.  Results
- * agree with every shape to rounding (the force terms are summed in a
- * different order). */
+ * bead's force terms; blocks_per_chain in 1..16 is the size C of the
+ * thread-block clusters, over which the longest chain is spread (positions
+ * replicated through distributed shared memory), Nc = ceil(longest / C) beads
+ * per block.  A shorter chain takes ceil(N / Nc) blocks, and chains share
+ * clusters.  0 = automatic.  A block may hold at most 512 threads
+ * (Nc * threads_per_bead); LBMD_ERR_INVALID_ARG otherwise.  Clusters above 8
+ * blocks are a non-portable size: where the device cannot schedule one, the
+ * next step returns LBMD_ERR_CUDA.  The placement does not change the
+ * arithmetic; other lane counts agree to rounding (the force terms are summed
+ * in a different order). */
 lbmd_status lbmd_set_md_shape(lbmd_handle *h, int32_t threads_per_bead, int32_t blocks_per_chain);
 lbmd_status lbmd_get_md_shape(lbmd_handle *h, int32_t *threads_per_bead, int32_t *blocks_per_chain);
 

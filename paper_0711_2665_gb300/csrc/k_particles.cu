@@ -745,10 +745,12 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
     PSmem sm;
     psmem_layout(Nmax, Nc, &sm, smem_raw);
     cg::cluster_group cl = cg::this_cluster();
-    const int rank = C > 1 ? (int)cl.block_rank() : 0;
-    const int r = blockIdx.x / C;
-    const int off = S.bead_off[r];
-    const int N = S.bead_off[r + 1] - off;
+    // this block's part: chain r (-1: an idle block), its rank among the
+    // chain's cc blocks, which start at rank c0 of the cluster
+    const int4 bm = S.md_map[blockIdx.x];
+    const int r = bm.x, rank = bm.y, cc = bm.z, c0 = bm.w;
+    const int off = r >= 0 ? S.bead_off[r] : 0;
+    const int N = r >= 0 ? S.bead_off[r + 1] - off : 0;
     const int lt = threadIdx.x % T, pl = threadIdx.x / T;
     const int p = rank * Nc + pl;
     const bool own = pl < Nc && p < N;
@@ -835,8 +837,8 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
                 const bool moved = dot3(dd, dd) > S.skin_half2;
                 // the T lanes of a bead hold the same position; they share
                 // the writes to the C replicas of the cluster
-                if (C > 1) {
-                    for (int c = lt; c < C; c += T) {
+                if (cc > 1) {
+                    for (int c = c0 + lt; c < c0 + cc; c += T) {
                         *cl.map_shared_rank(sm.ph[nb] + p, c) = mh;
                         *cl.map_shared_rank(sm.pl[nb] + p, c) = ml;
                         if (moved) *cl.map_shared_rank(&s_flag[t & 1], c) = 1;
@@ -941,7 +943,7 @@ static cudaError_t launch_particles_t(const Sim &S, const MdShape &m, cudaStream
         if (e != cudaSuccess) return e;
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(S.n_real * m.C);
+    cfg.gridDim = dim3(S.md_clusters * m.C);
     cfg.blockDim = dim3(m.threads);
     cfg.dynamicSmemBytes = m.smem;
     cfg.stream = st;
@@ -956,7 +958,7 @@ static cudaError_t launch_particles_t(const Sim &S, const MdShape &m, cudaStream
 }
 
 cudaError_t launch_particles(const Sim &S, const void *, cudaStream_t st) {
-    if (S.total_beads == 0) return cudaSuccess;
+    if (S.total_beads == 0 || S.md_clusters == 0) return cudaSuccess;
     const MdShape m = md_shape(S);
     switch (m.T) {
         case 1: return launch_particles_t<1>(S, m, st);

@@ -24,7 +24,7 @@ constexpr double SKIN = 0.6;  // Verlet-list skin (lattice units); 0.4 and 0.8 m
 
 struct Layout {
     size_t popA, popB, staging, link, wallmask, tileflag, solid, G, stamp;
-    size_t r_hi, r_lo, v, up, J, pair_node, pair_w, bead_real, bead_off, bsnap, fsum, ring, obs, tl, ctrl, loopc, snap, phase, total;
+    size_t r_hi, r_lo, v, up, J, pair_node, pair_w, bead_real, bead_off, bsnap, fsum, ring, obs, tl, ctrl, loopc, snap, md_map, phase, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -156,6 +156,9 @@ Layout layout_of(const lbmd_config *c, int total_beads) {
     L.ctrl = take(sizeof(Ctrl));
     L.loopc = take(sizeof(unsigned int));
     L.snap = take(nb * 48);  // bead state saved while the autotuner times particle shapes
+    // chain placement of the particle kernel: the current shape's and a trial
+    // shape's (autotuner); at most one cluster of MAX_CLUSTER blocks per chain
+    L.md_map = take(2 * (size_t)c->n_real * MAX_CLUSTER * sizeof(int4));
     L.phase = take(PHASES * sizeof(unsigned long long));
     L.total = o;
     return L;
@@ -208,6 +211,52 @@ struct ProfScope {
         }
     }
 };
+
+// Placement of the chains in the particle kernel's clusters of C blocks of
+// Nc beads: chain r takes ceil(N_r / Nc) consecutive blocks of one cluster,
+// first fit over the chains in decreasing length (ties by index), so that
+// short chains share a cluster instead of each holding C blocks.  A chain's
+// arithmetic does not depend on how many blocks share it.  Realizations
+// without beads get no block; blocks left over in a cluster idle.  Returns
+// the number of clusters; map gets C entries per cluster.
+int pack_chains(const std::vector<int32_t> &off, int C, int Nc, std::vector<int4> &map) {
+    const int R = (int)off.size() - 1;
+    std::vector<int> order;
+    for (int r = 0; r < R; ++r)
+        if (off[r + 1] > off[r]) order.push_back(r);
+    auto blocks = [&](int r) { return std::max(1, (off[r + 1] - off[r] + Nc - 1) / Nc); };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return blocks(a) > blocks(b); });
+    std::vector<int> fill;                      // blocks used per cluster
+    std::vector<int4> place;                    // (r, cluster, first block, blocks)
+    for (int r : order) {
+        const int c = std::min(blocks(r), C);
+        size_t k = 0;
+        while (k < fill.size() && fill[k] + c > C) ++k;
+        if (k == fill.size()) fill.push_back(0);
+        place.push_back(make_int4(r, (int)k, fill[k], c));
+        fill[k] += c;
+    }
+    map.assign(fill.size() * (size_t)C, make_int4(-1, 0, 1, 0));
+    for (size_t k = 0; k < fill.size(); ++k)
+        for (int j = 0; j < C; ++j) map[k * C + j].w = j;  // idle blocks: a chain of their own
+    for (const int4 &pl : place)
+        for (int j = 0; j < pl.w; ++j) map[(size_t)pl.y * C + pl.z + j] = make_int4(pl.x, j, pl.w, pl.z);
+    return (int)fill.size();
+}
+
+// Upload the placement for shape m into map region `region` (0: current, 1:
+// trial) and point S at it.  Ordered on the main stream, after every step
+// already enqueued (their particle kernels have joined it).
+lbmd_status upload_md_map(lbmd_handle *h, Sim &S, int region) {
+    const MdShape m = md_shape(S);
+    std::vector<int4> map;
+    const int nc = pack_chains(h->offsets, m.C, m.Nc, map);
+    int4 *dst = (int4 *)(h->dbuf + h->L.md_map) + (size_t)region * h->cfg.n_real * MAX_CLUSTER;
+    if (!map.empty()) CK(cudaMemcpyAsync(dst, map.data(), map.size() * sizeof(int4), cudaMemcpyHostToDevice, h->st));
+    S.md_map = dst;
+    S.md_clusters = nc;
+    return LBMD_OK;
+}
 
 // One coupled step: the gather runs alone (its latency-bound loads would queue
 // behind the lattice pass's traffic), then the particle kernel (aux stream)
@@ -589,6 +638,8 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
     S.bead_real = (const int *)(b + L.bead_real);
     S.bead_off = (const int *)(b + L.bead_off);
     S.bsnap = (float4 *)(b + L.bsnap);
+    S.md_map = (const int4 *)(b + L.md_map);
+    S.md_clusters = 0;
     S.fsum = (long long *)(b + L.fsum);
     S.ring = (lbmd_diag *)(b + L.ring);
     S.obs = (lbmd_obs *)(b + L.obs);
@@ -625,6 +676,8 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
     if (md_shape(S).smem > 200 * 1024) { fail(h, LBMD_ERR_CAPACITY, "too many beads per realization for shared memory"); return bail(LBMD_ERR_CAPACITY); }
     lbmd_status s = lbmd_set_beads(h, r_init, nullptr);
     if (s == LBMD_OK) s = lbmd_reset_translocation(h);
+    if (s == LBMD_OK) s = upload_md_map(h, h->S, 0);
+    if (s == LBMD_OK) s = cudaStreamSynchronize(h->st) == cudaSuccess ? LBMD_OK : LBMD_ERR_CUDA;
     if (s != LBMD_OK) return bail(s);
     *out = h;
     return LBMD_OK;
@@ -1110,7 +1163,7 @@ lbmd_status lbmd_set_md_shape(lbmd_handle *h, int32_t T, int32_t C) {
     h->S.md_T = T;
     h->S.md_C = C;
     h->md_fixed = T != 0 || C != 0;
-    return LBMD_OK;
+    return upload_md_map(h, h->S, 0);
 }
 
 lbmd_status lbmd_set_overlap(lbmd_handle *h, int32_t overlap) {
@@ -1202,6 +1255,8 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
             const MdShape m = md_shape(trial);
             if (m.threads > 512 || m.C != C || m.smem > 200 * 1024) continue;
             if (C > 1 && C > (h->S.max_beads + 15) / 16) continue;  // blocks of a few beads: barrier-bound
+            lbmd_status us = upload_md_map(h, trial, 1);
+            if (us != LBMD_OK) return us;
             float ms = 0.f;
             for (int pass = 0; pass < 2; ++pass) {  // warm-up pass, then the timed one
                 CK(cudaEventRecord(a, h->st));
@@ -1233,6 +1288,7 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
         h->S.md_T = bt;
         h->S.md_C = bc;
         drop_graph(h);
+        return upload_md_map(h, h->S, 0);
     }
     return LBMD_OK;
 }

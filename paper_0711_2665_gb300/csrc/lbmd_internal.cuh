@@ -167,6 +167,11 @@ struct Sim {
     float E, gamma, kT;
     int M, Mb;
     int md_T, md_C;          // particle-kernel shape override (0 = automatic)
+    // placement of the chains in the particle kernel's clusters: per block
+    // (realization or -1, rank within its chain, the chain's blocks, the
+    // chain's first rank in the cluster); md_clusters clusters of the shape's C
+    const int4 *md_map;
+    int md_clusters;
     float skin_half2;       // (skin/2)^2: displacement that forces a list rebuild
     float rl2, rlw2, rlw;    // bead and wall list radii (squared) and wall radius
     int ncell[3];            // cells per axis for the neighbour hash (>= 3 to use it)
