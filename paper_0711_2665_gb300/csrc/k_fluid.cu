@@ -120,16 +120,19 @@ __global__ void __launch_bounds__(512, FL ? 1 : 2) k_stream_collide(const Sim S,
             if (lmu[u] & SOLID_BIT) continue;
             const int s = su[u];
             const float *h = hh[u];
-            float drho_s = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+            // moments from the sums and differences of the opposite pairs
+            // (i odd, i + 1): c_{i+1} = -c_i
+            float drho_s = h[0], jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                drho_s += h[i];
-                if (cx(i) == 1) jx += h[i];
-                if (cx(i) == -1) jx -= h[i];
-                if (cy(i) == 1) jy += h[i];
-                if (cy(i) == -1) jy -= h[i];
-                if (cz(i) == 1) jz += h[i];
-                if (cz(i) == -1) jz -= h[i];
+            for (int i = 1; i < Q; i += 2) {
+                const float sp = h[i] + h[i + 1], dp = h[i] - h[i + 1];
+                drho_s += sp;
+                if (cx(i) == 1) jx += dp;
+                if (cx(i) == -1) jx -= dp;
+                if (cy(i) == 1) jy += dp;
+                if (cy(i) == -1) jy -= dp;
+                if (cz(i) == 1) jz += dp;
+                if (cz(i) == -1) jz -= dp;
             }
             const float drho = drho_s * down;
             jx *= down; jy *= down; jz *= down;
@@ -149,11 +152,23 @@ __global__ void __launch_bounds__(512, FL ? 1 : 2) k_stream_collide(const Sim S,
 #pragma unroll
                     for (int k = 0; k < 15; ++k) am_[k] = sr * S.fl_amp[k] * z[k];
                 }
+                // BGK towards heq_i = w_i (drho + rho (cu + cu^2 / 2 - 3 u.u / 2)),
+                // cu = 3 c_i.u: for the pair (i, i + 1) cu changes sign, so the
+                // even part (drho + rho (cu^2 / 2 - 3 u.u / 2)) and the odd part
+                // (rho cu) serve both
+                float hr[Q];
+                hr[0] = h[0] + om * (wq(0) * (drho_s - rho_s * usq) - h[0]);
+#pragma unroll
+                for (int i = 1; i < Q; i += 2) {
+                    const float cu = 3.0f * ((float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz);
+                    const float even = drho_s + rho_s * (0.5f * cu * cu - usq);
+                    const float odd = rho_s * cu;
+                    hr[i] = h[i] + om * (wq(i) * (even + odd) - h[i]);
+                    hr[i + 1] = h[i + 1] + om * (wq(i) * (even - odd) - h[i + 1]);
+                }
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
-                    const float cu = 3.0f * ((float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz);
-                    const float heq = wq(i) * (drho_s + rho_s * (cu + 0.5f * cu * cu - usq));
-                    float hn = h[i] + om * (heq - h[i]);
+                    float hn = hr[i];
                     if (FL) {
                         float d = 0.0f;
 #pragma unroll
