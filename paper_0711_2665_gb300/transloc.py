@@ -149,14 +149,18 @@ def main(argv=None):
     ap.add_argument("--E", type=float, default=None)
     ap.add_argument("--gamma", type=float, default=None)
     ap.add_argument("--kT", type=float, default=None)
+    ap.add_argument("--interp", type=int, default=None, help="0 trilinear, 1 nearest grid point")
+    ap.add_argument("--integrator", type=int, default=None, help="0 velocity Verlet, 1 stochastic position Verlet")
     ap.add_argument("--records", default=None, help="write the raw records (.npz) here")
     a = ap.parse_args(argv)
-    ov = {k: v for k, v in (("E", a.E), ("gamma", a.gamma), ("kT", a.kT)) if v is not None}
+    ov = {k: v for k, v in (("E", a.E), ("gamma", a.gamma), ("kT", a.kT), ("interp", a.interp),
+                            ("integrator", a.integrator)) if v is not None}
     lengths = [int(x) for x in a.lengths.split(",") if x]
     out = run(lengths, a.copies, a.max_steps, a.chunk, ov)
     summ = summarize(out["counts"], out["records"])
     w = out["workload"]
-    line = {"workload": {k: w[k] for k in ("nx", "ny", "nz", "wall_x", "pore_h", "E", "gamma", "kT", "tau")},
+    line = {"workload": {k: w.get(k, 0) for k in ("nx", "ny", "nz", "wall_x", "pore_h", "E", "gamma", "kT", "tau",
+                                                  "interp", "integrator")},
             "lengths": lengths, "copies": a.copies, "steps": out["steps"], "seconds": out["seconds"],
             "mlups": out["mlups"], **summ}
     if a.records:
