@@ -131,8 +131,8 @@ def test_observables_match_oracle():
 
 def test_per_step_diagnostics_match_observables():
     """The row each step records (fluid sums from the stream-collide kernel,
-    bead sums from the particle kernel) equals the observables of the state
-    the step started from."""
+    bead sums from the bead-diagnostics kernel) equals the observables of the
+    state the step started from."""
     w = small_workload()
     sim, orc, inp = make_pair(w)
     sim.step(7)
