@@ -195,6 +195,54 @@ def _sc_roofline(sim, w, peak, peak_kind, steps=10):
             "frac_in_step": b / (us["in_step"] * 1e-6) / 1e9 / peak}
 
 
+def _variants(dev, lbmd, workloads, tiles, steps=100):
+    """The method's variants on the headline workload (128x64x64, N = 400),
+    each timed like the headline (2-step graph launches, L2 flushed before
+    every launch), beside the default form: stochastic position Verlet
+    (integrator 1), nearest-grid-point coupling (interp 1), both (the paper's
+    own scheme), and the fluctuating fluid (lb_kT = kT = 1e-4)."""
+    import torch
+    flush_w = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    flush_r = torch.ones(64 << 20, dtype=torch.float32, device=dev)
+    res = {}
+    for name, ov in (("default", {}), ("spv", {"integrator": 1}), ("ngp", {"interp": 1}),
+                     ("ngp_spv", {"interp": 1, "integrator": 1}), ("fluctuating", {"lb_kT": 1e-4})):
+        w = workloads.get("plain_fp32", **ov)
+        inp = workloads.build_inputs(w)
+        sim = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"], device=str(dev))
+        if tiles:
+            sim.set_tiles(*tiles)
+        else:
+            sim.autotune(3)
+        st = sim.stream
+        sim.set_graph(2)
+        sim.step(6)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps // 2)]
+        torch.cuda.synchronize(dev)
+        for a, b in ev:
+            with torch.cuda.stream(st):
+                flush_w.zero_()
+                flush_r.sum()
+            a.record(st)
+            sim.step(2)
+            b.record(st)
+        torch.cuda.synchronize(dev)
+        ms = sum(a.elapsed_time(b) for a, b in ev) / (2 * len(ev))
+        sim.set_graph(0)
+        sim.profile(True)
+        sim.step(10)
+        kt = sim.kernel_times()
+        sim.profile(False)
+        sim.check()
+        sites = w["nx"] * w["ny"] * w["nz"]
+        res[name] = {"value": sites / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms,
+                     "us_particles": 1e3 * kt["particles"][1] / kt["particles"][0],
+                     "us_stream_collide": 1e3 * kt["stream_collide"][1] / kt["stream_collide"][0],
+                     "config": ov}
+        sim.close()
+    return res
+
+
 def extra_measurements(dev, stream, peak, peak_kind, forms, tiles=None):
     """The other forms of the step, each timed on its own workload with CUDA
     events on the library's stream (inputs larger than L2, no flush needed):
@@ -238,6 +286,8 @@ def extra_measurements(dev, stream, peak, peak_kind, forms, tiles=None):
                      "launch": "one CUDA-graph launch per run (device-side loop of two-step bodies)",
                      "roofline": rf}
         sim.close()
+    if "variants" in forms:
+        out["variants"] = _variants(dev, lbmd, workloads, tiles)
     if "adjoint" not in forms:
         return out
     w = workloads.get("adjoint")
@@ -279,8 +329,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--forms", default="ensemble_fp32,fp16dev,adjoint",
-                    help="comma list of the other forms to measure (ensemble_fp32, fp16dev, adjoint), or none")
+    ap.add_argument("--forms", default="ensemble_fp32,fp16dev,variants,adjoint",
+                    help="comma list of the other forms to measure (ensemble_fp32, fp16dev, variants, adjoint), or none")
     ap.add_argument("--tiles", type=int, nargs=2, metavar=("BY", "ZC"), default=None,
                     help="fixed stream-collide tile shape instead of the autotuner (for profiling runs)")
     args = ap.parse_args()
