@@ -336,9 +336,11 @@ struct PSmem {
     int *hkey, *hhead;      // [HASH_SIZE] cell hash
     int16_t *hnext;         // [Nmax] cell lists
     uint8_t *nn, *nw;       // [Nc] list lengths
+    float4 *znz;            // [Nc][Mb] noise of the SPV inner steps of one outer step (or none)
 };
 
-__host__ __device__ inline size_t psmem_layout(int nmax, int nc, PSmem *p, char *base) {
+// nzn: float4 slots for the SPV noise (Nc * Mb when that cycle draws noise, else 0)
+__host__ __device__ inline size_t psmem_layout(int nmax, int nc, int nzn, PSmem *p, char *base) {
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o += (bytes + 15) & ~(size_t)15; return base + at; };
     char *ph0 = take(16 * (size_t)nmax), *ph1 = take(16 * (size_t)nmax);
@@ -349,6 +351,7 @@ __host__ __device__ inline size_t psmem_layout(int nmax, int nc, PSmem *p, char 
     char *hkey = take(4 * (size_t)HASH_SIZE), *hhead = take(4 * (size_t)HASH_SIZE);
     char *hnext = take(2 * (size_t)nmax);
     char *nn = take((size_t)nc), *nw = take((size_t)nc);
+    char *znz = take(16 * (size_t)nzn);
     if (p) {
         p->ph[0] = (float4 *)ph0; p->ph[1] = (float4 *)ph1;
         p->pl[0] = (float4 *)pl0; p->pl[1] = (float4 *)pl1;
@@ -356,8 +359,14 @@ __host__ __device__ inline size_t psmem_layout(int nmax, int nc, PSmem *p, char 
         p->nbr = (uint16_t *)nbr; p->wal = (uint32_t *)wal;
         p->hkey = (int *)hkey; p->hhead = (int *)hhead; p->hnext = (int16_t *)hnext;
         p->nn = (uint8_t *)nn; p->nw = (uint8_t *)nw;
+        p->znz = (float4 *)znz;
     }
     return o;
+}
+
+// noise slots of the SPV cycle: one float4 per bead of a block and inner step
+__host__ __device__ inline int spv_noise_slots(const Sim &S, int nc) {
+    return (S.integrator == 1 && S.spv_sig > 0.0f) ? nc * S.Mb : 0;
 }
 
 // Automatic shape: 4 lanes per bead.  A single chain is spread over up to 8
@@ -375,7 +384,7 @@ MdShape md_shape(const Sim &S) {
     m.C = S.md_C > 0 ? S.md_C : spread;
     m.Nc = N > 0 ? (N + m.C - 1) / m.C : 1;
     m.threads = max(32, ((m.Nc * m.T + 31) / 32) * 32);
-    m.smem = psmem_layout(max(N, 1), m.Nc, nullptr, nullptr);
+    m.smem = psmem_layout(max(N, 1), m.Nc, spv_noise_slots(S, m.Nc), nullptr, nullptr);
     return m;
 }
 
@@ -743,7 +752,7 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
     extern __shared__ __align__(16) char smem_raw[];
     __shared__ int s_flag[2], s_err;
     PSmem sm;
-    psmem_layout(Nmax, Nc, &sm, smem_raw);
+    psmem_layout(Nmax, Nc, spv_noise_slots(S, Nc), &sm, smem_raw);
     cg::cluster_group cl = cg::this_cluster();
     // this block's part: chain r (-1: an idle block), its rank among the
     // chain's cc blocks, which start at rank c0 of the cluster
@@ -821,6 +830,20 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
                 J = J + h * fl;
             }
         }
+        // SPV: the noise of this outer step's inner steps for the block's
+        // beads, drawn by all threads at once (counter t = sub Mb + b, as
+        // each inner step would draw it), off the sub-steps' dependent chain
+        if (spv && S.spv_sig > 0.0f) {
+            __syncthreads();  // the previous outer step's noise has been used
+            for (int k = threadIdx.x; k < Nc * S.Mb; k += blockDim.x) {
+                const int bl = k / S.Mb, bb = k - bl * S.Mb, q = rank * Nc + bl;
+                if (q < N) {
+                    const float3 z = gauss3(S.seed, S.real_base + (uint32_t)r, (uint32_t)q, step, (uint32_t)(sub * S.Mb + bb));
+                    sm.znz[k] = make_float4(z.x, z.y, z.z, 0.f);
+                }
+            }
+            __syncthreads();
+        }
         for (int b = 0; b < S.Mb; ++b, ++t) {
             const int nb = buf ^ 1;
             if (own) {
@@ -865,7 +888,10 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
             if (own) {
                 if (spv) {
                     float3 z = make_float3(0.f, 0.f, 0.f);
-                    if (S.spv_sig > 0.0f) z = gauss3(S.seed, S.real_base + (uint32_t)r, (uint32_t)p, step, (uint32_t)t);
+                    if (S.spv_sig > 0.0f) {
+                        const float4 zz = sm.znz[pl * S.Mb + b];
+                        z = make_float3(zz.x, zz.y, zz.z);
+                    }
                     const float3 vn = S.spv_c * v + (1.0f - S.spv_c) * up + S.spv_g1 * F + S.spv_sig * z;
                     J = J + (vn - v - dtb * F);
                     v = vn;
