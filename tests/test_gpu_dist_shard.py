@@ -31,3 +31,30 @@ def test_split_ensemble_matches_unsplit():
         assert np.array_equal(part.get_deviations(), dev[lo:hi])
         r, v = part.get_beads()
         assert np.array_equal(r, r_all[b0:b1]) and np.array_equal(v, v_all[b0:b1])
+
+
+def test_packed_chains_match_chains_alone():
+    """Chains of very different lengths on clusters of 4 blocks of Nc = 10
+    beads: a chain takes ceil(N / 10) blocks, so the 25- and the 6-bead chain
+    share a cluster.  Each realization evolves exactly as it does alone (a
+    one-realization shard with the same noise stream)."""
+    counts = [40, 6, 25, 12, 33]
+    w = workloads.get("ensemble_fp32", nx=40, ny=20, nz=12, wall_x=20, n_real=len(counts), bead_counts=counts)
+    full_inp = workloads.build_inputs(w)
+    whole = lbmd.Simulation(w, full_inp["solid"], full_inp["offsets"], full_inp["r0"])
+    whole.set_md_shape(4, 4)
+    whole.step(8)
+    whole.check()
+    dev = whole.get_deviations()
+    r_all, v_all = whole.get_beads()
+    for r in range(len(counts)):
+        wr = pdist.rank_workload(w, r, len(counts))
+        inp = pdist.rank_inputs(wr, workloads.build_inputs)
+        alone = lbmd.Simulation(wr, inp["solid"], inp["offsets"], inp["r0"])
+        alone.set_md_shape(4, 4)
+        alone.step(8)
+        b0, b1 = int(full_inp["offsets"][r]), int(full_inp["offsets"][r + 1])
+        assert np.array_equal(alone.get_deviations(), dev[r:r + 1]), r
+        ra, va = alone.get_beads()
+        assert np.array_equal(ra, r_all[b0:b1]) and np.array_equal(va, v_all[b0:b1]), r
+        alone.close()
