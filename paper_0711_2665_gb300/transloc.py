@@ -149,12 +149,16 @@ def main(argv=None):
     ap.add_argument("--E", type=float, default=None)
     ap.add_argument("--gamma", type=float, default=None)
     ap.add_argument("--kT", type=float, default=None)
+    ap.add_argument("--box", type=int, default=None,
+                    help="Nx of an Nx x Nx/2 x Nx/2 box with the wall at Nx/2 (Sec. IV: 80 up to 400 beads)")
     ap.add_argument("--interp", type=int, default=None, help="0 trilinear, 1 nearest grid point")
     ap.add_argument("--integrator", type=int, default=None, help="0 velocity Verlet, 1 stochastic position Verlet")
     ap.add_argument("--records", default=None, help="write the raw records (.npz) here")
     a = ap.parse_args(argv)
     ov = {k: v for k, v in (("E", a.E), ("gamma", a.gamma), ("kT", a.kT), ("interp", a.interp),
                             ("integrator", a.integrator)) if v is not None}
+    if a.box:
+        ov.update(nx=a.box, ny=a.box // 2, nz=a.box // 2, wall_x=a.box // 2)
     lengths = [int(x) for x in a.lengths.split(",") if x]
     out = run(lengths, a.copies, a.max_steps, a.chunk, ov)
     summ = summarize(out["counts"], out["records"])
