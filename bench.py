@@ -282,7 +282,7 @@ def extra_measurements(dev, stream, peak, peak_kind, forms, tiles=None):
         out[name] = {"value": sites * K / t / 1e6, "unit": "MLUPS", "ms_per_step": 1e3 * t / K,
                      "steps_per_s": K / t, "realization_steps_per_s": K * w["n_real"] / t, "steps": K,
                      "lattice": [w["nx"], w["ny"], w["nz"]], "n_real": w["n_real"], "beads": int(inp["offsets"][-1]),
-                     "precision": w["precision"], "tiles": [by, zc], "md_shape": list(sim.md_shape()),
+                     "precision": w["precision"], "tiles": [by, zc], "md_shape": list(sim.md_shape()), "md_exchange": sim.md_exchange(),
                      "launch": "one CUDA-graph launch per run (device-side loop of two-step bodies)",
                      "roofline": rf}
         sim.close()
@@ -496,7 +496,8 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "strong" if "shard" in w else "weak", "vs_baseline": None,
                 "dtype": "f32" if w["precision"] == "fp32" else "f16-storage/f32-math",
-                "data": "synthetic", "config": dict(_config_block(w, flush), tiles=list(sim.tiles())),
+                "data": "synthetic", "config": dict(_config_block(w, flush), tiles=list(sim.tiles()),
+                                                     md_shape=list(sim.md_shape()), md_exchange=sim.md_exchange()),
                 "launch": "captured 2-step CUDA graphs, L2 flushed before every launch",
                 "roofline": roofline, "kernels": shares, "gpu_launches": launches,
                 "kernel_timing": {"pass": "the same K steps kernel by kernel, CUDA events around every kernel",

@@ -257,6 +257,19 @@ lbmd_status lbmd_get_tiles(lbmd_handle *h, int32_t *by, int32_t *zc);
 lbmd_status lbmd_set_md_shape(lbmd_handle *h, int32_t threads_per_bead, int32_t blocks_per_chain);
 lbmd_status lbmd_get_md_shape(lbmd_handle *h, int32_t *threads_per_bead, int32_t *blocks_per_chain);
 
+/* How the blocks of a chain exchange positions each MD sub-step (Sec. II,
+ * Eq. 22: every sub-step's forces need the positions of the one before):
+ * mode 1 push (each bead's new position is written to every block's replica
+ * of the chain before the cluster barrier), 2 pull (written to its own
+ * block's replica; after the barrier each block copies the other blocks' beads
+ * that its force terms read, and the whole chain when the lists are rebuilt),
+ * 0 leave the choice to lbmd_autotune (push until it runs).  Only chains over
+ * more than one block exchange anything.  The mode does not change the
+ * arithmetic: the state is bit-identical.  LBMD_ERR_INVALID_ARG for another
+ * mode.  lbmd_get_md_exchange reports the mode in effect (1 or 2). */
+lbmd_status lbmd_set_md_exchange(lbmd_handle *h, int32_t mode);
+lbmd_status lbmd_get_md_exchange(lbmd_handle *h, int32_t *mode);
+
 /* overlap = 1 (default): the particle kernel runs concurrently with the
  * stream-collide kernel of the same step (both only read the populations the
  * step starts from); 0: one after the other.  Concurrency shares SMs between
@@ -269,8 +282,9 @@ lbmd_status lbmd_get_overlap(lbmd_handle *h, int32_t *overlap);
  * current state and keep the fastest; then, unless the caller fixed the
  * particle-kernel shape with lbmd_set_md_shape, time pseudo-steps (gather,
  * particle kernel concurrent with the lattice pass) for every admissible
- * (lanes per bead in {2,4,8}, blocks per chain in {1,2,4,8}) and keep the
- * fastest.  The state (populations, beads, G, step) is restored afterwards.
+ * (lanes per bead in {2,4,8}, blocks per chain in {1,2,4,8}, and, unless the
+ * caller fixed it with lbmd_set_md_exchange, push or pull exchange for more
+ * than one block) and keep the fastest.  The state (populations, beads, G, step) is restored afterwards.
  * Synchronises the stream. */
 lbmd_status lbmd_autotune(lbmd_handle *h, int32_t steps_per_candidate, int32_t *by, int32_t *zc);
 

@@ -17,9 +17,15 @@
 // beads, and each bead is worked on by T consecutive threads that split its
 // force terms (bonds, the three angles that involve it, its bead and wall
 // pair lists) and add them with a butterfly of shuffles.  Every block keeps a
-// replica of the whole chain's positions in shared memory; a bead's new
-// position is written to all C replicas through distributed shared memory
-// before the cluster barrier of each sub-step.  Bead-bead pairs come from a
+// replica of the chain's positions in shared memory, exchanged through
+// distributed shared memory in one of two ways (S.md_pull, chosen by the
+// autotuner): push, where a bead's new position is written to every replica
+// of its chain before the cluster barrier of each sub-step; or pull, where it
+// goes into its own block's replica only, and after the barrier each block
+// copies its halo (the other blocks' beads that its bonds, angles and pair
+// lists read) from their owners, and a list rebuild copies the whole chain.
+// Push costs each block a store per bead and replica, pull one round trip per
+// sub-step for a few beads.  Bead-bead pairs come from a
 // Verlet list (cut-off + skin), built by a scan of the whole chain by all
 // lanes (chains up to 512 beads) or from a cell hash in shared memory, and
 // rebuilt whenever any bead has moved more than half the skin since the last
@@ -337,6 +343,8 @@ struct PSmem {
     int16_t *hnext;         // [Nmax] cell lists
     uint8_t *nn, *nw;       // [Nc] list lengths
     float4 *znz;            // [Nc][Mb] noise of the SPV inner steps of one outer step (or none)
+    uint16_t *halo;         // [Nmax] the other blocks' beads this block's force terms read
+    uint8_t *mark;          // [Nmax] scratch of the halo build
 };
 
 // nzn: float4 slots for the SPV noise (Nc * Mb when that cycle draws noise, else 0)
@@ -352,6 +360,7 @@ __host__ __device__ inline size_t psmem_layout(int nmax, int nc, int nzn, PSmem 
     char *hnext = take(2 * (size_t)nmax);
     char *nn = take((size_t)nc), *nw = take((size_t)nc);
     char *znz = take(16 * (size_t)nzn);
+    char *halo = take(2 * (size_t)nmax), *mark = take((size_t)nmax);
     if (p) {
         p->ph[0] = (float4 *)ph0; p->ph[1] = (float4 *)ph1;
         p->pl[0] = (float4 *)pl0; p->pl[1] = (float4 *)pl1;
@@ -360,6 +369,8 @@ __host__ __device__ inline size_t psmem_layout(int nmax, int nc, int nzn, PSmem 
         p->hkey = (int *)hkey; p->hhead = (int *)hhead; p->hnext = (int16_t *)hnext;
         p->nn = (uint8_t *)nn; p->nw = (uint8_t *)nw;
         p->znz = (float4 *)znz;
+        p->halo = (uint16_t *)halo;
+        p->mark = (uint8_t *)mark;
     }
     return o;
 }
@@ -560,8 +571,12 @@ __device__ __forceinline__ void cell_of(const Sim &S, float xw, float yw, float 
 }
 
 // Rebuild the lists of the block's beads from the block's replica (buffer
-// buf).  Called by every thread of the block; clear_flag (if not null) is
-// reset once every thread has read it.
+// buf), which must hold the whole chain.  Called by every thread of the block;
+// clear_flag (if not null) is reset once every thread has read it.  With
+// halo set (pull exchange, chain over more than one block) it also lists the
+// block's halo: the beads of other blocks (rank != this block's) in its beads'
+// pair lists or within two bonds of them, in no particular order, their count
+// in *nhalo.
 // Pair list of bead p by its T lanes over every bead of the chain in
 // ascending order: lane lt tests q = kT + lt and a ballot over the bead's
 // lanes compacts the hits, so the list comes out sorted (the order the
@@ -600,8 +615,8 @@ __device__ __forceinline__ int scan_pairs(const Sim &S, const float4 *ph, const 
 // busy); longer ones a cell hash in shared memory, scanned by one lane per
 // bead.  Both give each bead's pairs within the list radius in ascending order.
 template <int T>
-__device__ void build_lists(const Sim &S, const PSmem &sm, int buf, int N, int p, int pl, bool own,
-                            int *clear_flag, int *s_err) {
+__device__ void build_lists(const Sim &S, const PSmem &sm, int buf, int N, int p, int pl, bool own, int rank,
+                            int Nc, bool halo, int *clear_flag, int *s_err, int *nhalo) {
     const bool owner = own && (threadIdx.x % T) == 0;
     const bool brute = N <= BRUTE_MAX;
     const bool hashed = !brute && S.ncell[0] >= 3 && S.ncell[1] >= 3 && S.ncell[2] >= 3;
@@ -706,6 +721,49 @@ __device__ void build_lists(const Sim &S, const PSmem &sm, int buf, int N, int p
         sm.nw[pl] = (uint8_t)m;
     }
     __syncthreads();
+    if (halo) {
+        for (int q = threadIdx.x; q < N; q += blockDim.x) sm.mark[q] = 0;
+        if (threadIdx.x == 0) *nhalo = 0;
+        __syncthreads();
+        if (own) {
+            const int lt = threadIdx.x % T;
+            const uint16_t *lst = sm.nbr + pl * NBR_CAP;
+            const int n = sm.nn[pl];
+            for (int k = lt; k < n; k += T) {
+                const int q = lst[k];
+                if (q / Nc != rank) sm.mark[q] = 1;
+            }
+            if (lt == 0)
+                for (int d = -2; d <= 2; ++d) {
+                    const int q = p + d;
+                    if (q >= 0 && q < N && q / Nc != rank) sm.mark[q] = 1;
+                }
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < N; q += blockDim.x)
+            if (sm.mark[q]) sm.halo[atomicAdd(nhalo, 1)] = (uint16_t)q;
+        __syncthreads();
+    }
+}
+
+// Copy beads of other blocks of the chain from their owners' replicas
+// (buffer buf, written there before the last cluster barrier) into this
+// block's: the halo, or with all = true every bead this block does not own.
+// Called by every thread of the block; ends with a block barrier.
+__device__ __forceinline__ void pull_beads(cg::cluster_group &cl, const PSmem &sm, int buf, int N, int Nc, int rank,
+                                           int c0, bool all, int nhalo) {
+    float4 *ph = sm.ph[buf], *plo = sm.pl[buf];
+    const int n = all ? N : nhalo;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int q = all ? k : (int)sm.halo[k];
+        const int c = q / Nc;
+        if (c == rank) continue;
+        const float4 a = *cl.map_shared_rank(ph + q, c0 + c);
+        const float4 b = *cl.map_shared_rank(plo + q, c0 + c);
+        ph[q] = a;
+        plo[q] = b;
+    }
+    __syncthreads();
 }
 
 // SM cycles spent in phase k of realization 0 (only while profiling)
@@ -750,7 +808,7 @@ __device__ __forceinline__ void sync_all(cg::cluster_group &cl, int C) {
 template <int T>
 __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, const int Nmax, const int Nc) {
     extern __shared__ __align__(16) char smem_raw[];
-    __shared__ int s_flag[2], s_err;
+    __shared__ int s_flag[2], s_err, s_nhalo;
     PSmem sm;
     psmem_layout(Nmax, Nc, spv_noise_slots(S, Nc), &sm, smem_raw);
     cg::cluster_group cl = cg::this_cluster();
@@ -764,15 +822,20 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
     const int p = rank * Nc + pl;
     const bool own = pl < Nc && p < N;
     const bool owner = own && lt == 0;  // the lane that publishes the bead
+    const bool pull = S.md_pull != 0 && cc > 1;  // block-uniform
     const long long step = S.ctrl->step;
     const float fnx = (float)S.nx, fny = (float)S.ny, fnz = (float)S.nz;
     unsigned long long tclk = clock64();
     if (threadIdx.x == 0) { s_flag[0] = 0; s_flag[1] = 0; s_err = 0; }
 
-    // replica of the whole chain and the state of this lane's bead
+    // replica of the whole chain (both buffers, so that every entry a force
+    // term might read holds a finite position) and the state of this lane's bead
     for (int q = threadIdx.x; q < N; q += blockDim.x) {
-        sm.ph[0][q] = S.r_hi[off + q];
-        sm.pl[0][q] = S.r_lo[off + q];
+        const float4 a = S.r_hi[off + q], b = S.r_lo[off + q];
+        sm.ph[0][q] = a;
+        sm.pl[0][q] = b;
+        sm.ph[1][q] = a;
+        sm.pl[1][q] = b;
     }
     float4 mh = make_float4(0.f, 0.f, 0.f, 0.f), ml = mh;
     float3 v = make_float3(0.f, 0.f, 0.f), up = v;
@@ -795,7 +858,7 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
     // block writes into another's shared memory
     sync_all(cl, C);
     phase_mark(S, 0, tclk);
-    build_lists<T>(S, sm, 0, N, p, pl, own, nullptr, &s_err);
+    build_lists<T>(S, sm, 0, N, p, pl, own, rank, Nc, pull, nullptr, &s_err, &s_nhalo);
     phase_mark(S, 1, tclk);
 
     // MD cycle
@@ -858,9 +921,18 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
                 }
                 const float3 dd = ffsub(mh, ml, bh, bl);
                 const bool moved = dot3(dd, dd) > S.skin_half2;
-                // the T lanes of a bead hold the same position; they share
-                // the writes to the C replicas of the cluster
-                if (cc > 1) {
+                // push: the T lanes of a bead share the writes to the cc
+                // replicas of its chain; pull: the new position goes into
+                // this block's replica, and the lanes share the writes of a
+                // rebuild request
+                if (pull) {
+                    if (lt == 0) {
+                        sm.ph[nb][p] = mh;
+                        sm.pl[nb][p] = ml;
+                    }
+                    if (moved)
+                        for (int c = c0 + lt; c < c0 + cc; c += T) *cl.map_shared_rank(&s_flag[t & 1], c) = 1;
+                } else if (cc > 1) {
                     for (int c = c0 + lt; c < c0 + cc; c += T) {
                         *cl.map_shared_rank(sm.ph[nb] + p, c) = mh;
                         *cl.map_shared_rank(sm.pl[nb] + p, c) = ml;
@@ -876,13 +948,16 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
             buf = nb;
             if (s_flag[t & 1]) {
                 const unsigned long long t0 = clock64();
-                build_lists<T>(S, sm, buf, N, p, pl, own, &s_flag[t & 1], &s_err);
+                if (pull) pull_beads(cl, sm, buf, N, Nc, rank, c0, true, 0);
+                build_lists<T>(S, sm, buf, N, p, pl, own, rank, Nc, pull, &s_flag[t & 1], &s_err, &s_nhalo);
                 bh = mh;
                 bl = ml;
                 if (S.phase && blockIdx.x == 0 && threadIdx.x == 0) {
                     atomicAdd(S.phase + 4, clock64() - t0);  // cycles in rebuilds
                     atomicAdd(S.phase + 5, 1ull);            // rebuilds
                 }
+            } else if (pull) {
+                pull_beads(cl, sm, buf, N, Nc, rank, c0, false, s_nhalo);
             }
             const float3 F = group_sum<T>(force_part<T>(S, sm, buf, own, p, pl, N, mh, ml, lt));
             if (own) {
@@ -921,6 +996,10 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
             }
         }
     }
+    // pull: no block leaves while another may still be reading its replica
+    // (push: the last writes into another block's shared memory came before
+    // the last sub-step's cluster barrier)
+    if (S.md_pull) sync_all(cl, C);
     if (owner) sm.jbuf[pl] = make_float4(J.x, J.y, J.z, 0.f);
     __syncthreads();
     phase_mark(S, 2, tclk);
@@ -953,8 +1032,7 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
         if (trj) trj[(size_t)traj_slot_J(S.M, S.Mb) * TB + off + p] = make_float4(J.x, J.y, J.z, 0.f);
         if (!isfinite(mh.x + mh.y + mh.z + v.x + v.y + v.z)) atomicOr(&s_err, ST_NONFINITE);
     }
-    // the last writes into another block's shared memory came before the
-    // last sub-step's cluster barrier; this one collects the error flags
+    // this barrier collects the error flags
     __syncthreads();
     phase_mark(S, 3, tclk);
     if (threadIdx.x == 0 && s_err) atomicOr(&S.ctrl->status, s_err);

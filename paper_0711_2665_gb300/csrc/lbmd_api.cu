@@ -51,6 +51,7 @@ struct lbmd_handle {
     int by = 8, zc = 8;
     bool overlap = true;  // particle kernel concurrent with the lattice pass
     bool md_fixed = false;  // particle-kernel shape set by the caller (the autotuner leaves it)
+    int md_exchange = 0;    // chain exchange: 0 the autotuner's choice, 1 push, 2 pull
     int graph_steps = 0;
     cudaGraphExec_t gexec = nullptr;
     void *graph_A = nullptr;  // population buffer that was "A" when the graph was captured
@@ -1166,6 +1167,22 @@ lbmd_status lbmd_set_md_shape(lbmd_handle *h, int32_t T, int32_t C) {
     return upload_md_map(h, h->S, 0);
 }
 
+lbmd_status lbmd_set_md_exchange(lbmd_handle *h, int32_t mode) {
+    if (!h || mode < 0 || mode > 2) return LBMD_ERR_INVALID_ARG;
+    h->md_exchange = mode;
+    if (mode == 0) return LBMD_OK;
+    const int pull = mode == 2 ? 1 : 0;
+    if (pull != h->S.md_pull) drop_graph(h);
+    h->S.md_pull = pull;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_get_md_exchange(lbmd_handle *h, int32_t *mode) {
+    if (!h || !mode) return LBMD_ERR_INVALID_ARG;
+    *mode = h->S.md_pull ? 2 : 1;
+    return LBMD_OK;
+}
+
 lbmd_status lbmd_set_overlap(lbmd_handle *h, int32_t overlap) {
     if (!h || overlap < 0 || overlap > 1) return LBMD_ERR_INVALID_ARG;
     if ((overlap != 0) != h->overlap) drop_graph(h);
@@ -1246,12 +1263,18 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
     static const int TS[] = {2, 4, 8};
     static const int CS[] = {1, 2, 4, 8};
     float best_md = 1e30f;
-    int bt = 0, bc = 0;
+    int bt = 0, bc = 0, bx = h->S.md_pull;
     for (int T : TS)
-        for (int C : CS) {
+        for (int C : CS)
+          for (int X = 0; X < 2; ++X) {
+            // both exchanges for a chain over several blocks, unless the
+            // caller fixed one; a single block exchanges nothing
+            const int pull = h->md_exchange == 0 ? X : (h->md_exchange == 2 ? 1 : 0);
+            if (X == 1 && (h->md_exchange != 0 || C == 1)) continue;
             Sim trial = h->S;
             trial.md_T = T;
             trial.md_C = C;
+            trial.md_pull = pull;
             const MdShape m = md_shape(trial);
             if (m.threads > 512 || m.C != C || m.smem > 200 * 1024) continue;
             if (C > 1 && C > (h->S.max_beads + 15) / 16) continue;  // blocks of a few beads: barrier-bound
@@ -1275,8 +1298,8 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
                 CK(cudaEventElapsedTime(&ms, a, b));
                 h->launches += 3LL * reps;
             }
-            if (ms < best_md) { best_md = ms; bt = T; bc = C; }
-        }
+            if (ms < best_md) { best_md = ms; bt = T; bc = C; bx = pull; }
+          }
     CK(cudaMemcpyAsync(h->S.r_hi, snap, bb16, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(h->S.r_lo, snap + bb16, bb16, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(h->S.v, snap + 2 * bb16, bb16, cudaMemcpyDeviceToDevice, h->st));
@@ -1284,9 +1307,10 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
     CK(put_back());
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    if (bt > 0 && (bt != h->S.md_T || bc != h->S.md_C)) {
+    if (bt > 0 && (bt != h->S.md_T || bc != h->S.md_C || bx != h->S.md_pull)) {
         h->S.md_T = bt;
         h->S.md_C = bc;
+        h->S.md_pull = bx;
         drop_graph(h);
         return upload_md_map(h, h->S, 0);
     }

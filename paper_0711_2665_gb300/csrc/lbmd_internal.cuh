@@ -167,6 +167,7 @@ struct Sim {
     float E, gamma, kT;
     int M, Mb;
     int md_T, md_C;          // particle-kernel shape override (0 = automatic)
+    int md_pull;             // chain exchange between a cluster's blocks: 0 push, 1 pull (halo)
     // placement of the chains in the particle kernel's clusters: per block
     // (realization or -1, rank within its chain, the chain's blocks, the
     // chain's first rank in the cluster); md_clusters clusters of the shape's C

@@ -122,6 +122,8 @@ def lib():
         "lbmd_set_overlap": [vp, i32],
         "lbmd_get_overlap": [vp, P(i32)],
         "lbmd_get_md_shape": [vp, P(i32), P(i32)],
+        "lbmd_set_md_exchange": [vp, i32],
+        "lbmd_get_md_exchange": [vp, P(i32)],
         "lbmd_set_drive": [vp, ctypes.c_double, ctypes.c_double],
         "lbmd_step_loop": [vp, i64],
         "lbmd_adjoint_required_bytes": [vp, i32, i32, P(sz)],
@@ -258,6 +260,17 @@ class Simulation:
     def set_md_shape(self, threads_per_bead: int = 0, blocks_per_chain: int = 0):
         self._check(self._lib.lbmd_set_md_shape(self._h, int(threads_per_bead), int(blocks_per_chain)),
                     "lbmd_set_md_shape")
+
+    def set_md_exchange(self, mode: str = "auto"):
+        """Chain exchange between the blocks of a cluster: "push", "pull" or
+        "auto" (lbmd_autotune chooses)."""
+        code = {"auto": 0, "push": 1, "pull": 2}[mode]
+        self._check(self._lib.lbmd_set_md_exchange(self._h, code), "lbmd_set_md_exchange")
+
+    def md_exchange(self) -> str:
+        m = ctypes.c_int32()
+        self._check(self._lib.lbmd_get_md_exchange(self._h, ctypes.byref(m)), "lbmd_get_md_exchange")
+        return "pull" if m.value == 2 else "push"
 
     def set_overlap(self, overlap: bool):
         self._check(self._lib.lbmd_set_overlap(self._h, int(bool(overlap))), "lbmd_set_overlap")

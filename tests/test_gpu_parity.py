@@ -252,3 +252,44 @@ def test_cluster_size_does_not_change_the_arithmetic():
         other = run(T, C, 1)
         assert np.abs(other[1] - one[1]).max() <= 1e-6 + floor, (T, C)
         assert np.abs(other[2] - one[2]).max() <= 1e-5 * np.abs(one[2]).max() + floor, (T, C)
+
+
+
+def _run_exchange(w, inp, v0, mode, shape, n):
+    sim = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"])
+    sim.set_beads(inp["r0"], v0)
+    sim.set_md_shape(*shape)
+    sim.set_md_exchange(mode)
+    assert sim.md_exchange() == mode
+    sim.profile(True)
+    sim.step(n)
+    rebuilds = sim.kernel_times()["particles.rebuilds"][0]
+    sim.profile(False)
+    sim.check()
+    out = (sim.get_deviations(), *sim.get_beads(), *sim.get_coupling())
+    sim.close()
+    return out, rebuilds
+
+
+@pytest.mark.parametrize("case", ["chain over 8 blocks", "hashed lists", "shared clusters"])
+def test_exchange_modes_are_bit_identical(case):
+    """Push (every block's replica written) and pull (each block copies the
+    beads its force terms read, the whole chain at a list rebuild) move the
+    same positions between a chain's blocks: runs that rebuild their lists end
+    in the same state bit for bit.  The cases cover a chain spread over a
+    cluster of 8, a chain above 512 beads (cell-hash lists) and uneven chains
+    that share clusters.  The beads start with velocities of 0.1 per
+    component, so that they cross the half skin within the run."""
+    if case == "chain over 8 blocks":
+        w, shape = small_workload(n_beads=48, chain_seed=11), (4, 8)
+    elif case == "hashed lists":
+        w, shape = workloads.get("plain_fp32", nx=64, ny=48, nz=48, wall_x=40, n_beads=600), (4, 8)
+    else:
+        w, shape = small_workload(n_real=5, bead_counts=[40, 6, 25, 12, 33], chain_seed=3), (4, 4)
+    inp = workloads.build_inputs(w)
+    v0 = 0.1 * np.random.default_rng(4).choice([-1.0, 1.0], size=inp["r0"].shape)
+    push, _ = _run_exchange(w, inp, v0, "push", shape, 30)
+    pull, rebuilds = _run_exchange(w, inp, v0, "pull", shape, 30)
+    assert rebuilds > 0, "no list rebuild: the whole-chain copy was not exercised"
+    for a, b in zip(push, pull):
+        assert np.array_equal(a, b), case
