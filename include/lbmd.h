@@ -282,10 +282,11 @@ lbmd_status lbmd_get_overlap(lbmd_handle *h, int32_t *overlap);
  * current state and keep the fastest; then, unless the caller fixed the
  * particle-kernel shape with lbmd_set_md_shape, time pseudo-steps (gather,
  * particle kernel concurrent with the lattice pass) for every admissible
- * (lanes per bead in {2,4,8}, blocks per chain in {1,2,4,8}, and, unless the
- * caller fixed it with lbmd_set_md_exchange, push or pull exchange for more
- * than one block) and keep the fastest.  The state (populations, beads, G, step) is restored afterwards.
- * Synchronises the stream. */
+ * shape and keep the fastest: lanes per bead in {2,4,8}; blocks per chain in
+ * {1,2,4,8,16} (16 where the device can place such a cluster); push or pull
+ * exchange for more than one block, unless the caller fixed it with
+ * lbmd_set_md_exchange.  The state (populations, beads, G, step) is restored
+ * afterwards.  Synchronises the stream. */
 lbmd_status lbmd_autotune(lbmd_handle *h, int32_t steps_per_candidate, int32_t *by, int32_t *zc);
 
 /* Per-kernel timing with CUDA events on the launching streams (eager launches

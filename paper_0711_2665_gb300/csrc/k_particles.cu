@@ -1038,8 +1038,10 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
     if (threadIdx.x == 0 && s_err) atomicOr(&S.ctrl->status, s_err);
 }
 
+// Launch (n_fit null) or, with n_fit, report how many clusters of the shape
+// can be resident at once (0: the device cannot schedule one).
 template <int T>
-static cudaError_t launch_particles_t(const Sim &S, const MdShape &m, cudaStream_t st) {
+static cudaError_t launch_particles_t(const Sim &S, const MdShape &m, cudaStream_t st, int *n_fit) {
     cudaError_t e = cudaFuncSetAttribute(k_particles<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m.smem);
     if (e != cudaSuccess) return e;
     if (m.C > 8) {  // clusters above the portable size of 8 are opt-in
@@ -1058,18 +1060,29 @@ static cudaError_t launch_particles_t(const Sim &S, const MdShape &m, cudaStream
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (n_fit) return cudaOccupancyMaxActiveClusters(n_fit, (void *)k_particles<T>, &cfg);
     return cudaLaunchKernelEx(&cfg, k_particles<T>, S, m.C, max(S.max_beads, 1), m.Nc);
+}
+
+static cudaError_t particles_dispatch(const Sim &S, cudaStream_t st, int *n_fit) {
+    const MdShape m = md_shape(S);
+    switch (m.T) {
+        case 1: return launch_particles_t<1>(S, m, st, n_fit);
+        case 2: return launch_particles_t<2>(S, m, st, n_fit);
+        case 8: return launch_particles_t<8>(S, m, st, n_fit);
+        default: return launch_particles_t<4>(S, m, st, n_fit);
+    }
 }
 
 cudaError_t launch_particles(const Sim &S, const void *, cudaStream_t st) {
     if (S.total_beads == 0 || S.md_clusters == 0) return cudaSuccess;
-    const MdShape m = md_shape(S);
-    switch (m.T) {
-        case 1: return launch_particles_t<1>(S, m, st);
-        case 2: return launch_particles_t<2>(S, m, st);
-        case 8: return launch_particles_t<8>(S, m, st);
-        default: return launch_particles_t<4>(S, m, st);
-    }
+    return particles_dispatch(S, st, nullptr);
+}
+
+cudaError_t particles_clusters_fit(const Sim &S, int *n_fit) {
+    *n_fit = 0;
+    if (S.total_beads == 0 || S.md_clusters == 0) return cudaSuccess;
+    return particles_dispatch(S, 0, n_fit);
 }
 
 // ---------------------------------------------------------------------------

@@ -1261,7 +1261,7 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
     CK(cudaMemcpyAsync(snap + bb16, h->S.r_lo, bb16, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(snap + 2 * bb16, h->S.v, bb16, cudaMemcpyDeviceToDevice, h->st));
     static const int TS[] = {2, 4, 8};
-    static const int CS[] = {1, 2, 4, 8};
+    static const int CS[] = {1, 2, 4, 8, 16};
     float best_md = 1e30f;
     int bt = 0, bc = 0, bx = h->S.md_pull;
     for (int T : TS)
@@ -1280,6 +1280,11 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
             if (C > 1 && C > (h->S.max_beads + 15) / 16) continue;  // blocks of a few beads: barrier-bound
             lbmd_status us = upload_md_map(h, trial, 1);
             if (us != LBMD_OK) return us;
+            if (C > 8) {  // a non-portable cluster size: only where the device can place one
+                int fit = 0;
+                CK(particles_clusters_fit(trial, &fit));
+                if (fit < 1) continue;
+            }
             float ms = 0.f;
             for (int pass = 0; pass < 2; ++pass) {  // warm-up pass, then the timed one
                 CK(cudaEventRecord(a, h->st));

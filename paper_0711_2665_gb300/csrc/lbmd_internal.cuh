@@ -420,6 +420,8 @@ MdShape md_shape(const Sim &S);
 cudaError_t launch_gather(const Sim &S, const void *A, cudaStream_t st);
 cudaError_t launch_bead_diag(const Sim &S, cudaStream_t st);
 cudaError_t launch_particles(const Sim &S, const void *A, cudaStream_t st);
+// clusters of the particle kernel's shape for S that can be resident at once
+cudaError_t particles_clusters_fit(const Sim &S, int *n_fit);
 cudaError_t launch_bead_observables(const Sim &S, const void *A, cudaStream_t st);
 // reverse mode (FP32 populations only)
 cudaError_t launch_sc_adjoint(const Sim &S, const void *A, const float *Lin, float *Lout, int by, int zc, cudaStream_t st);
