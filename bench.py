@@ -333,6 +333,10 @@ def main():
                     help="comma list of the other forms to measure (ensemble_fp32, fp16dev, variants, adjoint), or none")
     ap.add_argument("--tiles", type=int, nargs=2, metavar=("BY", "ZC"), default=None,
                     help="fixed stream-collide tile shape instead of the autotuner (for profiling runs)")
+    ap.add_argument("--md-shape", type=int, nargs=2, metavar=("T", "C"), default=None,
+                    help="with --tiles: lanes per bead and blocks per chain of the particle kernel")
+    ap.add_argument("--md-exchange", choices=["push", "pull"], default=None,
+                    help="with --tiles: the particle kernel's chain exchange")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -363,6 +367,10 @@ def main():
     sim = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"], device=f"cuda:{local}")
     if args.tiles:
         sim.set_tiles(*args.tiles)
+        if args.md_shape:
+            sim.set_md_shape(*args.md_shape)
+        if args.md_exchange:
+            sim.set_md_exchange(args.md_exchange)
     else:
         sim.autotune(3)
     sites = w["nx"] * w["ny"] * w["nz"] * w["n_real"]
