@@ -411,18 +411,21 @@ __device__ __forceinline__ float3 bonded_part(const Sim &S, const PSmem &sm, int
                                               float4 ml, int lt) {
     float3 F = make_float3(0.f, 0.f, 0.f);
     const float4 *ph = sm.ph[buf], *plo = sm.pl[buf];
-    if (own) {
-        if constexpr (T >= 3) {
-            // Lane lt (< 3) takes the angle whose beads are a = p+lt-2,
-            // b = p+lt-1, c = p+lt, with u = r_b - r_a and w = r_c - r_b.  Its
-            // share of the force on p (p = c, b, a for lt = 0, 1, 2) is
-            // +A dcos/dw, A (dcos/du - dcos/dw), -A dcos/du.  Lanes 0 and 1 also
-            // take the bond along w (p = c: -k(|w| - r0) w/|w|; p = b: +...).
-            // Straight-line code with selects: the bond and angle chains of a
-            // lane are independent and overlap.
-            const int ia = p + lt - 2, ib = p + lt - 1, ic = p + lt;
-            const bool va = ia >= 0 && ia < N, vb = ib >= 0 && ib < N, vc = ic >= 0 && ic < N;
-            const int ja = va ? ia : p, jb = vb ? ib : p, jc = vc ? ic : p;
+    if constexpr (T >= 3) {
+        // Lane lt (< 3) takes the angle whose beads are a = p+lt-2,
+        // b = p+lt-1, c = p+lt, with u = r_b - r_a and w = r_c - r_b.  Its
+        // share of the force on p (p = c, b, a for lt = 0, 1, 2) is
+        // +A dcos/dw, A (dcos/du - dcos/dw), -A dcos/du.  Lanes 0 and 1 also
+        // take the bond along w (p = c: -k(|w| - r0) w/|w|; p = b: +...).
+        // Straight-line code with selects, for every lane (own or not: a
+        // lane without a bead reads bead 0 and selects nothing), so that the
+        // bond and angle chains and the pair terms that follow share one
+        // basic block and overlap.
+        {
+            const int pb = own ? p : 0;
+            const int ia = pb + lt - 2, ib = pb + lt - 1, ic = pb + lt;
+            const bool va = own && ia >= 0 && ia < N, vb = own && ib >= 0 && ib < N, vc = own && ic >= 0 && ic < N;
+            const int ja = va ? ia : pb, jb = vb ? ib : pb, jc = vc ? ic : pb;
             const float4 ha = ph[ja], la = plo[ja], hb = ph[jb], lb = plo[jb], hc = ph[jc], lc = plo[jc];
             const float3 u = ffsub(hb, lb, ha, la), w = ffsub(hc, lc, hb, lb);
             const bool bond_ok = lt < 2 && vb && vc;
@@ -441,7 +444,9 @@ __device__ __forceinline__ float3 bonded_part(const Sim &S, const PSmem &sm, int
             const float be = lt == 0 ? 1.0f : (lt == 1 ? -1.0f : 0.0f);
             if (bond_ok) F = F + (bsign * bc) * w;
             if (ang_ok) F = F + al * d1 + be * d2;
-        } else {
+        }
+    } else if (own) {
+        {
             const bool m1 = p >= 1, m2 = p >= 2, p1 = p + 1 < N, p2 = p + 2 < N;
             float4 hm1 = mh, lm1 = ml, hm2 = mh, lm2 = ml, hp1 = mh, lp1 = ml, hp2 = mh, lp2 = ml;
             if (m1) { hm1 = ph[p - 1]; lm1 = plo[p - 1]; }
@@ -490,11 +495,13 @@ __device__ __forceinline__ float3 pair_part(const Sim &S, const PSmem &sm, int b
     // Pair and wall lists, two entries per iteration, to the warp's longest
     // list: both entries' shared-memory loads are issued before either is
     // used, and no lane branches away (entries past a lane's own list point
-    // at the bead itself and are selected out).
+    // at the bead itself and are selected out).  The first pair iteration
+    // runs unconditionally, in the basic block of the bonded terms, so that
+    // its chain overlaps theirs (with no entries it adds zeros).
     {
         const uint16_t *lst = sm.nbr + (own ? pl : 0) * NBR_CAP;
         const int pself = own ? p : 0;  // a bead of the replica for lanes without one
-        for (int k = lt; k < nn_w; k += 2 * T) {
+        for (int k = lt; k == lt || k < nn_w; k += 2 * T) {
             const bool v0 = k < nn, v1 = k + T < nn;
             const int q0 = v0 ? (int)lst[k] : pself;
             const int q1 = v1 ? (int)lst[k + T] : pself;
