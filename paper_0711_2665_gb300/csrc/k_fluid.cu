@@ -247,25 +247,30 @@ __global__ void __launch_bounds__(256) k_source(const Sim S, void *__restrict__ 
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < 8 * S.total_beads) {
         const int gnode = S.pair_node[k];
-        if (gnode >= 0 && atomicExch(S.stamp + gnode, tag) != tag) {
+        if (gnode >= 0) {
             const int r = gnode / S.ns;
             const int s = gnode - r * S.ns;
             const size_t ns = (size_t)S.ns;
             unsigned long long *Gr = S.G + (size_t)r * 3 * ns + s;
-            const float G0 = (float)(long long)Gr[0] * FIX_INV_SCALE_F;
-            const float G1 = (float)(long long)Gr[ns] * FIX_INV_SCALE_F;
-            const float G2 = (float)(long long)Gr[2 * ns] * FIX_INV_SCALE_F;
-            Gr[0] = 0ull; Gr[ns] = 0ull; Gr[2 * ns] = 0ull;
             T *B = reinterpret_cast<T *>(Bv) + (size_t)r * Q * S.ps;
-            // all 19 loads first: loads and stores through one pointer would
-            // otherwise run one L2 round trip after another
+            // G and the 19 populations are loaded before the stamp decides
+            // whether this pair applies the source, so that all of them and
+            // the exchange travel together; a pair that loses the stamp
+            // drops what it loaded
+            const long long g0 = (long long)__ldcg(Gr), g1 = (long long)__ldcg(Gr + ns), g2 = (long long)__ldcg(Gr + 2 * ns);
             float h[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) h[i] = load_dev_cg(B, (uint32_t)i * (uint32_t)S.ps + (uint32_t)s);
+            if (atomicExch(S.stamp + gnode, tag) != tag) {
+                const float G0 = (float)g0 * FIX_INV_SCALE_F;
+                const float G1 = (float)g1 * FIX_INV_SCALE_F;
+                const float G2 = (float)g2 * FIX_INV_SCALE_F;
+                Gr[0] = 0ull; Gr[ns] = 0ull; Gr[2 * ns] = 0ull;
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const float src = 3.0f * wq(i) * ((float)cx(i) * G0 + (float)cy(i) * G1 + (float)cz(i) * G2);
-                store_dev(B, (uint32_t)i * (uint32_t)S.ps + (uint32_t)s, h[i] + src);
+                for (int i = 0; i < Q; ++i) {
+                    const float src = 3.0f * wq(i) * ((float)cx(i) * G0 + (float)cy(i) * G1 + (float)cz(i) * G2);
+                    store_dev(B, (uint32_t)i * (uint32_t)S.ps + (uint32_t)s, h[i] + src);
+                }
             }
         }
     }
@@ -282,8 +287,10 @@ __global__ void __launch_bounds__(256) k_source(const Sim S, void *__restrict__ 
         row->p_fluid[2] = (double)acc[3] * unit;
         acc[0] = 0; acc[1] = 0; acc[2] = 0; acc[3] = 0;
     }
+    // Every thread has used the step it read before this barrier, so the
+    // last block's update cannot reach an earlier read; the stores above are
+    // for later kernels, which the kernel boundary orders.  No fence.
     __shared__ int am_last;
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) am_last = (atomicAdd(&S.ctrl->src_done, 1u) == gridDim.x - 1u);
     __syncthreads();

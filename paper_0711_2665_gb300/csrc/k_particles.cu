@@ -343,7 +343,7 @@ struct PSmem {
     int16_t *hnext;         // [Nmax] cell lists
     uint8_t *nn, *nw;       // [Nc] list lengths
     float4 *znz;            // [Nc][Mb] noise of the SPV inner steps of one outer step (or none)
-    uint16_t *halo;         // [Nmax] the other blocks' beads this block's force terms read
+    uint32_t *halo;         // [Nmax] the other blocks' beads this block's force terms read: q | owner rank << 16
     uint8_t *mark;          // [Nmax] scratch of the halo build
 };
 
@@ -360,7 +360,7 @@ __host__ __device__ inline size_t psmem_layout(int nmax, int nc, int nzn, PSmem 
     char *hnext = take(2 * (size_t)nmax);
     char *nn = take((size_t)nc), *nw = take((size_t)nc);
     char *znz = take(16 * (size_t)nzn);
-    char *halo = take(2 * (size_t)nmax), *mark = take((size_t)nmax);
+    char *halo = take(4 * (size_t)nmax), *mark = take((size_t)nmax);
     if (p) {
         p->ph[0] = (float4 *)ph0; p->ph[1] = (float4 *)ph1;
         p->pl[0] = (float4 *)pl0; p->pl[1] = (float4 *)pl1;
@@ -369,7 +369,7 @@ __host__ __device__ inline size_t psmem_layout(int nmax, int nc, int nzn, PSmem 
         p->hkey = (int *)hkey; p->hhead = (int *)hhead; p->hnext = (int16_t *)hnext;
         p->nn = (uint8_t *)nn; p->nw = (uint8_t *)nw;
         p->znz = (float4 *)znz;
-        p->halo = (uint16_t *)halo;
+        p->halo = (uint32_t *)halo;
         p->mark = (uint8_t *)mark;
     }
     return o;
@@ -582,8 +582,8 @@ __device__ __forceinline__ void cell_of(const Sim &S, float xw, float yw, float 
 // clear_flag (if not null) is reset once every thread has read it.  With
 // halo set (pull exchange, chain over more than one block) it also lists the
 // block's halo: the beads of other blocks (rank != this block's) in its beads'
-// pair lists or within two bonds of them, in no particular order, their count
-// in *nhalo.
+// pair lists or within two bonds of them, in no particular order, each with
+// the chain rank of its block in bits 16 and up, their count in *nhalo.
 // Pair list of bead p by its T lanes over every bead of the chain in
 // ascending order: lane lt tests q = kT + lt and a ballot over the bead's
 // lanes compacts the hits, so the list comes out sorted (the order the
@@ -748,7 +748,7 @@ __device__ void build_lists(const Sim &S, const PSmem &sm, int buf, int N, int p
         }
         __syncthreads();
         for (int q = threadIdx.x; q < N; q += blockDim.x)
-            if (sm.mark[q]) sm.halo[atomicAdd(nhalo, 1)] = (uint16_t)q;
+            if (sm.mark[q]) sm.halo[atomicAdd(nhalo, 1)] = (uint32_t)q | ((uint32_t)(q / Nc) << 16);
         __syncthreads();
     }
 }
@@ -762,8 +762,9 @@ __device__ __forceinline__ void pull_beads(cg::cluster_group &cl, const PSmem &s
     float4 *ph = sm.ph[buf], *plo = sm.pl[buf];
     const int n = all ? N : nhalo;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        const int q = all ? k : (int)sm.halo[k];
-        const int c = q / Nc;
+        const uint32_t e = all ? 0u : sm.halo[k];
+        const int q = all ? k : (int)(e & 0xffffu);
+        const int c = all ? q / Nc : (int)(e >> 16);
         if (c == rank) continue;
         const float4 a = *cl.map_shared_rank(ph + q, c0 + c);
         const float4 b = *cl.map_shared_rank(plo + q, c0 + c);
