@@ -268,6 +268,19 @@ lbmd_status lbmd_get_md_shape(lbmd_handle *h, int32_t *threads_per_bead, int32_t
  * arithmetic: the state is bit-identical.  LBMD_ERR_INVALID_ARG for another
  * mode.  lbmd_get_md_exchange reports the mode in effect (1 or 2). */
 lbmd_status lbmd_set_md_exchange(lbmd_handle *h, int32_t mode);
+
+/* Who evaluates the bonded terms (bonds, Eq. 19, and the angular term) in
+ * the particle kernel: mode 1 every bead's lanes (an angle is evaluated by
+ * each of its three beads, a bond by both of its beads); 2 one extra warp per
+ * block, which evaluates each bond and angle once while the other warps sum
+ * the pair terms; 0 automatic (2 for blocks of at most 30 beads, else 1).
+ * The modes add the terms in different orders, so their results agree to
+ * rounding; within one mode the state does not depend on the shape's number of
+ * blocks.  LBMD_ERR_INVALID_ARG for another mode, or if the extra warp would
+ * take the block past 512 threads.  lbmd_get_md_bonded reports the mode in
+ * effect (1 or 2). */
+lbmd_status lbmd_set_md_bonded(lbmd_handle *h, int32_t mode);
+lbmd_status lbmd_get_md_bonded(lbmd_handle *h, int32_t *mode);
 lbmd_status lbmd_get_md_exchange(lbmd_handle *h, int32_t *mode);
 
 /* overlap = 1 (default): the particle kernel runs concurrently with the

@@ -345,6 +345,7 @@ struct PSmem {
     float4 *znz;            // [Nc][Mb] noise of the SPV inner steps of one outer step (or none)
     uint32_t *halo;         // [Nmax] the other blocks' beads this block's force terms read: q | owner rank << 16
     uint8_t *mark;          // [Nmax] scratch of the halo build
+    float4 *bnd;            // [Nc + 2][3] bonded terms of the centres first-1 .. last+1 (bonded_stage)
 };
 
 // nzn: float4 slots for the SPV noise (Nc * Mb when that cycle draws noise, else 0)
@@ -361,6 +362,7 @@ __host__ __device__ inline size_t psmem_layout(int nmax, int nc, int nzn, PSmem 
     char *nn = take((size_t)nc), *nw = take((size_t)nc);
     char *znz = take(16 * (size_t)nzn);
     char *halo = take(4 * (size_t)nmax), *mark = take((size_t)nmax);
+    char *bnd = take(48 * ((size_t)nc + 2));
     if (p) {
         p->ph[0] = (float4 *)ph0; p->ph[1] = (float4 *)ph1;
         p->pl[0] = (float4 *)pl0; p->pl[1] = (float4 *)pl1;
@@ -371,6 +373,7 @@ __host__ __device__ inline size_t psmem_layout(int nmax, int nc, int nzn, PSmem 
         p->znz = (float4 *)znz;
         p->halo = (uint32_t *)halo;
         p->mark = (uint8_t *)mark;
+        p->bnd = (float4 *)bnd;
     }
     return o;
 }
@@ -384,7 +387,8 @@ __host__ __device__ inline int spv_noise_slots(const Sim &S, int nc) {
 // blocks (about 50 beads per block: the sub-step is latency-bound, so fewer
 // beads per SM shorten it); an ensemble keeps each chain in as few blocks as
 // fit (<= 512 threads per block), since its realizations already fill the
-// GPU.  A shape set through lbmd_set_md_shape (S.md_T, S.md_C) takes precedence.
+// GPU.  A shape set through lbmd_set_md_shape (S.md_T, S.md_C) takes
+// precedence.
 MdShape md_shape(const Sim &S) {
     MdShape m;
     const int N = S.max_beads;
@@ -394,7 +398,9 @@ MdShape md_shape(const Sim &S) {
     const int spread = S.n_real == 1 ? min(8, max(fit, (N + 49) / 50)) : fit;
     m.C = S.md_C > 0 ? S.md_C : spread;
     m.Nc = N > 0 ? (N + m.C - 1) / m.C : 1;
-    m.threads = max(32, ((m.Nc * m.T + 31) / 32) * 32);
+    // the bonded warp: by request, else for blocks of at most 30 beads
+    m.bw = S.md_bw == 2 || (S.md_bw == 0 && m.Nc + 2 <= 32);
+    m.threads = max(32, ((m.Nc * m.T + 31) / 32) * 32) + (m.bw ? 32 : 0);
     m.smem = psmem_layout(max(N, 1), m.Nc, spv_noise_slots(S, m.Nc), nullptr, nullptr);
     return m;
 }
@@ -485,6 +491,64 @@ __device__ __forceinline__ float3 bonded_part(const Sim &S, const PSmem &sm, int
     return F;
 }
 
+// Bonded warp (blocks of at most 30 beads by default): each bond and angle
+// is evaluated once per block by the block's last warp (bonded_stage), which
+// leaves its terms in shared memory, while the other warps sum the pair and
+// wall terms with T lanes per bead (pair_part); full_force adds the two.
+// Without it, an angle is evaluated by each of its three beads' lanes and a
+// bond by both of its beads' (bonded_part), which costs every warp the
+// bonded instructions but needs no block barrier; with more than 30 beads a
+// block the one bonded warp would loop and set the pace.
+//
+// bonded_stage: slot s of sm.bnd holds, for centre j = first - 1 + s
+// (first = the block's first bead), the angle terms d1 = A dcos/du and
+// d2 = A dcos/dw of u = r_j - r_{j-1}, w = r_{j+1} - r_j (zero where the angle
+// does not exist or kappa = 0) and the bond term k (|w| - r0) w / |w| of
+// (j, j+1) (zero where that bond does not exist).  Called by the 32 lanes of
+// one warp; the block's own beads need the centres first - 1 .. last + 1.
+__device__ __forceinline__ void bonded_stage(const Sim &S, const PSmem &sm, int buf, int N, int first, int last) {
+    const float4 *ph = sm.ph[buf], *plo = sm.pl[buf];
+    const int nctr = last >= first ? last - first + 3 : 0;
+    for (int sl = threadIdx.x & 31; sl < nctr; sl += 32) {
+        const int j = first - 1 + sl;
+        const bool bond_ok = j >= 0 && j + 1 < N;
+        const bool ang_ok = j >= 1 && j + 1 < N && S.kappa != 0.0f;
+        const int jb = min(max(j, 0), N - 1);
+        const int ja = bond_ok || ang_ok ? max(j - 1, 0) : jb, jc = min(jb + 1, N - 1);
+        const float4 ha = ph[ja], la = plo[ja], hb = ph[jb], lb = plo[jb], hc = ph[jc], lc = plo[jc];
+        const float3 u = ffsub(hb, lb, ha, la), w = ffsub(hc, lc, hb, lb);
+        // |w| from the correctly rounded sqrt: |w| - r0 cancels and keeps
+        // only the absolute error of |w|
+        const float w2 = bond_ok ? dot3(w, w) : 1.0f;
+        const float len = sqrtf(w2);
+        const float bc = __fdividef(S.k_bond * (len - S.r0), len);
+        const float3 uu = ang_ok ? u : make_float3(1.f, 0.f, 0.f);
+        const float3 ww = ang_ok ? w : make_float3(0.f, 1.f, 0.f);
+        float3 d1, d2;
+        bend_terms(uu, ww, S.kappa, d1, d2);
+        const float3 z = make_float3(0.f, 0.f, 0.f);
+        if (!ang_ok) { d1 = z; d2 = z; }
+        const float3 bw = bond_ok ? bc * w : z;
+        sm.bnd[3 * sl + 0] = make_float4(d1.x, d1.y, d1.z, 0.f);
+        sm.bnd[3 * sl + 1] = make_float4(d2.x, d2.y, d2.z, 0.f);
+        sm.bnd[3 * sl + 2] = make_float4(bw.x, bw.y, bw.z, 0.f);
+    }
+}
+
+// Bonded force on the bead of slot s (s = p - first + 1) from the terms of
+// the slots s - 1, s, s + 1, in a fixed order: the bonds to p-1 and p+1, then
+// the angles centred at p-1 (p is its c), p (its b) and p+1 (its a).
+__device__ __forceinline__ float3 bonded_of(const PSmem &sm, int s) {
+    const float4 b0 = sm.bnd[3 * (s - 1) + 2], b1 = sm.bnd[3 * s + 2];
+    const float4 d2m = sm.bnd[3 * (s - 1) + 1], d1c = sm.bnd[3 * s + 0], d2c = sm.bnd[3 * s + 1];
+    const float4 d1p = sm.bnd[3 * (s + 1) + 0];
+    float3 F = make_float3(b1.x - b0.x, b1.y - b0.y, b1.z - b0.z);
+    F = F + make_float3(d2m.x, d2m.y, d2m.z);
+    F = F + make_float3(d1c.x - d2c.x, d1c.y - d2c.y, d1c.z - d2c.z);
+    F = F - make_float3(d1p.x, d1p.y, d1p.z);
+    return F;
+}
+
 template <int T>
 __device__ __forceinline__ float3 pair_part(const Sim &S, const PSmem &sm, int buf, bool own, int p, int pl, float4 mh,
                                             float4 ml, int lt, float3 F) {
@@ -538,6 +602,7 @@ __device__ __forceinline__ float3 pair_part(const Sim &S, const PSmem &sm, int b
     return F;
 }
 
+
 template <int T>
 __device__ __forceinline__ float3 force_part(const Sim &S, const PSmem &sm, int buf, bool own, int p, int pl, int N, float4 mh,
                                              float4 ml, int lt) {
@@ -553,6 +618,26 @@ __device__ __forceinline__ float3 group_sum(float3 F) {
         F.y += __shfl_xor_sync(0xffffffffu, F.y, o);
         F.z += __shfl_xor_sync(0xffffffffu, F.z, o);
     }
+    return F;
+}
+
+// The whole conservative force on this lane's bead (zero for a lane without
+// one), from replica buf; called by every thread of the block.  With a
+// bonded warp (BWM) the last warp (bw) evaluates the bonded
+// terms and the others the pair and wall terms, and a block barrier joins
+// them; otherwise every bead's T lanes evaluate all its terms (force_part).
+template <int T, bool BWM>
+__device__ __forceinline__ float3 full_force(const Sim &S, const PSmem &sm, int buf, bool own, bool bw, int p, int pl,
+                                             int N, int first, int last, float4 mh, float4 ml, int lt) {
+    float3 F = make_float3(0.f, 0.f, 0.f);
+    if constexpr (!BWM) {
+        F = group_sum<T>(force_part<T>(S, sm, buf, own, p, pl, N, mh, ml, lt));
+        return own ? F : make_float3(0.f, 0.f, 0.f);
+    }
+    if (bw) bonded_stage(S, sm, buf, N, first, last);
+    else F = group_sum<T>(pair_part<T>(S, sm, buf, own, p, pl, mh, ml, lt, F));
+    __syncthreads();
+    if (own) F = F + bonded_of(sm, p - first + 1);
     return F;
 }
 
@@ -813,7 +898,7 @@ __device__ __forceinline__ void sync_all(cg::cluster_group &cl, int C) {
 // ---------------------------------------------------------------------------
 // the particle kernel (one cluster of C blocks per realization)
 // ---------------------------------------------------------------------------
-template <int T>
+template <int T, bool BWM>
 __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, const int Nmax, const int Nc) {
     extern __shared__ __align__(16) char smem_raw[];
     __shared__ int s_flag[2], s_err, s_nhalo;
@@ -830,6 +915,8 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
     const int p = rank * Nc + pl;
     const bool own = pl < Nc && p < N;
     const bool owner = own && lt == 0;  // the lane that publishes the bead
+    const bool bw = BWM && threadIdx.x >= blockDim.x - 32;  // the warp of the bonded terms
+    const int first = rank * Nc, last = min(first + Nc, N) - 1;  // the block's beads
     const bool pull = S.md_pull != 0 && cc > 1;  // block-uniform
     const long long step = S.ctrl->step;
     const float fnx = (float)S.nx, fny = (float)S.ny, fnz = (float)S.nz;
@@ -876,8 +963,7 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
     float3 J = make_float3(0.f, 0.f, 0.f);
     float4 bh = mh, bl = ml;  // position at the last list build
     int buf = 0, t = 0;
-    float3 ff = group_sum<T>(force_part<T>(S, sm, buf, own, p, pl, N, mh, ml, lt));
-    if (!own) ff = make_float3(0.f, 0.f, 0.f);
+    float3 ff = full_force<T, BWM>(S, sm, buf, own, bw, p, pl, N, first, last, mh, ml, lt);
     // Stochastic position Verlet (integrator 1): the half kicks carry the
     // field only; each sub-step drifts to its mid-point (h/2 for the first,
     // then h: the second half of one sub-step and the first of the next),
@@ -967,7 +1053,7 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
             } else if (pull) {
                 pull_beads(cl, sm, buf, N, Nc, rank, c0, false, s_nhalo);
             }
-            const float3 F = group_sum<T>(force_part<T>(S, sm, buf, own, p, pl, N, mh, ml, lt));
+            const float3 F = full_force<T, BWM>(S, sm, buf, own, bw, p, pl, N, first, last, mh, ml, lt);
             if (own) {
                 if (spv) {
                     float3 z = make_float3(0.f, 0.f, 0.f);
@@ -1050,10 +1136,11 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
 // can be resident at once (0: the device cannot schedule one).
 template <int T>
 static cudaError_t launch_particles_t(const Sim &S, const MdShape &m, cudaStream_t st, int *n_fit) {
-    cudaError_t e = cudaFuncSetAttribute(k_particles<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m.smem);
+    auto kern = m.bw ? k_particles<T, true> : k_particles<T, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m.smem);
     if (e != cudaSuccess) return e;
     if (m.C > 8) {  // clusters above the portable size of 8 are opt-in
-        e = cudaFuncSetAttribute(k_particles<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
     }
     cudaLaunchConfig_t cfg = {};
@@ -1068,8 +1155,8 @@ static cudaError_t launch_particles_t(const Sim &S, const MdShape &m, cudaStream
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (n_fit) return cudaOccupancyMaxActiveClusters(n_fit, (void *)k_particles<T>, &cfg);
-    return cudaLaunchKernelEx(&cfg, k_particles<T>, S, m.C, max(S.max_beads, 1), m.Nc);
+    if (n_fit) return cudaOccupancyMaxActiveClusters(n_fit, (void *)kern, &cfg);
+    return cudaLaunchKernelEx(&cfg, kern, S, m.C, max(S.max_beads, 1), m.Nc);
 }
 
 static cudaError_t particles_dispatch(const Sim &S, cudaStream_t st, int *n_fit) {

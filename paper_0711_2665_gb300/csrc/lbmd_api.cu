@@ -1177,6 +1177,23 @@ lbmd_status lbmd_set_md_exchange(lbmd_handle *h, int32_t mode) {
     return LBMD_OK;
 }
 
+lbmd_status lbmd_set_md_bonded(lbmd_handle *h, int32_t mode) {
+    if (!h || mode < 0 || mode > 2) return LBMD_ERR_INVALID_ARG;
+    Sim trial = h->S;
+    trial.md_bw = mode;
+    if (md_shape(trial).threads > 512)
+        return fail(h, LBMD_ERR_INVALID_ARG, "particle-kernel shape needs more than 512 threads per block");
+    if (mode != h->S.md_bw) drop_graph(h);
+    h->S.md_bw = mode;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_get_md_bonded(lbmd_handle *h, int32_t *mode) {
+    if (!h || !mode) return LBMD_ERR_INVALID_ARG;
+    *mode = md_shape(h->S).bw ? 2 : 1;
+    return LBMD_OK;
+}
+
 lbmd_status lbmd_get_md_exchange(lbmd_handle *h, int32_t *mode) {
     if (!h || !mode) return LBMD_ERR_INVALID_ARG;
     *mode = h->S.md_pull ? 2 : 1;

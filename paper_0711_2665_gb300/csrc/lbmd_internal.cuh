@@ -168,6 +168,7 @@ struct Sim {
     int M, Mb;
     int md_T, md_C;          // particle-kernel shape override (0 = automatic)
     int md_pull;             // chain exchange between a cluster's blocks: 0 push, 1 pull (halo)
+    int md_bw;               // bonded terms: 0 automatic, 1 by every bead's lanes, 2 by a block's last warp
     // placement of the chains in the particle kernel's clusters: per block
     // (realization or -1, rank within its chain, the chain's blocks, the
     // chain's first rank in the cluster); md_clusters clusters of the shape's C
@@ -414,6 +415,7 @@ cudaError_t launch_push_from_staging(const Sim &S, const float *staging, void *A
 // blocks per realization, Nc beads per block
 struct MdShape {
     int T, C, Nc, threads;
+    bool bw;  // bonded terms by a block's last warp
     size_t smem;
 };
 MdShape md_shape(const Sim &S);

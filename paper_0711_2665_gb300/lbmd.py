@@ -124,6 +124,8 @@ def lib():
         "lbmd_get_md_shape": [vp, P(i32), P(i32)],
         "lbmd_set_md_exchange": [vp, i32],
         "lbmd_get_md_exchange": [vp, P(i32)],
+        "lbmd_set_md_bonded": [vp, i32],
+        "lbmd_get_md_bonded": [vp, P(i32)],
         "lbmd_set_drive": [vp, ctypes.c_double, ctypes.c_double],
         "lbmd_step_loop": [vp, i64],
         "lbmd_adjoint_required_bytes": [vp, i32, i32, P(sz)],
@@ -271,6 +273,17 @@ class Simulation:
         m = ctypes.c_int32()
         self._check(self._lib.lbmd_get_md_exchange(self._h, ctypes.byref(m)), "lbmd_get_md_exchange")
         return "pull" if m.value == 2 else "push"
+
+    def set_md_bonded(self, mode: str = "auto"):
+        """Bonded terms of the particle kernel: "lanes" (every bead's lanes),
+        "warp" (one extra warp per block) or "auto"."""
+        code = {"auto": 0, "lanes": 1, "warp": 2}[mode]
+        self._check(self._lib.lbmd_set_md_bonded(self._h, code), "lbmd_set_md_bonded")
+
+    def md_bonded(self) -> str:
+        m = ctypes.c_int32()
+        self._check(self._lib.lbmd_get_md_bonded(self._h, ctypes.byref(m)), "lbmd_get_md_bonded")
+        return "warp" if m.value == 2 else "lanes"
 
     def set_overlap(self, overlap: bool):
         self._check(self._lib.lbmd_set_overlap(self._h, int(bool(overlap))), "lbmd_set_overlap")

@@ -224,35 +224,39 @@ def test_nonfinite_state_is_reported():
 
 
 def test_cluster_size_does_not_change_the_arithmetic():
-    """With the lanes per bead fixed, spreading a chain over 1, 2, 4, 8 or 16
-    blocks of a cluster changes who computes a bead, not how: every run of
-    40 steps (list rebuilds included) ends in the same state bit for bit.
-    Other lane counts split each force differently: after one step they agree
-    to rounding.  Over many steps they part: the pore field is a step function
-    of position, so a rounding difference can decide a kick of E h."""
+    """With the lanes per bead and the bonded mode fixed, spreading a chain
+    over 1, 2, 4, 8 or 16 blocks of a cluster changes who computes a bead,
+    not how: every run of 40 steps (list rebuilds included) ends in the same
+    state bit for bit.  Other lane counts split each pair sum differently, and
+    the two bonded modes add the bonded terms in different orders: after one
+    step they agree to rounding.  Over many steps they part: the pore field is
+    a step function of position, so a rounding difference can decide a kick
+    of E h."""
     w = small_workload(n_beads=48, chain_seed=11)
     inp = workloads.build_inputs(w)
 
-    def run(T, C, n):
+    def run(T, C, n, bonded="lanes"):
         sim = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"])
         sim.set_md_shape(T, C)
+        sim.set_md_bonded(bonded)
+        assert sim.md_bonded() == bonded
         sim.step(n)
         sim.check()
         out = (sim.get_deviations(), *sim.get_beads())
         sim.close()
         return out
 
-    ref = run(4, 1, 40)
-    for C in (2, 4, 8, 16):
-        for a, b in zip(ref, run(4, C, 40)):
-            assert np.array_equal(a, b), C
+    for bonded in ("lanes", "warp"):
+        ref = run(4, 1, 40, bonded)
+        for C in (2, 4, 8, 16):
+            for a, b in zip(ref, run(4, C, 40, bonded)):
+                assert np.array_equal(a, b), (bonded, C)
     one = run(4, 1, 1)
     floor = w["k_bond"] * 2.0 ** -24
-    for T, C in ((2, 4), (8, 2), (1, 1)):
-        other = run(T, C, 1)
-        assert np.abs(other[1] - one[1]).max() <= 1e-6 + floor, (T, C)
-        assert np.abs(other[2] - one[2]).max() <= 1e-5 * np.abs(one[2]).max() + floor, (T, C)
-
+    for T, C, bonded in ((2, 4, "lanes"), (8, 2, "lanes"), (1, 1, "lanes"), (4, 1, "warp"), (8, 16, "warp")):
+        other = run(T, C, 1, bonded)
+        assert np.abs(other[1] - one[1]).max() <= 1e-6 + floor, (T, C, bonded)
+        assert np.abs(other[2] - one[2]).max() <= 1e-5 * np.abs(one[2]).max() + floor, (T, C, bonded)
 
 
 def _run_exchange(w, inp, v0, mode, shape, n):
