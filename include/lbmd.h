@@ -271,9 +271,10 @@ lbmd_status lbmd_set_md_exchange(lbmd_handle *h, int32_t mode);
 
 /* Who evaluates the bonded terms (bonds, Eq. 19, and the angular term) in
  * the particle kernel: mode 1 every bead's lanes (an angle is evaluated by
- * each of its three beads, a bond by both of its beads); 2 one extra warp per
- * block, which evaluates each bond and angle once while the other warps sum
- * the pair terms; 0 automatic (2 for blocks of at most 30 beads, else 1).
+ * each of its three beads, a bond by both of its beads); 2 ceil((Nc + 2)/32)
+ * extra warps per block of Nc beads, which evaluate each bond and angle once
+ * while the other warps sum the pair terms; 0 automatic (2 for blocks of at
+ * most 30 beads, else 1, until lbmd_autotune times both).
  * The modes add the terms in different orders, so their results agree to
  * rounding; within one mode the state does not depend on the shape's number of
  * blocks.  LBMD_ERR_INVALID_ARG for another mode, or if the extra warp would
@@ -298,7 +299,8 @@ lbmd_status lbmd_get_overlap(lbmd_handle *h, int32_t *overlap);
  * shape and keep the fastest: lanes per bead in {2,4,8}; blocks per chain in
  * {1,2,4,8,16} (16 where the device can place such a cluster); push or pull
  * exchange for more than one block, unless the caller fixed it with
- * lbmd_set_md_exchange.  The state (populations, beads, G, step) is restored
+ * lbmd_set_md_exchange; both bonded modes, unless fixed with
+ * lbmd_set_md_bonded.  The state (populations, beads, G, step) is restored
  * afterwards.  Synchronises the stream. */
 lbmd_status lbmd_autotune(lbmd_handle *h, int32_t steps_per_candidate, int32_t *by, int32_t *zc);
 

@@ -349,6 +349,9 @@ struct PSmem {
 };
 
 // nzn: float4 slots for the SPV noise (Nc * Mb when that cycle draws noise, else 0)
+// warps of the bonded terms for blocks of nc beads: one lane per centre
+__host__ __device__ inline int bonded_warps(int nc) { return (nc + 2 + 31) / 32; }
+
 __host__ __device__ inline size_t psmem_layout(int nmax, int nc, int nzn, PSmem *p, char *base) {
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o += (bytes + 15) & ~(size_t)15; return base + at; };
@@ -400,7 +403,7 @@ MdShape md_shape(const Sim &S) {
     m.Nc = N > 0 ? (N + m.C - 1) / m.C : 1;
     // the bonded warp: by request, else for blocks of at most 30 beads
     m.bw = S.md_bw == 2 || (S.md_bw == 0 && m.Nc + 2 <= 32);
-    m.threads = max(32, ((m.Nc * m.T + 31) / 32) * 32) + (m.bw ? 32 : 0);
+    m.threads = max(32, ((m.Nc * m.T + 31) / 32) * 32) + (m.bw ? 32 * bonded_warps(m.Nc) : 0);
     m.smem = psmem_layout(max(N, 1), m.Nc, spv_noise_slots(S, m.Nc), nullptr, nullptr);
     return m;
 }
@@ -491,14 +494,14 @@ __device__ __forceinline__ float3 bonded_part(const Sim &S, const PSmem &sm, int
     return F;
 }
 
-// Bonded warp (blocks of at most 30 beads by default): each bond and angle
-// is evaluated once per block by the block's last warp (bonded_stage), which
-// leaves its terms in shared memory, while the other warps sum the pair and
-// wall terms with T lanes per bead (pair_part); full_force adds the two.
-// Without it, an angle is evaluated by each of its three beads' lanes and a
-// bond by both of its beads' (bonded_part), which costs every warp the
-// bonded instructions but needs no block barrier; with more than 30 beads a
-// block the one bonded warp would loop and set the pace.
+// Bonded warps (by default for blocks of at most 30 beads, one warp): each
+// bond and angle is evaluated once per block by the block's last
+// ceil((Nc + 2) / 32) warps (bonded_stage), which leave their terms in
+// shared memory, while the other warps sum the pair and wall terms with T
+// lanes per bead (pair_part); full_force adds the two.  Without them, an
+// angle is evaluated by each of its three beads' lanes and a bond by both of
+// its beads' (bonded_part), which costs every warp the bonded instructions
+// but needs no block barrier and no extra threads.
 //
 // bonded_stage: slot s of sm.bnd holds, for centre j = first - 1 + s
 // (first = the block's first bead), the angle terms d1 = A dcos/du and
@@ -506,10 +509,12 @@ __device__ __forceinline__ float3 bonded_part(const Sim &S, const PSmem &sm, int
 // does not exist or kappa = 0) and the bond term k (|w| - r0) w / |w| of
 // (j, j+1) (zero where that bond does not exist).  Called by the 32 lanes of
 // one warp; the block's own beads need the centres first - 1 .. last + 1.
-__device__ __forceinline__ void bonded_stage(const Sim &S, const PSmem &sm, int buf, int N, int first, int last) {
+__device__ __forceinline__ void bonded_stage(const Sim &S, const PSmem &sm, int buf, int N, int Nc, int first,
+                                             int last) {
     const float4 *ph = sm.ph[buf], *plo = sm.pl[buf];
     const int nctr = last >= first ? last - first + 3 : 0;
-    for (int sl = threadIdx.x & 31; sl < nctr; sl += 32) {
+    const int nbt = 32 * bonded_warps(Nc);  // the block's last nbt threads
+    for (int sl = threadIdx.x - (blockDim.x - nbt); sl < nctr; sl += nbt) {
         const int j = first - 1 + sl;
         const bool bond_ok = j >= 0 && j + 1 < N;
         const bool ang_ok = j >= 1 && j + 1 < N && S.kappa != 0.0f;
@@ -628,13 +633,13 @@ __device__ __forceinline__ float3 group_sum(float3 F) {
 // them; otherwise every bead's T lanes evaluate all its terms (force_part).
 template <int T, bool BWM>
 __device__ __forceinline__ float3 full_force(const Sim &S, const PSmem &sm, int buf, bool own, bool bw, int p, int pl,
-                                             int N, int first, int last, float4 mh, float4 ml, int lt) {
+                                             int N, int Nc, int first, int last, float4 mh, float4 ml, int lt) {
     float3 F = make_float3(0.f, 0.f, 0.f);
     if constexpr (!BWM) {
         F = group_sum<T>(force_part<T>(S, sm, buf, own, p, pl, N, mh, ml, lt));
         return own ? F : make_float3(0.f, 0.f, 0.f);
     }
-    if (bw) bonded_stage(S, sm, buf, N, first, last);
+    if (bw) bonded_stage(S, sm, buf, N, Nc, first, last);
     else F = group_sum<T>(pair_part<T>(S, sm, buf, own, p, pl, mh, ml, lt, F));
     __syncthreads();
     if (own) F = F + bonded_of(sm, p - first + 1);
@@ -915,7 +920,7 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
     const int p = rank * Nc + pl;
     const bool own = pl < Nc && p < N;
     const bool owner = own && lt == 0;  // the lane that publishes the bead
-    const bool bw = BWM && threadIdx.x >= blockDim.x - 32;  // the warp of the bonded terms
+    const bool bw = BWM && threadIdx.x >= blockDim.x - 32 * bonded_warps(Nc);  // the warps of the bonded terms
     const int first = rank * Nc, last = min(first + Nc, N) - 1;  // the block's beads
     const bool pull = S.md_pull != 0 && cc > 1;  // block-uniform
     const long long step = S.ctrl->step;
@@ -963,7 +968,7 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
     float3 J = make_float3(0.f, 0.f, 0.f);
     float4 bh = mh, bl = ml;  // position at the last list build
     int buf = 0, t = 0;
-    float3 ff = full_force<T, BWM>(S, sm, buf, own, bw, p, pl, N, first, last, mh, ml, lt);
+    float3 ff = full_force<T, BWM>(S, sm, buf, own, bw, p, pl, N, Nc, first, last, mh, ml, lt);
     // Stochastic position Verlet (integrator 1): the half kicks carry the
     // field only; each sub-step drifts to its mid-point (h/2 for the first,
     // then h: the second half of one sub-step and the first of the next),
@@ -1053,7 +1058,7 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
             } else if (pull) {
                 pull_beads(cl, sm, buf, N, Nc, rank, c0, false, s_nhalo);
             }
-            const float3 F = full_force<T, BWM>(S, sm, buf, own, bw, p, pl, N, first, last, mh, ml, lt);
+            const float3 F = full_force<T, BWM>(S, sm, buf, own, bw, p, pl, N, Nc, first, last, mh, ml, lt);
             if (own) {
                 if (spv) {
                     float3 z = make_float3(0.f, 0.f, 0.f);

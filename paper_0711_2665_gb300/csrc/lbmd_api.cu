@@ -52,6 +52,7 @@ struct lbmd_handle {
     bool overlap = true;  // particle kernel concurrent with the lattice pass
     bool md_fixed = false;  // particle-kernel shape set by the caller (the autotuner leaves it)
     int md_exchange = 0;    // chain exchange: 0 the autotuner's choice, 1 push, 2 pull
+    int md_bonded = 0;      // bonded terms: 0 the autotuner's choice, 1 every bead's lanes, 2 bonded warps
     int graph_steps = 0;
     cudaGraphExec_t gexec = nullptr;
     void *graph_A = nullptr;  // population buffer that was "A" when the graph was captured
@@ -1157,12 +1158,14 @@ lbmd_status lbmd_set_md_shape(lbmd_handle *h, int32_t T, int32_t C) {
     Sim trial = h->S;
     trial.md_T = T;
     trial.md_C = C;
+    trial.md_bw = h->md_bonded;  // the caller's bonded mode, not an autotuned one
     const MdShape m = md_shape(trial);
     if (m.threads > 512 || m.C < 1 || m.C > MAX_CLUSTER || m.smem > 200 * 1024)
         return fail(h, LBMD_ERR_INVALID_ARG, "particle-kernel shape needs more than 512 threads per block");
-    if (T != h->S.md_T || C != h->S.md_C) drop_graph(h);
+    if (T != h->S.md_T || C != h->S.md_C || trial.md_bw != h->S.md_bw) drop_graph(h);
     h->S.md_T = T;
     h->S.md_C = C;
+    h->S.md_bw = trial.md_bw;
     h->md_fixed = T != 0 || C != 0;
     return upload_md_map(h, h->S, 0);
 }
@@ -1185,6 +1188,7 @@ lbmd_status lbmd_set_md_bonded(lbmd_handle *h, int32_t mode) {
         return fail(h, LBMD_ERR_INVALID_ARG, "particle-kernel shape needs more than 512 threads per block");
     if (mode != h->S.md_bw) drop_graph(h);
     h->S.md_bw = mode;
+    h->md_bonded = mode;
     return LBMD_OK;
 }
 
@@ -1280,10 +1284,13 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
     static const int TS[] = {2, 4, 8};
     static const int CS[] = {1, 2, 4, 8, 16};
     float best_md = 1e30f;
-    int bt = 0, bc = 0, bx = h->S.md_pull;
+    int bt = 0, bc = 0, bx = h->S.md_pull, bb_w = h->S.md_bw;
     for (int T : TS)
         for (int C : CS)
+          for (int B = 1; B <= 2; ++B)
           for (int X = 0; X < 2; ++X) {
+            // both bonded modes unless the caller fixed one
+            if (h->md_bonded != 0 && B != h->md_bonded) continue;
             // both exchanges for a chain over several blocks, unless the
             // caller fixed one; a single block exchanges nothing
             const int pull = h->md_exchange == 0 ? X : (h->md_exchange == 2 ? 1 : 0);
@@ -1292,6 +1299,7 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
             trial.md_T = T;
             trial.md_C = C;
             trial.md_pull = pull;
+            trial.md_bw = B;
             const MdShape m = md_shape(trial);
             if (m.threads > 512 || m.C != C || m.smem > 200 * 1024) continue;
             if (C > 1 && C > (h->S.max_beads + 15) / 16) continue;  // blocks of a few beads: barrier-bound
@@ -1320,7 +1328,7 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
                 CK(cudaEventElapsedTime(&ms, a, b));
                 h->launches += 3LL * reps;
             }
-            if (ms < best_md) { best_md = ms; bt = T; bc = C; bx = pull; }
+            if (ms < best_md) { best_md = ms; bt = T; bc = C; bx = pull; bb_w = B; }
           }
     CK(cudaMemcpyAsync(h->S.r_hi, snap, bb16, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(h->S.r_lo, snap + bb16, bb16, cudaMemcpyDeviceToDevice, h->st));
@@ -1329,10 +1337,11 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
     CK(put_back());
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    if (bt > 0 && (bt != h->S.md_T || bc != h->S.md_C || bx != h->S.md_pull)) {
+    if (bt > 0 && (bt != h->S.md_T || bc != h->S.md_C || bx != h->S.md_pull || bb_w != h->S.md_bw)) {
         h->S.md_T = bt;
         h->S.md_C = bc;
         h->S.md_pull = bx;
+        h->S.md_bw = bb_w;
         drop_graph(h);
         return upload_md_map(h, h->S, 0);
     }
