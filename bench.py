@@ -263,10 +263,12 @@ def extra_measurements(dev, stream, peak, peak_kind, forms, tiles=None):
         torch.cuda.synchronize(dev)
         return a.elapsed_time(b) * 1e-3
 
-    for name, K in (("ensemble_fp32", 100), ("fp16dev", 60)):
+    # fp32_matched: the FP16 form's workload (256x128x128, N = 1000) stored in
+    # FP32, the plain step at the 4.19 M sites of the ensemble and FP16 forms
+    for name, K in (("ensemble_fp32", 100), ("fp16dev", 60), ("fp32_matched", 60)):
         if name not in forms:
             continue
-        w = workloads.get(name)
+        w = workloads.get("fp16dev", precision="fp32") if name == "fp32_matched" else workloads.get(name)
         inp = workloads.build_inputs(w)
         sim = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"], device=str(dev))
         if tiles:
@@ -287,6 +289,10 @@ def extra_measurements(dev, stream, peak, peak_kind, forms, tiles=None):
                      "launch": "one CUDA-graph launch per run (device-side loop of two-step bodies)",
                      "roofline": rf}
         sim.close()
+    if "fp32_matched" in out:
+        base = out["fp32_matched"]["value"]
+        out["speedups_vs_fp32_matched"] = {
+            k: out[k]["value"] / base for k in ("ensemble_fp32", "fp16dev") if k in out}
     if "variants" in forms:
         out["variants"] = _variants(dev, lbmd, workloads, tiles)
     if "adjoint" not in forms:
@@ -330,8 +336,9 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--forms", default="ensemble_fp32,fp16dev,variants,adjoint",
-                    help="comma list of the other forms to measure (ensemble_fp32, fp16dev, variants, adjoint), or none")
+    ap.add_argument("--forms", default="ensemble_fp32,fp16dev,fp32_matched,variants,adjoint",
+                    help="comma list of the other forms to measure (ensemble_fp32, fp16dev, fp32_matched, "
+                         "variants, adjoint), or none")
     ap.add_argument("--tiles", type=int, nargs=2, metavar=("BY", "ZC"), default=None,
                     help="fixed stream-collide tile shape instead of the autotuner (for profiling runs)")
     ap.add_argument("--md-shape", type=int, nargs=2, metavar=("T", "C"), default=None,
