@@ -712,8 +712,8 @@ __device__ __forceinline__ int scan_pairs(const Sim &S, const float4 *ph, const 
 // busy); longer ones a cell hash in shared memory, scanned by one lane per
 // bead.  Both give each bead's pairs within the list radius in ascending order.
 template <int T>
-__device__ void build_lists(const Sim &S, const PSmem &sm, int buf, int N, int p, int pl, bool own, int rank,
-                            int Nc, bool halo, int *clear_flag, int *s_err, int *nhalo) {
+__device__ __forceinline__ void build_lists_body(const Sim &S, const PSmem &sm, int buf, int N, int p, int pl, bool own,
+                                                 int rank, int Nc, bool halo, int *clear_flag, int *s_err, int *nhalo) {
     const bool owner = own && (threadIdx.x % T) == 0;
     const bool brute = N <= BRUTE_MAX;
     const bool hashed = !brute && S.ncell[0] >= 3 && S.ncell[1] >= 3 && S.ncell[2] >= 3;
@@ -843,6 +843,24 @@ __device__ void build_lists(const Sim &S, const PSmem &sm, int buf, int N, int p
     }
 }
 
+// The list build, called out of line or inlined.  Out of line, the rare
+// rebuild's code stays out of the MD sub-step loop, which then fits the
+// instruction cache better (the headline's particle kernel: 183 -> 172 us per
+// LB step), at the price of a few registers.  Inlined, the kernel keeps its
+// register count, which the bead-lanes shapes of the ensemble, sharing SMs
+// with the lattice pass, need.
+template <int T>
+__device__ __noinline__ void build_lists_call(const Sim &S, const PSmem &sm, int buf, int N, int p, int pl, bool own,
+                                              int rank, int Nc, bool halo, int *clear_flag, int *s_err, int *nhalo) {
+    build_lists_body<T>(S, sm, buf, N, p, pl, own, rank, Nc, halo, clear_flag, s_err, nhalo);
+}
+template <int T, bool OUT_OF_LINE>
+__device__ __forceinline__ void build_lists(const Sim &S, const PSmem &sm, int buf, int N, int p, int pl, bool own,
+                                            int rank, int Nc, bool halo, int *clear_flag, int *s_err, int *nhalo) {
+    if constexpr (OUT_OF_LINE) build_lists_call<T>(S, sm, buf, N, p, pl, own, rank, Nc, halo, clear_flag, s_err, nhalo);
+    else build_lists_body<T>(S, sm, buf, N, p, pl, own, rank, Nc, halo, clear_flag, s_err, nhalo);
+}
+
 // Copy beads of other blocks of the chain from their owners' replicas
 // (buffer buf, written there before the last cluster barrier) into this
 // block's: the halo, or with all = true every bead this block does not own.
@@ -958,7 +976,7 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
     // block writes into another's shared memory
     sync_all(cl, C);
     phase_mark(S, 0, tclk);
-    build_lists<T>(S, sm, 0, N, p, pl, own, rank, Nc, pull, nullptr, &s_err, &s_nhalo);
+    build_lists<T, BWM>(S, sm, 0, N, p, pl, own, rank, Nc, pull, nullptr, &s_err, &s_nhalo);
     phase_mark(S, 1, tclk);
 
     // MD cycle
@@ -1048,7 +1066,7 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
             if (s_flag[t & 1]) {
                 const unsigned long long t0 = clock64();
                 if (pull) pull_beads(cl, sm, buf, N, Nc, rank, c0, true, 0);
-                build_lists<T>(S, sm, buf, N, p, pl, own, rank, Nc, pull, &s_flag[t & 1], &s_err, &s_nhalo);
+                build_lists<T, BWM>(S, sm, buf, N, p, pl, own, rank, Nc, pull, &s_flag[t & 1], &s_err, &s_nhalo);
                 bh = mh;
                 bl = ml;
                 if (S.phase && blockIdx.x == 0 && threadIdx.x == 0) {
