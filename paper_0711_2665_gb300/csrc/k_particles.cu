@@ -327,9 +327,12 @@ __device__ __forceinline__ void bend_terms(float3 b1, float3 b2, float kappa, fl
     d2 = A * (inv12 * b1 - __fdividef(c, l2s) * b2);
 }
 
-// WCA (Eq. 14 cut at its minimum, shifted): -dV/dd = coef * d
+// WCA (Eq. 14 cut at its minimum, shifted): -dV/dd = coef * d.  1/r^2 from
+// the hardware reciprocal (within about an ulp; the pair terms sit on the
+// sub-step's dependent chain, where the correctly rounded one costs a
+// Newton refinement)
 __device__ __forceinline__ float wca_coef(float r2, float eps, float sig2) {
-    const float ir2 = __frcp_rn(r2), sr2 = sig2 * ir2;
+    const float ir2 = __fdividef(1.0f, r2), sr2 = sig2 * ir2;
     const float sr6 = sr2 * sr2 * sr2;
     return 24.0f * eps * (2.0f * sr6 * sr6 - sr6) * ir2;
 }
