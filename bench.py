@@ -213,7 +213,7 @@ def _variants(dev, lbmd, workloads, tiles, steps=100):
         if tiles:
             sim.set_tiles(*tiles)
         else:
-            sim.autotune(3)
+            sim.autotune(8)
         st = sim.stream
         sim.set_graph(2)
         sim.step(6)
@@ -275,7 +275,7 @@ def extra_measurements(dev, stream, peak, peak_kind, forms, tiles=None):
             sim.set_tiles(*tiles)
             by, zc = tiles
         else:
-            by, zc = sim.autotune(3)
+            by, zc = sim.autotune(8)
         sim.step_loop(20)  # captures the device-side loop graph
         t = timed(lambda: sim.step_loop(K))
         sites = w["nx"] * w["ny"] * w["nz"] * w["n_real"]
@@ -304,7 +304,7 @@ def extra_measurements(dev, stream, peak, peak_kind, forms, tiles=None):
     if tiles:
         sim.set_tiles(*tiles)
     else:
-        sim.autotune(3)
+        sim.autotune(8)
     sim.step(4)
     t_fwd = timed(lambda: sim.step(K))
     sim2 = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"], device=str(dev))
@@ -380,7 +380,7 @@ def main():
         if args.md_exchange:
             sim.set_md_exchange(args.md_exchange)
     else:
-        sim.autotune(3)
+        sim.autotune(8)
     sites = w["nx"] * w["ny"] * w["nz"] * w["n_real"]
     flush = not args.no_flush
     # L2 flush between timed steps: write 256 MiB, then read another 256 MiB so
