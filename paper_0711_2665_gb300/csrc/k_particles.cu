@@ -12,11 +12,14 @@
 //      G(x) -= W(x - r_p) J_p with the gather's weights, as 2^40 fixed-point
 //      integer atomics (order-independent, so runs repeat bit for bit).
 //
-// Layout of the particle kernel.  Each realization is one thread-block
-// cluster of C blocks (C = 1 for short chains).  Block c owns Nc consecutive
-// beads, and each bead is worked on by T consecutive threads that split its
-// force terms (bonds, the three angles that involve it, its bead and wall
-// pair lists) and add them with a butterfly of shuffles.  Every block keeps a
+// Layout of the particle kernel.  A chain takes ceil(N / Nc) consecutive
+// blocks of one thread-block cluster of C blocks; short chains share a
+// cluster.  Block c owns Nc consecutive beads, and each bead is worked on by
+// T consecutive threads that split its pair and wall terms and add them with
+// a butterfly of shuffles.  The bonded terms (bonds, the three angles that
+// involve a bead) are either split over the same T lanes, or, in the
+// bonded-warp kernels (BWM), evaluated once per bond and angle by extra warps
+// at the end of the block (see bonded_stage).  Every block keeps a
 // replica of the chain's positions in shared memory, exchanged through
 // distributed shared memory in one of two ways (S.md_pull, chosen by the
 // autotuner): push, where a bead's new position is written to every replica
