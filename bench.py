@@ -59,7 +59,8 @@ def _traffic_record(sites: int):
 
 
 class ClockSampler:
-    """nvidia-smi samples every 200 ms while the timed region runs."""
+    """nvidia-smi samples every 20 ms while the timed regions run; entering
+    waits (at most 3 s) for the first sample, so that sampling covers them."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -75,8 +76,11 @@ class ClockSampler:
             fd, self.path = tempfile.mkstemp(prefix=f"lbmd_clocks_{self.gpu}_", suffix=".csv")
             self.fh = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
+            t_end = time.perf_counter() + 3.0
+            while time.perf_counter() < t_end and os.path.getsize(self.path) == 0 and self.proc.poll() is None:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
             if self.path:
@@ -428,27 +432,27 @@ def main():
             sim.step(n)
             ev[k][1].record(stream)
         barrier()
-    launches = sim.launch_count() - launches0
-    total_ms = pdist.max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world)
-    sim.check()
-    job_sites = pdist.sum_over_ranks(sites, world)
-    value = job_sites * args.steps / (total_ms * 1e-3) / 1e6
+        launches = sim.launch_count() - launches0
+        total_ms = pdist.max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world)
+        sim.check()
+        job_sites = pdist.sum_over_ranks(sites, world)
+        value = job_sites * args.steps / (total_ms * 1e-3) / 1e6
 
-    # Timed region 2 (kernel shares and the lattice kernel's roofline): the
-    # same K steps launched kernel by kernel with a CUDA event pair around
-    # every kernel on the stream it runs on.  The events lengthen the step,
-    # so this pass does not give the value.
-    sim.set_graph(0)
-    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    sim.profile(True)
-    barrier()
-    for k in range(args.steps):
-        if flush:
-            flush_l2()
-        ev2[k][0].record(stream)
-        sim.step(1)
-        ev2[k][1].record(stream)
-    barrier()
+        # Timed region 2 (kernel shares and the lattice kernel's roofline): the
+        # same K steps launched kernel by kernel with a CUDA event pair around
+        # every kernel on the stream it runs on.  The events lengthen the step,
+        # so this pass does not give the value.
+        sim.set_graph(0)
+        ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        sim.profile(True)
+        barrier()
+        for k in range(args.steps):
+            if flush:
+                flush_l2()
+            ev2[k][0].record(stream)
+            sim.step(1)
+            ev2[k][1].record(stream)
+        barrier()
     ktimes = sim.kernel_times()
     sim.profile(False)
     profiled_ms = pdist.max_over_ranks(sum(a.elapsed_time(b) for a, b in ev2), world)
