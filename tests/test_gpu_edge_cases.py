@@ -110,11 +110,17 @@ def test_ensemble_full_size_sampled_realizations():
         assert np.abs(v_all[o0:o1] - vo).max() < 1e-5 * np.abs(vo).max() + 4 * w["k_bond"] * 2.0 ** -24, r
 
 
-def test_fp16dev_full_size_one_step():
+@pytest.mark.parametrize("shape", [None, (4, 16, "pull", "warp")])
+def test_fp16dev_full_size_one_step(shape):
     """256x128x128 with FP16 deviations and a 1000-bead chain: one step from the
-    same FP16-representable state stays within the storage rounding."""
+    same FP16-representable state stays within the storage rounding, with the
+    default particle shape and with the one the bench's autotuner picks."""
     w = workloads.get("fp16dev")
     sim, orc, inp = make_pair(w)
+    if shape:
+        sim.set_md_shape(shape[0], shape[1])
+        sim.set_md_exchange(shape[2])
+        sim.set_md_bonded(shape[3])
     orc.step(2)
     f32, r, v = to_f32_state(orc)
     _, wts, _ = oracle.tables()

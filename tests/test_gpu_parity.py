@@ -82,12 +82,22 @@ def test_one_step_without_noise_and_with_body_force():
     _compare_one_step(sim, orc)
 
 
-@pytest.mark.parametrize("name", ["plain_fp64_small", "plain_fp32", "adjoint"])
-def test_one_step_at_full_workload_size(name):
-    """The named workloads at their full sizes and bench launch shapes: develop
-    a state in the oracle, then one step on both sides from the same state."""
+@pytest.mark.parametrize("name,shape", [
+    ("plain_fp64_small", None), ("plain_fp32", None), ("adjoint", None),
+    # the particle-kernel shapes the bench's autotuner picks for the 400-bead chain
+    ("plain_fp32", (8, 16, "pull", "warp")), ("plain_fp32", (4, 16, "pull", "warp")),
+    ("plain_fp32", (4, 8, "push", "lanes")),
+])
+def test_one_step_at_full_workload_size(name, shape):
+    """The named workloads at their full sizes, with the default particle
+    shape and with the shapes the bench times: develop a state in the oracle,
+    then one step on both sides from the same state."""
     w = workloads.get(name, precision="fp32")
     sim, orc, inp = make_pair(w)
+    if shape:
+        sim.set_md_shape(shape[0], shape[1])
+        sim.set_md_exchange(shape[2])
+        sim.set_md_bonded(shape[3])
     orc.step(3)
     f32, r, v = to_f32_state(orc)
     load_state(sim, orc, f32, r, v, 3)
