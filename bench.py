@@ -297,7 +297,7 @@ def extra_measurements(dev, stream, peak, peak_kind, forms, tiles=None):
                      "steps_per_s": K / t, "realization_steps_per_s": K * w["n_real"] / t, "steps": K,
                      "lattice": [w["nx"], w["ny"], w["nz"]], "n_real": w["n_real"], "beads": int(inp["offsets"][-1]),
                      "precision": w["precision"], "tiles": [by, zc], "md_shape": list(sim.md_shape()), "md_exchange": sim.md_exchange(),
-                     "md_bonded": sim.md_bonded(),
+                     "md_bonded": sim.md_bonded(), "md_reserve": sim.md_reserve(),
                      "launch": "one CUDA-graph launch per run (device-side loop of two-step bodies)",
                      "roofline": rf}
         sim.close()
@@ -526,7 +526,7 @@ def main():
                 "dtype": "f32" if w["precision"] == "fp32" else "f16-storage/f32-math",
                 "data": "synthetic", "config": dict(_config_block(w, flush), tiles=list(sim.tiles()),
                                                      md_shape=list(sim.md_shape()), md_exchange=sim.md_exchange(),
-                                                     md_bonded=sim.md_bonded()),
+                                                     md_bonded=sim.md_bonded(), md_reserve=sim.md_reserve()),
                 "launch": "captured 2-step CUDA graphs, L2 flushed before every launch",
                 "roofline": roofline, "kernels": shares, "gpu_launches": launches,
                 "kernel_timing": {"pass": "the same K steps kernel by kernel, CUDA events around every kernel",

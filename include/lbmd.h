@@ -282,6 +282,12 @@ lbmd_status lbmd_set_md_exchange(lbmd_handle *h, int32_t mode);
  * effect (1 or 2). */
 lbmd_status lbmd_set_md_bonded(lbmd_handle *h, int32_t mode);
 lbmd_status lbmd_get_md_bonded(lbmd_handle *h, int32_t *mode);
+
+/* 1 if the particle kernel's blocks are launched with their SMs' whole
+ * shared memory (226 KB), so that no block of the lattice pass or the gather
+ * shares their SMs; 0 if they take only what they use.  lbmd_autotune times
+ * both; the state does not depend on it. */
+lbmd_status lbmd_get_md_reserve(lbmd_handle *h, int32_t *reserve);
 lbmd_status lbmd_get_md_exchange(lbmd_handle *h, int32_t *mode);
 
 /* overlap = 1 (default): the particle kernel runs concurrently with the
@@ -300,7 +306,8 @@ lbmd_status lbmd_get_overlap(lbmd_handle *h, int32_t *overlap);
  * {1,2,4,8,16} (16 where the device can place such a cluster); push or pull
  * exchange for more than one block, unless the caller fixed it with
  * lbmd_set_md_exchange; both bonded modes, unless fixed with
- * lbmd_set_md_bonded.  The state (populations, beads, G, step) is restored
+ * lbmd_set_md_bonded; with and without reserving the SMs
+ * (lbmd_get_md_reserve).  The state (populations, beads, G, step) is restored
  * afterwards.  Synchronises the stream. */
 lbmd_status lbmd_autotune(lbmd_handle *h, int32_t steps_per_candidate, int32_t *by, int32_t *zc);
 

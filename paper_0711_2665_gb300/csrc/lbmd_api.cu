@@ -1198,6 +1198,12 @@ lbmd_status lbmd_get_md_bonded(lbmd_handle *h, int32_t *mode) {
     return LBMD_OK;
 }
 
+lbmd_status lbmd_get_md_reserve(lbmd_handle *h, int32_t *reserve) {
+    if (!h || !reserve) return LBMD_ERR_INVALID_ARG;
+    *reserve = h->S.md_reserve ? 1 : 0;
+    return LBMD_OK;
+}
+
 lbmd_status lbmd_get_md_exchange(lbmd_handle *h, int32_t *mode) {
     if (!h || !mode) return LBMD_ERR_INVALID_ARG;
     *mode = h->S.md_pull ? 2 : 1;
@@ -1284,9 +1290,10 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
     static const int TS[] = {2, 4, 8};
     static const int CS[] = {1, 2, 4, 8, 16};
     float best_md = 1e30f;
-    int bt = 0, bc = 0, bx = h->S.md_pull, bb_w = h->S.md_bw;
+    int bt = 0, bc = 0, bx = h->S.md_pull, bb_w = h->S.md_bw, brs = h->S.md_reserve;
     for (int T : TS)
         for (int C : CS)
+          for (int R = 0; R < 2; ++R)
           for (int B = 1; B <= 2; ++B)
           for (int X = 0; X < 2; ++X) {
             // both bonded modes unless the caller fixed one
@@ -1300,6 +1307,7 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
             trial.md_C = C;
             trial.md_pull = pull;
             trial.md_bw = B;
+            trial.md_reserve = R;
             const MdShape m = md_shape(trial);
             if (m.threads > 512 || m.C != C || m.smem > 200 * 1024) continue;
             if (C > 1 && C > (h->S.max_beads + 15) / 16) continue;  // blocks of a few beads: barrier-bound
@@ -1328,7 +1336,7 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
                 CK(cudaEventElapsedTime(&ms, a, b));
                 h->launches += 3LL * reps;
             }
-            if (ms < best_md) { best_md = ms; bt = T; bc = C; bx = pull; bb_w = B; }
+            if (ms < best_md) { best_md = ms; bt = T; bc = C; bx = pull; bb_w = B; brs = R; }
           }
     CK(cudaMemcpyAsync(h->S.r_hi, snap, bb16, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(h->S.r_lo, snap + bb16, bb16, cudaMemcpyDeviceToDevice, h->st));
@@ -1337,11 +1345,13 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
     CK(put_back());
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    if (bt > 0 && (bt != h->S.md_T || bc != h->S.md_C || bx != h->S.md_pull || bb_w != h->S.md_bw)) {
+    if (bt > 0 &&
+        (bt != h->S.md_T || bc != h->S.md_C || bx != h->S.md_pull || bb_w != h->S.md_bw || brs != h->S.md_reserve)) {
         h->S.md_T = bt;
         h->S.md_C = bc;
         h->S.md_pull = bx;
         h->S.md_bw = bb_w;
+        h->S.md_reserve = brs;
         drop_graph(h);
         return upload_md_map(h, h->S, 0);
     }

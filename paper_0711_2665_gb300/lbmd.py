@@ -126,6 +126,7 @@ def lib():
         "lbmd_get_md_exchange": [vp, P(i32)],
         "lbmd_set_md_bonded": [vp, i32],
         "lbmd_get_md_bonded": [vp, P(i32)],
+        "lbmd_get_md_reserve": [vp, P(i32)],
         "lbmd_set_drive": [vp, ctypes.c_double, ctypes.c_double],
         "lbmd_step_loop": [vp, i64],
         "lbmd_adjoint_required_bytes": [vp, i32, i32, P(sz)],
@@ -284,6 +285,11 @@ class Simulation:
         m = ctypes.c_int32()
         self._check(self._lib.lbmd_get_md_bonded(self._h, ctypes.byref(m)), "lbmd_get_md_bonded")
         return "warp" if m.value == 2 else "lanes"
+
+    def md_reserve(self) -> bool:
+        m = ctypes.c_int32()
+        self._check(self._lib.lbmd_get_md_reserve(self._h, ctypes.byref(m)), "lbmd_get_md_reserve")
+        return bool(m.value)
 
     def set_overlap(self, overlap: bool):
         self._check(self._lib.lbmd_set_overlap(self._h, int(bool(overlap))), "lbmd_set_overlap")
