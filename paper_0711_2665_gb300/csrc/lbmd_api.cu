@@ -1336,6 +1336,8 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
                 CK(cudaEventElapsedTime(&ms, a, b));
                 h->launches += 3LL * reps;
             }
+            // reserving SMs takes them from the lattice pass: it must win by 1%
+            if (R) ms *= 1.01f;
             if (ms < best_md) { best_md = ms; bt = T; bc = C; bx = pull; bb_w = B; brs = R; }
           }
     CK(cudaMemcpyAsync(h->S.r_hi, snap, bb16, cudaMemcpyDeviceToDevice, h->st));
