@@ -1,23 +1,30 @@
 """Benchmark of the coupled LB-MD step (one JSON line on stdout).
 
 A step is one coupled lattice-Boltzmann / molecular-dynamics step of the whole
-hot path: particle kernel (gather, MD cycle, spread) concurrently with the
-fused stream-collide kernel, then the source pass.  The metric is MLUPS
-(million lattice-site updates per second, all nx*ny*nz*n_real sites counted).
+hot path: gather, particle kernel (MD cycle and spread) and bead diagnostics
+concurrently with the fused stream-collide kernel, then the source pass.  The
+metric is MLUPS (million lattice-site updates per second, all
+nx*ny*nz*n_real sites counted).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
                   [--impl native|reference]
+
+The default workload is the largest single-lattice configuration: 256x128x128
+(4.19 M sites) with a 1000-bead chain, populations stored in FP32.
 
 Under torchrun (N > 1) every rank runs an independent replica of the workload
 (its own seed); value = all ranks' site updates / max-over-ranks time
 (weak scaling, no data-path collective).
 
-Timing: each timed step is bracketed by CUDA events on the library's stream;
-between timed steps a 256 MiB buffer is written to flush the 129 MB L2 (the
-populations of the default workload, 2 x 40 MB, would otherwise stay in L2).
+Timing: the K timed steps are one launch of the library's device-side
+step-loop graph, bracketed by CUDA events on the library's stream.  The
+populations (2 x 318 MB) are larger than the 129 MB L2; for a lattice small
+enough to stay in L2 the steps are launched as 2-step graphs instead, with a
+256 MiB buffer written and another read before each launch.
 The roofline object reports the stream-collide kernel: algorithmic bytes
 (19 x 4 B read + 19 x 4 B written per site in FP32, half that in FP16)
-over its CUDA-event duration, against the measured HBM copy bandwidth.
+over its CUDA-event duration, against the measured HBM copy bandwidth;
+`step_roofline` divides the same bytes by the whole step's time.
 """
 from __future__ import annotations
 
@@ -44,14 +51,17 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def _traffic_record(sites: int):
-    """DRAM bytes per launch of the stream-collide kernel from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
+def _traffic_record(workload: str, sites: int):
+    """DRAM bytes per launch of the stream-collide kernel on this workload from
+    the committed ncu summary, if it was taken on the current kernel source;
+    else None."""
     p = os.path.join(ROOT, "profiles", "stream_collide_traffic.json")
     src = os.path.join(ROOT, "paper_0711_2665_gb300", "csrc", "k_fluid.cu")
     if not os.path.exists(p):
         return None
-    rec = json.load(open(p))
+    rec = json.load(open(p)).get(workload)
+    if not rec:
+        return None
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
     if rec.get("k_fluid_sha256") != sha:
         return None
@@ -132,69 +142,90 @@ def _config_block(w, flush):
             "parallelism": "realizations split across ranks" if "shard" in w else "replicas"}
 
 
-def run_reference(args, w, world, rank):
-    """The oracle (FP64, plain C, one host thread) on the same workload; each
-    step is one oracle LB-MD step of realization 0."""
-    if rank != 0:
-        return
+def _oracle_worker(job):
+    """One oracle process: realization 0 of the workload, `warm` untimed
+    steps, then whole LB-MD steps until `steps` are done (steps > 0) or
+    `budget_s` seconds have passed.  Returns (steps, seconds)."""
+    w, warm, steps, budget_s = job
     import oracle
     from paper_0711_2665_gb300 import workloads
-    oracle.build()
     inp = workloads.build_inputs(w)
     o1 = int(inp["offsets"][1])
     orc = oracle.OracleSim(workloads.oracle_params(w, 0, o1), inp["solid"])
     orc.set_beads(inp["r0"][:o1])
-    for _ in range(args.warmup):
+    orc.step(max(warm, 1))
+    n, t0 = 0, time.perf_counter()
+    while (steps > 0 and n < steps) or (steps <= 0 and (time.perf_counter() - t0 < budget_s or n < 2)):
         orc.step(1)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        orc.step(1)
-    dt = time.perf_counter() - t0
+        n += 1
+    return n, time.perf_counter() - t0
+
+
+def oracle_on_host_cores(w, warm=1, steps=0, budget_s=10.0):
+    """The FP64 oracle, as it stands, on every host core: one spawned oracle
+    process per core, each stepping its own copy of realization 0 (replicas,
+    no shared work).  value = all processes' site updates / the slowest
+    process's time; per_core = the mean process's rate."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_worker, [(w, warm, steps, budget_s)] * cores)
     sites = w["nx"] * w["ny"] * w["nz"]
-    mlups = sites * args.steps / dt / 1e6 * w["n_real"] / w["n_real"]
-    sample = f"{args.steps} oracle steps of realization 0 ({sites} sites, {o1} beads)"
+    total = sum(n for n, _ in res)
+    t = max(dt for _, dt in res)
+    per_core = statistics.mean(sites * n / dt / 1e6 for n, dt in res)
+    beads = int(workloads_mod().bead_counts(w)[0])
+    return {"value": sites * total / t / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "per_core": per_core,
+            "sample": (f"{cores} oracle processes (one per host core), each {res[0][0]}+ FP64 steps of realization 0 "
+                       f"({sites} sites, {beads} beads) after {max(warm, 1)} untimed; slowest {t:.1f} s")}
+
+
+def workloads_mod():
+    from paper_0711_2665_gb300 import workloads
+    return workloads
+
+
+def run_reference(args, w, world, rank):
+    """The oracle (FP64, plain C) on the same workload, on every host core:
+    each of K timed steps is one oracle LB-MD step of realization 0 in every
+    core's process."""
+    if rank != 0:
+        return
+    cb = oracle_on_host_cores(w, warm=args.warmup, steps=args.steps)
+    mlups = cb["value"]
+    sites = w["nx"] * w["ny"] * w["nz"]
     line = {"impl": "reference", "metric": "coupled LB-MD MLUPS", "value": mlups, "unit": "MLUPS",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * sites * cb["cores"] / (mlups * 1e6), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _config_block(w, False),
-            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "config": _config_block(w, False), "cpu_baseline": cb,
             "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(w, budget_s=15.0):
-    """Oracle timed on a bounded sample of the workload (whole LB-MD steps of
-    realization 0) on one host core."""
-    import oracle
-    from paper_0711_2665_gb300 import workloads
-    oracle.build()
-    inp = workloads.build_inputs(w)
-    o1 = int(inp["offsets"][1])
-    orc = oracle.OracleSim(workloads.oracle_params(w, 0, o1), inp["solid"])
-    orc.set_beads(inp["r0"][:o1])
-    orc.step(1)
-    n, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < budget_s or n < 2:
-        orc.step(1)
-        n += 1
-    dt = time.perf_counter() - t0
-    sites = w["nx"] * w["ny"] * w["nz"]
-    return {"value": sites * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{n} FP64 oracle steps of realization 0 ({sites} sites, {o1} beads), {dt:.1f} s"}
+def cpu_baseline(w, budget_s=10.0):
+    """The oracle timed on a bounded sample of the workload on every host core."""
+    return oracle_on_host_cores(w, warm=1, steps=0, budget_s=budget_s)
 
 
-def _sc_roofline(sim, w, peak, peak_kind, steps=10):
+def _sc_roofline(sim, w, peak, peak_kind, steps=10, flush=None):
     """Stream-collide roofline from per-launch CUDA events over a few eager
     steps: inside the step (sharing the GPU with the particle kernel) and
-    alone (the particle kernel waited for); achieved/frac are the latter."""
+    alone (the particle kernel waited for); achieved/frac are the latter.
+    flush, if given, runs before every step (lattices that fit in L2)."""
     sites = w["nx"] * w["ny"] * w["nz"] * w["n_real"]
     b = (152 if w["precision"] == "fp32" else 76) * sites
     us = {}
     for overlap in (True, False):
         sim.set_overlap(overlap)
         sim.profile(True)
-        sim.step(steps)
+        for _ in range(steps):
+            if flush:
+                flush()
+            sim.step(1)
         kt = sim.kernel_times()
         sim.profile(False)
         n, ms = kt["stream_collide"]
@@ -255,12 +286,16 @@ def _variants(dev, lbmd, workloads, tiles, steps=100):
     return res
 
 
-def extra_measurements(dev, stream, peak, peak_kind, forms, tiles=None):
+def extra_measurements(dev, stream, peak, peak_kind, forms, tiles=None, headline=None):
     """The other forms of the step, each timed on its own workload with CUDA
-    events on the library's stream (inputs larger than L2, no flush needed):
-    the batched ensemble and the FP16-deviation storage, each run of K steps
-    one launch of the device-side step-loop graph, and the reverse sweep
-    (forward + checkpointed adjoint of 200 steps)."""
+    events on the library's stream: the 128x64x64 plain step (its 80 MB of
+    populations fit in L2, so it is launched as 2-step graphs with the L2
+    flushed before each launch), the batched ensemble and the FP16-deviation
+    storage (inputs larger than L2; each run of K steps one launch of the
+    device-side step-loop graph), and the reverse sweep (forward +
+    checkpointed adjoint of 200 steps).  The ensemble's and the FP16 form's
+    speedups are over the headline's plain FP32 step on the same 4.19 M
+    sites."""
     import numpy as np
     import torch
     from paper_0711_2665_gb300 import lbmd, workloads
@@ -275,12 +310,11 @@ def extra_measurements(dev, stream, peak, peak_kind, forms, tiles=None):
         torch.cuda.synchronize(dev)
         return a.elapsed_time(b) * 1e-3
 
-    # fp32_matched: the FP16 form's workload (256x128x128, N = 1000) stored in
-    # FP32, the plain step at the 4.19 M sites of the ensemble and FP16 forms
-    for name, K in (("ensemble_fp32", 100), ("fp16dev", 60), ("fp32_matched", 60)):
+    flush_w = flush_r = None
+    for name, K in (("plain_fp32", 60), ("ensemble_fp32", 100), ("fp16dev", 60)):
         if name not in forms:
             continue
-        w = workloads.get("fp16dev", precision="fp32") if name == "fp32_matched" else workloads.get(name)
+        w = workloads.get(name)
         inp = workloads.build_inputs(w)
         sim = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"], device=str(dev))
         if tiles:
@@ -288,23 +322,44 @@ def extra_measurements(dev, stream, peak, peak_kind, forms, tiles=None):
             by, zc = tiles
         else:
             by, zc = sim.autotune(8)
-        sim.step_loop(20)  # captures the device-side loop graph
-        t = timed(lambda: sim.step_loop(K))
         sites = w["nx"] * w["ny"] * w["nz"] * w["n_real"]
-        rf = _sc_roofline(sim, w, peak, peak_kind)
+        fits_l2 = sites * (152 if w["precision"] == "fp32" else 76) < 2 * L2_BYTES
+        if fits_l2:
+            if flush_w is None:
+                flush_w = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+                flush_r = torch.ones(64 << 20, dtype=torch.float32, device=dev)
+
+            def flush():
+                with torch.cuda.stream(stream):
+                    flush_w.zero_()
+                    flush_r.sum()
+            sim.set_graph(2)
+            for _ in range(3):
+                flush()
+                sim.step(2)
+            t = 0.0
+            for _ in range(K // 2):
+                flush()
+                t += timed(lambda: sim.step(2))
+            launch = "2-step CUDA graphs, L2 flushed before every launch"
+        else:
+            flush = None
+            sim.step_loop(20)  # captures the device-side loop graph
+            t = timed(lambda: sim.step_loop(K))
+            launch = "one CUDA-graph launch per run (device-side loop of two-step bodies)"
+        rf = _sc_roofline(sim, w, peak, peak_kind, flush=flush)
         sim.check()
         out[name] = {"value": sites * K / t / 1e6, "unit": "MLUPS", "ms_per_step": 1e3 * t / K,
                      "steps_per_s": K / t, "realization_steps_per_s": K * w["n_real"] / t, "steps": K,
                      "lattice": [w["nx"], w["ny"], w["nz"]], "n_real": w["n_real"], "beads": int(inp["offsets"][-1]),
-                     "precision": w["precision"], "tiles": [by, zc], "md_shape": list(sim.md_shape()), "md_exchange": sim.md_exchange(),
-                     "md_bonded": sim.md_bonded(), "md_reserve": sim.md_reserve(),
-                     "launch": "one CUDA-graph launch per run (device-side loop of two-step bodies)",
-                     "roofline": rf}
+                     "precision": w["precision"], "tiles": [by, zc], "md_shape": list(sim.md_shape()),
+                     "md_exchange": sim.md_exchange(), "md_bonded": sim.md_bonded(), "md_reserve": sim.md_reserve(),
+                     "launch": launch, "roofline": rf,
+                     "step_frac": rf["algorithmic_bytes_per_launch"] / (t / K) / 1e9 / peak}
         sim.close()
-    if "fp32_matched" in out:
-        base = out["fp32_matched"]["value"]
-        out["speedups_vs_fp32_matched"] = {
-            k: out[k]["value"] / base for k in ("ensemble_fp32", "fp16dev") if k in out}
+    if headline and headline[0] == "lattice_4m_fp32":
+        out["speedups_vs_headline_fp32"] = {
+            k: out[k]["value"] / headline[1] for k in ("ensemble_fp32", "fp16dev") if k in out}
     if "variants" in forms:
         out["variants"] = _variants(dev, lbmd, workloads, tiles)
     if "adjoint" not in forms:
@@ -339,17 +394,19 @@ def extra_measurements(dev, stream, peak, peak_kind, forms, tiles=None):
     return out
 
 
+L2_BYTES = 129 * 1024 * 1024
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="plain_fp32")
+    ap.add_argument("--workload", default="lattice_4m_fp32")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--forms", default="ensemble_fp32,fp16dev,fp32_matched,variants,adjoint",
-                    help="comma list of the other forms to measure (ensemble_fp32, fp16dev, fp32_matched, "
+    ap.add_argument("--forms", default="plain_fp32,ensemble_fp32,fp16dev,variants,adjoint",
+                    help="comma list of the other forms to measure (plain_fp32, ensemble_fp32, fp16dev, "
                          "variants, adjoint), or none")
     ap.add_argument("--tiles", type=int, nargs=2, metavar=("BY", "ZC"), default=None,
                     help="fixed stream-collide tile shape instead of the autotuner (for profiling runs)")
@@ -357,6 +414,8 @@ def main():
                     help="with --tiles: lanes per bead and blocks per chain of the particle kernel")
     ap.add_argument("--md-exchange", choices=["push", "pull"], default=None,
                     help="with --tiles: the particle kernel's chain exchange")
+    ap.add_argument("--md-bonded", choices=["lanes", "warp"], default=None,
+                    help="with --tiles: who evaluates the particle kernel's bonded terms")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -391,13 +450,16 @@ def main():
             sim.set_md_shape(*args.md_shape)
         if args.md_exchange:
             sim.set_md_exchange(args.md_exchange)
+        if args.md_bonded:
+            sim.set_md_bonded(args.md_bonded)
     else:
         sim.autotune(8)
     sites = w["nx"] * w["ny"] * w["nz"] * w["n_real"]
-    flush = not args.no_flush
-    # L2 flush between timed steps: write 256 MiB, then read another 256 MiB so
-    # that the L2 ends up holding clean lines (the written lines' write-backs
-    # happen during the read, not inside the next timed step)
+    bytes_site = 152 if w["precision"] == "fp32" else 76
+    # the populations' two buffers against the L2: a lattice that fits is
+    # launched as 2-step graphs with an L2 flush (write 256 MiB, then read
+    # another 256 MiB, so that the L2 ends up holding clean lines) before each
+    flush = sites * bytes_site < 2 * L2_BYTES
     scratch_w = torch.empty(64 << 20, dtype=torch.float32, device=dev) if flush else None
     scratch_r = torch.ones(64 << 20, dtype=torch.float32, device=dev) if flush else None
 
@@ -412,15 +474,18 @@ def main():
         torch.cuda.synchronize(dev)
 
     # Timed region 1 (the value): K coupled steps launched the library's
-    # production way, as captured 2-step CUDA graphs, the L2 flushed before
-    # every launch (an odd K ends with one kernel-by-kernel step).
-    sim.set_graph(2)
-    for _ in range(args.warmup):
-        if flush:
+    # production way: one step-loop graph launch (or 2-step graphs with an L2
+    # flush before each, for a lattice that fits in L2).
+    if flush:
+        sim.set_graph(2)
+        for _ in range(args.warmup):
             flush_l2()
-        sim.step(2)
+            sim.step(2)
+        units = [2] * (args.steps // 2) + [1] * (args.steps % 2)
+    else:
+        sim.step_loop(args.warmup + (args.warmup & 1))  # captures the loop graph
+        units = [args.steps]
     barrier()
-    units = [2] * (args.steps // 2) + [1] * (args.steps % 2)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in units]
     launches0 = sim.launch_count()
     with ClockSampler(local) as clk:
@@ -429,7 +494,10 @@ def main():
             if flush:
                 flush_l2()
             ev[k][0].record(stream)
-            sim.step(n)
+            if flush:
+                sim.step(n)
+            else:
+                sim.step_loop(n)
             ev[k][1].record(stream)
         barrier()
         launches = sim.launch_count() - launches0
@@ -458,17 +526,20 @@ def main():
     profiled_ms = pdist.max_over_ranks(sum(a.elapsed_time(b) for a, b in ev2), world)
     sim.check()
 
-    # roofline of the stream-collide kernel (the lattice pass)
+    # roofline of the stream-collide kernel (the lattice pass): inside the
+    # step (sharing the GPU with the particle kernel; the timed region) and
+    # alone (the particle kernel waited for)
     peak, peak_kind = _peaks()
     n_sc, ms_sc = ktimes["stream_collide"]
-    bytes_site = 152 if w["precision"] == "fp32" else 76
-    achieved = bytes_site * sites / (ms_sc / n_sc * 1e-3) / 1e9 if n_sc else None
-    traffic = _traffic_record(sites)
-    # the step's own kernels: the particle kernel dominates a single chain's
-    # step; it is latency-bound (100 cluster barriers per LB step) and has no
-    # byte or flop roofline, so the roofline is the lattice kernel's and the
+    alg = bytes_site * sites
+    achieved = alg / (ms_sc / n_sc * 1e-3) / 1e9 if n_sc else None
+    alone = _sc_roofline(sim, w, peak, peak_kind, steps=min(args.steps, 10), flush=flush_l2 if flush else None)
+    traffic = _traffic_record(w["name"], sites) if world == 1 else None
+    # the step's own kernels: the particle kernel sets a single chain's step;
+    # it is latency-bound (100 cluster barriers per LB step) and has no byte
+    # or flop roofline, so the roofline is the lattice kernel's and the
     # dominant kernel is named beside it with its share
-    kern_ms = {k: ktimes[k][1] for k in ("gather", "particles", "stream_collide", "source") if k in ktimes}
+    kern_ms = {k: ktimes[k][1] for k in ("gather", "particles", "stream_collide", "source", "bead_diag") if k in ktimes}
     n_p = ktimes["particles"][0] if "particles" in ktimes else 0
     dominant = None
     if n_p:
@@ -478,63 +549,74 @@ def main():
                     "us_per_md_substep": 1e3 * kern_ms["particles"] / n_p / (w["md_outer"] * w["md_inner"])}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
-                "peak_kind": peak_kind, "kernel": "k_stream_collide",
-                "algorithmic_bytes_per_launch": bytes_site * sites, "dominant_kernel": dominant}
+                "peak_kind": peak_kind, "kernel": "k_stream_collide", "algorithmic_bytes_per_launch": alg,
+                "us_per_launch_in_step": 1e3 * ms_sc / n_sc if n_sc else None,
+                "us_per_launch_alone": alone["us_per_launch_alone"], "frac_alone": alone["frac"],
+                "dominant_kernel": dominant}
+    ms_step = total_ms / args.steps
+    step_roofline = {"bound": "hbm", "bytes_per_step": alg, "achieved": alg / (ms_step * 1e-3) / 1e9,
+                     "peak": peak, "unit": "GB/s", "frac": alg / (ms_step * 1e-3) / 1e9 / peak,
+                     "note": "the lattice pass's algorithmic bytes over the whole coupled step's time"}
     shares = {k: {"launches": n, "ms_total": ms, "ms_per_launch": ms / n if n else None}
               for k, (n, ms) in ktimes.items()}
 
-    # end-to-end through the C ABI from pinned host buffers: upload the state,
-    # K steps each reading back its diagnostics row, download the final state
-    f_host = torch.empty(sim.n_real * 19 * sim.ns, dtype=torch.float32, pin_memory=True).numpy()
-    r_host, v_host = sim.get_beads()
-    f_host[:] = sim.get_populations().reshape(-1)
-    # Host wall clock, summed over the timed intervals: the upload, every step
-    # with its diagnostics read (the read synchronises), the download.  The
-    # L2 flush before each step runs, and is waited for, between intervals.
+    # End to end through the C ABI from pinned host buffers: upload the state
+    # (populations and beads), K steps as one step-loop launch, read back the
+    # K diagnostics rows, download the final state; host wall clock.
+    L = sim._lib
+    nf = sim.n_real * 19 * sim.ns
+    nb3 = 3 * max(sim.total_beads, 1)
+    f_in = torch.empty(nf, dtype=torch.float32, pin_memory=True)
+    f_out = torch.empty(nf, dtype=torch.float32, pin_memory=True)
+    r_in = torch.empty(nb3, dtype=torch.float64, pin_memory=True)
+    v_in = torch.empty(nb3, dtype=torch.float64, pin_memory=True)
+    r_out = torch.empty(nb3, dtype=torch.float64, pin_memory=True)
+    v_out = torch.empty(nb3, dtype=torch.float64, pin_memory=True)
+    f_in.numpy()[:] = sim.get_populations().reshape(-1)
+    r0h, v0h = sim.get_beads()
+    if sim.total_beads:
+        r_in.numpy()[:] = r0h.reshape(-1)
+        v_in.numpy()[:] = v0h.reshape(-1)
+    P = lambda t: ctypes.c_void_p(t.data_ptr())
+    diag = (lbmd.Diag * (sim.n_real * args.steps))()
+    rows = ctypes.c_int32()
+    if flush:
+        flush_l2()
     barrier()
     t0 = time.perf_counter()
-    sim.set_populations(f_host)
-    sim.set_beads(r_host, v_host)
-    torch.cuda.synchronize(dev)
+    ok = [L.lbmd_set_populations(sim._h, P(f_in)), L.lbmd_set_beads(sim._h, P(r_in), P(v_in))]
+    sim.step_loop(args.steps)
+    ok += [L.lbmd_diagnostics(sim._h, diag, args.steps, ctypes.byref(rows)),
+           L.lbmd_get_populations(sim._h, P(f_out)), L.lbmd_get_beads(sim._h, P(r_out), P(v_out))]
     wall = time.perf_counter() - t0
-    for _ in range(args.steps):
-        if flush:
-            flush_l2()
-            torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        sim.step(1)
-        sim.diagnostics(1)
-        wall += time.perf_counter() - t0
-    t0 = time.perf_counter()
-    f_back = sim.get_populations()
-    r_back, _ = sim.get_beads()
-    torch.cuda.synchronize(dev)
-    wall += time.perf_counter() - t0
+    assert all(x == 0 for x in ok) and rows.value == args.steps, (ok, rows.value)
     e2e_s = pdist.max_over_ranks(wall, world)
-    bi = f_host.nbytes + 2 * r_host.nbytes
-    bo = args.steps * sim.n_real * ctypes.sizeof(lbmd.Diag) + f_back.nbytes + 2 * r_back.nbytes
+    bi = f_in.numel() * 4 + 2 * 8 * 3 * sim.total_beads
+    bo = sim.n_real * rows.value * ctypes.sizeof(lbmd.Diag) + f_out.numel() * 4 + 2 * 8 * 3 * sim.total_beads
     e2e = {"value": job_sites * args.steps / e2e_s / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": bi / args.steps, "d2h_bytes_per_step": bo / args.steps,
-           "note": ("state uploaded once and downloaded once per K-step job; each step launched kernel by kernel "
-                    "and its diagnostics row read back; host wall clock, L2 flush between the timed intervals")}
+           "note": ("one K-step job through the C ABI from pinned host buffers: state upload, one step-loop launch, "
+                    "the K diagnostics rows and the final state read back; host wall clock")}
 
     if rank == 0:
         clocks = clk.summary()
         line = {"metric": "coupled LB-MD MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "strong" if "shard" in w else "weak", "vs_baseline": None,
                 "dtype": "f32" if w["precision"] == "fp32" else "f16-storage/f32-math",
                 "data": "synthetic", "config": dict(_config_block(w, flush), tiles=list(sim.tiles()),
                                                      md_shape=list(sim.md_shape()), md_exchange=sim.md_exchange(),
                                                      md_bonded=sim.md_bonded(), md_reserve=sim.md_reserve()),
-                "launch": "captured 2-step CUDA graphs, L2 flushed before every launch",
-                "roofline": roofline, "kernels": shares, "gpu_launches": launches,
+                "launch": ("captured 2-step CUDA graphs, L2 flushed before every launch" if flush else
+                           "one launch of the device-side step-loop graph for the K steps"),
+                "roofline": roofline, "step_roofline": step_roofline, "kernels": shares, "gpu_launches": launches,
                 "kernel_timing": {"pass": "the same K steps kernel by kernel, CUDA events around every kernel",
                                   "ms_per_step": profiled_ms / args.steps},
                 "clocks": clocks, "e2e": e2e}
         forms = [f for f in args.forms.split(",") if f and f != "none"]
         if forms and world == 1:
-            line["forms"] = extra_measurements(dev, stream, peak, peak_kind, forms, args.tiles)
+            line["forms"] = extra_measurements(dev, stream, peak, peak_kind, forms, args.tiles,
+                                               headline=(w["name"], value))
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line), flush=True)

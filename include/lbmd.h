@@ -51,7 +51,8 @@ typedef enum {
     LBMD_ERR_INVALID_ARG = 1, /* bad configuration or argument; nothing was changed */
     LBMD_ERR_CUDA = 2,        /* a CUDA runtime call failed (message in lbmd_last_error) */
     LBMD_ERR_NONFINITE = 3,   /* a NaN/Inf appeared in the fluid or bead state */
-    LBMD_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    LBMD_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up; reserved: no kernel of this
+                                 version waits on a flag, so no call returns it */
     LBMD_ERR_CAPACITY = 5,    /* a fixed-capacity list (neighbours, wall sites) overflowed */
     LBMD_ERR_BUFFER = 6       /* device buffer too small or misaligned */
 } lbmd_status;
@@ -205,8 +206,11 @@ lbmd_status lbmd_init_fluid(lbmd_handle *h, const double *rho, const double *u);
 lbmd_status lbmd_get_populations(lbmd_handle *h, float *f);
 lbmd_status lbmd_set_populations(lbmd_handle *h, const float *f);
 /* The same state as deviations from rest, h = f - w_i (what the library
- * stores), in FP32: accurate where the flow is weak.  Host [n_real][19][ns]. */
+ * stores), in FP32: accurate where the flow is weak.  Host [n_real][19][ns].
+ * lbmd_set_deviations loads such a state (solid sites are ignored); with
+ * FP32 storage it is stored exactly, with FP16 deviations rounded once. */
 lbmd_status lbmd_get_deviations(lbmd_handle *h, float *dev);
+lbmd_status lbmd_set_deviations(lbmd_handle *h, const float *dev);
 
 /* Bead state: r unwrapped positions, v velocities; host [total_beads][3]. */
 lbmd_status lbmd_get_beads(lbmd_handle *h, double *r, double *v);
@@ -364,6 +368,30 @@ lbmd_status lbmd_adjoint_required_bytes(const lbmd_handle *h, int32_t K, int32_t
 lbmd_status lbmd_adjoint(lbmd_handle *h, int32_t K, int32_t checkpoint_every, void *scratch,
                          size_t scratch_bytes, double *loss, double *dgamma, double *dE, double *dr0);
 
+/* ---- the random numbers of the noise ------------------------------------
+ * The bead noise of Sec. II, Eq. 15 (and the fluctuating fluid of Eq. 4's
+ * F_i term) draws from the counter-based generator Philox4x32-10 of Salmon,
+ * Moraes, Dror and Shaw (SC'11).  These two calls expose the device
+ * generator and the bead-noise mapping that the step kernels use, so that
+ * both can be checked against an independent implementation.  Neither is
+ * needed to run a simulation.
+ *
+ * lbmd_philox4x32_10: n independent draws.  ctr_key: device array [n][6] of
+ * uint32 (ctr0, ctr1, ctr2, ctr3, key0, key1); out: device array [n][4] of
+ * uint32, the four output words.  Asynchronous on `stream`.  n >= 0 and
+ * non-null pointers when n > 0, else LBMD_ERR_INVALID_ARG.
+ *
+ * lbmd_noise_gauss3: the three standard normals the particle kernel draws for
+ * beads bead0 .. bead0 + n - 1 of realization `realization` at LB step
+ * `step` and counter word 2 = `substep` (the outer MD step, or the inner step
+ * of the stochastic position Verlet cycle): key = (seed_lo, seed_hi ^
+ * realization), counter = (bead, step_lo, substep, step_hi), u = (top 24 bits
+ * + 1/2) 2^-24, Box-Muller in FP32.  out: device array [n][3] float.
+ * Asynchronous on `stream`. */
+lbmd_status lbmd_philox4x32_10(const uint32_t *ctr_key, uint32_t *out, int64_t n, void *stream);
+lbmd_status lbmd_noise_gauss3(uint64_t seed, uint32_t realization, uint32_t bead0, int64_t n, int64_t step,
+                              uint32_t substep, float *out, void *stream);
+
 /* Allocation-free fluid sums.  The paper has no counterpart: this is a
  * utility for callers that cannot allocate device memory where they call it,
  * such as a monitoring loop beside a running simulation on a GPU whose memory
@@ -378,14 +406,20 @@ lbmd_status lbmd_adjoint(lbmd_handle *h, int32_t K, int32_t checkpoint_every, vo
  * solid: device [nz][ny][nx] bytes (1 = solid, skipped) or NULL (all fluid).
  * Asynchronous on `stream` (cudaStream_t as void*).
  *
- * It allocates nothing: its per-block partial sums live in one file-scope
- * device array of about 160 KB that every GPU loading the library holds
- * until the process exits.  Lattices above LBMD_STATIC_SUMS_MAX_SITES sites
- * return LBMD_ERR_CAPACITY.  The first call on each device looks up that
- * array's device address (with the device current), so make the first call
- * before any stream capture.  Every call shares the array, and it keeps the
- * last call's contents: calls whose kernels overlap on the GPU race and give
- * wrong sums; order them on one stream. */
+ * It allocates nothing after its first call on a device: its per-block
+ * partial sums live in one file-scope device array of about 160 KB.  CUDA
+ * loads the array's module lazily (the default module loading), so the FIRST
+ * call on each device loads it, which allocates the array and may
+ * synchronise; the array then stays allocated until the process exits or the
+ * context is reset.  A caller that cannot allocate later makes one call
+ * early, before it hands the GPU's memory to a pool or starts a stream
+ * capture.  Every call looks the array's device address up again with the
+ * device current, so a call after cudaDeviceReset finds the new context's
+ * array (reloading the module, which allocates again).  Lattices above
+ * LBMD_STATIC_SUMS_MAX_SITES sites return LBMD_ERR_CAPACITY.  Every call
+ * shares the array, and it keeps the last call's contents: calls whose
+ * kernels overlap on the GPU race and give wrong sums; order them on one
+ * stream. */
 #define LBMD_STATIC_SUMS_MAX_SITES 8388608
 lbmd_status lbmd_population_sums_static(const float *dev, const uint8_t *solid, int32_t nx, int32_t ny,
                                         int32_t nz, double *out, void *stream);

@@ -411,10 +411,11 @@ MdShape md_shape(const Sim &S) {
     m.bw = S.md_bw == 2 || (S.md_bw == 0 && m.Nc + 2 <= 32);
     m.threads = max(32, ((m.Nc * m.T + 31) / 32) * 32) + (m.bw ? 32 * bonded_warps(m.Nc) : 0);
     m.smem = psmem_layout(max(N, 1), m.Nc, spv_noise_slots(S, m.Nc), nullptr, nullptr);
-    // Reserving: a block launched with 226 KB of shared memory leaves its SM
-    // too little for any block of the other kernels, so the lattice pass and
-    // the gather do not share the particle kernel's SMs.
-    m.launch_smem = S.md_reserve ? max(m.smem, (size_t)226 * 1024) : m.smem;
+    // Reserving: a block launched with the device's whole opt-in shared
+    // memory leaves its SM too little for any block of the other kernels, so
+    // the lattice pass and the gather do not share the particle kernel's SMs.
+    // The launch trims this by the kernel's static shared memory.
+    m.launch_smem = S.md_reserve ? max(m.smem, (size_t)max(S.smem_optin, 0)) : m.smem;
     return m;
 }
 
@@ -1170,7 +1171,14 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
 template <int T>
 static cudaError_t launch_particles_t(const Sim &S, const MdShape &m, cudaStream_t st, int *n_fit) {
     auto kern = m.bw ? k_particles<T, true> : k_particles<T, false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m.launch_smem);
+    size_t dyn = m.launch_smem;
+    if (dyn > m.smem) {  // reserving: the opt-in maximum counts static and dynamic shared memory together
+        cudaFuncAttributes fa;
+        cudaError_t ea = cudaFuncGetAttributes(&fa, kern);
+        if (ea != cudaSuccess) return ea;
+        dyn = dyn > fa.sharedSizeBytes ? max(m.smem, dyn - fa.sharedSizeBytes) : m.smem;
+    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
     if (m.C > 8) {  // clusters above the portable size of 8 are opt-in
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -1179,7 +1187,7 @@ static cudaError_t launch_particles_t(const Sim &S, const MdShape &m, cudaStream
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(S.md_clusters * m.C);
     cfg.blockDim = dim3(m.threads);
-    cfg.dynamicSmemBytes = m.launch_smem;
+    cfg.dynamicSmemBytes = dyn;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;

@@ -321,6 +321,30 @@ __global__ void k_loop_tick(cudaGraphConditionalHandle hdl, unsigned int *remain
 
 __global__ void k_set_u32(unsigned int *p, unsigned int v) { *p = v; }
 
+// n Philox4x32-10 draws: in [n][6] = (ctr0..ctr3, key0, key1), out [n][4]
+__global__ void k_philox_words(const uint32_t *in, uint32_t *out, long long n) {
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const uint32_t *a = in + 6 * k;
+    const uint4 x = philox4x32_10(make_uint4(a[0], a[1], a[2], a[3]), make_uint2(a[4], a[5]));
+    out[4 * k + 0] = x.x;
+    out[4 * k + 1] = x.y;
+    out[4 * k + 2] = x.z;
+    out[4 * k + 3] = x.w;
+}
+
+// the bead-noise normals of beads bead0 .. bead0 + n - 1 (the particle
+// kernel's own draw)
+__global__ void k_noise_gauss3(unsigned long long seed, uint32_t real, uint32_t bead0, long long n, long long step,
+                               uint32_t substep, float *out) {
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float3 z = gauss3(seed, real, bead0 + (uint32_t)k, step, substep);
+    out[3 * k + 0] = z.x;
+    out[3 * k + 1] = z.y;
+    out[3 * k + 2] = z.z;
+}
+
 // restart every realization's translocation record at step origin
 __global__ void k_reset_transloc(lbmd_transloc *tl, int n_real, long long origin) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -502,6 +526,24 @@ const char *lbmd_status_string(lbmd_status s) {
 
 const char *lbmd_last_error(const lbmd_handle *h) { return h ? h->err.c_str() : "null handle"; }
 
+lbmd_status lbmd_philox4x32_10(const uint32_t *ctr_key, uint32_t *out, int64_t n, void *stream) {
+    if (n < 0 || (n > 0 && (!ctr_key || !out))) return LBMD_ERR_INVALID_ARG;
+    if (n == 0) return LBMD_OK;
+    const int threads = 256;
+    k_philox_words<<<(unsigned)((n + threads - 1) / threads), threads, 0, (cudaStream_t)stream>>>(ctr_key, out, n);
+    return cudaGetLastError() == cudaSuccess ? LBMD_OK : LBMD_ERR_CUDA;
+}
+
+lbmd_status lbmd_noise_gauss3(uint64_t seed, uint32_t realization, uint32_t bead0, int64_t n, int64_t step,
+                              uint32_t substep, float *out, void *stream) {
+    if (n < 0 || (n > 0 && !out) || (double)bead0 + (double)n > 4294967296.0) return LBMD_ERR_INVALID_ARG;
+    if (n == 0) return LBMD_OK;
+    const int threads = 256;
+    k_noise_gauss3<<<(unsigned)((n + threads - 1) / threads), threads, 0, (cudaStream_t)stream>>>(
+        (unsigned long long)seed, realization, bead0, n, step, substep, out);
+    return cudaGetLastError() == cudaSuccess ? LBMD_OK : LBMD_ERR_CUDA;
+}
+
 lbmd_status lbmd_required_bytes(const lbmd_config *cfg, const int32_t *bead_offsets, size_t *bytes) {
     std::string why;
     if (!bytes || !config_ok(cfg, bead_offsets, why)) return LBMD_ERR_INVALID_ARG;
@@ -648,6 +690,12 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
     S.tl = (lbmd_transloc *)(b + L.tl);
     S.ctrl = (Ctrl *)(b + L.ctrl);
     S.phase = nullptr;
+    {
+        int dev = 0, optin = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess)
+            S.smem_optin = optin;
+    }
 
 #define CKI(call)                                                           \
     do {                                                                    \
@@ -840,15 +888,19 @@ lbmd_status lbmd_get_populations(lbmd_handle *h, float *f) { return pull_out(h, 
 
 lbmd_status lbmd_get_deviations(lbmd_handle *h, float *dev) { return pull_out(h, dev, true); }
 
-lbmd_status lbmd_set_populations(lbmd_handle *h, const float *f) {
+static lbmd_status push_in(lbmd_handle *h, const float *f, bool dev) {
     if (!h || !f) return LBMD_ERR_INVALID_ARG;
     CK(cudaMemcpyAsync(h->staging, f, (size_t)h->cfg.n_real * LBMD_Q * h->S.ns * sizeof(float),
                        cudaMemcpyHostToDevice, h->st));
-    CK(launch_push_from_staging(h->S, h->staging, h->popA, false, h->st));
+    CK(launch_push_from_staging(h->S, h->staging, h->popA, dev, h->st));
     h->launches += 1;
     CK(cudaStreamSynchronize(h->st));
     return LBMD_OK;
 }
+
+lbmd_status lbmd_set_populations(lbmd_handle *h, const float *f) { return push_in(h, f, false); }
+
+lbmd_status lbmd_set_deviations(lbmd_handle *h, const float *dev) { return push_in(h, dev, true); }
 
 lbmd_status lbmd_get_beads(lbmd_handle *h, double *r, double *v) {
     if (!h) return LBMD_ERR_INVALID_ARG;
@@ -1287,6 +1339,38 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
     CK(cudaMemcpyAsync(snap, h->S.r_hi, bb16, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(snap + bb16, h->S.r_lo, bb16, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(snap + 2 * bb16, h->S.v, bb16, cudaMemcpyDeviceToDevice, h->st));
+    // Time reps pseudo-steps of one candidate shape (a warm-up pass, then the
+    // timed one) into ms.
+    auto time_candidate = [&](Sim &trial, float &ms) -> cudaError_t {
+        if (upload_md_map(h, trial, 1) != LBMD_OK) return cudaErrorUnknown;
+        cudaError_t e = cudaSuccess;
+        if (md_shape(trial).C > 8) {  // a non-portable cluster size: only where the device can place one
+            int fit = 0;
+            e = particles_clusters_fit(trial, &fit);
+            if (e != cudaSuccess) return e;
+            if (fit < 1) return cudaErrorInvalidConfiguration;
+        }
+#define CKT(call) do { e = (call); if (e != cudaSuccess) return e; } while (0)
+        for (int pass = 0; pass < 2; ++pass) {
+            CKT(cudaEventRecord(a, h->st));
+            for (int k = 0; k < reps; ++k) {
+                CKT(launch_gather(trial, h->popA, h->st));
+                CKT(cudaEventRecord(h->ev_fork, h->st));
+                CKT(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+                CKT(launch_particles(trial, h->popA, h->aux));
+                CKT(cudaEventRecord(h->ev_join, h->aux));
+                if (!h->overlap) CKT(cudaStreamWaitEvent(h->st, h->ev_join, 0));
+                CKT(launch_stream_collide(trial, h->popA, h->popB, h->by, h->zc, false, h->st));
+                CKT(cudaStreamWaitEvent(h->st, h->ev_join, 0));
+            }
+            CKT(cudaEventRecord(b, h->st));
+            CKT(cudaEventSynchronize(b));
+            CKT(cudaEventElapsedTime(&ms, a, b));
+            h->launches += 3LL * reps;
+        }
+#undef CKT
+        return cudaSuccess;
+    };
     static const int TS[] = {2, 4, 8};
     static const int CS[] = {1, 2, 4, 8, 16};
     float best_md = 1e30f;
@@ -1311,30 +1395,12 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
             const MdShape m = md_shape(trial);
             if (m.threads > 512 || m.C != C || m.smem > 200 * 1024) continue;
             if (C > 1 && C > (h->S.max_beads + 15) / 16) continue;  // blocks of a few beads: barrier-bound
-            lbmd_status us = upload_md_map(h, trial, 1);
-            if (us != LBMD_OK) return us;
-            if (C > 8) {  // a non-portable cluster size: only where the device can place one
-                int fit = 0;
-                CK(particles_clusters_fit(trial, &fit));
-                if (fit < 1) continue;
-            }
+            // a candidate the device cannot set up or launch is skipped; the
+            // bead state is restored below whatever happened here
             float ms = 0.f;
-            for (int pass = 0; pass < 2; ++pass) {  // warm-up pass, then the timed one
-                CK(cudaEventRecord(a, h->st));
-                for (int k = 0; k < reps; ++k) {
-                    CK(launch_gather(trial, h->popA, h->st));
-                    CK(cudaEventRecord(h->ev_fork, h->st));
-                    CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
-                    CK(launch_particles(trial, h->popA, h->aux));
-                    CK(cudaEventRecord(h->ev_join, h->aux));
-                    if (!h->overlap) CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
-                    CK(launch_stream_collide(trial, h->popA, h->popB, h->by, h->zc, false, h->st));
-                    CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
-                }
-                CK(cudaEventRecord(b, h->st));
-                CK(cudaEventSynchronize(b));
-                CK(cudaEventElapsedTime(&ms, a, b));
-                h->launches += 3LL * reps;
+            if (time_candidate(trial, ms) != cudaSuccess) {
+                cudaGetLastError();  // clear a launch-configuration error
+                continue;
             }
             // reserving SMs takes them from the lattice pass: it must win by 1%
             if (R) ms *= 1.01f;

@@ -170,6 +170,7 @@ struct Sim {
     int md_pull;             // chain exchange between a cluster's blocks: 0 push, 1 pull (halo)
     int md_bw;               // bonded terms: 0 automatic, 1 by every bead's lanes, 2 by a block's last warp
     int md_reserve;          // 1: the particle kernel's blocks claim their SMs' whole shared memory
+    int smem_optin;          // the device's opt-in shared memory per block (bytes)
     // placement of the chains in the particle kernel's clusters: per block
     // (realization or -1, rank within its chain, the chain's blocks, the
     // chain's first rank in the cluster); md_clusters clusters of the shape's C
@@ -418,7 +419,8 @@ struct MdShape {
     int T, C, Nc, threads;
     bool bw;  // bonded terms by a block's last warp
     size_t smem;         // shared memory the kernel uses
-    size_t launch_smem;  // shared memory a block is launched with (smem, or the SM's whole when reserving)
+    size_t launch_smem;  // shared memory a block is launched with (smem, or the opt-in maximum when reserving,
+                         // less the kernel's static shared memory, which the launch adds)
 };
 MdShape md_shape(const Sim &S);
 cudaError_t launch_gather(const Sim &S, const void *A, cudaStream_t st);

@@ -9,12 +9,17 @@
 // synchronises the whole device.  Such a caller passes its populations and
 // an output buffer it already owns; this file supplies the scratch.
 //
-// The array below is allocated once per GPU when the library is loaded on it
-// and stays allocated until the process exits.  Every call shares it, and it
-// keeps the last call's contents, so two calls whose kernels overlap on the
-// GPU (different streams, no ordering between them) race on it.
-#include <mutex>
-
+// The array below belongs to this file's own CUDA module.  Under lazy module
+// loading (the CUDA default) a module is loaded, and its device arrays are
+// allocated, the first time the process uses it on a device: the first call
+// of lbmd_population_sums_static on that device.  That first call therefore
+// does allocate (and may synchronise); every later call on the device does
+// not.  A caller that cannot allocate later makes one call early, before
+// handing the GPU's memory to a pool or starting a stream capture.  The
+// array then stays allocated until the process exits (or the context is
+// reset).  Every call shares it, and it keeps the last call's contents, so
+// two calls whose kernels overlap on the GPU (different streams, no ordering
+// between them) race on it.
 #include "lbmd_internal.cuh"
 
 namespace {
@@ -30,10 +35,6 @@ static_assert(LBMD_STATIC_SUMS_MAX_SITES % SITES_PER_BLOCK == 0, "whole blocks")
 
 // the scratch: block partials, then one counter of finished blocks
 static __device__ __align__(256) unsigned char g_sums_scratch[SCRATCH_BYTES];
-
-// device address of g_sums_scratch per GPU, looked up once per device
-std::mutex g_mu;
-void *g_scratch_addr[64] = {nullptr};
 
 __global__ void __launch_bounds__(SUM_THREADS) k_population_sums(const float *__restrict__ dev,
                                                                  const uint8_t *__restrict__ solid,
@@ -100,21 +101,14 @@ extern "C" lbmd_status lbmd_population_sums_static(const float *dev, const uint8
     const double nsd = (double)nx * ny * nz;
     if (nsd > (double)LBMD_STATIC_SUMS_MAX_SITES) return LBMD_ERR_CAPACITY;
     const int ns = nx * ny * nz;
-    int gpu = 0;
-    if (cudaGetDevice(&gpu) != cudaSuccess || gpu < 0 || gpu >= 64) return LBMD_ERR_CUDA;
-    void *scratch = nullptr;
-    {
-        // first call on this device: look up the array's device address with
-        // the device current (a host-side reference to the symbol is not it)
-        std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_scratch_addr[gpu]) {
-            void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_sums_scratch) != cudaSuccess || !p) return LBMD_ERR_CUDA;
-            g_scratch_addr[gpu] = p;
-        }
-        scratch = g_scratch_addr[gpu];
-    }
     cudaStream_t st = (cudaStream_t)stream;
+    // The array's device address on the current device (a host-side reference
+    // to the symbol is not it), looked up on every call: nothing is cached, so
+    // a call after cudaDeviceReset (which unloads the module and frees the
+    // array) finds the array of the new context.  Once the module is loaded
+    // the lookup allocates nothing.
+    void *scratch = nullptr;
+    if (cudaGetSymbolAddress(&scratch, g_sums_scratch) != cudaSuccess || !scratch) return LBMD_ERR_CUDA;
     // the finished-blocks counter must start at zero; the partials are all
     // overwritten by this call
     if (cudaMemsetAsync((unsigned char *)scratch + PARTIAL_BYTES, 0, sizeof(unsigned int), st) != cudaSuccess)

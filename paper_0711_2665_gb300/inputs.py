@@ -131,3 +131,22 @@ def shear_wave_velocity(nx: int, ny: int, nz: int, amplitude: float) -> np.ndarr
     x = np.arange(nx)
     u[1] = amplitude * np.sin(2.0 * np.pi * x / nx)[None, None, :]
     return u
+
+
+def smooth_random_velocity(nx: int, ny: int, nz: int, amplitude: float, seed: int, modes: int = 3) -> np.ndarray:
+    """A seeded smooth periodic flow: a sum of ``modes`` plane waves per
+    component with random integer wave vectors (|k_a| <= 2 per axis), phases
+    and weights, scaled so that the largest |u_a| is ``amplitude``; shape
+    (3, nz, ny, nx).  Every site moves, so every population deviates."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    u = np.zeros((3, nz, ny, nx))
+    for a in range(3):
+        for _ in range(modes):
+            k = rng.integers(-2, 3, size=3)
+            if not k.any():
+                k[0] = 1
+            ph = 2.0 * np.pi * (k[0] * x / nx + k[1] * y / ny + k[2] * z / nz) + rng.uniform(0, 2 * np.pi)
+            u[a] += rng.uniform(0.5, 1.0) * np.sin(ph)
+        u[a] *= amplitude / max(np.abs(u[a]).max(), 1e-300)
+    return u

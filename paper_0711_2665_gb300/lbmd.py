@@ -105,6 +105,7 @@ def lib():
         "lbmd_get_populations": [vp, vp],
         "lbmd_get_deviations": [vp, vp],
         "lbmd_set_populations": [vp, vp],
+        "lbmd_set_deviations": [vp, vp],
         "lbmd_get_beads": [vp, vp, vp],
         "lbmd_set_beads": [vp, vp, vp],
         "lbmd_get_coupling": [vp, vp, vp],
@@ -131,6 +132,8 @@ def lib():
         "lbmd_step_loop": [vp, i64],
         "lbmd_adjoint_required_bytes": [vp, i32, i32, P(sz)],
         "lbmd_adjoint": [vp, i32, i32, vp, sz, vp, vp, vp, vp],
+        "lbmd_philox4x32_10": [vp, vp, i64, vp],
+        "lbmd_noise_gauss3": [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, i64, i64, ctypes.c_uint32, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -144,6 +147,36 @@ def lib():
     L.lbmd_destroy.restype = None
     _lib = L
     return L
+
+
+def philox4x32_10(ctr_key, device: str = "cuda:0") -> np.ndarray:
+    """Philox4x32-10 on the GPU (the generator of the noise): ctr_key is an
+    (n, 6) array of uint32 (ctr0..ctr3, key0, key1); returns (n, 4) uint32."""
+    import torch
+    a = np.ascontiguousarray(ctr_key, dtype=np.uint32).reshape(-1, 6)
+    src = torch.from_numpy(a.view(np.int32).copy()).to(device)
+    out = torch.empty((a.shape[0], 4), dtype=torch.int32, device=device)
+    st = torch.cuda.current_stream(device)
+    s = lib().lbmd_philox4x32_10(ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(out.data_ptr()), a.shape[0],
+                                 ctypes.c_void_p(st.cuda_stream))
+    if s != 0:
+        raise LbmdError(s, "lbmd_philox4x32_10")
+    st.synchronize()
+    return out.cpu().numpy().view(np.uint32)
+
+
+def noise_gauss3(seed: int, realization: int, bead0: int, n: int, step: int, substep: int,
+                 device: str = "cuda:0") -> np.ndarray:
+    """The bead-noise normals the particle kernel draws, (n, 3) float32."""
+    import torch
+    out = torch.empty((n, 3), dtype=torch.float32, device=device)
+    st = torch.cuda.current_stream(device)
+    s = lib().lbmd_noise_gauss3(seed, realization, bead0, n, step, substep, ctypes.c_void_p(out.data_ptr()),
+                                ctypes.c_void_p(st.cuda_stream))
+    if s != 0:
+        raise LbmdError(s, "lbmd_noise_gauss3")
+    st.synchronize()
+    return out.cpu().numpy()
 
 
 def make_config(w: dict) -> Config:
@@ -330,6 +363,13 @@ class Simulation:
         f = np.empty(self.n_real * LBMD_Q * self.ns, dtype=np.float32)
         self._check(self._lib.lbmd_get_deviations(self._h, _ptr(f)), "lbmd_get_deviations")
         return f.reshape(self.n_real, LBMD_Q, self.cfg.nz, self.cfg.ny, self.cfg.nx)
+
+    def set_deviations(self, h):
+        """Load f - w_i (FP32), shape (n_real, 19, nz, ny, nx)."""
+        a = np.ascontiguousarray(h, dtype=np.float32).reshape(-1)
+        if a.size != self.n_real * LBMD_Q * self.ns:
+            raise ValueError("deviations must have n_real*19*nsites entries")
+        self._check(self._lib.lbmd_set_deviations(self._h, _ptr(a)), "lbmd_set_deviations")
 
     def set_populations(self, f):
         a = np.ascontiguousarray(f, dtype=np.float32).reshape(-1)

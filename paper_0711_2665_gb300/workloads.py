@@ -1,4 +1,4 @@
-"""The five named workloads of the coupled LB-MD step, and how to build them.
+"""The six named workloads of the coupled LB-MD step, and how to build them.
 
 Each workload is a plain dict of parameters (lattice units) plus a recipe for
 its seeded inputs; it carries no arithmetic of the method.  Parameters the
@@ -16,6 +16,9 @@ WCA with the bead-bead sigma and eps; M = 5 and M^b = 20 (Sec. II).
                      N ~ U{20..200}, E=0.05, gamma 0.1, kT=1e-4, 5000 steps
   fp16dev            256x128x128, wall x=128, 3x3 pore, N=1000, E=0.1,
                      gamma 0.2, kT=1e-4, populations as FP16 deviations
+  lattice_4m_fp32    the same 256x128x128 lattice (4.19M sites) and chain
+                     with FP32 storage: the plain step on the largest
+                     single-lattice configuration
   adjoint            96x48x48, wall x=48, 4x4 pore, N=100, E=0.1,
                      gamma 0.1, kT=1e-4, K=200, checkpoints every 20
 """
@@ -42,6 +45,9 @@ WORKLOADS = {
     "fp16dev": dict(COMMON, nx=256, ny=128, nz=128, n_real=1, tau=0.8, wall_x=128, pore_h=3,
                     n_beads=1000, E=0.1, gamma=0.2, kT=1e-4, seed=3, chain_seed=3,
                     steps=20000, precision="fp16dev"),
+    "lattice_4m_fp32": dict(COMMON, nx=256, ny=128, nz=128, n_real=1, tau=0.8, wall_x=128, pore_h=3,
+                            n_beads=1000, E=0.1, gamma=0.2, kT=1e-4, seed=3, chain_seed=3,
+                            steps=20000, precision="fp32"),
     "adjoint": dict(COMMON, nx=96, ny=48, nz=48, n_real=1, tau=0.8, wall_x=48, pore_h=4,
                     n_beads=100, E=0.1, gamma=0.1, kT=1e-4, seed=4, chain_seed=4,
                     steps=200, checkpoint_every=20, precision="fp32"),

@@ -38,13 +38,47 @@ def _shear_rate(sim, nx, n1=60, n2=400):
     return (a2 / a1) ** (1.0 / n2), a1
 
 
-@pytest.mark.parametrize("precision,tol", [("fp32", 2e-5), ("fp16dev", 1e-2)])
-def test_shear_wave_decay(precision, tol):
-    """u_y = 1e-3 sin(2 pi x / 32): decay per step against the oracle's FP64
-    run (itself pinned to the linearised-LBGK eigenvalue).  The bound for the
-    FP16-deviation mode is the stated reduced-precision error: fp16 keeps 11
-    bits of each deviation, and the rounding noise of ~260 steps (one decay
-    time) moves the measured rate by a few 1e-3 relative (measured 0.4%)."""
+class _OracleRun:
+    """The oracle's FP64 run seen through get_deviations; with fp16 set, each
+    step's deviations are stored as FP16 (h 2^12 rounded to the nearest FP16
+    value by numpy's IEEE conversion), as the FP16 storage mode does."""
+
+    def __init__(self, orc, fp16=False):
+        self.orc, self.fp16 = orc, fp16
+        _, self.w, _ = oracle.tables()
+
+    def _h(self):
+        return self.orc.get_populations() - self.w[:, None, None, None]
+
+    def _round(self):
+        h = (self._h() * 4096.0).astype(np.float16).astype(np.float64) / 4096.0
+        self.orc.set_populations(self.w[:, None, None, None] + h)
+
+    def step(self, n):
+        for _ in range(n):
+            self.orc.step(1)
+            if self.fp16:
+                self._round()
+
+    def get_deviations(self):
+        return self._h()[None]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16dev"])
+def test_shear_wave_decay(precision):
+    """u_y = 1e-3 sin(2 pi x / 32): decay factor per step r against the
+    oracle's FP64 run (itself pinned to the linearised-LBGK eigenvalue).
+
+    FP32: |r_gpu - r_orc| <= 2e-5 (1 - r_orc).
+    FP16 deviations: against an oracle run that stores its deviations as FP16
+    each step (the same storage rule in FP64 arithmetic), |dr| <= 2e-4 (1 - r)
+    (a few storage roundings flip where the FP32 and FP64 values straddle an
+    FP16 midpoint).  Against the plain FP64 run the worst case is derived:
+    storage moves each stored deviation by at most 2^-11 |h|, and for a shear
+    wave h_i = 3 w_i c_iy u_y, so the wave's projected amplitude moves by at
+    most 2^-11 of itself per step (sum_i 3 w_i c_iy^2 = 1), and so does r:
+    |r_fp16 - r_fp64| <= 2^-11 (13% of this wave's 1 - r = 3.85e-3); the
+    measured error is reported in the design notes."""
     nx, tau = 32, 0.8
     sim = _fluid_only(nx, 4, 4, tau, precision=precision)
     u0 = inputs.shear_wave_velocity(nx, 4, 4, 1e-3)
@@ -52,15 +86,17 @@ def test_shear_wave_decay(precision, tol):
     rate_g, _ = _shear_rate(sim, nx)
     orc = oracle.OracleSim(dict(nx=nx, ny=4, nz=4, tau=tau))
     orc.init_fluid(None, u0)
-
-    _, wts, _ = oracle.tables()
-
-    class _O:
-        def step(self, n): orc.step(n)
-        def get_deviations(self): return (orc.get_populations() - wts[:, None, None, None])[None]
-
-    rate_o, _ = _shear_rate(_O(), nx)
-    assert abs(rate_g - rate_o) <= tol * (1 - rate_o), (rate_g, rate_o)
+    rate_o, _ = _shear_rate(_OracleRun(orc), nx)
+    if precision == "fp32":
+        assert abs(rate_g - rate_o) <= 2e-5 * (1 - rate_o), (rate_g, rate_o)
+        return
+    assert abs(rate_g - rate_o) <= 2.0 ** -11, (rate_g, rate_o)
+    orc16 = oracle.OracleSim(dict(nx=nx, ny=4, nz=4, tau=tau))
+    orc16.init_fluid(None, u0)
+    run16 = _OracleRun(orc16, fp16=True)
+    run16._round()  # the initial state as FP16 storage holds it
+    rate_16, _ = _shear_rate(run16, nx)
+    assert abs(rate_g - rate_16) <= 2e-4 * (1 - rate_16), (rate_g, rate_16, rate_o)
 
 
 def test_poiseuille_curvature_fp32():
@@ -98,23 +134,24 @@ def test_momentum_and_mass_conserved_gpu():
 
 
 def test_fp16dev_one_step_error_is_bounded():
-    """FP16 deviation storage: one step from the same FP16-representable state
-    differs from the FP64 oracle by at most the storage rounding
-    (half an fp16 ulp of the largest deviation, 2^-12 relative) plus FP32."""
-    from gpu_helpers import to_f32_state, load_state
+    """FP16 deviation storage: one step from the same FP16-representable
+    state (a developed flow under the chain) differs from the FP64 oracle, at
+    every element, by at most the storage rounding of that element (half an
+    FP16 ulp, 2^-11 |h|, or 2^-37 below the FP16 normal range) plus the FP32
+    bound of the parity tests."""
+    from gpu_helpers import (assert_dev_close, deviations, dev_tolerance, load_dev_state, near_bead_sites)
     w = small_workload(precision="fp16dev")
     sim, orc, inp = make_pair(w)
+    orc.init_fluid(None, inputs.smooth_random_velocity(w["nx"], w["ny"], w["nz"], 1e-2, 5))
     orc.step(20)
-    f32, r, v = to_f32_state(orc)
-    _, wts, _ = oracle.tables()
-    fluid = (inp["solid"] == 0)
-    dev = (f32 - wts[:, None, None, None].astype(np.float32)) * 4096.0
-    f16 = (dev.astype(np.float16).astype(np.float32) / 4096.0 + wts[:, None, None, None].astype(np.float32))
-    f16[:, ~fluid] = 0
-    load_state(sim, orc, f16.astype(np.float32), r, v, 20)
+    h = deviations(orc, inp["solid"])
+    h16 = ((h * 4096.0).astype(np.float16).astype(np.float32) / np.float32(4096.0)).astype(np.float32)
+    r, v = orc.get_beads()
+    load_dev_state(sim, orc, h16, r.copy(), v.astype(np.float32).astype(np.float64), 20, inp["solid"])
     sim.step(1)
     orc.step(1)
-    fo = orc.get_populations()
-    fg = sim.get_populations()[0]
-    devmax = np.abs(fo - wts[:, None, None, None])[:, fluid].max()
-    assert np.abs(fg - fo)[:, fluid].max() <= 2.0 ** -11 * devmax + 1e-6
+    h_o = deviations(orc, inp["solid"])
+    J_max = float(np.abs(orc.last_coupling()[1]).max())
+    near = near_bead_sites(r, (w["nx"], w["ny"], w["nz"]))
+    assert_dev_close(sim.get_deviations()[0], h_o, dev_tolerance(h_o, near, J_max, fp16=True),
+                     inp["solid"] == 0, "fp16")

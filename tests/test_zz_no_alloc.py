@@ -52,6 +52,22 @@ def test_static_sums_match_observables_on_two_calls():
             assert got[1 + a] == pytest.approx(obs[f"p_fluid_{k}"], rel=1e-5, abs=1e-8), (call, k)
 
 
+def test_static_sums_under_lazy_module_loading():
+    """The same two-call check in a fresh process with lazy module loading
+    asked for explicitly: the first call loads the array's module on the
+    device, the second reuses it."""
+    import os
+    import subprocess
+    import sys
+    here = os.path.dirname(os.path.abspath(__file__))
+    code = ("import sys; sys.path.insert(0, %r); sys.path.insert(0, %r); "
+            "import test_zz_no_alloc as t; t.test_static_sums_match_observables_on_two_calls(); print('ok')"
+            % (here, os.path.dirname(here)))
+    env = dict(os.environ, CUDA_MODULE_LOADING="LAZY")
+    p = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0 and p.stdout.strip().endswith("ok"), p.stderr[-2000:]
+
+
 def test_static_sums_reject_oversized_lattice():
     from paper_0711_2665_gb300 import lbmd
     lib = lbmd.lib()
