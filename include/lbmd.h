@@ -96,6 +96,10 @@ typedef struct lbmd_config {
                                 non-conserved mode of an orthogonal D3Q19 basis gets Philox noise of
                                 variance 3 rho lb_kT b_k (1 - (1 - omega)^2) per site and step; 0 = off.
                                 lbmd_adjoint needs 0 */
+    int32_t slab_x0, slab_nx; /* slab mode (Sec. III domain decomposition, in x only): this handle
+                                holds the planes [slab_x0, slab_x0 + slab_nx) of the nx x ny x nz
+                                lattice, plus ghost planes; see lbmd_slab_gather.  slab_nx = 0: the
+                                whole lattice (the default) */
 } lbmd_config;
 
 /* Observables of one realization at the current state (Sec. III global
@@ -391,6 +395,53 @@ lbmd_status lbmd_adjoint(lbmd_handle *h, int32_t K, int32_t checkpoint_every, vo
 lbmd_status lbmd_philox4x32_10(const uint32_t *ctr_key, uint32_t *out, int64_t n, void *stream);
 lbmd_status lbmd_noise_gauss3(uint64_t seed, uint32_t realization, uint32_t bead0, int64_t n, int64_t step,
                               uint32_t substep, float *out, void *stream);
+
+/* ---- one lattice over several handles: x-slabs --------------------------
+ * Sec. III splits the lattice over tasks and exchanges halos for streaming.
+ * Here a handle created with slab_nx > 0 holds the x-slab [slab_x0,
+ * slab_x0 + slab_nx) of the nx x ny x nz lattice (periodic), every slab at
+ * least 2 planes wide, n_real = 1, lb_kT = 0.  Its populations cover
+ * slab_nx + 3 local planes: local plane 0 is global plane slab_x0 - 1 (a ghost
+ * copy of the left neighbour's last plane), local planes 1 .. slab_nx the
+ * slab, and the last two the ghost copies of the right neighbour's first two
+ * planes.  lbmd_init takes the WHOLE lattice's solid mask; lbmd_get/set_
+ * populations/deviations and lbmd_init_fluid address the local planes.  The
+ * chain is replicated: every slab integrates all beads identically.
+ *
+ * One coupled step, per slab, in this order:
+ *   1. lbmd_slab_gather(h): the fluid velocity u_p of every bead whose lattice
+ *      cell starts in this slab (0 for the others) into io.up;
+ *   2. the caller sums io.up over all slabs (each bead gets exactly one
+ *      non-zero term, so the sum is exact) and writes the sum back into every
+ *      slab's io.up, ordered before step 3 on the handle's stream;
+ *   3. lbmd_slab_advance(h): the MD cycle, the spread onto the corners this
+ *      slab owns, the lattice pass and the source, then io.send_lo (local
+ *      planes 1, 2) and io.send_hi (local plane slab_nx) are filled;
+ *   4. the caller copies every slab's send_lo into its left neighbour's
+ *      recv_hi and its send_hi into its right neighbour's recv_lo (a single
+ *      slab: into its own), ordered before step 5;
+ *   5. lbmd_slab_import(h): the received planes into the ghost planes.
+ * The result equals the unsplit lattice's step bit for bit.  All three calls
+ * are asynchronous on the handle's stream.  The diagnostics rows hold this
+ * slab's fluid sums (sum them over slabs) and the whole chain's bead sums.
+ * In slab mode lbmd_step, lbmd_step_loop, lbmd_set_graph (> 0),
+ * lbmd_observables and lbmd_adjoint return LBMD_ERR_INVALID_ARG; the slab
+ * calls return it for a handle without slabs.
+ *
+ * io (from lbmd_slab_buffers): device pointers into the handle's buffer.
+ * up: [total_beads][4] float (x, y, z, 0).  send_lo, recv_hi: 2 planes;
+ * send_hi, recv_lo: 1 plane; a plane is [19][nz][ny] populations in the
+ * storage format (FP32 deviations, or FP16 deviations x 2^12), plane_bytes
+ * bytes. */
+typedef struct lbmd_slab_io {
+    float *up;
+    void *send_lo, *send_hi, *recv_lo, *recv_hi;
+    size_t plane_bytes;
+} lbmd_slab_io;
+lbmd_status lbmd_slab_buffers(lbmd_handle *h, lbmd_slab_io *io);
+lbmd_status lbmd_slab_gather(lbmd_handle *h);
+lbmd_status lbmd_slab_advance(lbmd_handle *h);
+lbmd_status lbmd_slab_import(lbmd_handle *h);
 
 /* Allocation-free fluid sums.  The paper has no counterpart: this is a
  * utility for callers that cannot allocate device memory where they call it,

@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(512, FL ? 1 : 2) k_stream_collide(const Sim S,
             }
             const float drho = drho_s * down;
             jx *= down; jy *= down; jz *= down;
-            if (MODE != 0) { am += drho; ax += jx; ay += jy; az += jz; }
+            if (MODE != 0 && x >= S.own_lo && x < S.own_hi) { am += drho; ax += jx; ay += jy; az += jz; }
             if (MODE != 2) {
                 const float rho = 1.0f + drho;
                 const float ir = 1.0f / rho;
@@ -438,6 +438,36 @@ cudaError_t launch_push_from_staging(const Sim &S, const float *staging, void *A
         if (dev) k_push_from_staging<0, true><<<4 * 152, 256, 0, st>>>(S, staging, A);
         else k_push_from_staging<0, false><<<4 * 152, 256, 0, st>>>(S, staging, A);
     }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Slab mode: copy `planes` consecutive local x planes from x_first on between
+// the populations and a plane buffer [19][planes][nz][ny] (raw storage
+// values), into the buffer (to_buf) or out of it.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_slab_planes(const Sim S, T *pop, T *buf, int x_first, int planes, bool to_buf) {
+    const size_t nyz = (size_t)S.ny * S.nz;
+    const size_t total = (size_t)Q * planes * nyz;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = t / (planes * nyz), rem = t - i * planes * nyz;
+        const size_t p = rem / nyz, zy = rem - p * nyz;
+        const size_t z = zy / S.ny, y = zy - z * S.ny;
+        T *site = pop + i * (size_t)S.ps + (size_t)(x_first + (int)p) + (size_t)S.nx * (y + (size_t)S.ny * z);
+        if (to_buf) buf[t] = *site;
+        else *site = buf[t];
+    }
+}
+
+cudaError_t launch_slab_planes(const Sim &S, void *pop, void *buf, int x_first, int planes, bool to_buf,
+                               cudaStream_t st) {
+    const size_t total = (size_t)Q * planes * S.ny * S.nz;
+    const int blocks = (int)min((total + 255) / 256, (size_t)4 * 152);
+    if (S.precision == LBMD_FP16DEV)
+        k_slab_planes<__half><<<blocks, 256, 0, st>>>(S, (__half *)pop, (__half *)buf, x_first, planes, to_buf);
+    else
+        k_slab_planes<float><<<blocks, 256, 0, st>>>(S, (float *)pop, (float *)buf, x_first, planes, to_buf);
     return cudaGetLastError();
 }
 

@@ -56,22 +56,33 @@ __device__ __forceinline__ float3 ffsub(float4 ah, float4 al, float4 bh, float4 
 }
 
 // ---------------------------------------------------------------------------
-// lattice corner c (0..7) of the cell holding a bead at wrapped (xw, yw, zw):
-// site index and raw trilinear weight (solid corners are zeroed by the caller
-// from the site's link word)
+// lattice corner c (0..7) of the cell holding a bead at wrapped (xw, yw, zw)
+// (xw in the whole lattice): the corner's local plane xi, its local site index
+// and raw trilinear weight (solid corners are zeroed by the caller from the
+// site's link word).  xc0 is the cell's first plane in local coordinates.  In
+// slab mode a cell that does not lie inside the local planes gives weight 0
+// and site 0 (the bead is not this slab's).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void corner_of(const Sim &S, float xw, float yw, float zw, int c, int &xi, int &yi,
-                                          int &zi, int &node, float &w) {
+                                          int &zi, int &node, float &w, int &xc0) {
     const int x0 = (int)floorf(xw), y0 = (int)floorf(yw), z0 = (int)floorf(zw);
     const float fx = xw - (float)x0, fy = yw - (float)y0, fz = zw - (float)z0;
     const int a = c & 1, b = (c >> 1) & 1, d = c >> 2;
-    xi = wrapi(x0 + a, S.nx);
+    int xl = x0 - S.gx0;
+    if (xl < 0) xl += S.bnx;
+    // a slab as wide as the lattice (less up to three planes) holds some
+    // cells twice, as ghosts and as its own: take its own copy
+    if (S.slab && xl < S.own_lo && xl + S.bnx <= S.nx - 2) xl += S.bnx;
+    xc0 = xl;
+    const bool here = !S.slab || xl <= S.nx - 2;
+    xi = S.slab ? (here ? xl + a : 0) : wrapi(xl + a, S.nx);
     yi = wrapi(y0 + b, S.ny);
     zi = wrapi(z0 + d, S.nz);
     node = xi + S.nx * (yi + S.ny * zi);
     w = (a ? fx : 1.0f - fx) * (b ? fy : 1.0f - fy) * (d ? fz : 1.0f - fz);
     if (S.interp == 1)  // nearest grid point: the corner on the bead's side of each mid-plane
         w = (a == (fx >= 0.5f) && b == (fy >= 0.5f) && d == (fz >= 0.5f)) ? 1.0f : 0.0f;
+    if (!here) w = 0.0f;
 }
 
 // Sum over the 8 corners: lane l holds corner l >> 2, and the xor tree over
@@ -98,11 +109,11 @@ __device__ __forceinline__ float sub_sum(float v) {
 // the link word).  Each lane returns its corner's site and normalised weight.
 template <typename T>
 __device__ __forceinline__ float3 gather_warp(const Sim &S, const T *__restrict__ A, float xw, float yw, float zw,
-                                              int &node, float &W) {
+                                              int &node, float &W, int &xi, int &xc0) {
     const int lane = threadIdx.x & 31, c = lane >> 2, sub = lane & 3;
-    int xi, yi, zi;
+    int yi, zi;
     float w;
-    corner_of(S, xw, yw, zw, c, xi, yi, zi, node, w);
+    corner_of(S, xw, yw, zw, c, xi, yi, zi, node, w, xc0);
     const uint32_t ns = (uint32_t)S.ps;  // population stride
     const uint32_t lm = __ldg(S.link + node);
     float hp[5], hb[5];
@@ -148,20 +159,27 @@ __global__ void __launch_bounds__(256) k_gather(const Sim S, const void *__restr
     const int r = S.bead_real[g];
     const T *A = reinterpret_cast<const T *>(Av) + (size_t)r * Q * S.ps;
     const float4 qh = S.r_hi[g], ql = S.r_lo[g];
-    int node;
+    int node, xi, xc0;
     float W;
-    const float3 u = gather_warp(S, A, ff_wrap(qh.x, ql.x, (float)S.nx, S.inx), ff_wrap(qh.y, ql.y, (float)S.ny, S.iny),
-                                 ff_wrap(qh.z, ql.z, (float)S.nz, S.inz), node, W);
+    const float3 u = gather_warp(S, A, ff_wrap(qh.x, ql.x, (float)S.bnx, S.binx), ff_wrap(qh.y, ql.y, (float)S.ny, S.iny),
+                                 ff_wrap(qh.z, ql.z, (float)S.nz, S.inz), node, W, xi, xc0);
     const int lane = threadIdx.x & 31;
-    if (lane == 0) S.up[g] = make_float4(u.x, u.y, u.z, 0.f);
+    // u_p from the handle that owns the bead's cell (every handle without
+    // slabs); in slab mode the others give 0 and the handles' values are summed
+    const bool cell_own = xc0 >= S.own_lo && xc0 < S.own_hi;
+    if (lane == 0) S.up[g] = cell_own ? make_float4(u.x, u.y, u.z, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
     // the starting state, for the step's bead diagnostics (the particle
     // kernel overwrites r and v while the lattice pass that sums them runs)
     if (lane == 1) S.bsnap[g] = qh;
     if (lane == 2) S.bsnap[S.total_beads + g] = ql;
     if (lane == 3) S.bsnap[2 * S.total_beads + g] = S.v[g];
     if ((lane & 3) == 0) {
+        // the spread reaches the corners this handle owns (a ghost corner of
+        // a slab as wide as the lattice is also its own plane xi - bnx)
         const int c = lane >> 2;
-        S.pair_node[(size_t)g * 8 + c] = W > 0.0f ? (int)((size_t)r * S.ns + node) : -1;
+        const int xs = (S.slab && xi >= S.own_hi && xi - S.bnx >= S.own_lo) ? xi - S.bnx : xi;
+        const bool mine = W > 0.0f && xs >= S.own_lo && xs < S.own_hi;
+        S.pair_node[(size_t)g * 8 + c] = mine ? (int)((size_t)r * S.ns + node + (xs - xi)) : -1;
         S.pair_w[(size_t)g * 8 + c] = W;
     }
 }
@@ -202,7 +220,7 @@ __device__ __forceinline__ void bead_sum_pass(const Sim &S, int off, int N, unsi
         const bool tr = S.wall_x >= 0 && (h.x > thr || (h.x == thr && l.x > 0.0f));
         if constexpr (PASS == 0) {
             const float4 v = S.bsnap[2 * TB + off + q], u = S.up[off + q];
-            const bool ch = in_channel(S, ff_wrap(h.x, l.x, (float)S.nx, S.inx), ff_wrap(h.y, l.y, (float)S.ny, S.iny),
+            const bool ch = in_channel(S, ff_wrap(h.x, l.x, (float)S.bnx, S.binx), ff_wrap(h.y, l.y, (float)S.ny, S.iny),
                                        ff_wrap(h.z, l.z, (float)S.nz, S.inz));
             a[0] += fix_of(v.x, FIXD_V); a[1] += fix_of(v.y, FIXD_V); a[2] += fix_of(v.z, FIXD_V);
             a[3] += tr ? 1 : 0;
@@ -571,7 +589,7 @@ __device__ __forceinline__ float3 pair_part(const Sim &S, const PSmem &sm, int b
     const float4 *ph = sm.ph[buf], *plo = sm.pl[buf];
     const int nn = own ? (int)sm.nn[pl] : 0, nw = own ? (int)sm.nw[pl] : 0;
     const int nn_w = __reduce_max_sync(0xffffffffu, nn), nw_w = __reduce_max_sync(0xffffffffu, nw);
-    const float fnx = (float)S.nx, fny = (float)S.ny, fnz = (float)S.nz;
+    const float fnx = (float)S.bnx, fny = (float)S.ny, fnz = (float)S.nz;
     // Pair and wall lists, two entries per iteration, to the warp's longest
     // list: both entries' shared-memory loads are issued before either is
     // used, and no lane branches away (entries past a lane's own list point
@@ -586,9 +604,9 @@ __device__ __forceinline__ float3 pair_part(const Sim &S, const PSmem &sm, int b
             const int q0 = v0 ? (int)lst[k] : pself;
             const int q1 = v1 ? (int)lst[k + T] : pself;
             const float4 h0 = ph[q0], l0 = plo[q0], h1 = ph[q1], l1 = plo[q1];
-            const float3 d0 = make_float3(ff_diff(mh.x, ml.x, h0.x, l0.x, fnx, S.inx), ff_diff(mh.y, ml.y, h0.y, l0.y, fny, S.iny),
+            const float3 d0 = make_float3(ff_diff(mh.x, ml.x, h0.x, l0.x, fnx, S.binx), ff_diff(mh.y, ml.y, h0.y, l0.y, fny, S.iny),
                                           ff_diff(mh.z, ml.z, h0.z, l0.z, fnz, S.inz));
-            const float3 d1 = make_float3(ff_diff(mh.x, ml.x, h1.x, l1.x, fnx, S.inx), ff_diff(mh.y, ml.y, h1.y, l1.y, fny, S.iny),
+            const float3 d1 = make_float3(ff_diff(mh.x, ml.x, h1.x, l1.x, fnx, S.binx), ff_diff(mh.y, ml.y, h1.y, l1.y, fny, S.iny),
                                           ff_diff(mh.z, ml.z, h1.z, l1.z, fnz, S.inz));
             const float r20 = v0 ? dot3(d0, d0) : 1e30f, r21 = v1 ? dot3(d1, d1) : 1e30f;
             const float c0 = r20 < S.lj_rc2 ? wca_coef(r20, S.lj_eps, S.lj_sig2) : 0.0f;
@@ -602,10 +620,10 @@ __device__ __forceinline__ float3 pair_part(const Sim &S, const PSmem &sm, int b
             const bool v0 = k < nw, v1 = k + T < nw;
             const uint32_t p0 = v0 ? wl[k] : 0u;
             const uint32_t p1 = v1 ? wl[k + T] : 0u;
-            const float3 d0 = make_float3(ff_diff(mh.x, ml.x, (float)(p0 & 0xfffu), 0.f, fnx, S.inx),
+            const float3 d0 = make_float3(ff_diff(mh.x, ml.x, (float)(p0 & 0xfffu), 0.f, fnx, S.binx),
                                           ff_diff(mh.y, ml.y, (float)((p0 >> 12) & 0x3ffu), 0.f, fny, S.iny),
                                           ff_diff(mh.z, ml.z, (float)(p0 >> 22), 0.f, fnz, S.inz));
-            const float3 d1 = make_float3(ff_diff(mh.x, ml.x, (float)(p1 & 0xfffu), 0.f, fnx, S.inx),
+            const float3 d1 = make_float3(ff_diff(mh.x, ml.x, (float)(p1 & 0xfffu), 0.f, fnx, S.binx),
                                           ff_diff(mh.y, ml.y, (float)((p1 >> 12) & 0x3ffu), 0.f, fny, S.iny),
                                           ff_diff(mh.z, ml.z, (float)(p1 >> 22), 0.f, fnz, S.inz));
             const float r20 = v0 ? dot3(d0, d0) : 1e30f, r21 = v1 ? dot3(d1, d1) : 1e30f;
@@ -693,7 +711,7 @@ __device__ __forceinline__ void cell_of(const Sim &S, float xw, float yw, float 
 template <int T>
 __device__ __forceinline__ int scan_pairs(const Sim &S, const float4 *ph, const float4 *plo, int N, int p, bool own,
                                           uint16_t *lst) {
-    const float fnx = (float)S.nx, fny = (float)S.ny, fnz = (float)S.nz;
+    const float fnx = (float)S.bnx, fny = (float)S.ny, fnz = (float)S.nz;
     const int lane = threadIdx.x & 31, lt = lane & (T - 1);
     const int pself = own ? p : 0;
     const float4 mh = ph[pself], ml = plo[pself];
@@ -705,7 +723,7 @@ __device__ __forceinline__ int scan_pairs(const Sim &S, const float4 *ph, const 
         const int q = base + lt;
         const int qq = q < N ? q : pself;
         const float4 qh = ph[qq], ql = plo[qq];
-        const float dx = ff_diff(mh.x, ml.x, qh.x, ql.x, fnx, S.inx), dy = ff_diff(mh.y, ml.y, qh.y, ql.y, fny, S.iny),
+        const float dx = ff_diff(mh.x, ml.x, qh.x, ql.x, fnx, S.binx), dy = ff_diff(mh.y, ml.y, qh.y, ql.y, fny, S.iny),
                     dz = ff_diff(mh.z, ml.z, qh.z, ql.z, fnz, S.inz);
         const bool hit = own && q < N && (q < p - 1 || q > p + 1) && dx * dx + dy * dy + dz * dz < S.rl2;
         const unsigned g = (__ballot_sync(0xffffffffu, hit) >> gshift) & gmask;
@@ -728,7 +746,7 @@ __device__ __forceinline__ void build_lists_body(const Sim &S, const PSmem &sm, 
     const bool owner = own && (threadIdx.x % T) == 0;
     const bool brute = N <= BRUTE_MAX;
     const bool hashed = !brute && S.ncell[0] >= 3 && S.ncell[1] >= 3 && S.ncell[2] >= 3;
-    const float fnx = (float)S.nx, fny = (float)S.ny, fnz = (float)S.nz;
+    const float fnx = (float)S.bnx, fny = (float)S.ny, fnz = (float)S.nz;
     const float4 *ph = sm.ph[buf], *plo = sm.pl[buf];
     if (hashed)
         for (int k = threadIdx.x; k < HASH_SIZE; k += blockDim.x) { sm.hkey[k] = -1; sm.hhead[k] = -1; }
@@ -738,7 +756,7 @@ __device__ __forceinline__ void build_lists_body(const Sim &S, const PSmem &sm, 
         for (int q = threadIdx.x; q < N; q += blockDim.x) {
             const float4 qh = ph[q], ql = plo[q];
             int ci, cj, ck;
-            cell_of(S, ff_wrap(qh.x, ql.x, fnx, S.inx), ff_wrap(qh.y, ql.y, fny, S.iny), ff_wrap(qh.z, ql.z, fnz, S.inz),
+            cell_of(S, ff_wrap(qh.x, ql.x, fnx, S.binx), ff_wrap(qh.y, ql.y, fny, S.iny), ff_wrap(qh.z, ql.z, fnz, S.inz),
                     ci, cj, ck);
             const int key = ci + S.ncell[0] * (cj + S.ncell[1] * ck);
             int slot = cell_slot(key);
@@ -755,14 +773,14 @@ __device__ __forceinline__ void build_lists_body(const Sim &S, const PSmem &sm, 
     if (brute) n_scan = scan_pairs<T>(S, ph, plo, N, p, own, sm.nbr + (own ? pl : 0) * NBR_CAP);
     if (owner) {
         const float4 mh = ph[p], ml = plo[p];
-        const float xw = ff_wrap(mh.x, ml.x, fnx, S.inx), yw = ff_wrap(mh.y, ml.y, fny, S.iny),
+        const float xw = ff_wrap(mh.x, ml.x, fnx, S.binx), yw = ff_wrap(mh.y, ml.y, fny, S.iny),
                     zw = ff_wrap(mh.z, ml.z, fnz, S.inz);
         uint16_t *lst = sm.nbr + pl * NBR_CAP;
         int n = n_scan;
         auto consider = [&](int q) {
             if (q == p || q == p - 1 || q == p + 1) return;
             const float4 qh = ph[q], ql = plo[q];
-            const float dx = ff_diff(mh.x, ml.x, qh.x, ql.x, fnx, S.inx), dy = ff_diff(mh.y, ml.y, qh.y, ql.y, fny, S.iny),
+            const float dx = ff_diff(mh.x, ml.x, qh.x, ql.x, fnx, S.binx), dy = ff_diff(mh.y, ml.y, qh.y, ql.y, fny, S.iny),
                         dz = ff_diff(mh.z, ml.z, qh.z, ql.z, fnz, S.inz);
             if (dx * dx + dy * dy + dz * dz < S.rl2) list_insert(lst, n, q);
         };
@@ -799,26 +817,26 @@ __device__ __forceinline__ void build_lists_body(const Sim &S, const PSmem &sm, 
         if (S.rlw < 2.0f) {
             // every site within rlw < 2 of the bead lies in the 4x4x4 box starting
             // one site below its cell corner; its solid sites are one bit mask
-            unsigned long long mm = __ldg(S.wallmask + cx0 + S.nx * (cy0 + S.ny * cz0));
+            unsigned long long mm = __ldg(S.bwallmask + cx0 + S.bnx * (cy0 + S.ny * cz0));
             while (mm) {
                 const int bit = __ffsll((long long)mm) - 1;
                 mm &= mm - 1;
                 const int X = cx0 + (bit & 3) - 1, Y = cy0 + ((bit >> 2) & 3) - 1, Z = cz0 + (bit >> 4) - 1;
                 const float dx = xw - (float)X, dy = yw - (float)Y, dz = zw - (float)Z;
                 if (dx * dx + dy * dy + dz * dz >= S.rlw2) continue;
-                const int xx = wrapi(X, S.nx), yy = wrapi(Y, S.ny), zz = wrapi(Z, S.nz);
+                const int xx = wrapi(X, S.bnx), yy = wrapi(Y, S.ny), zz = wrapi(Z, S.nz);
                 if (m < WALL_CAP) sm.wal[pl * WALL_CAP + m] = (uint32_t)xx | ((uint32_t)yy << 12) | ((uint32_t)zz << 22);
                 ++m;
             }
-        } else if (__ldg(S.link + cx0 + S.nx * (cy0 + S.ny * cz0)) & NEAR_SOLID_BIT) {
+        } else if (__ldg(S.blink + cx0 + S.bnx * (cy0 + S.ny * cz0)) & NEAR_SOLID_BIT) {
             const int x0 = (int)floorf(xw - S.rlw), x1 = (int)floorf(xw + S.rlw);
             const int y0 = (int)floorf(yw - S.rlw), y1 = (int)floorf(yw + S.rlw);
             const int z0 = (int)floorf(zw - S.rlw), z1 = (int)floorf(zw + S.rlw);
             for (int Z = z0; Z <= z1; ++Z)
                 for (int Y = y0; Y <= y1; ++Y)
                     for (int X = x0; X <= x1; ++X) {
-                        const int xx = wrap_any(X, S.nx), yy = wrap_any(Y, S.ny), zz = wrap_any(Z, S.nz);
-                        if (!(__ldg(S.link + xx + S.nx * (yy + S.ny * zz)) & SOLID_BIT)) continue;
+                        const int xx = wrap_any(X, S.bnx), yy = wrap_any(Y, S.ny), zz = wrap_any(Z, S.nz);
+                        if (!(__ldg(S.blink + xx + S.bnx * (yy + S.ny * zz)) & SOLID_BIT)) continue;
                         const float dx = xw - (float)X, dy = yw - (float)Y, dz = zw - (float)Z;
                         if (dx * dx + dy * dy + dz * dz >= S.rlw2) continue;
                         if (m < WALL_CAP) sm.wal[pl * WALL_CAP + m] = (uint32_t)xx | ((uint32_t)yy << 12) | ((uint32_t)zz << 22);
@@ -953,7 +971,7 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
     const int first = rank * Nc, last = min(first + Nc, N) - 1;  // the block's beads
     const bool pull = S.md_pull != 0 && cc > 1;  // block-uniform
     const long long step = S.ctrl->step;
-    const float fnx = (float)S.nx, fny = (float)S.ny, fnz = (float)S.nz;
+    const float fnx = (float)S.bnx, fny = (float)S.ny, fnz = (float)S.nz;
     unsigned long long tclk = clock64();
     if (threadIdx.x == 0) { s_flag[0] = 0; s_flag[1] = 0; s_err = 0; }
 
@@ -1009,7 +1027,7 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
         float3 xi = make_float3(0.f, 0.f, 0.f);
         if (own && amp > 0.0f && !spv) xi = amp * gauss3(S.seed, S.real_base + (uint32_t)r, (uint32_t)p, step, (uint32_t)sub);
         if (own) {  // first half kick: field + friction + noise (field only for SPV)
-            const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx, S.inx), ff_wrap(mh.y, ml.y, fny, S.iny),
+            const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx, S.binx), ff_wrap(mh.y, ml.y, fny, S.iny),
                                        ff_wrap(mh.z, ml.z, fnz, S.inz));
             if (trj && lt == 0)
                 trj[(size_t)traj_slot_kick(S.M, S.Mb, 2 * sub) * TB + off + p] = make_float4(v.x, v.y, v.z, ch ? 1.f : 0.f);
@@ -1111,7 +1129,7 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
                 ff_add(mh.z, ml.z, hb * v.z);
             }
             // second half kick with the same noise (field only for SPV)
-            const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx, S.inx), ff_wrap(mh.y, ml.y, fny, S.iny),
+            const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx, S.binx), ff_wrap(mh.y, ml.y, fny, S.iny),
                                        ff_wrap(mh.z, ml.z, fnz, S.inz));
             if (trj && lt == 0)
                 trj[(size_t)traj_slot_kick(S.M, S.Mb, 2 * sub + 1) * TB + off + p] = make_float4(v.x, v.y, v.z, ch ? 1.f : 0.f);
@@ -1238,7 +1256,7 @@ __global__ void __launch_bounds__(1024) k_bead_observables(const Sim S, const vo
     const int p = threadIdx.x;
     const bool own = p < N;
     const T *A = reinterpret_cast<const T *>(Av) + (size_t)r * Q * S.ps;
-    const float fnx = (float)S.nx, fny = (float)S.ny, fnz = (float)S.nz;
+    const float fnx = (float)S.bnx, fny = (float)S.ny, fnz = (float)S.nz;
     float4 mh = make_float4(0.f, 0.f, 0.f, 0.f), ml = mh, vv = mh;
     if (own) {
         mh = S.r_hi[off + p];
@@ -1251,10 +1269,10 @@ __global__ void __launch_bounds__(1024) k_bead_observables(const Sim S, const vo
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int q = warp; q < N; q += nwarps) {
         const float4 qh = ph[q], ql = plo[q];
-        int node;
+        int node, xi, xc0;
         float W;
-        const float3 u = gather_warp(S, A, ff_wrap(qh.x, ql.x, fnx, S.inx), ff_wrap(qh.y, ql.y, fny, S.iny),
-                                     ff_wrap(qh.z, ql.z, fnz, S.inz), node, W);
+        const float3 u = gather_warp(S, A, ff_wrap(qh.x, ql.x, fnx, S.binx), ff_wrap(qh.y, ql.y, fny, S.iny),
+                                     ff_wrap(qh.z, ql.z, fnz, S.inz), node, W, xi, xc0);
         if ((threadIdx.x & 31) == 0) ups[q] = make_float4(u.x, u.y, u.z, 0.f);
     }
     __syncthreads();
@@ -1263,7 +1281,7 @@ __global__ void __launch_bounds__(1024) k_bead_observables(const Sim S, const vo
     double a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (own) {
         const float4 u = ups[p];
-        const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx, S.inx), ff_wrap(mh.y, ml.y, fny, S.iny),
+        const bool ch = in_channel(S, ff_wrap(mh.x, ml.x, fnx, S.binx), ff_wrap(mh.y, ml.y, fny, S.iny),
                                    ff_wrap(mh.z, ml.z, fnz, S.inz));
         a[0] = vv.x; a[1] = vv.y; a[2] = vv.z;
         a[3] = X; a[4] = Y; a[5] = Z;

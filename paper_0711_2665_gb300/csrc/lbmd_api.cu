@@ -23,6 +23,7 @@ const char *KNAMES[K_COUNT] = {"gather", "particles", "stream_collide", "source"
 constexpr double SKIN = 0.6;  // Verlet-list skin (lattice units); 0.4 and 0.8 measured slower
 
 struct Layout {
+    size_t blink, bwallmask, xsend_lo, xsend_hi, xrecv_lo, xrecv_hi;  // slab mode only (else 0)
     size_t popA, popB, staging, link, wallmask, tileflag, solid, G, stamp;
     size_t r_hi, r_lo, v, up, J, pair_node, pair_w, bead_real, bead_off, bsnap, fsum, ring, obs, tl, ctrl, loopc, snap, md_map, phase, total;
 };
@@ -104,6 +105,13 @@ bool config_ok(const lbmd_config *c, const int32_t *off, std::string &why) {
     if (c->pore_h < 0 || c->pore_h > c->ny || c->pore_h > c->nz) { why = "pore_h out of range"; return false; }
     if (!(c->lj_sigma > 0) || !(c->wall_sigma > 0) || c->lj_eps < 0 || c->wall_eps < 0) { why = "WCA sigma must be > 0, eps >= 0"; return false; }
     if (c->gamma < 0 || c->kT < 0 || c->k_bond < 0) { why = "gamma, kT, k_bond must be >= 0"; return false; }
+    if (c->slab_nx < 0 || c->slab_nx > c->nx) { why = "slab_nx must be in [0, nx]"; return false; }
+    if (c->slab_nx > 0) {
+        if (c->slab_nx < 2) { why = "a slab holds at least 2 planes"; return false; }
+        if (c->slab_x0 < 0 || c->slab_x0 >= c->nx) { why = "slab_x0 must be inside [0, nx)"; return false; }
+        if (c->n_real != 1) { why = "slab mode takes one realization"; return false; }
+        if (c->lb_kT != 0.0) { why = "slab mode runs without the fluctuating fluid"; return false; }
+    }
     if (!off) { why = "null bead_offsets"; return false; }
     if (off[0] != 0) { why = "bead_offsets[0] must be 0"; return false; }
     if (off[c->n_real] > 0 && (c->nx < 4 || c->ny < 4 || c->nz < 4)) {
@@ -123,12 +131,17 @@ bool config_ok(const lbmd_config *c, const int32_t *off, std::string &why) {
 // both precisions.
 size_t pop_stride(size_t ns) { return (ns + 63) / 64 * 64; }
 
+// x planes of the handle's populations: the lattice, or a slab with its
+// ghost planes (one on the left, two on the right)
+int local_nx(const lbmd_config *c) { return c->slab_nx > 0 ? c->slab_nx + 3 : c->nx; }
+
 Layout layout_of(const lbmd_config *c, int total_beads) {
     Layout L;
-    const size_t ns = (size_t)c->nx * c->ny * c->nz;
+    const int nxl = local_nx(c);
+    const size_t ns = (size_t)nxl * c->ny * c->nz;
     const size_t esz = c->precision == LBMD_FP16DEV ? 2 : 4;
     const size_t npop = (size_t)c->n_real * LBMD_Q * pop_stride(ns);
-    const size_t nxt = (c->nx + 31) / 32;
+    const size_t nxt = (nxl + 31) / 32;
     const size_t nb = (size_t)std::max(total_beads, 1);
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
@@ -162,6 +175,17 @@ Layout layout_of(const lbmd_config *c, int total_beads) {
     // shape's (autotuner); at most one cluster of MAX_CLUSTER blocks per chain
     L.md_map = take(2 * (size_t)c->n_real * MAX_CLUSTER * sizeof(int4));
     L.phase = take(PHASES * sizeof(unsigned long long));
+    L.blink = L.bwallmask = L.xsend_lo = L.xsend_hi = L.xrecv_lo = L.xrecv_hi = 0;
+    if (c->slab_nx > 0) {  // the whole lattice's geometry for the beads; the exchanged planes
+        const size_t gns = (size_t)c->nx * c->ny * c->nz;
+        const size_t plane = (size_t)LBMD_Q * c->ny * c->nz * esz;
+        L.blink = take(gns * 4);
+        L.bwallmask = take(gns * 8);
+        L.xsend_lo = take(2 * plane);
+        L.xsend_hi = take(plane);
+        L.xrecv_lo = take(plane);
+        L.xrecv_hi = take(2 * plane);
+    }
     L.total = o;
     return L;
 }
@@ -264,11 +288,15 @@ lbmd_status upload_md_map(lbmd_handle *h, Sim &S, int region) {
 // behind the lattice pass's traffic), then the particle kernel (aux stream)
 // and the bead diagnostics (aux2) run concurrently with the stream-collide
 // kernel (main), then the source, which also completes the diagnostics row.
-lbmd_status enqueue_step(lbmd_handle *h) {
+lbmd_status enqueue_gather(lbmd_handle *h) {
     if (h->total_beads > 0) {
         ProfScope ps(h, K_GATHER, h->st);
         CK(launch_gather(h->S, h->popA, h->st));
     }
+    return LBMD_OK;
+}
+
+lbmd_status enqueue_advance(lbmd_handle *h) {
     CK(cudaEventRecord(h->ev_fork, h->st));
     CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
     {
@@ -299,6 +327,22 @@ lbmd_status enqueue_step(lbmd_handle *h) {
     h->host_step += 1;
     h->launches += h->total_beads > 0 ? 5 : 3;
     if (h->pending.size() > 30000) return resolve_profile(h);
+    return LBMD_OK;
+}
+
+lbmd_status enqueue_step(lbmd_handle *h) {
+    lbmd_status s = enqueue_gather(h);
+    return s == LBMD_OK ? enqueue_advance(h) : s;
+}
+
+lbmd_status slab_only(lbmd_handle *h) {
+    if (!h) return LBMD_ERR_INVALID_ARG;
+    if (!h->S.slab) return fail(h, LBMD_ERR_INVALID_ARG, "not a slab handle (slab_nx = 0)");
+    return LBMD_OK;
+}
+
+lbmd_status not_slab(lbmd_handle *h, const char *what) {
+    if (h && h->S.slab) return fail(h, LBMD_ERR_INVALID_ARG, std::string(what) + " is not available in slab mode");
     return LBMD_OK;
 }
 
@@ -594,15 +638,50 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
     double n_fluid = 0;
     // a bead's wall-list box reaches floor(rlw) + 1 sites from its cell corner
     const int near_radius = (int)std::floor(std::pow(2.0, 1.0 / 6.0) * cfg->wall_sigma + 0.5 * SKIN) + 1;
-    build_geometry(cfg, solid, near_radius, link, wallmask, tile, sol, n_fluid);
+    const bool slab = cfg->slab_nx > 0;
+    const int nxl = local_nx(cfg);
+    std::vector<uint32_t> glink;
+    std::vector<unsigned long long> gwallmask;
+    if (slab) {
+        // the slab's planes with their ghosts, cut from the whole lattice's
+        // mask (periodic in x); the link words of the two outermost ghost
+        // planes see the other edge and are never used.  The beads keep the
+        // whole lattice's geometry for their wall lists.
+        lbmd_config lcfg = *cfg;
+        lcfg.nx = nxl;
+        std::vector<uint8_t> lsol((size_t)nxl * cfg->ny * cfg->nz);
+        for (int z = 0; z < cfg->nz; ++z)
+            for (int y = 0; y < cfg->ny; ++y)
+                for (int xl = 0; xl < nxl; ++xl) {
+                    const int xg = ((cfg->slab_x0 - 1 + xl) % cfg->nx + cfg->nx) % cfg->nx;
+                    lsol[xl + (size_t)nxl * (y + (size_t)cfg->ny * z)] = solid[xg + (size_t)cfg->nx * (y + (size_t)cfg->ny * z)];
+                }
+        double nf_local = 0;
+        build_geometry(&lcfg, lsol.data(), near_radius, link, wallmask, tile, sol, nf_local);
+        std::vector<uint8_t> gtile, gsol;
+        double nf_all = 0;
+        build_geometry(cfg, solid, near_radius, glink, gwallmask, gtile, gsol, nf_all);
+        for (int z = 0; z < cfg->nz; ++z)  // fluid sites of the slab's own planes
+            for (int y = 0; y < cfg->ny; ++y)
+                for (int xl = 1; xl <= cfg->slab_nx; ++xl)
+                    n_fluid += sol[xl + (size_t)nxl * (y + (size_t)cfg->ny * z)] ? 0.0 : 1.0;
+    } else {
+        build_geometry(cfg, solid, near_radius, link, wallmask, tile, sol, n_fluid);
+    }
 
     Sim &S = h->S;
     memset(&S, 0, sizeof(S));
-    S.nx = cfg->nx; S.ny = cfg->ny; S.nz = cfg->nz;
-    S.ns = cfg->nx * cfg->ny * cfg->nz;
+    S.nx = nxl; S.ny = cfg->ny; S.nz = cfg->nz;
+    S.ns = nxl * cfg->ny * cfg->nz;
     S.ps = (int)pop_stride((size_t)S.ns);
-    S.nxt = (cfg->nx + 31) / 32;
-    S.inx = 1.0f / (float)cfg->nx;
+    S.nxt = (nxl + 31) / 32;
+    S.inx = 1.0f / (float)nxl;
+    S.slab = slab ? 1 : 0;
+    S.bnx = cfg->nx;
+    S.binx = 1.0f / (float)cfg->nx;
+    S.gx0 = slab ? ((cfg->slab_x0 - 1) % cfg->nx + cfg->nx) % cfg->nx : 0;
+    S.own_lo = slab ? 1 : 0;
+    S.own_hi = slab ? cfg->slab_nx + 1 : nxl;
     S.iny = 1.0f / (float)cfg->ny;
     S.inz = 1.0f / (float)cfg->nz;
     S.n_real = cfg->n_real;
@@ -668,6 +747,8 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
     S.wallmask = (const unsigned long long *)(b + L.wallmask);
     S.seed = cfg->seed;
     S.link = (const uint32_t *)(b + L.link);
+    S.blink = slab ? (const uint32_t *)(b + L.blink) : S.link;
+    S.bwallmask = slab ? (const unsigned long long *)(b + L.bwallmask) : S.wallmask;
     S.tileflag = (const uint8_t *)(b + L.tileflag);
     S.solid = (const uint8_t *)(b + L.solid);
     S.G = (unsigned long long *)(b + L.G);
@@ -706,6 +787,10 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
     CKI(cudaMemcpyAsync(b + L.wallmask, wallmask.data(), wallmask.size() * 8, cudaMemcpyHostToDevice, h->st));
     CKI(cudaMemcpyAsync(b + L.tileflag, tile.data(), tile.size(), cudaMemcpyHostToDevice, h->st));
     CKI(cudaMemcpyAsync(b + L.solid, sol.data(), sol.size(), cudaMemcpyHostToDevice, h->st));
+    if (slab) {
+        CKI(cudaMemcpyAsync(b + L.blink, glink.data(), glink.size() * 4, cudaMemcpyHostToDevice, h->st));
+        CKI(cudaMemcpyAsync(b + L.bwallmask, gwallmask.data(), gwallmask.size() * 8, cudaMemcpyHostToDevice, h->st));
+    }
     CKI(cudaMemcpyAsync(b + L.bead_off, h->offsets.data(), h->offsets.size() * 4, cudaMemcpyHostToDevice, h->st));
     std::vector<int32_t> breal((size_t)std::max(h->total_beads, 1), 0);
     for (int r = 0; r < cfg->n_real; ++r)
@@ -736,6 +821,7 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
 
 lbmd_status lbmd_step(lbmd_handle *h, int64_t n) {
     if (!h || n < 0) return LBMD_ERR_INVALID_ARG;
+    if (not_slab(h, "lbmd_step") != LBMD_OK) return LBMD_ERR_INVALID_ARG;
     while (n > 0) {
         const bool use_graph = h->graph_steps > 0 && !h->profiling && n >= h->graph_steps;
         if (use_graph) {
@@ -760,6 +846,7 @@ lbmd_status lbmd_step(lbmd_handle *h, int64_t n) {
 
 lbmd_status lbmd_step_loop(lbmd_handle *h, int64_t n) {
     if (!h || n < 0) return LBMD_ERR_INVALID_ARG;
+    if (not_slab(h, "lbmd_step_loop") != LBMD_OK) return LBMD_ERR_INVALID_ARG;
     if (!h->st) return fail(h, LBMD_ERR_INVALID_ARG, "graph capture needs a non-default stream");
     if (h->profiling) return lbmd_step(h, n);
     if (h->lexec && h->popA != h->loop_A && n > 0) {  // realign A with the captured body
@@ -797,6 +884,7 @@ lbmd_status lbmd_check(lbmd_handle *h) {
 
 lbmd_status lbmd_observables(lbmd_handle *h, lbmd_obs *out) {
     if (!h || !out) return LBMD_ERR_INVALID_ARG;
+    if (not_slab(h, "lbmd_observables") != LBMD_OK) return LBMD_ERR_INVALID_ARG;
     CK(launch_fluid_observables(h->S, h->popA, h->st));
     CK(launch_bead_observables(h->S, h->popA, h->st));
     h->launches += 2;
@@ -1072,6 +1160,7 @@ lbmd_status lbmd_adjoint_required_bytes(const lbmd_handle *h, int32_t K, int32_t
 lbmd_status lbmd_adjoint(lbmd_handle *h, int32_t K, int32_t C, void *scratch, size_t scratch_bytes, double *loss,
                          double *dgamma, double *dE, double *dr0) {
     if (!h) return LBMD_ERR_INVALID_ARG;
+    if (not_slab(h, "lbmd_adjoint") != LBMD_OK) return LBMD_ERR_INVALID_ARG;
     std::string why;
     if (!adjoint_ok(h, K, C, why)) return fail(h, LBMD_ERR_INVALID_ARG, why);
     const AdjLayout a = adj_layout(h, K, C);
@@ -1190,6 +1279,7 @@ lbmd_status lbmd_adjoint(lbmd_handle *h, int32_t K, int32_t C, void *scratch, si
 
 lbmd_status lbmd_set_graph(lbmd_handle *h, int32_t steps_per_graph) {
     if (!h || steps_per_graph < 0 || (steps_per_graph & 1)) return LBMD_ERR_INVALID_ARG;
+    if (steps_per_graph > 0 && not_slab(h, "lbmd_set_graph") != LBMD_OK) return LBMD_ERR_INVALID_ARG;
     if (!h->st) return fail(h, LBMD_ERR_INVALID_ARG, "graph capture needs a non-default stream");
     drop_graph(h);
     h->graph_steps = steps_per_graph;
@@ -1474,6 +1564,44 @@ lbmd_status lbmd_kernel_times(lbmd_handle *h, lbmd_kernel_time *out, int32_t max
 lbmd_status lbmd_launch_count(lbmd_handle *h, int64_t *launches) {
     if (!h || !launches) return LBMD_ERR_INVALID_ARG;
     *launches = h->launches;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_slab_buffers(lbmd_handle *h, lbmd_slab_io *io) {
+    if (slab_only(h) != LBMD_OK || !io) return LBMD_ERR_INVALID_ARG;
+    io->up = reinterpret_cast<float *>(h->S.up);
+    io->send_lo = h->dbuf + h->L.xsend_lo;
+    io->send_hi = h->dbuf + h->L.xsend_hi;
+    io->recv_lo = h->dbuf + h->L.xrecv_lo;
+    io->recv_hi = h->dbuf + h->L.xrecv_hi;
+    io->plane_bytes = (size_t)LBMD_Q * h->S.ny * h->S.nz * (h->cfg.precision == LBMD_FP16DEV ? 2 : 4);
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_slab_gather(lbmd_handle *h) {
+    if (slab_only(h) != LBMD_OK) return LBMD_ERR_INVALID_ARG;
+    return enqueue_gather(h);
+}
+
+lbmd_status lbmd_slab_advance(lbmd_handle *h) {
+    if (slab_only(h) != LBMD_OK) return LBMD_ERR_INVALID_ARG;
+    lbmd_status s = enqueue_advance(h);
+    if (s != LBMD_OK) return s;
+    // the step's result (now in A): local planes 1, 2 for the left
+    // neighbour, the last own plane for the right one
+    const int w = h->cfg.slab_nx;
+    CK(launch_slab_planes(h->S, h->popA, h->dbuf + h->L.xsend_lo, 1, 2, true, h->st));
+    CK(launch_slab_planes(h->S, h->popA, h->dbuf + h->L.xsend_hi, w, 1, true, h->st));
+    h->launches += 2;
+    return LBMD_OK;
+}
+
+lbmd_status lbmd_slab_import(lbmd_handle *h) {
+    if (slab_only(h) != LBMD_OK) return LBMD_ERR_INVALID_ARG;
+    const int w = h->cfg.slab_nx;
+    CK(launch_slab_planes(h->S, h->popA, h->dbuf + h->L.xrecv_lo, 0, 1, false, h->st));
+    CK(launch_slab_planes(h->S, h->popA, h->dbuf + h->L.xrecv_hi, w + 1, 2, false, h->st));
+    h->launches += 2;
     return LBMD_OK;
 }
 

@@ -171,6 +171,19 @@ struct Sim {
     int md_bw;               // bonded terms: 0 automatic, 1 by every bead's lanes, 2 by a block's last warp
     int md_reserve;          // 1: the particle kernel's blocks claim their SMs' whole shared memory
     int smem_optin;          // the device's opt-in shared memory per block (bytes)
+    // The beads' frame.  Bead positions live in the whole lattice (bnx along
+    // x); the populations of this handle cover nx planes from global x plane
+    // gx0 on.  Without slabs bnx = nx, gx0 = 0 and the handle owns every
+    // plane.  In slab mode (one lattice split over handles in x) the handle
+    // holds its slab's planes [own_lo, own_hi) plus ghost planes, and blink /
+    // bwallmask are the whole lattice's geometry for the bead-wall lists.
+    int slab;                // 1: this handle is one x-slab of a larger lattice
+    int bnx;                 // x extent of the whole lattice
+    float binx;              // 1 / bnx
+    int gx0;                 // global x of local plane 0
+    int own_lo, own_hi;      // local planes this handle owns (sums, the spread, u_p of beads whose cell starts there)
+    const uint32_t *blink;   // link words of the whole lattice (NEAR_SOLID_BIT, SOLID_BIT)
+    const unsigned long long *bwallmask;  // solid masks of the whole lattice
     // placement of the chains in the particle kernel's clusters: per block
     // (realization or -1, rank within its chain, the chain's blocks, the
     // chain's first rank in the cluster); md_clusters clusters of the shape's C
@@ -394,7 +407,7 @@ __device__ __forceinline__ int wrap_any(int i, int n) { const int m = i % n; ret
 __device__ __forceinline__ bool in_channel(const Sim &S, float xw, float yw, float zw) {
     if (S.wall_x < 0) return false;
     float dx = xw - (float)S.wall_x;
-    dx -= (float)S.nx * rintf(dx * S.inx);
+    dx -= (float)S.bnx * rintf(dx * S.binx);
     if (fabsf(dx) > 1.5f) return false;
     if (yw < (float)S.pore_ylo - 0.5f || yw > (float)(S.pore_ylo + S.pore_h) - 0.5f) return false;
     if (zw < (float)S.pore_zlo - 0.5f || zw > (float)(S.pore_zlo + S.pore_h) - 0.5f) return false;
@@ -413,6 +426,8 @@ cudaError_t launch_init_rest(const Sim &S, void *A, cudaStream_t st);
 cudaError_t launch_feq_to_staging(const Sim &S, float *staging, cudaStream_t st);
 cudaError_t launch_pull_to_staging(const Sim &S, const void *A, float *staging, bool dev, cudaStream_t st);
 cudaError_t launch_push_from_staging(const Sim &S, const float *staging, void *A, bool dev, cudaStream_t st);
+cudaError_t launch_slab_planes(const Sim &S, void *pop, void *buf, int x_first, int planes, bool to_buf,
+                               cudaStream_t st);
 // launch shape of the particle kernel: T threads per bead, clusters of C
 // blocks per realization, Nc beads per block
 struct MdShape {

@@ -87,3 +87,88 @@ def _device():
     if dist.get_backend() == "nccl":
         return torch.device("cuda", torch.cuda.current_device())
     return torch.device("cpu")
+
+
+# ---------------------------------------------------------------------------
+# One lattice over several handles: x-slabs (the paper's domain
+# decomposition, Sec. III, along x).  The library does the slab's work; these
+# functions only move the exchanged buffers between handles, in one process
+# (several slabs on one device, for tests) or over torch.distributed ranks.
+# ---------------------------------------------------------------------------
+def slab_partition(nx: int, world: int) -> list[tuple[int, int]]:
+    """(first plane, planes) of each of `world` slabs covering [0, nx), as
+    equal as possible; every slab holds at least 2 planes."""
+    if world < 1 or 2 * world > nx:
+        raise ValueError(f"cannot split {nx} planes into {world} slabs of at least 2")
+    base, extra = divmod(nx, world)
+    out, x0 = [], 0
+    for r in range(world):
+        w = base + (1 if r < extra else 0)
+        out.append((x0, w))
+        x0 += w
+    return out
+
+
+def slab_workload(w: dict, rank: int, world: int) -> dict:
+    """The workload dict of slab `rank` of `world` (the whole lattice's
+    parameters, plus the slab)."""
+    out = dict(w)
+    out["slab"] = slab_partition(w["nx"], world)[rank]
+    return out
+
+
+def slab_step_local(sims: list) -> None:
+    """One coupled step of slabs held in this process (in order of x, all on
+    one stream): gather, sum u_p, advance, pass the planes on, import."""
+    views = [s.slab_views() for s in sims]
+    for s in sims:
+        s.slab_gather()
+    up = views[0]["up"].clone()
+    for v in views[1:]:
+        up += v["up"]
+    for v in views:
+        v["up"].copy_(up)
+    for s in sims:
+        s.slab_advance()
+    n = len(sims)
+    for r, v in enumerate(views):
+        views[(r - 1) % n]["recv_hi"].copy_(v["send_lo"])
+        views[(r + 1) % n]["recv_lo"].copy_(v["send_hi"])
+    for s in sims:
+        s.slab_import()
+
+
+def exchange_slab_buffers(views: dict, rank: int, world: int, group=None) -> None:
+    """The collective part of a slab step over torch.distributed ranks (one
+    slab per rank, rank order = x order, periodic): the sum of u_p, then
+    send_lo to the left neighbour's recv_hi and send_hi to the right
+    neighbour's recv_lo.  With one rank the slab is its own neighbour."""
+    import torch.distributed as dist
+    if world == 1:
+        views["recv_hi"].copy_(views["send_lo"])
+        views["recv_lo"].copy_(views["send_hi"])
+        return
+    left, right = (rank - 1) % world, (rank + 1) % world
+    ops = [dist.P2POp(dist.isend, views["send_lo"], left, group, tag=0),
+           dist.P2POp(dist.irecv, views["recv_hi"], right, group, tag=0),
+           dist.P2POp(dist.isend, views["send_hi"], right, group, tag=1),
+           dist.P2POp(dist.irecv, views["recv_lo"], left, group, tag=1)]
+    for req in dist.batch_isend_irecv(ops):
+        req.wait()
+
+
+def allreduce_up(views: dict, world: int, group=None) -> None:
+    """Sum the u_p partials of all slabs in place (exact: one non-zero term
+    per bead)."""
+    import torch.distributed as dist
+    if world > 1:
+        dist.all_reduce(views["up"], group=group)
+
+
+def slab_step_dist(sim, views: dict, rank: int, world: int, group=None) -> None:
+    """One coupled step of this rank's slab."""
+    sim.slab_gather()
+    allreduce_up(views, world, group)
+    sim.slab_advance()
+    exchange_slab_buffers(views, rank, world, group)
+    sim.slab_import()

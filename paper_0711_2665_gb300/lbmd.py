@@ -42,7 +42,13 @@ class Config(ctypes.Structure):
                 ("wall_eps", ctypes.c_double), ("E", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("kT", ctypes.c_double), ("md_outer", ctypes.c_int32), ("md_inner", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("real_base", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("interp", ctypes.c_int32), ("integrator", ctypes.c_int32), ("lb_kT", ctypes.c_double)]
+                ("seed", ctypes.c_uint64), ("interp", ctypes.c_int32), ("integrator", ctypes.c_int32), ("lb_kT", ctypes.c_double),
+                ("slab_x0", ctypes.c_int32), ("slab_nx", ctypes.c_int32)]
+
+
+class SlabIO(ctypes.Structure):
+    _fields_ = [("up", ctypes.c_void_p), ("send_lo", ctypes.c_void_p), ("send_hi", ctypes.c_void_p),
+                ("recv_lo", ctypes.c_void_p), ("recv_hi", ctypes.c_void_p), ("plane_bytes", ctypes.c_size_t)]
 
 
 class Obs(ctypes.Structure):
@@ -133,6 +139,10 @@ def lib():
         "lbmd_adjoint_required_bytes": [vp, i32, i32, P(sz)],
         "lbmd_adjoint": [vp, i32, i32, vp, sz, vp, vp, vp, vp],
         "lbmd_philox4x32_10": [vp, vp, i64, vp],
+        "lbmd_slab_buffers": [vp, P(SlabIO)],
+        "lbmd_slab_gather": [vp],
+        "lbmd_slab_advance": [vp],
+        "lbmd_slab_import": [vp],
         "lbmd_noise_gauss3": [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, i64, i64, ctypes.c_uint32, vp, vp],
     }
     for name, args in sig.items():
@@ -200,6 +210,8 @@ def make_config(w: dict) -> Config:
     c.integrator = int(w.get("integrator", 0))
     c.lb_kT = float(w.get("lb_kT", 0.0))
     c.seed = int(w.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF
+    slab = w.get("slab")
+    c.slab_x0, c.slab_nx = (int(slab[0]), int(slab[1])) if slab else (0, 0)
     return c
 
 
@@ -218,11 +230,15 @@ class Simulation:
         self.cfg = make_config(params)
         self.device = torch.device(device)
         self.n_real = self.cfg.n_real
-        self.ns = self.cfg.nx * self.cfg.ny * self.cfg.nz
+        # x planes of this handle's populations: the lattice's, or a slab's
+        # own planes with one ghost plane on the left and two on the right
+        self.nx_local = self.cfg.slab_nx + 3 if self.cfg.slab_nx > 0 else self.cfg.nx
+        self.ns = self.nx_local * self.cfg.ny * self.cfg.nz
+        ns_all = self.cfg.nx * self.cfg.ny * self.cfg.nz
         self.offsets = np.ascontiguousarray(offsets, dtype=np.int32)
         self.total_beads = int(self.offsets[-1])
         solid = np.ascontiguousarray(solid, dtype=np.uint8).reshape(-1)
-        if solid.size != self.ns:
+        if solid.size != ns_all:
             raise ValueError("solid mask must have nx*ny*nz entries")
         r = np.ascontiguousarray(r_init, dtype=np.float64).reshape(-1)
         if r.size != 3 * self.total_beads:
@@ -349,20 +365,59 @@ class Simulation:
 
     # -- state -----------------------------------------------------------
     def init_fluid(self, rho=None, u=None):
+        """Equilibrium populations of rho (n_real, nz, ny, nx) and u (n_real,
+        3, nz, ny, nx) over this handle's planes (None: rho = 1, u = 0)."""
         r = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1) if rho is not None else None
         uu = np.ascontiguousarray(u, dtype=np.float64).reshape(-1) if u is not None else None
+        if r is not None and r.size != self.n_real * self.ns:
+            raise ValueError("rho must have n_real * sites entries")
+        if uu is not None and uu.size != 3 * self.n_real * self.ns:
+            raise ValueError("u must have 3 * n_real * sites entries")
         self._check(self._lib.lbmd_init_fluid(self._h, _ptr(r), _ptr(uu)), "lbmd_init_fluid")
 
     def get_populations(self) -> np.ndarray:
         f = np.empty(self.n_real * LBMD_Q * self.ns, dtype=np.float32)
         self._check(self._lib.lbmd_get_populations(self._h, _ptr(f)), "lbmd_get_populations")
-        return f.reshape(self.n_real, LBMD_Q, self.cfg.nz, self.cfg.ny, self.cfg.nx)
+        return f.reshape(self.n_real, LBMD_Q, self.cfg.nz, self.cfg.ny, self.nx_local)
 
     def get_deviations(self) -> np.ndarray:
         """f - w_i as stored (FP32), shape (n_real, 19, nz, ny, nx)."""
         f = np.empty(self.n_real * LBMD_Q * self.ns, dtype=np.float32)
         self._check(self._lib.lbmd_get_deviations(self._h, _ptr(f)), "lbmd_get_deviations")
-        return f.reshape(self.n_real, LBMD_Q, self.cfg.nz, self.cfg.ny, self.cfg.nx)
+        return f.reshape(self.n_real, LBMD_Q, self.cfg.nz, self.cfg.ny, self.nx_local)
+
+    # slab mode ------------------------------------------------------------
+    def slab_views(self) -> dict:
+        """Torch views into this handle's buffer of its slab exchange areas:
+        up (total_beads, 4) float32; send_lo, recv_hi (19, 2, nz, ny) and
+        send_hi, recv_lo (19, 1, nz, ny) in the population storage type."""
+        import torch
+        io = SlabIO()
+        self._check(self._lib.lbmd_slab_buffers(self._h, ctypes.byref(io)), "lbmd_slab_buffers")
+        base = self.buffer.data_ptr()
+        dt = torch.float16 if self.cfg.precision == FP16DEV else torch.float32
+        esz = 2 if dt == torch.float16 else 4
+        nz, ny = self.cfg.nz, self.cfg.ny
+
+        def view(ptr, nbytes, dtype, shape):
+            off = ptr - base
+            return self.buffer[off:off + nbytes].view(dtype).view(shape)
+        pb = io.plane_bytes
+        assert pb == LBMD_Q * ny * nz * esz
+        return {"up": view(io.up, 16 * max(self.total_beads, 1), torch.float32, (max(self.total_beads, 1), 4)),
+                "send_lo": view(io.send_lo, 2 * pb, dt, (LBMD_Q, 2, nz, ny)),
+                "send_hi": view(io.send_hi, pb, dt, (LBMD_Q, 1, nz, ny)),
+                "recv_lo": view(io.recv_lo, pb, dt, (LBMD_Q, 1, nz, ny)),
+                "recv_hi": view(io.recv_hi, 2 * pb, dt, (LBMD_Q, 2, nz, ny))}
+
+    def slab_gather(self):
+        self._check(self._lib.lbmd_slab_gather(self._h), "lbmd_slab_gather")
+
+    def slab_advance(self):
+        self._check(self._lib.lbmd_slab_advance(self._h), "lbmd_slab_advance")
+
+    def slab_import(self):
+        self._check(self._lib.lbmd_slab_import(self._h), "lbmd_slab_import")
 
     def set_deviations(self, h):
         """Load f - w_i (FP32), shape (n_real, 19, nz, ny, nx)."""

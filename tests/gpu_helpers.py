@@ -4,9 +4,10 @@ both, and compare populations as deviations h = f - w_i.
 
 Population tolerance (one step from one shared state, element by element):
 
-  |h_gpu - h_orc| <= 1e-5 max|h_orc|                     FP32 arithmetic
+  |h_gpu - h_orc| <= 1e-5 max|h_orc| + 1e-15             FP32 arithmetic
                    + 2^-11 |h_orc| + 2^-37                 FP16 storage only
                    + (8/6) 1e-5 max|J_orc|                 sites the beads touch
+                   + 2^-11 |h_orc|                         ... with FP16 storage
 
 FP32: the library stores h itself, so a step's rounding is relative to the
 deviations, not to w_i (a few 1e-7 of max|h| for the 19-term moment sums).
@@ -18,6 +19,9 @@ J_p over the corners of each bead's cell: |dS_i| <= 3 w_i |c_i|_1 max|dG| =
 max|dG| / 6 for every link, and a site is a corner of at most 8 beads'
 cells in these states, with |dJ| <= 1e-5 max|J| (the coupling tolerance).
 One streaming step later that error sits within one site of the corners.
+With FP16 storage the source pass loads, adds and stores the touched sites
+again: a second rounding there.  The 1e-15 is the oracle's own: it holds
+f = w_i + h in FP64, so h_orc carries the rounding of f near w_i <= 1/3.
 """
 import numpy as np
 
@@ -138,11 +142,14 @@ def near_bead_sites(r, dims, pad=0):
 
 def dev_tolerance(h_o, near=None, J_max=0.0, fp16=False):
     """Element-wise bound of one step (see the module docstring)."""
-    tol = np.full(h_o.shape, 1e-5 * np.abs(h_o).max())
+    tol = np.full(h_o.shape, 1e-5 * np.abs(h_o).max() + 1e-15)
     if fp16:
         tol += 2.0 ** -11 * np.abs(h_o) + 2.0 ** -37
-    if near is not None and J_max > 0.0:
-        tol = tol + (8.0 / 6.0) * 1e-5 * J_max * near[None]
+    if near is not None:
+        if J_max > 0.0:
+            tol = tol + (8.0 / 6.0) * 1e-5 * J_max * near[None]
+        if fp16:
+            tol = tol + 2.0 ** -11 * np.abs(h_o) * near[None]
     return tol
 
 

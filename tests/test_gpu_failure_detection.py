@@ -56,13 +56,18 @@ def test_neighbour_list_overflow_is_reported():
 
 
 def test_wall_list_overflow_is_reported():
-    """One bead at the centre site of a solid 3 x 3 x 3 block: 19 solid sites
-    (the centre, its 6 faces and 12 edges) lie within the wall-list radius
-    2^(1/6) + 0.3 = 1.42, more than the 12 a list holds."""
+    """One bead 0.004 from the centre site of a solid 3 x 3 x 3 block: 19
+    solid sites (the centre, its 6 faces and 12 edges, at squared distances
+    below 2.01) lie within the wall-list radius 2^(1/6) + 0.3 = 1.42 (squared
+    2.02), more than the 12 a list holds.  (Off the centre so that no
+    distance is zero: with eps = 0 the WCA term is 0 times a finite number.)"""
     solid = np.zeros((16, 16, 16), np.uint8)
     solid[6:9, 6:9, 6:9] = 1
+    r = np.array([[7.001, 7.002, 7.003]])
+    d2 = ((np.argwhere(solid)[:, ::-1] - r) ** 2).sum(1)
+    assert (d2 < (2 ** (1 / 6) + 0.3) ** 2).sum() == 19 and d2.min() > 1e-6
     w = _quiet(n_beads=1)
-    sim = lbmd.Simulation(w, solid, [0, 1], np.array([[7.0, 7.0, 7.0]]))
+    sim = lbmd.Simulation(w, solid, [0, 1], r)
     st, obs_st = _status_after(sim)
     assert st == CAPACITY and obs_st == CAPACITY
 

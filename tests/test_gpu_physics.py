@@ -38,30 +38,67 @@ def _shear_rate(sim, nx, n1=60, n2=400):
     return (a2 / a1) ** (1.0 / n2), a1
 
 
-class _OracleRun:
-    """The oracle's FP64 run seen through get_deviations; with fp16 set, each
-    step's deviations are stored as FP16 (h 2^12 rounded to the nearest FP16
-    value by numpy's IEEE conversion), as the FP16 storage mode does."""
+def _fp32_fp16_replica_rate(nx, ny, nz, tau, amp, n1=60, n2=400):
+    """The FP16 storage mode's arithmetic written out in numpy on a periodic
+    box without walls or beads: populations stored as FP16 values of
+    h 2^12, every step pulled, collided in FP32 in the kernel's order (moments
+    from opposite-link sums and differences, BGK in even/odd form) and
+    rounded to FP16 again.  Returns the shear-wave decay factor per step."""
+    c, wts, _ = oracle.tables()
+    f32 = np.float32
+    up, down = f32(4096.0), f32(1.0 / 4096.0)
+    om = f32(1.0 / tau)
+    wq = wts.astype(f32)
+    orc = oracle.OracleSim(dict(nx=nx, ny=ny, nz=nz, tau=tau))
+    orc.init_fluid(None, inputs.shear_wave_velocity(nx, ny, nz, amp))
+    st = ((orc.get_populations() - wts[:, None, None, None]) * 4096.0).astype(np.float16)
 
-    def __init__(self, orc, fp16=False):
-        self.orc, self.fp16 = orc, fp16
-        _, self.w, _ = oracle.tables()
+    def pull(a):
+        return np.stack([np.roll(a[i], shift=(c[i, 2], c[i, 1], c[i, 0]), axis=(0, 1, 2)) for i in range(19)])
 
-    def _h(self):
-        return self.orc.get_populations() - self.w[:, None, None, None]
+    def amp_of(h16):
+        return _mode_amp((h16.astype(np.float64) / 4096.0), nx)
 
-    def _round(self):
-        h = (self._h() * 4096.0).astype(np.float16).astype(np.float64) / 4096.0
-        self.orc.set_populations(self.w[:, None, None, None] + h)
+    a1 = None
+    for n in range(n1 + n2):
+        h = (st if n == 0 else pull(st)).astype(f32)
+        drs = h[0].copy()
+        j = np.zeros((3,) + h.shape[1:], f32)
+        for i in range(1, 19, 2):
+            sp, dp = h[i] + h[i + 1], h[i] - h[i + 1]
+            drs = drs + sp
+            for a in range(3):
+                if c[i, a] == 1:
+                    j[a] = j[a] + dp
+                elif c[i, a] == -1:
+                    j[a] = j[a] - dp
+        drho = drs * down
+        j = j * down
+        rho = f32(1.0) + drho
+        ir = f32(1.0) / rho
+        u = j * ir
+        usq = f32(1.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2])
+        rs = rho * up
+        out = np.empty_like(h)
+        out[0] = h[0] + om * (wq[0] * (drs - rs * usq) - h[0])
+        for i in range(1, 19, 2):
+            cu = f32(3.0) * (f32(c[i, 0]) * u[0] + f32(c[i, 1]) * u[1] + f32(c[i, 2]) * u[2])
+            even = drs + rs * (f32(0.5) * cu * cu - usq)
+            odd = rs * cu
+            out[i] = h[i] + om * (wq[i] * (even + odd) - h[i])
+            out[i + 1] = h[i + 1] + om * (wq[i] * (even - odd) - h[i + 1])
+        st = out.astype(np.float16)
+        if n + 1 == n1:
+            a1 = amp_of(pull(st))
+    return (amp_of(pull(st)) / a1) ** (1.0 / n2)
 
-    def step(self, n):
-        for _ in range(n):
-            self.orc.step(1)
-            if self.fp16:
-                self._round()
 
-    def get_deviations(self):
-        return self._h()[None]
+def _mode_amp(h, nx):
+    c, _, _ = oracle.tables()
+    s = np.sin(2 * np.pi * np.arange(nx) / nx)
+    rho = 1.0 + h.sum(0)
+    uy = np.einsum("izyx,i->zyx", h, c[:, 1].astype(float)) / rho
+    return 2.0 / nx * float(uy.mean(axis=(0, 1)) @ s)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp16dev"])
@@ -70,15 +107,18 @@ def test_shear_wave_decay(precision):
     oracle's FP64 run (itself pinned to the linearised-LBGK eigenvalue).
 
     FP32: |r_gpu - r_orc| <= 2e-5 (1 - r_orc).
-    FP16 deviations: against an oracle run that stores its deviations as FP16
-    each step (the same storage rule in FP64 arithmetic), |dr| <= 2e-4 (1 - r)
-    (a few storage roundings flip where the FP32 and FP64 values straddle an
-    FP16 midpoint).  Against the plain FP64 run the worst case is derived:
-    storage moves each stored deviation by at most 2^-11 |h|, and for a shear
-    wave h_i = 3 w_i c_iy u_y, so the wave's projected amplitude moves by at
-    most 2^-11 of itself per step (sum_i 3 w_i c_iy^2 = 1), and so does r:
-    |r_fp16 - r_fp64| <= 2^-11 (13% of this wave's 1 - r = 3.85e-3); the
-    measured error is reported in the design notes."""
+
+    FP16 deviations, derived worst case: storage moves each stored deviation
+    by at most 2^-11 |h|; for a shear wave h_i = 3 w_i c_iy u_y, so the
+    wave's projected amplitude moves by at most 2^-11 of itself per step
+    (sum_i 3 w_i c_iy^2 = 1), and so does r: |r_fp16 - r_fp64| <= 2^-11 (13%
+    of this wave's 1 - r = 3.85e-3; measured 0.39%).  Of that 0.39%, FP16
+    storage under exact arithmetic gives 0.28% (an FP64 oracle run whose
+    deviations are rounded to FP16 after every step); the rest comes from the
+    FP32 roundings of the collision, which the storage rounding does not
+    average out.  So the GPU is also held to a numpy replica of FP32
+    arithmetic + FP16 storage: |r_gpu - r_replica| <= 2e-4 (1 - r) (the
+    kernel fuses multiply-adds where numpy rounds twice; measured 0)."""
     nx, tau = 32, 0.8
     sim = _fluid_only(nx, 4, 4, tau, precision=precision)
     u0 = inputs.shear_wave_velocity(nx, 4, 4, 1e-3)
@@ -86,17 +126,19 @@ def test_shear_wave_decay(precision):
     rate_g, _ = _shear_rate(sim, nx)
     orc = oracle.OracleSim(dict(nx=nx, ny=4, nz=4, tau=tau))
     orc.init_fluid(None, u0)
-    rate_o, _ = _shear_rate(_OracleRun(orc), nx)
+    _, wts, _ = oracle.tables()
+
+    class _O:
+        def step(self, n): orc.step(n)
+        def get_deviations(self): return (orc.get_populations() - wts[:, None, None, None])[None]
+
+    rate_o, _ = _shear_rate(_O(), nx)
     if precision == "fp32":
         assert abs(rate_g - rate_o) <= 2e-5 * (1 - rate_o), (rate_g, rate_o)
         return
     assert abs(rate_g - rate_o) <= 2.0 ** -11, (rate_g, rate_o)
-    orc16 = oracle.OracleSim(dict(nx=nx, ny=4, nz=4, tau=tau))
-    orc16.init_fluid(None, u0)
-    run16 = _OracleRun(orc16, fp16=True)
-    run16._round()  # the initial state as FP16 storage holds it
-    rate_16, _ = _shear_rate(run16, nx)
-    assert abs(rate_g - rate_16) <= 2e-4 * (1 - rate_16), (rate_g, rate_16, rate_o)
+    rate_r = _fp32_fp16_replica_rate(nx, 4, 4, tau, 1e-3)
+    assert abs(rate_g - rate_r) <= 2e-4 * (1 - rate_r), (rate_g, rate_r, rate_o)
 
 
 def test_poiseuille_curvature_fp32():
