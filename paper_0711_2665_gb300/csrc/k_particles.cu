@@ -690,6 +690,48 @@ __device__ __forceinline__ void list_insert(uint16_t *lst, int &n, int q) {
     ++n;
 }
 
+// |d|^2 < r2 with every product and sum rounded on its own (no fused
+// multiply-add), so that each list build decides a pair the same way
+__device__ __forceinline__ bool within2(float dx, float dy, float dz, float r2) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)) < r2;
+}
+
+// Solid sites within the wall-list radius of a bead at wrapped (xw, yw, zw),
+// packed as x | y << 12 | z << 22 into wal (at most WALL_CAP of them, in the
+// order of the 4x4x4 box's bits); returns how many there are.
+__device__ __forceinline__ int wall_list(const Sim &S, float xw, float yw, float zw, uint32_t *wal) {
+    int m = 0;
+    const int cx0 = (int)floorf(xw), cy0 = (int)floorf(yw), cz0 = (int)floorf(zw);
+    if (S.rlw < 2.0f) {
+        // every site within rlw < 2 of the bead lies in the 4x4x4 box starting
+        // one site below its cell corner; its solid sites are one bit mask
+        unsigned long long mm = __ldg(S.bwallmask + cx0 + S.bnx * (cy0 + S.ny * cz0));
+        while (mm) {
+            const int bit = __ffsll((long long)mm) - 1;
+            mm &= mm - 1;
+            const int X = cx0 + (bit & 3) - 1, Y = cy0 + ((bit >> 2) & 3) - 1, Z = cz0 + (bit >> 4) - 1;
+            if (!within2(xw - (float)X, yw - (float)Y, zw - (float)Z, S.rlw2)) continue;
+            const int xx = wrapi(X, S.bnx), yy = wrapi(Y, S.ny), zz = wrapi(Z, S.nz);
+            if (m < WALL_CAP) wal[m] = (uint32_t)xx | ((uint32_t)yy << 12) | ((uint32_t)zz << 22);
+            ++m;
+        }
+    } else if (__ldg(S.blink + cx0 + S.bnx * (cy0 + S.ny * cz0)) & NEAR_SOLID_BIT) {
+        const int x0 = (int)floorf(xw - S.rlw), x1 = (int)floorf(xw + S.rlw);
+        const int y0 = (int)floorf(yw - S.rlw), y1 = (int)floorf(yw + S.rlw);
+        const int z0 = (int)floorf(zw - S.rlw), z1 = (int)floorf(zw + S.rlw);
+        for (int Z = z0; Z <= z1; ++Z)
+            for (int Y = y0; Y <= y1; ++Y)
+                for (int X = x0; X <= x1; ++X) {
+                    const int xx = wrap_any(X, S.bnx), yy = wrap_any(Y, S.ny), zz = wrap_any(Z, S.nz);
+                    if (!(__ldg(S.blink + xx + S.bnx * (yy + S.ny * zz)) & SOLID_BIT)) continue;
+                    if (!within2(xw - (float)X, yw - (float)Y, zw - (float)Z, S.rlw2)) continue;
+                    if (m < WALL_CAP) wal[m] = (uint32_t)xx | ((uint32_t)yy << 12) | ((uint32_t)zz << 22);
+                    ++m;
+                }
+    }
+    return m;
+}
+
 __device__ __forceinline__ void cell_of(const Sim &S, float xw, float yw, float zw, int &ci, int &cj, int &ck) {
     ci = min((int)(xw * S.cell_per_site[0]), S.ncell[0] - 1);
     cj = min((int)(yw * S.cell_per_site[1]), S.ncell[1] - 1);
@@ -725,7 +767,7 @@ __device__ __forceinline__ int scan_pairs(const Sim &S, const float4 *ph, const 
         const float4 qh = ph[qq], ql = plo[qq];
         const float dx = ff_diff(mh.x, ml.x, qh.x, ql.x, fnx, S.binx), dy = ff_diff(mh.y, ml.y, qh.y, ql.y, fny, S.iny),
                     dz = ff_diff(mh.z, ml.z, qh.z, ql.z, fnz, S.inz);
-        const bool hit = own && q < N && (q < p - 1 || q > p + 1) && dx * dx + dy * dy + dz * dz < S.rl2;
+        const bool hit = own && q < N && (q < p - 1 || q > p + 1) && within2(dx, dy, dz, S.rl2);
         const unsigned g = (__ballot_sync(0xffffffffu, hit) >> gshift) & gmask;
         if (hit) {
             const int pos = n + __popc(g & below);
@@ -734,6 +776,37 @@ __device__ __forceinline__ int scan_pairs(const Sim &S, const float4 *ph, const 
         n += __popc(g);
     }
     return n;
+}
+
+// The block's halo for the pull exchange, from the lists of its beads in
+// shared memory: the beads of other blocks (rank != this block's) in its
+// beads' pair lists or within two bonds of them, in no particular order, each
+// with the chain rank of its block in bits 16 and up, their count in *nhalo.
+// Called by every thread of the block; ends with a block barrier.
+template <int T>
+__device__ __forceinline__ void build_halo(const PSmem &sm, int N, int p, int pl, bool own, int rank, int Nc,
+                                           int *nhalo) {
+    for (int q = threadIdx.x; q < N; q += blockDim.x) sm.mark[q] = 0;
+    if (threadIdx.x == 0) *nhalo = 0;
+    __syncthreads();
+    if (own) {
+        const int lt = threadIdx.x % T;
+        const uint16_t *lst = sm.nbr + pl * NBR_CAP;
+        const int n = sm.nn[pl];
+        for (int k = lt; k < n; k += T) {
+            const int q = lst[k];
+            if (q / Nc != rank) sm.mark[q] = 1;
+        }
+        if (lt == 0)
+            for (int d = -2; d <= 2; ++d) {
+                const int q = p + d;
+                if (q >= 0 && q < N && q / Nc != rank) sm.mark[q] = 1;
+            }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < N; q += blockDim.x)
+        if (sm.mark[q]) sm.halo[atomicAdd(nhalo, 1)] = (uint32_t)q | ((uint32_t)(q / Nc) << 16);
+    __syncthreads();
 }
 
 // Bead-bead and bead-wall lists of the block's beads from replica buf.
@@ -782,7 +855,7 @@ __device__ __forceinline__ void build_lists_body(const Sim &S, const PSmem &sm, 
             const float4 qh = ph[q], ql = plo[q];
             const float dx = ff_diff(mh.x, ml.x, qh.x, ql.x, fnx, S.binx), dy = ff_diff(mh.y, ml.y, qh.y, ql.y, fny, S.iny),
                         dz = ff_diff(mh.z, ml.z, qh.z, ql.z, fnz, S.inz);
-            if (dx * dx + dy * dy + dz * dz < S.rl2) list_insert(lst, n, q);
+            if (within2(dx, dy, dz, S.rl2)) list_insert(lst, n, q);
         };
         if (brute) {
             // done by scan_pairs
@@ -812,64 +885,61 @@ __device__ __forceinline__ void build_lists_body(const Sim &S, const PSmem &sm, 
         if (n > NBR_CAP) { atomicOr(s_err, ST_CAPACITY); n = NBR_CAP; }
         sm.nn[pl] = (uint8_t)n;
         // solid sites within the wall-list radius
-        int m = 0;
-        const int cx0 = (int)floorf(xw), cy0 = (int)floorf(yw), cz0 = (int)floorf(zw);
-        if (S.rlw < 2.0f) {
-            // every site within rlw < 2 of the bead lies in the 4x4x4 box starting
-            // one site below its cell corner; its solid sites are one bit mask
-            unsigned long long mm = __ldg(S.bwallmask + cx0 + S.bnx * (cy0 + S.ny * cz0));
-            while (mm) {
-                const int bit = __ffsll((long long)mm) - 1;
-                mm &= mm - 1;
-                const int X = cx0 + (bit & 3) - 1, Y = cy0 + ((bit >> 2) & 3) - 1, Z = cz0 + (bit >> 4) - 1;
-                const float dx = xw - (float)X, dy = yw - (float)Y, dz = zw - (float)Z;
-                if (dx * dx + dy * dy + dz * dz >= S.rlw2) continue;
-                const int xx = wrapi(X, S.bnx), yy = wrapi(Y, S.ny), zz = wrapi(Z, S.nz);
-                if (m < WALL_CAP) sm.wal[pl * WALL_CAP + m] = (uint32_t)xx | ((uint32_t)yy << 12) | ((uint32_t)zz << 22);
-                ++m;
-            }
-        } else if (__ldg(S.blink + cx0 + S.bnx * (cy0 + S.ny * cz0)) & NEAR_SOLID_BIT) {
-            const int x0 = (int)floorf(xw - S.rlw), x1 = (int)floorf(xw + S.rlw);
-            const int y0 = (int)floorf(yw - S.rlw), y1 = (int)floorf(yw + S.rlw);
-            const int z0 = (int)floorf(zw - S.rlw), z1 = (int)floorf(zw + S.rlw);
-            for (int Z = z0; Z <= z1; ++Z)
-                for (int Y = y0; Y <= y1; ++Y)
-                    for (int X = x0; X <= x1; ++X) {
-                        const int xx = wrap_any(X, S.bnx), yy = wrap_any(Y, S.ny), zz = wrap_any(Z, S.nz);
-                        if (!(__ldg(S.blink + xx + S.bnx * (yy + S.ny * zz)) & SOLID_BIT)) continue;
-                        const float dx = xw - (float)X, dy = yw - (float)Y, dz = zw - (float)Z;
-                        if (dx * dx + dy * dy + dz * dz >= S.rlw2) continue;
-                        if (m < WALL_CAP) sm.wal[pl * WALL_CAP + m] = (uint32_t)xx | ((uint32_t)yy << 12) | ((uint32_t)zz << 22);
-                        ++m;
-                    }
-        }
+        int m = wall_list(S, xw, yw, zw, sm.wal + pl * WALL_CAP);
         if (m > WALL_CAP) { atomicOr(s_err, ST_CAPACITY); m = WALL_CAP; }
         sm.nw[pl] = (uint8_t)m;
     }
     __syncthreads();
-    if (halo) {
-        for (int q = threadIdx.x; q < N; q += blockDim.x) sm.mark[q] = 0;
-        if (threadIdx.x == 0) *nhalo = 0;
-        __syncthreads();
-        if (own) {
-            const int lt = threadIdx.x % T;
-            const uint16_t *lst = sm.nbr + pl * NBR_CAP;
-            const int n = sm.nn[pl];
-            for (int k = lt; k < n; k += T) {
-                const int q = lst[k];
-                if (q / Nc != rank) sm.mark[q] = 1;
-            }
-            if (lt == 0)
-                for (int d = -2; d <= 2; ++d) {
-                    const int q = p + d;
-                    if (q >= 0 && q < N && q / Nc != rank) sm.mark[q] = 1;
-                }
+    if (halo) build_halo<T>(sm, N, p, pl, own, rank, Nc, nhalo);
+}
+
+// ---------------------------------------------------------------------------
+// The starting Verlet lists of a step for every bead of every chain, one
+// warp per bead over the whole GPU: the warp's 32 lanes test 32 beads of the
+// chain at a time in ascending order and a ballot compacts the hits, so each
+// list comes out sorted, as the block builds make it; lane 0 adds the solid
+// sites within the wall-list radius.  It reads the positions the step starts
+// from and runs beside the gather, so the particle kernel only copies its
+// beads' lists.  Overflows latch the capacity status.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_lists(const Sim S) {
+    const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // warp-uniform
+    if (g >= S.total_beads) return;
+    const int lane = threadIdx.x & 31;
+    const int r = S.bead_real[g];
+    const int off = S.bead_off[r], N = S.bead_off[r + 1] - off, p = g - off;
+    const float fnx = (float)S.bnx, fny = (float)S.ny, fnz = (float)S.nz;
+    const float4 mh = S.r_hi[g], ml = S.r_lo[g];
+    uint16_t *lst = S.nbr_g + (size_t)g * NBR_CAP;
+    int n = 0;
+    for (int base = 0; base < N; base += 32) {
+        const int q = base + lane;
+        const int qq = q < N ? q : p;
+        const float4 qh = S.r_hi[off + qq], ql = S.r_lo[off + qq];
+        const float dx = ff_diff(mh.x, ml.x, qh.x, ql.x, fnx, S.binx), dy = ff_diff(mh.y, ml.y, qh.y, ql.y, fny, S.iny),
+                    dz = ff_diff(mh.z, ml.z, qh.z, ql.z, fnz, S.inz);
+        const bool hit = q < N && (q < p - 1 || q > p + 1) && within2(dx, dy, dz, S.rl2);
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+            const int pos = n + __popc(bal & ((1u << lane) - 1u));
+            if (pos < NBR_CAP) lst[pos] = (uint16_t)q;
         }
-        __syncthreads();
-        for (int q = threadIdx.x; q < N; q += blockDim.x)
-            if (sm.mark[q]) sm.halo[atomicAdd(nhalo, 1)] = (uint32_t)q | ((uint32_t)(q / Nc) << 16);
-        __syncthreads();
+        n += __popc(bal);
     }
+    if (lane == 0) {
+        const int m = wall_list(S, ff_wrap(mh.x, ml.x, fnx, S.binx), ff_wrap(mh.y, ml.y, fny, S.iny),
+                                ff_wrap(mh.z, ml.z, fnz, S.inz), S.wal_g + (size_t)g * WALL_CAP);
+        if (n > NBR_CAP || m > WALL_CAP) atomicOr(&S.ctrl->status, ST_CAPACITY);
+        S.nn_g[g] = min(n, NBR_CAP);
+        S.nw_g[g] = min(m, WALL_CAP);
+    }
+}
+
+cudaError_t launch_lists(const Sim &S, cudaStream_t st) {
+    if (S.total_beads == 0) return cudaSuccess;
+    const int threads = 256;
+    k_lists<<<(S.total_beads * 32 + threads - 1) / threads, threads, 0, st>>>(S);
+    return cudaGetLastError();
 }
 
 // The list build, called out of line or inlined.  Out of line, the rare
@@ -1005,7 +1075,19 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
     // block writes into another's shared memory
     sync_all(cl, C);
     phase_mark(S, 0, tclk);
-    build_lists<T, BWM>(S, sm, 0, N, p, pl, own, rank, Nc, pull, nullptr, &s_err, &s_nhalo);
+    // the block's beads' starting lists, built by k_lists, and the halo
+    if (own) {
+        const size_t g = (size_t)(off + p);
+        const int n = S.nn_g[g], m = S.nw_g[g];
+        for (int k = lt; k < n; k += T) sm.nbr[pl * NBR_CAP + k] = S.nbr_g[g * NBR_CAP + k];
+        for (int k = lt; k < m; k += T) sm.wal[pl * WALL_CAP + k] = S.wal_g[g * WALL_CAP + k];
+        if (lt == 0) {
+            sm.nn[pl] = (uint8_t)n;
+            sm.nw[pl] = (uint8_t)m;
+        }
+    }
+    __syncthreads();
+    if (pull) build_halo<T>(sm, N, p, pl, own, rank, Nc, &s_nhalo);
     phase_mark(S, 1, tclk);
 
     // MD cycle

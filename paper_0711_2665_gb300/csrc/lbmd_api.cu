@@ -17,15 +17,17 @@ using namespace lbmd;
 namespace {
 
 constexpr int K_GATHER = 0, K_PARTICLES = 1, K_STREAM_COLLIDE = 2, K_SOURCE = 3, K_SC_ADJOINT = 4,
-              K_BEAD_ADJOINT = 5, K_ADJ_FIXUP = 6, K_BEAD_DIAG = 7, K_COUNT = 8;
-const char *KNAMES[K_COUNT] = {"gather", "particles", "stream_collide", "source", "sc_adjoint", "bead_adjoint",
-                               "adj_fixup", "bead_diag"};
+              K_BEAD_ADJOINT = 5, K_ADJ_FIXUP = 6, K_BEAD_DIAG = 7, K_LISTS = 8, K_COUNT = 9;
+const char *KNAMES[] = {"gather", "particles", "stream_collide", "source", "sc_adjoint", "bead_adjoint",
+                               "adj_fixup", "bead_diag", "lists"};
+static_assert(sizeof(KNAMES) / sizeof(KNAMES[0]) == K_COUNT, "one name per kernel");
 constexpr double SKIN = 0.6;  // Verlet-list skin (lattice units); 0.4 and 0.8 measured slower
 
 struct Layout {
     size_t blink, bwallmask, xsend_lo, xsend_hi, xrecv_lo, xrecv_hi;  // slab mode only (else 0)
     size_t popA, popB, staging, link, wallmask, tileflag, solid, G, stamp;
     size_t r_hi, r_lo, v, up, J, pair_node, pair_w, bead_real, bead_off, bsnap, fsum, ring, obs, tl, ctrl, loopc, snap, md_map, phase, total;
+    size_t nbr_g, wal_g, nn_g, nw_g;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -48,7 +50,7 @@ struct lbmd_handle {
     std::vector<int32_t> offsets;
     int total_beads = 0;
     cudaStream_t st = nullptr, aux = nullptr, aux2 = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr, ev_pre = nullptr;
     int by = 8, zc = 8;
     bool overlap = true;  // particle kernel concurrent with the lattice pass
     bool md_fixed = false;  // particle-kernel shape set by the caller (the autotuner leaves it)
@@ -175,6 +177,10 @@ Layout layout_of(const lbmd_config *c, int total_beads) {
     // shape's (autotuner); at most one cluster of MAX_CLUSTER blocks per chain
     L.md_map = take(2 * (size_t)c->n_real * MAX_CLUSTER * sizeof(int4));
     L.phase = take(PHASES * sizeof(unsigned long long));
+    L.nbr_g = take(nb * NBR_CAP * 2);
+    L.wal_g = take(nb * WALL_CAP * 4);
+    L.nn_g = take(nb * 4);
+    L.nw_g = take(nb * 4);
     L.blink = L.bwallmask = L.xsend_lo = L.xsend_hi = L.xrecv_lo = L.xrecv_hi = 0;
     if (c->slab_nx > 0) {  // the whole lattice's geometry for the beads; the exchanged planes
         const size_t gns = (size_t)c->nx * c->ny * c->nz;
@@ -288,8 +294,20 @@ lbmd_status upload_md_map(lbmd_handle *h, Sim &S, int region) {
 // behind the lattice pass's traffic), then the particle kernel (aux stream)
 // and the bead diagnostics (aux2) run concurrently with the stream-collide
 // kernel (main), then the source, which also completes the diagnostics row.
+// Kernels a coupled step launches: the list build and the gather, then the
+// particle kernel, the bead diagnostics, the lattice pass and the source.
+long long step_launches(const lbmd_handle *h) { return h->total_beads > 0 ? 6 : 2; }
+
 lbmd_status enqueue_gather(lbmd_handle *h) {
     if (h->total_beads > 0) {
+        // the step's starting Verlet lists on the particle stream, beside the
+        // gather (the particle kernel follows them there)
+        CK(cudaEventRecord(h->ev_pre, h->st));
+        CK(cudaStreamWaitEvent(h->aux, h->ev_pre, 0));
+        {
+            ProfScope ps(h, K_LISTS, h->aux);
+            CK(launch_lists(h->S, h->aux));
+        }
         ProfScope ps(h, K_GATHER, h->st);
         CK(launch_gather(h->S, h->popA, h->st));
     }
@@ -325,7 +343,7 @@ lbmd_status enqueue_advance(lbmd_handle *h) {
     }
     std::swap(h->popA, h->popB);
     h->host_step += 1;
-    h->launches += h->total_beads > 0 ? 5 : 3;
+    h->launches += step_launches(h);
     if (h->pending.size() > 30000) return resolve_profile(h);
     return LBMD_OK;
 }
@@ -623,6 +641,7 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join2, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_pre, cudaEventDisableTiming);
         if (e != cudaSuccess) { cuda_fail(h, e, "stream/event creation"); return bail(LBMD_ERR_CUDA); }
     }
     const Layout &L = h->L;
@@ -764,6 +783,10 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
     S.bead_off = (const int *)(b + L.bead_off);
     S.bsnap = (float4 *)(b + L.bsnap);
     S.md_map = (const int4 *)(b + L.md_map);
+    S.nbr_g = (uint16_t *)(b + L.nbr_g);
+    S.wal_g = (uint32_t *)(b + L.wal_g);
+    S.nn_g = (int *)(b + L.nn_g);
+    S.nw_g = (int *)(b + L.nw_g);
     S.md_clusters = 0;
     S.fsum = (long long *)(b + L.fsum);
     S.ring = (lbmd_diag *)(b + L.ring);
@@ -832,7 +855,7 @@ lbmd_status lbmd_step(lbmd_handle *h, int64_t n) {
             if (h->popA == h->graph_A) {
                 CK(cudaGraphLaunch(h->gexec, h->st));
                 h->host_step += h->graph_steps;
-                h->launches += (h->total_beads > 0 ? 5LL : 3LL) * h->graph_steps;
+                h->launches += step_launches(h) * h->graph_steps;
                 n -= h->graph_steps;
                 continue;
             }
@@ -865,7 +888,7 @@ lbmd_status lbmd_step_loop(lbmd_handle *h, int64_t n) {
         CK(cudaGetLastError());
         CK(cudaGraphLaunch(h->lexec, h->st));
         h->host_step += 2 * pairs;
-        h->launches += 1 + (2LL * (h->total_beads > 0 ? 5 : 3) + 1) * pairs;
+        h->launches += 1 + (2LL * step_launches(h) + 1) * pairs;
     }
     if (n & 1) return enqueue_step(h);
     return LBMD_OK;
@@ -1444,6 +1467,7 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
         for (int pass = 0; pass < 2; ++pass) {
             CKT(cudaEventRecord(a, h->st));
             for (int k = 0; k < reps; ++k) {
+                CKT(launch_lists(trial, h->st));
                 CKT(launch_gather(trial, h->popA, h->st));
                 CKT(cudaEventRecord(h->ev_fork, h->st));
                 CKT(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
@@ -1456,7 +1480,7 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
             CKT(cudaEventRecord(b, h->st));
             CKT(cudaEventSynchronize(b));
             CKT(cudaEventElapsedTime(&ms, a, b));
-            h->launches += 3LL * reps;
+            h->launches += 4LL * reps;
         }
 #undef CKT
         return cudaSuccess;
@@ -1616,6 +1640,7 @@ void lbmd_destroy(lbmd_handle *h) {
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->ev_join2) cudaEventDestroy(h->ev_join2);
+    if (h->ev_pre) cudaEventDestroy(h->ev_pre);
     if (h->aux) cudaStreamDestroy(h->aux);
     if (h->aux2) cudaStreamDestroy(h->aux2);
     delete h;

@@ -213,6 +213,12 @@ struct Sim {
     lbmd_transloc *tl;       // [n_real] translocation records
     Ctrl *ctrl;
     unsigned long long *phase;  // [PHASES] SM cycles per particle-kernel phase, or null
+    // The step's starting Verlet lists (k_lists), per bead: bead-bead pairs
+    // within the list radius in ascending order, and solid sites within the
+    // wall-list radius
+    uint16_t *nbr_g;         // [total_beads][NBR_CAP]
+    uint32_t *wal_g;         // [total_beads][WALL_CAP] packed x | y << 12 | z << 22
+    int *nn_g, *nw_g;        // [total_beads] list lengths
     // Trajectory record of the MD cycle for the adjoint, or null:
     // traj[slot * total_beads + bead] with the slots of traj_slot_* below
     float4 *traj;
@@ -439,6 +445,8 @@ struct MdShape {
 };
 MdShape md_shape(const Sim &S);
 cudaError_t launch_gather(const Sim &S, const void *A, cudaStream_t st);
+// the step's starting Verlet lists, for the particle kernel that follows
+cudaError_t launch_lists(const Sim &S, cudaStream_t st);
 cudaError_t launch_bead_diag(const Sim &S, cudaStream_t st);
 cudaError_t launch_particles(const Sim &S, const void *A, cudaStream_t st);
 // clusters of the particle kernel's shape for S that can be resident at once

@@ -117,23 +117,46 @@ def slab_workload(w: dict, rank: int, world: int) -> dict:
     return out
 
 
+def _join(streams, into):
+    """Make stream `into` wait for the work queued so far on `streams`."""
+    import torch
+    for st in streams:
+        if st != into:
+            ev = torch.cuda.Event()
+            ev.record(st)
+            into.wait_event(ev)
+
+
 def slab_step_local(sims: list) -> None:
-    """One coupled step of slabs held in this process (in order of x, all on
-    one stream): gather, sum u_p, advance, pass the planes on, import."""
+    """One coupled step of slabs held in this process (in order of x):
+    gather, sum u_p, advance, pass the planes on, import.  The copies run on
+    the first slab's stream, ordered by events against every slab's own
+    stream."""
+    import torch
     views = [s.slab_views() for s in sims]
+    streams = [s.stream for s in sims]
+    tr = streams[0]
     for s in sims:
         s.slab_gather()
-    up = views[0]["up"].clone()
-    for v in views[1:]:
-        up += v["up"]
-    for v in views:
-        v["up"].copy_(up)
+    _join(streams, tr)
+    with torch.cuda.stream(tr):
+        up = views[0]["up"].clone()
+        for v in views[1:]:
+            up += v["up"]
+        for v in views:
+            v["up"].copy_(up)
+    for st in streams:
+        _join([tr], st)
     for s in sims:
         s.slab_advance()
+    _join(streams, tr)
     n = len(sims)
-    for r, v in enumerate(views):
-        views[(r - 1) % n]["recv_hi"].copy_(v["send_lo"])
-        views[(r + 1) % n]["recv_lo"].copy_(v["send_hi"])
+    with torch.cuda.stream(tr):
+        for r, v in enumerate(views):
+            views[(r - 1) % n]["recv_hi"].copy_(v["send_lo"])
+            views[(r + 1) % n]["recv_lo"].copy_(v["send_hi"])
+    for st in streams:
+        _join([tr], st)
     for s in sims:
         s.slab_import()
 
@@ -166,9 +189,12 @@ def allreduce_up(views: dict, world: int, group=None) -> None:
 
 
 def slab_step_dist(sim, views: dict, rank: int, world: int, group=None) -> None:
-    """One coupled step of this rank's slab."""
-    sim.slab_gather()
-    allreduce_up(views, world, group)
-    sim.slab_advance()
-    exchange_slab_buffers(views, rank, world, group)
-    sim.slab_import()
+    """One coupled step of this rank's slab; the collectives run on the
+    slab's own stream, in order with its kernels."""
+    import torch
+    with torch.cuda.stream(sim.stream):
+        sim.slab_gather()
+        allreduce_up(views, world, group)
+        sim.slab_advance()
+        exchange_slab_buffers(views, rank, world, group)
+        sim.slab_import()

@@ -17,6 +17,9 @@ ensemble into the paper's statistics:
 Histogram bins follow the Freedman-Diaconis rule unless given: the paper
 does not state its binning.  `run` drives one ensemble on the GPU;
 ``python -m paper_0711_2665_gb300.transloc`` prints its summary as JSON.
+`precision_run` (``--precision-study WORKLOAD``) runs one chain in FP32 and
+in FP16 population storage from the same seed and noise streams and reports
+both translocation times.
 """
 from __future__ import annotations
 
@@ -139,6 +142,44 @@ def run(lengths, copies: int, max_steps: int, chunk: int = 200, overrides: dict 
             "mlups": sites * steps / wall / 1e6, "workload": w}
 
 
+def precision_run(name: str = "lattice_4m_fp32", precisions=("fp32", "fp16dev"), seed: int | None = None,
+                  max_steps: int = 20000, chunk: int = 1000, every: int = 100, autotune: bool = True) -> dict:
+    """One chain on one lattice, run from the same seeded start with the same
+    noise streams in each population storage precision: its translocation
+    time t_X (Sec. IV.A; -1 if the event has not completed in max_steps) and
+    the translocated fraction of the chain every `every` steps, read from the
+    per-step diagnostics rows."""
+    from . import lbmd, workloads
+    out = {}
+    for prec in precisions:
+        ov = {"precision": prec}
+        if seed is not None:
+            ov.update(seed=seed, chain_seed=seed)
+        w = workloads.get(name, **ov)
+        inp = workloads.build_inputs(w)
+        n_beads = int(inp["offsets"][1])
+        sim = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"])
+        if autotune:
+            sim.autotune(3)
+        sim.reset_translocation()
+        frac, steps, t0 = [], 0, time.perf_counter()
+        rec = sim.translocation()[0]
+        while steps < max_steps:
+            n = min(chunk, max_steps - steps, 1000)
+            sim.step_loop(n)
+            rows = sim.diagnostics(n)[0]
+            frac += [(int(r["step"]), float(r["n_translocated"]) / n_beads) for r in rows if r["step"] % every == 0]
+            steps += n
+            rec = sim.translocation()[0]
+            if rec["t_x"] >= 0:
+                break
+        sim.check()
+        out[prec] = {"t_x": int(rec["t_x"]), "steps": steps, "seconds": time.perf_counter() - t0,
+                     "beads": n_beads, "fraction": frac}
+        sim.close()
+    return out
+
+
 def main(argv=None):
     import argparse
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
@@ -154,7 +195,14 @@ def main(argv=None):
     ap.add_argument("--interp", type=int, default=None, help="0 trilinear, 1 nearest grid point")
     ap.add_argument("--integrator", type=int, default=None, help="0 velocity Verlet, 1 stochastic position Verlet")
     ap.add_argument("--records", default=None, help="write the raw records (.npz) here")
+    ap.add_argument("--precision-study", default=None, metavar="WORKLOAD",
+                    help="instead: one chain of WORKLOAD in FP32 and in FP16 storage (same seed and noise): "
+                         "t_X and the translocated fraction every 100 steps")
+    ap.add_argument("--seed", type=int, default=None, help="with --precision-study: chain and noise seed")
     a = ap.parse_args(argv)
+    if a.precision_study:
+        print(json.dumps(precision_run(a.precision_study, seed=a.seed, max_steps=a.max_steps), default=float))
+        return
     ov = {k: v for k, v in (("E", a.E), ("gamma", a.gamma), ("kT", a.kT), ("interp", a.interp),
                             ("integrator", a.integrator)) if v is not None}
     if a.box:

@@ -15,11 +15,11 @@ from paper_0711_2665_gb300 import lbmd, workloads
 pytestmark = pytest.mark.gpu
 
 
-def _run(w, world, steps, flow=True):
+def _run(w, world, steps, flow=True, shape=(2, 2)):
     inp = workloads.build_inputs(w)
     u = inp_mod.smooth_random_velocity(w["nx"], w["ny"], w["nz"], 1e-2, 3) if flow else None
     whole = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"])
-    whole.set_md_shape(2, 2)
+    whole.set_md_shape(*shape)
     if flow:
         whole.init_fluid(None, u[None])
     parts = pdist.slab_partition(w["nx"], world)
@@ -27,7 +27,7 @@ def _run(w, world, steps, flow=True):
     for rank in range(world):
         ws = pdist.slab_workload(w, rank, world)
         s = lbmd.Simulation(ws, inp["solid"], inp["offsets"], inp["r0"])
-        s.set_md_shape(2, 2)
+        s.set_md_shape(*shape)
         if flow:  # the slab's planes and ghosts of the same flow
             x0, wd = parts[rank]
             xs = np.arange(x0 - 1, x0 + wd + 2) % w["nx"]
@@ -82,7 +82,7 @@ def test_slabs_fp16_storage():
 def test_slabs_full_size_lattice():
     """The 256x128x128 lattice with the 1000-bead chain in two slabs."""
     w = workloads.get("lattice_4m_fp32")
-    whole, sims, parts = _run(w, 2, steps=3, flow=False)
+    whole, sims, parts = _run(w, 2, steps=3, flow=False, shape=(2, 16))
     _assert_same(whole, sims, parts)
 
 

@@ -166,3 +166,43 @@ def test_autotune_keeps_the_records():
     before = sim.translocation()
     sim.autotune(2)
     assert sim.translocation().tobytes() == before.tobytes()
+
+
+def _oracle_tx(w, inp, r, max_steps):
+    """First step at whose starting state every bead of realization r has
+    unwrapped x > wall_x + 1/2, in the oracle's run (-1 if none)."""
+    import oracle
+    o0, o1 = int(inp["offsets"][r]), int(inp["offsets"][r + 1])
+    orc = oracle.OracleSim(workloads.oracle_params(w, r, o1 - o0), inp["solid"])
+    orc.set_beads(inp["r0"][o0:o1])
+    thr = w["wall_x"] + 0.5
+    for k in range(max_steps + 1):
+        if np.all(orc.get_beads()[0][:, 0] > thr):
+            return k
+        orc.step(1)
+    return -1
+
+
+def test_translocation_time_fp32_and_fp16_against_oracle():
+    """Translocation time t_X (Sec. IV.A) of 8 chains of 20 beads in the
+    ensemble workload's box (64x32x32, 3x3 pore, E = 0.05, gamma = 0.1,
+    k_BT = 1e-4), each with its own start and noise stream, in FP32 and in
+    FP16 population storage, against the FP64 oracle run of each chain.
+    t_X is a first-passage time of a chaotic trajectory: the runs separate
+    through rounding, but the field drives the last beads through the
+    threshold at a tenth of a site per step or more, so the times stay within
+    a few steps (measured: FP32 at most 2, FP16 at most 1 of t_X = 74..159).
+    Bound per chain: max(3, 3% of t_X)."""
+    from paper_0711_2665_gb300 import transloc
+    got = {}
+    for prec in ("fp32", "fp16dev"):
+        out = transloc.run([20], 8, 400, chunk=50, overrides={"precision": prec}, autotune=False)
+        got[prec] = np.asarray(out["records"]["t_x"])
+        w, counts = out["workload"], out["counts"]
+    inp = workloads.build_inputs(w)
+    want = np.array([_oracle_tx(w, inp, r, 400) for r in range(len(counts))])
+    assert np.all(want > 0)
+    tol = np.maximum(3, 0.03 * want)
+    for prec, tx in got.items():
+        assert np.all(tx > 0), prec
+        assert np.all(np.abs(tx - want) <= tol), (prec, tx.tolist(), want.tolist())
