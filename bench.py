@@ -397,6 +397,90 @@ def extra_measurements(dev, stream, peak, peak_kind, forms, tiles=None, headline
 L2_BYTES = 129 * 1024 * 1024
 
 
+def run_slabs(args, w_full, world, rank, local):
+    """One lattice split into x-slabs over the ranks (one slab per rank and
+    GPU): each step gathers, sums u_p over the ranks, advances and exchanges
+    the slab faces with the neighbours (NCCL), then imports them.  value =
+    the whole lattice's site updates / the slowest rank's time (strong
+    scaling: the lattice is fixed as N grows)."""
+    import torch
+    import torch.distributed as dist
+    from paper_0711_2665_gb300 import build as libbuild, dist as pdist, lbmd, workloads
+    libbuild.build_library()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    w = pdist.slab_workload(w_full, rank, world)
+    inp = workloads.build_inputs(w_full)
+    sim = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"], device=f"cuda:{local}")
+    sim.autotune(8)
+    views = sim.slab_views()
+    for _ in range(args.warmup):
+        pdist.slab_step_dist(sim, views, rank, world)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    barrier()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        a.record(stream)
+        for _ in range(args.steps):
+            pdist.slab_step_dist(sim, views, rank, world)
+        b.record(stream)
+        barrier()
+    total_ms = pdist.max_over_ranks(a.elapsed_time(b), world)
+    sim.check()
+    sites = w_full["nx"] * w_full["ny"] * w_full["nz"]
+    value = sites * args.steps / (total_ms * 1e-3) / 1e6
+    # end to end: upload this slab's state from pinned host memory, K steps,
+    # read back the K diagnostics rows and the final state
+    L = sim._lib
+    f_in = torch.empty(sim.n_real * 19 * sim.ns, dtype=torch.float32, pin_memory=True)
+    f_in.numpy()[:] = sim.get_populations().reshape(-1)
+    r0h, v0h = sim.get_beads()
+    r_in = torch.from_numpy(r0h.reshape(-1).copy()).pin_memory()
+    v_in = torch.from_numpy(v0h.reshape(-1).copy()).pin_memory()
+    diag = (lbmd.Diag * args.steps)()
+    rows = ctypes.c_int32()
+    P = lambda t: ctypes.c_void_p(t.data_ptr())
+    barrier()
+    t0 = time.perf_counter()
+    ok = [L.lbmd_set_populations(sim._h, P(f_in)), L.lbmd_set_beads(sim._h, P(r_in), P(v_in))]
+    for _ in range(args.steps):
+        pdist.slab_step_dist(sim, views, rank, world)
+    ok += [L.lbmd_diagnostics(sim._h, diag, args.steps, ctypes.byref(rows)),
+           L.lbmd_get_populations(sim._h, P(f_in)), L.lbmd_get_beads(sim._h, P(r_in), P(v_in))]
+    barrier()
+    e2e_s = pdist.max_over_ranks(time.perf_counter() - t0, world)
+    assert all(x == 0 for x in ok)
+    nb = 2 * 8 * 3 * sim.total_beads
+    if rank == 0:
+        line = {"metric": "coupled LB-MD MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+                "dtype": "f32" if w["precision"] == "fp32" else "f16-storage/f32-math", "data": "synthetic",
+                "config": dict(_config_block(w, False), parallelism=f"x-slabs over {world} ranks",
+                               slab_planes=[p for _, p in pdist.slab_partition(w_full["nx"], world)]),
+                "launch": "per step: gather, u_p all-reduce, advance, face exchange (NCCL send/recv), import",
+                "roofline": {"bound": "hbm", "achieved": None, "peak": _peaks()[0], "unit": "GB/s", "frac": None,
+                             "traffic": None, "note": "see the single-lattice run"},
+                "gpu_launches": sim.launch_count(), "clocks": clk.summary(),
+                "e2e": {"value": sites * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+                        "h2d_bytes_per_step": (f_in.numel() * 4 + nb) / args.steps,
+                        "d2h_bytes_per_step": (rows.value * ctypes.sizeof(lbmd.Diag) + f_in.numel() * 4 + nb) / args.steps}}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -416,11 +500,16 @@ def main():
                     help="with --tiles: the particle kernel's chain exchange")
     ap.add_argument("--md-bonded", choices=["lanes", "warp"], default=None,
                     help="with --tiles: who evaluates the particle kernel's bonded terms")
+    ap.add_argument("--slabs", action="store_true",
+                    help="with N ranks: split the one lattice into N x-slabs (strong scaling) instead of "
+                         "running N replicas")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
     from paper_0711_2665_gb300 import dist as pdist, workloads
     world, rank, local = pdist.env()
+    if args.slabs and args.impl == "native":
+        return run_slabs(args, workloads.get(args.workload), world, rank, local)
     # one lattice: every rank runs a replica with its own seed; an ensemble:
     # each rank runs its block of realizations (same noise streams as unsplit)
     w_full = workloads.get(args.workload)

@@ -188,121 +188,6 @@ __global__ void __launch_bounds__(512, FL ? 1 : 2) k_stream_collide(const Sim S,
         block_partial4(am, ax, ay, az, S.fsum + 4 * ((size_t)(MODE == 2 ? S.n_real : 0) + r), &S.ctrl->status);
 }
 
-// ---------------------------------------------------------------------------
-// FP16 storage, two consecutive z sites per thread (MODE 0 or 1, no
-// fluctuations).  Each link's two raw FP16 values share one register
-// (__half2: .x the site at z, .y the one at z + 1), so a thread keeps 38
-// loads in flight in the registers that one site's 19 FP32 values take.  The
-// per-site arithmetic is that of k_stream_collide<1, MODE, 1, false>.
-// ---------------------------------------------------------------------------
-template <int MODE>
-__global__ void __launch_bounds__(512, 2) k_stream_collide_fp16z2(const Sim S, const void *__restrict__ Av,
-                                                                  void *__restrict__ Bv, const int zc, const int nzb) {
-    const int x = blockIdx.x * 32 + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int r = blockIdx.z / nzb;
-    const int z0 = (blockIdx.z - r * nzb) * zc;
-    const int nx = S.nx, ny = S.ny, nz = S.nz;
-    const uint32_t ns = (uint32_t)S.ps;
-    const __half *__restrict__ A = reinterpret_cast<const __half *>(Av) + (size_t)r * Q * ns;
-    __half *__restrict__ B = reinterpret_cast<__half *>(Bv) + (size_t)r * Q * ns;
-    float am = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
-    const float om = S.omega;
-    const float g0 = S.g[0], g1 = S.g[1], g2 = S.g[2];
-    const bool has_g = (g0 != 0.f) || (g1 != 0.f) || (g2 != 0.f);
-    constexpr float up = FP16_SCALE, down = FP16_INV_SCALE;
-    if (x < nx && y < ny) {
-        const int xv0 = (x == 0 ? nx - 1 : x - 1), xv2 = (x == nx - 1 ? 0 : x + 1);
-        const int yv0 = (y == 0 ? ny - 1 : y - 1), yv2 = (y == ny - 1 ? 0 : y + 1);
-        const int zend = min(z0 + zc, nz);
-        for (int zb = z0; zb < zend; zb += 2) {
-            __half2 hp[Q];
-            uint32_t lmu[2];
-            int su[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int z = zb + u;
-                lmu[u] = SOLID_BIT;
-                su[u] = 0;
-                __half hv[Q];
-#pragma unroll
-                for (int i = 0; i < Q; ++i) hv[i] = __ushort_as_half(0);
-                if (z < zend) {
-                    const int zv0 = (z == 0 ? nz - 1 : z - 1), zv2 = (z == nz - 1 ? 0 : z + 1);
-                    const int s = x + nx * (y + ny * z);
-                    su[u] = s;
-                    const bool flagged = S.tileflag[blockIdx.x + S.nxt * (y + ny * z)] != 0;
-                    const uint32_t lm = flagged ? __ldg(S.link + s) : 0u;
-                    lmu[u] = lm;
-                    if (!(lm & SOLID_BIT)) {
-#pragma unroll
-                        for (int i = 0; i < Q; ++i) {
-                            const int sx = cx(i) == 1 ? xv0 : (cx(i) == -1 ? xv2 : x);
-                            const int sy = cy(i) == 1 ? yv0 : (cy(i) == -1 ? yv2 : y);
-                            const int sz = cz(i) == 1 ? zv0 : (cz(i) == -1 ? zv2 : z);
-                            const uint32_t src = (uint32_t)(sx + nx * (sy + ny * sz));
-                            const bool bb = (lm >> i) & 1u;
-                            const uint32_t idx = bb ? (uint32_t)opp(i) * ns + (uint32_t)s : (uint32_t)i * ns + src;
-                            hv[i] = __ldg(A + idx);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    if (u == 0) hp[i] = __halves2half2(hv[i], __ushort_as_half(0));
-                    else hp[i] = __halves2half2(__low2half(hp[i]), hv[i]);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                if (lmu[u] & SOLID_BIT) continue;
-                const int s = su[u];
-                float h[Q];
-#pragma unroll
-                for (int i = 0; i < Q; ++i) h[i] = __half2float(u ? __high2half(hp[i]) : __low2half(hp[i]));
-                float drho_s = h[0], jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-                for (int i = 1; i < Q; i += 2) {
-                    const float sp = h[i] + h[i + 1], dp = h[i] - h[i + 1];
-                    drho_s += sp;
-                    if (cx(i) == 1) jx += dp;
-                    if (cx(i) == -1) jx -= dp;
-                    if (cy(i) == 1) jy += dp;
-                    if (cy(i) == -1) jy -= dp;
-                    if (cz(i) == 1) jz += dp;
-                    if (cz(i) == -1) jz -= dp;
-                }
-                const float drho = drho_s * down;
-                jx *= down; jy *= down; jz *= down;
-                if (MODE != 0 && x >= S.own_lo && x < S.own_hi) { am += drho; ax += jx; ay += jy; az += jz; }
-                const float rho = 1.0f + drho;
-                const float ir = 1.0f / rho;
-                const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
-                const float usq = 1.5f * (ux * ux + uy * uy + uz * uz);
-                const float rho_s = rho * up;
-                float hr[Q];
-                hr[0] = h[0] + om * (wq(0) * (drho_s - rho_s * usq) - h[0]);
-#pragma unroll
-                for (int i = 1; i < Q; i += 2) {
-                    const float cu = 3.0f * ((float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz);
-                    const float even = drho_s + rho_s * (0.5f * cu * cu - usq);
-                    const float odd = rho_s * cu;
-                    hr[i] = h[i] + om * (wq(i) * (even + odd) - h[i]);
-                    hr[i + 1] = h[i + 1] + om * (wq(i) * (even - odd) - h[i + 1]);
-                }
-#pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    float hn = hr[i];
-                    if (has_g)
-                        hn += up * (3.0f * wq(i) * ((float)cx(i) * g0 + (float)cy(i) * g1 + (float)cz(i) * g2));
-                    B[(uint32_t)i * ns + (uint32_t)s] = __float2half_rn(hn);
-                }
-            }
-        }
-    }
-    if (MODE != 0) block_partial4(am, ax, ay, az, S.fsum + 4 * (size_t)r, &S.ctrl->status);
-}
-
 static dim3 sc_grid(const Sim &S, int by, int zc, int *nzb) {
     *nzb = (S.nz + zc - 1) / zc;
     return dim3((S.nx + 31) / 32, (S.ny + by - 1) / by, (*nzb) * S.n_real);
@@ -324,10 +209,7 @@ cudaError_t launch_stream_collide(const Sim &S, const void *A, void *B, int by, 
     // every tile shape on GB300.
 #define SC_LAUNCH(P, M, F) k_stream_collide<P, M, 1, F><<<grid, block, 0, st>>>(S, A, B, zc, nzb)
     const bool fl = S.fluct != 0;
-    if (S.precision == LBMD_FP16DEV && !fl && zc >= 2) {
-        if (diag) k_stream_collide_fp16z2<1><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
-        else k_stream_collide_fp16z2<0><<<grid, block, 0, st>>>(S, A, B, zc, nzb);
-    } else if (S.precision == LBMD_FP16DEV) {
+    if (S.precision == LBMD_FP16DEV) {
         if (diag) { if (fl) SC_LAUNCH(1, 1, true); else SC_LAUNCH(1, 1, false); }
         else { if (fl) SC_LAUNCH(1, 0, true); else SC_LAUNCH(1, 0, false); }
     } else {

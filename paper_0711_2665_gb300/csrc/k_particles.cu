@@ -895,27 +895,41 @@ __device__ __forceinline__ void build_lists_body(const Sim &S, const PSmem &sm, 
 
 // ---------------------------------------------------------------------------
 // The starting Verlet lists of a step for every bead of every chain, one
-// warp per bead over the whole GPU: the warp's 32 lanes test 32 beads of the
-// chain at a time in ascending order and a ballot compacts the hits, so each
-// list comes out sorted, as the block builds make it; lane 0 adds the solid
-// sites within the wall-list radius.  It reads the positions the step starts
-// from and runs beside the gather, so the particle kernel only copies its
-// beads' lists.  Overflows latch the capacity status.
+// warp per bead over the whole GPU.  A block serves up to 8 consecutive beads
+// of one chain and first copies that chain's positions into shared memory;
+// each warp's 32 lanes then test 32 beads of the chain at a time in ascending
+// order and a ballot compacts the hits, so each list comes out sorted, as the
+// block builds make it; lane 0 adds the solid sites within the wall-list
+// radius.  It reads the positions the step starts from and runs beside the
+// gather, so the particle kernel only copies its beads' lists.  Overflows
+// latch the capacity status.  Grid: (ceil(max beads / 8), n_real).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_lists(const Sim S) {
-    const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // warp-uniform
-    if (g >= S.total_beads) return;
+constexpr int LIST_WARPS = 8;
+
+__global__ void __launch_bounds__(32 * LIST_WARPS) k_lists(const Sim S) {
+    extern __shared__ __align__(16) float4 lpos[];  // [N] hi, then [N] lo
+    const int r = blockIdx.y;
+    const int off = S.bead_off[r], N = S.bead_off[r + 1] - off;
+    const int first = blockIdx.x * LIST_WARPS;
+    if (first >= N) return;  // block-uniform
+    float4 *ph = lpos, *plo = lpos + N;
+    for (int q = threadIdx.x; q < N; q += blockDim.x) {
+        ph[q] = S.r_hi[off + q];
+        plo[q] = S.r_lo[off + q];
+    }
+    __syncthreads();
+    const int p = first + (threadIdx.x >> 5);
+    if (p >= N) return;  // warp-uniform, after the block's last barrier
     const int lane = threadIdx.x & 31;
-    const int r = S.bead_real[g];
-    const int off = S.bead_off[r], N = S.bead_off[r + 1] - off, p = g - off;
+    const size_t g = (size_t)(off + p);
     const float fnx = (float)S.bnx, fny = (float)S.ny, fnz = (float)S.nz;
-    const float4 mh = S.r_hi[g], ml = S.r_lo[g];
-    uint16_t *lst = S.nbr_g + (size_t)g * NBR_CAP;
+    const float4 mh = ph[p], ml = plo[p];
+    uint16_t *lst = S.nbr_g + g * NBR_CAP;
     int n = 0;
     for (int base = 0; base < N; base += 32) {
         const int q = base + lane;
         const int qq = q < N ? q : p;
-        const float4 qh = S.r_hi[off + qq], ql = S.r_lo[off + qq];
+        const float4 qh = ph[qq], ql = plo[qq];
         const float dx = ff_diff(mh.x, ml.x, qh.x, ql.x, fnx, S.binx), dy = ff_diff(mh.y, ml.y, qh.y, ql.y, fny, S.iny),
                     dz = ff_diff(mh.z, ml.z, qh.z, ql.z, fnz, S.inz);
         const bool hit = q < N && (q < p - 1 || q > p + 1) && within2(dx, dy, dz, S.rl2);
@@ -928,7 +942,7 @@ __global__ void __launch_bounds__(256) k_lists(const Sim S) {
     }
     if (lane == 0) {
         const int m = wall_list(S, ff_wrap(mh.x, ml.x, fnx, S.binx), ff_wrap(mh.y, ml.y, fny, S.iny),
-                                ff_wrap(mh.z, ml.z, fnz, S.inz), S.wal_g + (size_t)g * WALL_CAP);
+                                ff_wrap(mh.z, ml.z, fnz, S.inz), S.wal_g + g * WALL_CAP);
         if (n > NBR_CAP || m > WALL_CAP) atomicOr(&S.ctrl->status, ST_CAPACITY);
         S.nn_g[g] = min(n, NBR_CAP);
         S.nw_g[g] = min(m, WALL_CAP);
@@ -936,9 +950,9 @@ __global__ void __launch_bounds__(256) k_lists(const Sim S) {
 }
 
 cudaError_t launch_lists(const Sim &S, cudaStream_t st) {
-    if (S.total_beads == 0) return cudaSuccess;
-    const int threads = 256;
-    k_lists<<<(S.total_beads * 32 + threads - 1) / threads, threads, 0, st>>>(S);
+    if (S.total_beads == 0 || S.max_beads == 0) return cudaSuccess;
+    const dim3 grid((S.max_beads + LIST_WARPS - 1) / LIST_WARPS, S.n_real);
+    k_lists<<<grid, 32 * LIST_WARPS, (size_t)32 * S.max_beads, st>>>(S);
     return cudaGetLastError();
 }
 

@@ -50,7 +50,7 @@ struct lbmd_handle {
     std::vector<int32_t> offsets;
     int total_beads = 0;
     cudaStream_t st = nullptr, aux = nullptr, aux2 = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr, ev_pre = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr, ev_pre = nullptr, ev_lists = nullptr;
     int by = 8, zc = 8;
     bool overlap = true;  // particle kernel concurrent with the lattice pass
     bool md_fixed = false;  // particle-kernel shape set by the caller (the autotuner leaves it)
@@ -308,8 +308,16 @@ lbmd_status enqueue_gather(lbmd_handle *h) {
             ProfScope ps(h, K_LISTS, h->aux);
             CK(launch_lists(h->S, h->aux));
         }
-        ProfScope ps(h, K_GATHER, h->st);
-        CK(launch_gather(h->S, h->popA, h->st));
+        CK(cudaEventRecord(h->ev_lists, h->aux));
+        {
+            ProfScope ps(h, K_GATHER, h->st);
+            CK(launch_gather(h->S, h->popA, h->st));
+        }
+        // the lattice pass starts no earlier than the particle kernel can: a
+        // lattice pass already spread over every SM would keep the particle
+        // blocks (each asks for a whole SM's shared memory when reserving)
+        // waiting until it drained
+        CK(cudaStreamWaitEvent(h->st, h->ev_lists, 0));
     }
     return LBMD_OK;
 }
@@ -642,6 +650,7 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_pre, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_lists, cudaEventDisableTiming);
         if (e != cudaSuccess) { cuda_fail(h, e, "stream/event creation"); return bail(LBMD_ERR_CUDA); }
     }
     const Layout &L = h->L;
@@ -1641,6 +1650,7 @@ void lbmd_destroy(lbmd_handle *h) {
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->ev_join2) cudaEventDestroy(h->ev_join2);
     if (h->ev_pre) cudaEventDestroy(h->ev_pre);
+    if (h->ev_lists) cudaEventDestroy(h->ev_lists);
     if (h->aux) cudaStreamDestroy(h->aux);
     if (h->aux2) cudaStreamDestroy(h->aux2);
     delete h;
