@@ -63,6 +63,13 @@ struct lbmd_handle {
     void *loop_A = nullptr;
     bool capturing = false;
     bool profiling = false;
+    // The starting Verlet lists of the next step: lists_ready means a k_lists
+    // launch for the current bead positions is queued on the particle stream
+    // (ev_lists marks its end).  Every write of bead positions outside a step
+    // clears it.  lists_in_capture: that launch belongs to the stream capture
+    // under way.
+    bool lists_ready = false;
+    bool lists_in_capture = false;
     std::vector<ProfRec> pending;
     std::vector<cudaEvent_t> free_events;
     double prof_ms[K_COUNT] = {};
@@ -294,21 +301,51 @@ lbmd_status upload_md_map(lbmd_handle *h, Sim &S, int region) {
 // behind the lattice pass's traffic), then the particle kernel (aux stream)
 // and the bead diagnostics (aux2) run concurrently with the stream-collide
 // kernel (main), then the source, which also completes the diagnostics row.
-// Kernels a coupled step launches: the list build and the gather, then the
-// particle kernel, the bead diagnostics, the lattice pass and the source.
+// Kernels a coupled step launches: the gather, the particle kernel, the bead
+// diagnostics, the lattice pass, the source, and the next step's lists.
 long long step_launches(const lbmd_handle *h) { return h->total_beads > 0 ? 6 : 2; }
+
+// k_lists for the current bead positions on the particle stream, where the
+// next particle kernel follows it; ev_lists marks its end.
+lbmd_status enqueue_lists(lbmd_handle *h) {
+    {
+        ProfScope ps(h, K_LISTS, h->aux);
+        CK(launch_lists(h->S, h->aux));
+    }
+    CK(cudaEventRecord(h->ev_lists, h->aux));
+    h->lists_ready = true;
+    if (h->capturing) h->lists_in_capture = true;
+    return LBMD_OK;
+}
+
+// Lists for the current positions queued (outside any capture) and joined
+// into the main stream: before a graph launch or a capture, whose first step
+// relies on them.
+lbmd_status lists_before_graph(lbmd_handle *h) {
+    if (h->total_beads == 0) return LBMD_OK;
+    if (!h->lists_ready) {
+        CK(cudaEventRecord(h->ev_pre, h->st));
+        CK(cudaStreamWaitEvent(h->aux, h->ev_pre, 0));
+        lbmd_status s = enqueue_lists(h);
+        if (s != LBMD_OK) return s;
+        h->launches += 1;
+    }
+    CK(cudaStreamWaitEvent(h->st, h->ev_lists, 0));
+    return LBMD_OK;
+}
 
 lbmd_status enqueue_gather(lbmd_handle *h) {
     if (h->total_beads > 0) {
-        // the step's starting Verlet lists on the particle stream, beside the
-        // gather (the particle kernel follows them there)
-        CK(cudaEventRecord(h->ev_pre, h->st));
-        CK(cudaStreamWaitEvent(h->aux, h->ev_pre, 0));
-        {
-            ProfScope ps(h, K_LISTS, h->aux);
-            CK(launch_lists(h->S, h->aux));
+        // the step's starting Verlet lists: normally queued by the previous
+        // step right after its particle kernel, so they overlap its source
+        // pass and this gather; else queued here, beside the gather
+        if (!h->lists_ready) {
+            CK(cudaEventRecord(h->ev_pre, h->st));
+            CK(cudaStreamWaitEvent(h->aux, h->ev_pre, 0));
+            lbmd_status s = enqueue_lists(h);
+            if (s != LBMD_OK) return s;
+            h->launches += 1;
         }
-        CK(cudaEventRecord(h->ev_lists, h->aux));
         {
             ProfScope ps(h, K_GATHER, h->st);
             CK(launch_gather(h->S, h->popA, h->st));
@@ -316,8 +353,9 @@ lbmd_status enqueue_gather(lbmd_handle *h) {
         // the lattice pass starts no earlier than the particle kernel can: a
         // lattice pass already spread over every SM would keep the particle
         // blocks (each asks for a whole SM's shared memory when reserving)
-        // waiting until it drained
-        CK(cudaStreamWaitEvent(h->st, h->ev_lists, 0));
+        // waiting until it drained.  (Inside a capture whose lists were
+        // queued before it, the graph launch itself waits for them.)
+        if (!h->capturing || h->lists_in_capture) CK(cudaStreamWaitEvent(h->st, h->ev_lists, 0));
     }
     return LBMD_OK;
 }
@@ -330,6 +368,12 @@ lbmd_status enqueue_advance(lbmd_handle *h) {
         CK(launch_particles(h->S, h->popA, h->aux));
     }
     CK(cudaEventRecord(h->ev_join, h->aux));
+    // the next step's starting lists, from the positions this particle kernel
+    // leaves, beside this step's source pass and the next gather
+    if (h->total_beads > 0) {
+        lbmd_status s = enqueue_lists(h);
+        if (s != LBMD_OK) return s;
+    }
     if (h->total_beads > 0) {
         CK(cudaStreamWaitEvent(h->aux2, h->ev_fork, 0));
         {
@@ -453,11 +497,18 @@ lbmd_status capture_loop(lbmd_handle *h) {
     cudaGraph_t body = np.conditional.phGraph_out[0];
     void *A0 = h->popA;
     const long long s0 = h->host_step, l0 = h->launches;
+    {   // the body's first step relies on lists queued before the loop starts
+        lbmd_status sl = lists_before_graph(h);
+        if (sl != LBMD_OK) { cudaGraphDestroy(g); return sl; }
+    }
     h->capturing = true;
+    h->lists_in_capture = false;
     e = cudaStreamBeginCaptureToGraph(h->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { h->capturing = false; cudaGraphDestroy(g); return cuda_fail(h, e, "cudaStreamBeginCaptureToGraph"); }
     lbmd_status s = enqueue_step(h);
     if (s == LBMD_OK) s = enqueue_step(h);
+    // the next body's lists join the body before its end
+    if (s == LBMD_OK && h->total_beads > 0 && cudaStreamWaitEvent(h->st, h->ev_lists, 0) != cudaSuccess) s = LBMD_ERR_CUDA;
     if (s == LBMD_OK) {
         k_loop_tick<<<1, 1, 0, h->st>>>(hdl, (unsigned int *)(h->dbuf + h->L.loopc));
         if (cudaGetLastError() != cudaSuccess) s = LBMD_ERR_CUDA;
@@ -465,6 +516,7 @@ lbmd_status capture_loop(lbmd_handle *h) {
     cudaGraph_t captured = nullptr;
     e = cudaStreamEndCapture(h->st, &captured);
     h->capturing = false;
+    h->lists_in_capture = false;
     h->host_step = s0;
     h->launches = l0;
     if (s != LBMD_OK || e != cudaSuccess) {
@@ -482,15 +534,23 @@ lbmd_status capture_graph(lbmd_handle *h) {
     drop_graph(h);
     if (h->graph_steps <= 0) return LBMD_OK;
     cudaGraph_t g = nullptr;
+    {   // the graph's first step relies on lists queued before each launch
+        lbmd_status sl = lists_before_graph(h);
+        if (sl != LBMD_OK) return sl;
+    }
     h->capturing = true;
+    h->lists_in_capture = false;
     void *A0 = h->popA;
     const long long s0 = h->host_step, l0 = h->launches;
     cudaError_t e = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { h->capturing = false; return cuda_fail(h, e, "cudaStreamBeginCapture"); }
     lbmd_status s = LBMD_OK;
     for (int k = 0; k < h->graph_steps && s == LBMD_OK; ++k) s = enqueue_step(h);
+    // the lists for the step after the graph join the graph before its end
+    if (s == LBMD_OK && h->total_beads > 0 && cudaStreamWaitEvent(h->st, h->ev_lists, 0) != cudaSuccess) s = LBMD_ERR_CUDA;
     e = cudaStreamEndCapture(h->st, &g);
     h->capturing = false;
+    h->lists_in_capture = false;
     h->host_step = s0;
     h->launches = l0;
     if (s != LBMD_OK) { if (g) cudaGraphDestroy(g); return s; }
@@ -862,7 +922,10 @@ lbmd_status lbmd_step(lbmd_handle *h, int64_t n) {
                 if (s != LBMD_OK) return s;
             }
             if (h->popA == h->graph_A) {
+                lbmd_status sl = lists_before_graph(h);
+                if (sl != LBMD_OK) return sl;
                 CK(cudaGraphLaunch(h->gexec, h->st));
+                h->lists_ready = h->total_beads > 0;  // the graph's last step queued the next lists
                 h->host_step += h->graph_steps;
                 h->launches += step_launches(h) * h->graph_steps;
                 n -= h->graph_steps;
@@ -893,9 +956,12 @@ lbmd_status lbmd_step_loop(lbmd_handle *h, int64_t n) {
             lbmd_status s = capture_loop(h);
             if (s != LBMD_OK) return s;
         }
+        lbmd_status sl = lists_before_graph(h);
+        if (sl != LBMD_OK) return sl;
         k_set_u32<<<1, 1, 0, h->st>>>((unsigned int *)(h->dbuf + h->L.loopc), (unsigned int)pairs);
         CK(cudaGetLastError());
         CK(cudaGraphLaunch(h->lexec, h->st));
+        h->lists_ready = h->total_beads > 0;  // the loop's last step queued the next lists
         h->host_step += 2 * pairs;
         h->launches += 1 + (2LL * step_launches(h) + 1) * pairs;
     }
@@ -1058,6 +1124,7 @@ lbmd_status lbmd_set_beads(lbmd_handle *h, const double *r, const double *v) {
         lo[i] = make_float4(l[0], l[1], l[2], 0.f);
         vv[i] = v ? make_float4((float)v[3 * i], (float)v[3 * i + 1], (float)v[3 * i + 2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    h->lists_ready = false;  // the next particle kernel needs lists of these positions
     CK(cudaMemcpyAsync(h->S.r_hi, hi.data(), n * 16, cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(h->S.r_lo, lo.data(), n * 16, cudaMemcpyHostToDevice, h->st));
     CK(cudaMemcpyAsync(h->S.v, vv.data(), n * 16, cudaMemcpyHostToDevice, h->st));
@@ -1214,6 +1281,7 @@ lbmd_status lbmd_adjoint(lbmd_handle *h, int32_t K, int32_t C, void *scratch, si
         return LBMD_OK;
     };
     auto restore = [&](int j, long long step) -> lbmd_status {
+        h->lists_ready = false;  // positions come back from a checkpoint
         const char *c = b + a.ck + (size_t)j * a.ck_rec;
         const char *cb = c + align256(a.pop);
         CK(cudaMemcpyAsync(h->popA, c, a.pop, cudaMemcpyDeviceToDevice, h->st));
@@ -1421,6 +1489,9 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
         return e;
     };
+    // no k_lists of a step may still be writing the list arrays while the
+    // candidates' own builds run
+    if (h->total_beads > 0 && h->lists_ready) CK(cudaStreamWaitEvent(h->st, h->ev_lists, 0));
     static const int BYS[] = {1, 2, 4, 8, 16};
     static const int ZCS[] = {1, 2, 4, 8, 16, 32};
     cudaEvent_t a, b;
@@ -1534,6 +1605,7 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
     CK(cudaMemcpyAsync(h->S.v, snap + 2 * bb16, bb16, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemsetAsync(h->S.G, 0, (size_t)h->cfg.n_real * 3 * h->S.ns * 8, h->st));
     CK(put_back());
+    h->lists_ready = false;  // the candidates' lists are of their pseudo-steps' positions
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (bt > 0 &&
