@@ -245,9 +245,13 @@ lbmd_status lbmd_step_loop(lbmd_handle *h, int64_t n);
 
 /* Launch shapes of the stream-collide kernel: block (32, by) threads, each
  * thread walking zc consecutive z planes.  by in {1,2,4,8,16}, zc in 1..64.
- * The state (populations, beads) is bit-identical for every shape; the
- * diagnostics sums group their FP32 per-thread partials by shape and so agree
- * to rounding only. */
+ * by = 0 selects the kernel fed by tensor copies (rows of x staged in shared
+ * memory by cp.async.bulk.tensor), with zc in 1..256 row groups per thread
+ * block; it needs nx <= 256, rows of a multiple of 16 bytes and no
+ * fluctuating fluid (LBMD_ERR_INVALID_ARG otherwise).  The state
+ * (populations, beads) is bit-identical for every shape; the diagnostics
+ * sums group their FP32 per-thread partials by shape and so agree to
+ * rounding only. */
 lbmd_status lbmd_set_tiles(lbmd_handle *h, int32_t by, int32_t zc);
 lbmd_status lbmd_get_tiles(lbmd_handle *h, int32_t *by, int32_t *zc);
 

@@ -188,6 +188,247 @@ __global__ void __launch_bounds__(512, FL ? 1 : 2) k_stream_collide(const Sim S,
         block_partial4(am, ax, ay, az, S.fsum + 4 * ((size_t)(MODE == 2 ? S.n_real : 0) + r), &S.ctrl->status);
 }
 
+// ---------------------------------------------------------------------------
+// The lattice pass fed by tensor copies.  A CTA of 256 threads owns a run of
+// row groups; a group is floor(256 / nx) consecutive x rows (rows over y, then
+// z, then realizations), one thread per site.  For every row of a group and
+// every link i, one cp.async.bulk.tensor copies the source row (y - c_iy,
+// z - c_iz), wrapped periodically, into a ring of shared-memory stages that
+// an mbarrier per stage tracks; the x shift -c_ix (also periodic) is an index
+// into that row.  A stage is refilled once every thread has used it.  Each
+// CTA keeps up to STAGES groups in flight, far more bytes than its registers
+// could hold, so fewer SMs reach the HBM rate.  Bounce-back links and solid
+// sites are read from global memory, as in k_stream_collide, whose per-site
+// arithmetic this is.  Waits are bounded: a CTA that gives up latches
+// ST_TIMEOUT, waits (bounded) for its copies in flight and leaves.
+// ---------------------------------------------------------------------------
+constexpr int TMA_THREADS = 256;
+template <int PREC> struct TmaStages;
+template <> struct TmaStages<0> { static constexpr int n = 4; };  // 4 x 19.5 KB with 256-site rows
+template <> struct TmaStages<1> { static constexpr int n = 8; };  // 8 x 9.7 KB
+constexpr unsigned TMA_WAIT_LIMIT = 1u << 22;  // try_wait rounds before a CTA gives up
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for phase `parity` of a stage's barrier; false: gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (unsigned k = 0; k < TMA_WAIT_LIMIT; ++k)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+// one row (x = 0 .. nx-1) of link i at (y, z) of realization r into dst
+__device__ __forceinline__ void tma_row(void *dst, const CUtensorMap *map, int y, int z, int i, int r, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(y), "r"(z), "r"(i), "r"(r), "r"(smem_addr(bar))
+        : "memory");
+}
+
+template <int PREC, int MODE>
+__global__ void __launch_bounds__(TMA_THREADS) k_stream_collide_tma(const Sim S, const __grid_constant__ CUtensorMap tmA,
+                                                                     const void *__restrict__ Av, void *__restrict__ Bv,
+                                                                     const int groups) {
+    using T = typename PopT<PREC>::T;
+    constexpr int STAGES = TmaStages<PREC>::n;
+    extern __shared__ __align__(128) unsigned char tsm[];
+    __shared__ uint64_t bars[STAGES];
+    __shared__ int s_abort;
+    const int nx = S.nx, ny = S.ny, nz = S.nz;
+    const int rows = TMA_THREADS / nx;  // rows per group
+    const uint32_t row_bytes = (uint32_t)nx * sizeof(T);
+    const uint32_t stage_elems = (uint32_t)Q * rows * nx;
+    const int r = blockIdx.y;  // the realization: a CTA's rows are all of one
+    const long long total_rows = (long long)nz * ny;
+    const long long n_groups = (total_rows + rows - 1) / rows;
+    const long long g0 = (long long)blockIdx.x * groups;
+    const int ng = (int)max(0ll, min((long long)groups, n_groups - g0));
+    const uint32_t ns = (uint32_t)S.ps;
+    T *const ring = reinterpret_cast<T *>(tsm);
+    const int tid = threadIdx.x;
+    const int j = tid / nx, x = tid - j * nx;  // this thread's row in a group and its x
+    const bool lane_ok = j < rows;
+    float am = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
+    const float om = S.omega;
+    const float g0f = S.g[0], g1f = S.g[1], g2f = S.g[2];
+    const bool has_g = (g0f != 0.f) || (g1f != 0.f) || (g2f != 0.f);
+    constexpr float up = PopScale<PREC>::up, down = PopScale<PREC>::down;
+    const int xv0 = (x == 0 ? nx - 1 : x - 1), xv2 = (x == nx - 1 ? 0 : x + 1);
+
+    // issue the copies of group k (of this CTA) into its stage
+    auto issue = [&](int k) {
+        const int st = k % STAGES;
+        const long long R0 = (g0 + k) * rows;
+        const int nrow = (int)min((long long)rows, total_rows - R0);
+        mbar_expect_tx(&bars[st], (uint32_t)nrow * Q * row_bytes);
+        for (int jj = 0; jj < nrow; ++jj) {
+            const long long R = R0 + jj;
+            const int y = (int)(R % ny), z = (int)(R / ny);
+            const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+            const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int sy = cy(i) == 1 ? ym : (cy(i) == -1 ? yp : y);
+                const int sz = cz(i) == 1 ? zm : (cz(i) == -1 ? zp : z);
+                tma_row(ring + (size_t)st * stage_elems + ((size_t)i * rows + jj) * nx, &tmA, sy, sz, i, r, &bars[st]);
+            }
+        }
+    };
+
+    if (tid == 0) {
+        for (int st = 0; st < STAGES; ++st) mbar_init(&bars[st], 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int k = 0; k < min(STAGES, ng); ++k) issue(k);
+    int k = 0;
+    for (; k < ng; ++k) {
+        const int st = k % STAGES;
+        const uint32_t par = (uint32_t)((k / STAGES) & 1);
+        const bool ready = mbar_wait(&bars[st], par);
+        if (!ready) {
+            atomicOr(&S.ctrl->status, ST_TIMEOUT);
+            s_abort = 1;
+        }
+        const long long R = (g0 + k) * rows + j;
+        if (ready && lane_ok && R < total_rows) {
+            const int y = (int)(R % ny), z = (int)(R / ny);
+            const int s = x + nx * (y + ny * z);
+            const T *A = reinterpret_cast<const T *>(Av) + (size_t)r * Q * ns;
+            T *B = reinterpret_cast<T *>(Bv) + (size_t)r * Q * ns;
+            const T *row = ring + (size_t)st * stage_elems + (size_t)j * nx;  // link i: + i * rows * nx
+            uint32_t lm = 0u;
+            if (S.tileflag[(x >> 5) + S.nxt * (y + ny * z)]) lm = __ldg(S.link + s);
+            if (!(lm & SOLID_BIT)) {
+                float h[Q];
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const int sx = cx(i) == 1 ? xv0 : (cx(i) == -1 ? xv2 : x);
+                    h[i] = ((lm >> i) & 1u) ? load_raw(A, (uint32_t)opp(i) * ns + (uint32_t)s)
+                                            : load_raw(row + (size_t)i * rows * nx, (uint32_t)sx);
+                }
+                float drho_s = h[0], jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+                for (int i = 1; i < Q; i += 2) {
+                    const float sp = h[i] + h[i + 1], dp = h[i] - h[i + 1];
+                    drho_s += sp;
+                    if (cx(i) == 1) jx += dp;
+                    if (cx(i) == -1) jx -= dp;
+                    if (cy(i) == 1) jy += dp;
+                    if (cy(i) == -1) jy -= dp;
+                    if (cz(i) == 1) jz += dp;
+                    if (cz(i) == -1) jz -= dp;
+                }
+                const float drho = drho_s * down;
+                jx *= down; jy *= down; jz *= down;
+                if (MODE != 0 && x >= S.own_lo && x < S.own_hi) { am += drho; ax += jx; ay += jy; az += jz; }
+                const float rho = 1.0f + drho;
+                const float ir = 1.0f / rho;
+                const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
+                const float usq = 1.5f * (ux * ux + uy * uy + uz * uz);
+                const float rho_s = rho * up;
+                float hr[Q];
+                hr[0] = h[0] + om * (wq(0) * (drho_s - rho_s * usq) - h[0]);
+#pragma unroll
+                for (int i = 1; i < Q; i += 2) {
+                    const float cu = 3.0f * ((float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz);
+                    const float even = drho_s + rho_s * (0.5f * cu * cu - usq);
+                    const float odd = rho_s * cu;
+                    hr[i] = h[i] + om * (wq(i) * (even + odd) - h[i]);
+                    hr[i + 1] = h[i + 1] + om * (wq(i) * (even - odd) - h[i + 1]);
+                }
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    float hn = hr[i];
+                    if (has_g)
+                        hn += up * (3.0f * wq(i) * ((float)cx(i) * g0f + (float)cy(i) * g1f + (float)cz(i) * g2f));
+                    store_raw(B, (uint32_t)i * ns + (uint32_t)s, hn);
+                }
+            }
+        }
+        __syncthreads();  // every thread is done with stage st (and s_abort is seen by all)
+        if (s_abort) break;
+        if (tid == 0 && k + STAGES < ng) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(k + STAGES);
+        }
+    }
+    if (s_abort) {
+        // copies still in flight land before the CTA's shared memory is released
+        if (tid == 0)
+            for (int kk = k; kk < min(ng, k + STAGES); ++kk)
+                mbar_wait(&bars[kk % STAGES], (uint32_t)((kk / STAGES) & 1));
+        return;
+    }
+    if (MODE != 0) block_partial4(am, ax, ay, az, S.fsum + 4 * (size_t)r, &S.ctrl->status);
+}
+
+bool tma_lattice_ok(const Sim &S) {
+    const int esz = S.precision == LBMD_FP16DEV ? 2 : 4;
+    return !S.fluct && S.nx <= TMA_THREADS && (S.nx * esz) % 16 == 0;
+}
+
+static size_t tma_smem(const Sim &S);
+
+// grant the kernel its shared memory once (not inside a stream capture)
+cudaError_t prepare_stream_collide_tma(const Sim &S) {
+    const int smem = (int)tma_smem(S);
+    cudaError_t e = cudaSuccess;
+    if (S.precision == LBMD_FP16DEV) {
+        e = cudaFuncSetAttribute(k_stream_collide_tma<1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_stream_collide_tma<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    } else {
+        e = cudaFuncSetAttribute(k_stream_collide_tma<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_stream_collide_tma<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    }
+    return e;
+}
+
+static size_t tma_smem(const Sim &S) {
+    const int esz = S.precision == LBMD_FP16DEV ? 2 : 4;
+    const int stages = S.precision == LBMD_FP16DEV ? TmaStages<1>::n : TmaStages<0>::n;
+    return (size_t)stages * Q * (TMA_THREADS / S.nx) * S.nx * esz;
+}
+
+cudaError_t launch_stream_collide_tma(const Sim &S, const CUtensorMap &tmA, const void *A, void *B, int groups,
+                                      bool diag, cudaStream_t st) {
+    if (!tma_lattice_ok(S) || groups < 1) return cudaErrorInvalidValue;
+    const long long total_rows = (long long)S.nz * S.ny;  // per realization
+    const int rows = TMA_THREADS / S.nx;
+    const long long n_groups = (total_rows + rows - 1) / rows;
+    const dim3 grid((unsigned)((n_groups + groups - 1) / groups), S.n_real);
+    const size_t smem = tma_smem(S);
+#define TMA_LAUNCH(P, M) k_stream_collide_tma<P, M><<<grid, TMA_THREADS, smem, st>>>(S, tmA, A, B, groups)
+    if (S.precision == LBMD_FP16DEV) {
+        if (diag) TMA_LAUNCH(1, 1); else TMA_LAUNCH(1, 0);
+    } else {
+        if (diag) TMA_LAUNCH(0, 1); else TMA_LAUNCH(0, 0);
+    }
+#undef TMA_LAUNCH
+    return cudaGetLastError();
+}
+
 static dim3 sc_grid(const Sim &S, int by, int zc, int *nzb) {
     *nzb = (S.nz + zc - 1) / zc;
     return dim3((S.nx + 31) / 32, (S.ny + by - 1) / by, (*nzb) * S.n_real);

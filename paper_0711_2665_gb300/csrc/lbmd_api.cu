@@ -51,7 +51,10 @@ struct lbmd_handle {
     int total_beads = 0;
     cudaStream_t st = nullptr, aux = nullptr, aux2 = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr, ev_pre = nullptr, ev_lists = nullptr;
-    int by = 8, zc = 8;
+    cudaEvent_t ev_lists_cap = nullptr;  // ev_lists inside a stream capture (a captured record cannot be waited on outside it)
+    int by = 8, zc = 8;   // by = 0: the tensor-copy lattice kernel with zc row groups per block
+    CUtensorMap tmap[2];  // the two population buffers (at L.popA, L.popB) as 5-D tensors
+    bool tma_ok = false;  // tmap encoded and the lattice fits the tensor-copy kernel
     bool overlap = true;  // particle kernel concurrent with the lattice pass
     bool md_fixed = false;  // particle-kernel shape set by the caller (the autotuner leaves it)
     int md_exchange = 0;    // chain exchange: 0 the autotuner's choice, 1 push, 2 pull
@@ -87,6 +90,7 @@ lbmd_status fail(lbmd_handle *h, lbmd_status s, const std::string &msg) {
 }
 
 lbmd_status cuda_fail(lbmd_handle *h, cudaError_t e, const char *where) {
+    cudaGetLastError();  // a failed call leaves no error for a later launch check to pick up
     return fail(h, LBMD_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
@@ -301,9 +305,65 @@ lbmd_status upload_md_map(lbmd_handle *h, Sim &S, int region) {
 // behind the lattice pass's traffic), then the particle kernel (aux stream)
 // and the bead diagnostics (aux2) run concurrently with the stream-collide
 // kernel (main), then the source, which also completes the diagnostics row.
+// The lattice pass A -> B with tile shape (by, zc): by = 0 is the kernel fed
+// by tensor copies, with the map of whichever buffer is A now.
+cudaError_t lattice_pass(lbmd_handle *h, const Sim &S, int by, int zc, bool diag) {
+    if (by == 0) {
+        const CUtensorMap &m = h->popA == (void *)(h->dbuf + h->L.popA) ? h->tmap[0] : h->tmap[1];
+        return launch_stream_collide_tma(S, m, h->popA, h->popB, zc, diag, h->st);
+    }
+    return launch_stream_collide(S, h->popA, h->popB, by, zc, diag, h->st);
+}
+
+// The two population buffers as 5-D tensors (x, y, z, link, realization) of
+// the storage type, one-row boxes, for the tensor-copy lattice kernel.  The
+// encoder comes from the driver through the runtime (no driver library is
+// linked).  Leaves tma_ok false where the lattice does not fit the kernel or
+// the driver lacks the call.
+void encode_tensor_maps(lbmd_handle *h) {
+    h->tma_ok = false;
+    if (!tma_lattice_ok(h->S)) return;
+    typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        return;
+    }
+    const bool f16 = h->cfg.precision == LBMD_FP16DEV;
+    const cuuint64_t esz = f16 ? 2 : 4;
+    const Sim &S = h->S;
+    const cuuint64_t dims[5] = {(cuuint64_t)S.nx, (cuuint64_t)S.ny, (cuuint64_t)S.nz, (cuuint64_t)LBMD_Q,
+                                (cuuint64_t)S.n_real};
+    const cuuint64_t strides[4] = {(cuuint64_t)S.nx * esz, (cuuint64_t)S.nx * S.ny * esz, (cuuint64_t)S.ps * esz,
+                                   (cuuint64_t)LBMD_Q * S.ps * esz};
+    const cuuint32_t box[5] = {(cuuint32_t)S.nx, 1, 1, 1, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    void *bufs[2] = {h->dbuf + h->L.popA, h->dbuf + h->L.popB};
+    for (int k = 0; k < 2; ++k) {
+        const CUresult r = ((EncodeTiled)fn)(&h->tmap[k], f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                                             5, bufs[k], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return;
+    }
+    if (prepare_stream_collide_tma(S) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    h->tma_ok = true;
+}
+
 // Kernels a coupled step launches: the gather, the particle kernel, the bead
 // diagnostics, the lattice pass, the source, and the next step's lists.
 long long step_launches(const lbmd_handle *h) { return h->total_beads > 0 ? 6 : 2; }
+
+// the event marking the end of the latest k_lists launch: a separate one
+// inside a stream capture
+cudaEvent_t lists_event(const lbmd_handle *h) { return h->capturing ? h->ev_lists_cap : h->ev_lists; }
 
 // k_lists for the current bead positions on the particle stream, where the
 // next particle kernel follows it; ev_lists marks its end.
@@ -312,7 +372,7 @@ lbmd_status enqueue_lists(lbmd_handle *h) {
         ProfScope ps(h, K_LISTS, h->aux);
         CK(launch_lists(h->S, h->aux));
     }
-    CK(cudaEventRecord(h->ev_lists, h->aux));
+    CK(cudaEventRecord(lists_event(h), h->aux));
     h->lists_ready = true;
     if (h->capturing) h->lists_in_capture = true;
     return LBMD_OK;
@@ -355,7 +415,7 @@ lbmd_status enqueue_gather(lbmd_handle *h) {
         // blocks (each asks for a whole SM's shared memory when reserving)
         // waiting until it drained.  (Inside a capture whose lists were
         // queued before it, the graph launch itself waits for them.)
-        if (!h->capturing || h->lists_in_capture) CK(cudaStreamWaitEvent(h->st, h->ev_lists, 0));
+        if (!h->capturing || h->lists_in_capture) CK(cudaStreamWaitEvent(h->st, lists_event(h), 0));
     }
     return LBMD_OK;
 }
@@ -385,7 +445,7 @@ lbmd_status enqueue_advance(lbmd_handle *h) {
     if (!h->overlap) CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
     {
         ProfScope ps(h, K_STREAM_COLLIDE, h->st);
-        CK(launch_stream_collide(h->S, h->popA, h->popB, h->by, h->zc, true, h->st));
+        CK(lattice_pass(h, h->S, h->by, h->zc, true));
     }
     CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
     if (h->total_beads > 0) CK(cudaStreamWaitEvent(h->st, h->ev_join2, 0));
@@ -508,7 +568,7 @@ lbmd_status capture_loop(lbmd_handle *h) {
     lbmd_status s = enqueue_step(h);
     if (s == LBMD_OK) s = enqueue_step(h);
     // the next body's lists join the body before its end
-    if (s == LBMD_OK && h->total_beads > 0 && cudaStreamWaitEvent(h->st, h->ev_lists, 0) != cudaSuccess) s = LBMD_ERR_CUDA;
+    if (s == LBMD_OK && h->total_beads > 0 && cudaStreamWaitEvent(h->st, h->ev_lists_cap, 0) != cudaSuccess) s = LBMD_ERR_CUDA;
     if (s == LBMD_OK) {
         k_loop_tick<<<1, 1, 0, h->st>>>(hdl, (unsigned int *)(h->dbuf + h->L.loopc));
         if (cudaGetLastError() != cudaSuccess) s = LBMD_ERR_CUDA;
@@ -547,7 +607,7 @@ lbmd_status capture_graph(lbmd_handle *h) {
     lbmd_status s = LBMD_OK;
     for (int k = 0; k < h->graph_steps && s == LBMD_OK; ++k) s = enqueue_step(h);
     // the lists for the step after the graph join the graph before its end
-    if (s == LBMD_OK && h->total_beads > 0 && cudaStreamWaitEvent(h->st, h->ev_lists, 0) != cudaSuccess) s = LBMD_ERR_CUDA;
+    if (s == LBMD_OK && h->total_beads > 0 && cudaStreamWaitEvent(h->st, h->ev_lists_cap, 0) != cudaSuccess) s = LBMD_ERR_CUDA;
     e = cudaStreamEndCapture(h->st, &g);
     h->capturing = false;
     h->lists_in_capture = false;
@@ -685,6 +745,7 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
                       void *device_buffer, size_t device_bytes, void *stream, lbmd_handle **out) {
     if (!out) return LBMD_ERR_INVALID_ARG;
     *out = nullptr;
+    cudaGetLastError();  // an error the caller left pending is not this handle's
     std::string why;
     if (!config_ok(cfg, bead_offsets, why) || !solid) return LBMD_ERR_INVALID_ARG;
     lbmd_handle *h = new lbmd_handle();
@@ -711,6 +772,7 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_pre, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_lists, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_lists_cap, cudaEventDisableTiming);
         if (e != cudaSuccess) { cuda_fail(h, e, "stream/event creation"); return bail(LBMD_ERR_CUDA); }
     }
     const Layout &L = h->L;
@@ -899,6 +961,7 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
     CKI(cudaMemsetAsync(b + L.up, 0, (size_t)std::max(h->total_beads, 1) * 32, h->st));
     CKI(launch_init_rest(S, h->popA, h->st));
     CKI(cudaStreamSynchronize(h->st));
+    encode_tensor_maps(h);
     // the particle kernel needs its shared-memory size granted once
     if (md_shape(S).smem > 200 * 1024) { fail(h, LBMD_ERR_CAPACITY, "too many beads per realization for shared memory"); return bail(LBMD_ERR_CAPACITY); }
     lbmd_status s = lbmd_set_beads(h, r_init, nullptr);
@@ -1387,8 +1450,12 @@ lbmd_status lbmd_set_graph(lbmd_handle *h, int32_t steps_per_graph) {
 }
 
 lbmd_status lbmd_set_tiles(lbmd_handle *h, int32_t by, int32_t zc) {
-    if (!h || !(by == 1 || by == 2 || by == 4 || by == 8 || by == 16) || zc < 1 || zc > 64)
+    if (!h) return LBMD_ERR_INVALID_ARG;
+    if (by == 0) {
+        if (!h->tma_ok || zc < 1 || zc > 256) return LBMD_ERR_INVALID_ARG;
+    } else if (!(by == 1 || by == 2 || by == 4 || by == 8 || by == 16) || zc < 1 || zc > 64) {
         return LBMD_ERR_INVALID_ARG;
+    }
     if (by != h->by || zc != h->zc) drop_graph(h);
     h->by = by;
     h->zc = zc;
@@ -1503,9 +1570,9 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
         for (int zc : ZCS) {
             if (zc > h->cfg.nz) continue;
             // warm-up, then time reps launches; B is scratch until the next step overwrites it
-            CK(launch_stream_collide(h->S, h->popA, h->popB, by, zc, true, h->st));
+            CK(lattice_pass(h, h->S, by, zc, true));
             CK(cudaEventRecord(a, h->st));
-            for (int k = 0; k < reps; ++k) CK(launch_stream_collide(h->S, h->popA, h->popB, by, zc, true, h->st));
+            for (int k = 0; k < reps; ++k) CK(lattice_pass(h, h->S, by, zc, true));
             CK(cudaEventRecord(b, h->st));
             CK(cudaEventSynchronize(b));
             float ms = 0.f;
@@ -1513,6 +1580,20 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
             h->launches += reps + 1;
             if (ms < best) { best = ms; bb = by; bz = zc; }
         }
+    // the tensor-copy kernel, row groups per thread block
+    static const int GROUPS[] = {2, 4, 8, 16, 32, 64};
+    for (int g : GROUPS) {
+        if (!h->tma_ok) break;
+        CK(lattice_pass(h, h->S, 0, g, true));
+        CK(cudaEventRecord(a, h->st));
+        for (int k = 0; k < reps; ++k) CK(lattice_pass(h, h->S, 0, g, true));
+        CK(cudaEventRecord(b, h->st));
+        CK(cudaEventSynchronize(b));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, a, b));
+        h->launches += reps + 1;
+        if (ms < best) { best = ms; bb = 0; bz = g; }
+    }
     lbmd_status s = lbmd_set_tiles(h, bb, bz);
     if (s != LBMD_OK) { cudaEventDestroy(a); cudaEventDestroy(b); return s; }
     if (by_out) *by_out = bb;
@@ -1554,7 +1635,7 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
                 CKT(launch_particles(trial, h->popA, h->aux));
                 CKT(cudaEventRecord(h->ev_join, h->aux));
                 if (!h->overlap) CKT(cudaStreamWaitEvent(h->st, h->ev_join, 0));
-                CKT(launch_stream_collide(trial, h->popA, h->popB, h->by, h->zc, false, h->st));
+                CKT(lattice_pass(h, trial, h->by, h->zc, false));
                 CKT(cudaStreamWaitEvent(h->st, h->ev_join, 0));
             }
             CKT(cudaEventRecord(b, h->st));
@@ -1723,6 +1804,7 @@ void lbmd_destroy(lbmd_handle *h) {
     if (h->ev_join2) cudaEventDestroy(h->ev_join2);
     if (h->ev_pre) cudaEventDestroy(h->ev_pre);
     if (h->ev_lists) cudaEventDestroy(h->ev_lists);
+    if (h->ev_lists_cap) cudaEventDestroy(h->ev_lists_cap);
     if (h->aux) cudaStreamDestroy(h->aux);
     if (h->aux2) cudaStreamDestroy(h->aux2);
     delete h;

@@ -20,6 +20,7 @@
 //   partial / ring / ctrl  reduction scratch, per-step diagnostics, counters
 #pragma once
 
+#include <cuda.h>  // CUtensorMap and its enums (no driver library is linked)
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -426,6 +427,13 @@ __device__ __forceinline__ bool in_channel(const Sim &S, float xw, float yw, flo
 int sc_blocks(const Sim &S, int by, int zc);
 cudaError_t launch_stream_collide(const Sim &S, const void *A, void *B, int by, int zc,
                                   bool diag, cudaStream_t st);
+// the lattice pass fed by tensor copies (no fluctuations, nx <= 256, rows of
+// a multiple of 16 bytes): tmA describes buffer A as a 5-D tensor
+// (x, y, z, link, realization) with one-row boxes; groups: row groups per CTA
+bool tma_lattice_ok(const Sim &S);
+cudaError_t prepare_stream_collide_tma(const Sim &S);
+cudaError_t launch_stream_collide_tma(const Sim &S, const CUtensorMap &tmA, const void *A, void *B, int groups,
+                                      bool diag, cudaStream_t st);
 cudaError_t launch_fluid_observables(const Sim &S, const void *A, cudaStream_t st);
 cudaError_t launch_source(const Sim &S, void *B, cudaStream_t st);
 cudaError_t launch_init_rest(const Sim &S, void *A, cudaStream_t st);
