@@ -51,8 +51,10 @@ typedef enum {
     LBMD_ERR_INVALID_ARG = 1, /* bad configuration or argument; nothing was changed */
     LBMD_ERR_CUDA = 2,        /* a CUDA runtime call failed (message in lbmd_last_error) */
     LBMD_ERR_NONFINITE = 3,   /* a NaN/Inf appeared in the fluid or bead state */
-    LBMD_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up; reserved: no kernel of this
-                                 version waits on a flag, so no call returns it */
+    LBMD_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up: the tensor-copy lattice
+                                 pass (tiles by = 0) waits at most 2^22 polls for each stage's
+                                 copies; a CTA that gives up latches this code and leaves its
+                                 sites unwritten, so the state after it is not a valid step */
     LBMD_ERR_CAPACITY = 5,    /* a fixed-capacity list (neighbours, wall sites) overflowed */
     LBMD_ERR_BUFFER = 6       /* device buffer too small or misaligned */
 } lbmd_status;

@@ -206,7 +206,8 @@ constexpr int TMA_THREADS = 256;
 template <int PREC> struct TmaStages;
 template <> struct TmaStages<0> { static constexpr int n = 4; };  // 4 x 19.5 KB with 256-site rows
 template <> struct TmaStages<1> { static constexpr int n = 8; };  // 8 x 9.7 KB
-constexpr unsigned TMA_WAIT_LIMIT = 1u << 22;  // try_wait rounds before a CTA gives up
+constexpr unsigned TMA_WAIT_LIMIT = 1u << 22;         // try_wait rounds before a CTA gives up ...
+constexpr unsigned long long TMA_WAIT_NS = 250000000;  // ... or this many ns (a stage takes microseconds)
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
@@ -226,12 +227,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 // bounded wait for phase `parity` of a stage's barrier; false: gave up
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (unsigned k = 0; k < TMA_WAIT_LIMIT; ++k)
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned k = 0; k < TMA_WAIT_LIMIT; ++k) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((k & 63u) == 63u && global_ns() - t0 > TMA_WAIT_NS) return false;
+    }
     return false;
 }
+// a staged population (load_raw is a global-only read: not for the ring)
+__device__ __forceinline__ float ring_load(const float *row, int x) { return row[x]; }
+__device__ __forceinline__ float ring_load(const __half *row, int x) { return __half2float(row[x]); }
 // one row (x = 0 .. nx-1) of link i at (y, z) of realization r into dst
 __device__ __forceinline__ void tma_row(void *dst, const CUtensorMap *map, int y, int z, int i, int r, uint64_t *bar) {
     asm volatile(
@@ -253,14 +266,18 @@ __global__ void __launch_bounds__(TMA_THREADS) k_stream_collide_tma(const Sim S,
     const int nx = S.nx, ny = S.ny, nz = S.nz;
     const int rows = TMA_THREADS / nx;  // rows per group
     const uint32_t row_bytes = (uint32_t)nx * sizeof(T);
-    const uint32_t stage_elems = (uint32_t)Q * rows * nx;
+    // a tensor copy lands on a 128-byte boundary: each staged row takes a
+    // multiple of 128 bytes, and the ring starts on the first such boundary
+    // of the dynamic shared memory (the launch adds 128 bytes for that)
+    const uint32_t row_elems = ((row_bytes + 127u) & ~127u) / (uint32_t)sizeof(T);
+    const uint32_t stage_elems = (uint32_t)Q * rows * row_elems;
     const int r = blockIdx.y;  // the realization: a CTA's rows are all of one
     const long long total_rows = (long long)nz * ny;
     const long long n_groups = (total_rows + rows - 1) / rows;
     const long long g0 = (long long)blockIdx.x * groups;
     const int ng = (int)max(0ll, min((long long)groups, n_groups - g0));
     const uint32_t ns = (uint32_t)S.ps;
-    T *const ring = reinterpret_cast<T *>(tsm);
+    T *const ring = reinterpret_cast<T *>(tsm + ((128u - (smem_addr(tsm) & 127u)) & 127u));
     const int tid = threadIdx.x;
     const int j = tid / nx, x = tid - j * nx;  // this thread's row in a group and its x
     const bool lane_ok = j < rows;
@@ -286,7 +303,8 @@ __global__ void __launch_bounds__(TMA_THREADS) k_stream_collide_tma(const Sim S,
             for (int i = 0; i < Q; ++i) {
                 const int sy = cy(i) == 1 ? ym : (cy(i) == -1 ? yp : y);
                 const int sz = cz(i) == 1 ? zm : (cz(i) == -1 ? zp : z);
-                tma_row(ring + (size_t)st * stage_elems + ((size_t)i * rows + jj) * nx, &tmA, sy, sz, i, r, &bars[st]);
+                tma_row(ring + (size_t)st * stage_elems + ((size_t)i * rows + jj) * row_elems, &tmA, sy, sz, i, r,
+                        &bars[st]);
             }
         }
     };
@@ -315,7 +333,7 @@ __global__ void __launch_bounds__(TMA_THREADS) k_stream_collide_tma(const Sim S,
             const int s = x + nx * (y + ny * z);
             const T *A = reinterpret_cast<const T *>(Av) + (size_t)r * Q * ns;
             T *B = reinterpret_cast<T *>(Bv) + (size_t)r * Q * ns;
-            const T *row = ring + (size_t)st * stage_elems + (size_t)j * nx;  // link i: + i * rows * nx
+            const T *row = ring + (size_t)st * stage_elems + (size_t)j * row_elems;  // link i: + i * rows * row_elems
             uint32_t lm = 0u;
             if (S.tileflag[(x >> 5) + S.nxt * (y + ny * z)]) lm = __ldg(S.link + s);
             if (!(lm & SOLID_BIT)) {
@@ -324,7 +342,7 @@ __global__ void __launch_bounds__(TMA_THREADS) k_stream_collide_tma(const Sim S,
                 for (int i = 0; i < Q; ++i) {
                     const int sx = cx(i) == 1 ? xv0 : (cx(i) == -1 ? xv2 : x);
                     h[i] = ((lm >> i) & 1u) ? load_raw(A, (uint32_t)opp(i) * ns + (uint32_t)s)
-                                            : load_raw(row + (size_t)i * rows * nx, (uint32_t)sx);
+                                            : ring_load(row + (size_t)i * rows * row_elems, sx);
                 }
                 float drho_s = h[0], jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
@@ -382,12 +400,19 @@ __global__ void __launch_bounds__(TMA_THREADS) k_stream_collide_tma(const Sim S,
     if (MODE != 0) block_partial4(am, ax, ay, az, S.fsum + 4 * (size_t)r, &S.ctrl->status);
 }
 
-bool tma_lattice_ok(const Sim &S) {
+static size_t tma_smem(const Sim &S) {
     const int esz = S.precision == LBMD_FP16DEV ? 2 : 4;
-    return !S.fluct && S.nx <= TMA_THREADS && (S.nx * esz) % 16 == 0;
+    const int stages = S.precision == LBMD_FP16DEV ? TmaStages<1>::n : TmaStages<0>::n;
+    const size_t row = ((size_t)S.nx * esz + 127) & ~(size_t)127;  // 128-byte rows
+    return (size_t)stages * Q * (TMA_THREADS / S.nx) * row + 128;   // + the alignment of the ring
 }
 
-static size_t tma_smem(const Sim &S);
+// rows of at most 256 sites and a multiple of 16 bytes, a ring within the
+// 227 KB a CTA may hold, no thermal noise (the noise needs each site's counter)
+bool tma_lattice_ok(const Sim &S) {
+    const int esz = S.precision == LBMD_FP16DEV ? 2 : 4;
+    return !S.fluct && S.nx >= 1 && S.nx <= TMA_THREADS && (S.nx * esz) % 16 == 0 && tma_smem(S) <= 227u * 1024u;
+}
 
 // grant the kernel its shared memory once (not inside a stream capture)
 cudaError_t prepare_stream_collide_tma(const Sim &S) {
@@ -403,12 +428,6 @@ cudaError_t prepare_stream_collide_tma(const Sim &S) {
             e = cudaFuncSetAttribute(k_stream_collide_tma<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     }
     return e;
-}
-
-static size_t tma_smem(const Sim &S) {
-    const int esz = S.precision == LBMD_FP16DEV ? 2 : 4;
-    const int stages = S.precision == LBMD_FP16DEV ? TmaStages<1>::n : TmaStages<0>::n;
-    return (size_t)stages * Q * (TMA_THREADS / S.nx) * S.nx * esz;
 }
 
 cudaError_t launch_stream_collide_tma(const Sim &S, const CUtensorMap &tmA, const void *A, void *B, int groups,

@@ -270,6 +270,7 @@ __device__ __forceinline__ void store_dev(float *base, uint32_t idx, float h) { 
 template <int PREC> struct PopScale;
 template <> struct PopScale<0> { static constexpr float up = 1.0f, down = 1.0f; };
 template <> struct PopScale<1> { static constexpr float up = FP16_SCALE, down = FP16_INV_SCALE; };
+// global memory only (a read-only cached load)
 __device__ __forceinline__ float load_raw(const float *base, uint32_t idx) { return __ldg(base + idx); }
 __device__ __forceinline__ float load_raw(const __half *base, uint32_t idx) { return __half2float(__ldg(base + idx)); }
 __device__ __forceinline__ void store_raw(float *base, uint32_t idx, float v) { base[idx] = v; }
