@@ -500,6 +500,8 @@ def main():
                     help="with --tiles: the particle kernel's chain exchange")
     ap.add_argument("--md-bonded", choices=["lanes", "warp"], default=None,
                     help="with --tiles: who evaluates the particle kernel's bonded terms")
+    ap.add_argument("--md-reserve", choices=["share", "reserve"], default=None,
+                    help="whether the particle kernel's blocks claim their SMs (else the autotuner's choice)")
     ap.add_argument("--slabs", action="store_true",
                     help="with N ranks: split the one lattice into N x-slabs (strong scaling) instead of "
                          "running N replicas")
@@ -533,6 +535,8 @@ def main():
 
     inp = pdist.rank_inputs(w, workloads.build_inputs)
     sim = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"], device=f"cuda:{local}")
+    if args.md_reserve:
+        sim.set_md_reserve(args.md_reserve)
     if args.tiles:
         sim.set_tiles(*args.tiles)
         if args.md_shape:

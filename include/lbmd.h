@@ -52,9 +52,9 @@ typedef enum {
     LBMD_ERR_CUDA = 2,        /* a CUDA runtime call failed (message in lbmd_last_error) */
     LBMD_ERR_NONFINITE = 3,   /* a NaN/Inf appeared in the fluid or bead state */
     LBMD_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up: the tensor-copy lattice
-                                 pass (tiles by = 0) waits at most 2^22 polls for each stage's
-                                 copies; a CTA that gives up latches this code and leaves its
-                                 sites unwritten, so the state after it is not a valid step */
+                                 pass (tiles by = 0) waits at most 2^22 polls or 0.25 s for each
+                                 stage's copies; a CTA that gives up latches this code and leaves
+                                 its sites unwritten, so the state after it is not a valid step */
     LBMD_ERR_CAPACITY = 5,    /* a fixed-capacity list (neighbours, wall sites) overflowed */
     LBMD_ERR_BUFFER = 6       /* device buffer too small or misaligned */
 } lbmd_status;
@@ -299,8 +299,11 @@ lbmd_status lbmd_get_md_bonded(lbmd_handle *h, int32_t *mode);
 
 /* 1 if the particle kernel's blocks are launched with their SMs' whole
  * shared memory (226 KB), so that no block of the lattice pass or the gather
- * shares their SMs; 0 if they take only what they use.  lbmd_autotune times
- * both; the state does not depend on it. */
+ * shares their SMs; 0 if they take only what they use.  lbmd_set_md_reserve:
+ * mode 1 do not reserve, 2 reserve, 0 leave it to lbmd_autotune (which
+ * times both; until it runs, no reserving).  The state does not depend on
+ * it.  LBMD_ERR_INVALID_ARG for another mode. */
+lbmd_status lbmd_set_md_reserve(lbmd_handle *h, int32_t mode);
 lbmd_status lbmd_get_md_reserve(lbmd_handle *h, int32_t *reserve);
 lbmd_status lbmd_get_md_exchange(lbmd_handle *h, int32_t *mode);
 

@@ -206,42 +206,6 @@ constexpr int TMA_THREADS = 256;
 template <int PREC> struct TmaStages;
 template <> struct TmaStages<0> { static constexpr int n = 4; };  // 4 x 19.5 KB with 256-site rows
 template <> struct TmaStages<1> { static constexpr int n = 8; };  // 8 x 9.7 KB
-constexpr unsigned TMA_WAIT_LIMIT = 1u << 22;         // try_wait rounds before a CTA gives up ...
-constexpr unsigned long long TMA_WAIT_NS = 250000000;  // ... or this many ns (a stage takes microseconds)
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-// bounded wait for phase `parity` of a stage's barrier; false: gave up
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    for (unsigned k = 0; k < TMA_WAIT_LIMIT; ++k) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((k & 63u) == 63u && global_ns() - t0 > TMA_WAIT_NS) return false;
-    }
-    return false;
-}
 // a staged population (load_raw is a global-only read: not for the ring)
 __device__ __forceinline__ float ring_load(const float *row, int x) { return row[x]; }
 __device__ __forceinline__ float ring_load(const __half *row, int x) { return __half2float(row[x]); }

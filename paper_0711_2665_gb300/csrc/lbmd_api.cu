@@ -59,6 +59,7 @@ struct lbmd_handle {
     bool md_fixed = false;  // particle-kernel shape set by the caller (the autotuner leaves it)
     int md_exchange = 0;    // chain exchange: 0 the autotuner's choice, 1 push, 2 pull
     int md_bonded = 0;      // bonded terms: 0 the autotuner's choice, 1 every bead's lanes, 2 bonded warps
+    int md_reserve = 0;     // SMs of the particle kernel: 0 the autotuner's choice, 1 shared, 2 reserved
     int graph_steps = 0;
     cudaGraphExec_t gexec = nullptr;
     void *graph_A = nullptr;  // population buffer that was "A" when the graph was captured
@@ -1507,6 +1508,15 @@ lbmd_status lbmd_get_md_bonded(lbmd_handle *h, int32_t *mode) {
     return LBMD_OK;
 }
 
+lbmd_status lbmd_set_md_reserve(lbmd_handle *h, int32_t mode) {
+    if (!h || mode < 0 || mode > 2) return LBMD_ERR_INVALID_ARG;
+    h->md_reserve = mode;
+    if (mode == 0) return LBMD_OK;
+    if ((mode == 2) != (h->S.md_reserve != 0)) drop_graph(h);
+    h->S.md_reserve = mode == 2 ? 1 : 0;
+    return LBMD_OK;
+}
+
 lbmd_status lbmd_get_md_reserve(lbmd_handle *h, int32_t *reserve) {
     if (!h || !reserve) return LBMD_ERR_INVALID_ARG;
     *reserve = h->S.md_reserve ? 1 : 0;
@@ -1655,8 +1665,9 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
           for (int R = 0; R < 2; ++R)
           for (int B = 1; B <= 2; ++B)
           for (int X = 0; X < 2; ++X) {
-            // both bonded modes unless the caller fixed one
+            // both bonded modes and both SM uses unless the caller fixed one
             if (h->md_bonded != 0 && B != h->md_bonded) continue;
+            if (h->md_reserve != 0 && R != h->md_reserve - 1) continue;
             // both exchanges for a chain over several blocks, unless the
             // caller fixed one; a single block exchanges nothing
             const int pull = h->md_exchange == 0 ? X : (h->md_exchange == 2 ? 1 : 0);

@@ -280,6 +280,49 @@ __device__ __forceinline__ void store_dev(__half *base, uint32_t idx, float h) {
 }
 
 // ---------------------------------------------------------------------------
+// mbarriers (sm_90 and later).  Every wait is bounded: at most
+// MBAR_WAIT_LIMIT polls or MBAR_WAIT_NS ns, after which the caller latches
+// ST_TIMEOUT.  An expected phase takes microseconds.
+// ---------------------------------------------------------------------------
+constexpr unsigned MBAR_WAIT_LIMIT = 1u << 22;
+constexpr unsigned long long MBAR_WAIT_NS = 250000000;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// the phase's one arrival, announcing `bytes` of transfers that complete it
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// bounded wait for the phase of parity `parity` to complete; false: gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned k = 0; k < MBAR_WAIT_LIMIT; ++k) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((k & 63u) == 63u && global_ns() - t0 > MBAR_WAIT_NS) return false;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and the Gaussian mapping
 // used for the bead noise: key = (seed_lo, seed_hi ^ realization), counter =
 // (bead, step_lo, substep, step_hi); u = (top 24 bits + 1/2) 2^-24; Box-Muller.

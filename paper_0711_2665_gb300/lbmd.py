@@ -134,6 +134,7 @@ def lib():
         "lbmd_set_md_bonded": [vp, i32],
         "lbmd_get_md_bonded": [vp, P(i32)],
         "lbmd_get_md_reserve": [vp, P(i32)],
+        "lbmd_set_md_reserve": [vp, i32],
         "lbmd_set_drive": [vp, ctypes.c_double, ctypes.c_double],
         "lbmd_step_loop": [vp, i64],
         "lbmd_adjoint_required_bytes": [vp, i32, i32, P(sz)],
@@ -334,6 +335,12 @@ class Simulation:
         m = ctypes.c_int32()
         self._check(self._lib.lbmd_get_md_bonded(self._h, ctypes.byref(m)), "lbmd_get_md_bonded")
         return "warp" if m.value == 2 else "lanes"
+
+    def set_md_reserve(self, mode: str = "auto"):
+        """SMs of the particle kernel: "reserve" (its blocks claim their SMs'
+        shared memory), "share" or "auto" (lbmd_autotune chooses)."""
+        code = {"auto": 0, "share": 1, "reserve": 2}[mode]
+        self._check(self._lib.lbmd_set_md_reserve(self._h, code), "lbmd_set_md_reserve")
 
     def md_reserve(self) -> bool:
         m = ctypes.c_int32()

@@ -288,17 +288,20 @@ def _run_exchange(w, inp, v0, mode, shape, n):
     return out, rebuilds
 
 
-@pytest.mark.parametrize("case", ["chain over 8 blocks", "hashed lists", "shared clusters"])
+@pytest.mark.parametrize("case", ["chain over 8 blocks", "chain over 16 blocks", "hashed lists", "shared clusters"])
 def test_exchange_modes_are_bit_identical(case):
     """Push (every block's replica written) and pull (each block copies the
     beads its force terms read, the whole chain at a list rebuild) move the
     same positions between a chain's blocks: runs that rebuild their lists end
     in the same state bit for bit.  The cases cover a chain spread over a
-    cluster of 8, a chain above 512 beads (cell-hash lists) and uneven chains
-    that share clusters.  The beads start with velocities of 0.1 per
-    component, so that they cross the half skin within the run."""
+    cluster of 8 and of 16, a chain above 512 beads (cell-hash lists) and
+    uneven chains that share clusters (some of one block, which exchange
+    nothing).  The beads start with velocities of 0.1 per component, so that
+    they cross the half skin within the run."""
     if case == "chain over 8 blocks":
         w, shape = small_workload(n_beads=48, chain_seed=11), (4, 8)
+    elif case == "chain over 16 blocks":
+        w, shape = small_workload(nx=48, ny=32, nz=32, wall_x=24, n_beads=160, chain_seed=5), (2, 16)
     elif case == "hashed lists":
         w, shape = workloads.get("plain_fp32", nx=64, ny=48, nz=48, wall_x=40, n_beads=600), (4, 8)
     else:
