@@ -250,7 +250,10 @@ lbmd_status lbmd_step_loop(lbmd_handle *h, int64_t n);
  * by = 0 selects the kernel fed by tensor copies (rows of x staged in shared
  * memory by cp.async.bulk.tensor), with zc in 1..256 row groups per thread
  * block; it needs nx <= 256, rows of a multiple of 16 bytes and no
- * fluctuating fluid (LBMD_ERR_INVALID_ARG otherwise).  The state
+ * fluctuating fluid.  by in {-1,-2,-4,-8,-16} selects the kernel with two x
+ * sites per thread (block (32, -by), 64 sites of a row per warp, pair loads
+ * and stores, shuffles for the x-shifted links), zc in 1..64; it needs an
+ * even nx and no fluctuating fluid.  LBMD_ERR_INVALID_ARG otherwise.  The state
  * (populations, beads) is bit-identical for every shape; the diagnostics
  * sums group their FP32 per-thread partials by shape and so agree to
  * rounding only. */
@@ -319,7 +322,7 @@ lbmd_status lbmd_get_overlap(lbmd_handle *h, int32_t *overlap);
  * current state and keep the fastest; then, unless the caller fixed the
  * particle-kernel shape with lbmd_set_md_shape, time pseudo-steps (gather,
  * particle kernel concurrent with the lattice pass) for every admissible
- * shape and keep the fastest: lanes per bead in {2,4,8}; blocks per chain in
+ * shape and keep the fastest: lanes per bead in {1,2,4,8}; blocks per chain in
  * {1,2,4,8,16} (16 where the device can place such a cluster); push or pull
  * exchange for more than one block, unless the caller fixed it with
  * lbmd_set_md_exchange; both bonded modes, unless fixed with

@@ -189,6 +189,179 @@ __global__ void __launch_bounds__(512, FL ? 1 : 2) k_stream_collide(const Sim S,
 }
 
 // ---------------------------------------------------------------------------
+// The lattice pass with two x sites per thread (x0 = 2k and x0 + 1): a warp
+// covers 64 consecutive sites of one row.  Every link's source row is read as
+// aligned pairs, one 8-byte (FP32) or 4-byte (FP16) load for both sites; a
+// c_x = +-1 link takes the site beyond the pair from the neighbouring lane's
+// pair by a shuffle, and the warp's end lanes (or the lane next to the
+// periodic wrap) load that one directly.  Stores go as pairs, except in tiles
+// with a bounce-back link, which store site by site (solid sites are never
+// written, as in k_stream_collide).  Every address and the loop overhead
+// serve two sites.  The per-site arithmetic is k_stream_collide's,
+// expression for expression; no thermal noise.  Needs an even nx.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 pair_load(const float *base, uint32_t idx) {
+    return __ldg(reinterpret_cast<const float2 *>(base + idx));
+}
+__device__ __forceinline__ float2 pair_load(const __half *base, uint32_t idx) {
+    return __half22float2(__ldg(reinterpret_cast<const __half2 *>(base + idx)));
+}
+__device__ __forceinline__ void pair_store(float *base, uint32_t idx, float a, float b) {
+    *reinterpret_cast<float2 *>(base + idx) = make_float2(a, b);
+}
+__device__ __forceinline__ void pair_store(__half *base, uint32_t idx, float a, float b) {
+    *reinterpret_cast<__half2 *>(base + idx) = __floats2half2_rn(a, b);
+}
+
+// BGK update of one site from its pulled h (stored units): hn, and the
+// site's moments (unscaled) for the diagnostics sums
+template <int PREC>
+__device__ __forceinline__ void bgk_site(const float (&h)[Q], float om, bool has_g, float g0f, float g1f, float g2f,
+                                         float (&hn)[Q], float &drho, float &jx, float &jy, float &jz) {
+    constexpr float up = PopScale<PREC>::up, down = PopScale<PREC>::down;
+    float drho_s = h[0];
+    jx = 0.f; jy = 0.f; jz = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const float sp = h[i] + h[i + 1], dp = h[i] - h[i + 1];
+        drho_s += sp;
+        if (cx(i) == 1) jx += dp;
+        if (cx(i) == -1) jx -= dp;
+        if (cy(i) == 1) jy += dp;
+        if (cy(i) == -1) jy -= dp;
+        if (cz(i) == 1) jz += dp;
+        if (cz(i) == -1) jz -= dp;
+    }
+    drho = drho_s * down;
+    jx *= down; jy *= down; jz *= down;
+    const float rho = 1.0f + drho;
+    const float ir = 1.0f / rho;
+    const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
+    const float usq = 1.5f * (ux * ux + uy * uy + uz * uz);
+    const float rho_s = rho * up;
+    hn[0] = h[0] + om * (wq(0) * (drho_s - rho_s * usq) - h[0]);
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const float cu = 3.0f * ((float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz);
+        const float even = drho_s + rho_s * (0.5f * cu * cu - usq);
+        const float odd = rho_s * cu;
+        hn[i] = h[i] + om * (wq(i) * (even + odd) - h[i]);
+        hn[i + 1] = h[i + 1] + om * (wq(i) * (even - odd) - h[i + 1]);
+    }
+    if (has_g) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            hn[i] += up * (3.0f * wq(i) * ((float)cx(i) * g0f + (float)cy(i) * g1f + (float)cz(i) * g2f));
+    }
+}
+
+template <int PREC, int MODE>
+__global__ void __launch_bounds__(512, 1) k_stream_collide_x2(const Sim S, const void *__restrict__ Av,
+                                                              void *__restrict__ Bv, const int zc, const int nzb) {
+    using T = typename PopT<PREC>::T;
+    const int lane = threadIdx.x;
+    const int x0 = 2 * (blockIdx.x * 32 + lane);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int r = blockIdx.z / nzb;
+    const int z0 = (blockIdx.z - r * nzb) * zc;
+    const int nx = S.nx, ny = S.ny, nz = S.nz;
+    const uint32_t ns = (uint32_t)S.ps;
+    const T *__restrict__ A = reinterpret_cast<const T *>(Av) + (size_t)r * Q * ns;
+    T *__restrict__ B = reinterpret_cast<T *>(Bv) + (size_t)r * Q * ns;
+    float am = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
+    const float om = S.omega;
+    const float g0f = S.g[0], g1f = S.g[1], g2f = S.g[2];
+    const bool has_g = (g0f != 0.f) || (g1f != 0.f) || (g2f != 0.f);
+    const bool act = x0 < nx;
+
+    if (y < ny) {  // warp-uniform: a warp is one row
+        const int xl = x0 == 0 ? nx - 1 : x0 - 1;           // the site before the pair (periodic)
+        const int xr = x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2;  // the site after it
+        const bool edge_l = lane == 0, edge_r = lane == 31 || x0 + 2 >= nx;
+        const int yv0 = (y == 0 ? ny - 1 : y - 1), yv2 = (y == ny - 1 ? 0 : y + 1);
+        const int zend = min(z0 + zc, nz);
+        for (int z = z0; z < zend; ++z) {
+            const int zv0 = (z == 0 ? nz - 1 : z - 1), zv2 = (z == nz - 1 ? 0 : z + 1);
+            const int s0 = x0 + nx * (y + ny * z);
+            float h0[Q], h1[Q];
+            // every lane takes part in the shuffles; lanes past nx load nothing
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int sy = cy(i) == 1 ? yv0 : (cy(i) == -1 ? yv2 : y);
+                const int sz = cz(i) == 1 ? zv0 : (cz(i) == -1 ? zv2 : z);
+                const uint32_t row = (uint32_t)i * ns + (uint32_t)(nx * (sy + ny * sz));
+                float2 c = make_float2(0.f, 0.f);
+                if (act) c = pair_load(A, row + (uint32_t)x0);
+                if (cx(i) == 0) {
+                    h0[i] = c.x;
+                    h1[i] = c.y;
+                } else if (cx(i) == 1) {  // from x - 1: site x0 - 1 is the previous lane's second
+                    float e = __shfl_up_sync(0xffffffffu, c.y, 1);
+                    if (act && edge_l) e = load_raw(A, row + (uint32_t)xl);
+                    h0[i] = e;
+                    h1[i] = c.x;
+                } else {  // from x + 1: site x0 + 2 is the next lane's first
+                    float e = __shfl_down_sync(0xffffffffu, c.x, 1);
+                    if (act && edge_r) e = load_raw(A, row + (uint32_t)xr);
+                    h0[i] = c.y;
+                    h1[i] = e;
+                }
+            }
+            if (!act) continue;
+            // a flagged tile (x0 and x0 + 1 share it) holds a bounce-back link somewhere
+            uint32_t lm0 = 0u, lm1 = 0u;
+            const bool flagged = S.tileflag[(x0 >> 5) + S.nxt * (y + ny * z)] != 0;
+            if (flagged) {
+                const uint2 lw = __ldg(reinterpret_cast<const uint2 *>(S.link + s0));
+                lm0 = lw.x;
+                lm1 = lw.y;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    if ((lm0 >> i) & 1u) h0[i] = load_raw(A, (uint32_t)opp(i) * ns + (uint32_t)s0);
+                    if ((lm1 >> i) & 1u) h1[i] = load_raw(A, (uint32_t)opp(i) * ns + (uint32_t)s0 + 1u);
+                }
+            }
+            float n0[Q], n1[Q], d0, jx0, jy0, jz0, d1, jx1, jy1, jz1;
+            bgk_site<PREC>(h0, om, has_g, g0f, g1f, g2f, n0, d0, jx0, jy0, jz0);
+            bgk_site<PREC>(h1, om, has_g, g0f, g1f, g2f, n1, d1, jx1, jy1, jz1);
+            const bool f0 = !(lm0 & SOLID_BIT), f1 = !(lm1 & SOLID_BIT);
+            if (MODE != 0) {
+                if (f0 && x0 >= S.own_lo && x0 < S.own_hi) { am += d0; ax += jx0; ay += jy0; az += jz0; }
+                if (f1 && x0 + 1 >= S.own_lo && x0 + 1 < S.own_hi) { am += d1; ax += jx1; ay += jy1; az += jz1; }
+            }
+            if (!flagged) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) pair_store(B, (uint32_t)i * ns + (uint32_t)s0, n0[i], n1[i]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    if (f0) store_raw(B, (uint32_t)i * ns + (uint32_t)s0, n0[i]);
+                    if (f1) store_raw(B, (uint32_t)i * ns + (uint32_t)s0 + 1u, n1[i]);
+                }
+            }
+        }
+    }
+    if (MODE != 0) block_partial4(am, ax, ay, az, S.fsum + 4 * (size_t)r, &S.ctrl->status);
+}
+
+bool x2_lattice_ok(const Sim &S) { return !S.fluct && S.nx % 2 == 0; }
+
+cudaError_t launch_stream_collide_x2(const Sim &S, const void *A, void *B, int by, int zc, bool diag,
+                                     cudaStream_t st) {
+    if (!x2_lattice_ok(S) || by < 1 || by > 16 || zc < 1) return cudaErrorInvalidValue;
+    const int nzb = (S.nz + zc - 1) / zc;
+    const dim3 grid((S.nx + 63) / 64, (S.ny + by - 1) / by, nzb * S.n_real), block(32, by);
+#define X2_LAUNCH(P, M) k_stream_collide_x2<P, M><<<grid, block, 0, st>>>(S, A, B, zc, nzb)
+    if (S.precision == LBMD_FP16DEV) {
+        if (diag) X2_LAUNCH(1, 1); else X2_LAUNCH(1, 0);
+    } else {
+        if (diag) X2_LAUNCH(0, 1); else X2_LAUNCH(0, 0);
+    }
+#undef X2_LAUNCH
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // The lattice pass fed by tensor copies.  A CTA of 256 threads owns a run of
 // row groups; a group is floor(256 / nx) consecutive x rows (rows over y, then
 // z, then realizations), one thread per site.  For every row of a group and

@@ -313,6 +313,7 @@ cudaError_t lattice_pass(lbmd_handle *h, const Sim &S, int by, int zc, bool diag
         const CUtensorMap &m = h->popA == (void *)(h->dbuf + h->L.popA) ? h->tmap[0] : h->tmap[1];
         return launch_stream_collide_tma(S, m, h->popA, h->popB, zc, diag, h->st);
     }
+    if (by < 0) return launch_stream_collide_x2(S, h->popA, h->popB, -by, zc, diag, h->st);
     return launch_stream_collide(S, h->popA, h->popB, by, zc, diag, h->st);
 }
 
@@ -1407,7 +1408,10 @@ lbmd_status lbmd_adjoint(lbmd_handle *h, int32_t K, int32_t C, void *scratch, si
             CK(cudaEventRecord(h->ev_join, h->aux));
             {
                 ProfScope ps(h, K_SC_ADJOINT, h->st);
-                CK(launch_sc_adjoint(S, An, Lin, Lout, h->by, h->zc, h->st));
+                // the adjoint pass has the scalar kernel's block shape: the
+                // step's tiles where they are the scalar kernel's, else (4, 4)
+                const bool scalar = h->by > 0;
+                CK(launch_sc_adjoint(S, An, Lin, Lout, scalar ? h->by : 4, scalar ? h->zc : 4, h->st));
             }
             CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
             {
@@ -1452,9 +1456,12 @@ lbmd_status lbmd_set_graph(lbmd_handle *h, int32_t steps_per_graph) {
 
 lbmd_status lbmd_set_tiles(lbmd_handle *h, int32_t by, int32_t zc) {
     if (!h) return LBMD_ERR_INVALID_ARG;
+    const int aby = by < 0 ? -by : by;
     if (by == 0) {
         if (!h->tma_ok || zc < 1 || zc > 256) return LBMD_ERR_INVALID_ARG;
-    } else if (!(by == 1 || by == 2 || by == 4 || by == 8 || by == 16) || zc < 1 || zc > 64) {
+    } else if (by < 0 && !x2_lattice_ok(h->S)) {
+        return LBMD_ERR_INVALID_ARG;
+    } else if (!(aby == 1 || aby == 2 || aby == 4 || aby == 8 || aby == 16) || zc < 1 || zc > 64) {
         return LBMD_ERR_INVALID_ARG;
     }
     if (by != h->by || zc != h->zc) drop_graph(h);
@@ -1590,6 +1597,20 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
             h->launches += reps + 1;
             if (ms < best) { best = ms; bb = by; bz = zc; }
         }
+    // two x sites per thread (tiles (-by, zc))
+    for (int by : BYS)
+        for (int zc : ZCS) {
+            if (!x2_lattice_ok(h->S) || zc > h->cfg.nz) break;
+            CK(lattice_pass(h, h->S, -by, zc, true));
+            CK(cudaEventRecord(a, h->st));
+            for (int k = 0; k < reps; ++k) CK(lattice_pass(h, h->S, -by, zc, true));
+            CK(cudaEventRecord(b, h->st));
+            CK(cudaEventSynchronize(b));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, a, b));
+            h->launches += reps + 1;
+            if (ms < best) { best = ms; bb = -by; bz = zc; }
+        }
     // the tensor-copy kernel, row groups per thread block
     static const int GROUPS[] = {2, 4, 8, 16, 32, 64};
     for (int g : GROUPS) {
@@ -1656,7 +1677,7 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
 #undef CKT
         return cudaSuccess;
     };
-    static const int TS[] = {2, 4, 8};
+    static const int TS[] = {1, 2, 4, 8};
     static const int CS[] = {1, 2, 4, 8, 16};
     float best_md = 1e30f;
     int bt = 0, bc = 0, bx = h->S.md_pull, bb_w = h->S.md_bw, brs = h->S.md_reserve;

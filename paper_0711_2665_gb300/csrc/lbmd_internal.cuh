@@ -475,6 +475,9 @@ cudaError_t launch_stream_collide(const Sim &S, const void *A, void *B, int by, 
 // a multiple of 16 bytes): tmA describes buffer A as a 5-D tensor
 // (x, y, z, link, realization) with one-row boxes; groups: row groups per CTA
 bool tma_lattice_ok(const Sim &S);
+bool x2_lattice_ok(const Sim &S);
+cudaError_t launch_stream_collide_x2(const Sim &S, const void *A, void *B, int by, int zc, bool diag,
+                                     cudaStream_t st);
 cudaError_t prepare_stream_collide_tma(const Sim &S);
 cudaError_t launch_stream_collide_tma(const Sim &S, const CUtensorMap &tmA, const void *A, void *B, int groups,
                                       bool diag, cudaStream_t st);
