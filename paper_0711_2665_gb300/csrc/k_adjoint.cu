@@ -671,15 +671,16 @@ cudaError_t launch_bead_adjoint(const Sim &S, const void *A, const float *Lin, c
 // corner-site fix-up: lam_f_i(x) += lam_u(x) . (c_i - u(x)) / rho(x)  (u = j / rho),
 // added through the transposed pull.  The first (bead, corner) pair to stamp a
 // site with this step's (negative) tag serves it; distinct sites have
-// distinct targets, so the read-modify-writes do not race.
+// distinct targets, so the read-modify-writes do not race.  The stamps are
+// the adjoint's own (the forward replay beside it stamps S.stamp).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_adj_fixup(const Sim S, const float *__restrict__ Av, float *__restrict__ Lout,
                                                    const int *__restrict__ adj_node, unsigned long long *__restrict__ LU,
-                                                   const int tag) {
+                                                   int *__restrict__ stamp, const int tag) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= 8 * S.total_beads) return;
     const int gnode = adj_node[k];
-    if (gnode < 0 || atomicExch(S.stamp + gnode, tag) == tag) return;
+    if (gnode < 0 || atomicExch(stamp + gnode, tag) == tag) return;
     const size_t ns = (size_t)S.ns;
     const int r = (int)(gnode / ns);
     const int s = (int)(gnode - (size_t)r * ns);
@@ -712,12 +713,13 @@ __global__ void __launch_bounds__(256) k_adj_fixup(const Sim S, const float *__r
     }
 }
 
-cudaError_t launch_adj_fixup(const Sim &S, const void *A, float *Lout, const int *adj_node, unsigned long long *LU, int tag,
+cudaError_t launch_adj_fixup(const Sim &S, const void *A, float *Lout, const int *adj_node, unsigned long long *LU, int *stamp,
+                             int tag,
                              cudaStream_t st) {
     if (S.total_beads == 0) return cudaSuccess;
     const int threads = 256;
     const int blocks = (8 * S.total_beads + threads - 1) / threads;
-    k_adj_fixup<<<blocks, threads, 0, st>>>(S, reinterpret_cast<const float *>(A), Lout, adj_node, LU, tag);
+    k_adj_fixup<<<blocks, threads, 0, st>>>(S, reinterpret_cast<const float *>(A), Lout, adj_node, LU, stamp, tag);
     return cudaGetLastError();
 }
 

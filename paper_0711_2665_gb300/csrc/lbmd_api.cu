@@ -52,6 +52,11 @@ struct lbmd_handle {
     cudaStream_t st = nullptr, aux = nullptr, aux2 = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr, ev_pre = nullptr, ev_lists = nullptr;
     cudaEvent_t ev_lists_cap = nullptr;  // ev_lists inside a stream capture (a captured record cannot be waited on outside it)
+    // the adjoint's backward sweep: its streams (the bead adjoint on baux),
+    // fork/join, start, and per record buffer the ends of replay and backward
+    cudaStream_t bst = nullptr, baux = nullptr;
+    cudaEvent_t ev_bfork = nullptr, ev_bjoin = nullptr, ev_bstart = nullptr, ev_rep[2] = {nullptr, nullptr},
+                ev_bwd[2] = {nullptr, nullptr};
     int by = 8, zc = 8;   // by = 0: the tensor-copy lattice kernel with zc row groups per block
     CUtensorMap tmap[2];  // the two population buffers (at L.popA, L.popB) as 5-D tensors
     bool tma_ok = false;  // tmap encoded and the lattice fits the tensor-copy kernel
@@ -775,6 +780,12 @@ lbmd_status lbmd_init(const lbmd_config *cfg, const uint8_t *solid, const int32_
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_pre, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_lists, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_lists_cap, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->bst, cudaStreamNonBlocking, hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->baux, cudaStreamNonBlocking, hi);
+        cudaEvent_t *bev[] = {&h->ev_bfork, &h->ev_bjoin, &h->ev_bstart, &h->ev_rep[0], &h->ev_rep[1], &h->ev_bwd[0],
+                              &h->ev_bwd[1]};
+        for (cudaEvent_t *ev : bev)
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
         if (e != cudaSuccess) { cuda_fail(h, e, "stream/event creation"); return bail(LBMD_ERR_CUDA); }
     }
     const Layout &L = h->L;
@@ -1256,7 +1267,7 @@ struct AdjLayout {
     size_t pop, bead, traj;      // bytes of one population set, bead state (hi, lo, v), trajectory record
     size_t ck_rec, seg_rec;      // bytes of one checkpoint, one replayed step
     int nck, nseg;               // checkpoints (+ the final state), steps per segment
-    size_t ck, seg, lamA, lamB, lam_r, lam_v, LU, adj_node, dpar, total;
+    size_t ck, seg, lamA, lamB, lam_r, lam_v, LU, adj_node, dpar, stamp, total;
 };
 
 AdjLayout adj_layout(const lbmd_handle *h, int K, int C) {
@@ -1273,7 +1284,7 @@ AdjLayout adj_layout(const lbmd_handle *h, int K, int C) {
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
     a.ck = take(a.ck_rec * a.nck);
-    a.seg = take(a.seg_rec * a.nseg);
+    a.seg = take(2 * a.seg_rec * a.nseg);  // two segments: one replayed while the other runs backward
     a.lamA = take(a.pop);
     a.lamB = take(a.pop);
     a.lam_r = take(TB * 16);
@@ -1281,6 +1292,7 @@ AdjLayout adj_layout(const lbmd_handle *h, int K, int C) {
     a.LU = take((size_t)h->cfg.n_real * 3 * S.ns * 8);
     a.adj_node = take(TB * 8 * 4);
     a.dpar = take((size_t)h->cfg.n_real * 2 * sizeof(double));
+    a.stamp = take((size_t)h->cfg.n_real * S.ns * sizeof(int));
     a.total = o;
     return a;
 }
@@ -1372,6 +1384,7 @@ lbmd_status lbmd_adjoint(lbmd_handle *h, int32_t K, int32_t C, void *scratch, si
     unsigned long long *LU = (unsigned long long *)(b + a.LU);
     int *adj_node = (int *)(b + a.adj_node);
     double *dpar = (double *)(b + a.dpar);
+    int *stamp = (int *)(b + a.stamp);
     std::vector<float4> lr0(TB);
     for (int q = 0; q < n_real; ++q)
         for (int i = h->offsets[q]; i < h->offsets[q + 1]; ++i)
@@ -1380,48 +1393,76 @@ lbmd_status lbmd_adjoint(lbmd_handle *h, int32_t K, int32_t C, void *scratch, si
     CK(cudaMemsetAsync(Lout, 0, a.pop, h->st));
     CK(cudaMemsetAsync(LU, 0, (size_t)n_real * 3 * S.ns * 8, h->st));
     CK(cudaMemsetAsync(dpar, 0, (size_t)n_real * 2 * sizeof(double), h->st));
+    CK(cudaMemsetAsync(stamp, 0, (size_t)n_real * S.ns * sizeof(int), h->st));
     CK(cudaMemsetAsync(lam_v, 0, (size_t)TB * 16, h->st));
     CK(cudaMemcpyAsync(lam_r, lr0.data(), (size_t)TB * 16, cudaMemcpyHostToDevice, h->st));
 
-    // backward sweep, segment by segment from the last
-    for (int j = (K - 1) / C; j >= 0; --j) {
+    // Backward sweep, segment by segment from the last.  A segment is
+    // replayed from its checkpoint on the main stream, recording every
+    // step's populations and the MD trajectory, then run backward on the
+    // adjoint's own streams (bst, and baux for the bead adjoint beside the
+    // lattice adjoint).  The replay of segment j - 1 runs while segment j
+    // runs backward: the records alternate between two buffers, a replay
+    // waits for the backward pass that last read its buffer, a backward pass
+    // for its replay.  The backward kernels read only the records, the
+    // adjoint scratch and the geometry.
+    auto seg_buf = [&](int j) { return b + a.seg + (size_t)(j & 1) * a.seg_rec * a.nseg; };
+    auto replay = [&](int j) -> lbmd_status {
         const int n0 = j * C, n1 = std::min(K, n0 + C);
-        if ((st = restore(j, step0 + n0)) != LBMD_OK) return st;
+        lbmd_status s2 = restore(j, step0 + n0);
+        if (s2 != LBMD_OK) return s2;
         for (int n = n0; n < n1; ++n) {
-            char *rec = b + a.seg + (size_t)(n - n0) * a.seg_rec;
+            char *rec = seg_buf(j) + (size_t)(n - n0) * a.seg_rec;
             CK(cudaMemcpyAsync(rec, h->popA, a.pop, cudaMemcpyDeviceToDevice, h->st));
             S.traj = (float4 *)(rec + align256(a.pop));
-            st = enqueue_step(h);
+            s2 = enqueue_step(h);
             S.traj = nullptr;
-            if (st != LBMD_OK) return st;
+            if (s2 != LBMD_OK) return s2;
         }
+        CK(cudaEventRecord(h->ev_rep[j & 1], h->st));
+        return LBMD_OK;
+    };
+    CK(cudaEventRecord(h->ev_bstart, h->st));  // the adjoint's starting values are set
+    CK(cudaStreamWaitEvent(h->bst, h->ev_bstart, 0));
+    const int jl = (K - 1) / C;
+    if ((st = replay(jl)) != LBMD_OK) return st;
+    for (int j = jl; j >= 0; --j) {
+        const int n0 = j * C, n1 = std::min(K, n0 + C);
+        CK(cudaStreamWaitEvent(h->bst, h->ev_rep[j & 1], 0));
         for (int n = n1 - 1; n >= n0; --n) {
-            const char *rec = b + a.seg + (size_t)(n - n0) * a.seg_rec;
+            const char *rec = seg_buf(j) + (size_t)(n - n0) * a.seg_rec;
             const void *An = rec;
             const float4 *trj = (const float4 *)(rec + align256(a.pop));
-            CK(cudaEventRecord(h->ev_fork, h->st));
-            CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+            CK(cudaEventRecord(h->ev_bfork, h->bst));
+            CK(cudaStreamWaitEvent(h->baux, h->ev_bfork, 0));
             {
-                ProfScope ps(h, K_BEAD_ADJOINT, h->aux);
-                CK(launch_bead_adjoint(S, An, Lin, trj, lam_r, lam_v, LU, adj_node, dpar, step0 + n, h->aux));
+                ProfScope ps(h, K_BEAD_ADJOINT, h->baux);
+                CK(launch_bead_adjoint(S, An, Lin, trj, lam_r, lam_v, LU, adj_node, dpar, step0 + n, h->baux));
             }
-            CK(cudaEventRecord(h->ev_join, h->aux));
+            CK(cudaEventRecord(h->ev_bjoin, h->baux));
             {
-                ProfScope ps(h, K_SC_ADJOINT, h->st);
+                ProfScope ps(h, K_SC_ADJOINT, h->bst);
                 // the adjoint pass has the scalar kernel's block shape: the
                 // step's tiles where they are the scalar kernel's, else (4, 4)
                 const bool scalar = h->by > 0;
-                CK(launch_sc_adjoint(S, An, Lin, Lout, scalar ? h->by : 4, scalar ? h->zc : 4, h->st));
+                CK(launch_sc_adjoint(S, An, Lin, Lout, scalar ? h->by : 4, scalar ? h->zc : 4, h->bst));
             }
-            CK(cudaStreamWaitEvent(h->st, h->ev_join, 0));
+            CK(cudaStreamWaitEvent(h->bst, h->ev_bjoin, 0));
             {
-                ProfScope ps(h, K_ADJ_FIXUP, h->st);
-                CK(launch_adj_fixup(S, An, Lout, adj_node, LU, -1 - (int)((step0 + n) & 0x3fffffffll), h->st));
+                ProfScope ps(h, K_ADJ_FIXUP, h->bst);
+                CK(launch_adj_fixup(S, An, Lout, adj_node, LU, stamp, -1 - (int)((step0 + n) & 0x3fffffffll), h->bst));
             }
             std::swap(Lin, Lout);
             h->launches += 3;
         }
+        CK(cudaEventRecord(h->ev_bwd[j & 1], h->bst));
+        if (j > 0) {
+            // segment j - 1's records go where segment j + 1's were read
+            if (j + 1 <= jl) CK(cudaStreamWaitEvent(h->st, h->ev_bwd[(j + 1) & 1], 0));
+            if ((st = replay(j - 1)) != LBMD_OK) return st;
+        }
     }
+    CK(cudaStreamWaitEvent(h->st, h->ev_bwd[0], 0));  // segment 0's backward pass ends the sweep
 
     // outputs, and the state after the K steps
     std::vector<float4> lr(TB);
@@ -1828,6 +1869,8 @@ void lbmd_destroy(lbmd_handle *h) {
     if (h->st) cudaStreamSynchronize(h->st);
     if (h->aux) cudaStreamSynchronize(h->aux);
     if (h->aux2) cudaStreamSynchronize(h->aux2);
+    if (h->bst) cudaStreamSynchronize(h->bst);
+    if (h->baux) cudaStreamSynchronize(h->baux);
     for (auto &p : h->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : h->free_events) cudaEventDestroy(e);
     drop_graph(h);
@@ -1837,8 +1880,12 @@ void lbmd_destroy(lbmd_handle *h) {
     if (h->ev_pre) cudaEventDestroy(h->ev_pre);
     if (h->ev_lists) cudaEventDestroy(h->ev_lists);
     if (h->ev_lists_cap) cudaEventDestroy(h->ev_lists_cap);
+    for (cudaEvent_t ev : {h->ev_bfork, h->ev_bjoin, h->ev_bstart, h->ev_rep[0], h->ev_rep[1], h->ev_bwd[0], h->ev_bwd[1]})
+        if (ev) cudaEventDestroy(ev);
     if (h->aux) cudaStreamDestroy(h->aux);
     if (h->aux2) cudaStreamDestroy(h->aux2);
+    if (h->bst) cudaStreamDestroy(h->bst);
+    if (h->baux) cudaStreamDestroy(h->baux);
     delete h;
 }
 

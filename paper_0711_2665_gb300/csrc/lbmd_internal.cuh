@@ -512,7 +512,7 @@ cudaError_t launch_sc_adjoint(const Sim &S, const void *A, const float *Lin, flo
 size_t bead_adjoint_smem(const Sim &S);
 cudaError_t launch_bead_adjoint(const Sim &S, const void *A, const float *Lin, const float4 *trj, float4 *lam_r, float4 *lam_v,
                                 unsigned long long *LU, int *adj_node, double *dpar, long long step, cudaStream_t st);
-cudaError_t launch_adj_fixup(const Sim &S, const void *A, float *Lout, const int *adj_node, unsigned long long *LU, int tag,
-                             cudaStream_t st);
+cudaError_t launch_adj_fixup(const Sim &S, const void *A, float *Lout, const int *adj_node, unsigned long long *LU, int *stamp,
+                             int tag, cudaStream_t st);
 
 }  // namespace lbmd
