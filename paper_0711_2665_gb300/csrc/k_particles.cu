@@ -1032,9 +1032,15 @@ __device__ __forceinline__ void sync_all(cg::cluster_group &cl, int C) {
 }
 
 // ---------------------------------------------------------------------------
-// the particle kernel (one cluster of C blocks per realization)
+// the particle kernel (one cluster of C blocks per realization).  VAR 0 and 1
+// are the lean forms of the velocity-Verlet cycle without a trajectory
+// record, with the push (0) or pull (1) exchange fixed at compile time; VAR
+// 2 has every path (exchange from S.md_pull, the SPV integrator, the
+// adjoint's trajectory record).  The MD cycle is bound by the latency of its
+// dependent sub-steps, and a smaller loop body runs it faster (about 6% on a
+// 1000-bead chain over 16 blocks).
 // ---------------------------------------------------------------------------
-template <int T, bool BWM>
+template <int T, bool BWM, int VAR>
 __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, const int Nmax, const int Nc) {
     extern __shared__ __align__(16) char smem_raw[];
     __shared__ int s_flag[2], s_err, s_nhalo;
@@ -1053,7 +1059,8 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
     const bool owner = own && lt == 0;  // the lane that publishes the bead
     const bool bw = BWM && threadIdx.x >= blockDim.x - 32 * bonded_warps(Nc);  // the warps of the bonded terms
     const int first = rank * Nc, last = min(first + Nc, N) - 1;  // the block's beads
-    const bool pull = S.md_pull != 0 && cc > 1;  // block-uniform
+    const bool pull_mode = VAR == 2 ? S.md_pull != 0 : VAR == 1;
+    const bool pull = pull_mode && cc > 1;  // block-uniform
     const long long step = S.ctrl->step;
     const float fnx = (float)S.bnx, fny = (float)S.ny, fnz = (float)S.nz;
     unsigned long long tclk = clock64();
@@ -1078,7 +1085,7 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
         const float4 uu = S.up[off + p];
         up = make_float3(uu.x, uu.y, uu.z);
     }
-    float4 *const trj = S.traj;  // trajectory record for the adjoint (usually null)
+    float4 *const trj = VAR == 2 ? S.traj : nullptr;  // trajectory record for the adjoint (usually null)
     const int TB = S.total_beads;
     if (trj && owner) {
         trj[(size_t)traj_slot_hi(S.M, S.Mb, 0) * TB + off + p] = mh;
@@ -1118,7 +1125,7 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
     // evaluates the forces there and updates v with the exact
     // Ornstein-Uhlenbeck step v' = c v + (1 - c) u_p + g1 F + sig z; the
     // fluid's impulse is v' - v - h F; a last half drift closes the cycle.
-    const bool spv = S.integrator == 1;
+    const bool spv = VAR == 2 && S.integrator == 1;
     for (int sub = 0; sub < S.M; ++sub) {
         float3 xi = make_float3(0.f, 0.f, 0.f);
         if (own && amp > 0.0f && !spv) xi = amp * gauss3(S.seed, S.real_base + (uint32_t)r, (uint32_t)p, step, (uint32_t)sub);
@@ -1241,7 +1248,7 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
     // pull: no block leaves while another may still be reading its replica
     // (push: the last writes into another block's shared memory came before
     // the last sub-step's cluster barrier)
-    if (S.md_pull) sync_all(cl, C);
+    if (pull_mode) sync_all(cl, C);
     if (owner) sm.jbuf[pl] = make_float4(J.x, J.y, J.z, 0.f);
     __syncthreads();
     phase_mark(S, 2, tclk);
@@ -1284,7 +1291,11 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
 // can be resident at once (0: the device cannot schedule one).
 template <int T>
 static cudaError_t launch_particles_t(const Sim &S, const MdShape &m, cudaStream_t st, int *n_fit) {
-    auto kern = m.bw ? k_particles<T, true> : k_particles<T, false>;
+    // the lean kernels where no SPV cycle and no trajectory record is asked for
+    const bool full = S.integrator == 1 || S.traj != nullptr;
+    auto kern = full ? (m.bw ? k_particles<T, true, 2> : k_particles<T, false, 2>)
+                : S.md_pull ? (m.bw ? k_particles<T, true, 1> : k_particles<T, false, 1>)
+                            : (m.bw ? k_particles<T, true, 0> : k_particles<T, false, 0>);
     size_t dyn = m.launch_smem;
     if (dyn > m.smem) {  // reserving: the opt-in maximum counts static and dynamic shared memory together
         cudaFuncAttributes fa;
