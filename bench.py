@@ -211,37 +211,6 @@ def cpu_baseline(w, budget_s=10.0):
     return oracle_on_host_cores(w, warm=1, steps=0, budget_s=budget_s)
 
 
-def _md_shape_check(sim, timed, candidates, steps=40):
-    """The autotuner ranks particle shapes by pseudo-steps (gather, particle
-    kernel beside the lattice pass); for an ensemble it can rank the shape
-    with one block per chain below one that is faster in real steps.  Time
-    real device-side step loops of the autotuner's shape and of each
-    candidate (lanes per bead, blocks per chain, exchange, bonded mode),
-    keep the fastest, and return what was timed (us per step)."""
-    cur = (*sim.md_shape(), sim.md_exchange(), sim.md_bonded())
-    sim.step_loop(10)
-    times = {str(list(cur)): 1e6 * timed(lambda: sim.step_loop(steps)) / steps}
-    best, best_t = cur, times[str(list(cur))]
-    for T, C, X, B in candidates:
-        try:
-            sim.set_md_bonded("lanes")
-            sim.set_md_shape(T, C)
-            sim.set_md_bonded(B)
-            sim.set_md_exchange(X)
-        except Exception:
-            continue
-        sim.step_loop(10)
-        t = 1e6 * timed(lambda: sim.step_loop(steps)) / steps
-        times[str([T, C, X, B])] = t
-        if t < best_t:
-            best, best_t = (T, C, X, B), t
-    sim.set_md_bonded("lanes")
-    sim.set_md_shape(best[0], best[1])
-    sim.set_md_bonded(best[3])
-    sim.set_md_exchange(best[2])
-    return {"us_per_step": {k: round(v, 1) for k, v in times.items()}, "kept": list(best)}
-
-
 def _sc_roofline(sim, w, peak, peak_kind, steps=10, flush=None):
     """Stream-collide roofline from per-launch CUDA events over a few eager
     steps: inside the step (sharing the GPU with the particle kernel) and
@@ -353,9 +322,6 @@ def extra_measurements(dev, stream, peak, peak_kind, forms, tiles=None, headline
             by, zc = tiles
         else:
             by, zc = sim.autotune(8)
-        shape_check = None
-        if not tiles and w["n_real"] > 1:
-            shape_check = _md_shape_check(sim, timed, [(1, 1, "push", "warp")])
         sites = w["nx"] * w["ny"] * w["nz"] * w["n_real"]
         fits_l2 = sites * (152 if w["precision"] == "fp32" else 76) < 2 * L2_BYTES
         if fits_l2:
@@ -390,8 +356,6 @@ def extra_measurements(dev, stream, peak, peak_kind, forms, tiles=None, headline
                      "md_exchange": sim.md_exchange(), "md_bonded": sim.md_bonded(), "md_reserve": sim.md_reserve(),
                      "launch": launch, "roofline": rf,
                      "step_frac": rf["algorithmic_bytes_per_launch"] / (t / K) / 1e9 / peak}
-        if shape_check:
-            out[name]["md_shape_check"] = shape_check
         sim.close()
     if headline and headline[0] == "lattice_4m_fp32":
         out["speedups_vs_headline_fp32"] = {
