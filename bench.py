@@ -211,6 +211,13 @@ def cpu_baseline(w, budget_s=10.0):
     return oracle_on_host_cores(w, warm=1, steps=0, budget_s=budget_s)
 
 
+def _lattice_kernel(sim):
+    """The lattice-pass kernel the tiles select: one site per thread (by > 0),
+    fed by tensor copies (by = 0) or two x sites per thread (by < 0)."""
+    by = sim.tiles()[0]
+    return "k_stream_collide" if by > 0 else ("k_stream_collide_tma" if by == 0 else "k_stream_collide_x2")
+
+
 def _sc_roofline(sim, w, peak, peak_kind, steps=10, flush=None):
     """Stream-collide roofline from per-launch CUDA events over a few eager
     steps: inside the step (sharing the GPU with the particle kernel) and
@@ -233,7 +240,7 @@ def _sc_roofline(sim, w, peak, peak_kind, steps=10, flush=None):
     sim.set_overlap(True)
     achieved = b / (us["alone"] * 1e-6) / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_kind": peak_kind, "kernel": "k_stream_collide", "algorithmic_bytes_per_launch": b,
+            "peak_kind": peak_kind, "kernel": _lattice_kernel(sim), "algorithmic_bytes_per_launch": b,
             "us_per_launch_alone": us["alone"], "us_per_launch_in_step": us["in_step"],
             "frac_in_step": b / (us["in_step"] * 1e-6) / 1e9 / peak}
 
@@ -627,7 +634,8 @@ def main():
     alg = bytes_site * sites
     achieved = alg / (ms_sc / n_sc * 1e-3) / 1e9 if n_sc else None
     alone = _sc_roofline(sim, w, peak, peak_kind, steps=min(args.steps, 10), flush=flush_l2 if flush else None)
-    traffic = _traffic_record(w["name"], sites) if world == 1 else None
+    # the committed capture is of the one-site-per-thread kernel
+    traffic = _traffic_record(w["name"], sites) if world == 1 and sim.tiles()[0] > 0 else None
     # the step's own kernels: the particle kernel sets a single chain's step;
     # it is latency-bound (100 cluster barriers per LB step) and has no byte
     # or flop roofline, so the roofline is the lattice kernel's and the
@@ -642,7 +650,7 @@ def main():
                     "us_per_md_substep": 1e3 * kern_ms["particles"] / n_p / (w["md_outer"] * w["md_inner"])}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
-                "peak_kind": peak_kind, "kernel": "k_stream_collide", "algorithmic_bytes_per_launch": alg,
+                "peak_kind": peak_kind, "kernel": _lattice_kernel(sim), "algorithmic_bytes_per_launch": alg,
                 "us_per_launch_in_step": 1e3 * ms_sc / n_sc if n_sc else None,
                 "us_per_launch_alone": alone["us_per_launch_alone"], "frac_alone": alone["frac"],
                 "dominant_kernel": dominant}
