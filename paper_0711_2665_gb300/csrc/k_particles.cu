@@ -956,24 +956,6 @@ cudaError_t launch_lists(const Sim &S, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// The list build, called out of line or inlined.  Out of line, the rare
-// rebuild's code stays out of the MD sub-step loop, which then fits the
-// instruction cache better (the headline's particle kernel: 183 -> 172 us per
-// LB step), at the price of a few registers.  Inlined, the kernel keeps its
-// register count, which the bead-lanes shapes of the ensemble, sharing SMs
-// with the lattice pass, need.
-template <int T>
-__device__ __noinline__ void build_lists_call(const Sim &S, const PSmem &sm, int buf, int N, int p, int pl, bool own,
-                                              int rank, int Nc, bool halo, int *clear_flag, int *s_err, int *nhalo) {
-    build_lists_body<T>(S, sm, buf, N, p, pl, own, rank, Nc, halo, clear_flag, s_err, nhalo);
-}
-template <int T, bool OUT_OF_LINE>
-__device__ __forceinline__ void build_lists(const Sim &S, const PSmem &sm, int buf, int N, int p, int pl, bool own,
-                                            int rank, int Nc, bool halo, int *clear_flag, int *s_err, int *nhalo) {
-    if constexpr (OUT_OF_LINE) build_lists_call<T>(S, sm, buf, N, p, pl, own, rank, Nc, halo, clear_flag, s_err, nhalo);
-    else build_lists_body<T>(S, sm, buf, N, p, pl, own, rank, Nc, halo, clear_flag, s_err, nhalo);
-}
-
 // Copy beads of other blocks of the chain from their owners' replicas
 // (buffer buf, written there before the last cluster barrier) into this
 // block's: the halo, or with all = true every bead this block does not own.
@@ -993,6 +975,37 @@ __device__ __forceinline__ void pull_beads(cg::cluster_group &cl, const PSmem &s
         plo[q] = b;
     }
     __syncthreads();
+}
+
+// A list rebuild in the MD cycle: with the pull exchange the whole chain is
+// first copied into this block's replica, then the block's lists (and halo)
+// are built.  Called out of line or inlined.  Out of line, the rare
+// rebuild's code stays out of the MD sub-step loop, which then fits the
+// instruction cache better (the 400-bead particle kernel: 183 -> 172 us per
+// LB step), at the price of a few registers.  Inlined, the kernel keeps its
+// register count, which the bead-lanes shapes of the ensemble, sharing SMs
+// with the lattice pass, need.
+template <int T>
+__device__ __forceinline__ void rebuild_body(const Sim &S, const PSmem &sm, int buf, int N, int p, int pl, bool own,
+                                             int rank, int Nc, int c0, bool pull, int *clear_flag, int *s_err,
+                                             int *nhalo) {
+    if (pull) {
+        cg::cluster_group cl = cg::this_cluster();
+        pull_beads(cl, sm, buf, N, Nc, rank, c0, true, 0);
+    }
+    build_lists_body<T>(S, sm, buf, N, p, pl, own, rank, Nc, pull, clear_flag, s_err, nhalo);
+}
+template <int T>
+__device__ __noinline__ void rebuild_call(const Sim &S, const PSmem &sm, int buf, int N, int p, int pl, bool own,
+                                          int rank, int Nc, int c0, bool pull, int *clear_flag, int *s_err,
+                                          int *nhalo) {
+    rebuild_body<T>(S, sm, buf, N, p, pl, own, rank, Nc, c0, pull, clear_flag, s_err, nhalo);
+}
+template <int T, bool OUT_OF_LINE>
+__device__ __forceinline__ void rebuild(const Sim &S, const PSmem &sm, int buf, int N, int p, int pl, bool own,
+                                        int rank, int Nc, int c0, bool pull, int *clear_flag, int *s_err, int *nhalo) {
+    if constexpr (OUT_OF_LINE) rebuild_call<T>(S, sm, buf, N, p, pl, own, rank, Nc, c0, pull, clear_flag, s_err, nhalo);
+    else rebuild_body<T>(S, sm, buf, N, p, pl, own, rank, Nc, c0, pull, clear_flag, s_err, nhalo);
 }
 
 // SM cycles spent in phase k of realization 0 (only while profiling)
@@ -1197,8 +1210,7 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
             buf = nb;
             if (s_flag[t & 1]) {
                 const unsigned long long t0 = clock64();
-                if (pull) pull_beads(cl, sm, buf, N, Nc, rank, c0, true, 0);
-                build_lists<T, BWM>(S, sm, buf, N, p, pl, own, rank, Nc, pull, &s_flag[t & 1], &s_err, &s_nhalo);
+                rebuild<T, BWM>(S, sm, buf, N, p, pl, own, rank, Nc, c0, pull, &s_flag[t & 1], &s_err, &s_nhalo);
                 bh = mh;
                 bl = ml;
                 if (S.phase && blockIdx.x == 0 && threadIdx.x == 0) {
