@@ -201,6 +201,34 @@ def test_autotune_keeps_results():
     assert sim2.md_shape() == shape
 
 
+def test_reserving_sms_changes_nothing_and_is_kept():
+    """The particle blocks claiming their SMs' shared memory (or not) changes
+    where the kernels run, not what they compute: both give the same state
+    bit for bit; a choice fixed by the caller survives the autotuner, and
+    "auto" hands it back."""
+    w = small_workload()
+    inp = workloads.build_inputs(w)
+    out = []
+    for mode in ("share", "reserve"):
+        sim = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"])
+        sim.set_md_reserve(mode)
+        assert sim.md_reserve() == (mode == "reserve")
+        sim.step(6)
+        out.append((sim.get_deviations(), *sim.get_beads()))
+        sim.autotune(1)
+        assert sim.md_reserve() == (mode == "reserve")
+        sim.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+    sim = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"])
+    sim.set_md_reserve("reserve")
+    sim.set_md_reserve("auto")
+    sim.autotune(1)  # free again: either choice is valid
+    assert sim.md_reserve() in (True, False)
+    with pytest.raises(KeyError):
+        sim.set_md_reserve("always")
+
+
 def test_ensemble_realizations_match_oracle():
     """Three realizations with chains of different lengths in one launch; each
     matches its own oracle run (realization index in the Philox key)."""
