@@ -54,7 +54,8 @@ typedef enum {
     LBMD_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up: the tensor-copy lattice
                                  pass (tiles by = 0) waits at most 2^22 polls or 0.25 s for each
                                  stage's copies; a CTA that gives up latches this code and leaves
-                                 its sites unwritten, so the state after it is not a valid step */
+                                 its sites unwritten, so the state after it is not a valid step
+                                 (lbmd_set_wait_probe makes such a wait run out, for tests) */
     LBMD_ERR_CAPACITY = 5,    /* a fixed-capacity list (neighbours, wall sites) overflowed */
     LBMD_ERR_BUFFER = 6       /* device buffer too small or misaligned */
 } lbmd_status;
@@ -307,6 +308,16 @@ lbmd_status lbmd_get_md_bonded(lbmd_handle *h, int32_t *mode);
  * times both; until it runs, no reserving).  The state does not depend on
  * it.  LBMD_ERR_INVALID_ARG for another mode. */
 lbmd_status lbmd_set_md_reserve(lbmd_handle *h, int32_t mode);
+
+/* Test of the device-side bounded waits (failure detection without a fault):
+ * with on = 1, every launch of the tensor-copy lattice pass (tiles by = 0)
+ * first waits on an mbarrier phase that nothing completes, before it issues
+ * any copy; the wait gives up after 1 ms, the kernel latches the timeout and
+ * returns without writing its sites, and lbmd_check then returns
+ * LBMD_ERR_TIMEOUT.  The step's state after such a launch is not valid.  No
+ * other kernel is affected.  on = 0 (the default) turns it off;
+ * LBMD_ERR_INVALID_ARG for another value. */
+lbmd_status lbmd_set_wait_probe(lbmd_handle *h, int32_t on);
 lbmd_status lbmd_get_md_reserve(lbmd_handle *h, int32_t *reserve);
 lbmd_status lbmd_get_md_exchange(lbmd_handle *h, int32_t *mode);
 

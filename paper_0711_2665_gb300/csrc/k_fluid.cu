@@ -453,6 +453,12 @@ __global__ void __launch_bounds__(TMA_THREADS) k_stream_collide_tma(const Sim S,
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
+    if (S.wait_probe) {
+        // test of the bounded wait: stage 0's first phase, which nothing
+        // completes (no copy has been issued), runs out after 1 ms
+        if (tid == 0 && !mbar_wait(&bars[0], 0u, 1000000ull)) atomicOr(&S.ctrl->status, ST_TIMEOUT);
+        return;
+    }
     if (tid == 0)
         for (int k = 0; k < min(STAGES, ng); ++k) issue(k);
     int k = 0;

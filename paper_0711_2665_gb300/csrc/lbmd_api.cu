@@ -1565,6 +1565,13 @@ lbmd_status lbmd_set_md_reserve(lbmd_handle *h, int32_t mode) {
     return LBMD_OK;
 }
 
+lbmd_status lbmd_set_wait_probe(lbmd_handle *h, int32_t on) {
+    if (!h || on < 0 || on > 1) return LBMD_ERR_INVALID_ARG;
+    if ((on != 0) != (h->S.wait_probe != 0)) drop_graph(h);
+    h->S.wait_probe = on;
+    return LBMD_OK;
+}
+
 lbmd_status lbmd_get_md_reserve(lbmd_handle *h, int32_t *reserve) {
     if (!h || !reserve) return LBMD_ERR_INVALID_ARG;
     *reserve = h->S.md_reserve ? 1 : 0;

@@ -172,6 +172,8 @@ struct Sim {
     int md_bw;               // bonded terms: 0 automatic, 1 by every bead's lanes, 2 by a block's last warp
     int md_reserve;          // 1: the particle kernel's blocks claim their SMs' whole shared memory
     int smem_optin;          // the device's opt-in shared memory per block (bytes)
+    int wait_probe;          // test of the bounded waits: the tensor-copy lattice pass waits on a barrier
+                             // nothing completes (1 ms), before any copy, and latches ST_TIMEOUT
     // The beads' frame.  Bead positions live in the whole lattice (bnx along
     // x); the populations of this handle cover nx planes from global x plane
     // gx0 on.  Without slabs bnx = nx, gx0 = 0 and the handle owns every
@@ -311,13 +313,15 @@ __device__ __forceinline__ unsigned long long global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// bounded wait for the phase of parity `parity` to complete; false: gave up
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// bounded wait for the phase of parity `parity` to complete (at most
+// MBAR_WAIT_LIMIT polls or limit_ns); false: gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          unsigned long long limit_ns = MBAR_WAIT_NS) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (unsigned k = 0; k < MBAR_WAIT_LIMIT; ++k) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((k & 63u) == 63u && global_ns() - t0 > MBAR_WAIT_NS) return false;
+        if ((k & 63u) == 63u && global_ns() - t0 > limit_ns) return false;
     }
     return false;
 }

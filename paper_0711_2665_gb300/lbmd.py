@@ -135,6 +135,7 @@ def lib():
         "lbmd_get_md_bonded": [vp, P(i32)],
         "lbmd_get_md_reserve": [vp, P(i32)],
         "lbmd_set_md_reserve": [vp, i32],
+        "lbmd_set_wait_probe": [vp, i32],
         "lbmd_set_drive": [vp, ctypes.c_double, ctypes.c_double],
         "lbmd_step_loop": [vp, i64],
         "lbmd_adjoint_required_bytes": [vp, i32, i32, P(sz)],
@@ -341,6 +342,11 @@ class Simulation:
         shared memory), "share" or "auto" (lbmd_autotune chooses)."""
         code = {"auto": 0, "share": 1, "reserve": 2}[mode]
         self._check(self._lib.lbmd_set_md_reserve(self._h, code), "lbmd_set_md_reserve")
+
+    def set_wait_probe(self, on: bool):
+        """Test hook: the tensor-copy lattice pass waits on a barrier nothing
+        completes and reports a timeout (lbmd_set_wait_probe)."""
+        self._check(self._lib.lbmd_set_wait_probe(self._h, int(bool(on))), "lbmd_set_wait_probe")
 
     def md_reserve(self) -> bool:
         m = ctypes.c_int32()

@@ -9,7 +9,9 @@ LBMD_ERR_NONFINITE.  The states below are built on the host: crowded beads
 with the pair forces switched off (eps = 0) so that nothing else goes wrong,
 and a NaN planted in one bead's velocity or position.  Positions that are
 not finite are mapped to site 0 before any lattice index is formed, so the
-NaN cases index only inside the lattice.
+NaN cases index only inside the lattice.  The bounded device waits are
+tested through lbmd_set_wait_probe: a wait on an mbarrier phase that nothing
+completes, with no copy in flight, runs out after 1 ms (LBMD_ERR_TIMEOUT).
 """
 import numpy as np
 import pytest
@@ -19,7 +21,7 @@ from paper_0711_2665_gb300 import lbmd
 
 pytestmark = pytest.mark.gpu
 
-CAPACITY, NONFINITE = 5, 3
+CAPACITY, NONFINITE, TIMEOUT = 5, 3, 4
 
 
 def _quiet(**kw):
@@ -103,3 +105,32 @@ def test_nonfinite_bead_state_is_reported(what):
     sim.set_beads(r, v)
     st, obs_st = _status_after(sim)
     assert st == NONFINITE and obs_st == NONFINITE
+
+
+def test_bounded_wait_that_runs_out_is_reported():
+    """The tensor-copy lattice pass told to wait on an mbarrier phase that
+    nothing completes (before it issues any copy) gives up after 1 ms,
+    latches the timeout and returns: lbmd_check reports LBMD_ERR_TIMEOUT and
+    the context stays usable, a fresh handle stepping exactly like one that
+    never waited.  Two ordinary steps first leave both population buffers
+    finite, so the skipped pass leaves a finite (if invalid) state."""
+    from paper_0711_2665_gb300 import workloads
+    w = small_workload()
+    inp = workloads.build_inputs(w)
+    sim = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"])
+    sim.set_tiles(0, 4)
+    sim.step(2)
+    sim.check()
+    sim.set_wait_probe(True)
+    st, obs_st = _status_after(sim)
+    assert st == TIMEOUT and obs_st == TIMEOUT
+    sim.close()
+    runs = []
+    for tiles in ((0, 4), (4, 4)):
+        s2 = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"])
+        s2.set_tiles(*tiles)
+        s2.step(3)
+        s2.check()
+        runs.append(s2.get_deviations())
+        s2.close()
+    assert np.array_equal(runs[0], runs[1])
