@@ -251,7 +251,7 @@ lbmd_status lbmd_step_loop(lbmd_handle *h, int64_t n);
  * by = 0 selects the kernel fed by tensor copies (rows of x staged in shared
  * memory by cp.async.bulk.tensor), with zc in 1..256 row groups per thread
  * block; it needs nx <= 256, rows of a multiple of 16 bytes and no
- * fluctuating fluid.  by in {-1,-2,-4,-8,-16} selects the kernel with two x
+ * fluctuating fluid.  by in {-1,-2,-4,-8} selects the kernel with two x
  * sites per thread (block (32, -by), 64 sites of a row per warp, pair loads
  * and stores, shuffles for the x-shifted links), zc in 1..64; it needs an
  * even nx and no fluctuating fluid.  LBMD_ERR_INVALID_ARG otherwise.  The state

@@ -198,7 +198,9 @@ __global__ void __launch_bounds__(512, FL ? 1 : 2) k_stream_collide(const Sim S,
 // with a bounce-back link, which store site by site (solid sites are never
 // written, as in k_stream_collide).  Every address and the loop overhead
 // serve two sites.  The per-site arithmetic is k_stream_collide's,
-// expression for expression; no thermal noise.  Needs an even nx.
+// expression for expression; no thermal noise.  Needs an even nx.  Blocks of
+// at most 256 threads, three per SM: 80 registers, no spills (left free, the
+// compiler takes 128 and holds half the warps: FP16 135 instead of 107 us).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float2 pair_load(const float *base, uint32_t idx) {
     return __ldg(reinterpret_cast<const float2 *>(base + idx));
@@ -256,7 +258,7 @@ __device__ __forceinline__ void bgk_site(const float (&h)[Q], float om, bool has
 }
 
 template <int PREC, int MODE>
-__global__ void __launch_bounds__(512, 1) k_stream_collide_x2(const Sim S, const void *__restrict__ Av,
+__global__ void __launch_bounds__(256, 3) k_stream_collide_x2(const Sim S, const void *__restrict__ Av,
                                                               void *__restrict__ Bv, const int zc, const int nzb) {
     using T = typename PopT<PREC>::T;
     const int lane = threadIdx.x;
@@ -348,7 +350,7 @@ bool x2_lattice_ok(const Sim &S) { return !S.fluct && S.nx % 2 == 0; }
 
 cudaError_t launch_stream_collide_x2(const Sim &S, const void *A, void *B, int by, int zc, bool diag,
                                      cudaStream_t st) {
-    if (!x2_lattice_ok(S) || by < 1 || by > 16 || zc < 1) return cudaErrorInvalidValue;
+    if (!x2_lattice_ok(S) || by < 1 || by > 8 || zc < 1) return cudaErrorInvalidValue;
     const int nzb = (S.nz + zc - 1) / zc;
     const dim3 grid((S.nx + 63) / 64, (S.ny + by - 1) / by, nzb * S.n_real), block(32, by);
 #define X2_LAUNCH(P, M) k_stream_collide_x2<P, M><<<grid, block, 0, st>>>(S, A, B, zc, nzb)

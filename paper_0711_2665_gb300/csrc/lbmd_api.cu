@@ -1500,7 +1500,7 @@ lbmd_status lbmd_set_tiles(lbmd_handle *h, int32_t by, int32_t zc) {
     const int aby = by < 0 ? -by : by;
     if (by == 0) {
         if (!h->tma_ok || zc < 1 || zc > 256) return LBMD_ERR_INVALID_ARG;
-    } else if (by < 0 && !x2_lattice_ok(h->S)) {
+    } else if (by < 0 && (!x2_lattice_ok(h->S) || by < -8)) {
         return LBMD_ERR_INVALID_ARG;
     } else if (!(aby == 1 || aby == 2 || aby == 4 || aby == 8 || aby == 16) || zc < 1 || zc > 64) {
         return LBMD_ERR_INVALID_ARG;
@@ -1648,7 +1648,7 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
     // two x sites per thread (tiles (-by, zc))
     for (int by : BYS)
         for (int zc : ZCS) {
-            if (!x2_lattice_ok(h->S) || zc > h->cfg.nz) break;
+            if (!x2_lattice_ok(h->S) || by > 8 || zc > h->cfg.nz) break;
             CK(lattice_pass(h, h->S, -by, zc, true));
             CK(cudaEventRecord(a, h->st));
             for (int k = 0; k < reps; ++k) CK(lattice_pass(h, h->S, -by, zc, true));

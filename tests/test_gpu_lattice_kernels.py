@@ -125,11 +125,19 @@ def test_paired_pass_ensemble_full_lattice_and_slab():
 
 
 def test_paired_pass_needs_an_even_row():
+    """An odd nx has no aligned pairs; blocks hold at most 256 threads (three
+    per SM at 80 registers), so by = -16 is refused too."""
     w = small_workload(nx=41, wall_x=20)
     inp = workloads.build_inputs(w)
     sim = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"])
     with pytest.raises(lbmd.LbmdError):
         sim.set_tiles(-4, 4)
+    w = small_workload()
+    inp = workloads.build_inputs(w)
+    sim = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"])
+    sim.set_tiles(-8, 4)
+    with pytest.raises(lbmd.LbmdError):
+        sim.set_tiles(-16, 4)
 
 
 def test_tensor_copy_pass_needs_a_fitting_lattice():
