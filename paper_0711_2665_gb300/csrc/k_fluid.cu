@@ -36,13 +36,77 @@ __device__ __forceinline__ void block_partial4(float a, float b, float c, float 
     }
 }
 
+// c_i . (x, y, z) for a D3Q19 velocity (components in {-1, 0, 1}): only the
+// nonzero components enter, so an axis velocity costs no instruction and an
+// edge velocity one addition
+template <int I>
+__device__ __forceinline__ float cdot(float x, float y, float z) {
+    float s = 0.0f;
+    bool any = false;
+    if (cx(I) != 0) { s = cx(I) > 0 ? x : -x; any = true; }
+    if (cy(I) != 0) { const float t = cy(I) > 0 ? y : -y; s = any ? s + t : t; any = true; }
+    if (cz(I) != 0) { const float t = cz(I) > 0 ? z : -z; s = any ? s + t : t; }
+    return s;
+}
+
+// BGK relaxation of one site in stored units (h, or h * 2^12 for FP16).
+// With j = rho u the equilibrium (Eq. 5) reads
+//   heq_i = w_i [ K + 9/2 (c_i.u)(c_i.j) + 3 c_i.j ],   K = (rho - 1) - 3/2 u.j,
+// since rho (c.u) = c.j.  The relaxation (Eq. 4) then is
+//   hr_i = (1 - om) h_i + om heq_i,
+// and an opposite pair (i, i + 1) (c_{i+1} = -c_i) shares
+//   E = om w_i (K + 9/2 (c_i.u)(c_i.j)),   O = 3 om w_i c_i.j:
+//   hr_i = (1 - om) h_i + (E + O),   hr_{i+1} = (1 - om) h_{i+1} + (E - O).
+// Out: hr, the moment sums in stored units (rho - 1, j) and rho.
+template <int PREC>
+__device__ __forceinline__ void bgk_relax(const float (&h)[Q], float om, float (&hr)[Q], float &drho_s, float &jx,
+                                          float &jy, float &jz, float &rho) {
+    constexpr float down = PopScale<PREC>::down;
+    // moments from the sums and differences of the opposite pairs
+    drho_s = h[0];
+    jx = 0.f; jy = 0.f; jz = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const float sp = h[i] + h[i + 1], dp = h[i] - h[i + 1];
+        drho_s += sp;
+        if (cx(i) == 1) jx += dp;
+        if (cx(i) == -1) jx -= dp;
+        if (cy(i) == 1) jy += dp;
+        if (cy(i) == -1) jy -= dp;
+        if (cz(i) == 1) jz += dp;
+        if (cz(i) == -1) jz -= dp;
+    }
+    rho = 1.0f + drho_s * down;
+    const float t = (1.5f * down) / rho;  // v = 3/2 u (the scale power of two is exact)
+    const float vx = jx * t, vy = jy * t, vz = jz * t;
+    const float K = drho_s - (vx * jx + vy * jy + vz * jz);
+    const float c1 = 1.0f - om;
+    hr[0] = c1 * h[0] + (om * wq(0)) * K;
+    // weight classes: axis velocities (wq 1/18), edge velocities (1/36)
+    const float oa = om * wq(1), oe = om * wq(7);
+    const float ka = oa * K, ke = oe * K;
+    const float ax = (3.0f * oa) * jx, ay = (3.0f * oa) * jy, az = (3.0f * oa) * jz;
+    const float ex = (3.0f * oe) * jx, ey = (3.0f * oe) * jy, ez = (3.0f * oe) * jz;
+#define LBMD_PAIR(I)                                                                                           \
+    {                                                                                                          \
+        constexpr bool edge = (cx(I) != 0) + (cy(I) != 0) + (cz(I) != 0) == 2;                                 \
+        const float O = edge ? cdot<I>(ex, ey, ez) : cdot<I>(ax, ay, az);                                      \
+        const float E = fmaf(cdot<I>(vx, vy, vz), O, edge ? ke : ka);                                          \
+        hr[I] = fmaf(c1, h[I], E + O);                                                                         \
+        hr[I + 1] = fmaf(c1, h[I + 1], E - O);                                                                 \
+    }
+    LBMD_PAIR(1) LBMD_PAIR(3) LBMD_PAIR(5) LBMD_PAIR(7) LBMD_PAIR(9) LBMD_PAIR(11) LBMD_PAIR(13) LBMD_PAIR(15)
+    LBMD_PAIR(17)
+#undef LBMD_PAIR
+}
+
 // ---------------------------------------------------------------------------
 // Fused pull stream + bounce-back + moments + BGK collision.
 //   h_i(x)   = h*_i(x - c_i)          pulled from A, or h*_opp(i)(x) when x - c_i is solid
 //   rho      = 1 + sum_i h_i,  rho u = sum_i h_i c_i               (Eqs. 1-2)
 //   h*_i     = h_i + omega (heq_i - h_i) + 3 w_i g.c_i              (Eqs. 4-5)
 //   heq_i    = w_i [ (rho - 1) + rho (3 c.u + 9/2 (c.u)^2 - 3/2 u.u) ]
-// (h = f - w).  Block (32, by) covers 32 consecutive x of `by` rows; each thread
+// (h = f - w; the arithmetic is bgk_relax's).  Block (32, by) covers 32 consecutive x of `by` rows; each thread
 // walks zc consecutive z planes.  MODE 0: store; 1: store + per-step sums;
 // 2: sums only (observables).
 // ---------------------------------------------------------------------------
@@ -119,30 +183,12 @@ __global__ void __launch_bounds__(512, FL ? 1 : 2) k_stream_collide(const Sim S,
           for (int u = 0; u < U; ++u) {
             if (lmu[u] & SOLID_BIT) continue;
             const int s = su[u];
-            const float *h = hh[u];
-            // moments from the sums and differences of the opposite pairs
-            // (i odd, i + 1): c_{i+1} = -c_i
-            float drho_s = h[0], jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-            for (int i = 1; i < Q; i += 2) {
-                const float sp = h[i] + h[i + 1], dp = h[i] - h[i + 1];
-                drho_s += sp;
-                if (cx(i) == 1) jx += dp;
-                if (cx(i) == -1) jx -= dp;
-                if (cy(i) == 1) jy += dp;
-                if (cy(i) == -1) jy -= dp;
-                if (cz(i) == 1) jz += dp;
-                if (cz(i) == -1) jz -= dp;
+            float hr[Q], drho_s, jx, jy, jz, rho;
+            bgk_relax<PREC>(hh[u], om, hr, drho_s, jx, jy, jz, rho);
+            if (MODE != 0 && x >= S.own_lo && x < S.own_hi) {
+                am += drho_s * down; ax += jx * down; ay += jy * down; az += jz * down;
             }
-            const float drho = drho_s * down;
-            jx *= down; jy *= down; jz *= down;
-            if (MODE != 0 && x >= S.own_lo && x < S.own_hi) { am += drho; ax += jx; ay += jy; az += jz; }
             if (MODE != 2) {
-                const float rho = 1.0f + drho;
-                const float ir = 1.0f / rho;
-                const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
-                const float usq = 1.5f * (ux * ux + uy * uy + uz * uz);
-                const float rho_s = rho * up;
                 // fluctuating LB: mode k (4..18) gets amplitude sqrt(rho) fl_amp[k-4] r_k
                 float am_[15];
                 if (FL) {
@@ -151,20 +197,6 @@ __global__ void __launch_bounds__(512, FL ? 1 : 2) k_stream_collide(const Sim S,
                     const float sr = sqrtf(fmaxf(rho, 0.0f)) * up;
 #pragma unroll
                     for (int k = 0; k < 15; ++k) am_[k] = sr * S.fl_amp[k] * z[k];
-                }
-                // BGK towards heq_i = w_i (drho + rho (cu + cu^2 / 2 - 3 u.u / 2)),
-                // cu = 3 c_i.u: for the pair (i, i + 1) cu changes sign, so the
-                // even part (drho + rho (cu^2 / 2 - 3 u.u / 2)) and the odd part
-                // (rho cu) serve both
-                float hr[Q];
-                hr[0] = h[0] + om * (wq(0) * (drho_s - rho_s * usq) - h[0]);
-#pragma unroll
-                for (int i = 1; i < Q; i += 2) {
-                    const float cu = 3.0f * ((float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz);
-                    const float even = drho_s + rho_s * (0.5f * cu * cu - usq);
-                    const float odd = rho_s * cu;
-                    hr[i] = h[i] + om * (wq(i) * (even + odd) - h[i]);
-                    hr[i + 1] = h[i + 1] + om * (wq(i) * (even - odd) - h[i + 1]);
                 }
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
@@ -197,8 +229,8 @@ __global__ void __launch_bounds__(512, FL ? 1 : 2) k_stream_collide(const Sim S,
 // periodic wrap) load that one directly.  Stores go as pairs, except in tiles
 // with a bounce-back link, which store site by site (solid sites are never
 // written, as in k_stream_collide).  Every address and the loop overhead
-// serve two sites.  The per-site arithmetic is k_stream_collide's,
-// expression for expression; no thermal noise.  Needs an even nx.  Blocks of
+// serve two sites.  The per-site arithmetic is k_stream_collide's
+// (bgk_relax); no thermal noise.  Needs an even nx.  Blocks of
 // at most 256 threads, three per SM: 80 registers, no spills (left free, the
 // compiler takes 128 and holds half the warps: FP16 135 instead of 107 us).
 // ---------------------------------------------------------------------------
@@ -221,35 +253,10 @@ template <int PREC>
 __device__ __forceinline__ void bgk_site(const float (&h)[Q], float om, bool has_g, float g0f, float g1f, float g2f,
                                          float (&hn)[Q], float &drho, float &jx, float &jy, float &jz) {
     constexpr float up = PopScale<PREC>::up, down = PopScale<PREC>::down;
-    float drho_s = h[0];
-    jx = 0.f; jy = 0.f; jz = 0.f;
-#pragma unroll
-    for (int i = 1; i < Q; i += 2) {
-        const float sp = h[i] + h[i + 1], dp = h[i] - h[i + 1];
-        drho_s += sp;
-        if (cx(i) == 1) jx += dp;
-        if (cx(i) == -1) jx -= dp;
-        if (cy(i) == 1) jy += dp;
-        if (cy(i) == -1) jy -= dp;
-        if (cz(i) == 1) jz += dp;
-        if (cz(i) == -1) jz -= dp;
-    }
+    float drho_s, rho;
+    bgk_relax<PREC>(h, om, hn, drho_s, jx, jy, jz, rho);
     drho = drho_s * down;
     jx *= down; jy *= down; jz *= down;
-    const float rho = 1.0f + drho;
-    const float ir = 1.0f / rho;
-    const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
-    const float usq = 1.5f * (ux * ux + uy * uy + uz * uz);
-    const float rho_s = rho * up;
-    hn[0] = h[0] + om * (wq(0) * (drho_s - rho_s * usq) - h[0]);
-#pragma unroll
-    for (int i = 1; i < Q; i += 2) {
-        const float cu = 3.0f * ((float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz);
-        const float even = drho_s + rho_s * (0.5f * cu * cu - usq);
-        const float odd = rho_s * cu;
-        hn[i] = h[i] + om * (wq(i) * (even + odd) - h[i]);
-        hn[i + 1] = h[i + 1] + om * (wq(i) * (even - odd) - h[i + 1]);
-    }
     if (has_g) {
 #pragma unroll
         for (int i = 0; i < Q; ++i)
@@ -489,35 +496,10 @@ __global__ void __launch_bounds__(TMA_THREADS) k_stream_collide_tma(const Sim S,
                     h[i] = ((lm >> i) & 1u) ? load_raw(A, (uint32_t)opp(i) * ns + (uint32_t)s)
                                             : ring_load(row + (size_t)i * rows * row_elems, sx);
                 }
-                float drho_s = h[0], jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-                for (int i = 1; i < Q; i += 2) {
-                    const float sp = h[i] + h[i + 1], dp = h[i] - h[i + 1];
-                    drho_s += sp;
-                    if (cx(i) == 1) jx += dp;
-                    if (cx(i) == -1) jx -= dp;
-                    if (cy(i) == 1) jy += dp;
-                    if (cy(i) == -1) jy -= dp;
-                    if (cz(i) == 1) jz += dp;
-                    if (cz(i) == -1) jz -= dp;
-                }
-                const float drho = drho_s * down;
-                jx *= down; jy *= down; jz *= down;
-                if (MODE != 0 && x >= S.own_lo && x < S.own_hi) { am += drho; ax += jx; ay += jy; az += jz; }
-                const float rho = 1.0f + drho;
-                const float ir = 1.0f / rho;
-                const float ux = jx * ir, uy = jy * ir, uz = jz * ir;
-                const float usq = 1.5f * (ux * ux + uy * uy + uz * uz);
-                const float rho_s = rho * up;
-                float hr[Q];
-                hr[0] = h[0] + om * (wq(0) * (drho_s - rho_s * usq) - h[0]);
-#pragma unroll
-                for (int i = 1; i < Q; i += 2) {
-                    const float cu = 3.0f * ((float)cx(i) * ux + (float)cy(i) * uy + (float)cz(i) * uz);
-                    const float even = drho_s + rho_s * (0.5f * cu * cu - usq);
-                    const float odd = rho_s * cu;
-                    hr[i] = h[i] + om * (wq(i) * (even + odd) - h[i]);
-                    hr[i + 1] = h[i + 1] + om * (wq(i) * (even - odd) - h[i + 1]);
+                float hr[Q], drho_s, jx, jy, jz, rho;
+                bgk_relax<PREC>(h, om, hr, drho_s, jx, jy, jz, rho);
+                if (MODE != 0 && x >= S.own_lo && x < S.own_hi) {
+                    am += drho_s * down; ax += jx * down; ay += jy * down; az += jz * down;
                 }
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {

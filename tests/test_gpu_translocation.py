@@ -203,6 +203,7 @@ def test_translocation_time_fp32_and_fp16_against_oracle():
     want = np.array([_oracle_tx(w, inp, r, 400) for r in range(len(counts))])
     assert np.all(want > 0)
     tol = np.maximum(3, 0.03 * want)
+    print("t_X oracle", want.tolist(), {k: v.tolist() for k, v in got.items()})
     for prec, tx in got.items():
         assert np.all(tx > 0), prec
         assert np.all(np.abs(tx - want) <= tol), (prec, tx.tolist(), want.tolist())
