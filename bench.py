@@ -684,24 +684,31 @@ def main():
     # the step-loop graph is captured once per configuration (the profiling
     # passes above dropped it); a caller's jobs reuse it, so capture it here
     sim.step_loop(2)
-    if flush:
-        flush_l2()
-    barrier()
-    t0 = time.perf_counter()
-    ok = [L.lbmd_set_populations(sim._h, P(f_in)), L.lbmd_set_beads(sim._h, P(r_in), P(v_in))]
-    sim.step_loop(args.steps)
-    ok += [L.lbmd_diagnostics(sim._h, diag, args.steps, ctypes.byref(rows)),
-           L.lbmd_get_populations(sim._h, P(f_out)), L.lbmd_get_beads(sim._h, P(r_out), P(v_out))]
-    wall = time.perf_counter() - t0
-    assert all(x == 0 for x in ok) and rows.value == args.steps, (ok, rows.value)
+    # three identical jobs (each uploads the same state); the median is
+    # reported, every job's time beside it: the copies share the host's
+    # memory with whatever else runs on it, and one job can catch a stall
+    walls = []
+    for _ in range(3):
+        if flush:
+            flush_l2()
+        barrier()
+        t0 = time.perf_counter()
+        ok = [L.lbmd_set_populations(sim._h, P(f_in)), L.lbmd_set_beads(sim._h, P(r_in), P(v_in))]
+        sim.step_loop(args.steps)
+        ok += [L.lbmd_diagnostics(sim._h, diag, args.steps, ctypes.byref(rows)),
+               L.lbmd_get_populations(sim._h, P(f_out)), L.lbmd_get_beads(sim._h, P(r_out), P(v_out))]
+        walls.append(time.perf_counter() - t0)
+        assert all(x == 0 for x in ok) and rows.value == args.steps, (ok, rows.value)
+    wall = statistics.median(walls)
     e2e_s = pdist.max_over_ranks(wall, world)
     bi = f_in.numel() * 4 + 2 * 8 * 3 * sim.total_beads
     bo = sim.n_real * rows.value * ctypes.sizeof(lbmd.Diag) + f_out.numel() * 4 + 2 * 8 * 3 * sim.total_beads
     e2e = {"value": job_sites * args.steps / e2e_s / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": bi / args.steps, "d2h_bytes_per_step": bo / args.steps,
-           "note": ("one K-step job through the C ABI from pinned host buffers: state upload, one step-loop launch "
+           "jobs_ms": [round(1e3 * x, 3) for x in walls],
+           "note": ("K-step jobs through the C ABI from pinned host buffers: state upload, one step-loop launch "
                     "(its graph captured before, as a caller's later jobs reuse it), the K diagnostics rows and the "
-                    "final state read back; host wall clock")}
+                    "final state read back; host wall clock, the median of three identical jobs")}
 
     if rank == 0:
         clocks = clk.summary()

@@ -8,6 +8,8 @@
 //     fp32 staging area) and the fluid part of the observables.
 #include "lbmd_internal.cuh"
 
+#include <utility>
+
 namespace lbmd {
 
 // ---------------------------------------------------------------------------
@@ -746,84 +748,148 @@ cudaError_t launch_feq_to_staging(const Sim &S, float *staging, cudaStream_t st)
     return cudaGetLastError();
 }
 
-// pulled populations f^n (what the next step starts from) -> staging
+// ---------------------------------------------------------------------------
+// State transfer between the populations and the fp32 staging area
+// [realization][19][site], with f = w_i + h at the host.  The conversions
+// round as the FP64 expressions float(double(h) + w_i) and
+// float(double(f) - w_i) do (w_i the double nearest the weight), without FP64
+// arithmetic in all but rare cases: FP64 runs at a small fraction of the FP32
+// rate on this GPU, and with 19 conversions per site in FP64 a transfer of the
+// 4.19M-site lattice took 444 us (1.4 TB/s); in FP32 it takes 179-197 us.
+//
+// The double constant cd is the exact sum of three floats c0 + c1 + c2.  Two
+// error-free sums (TwoSum, Knuth) give r = RN32(v + c0 + c1) and the exact
+// remainder, so v + cd = r + rho exactly, rho = d + et + c2 (computed in FP32,
+// within `bound`).  RN64 moves v + cd by at most 2^-53 |v + cd|.  When
+// |rho| stays below half an ulp of r by more than both, RN32(RN64(v + cd)) = r;
+// when r is zero, tiny, a power of two (unequal gaps), not finite, or rho is
+// near the midpoint, the FP64 expression is evaluated instead.
+// ---------------------------------------------------------------------------
+struct WSplit { float c0, c1, c2; };
+__host__ __device__ constexpr WSplit wsplit(double cd) {
+    return {(float)cd, (float)(cd - (double)(float)cd),
+            (float)(cd - (double)(float)cd - (double)(float)(cd - (double)(float)cd))};
+}
+
+// the FP64 expression itself, out of line: evaluated only where the fast
+// path cannot decide (inline, the compiler may evaluate it for every element
+// and select, which costs the FP64 rate the fast path avoids)
+__device__ __noinline__ float add_double_rn_fp64(float v, double cd) { return (float)((double)v + cd); }
+
+// float(double(v) + cd) for cd = W.c0 + W.c1 + W.c2
+__device__ __forceinline__ float add_double_rn(float v, WSplit W, double cd) {
+    float s, e, t, et, r, d;
+    two_sum(v, W.c0, s, e);
+    two_sum(e, W.c1, t, et);
+    two_sum(s, t, r, d);
+    const float rho = (d + et) + W.c2;
+    const float bound = fmaf(fabsf(d) + fabsf(et) + fabsf(W.c2), 0x1p-22f, fabsf(r) * 0x1p-50f);
+    const uint32_t rb = __float_as_uint(r), eb = rb & 0x7f800000u;
+    const bool fast = eb >= (25u << 23) && eb != 0x7f800000u && (rb & 0x007fffffu) != 0u &&
+                      fmaf(__uint_as_float(eb), 0x1p-24f, -fabsf(rho)) > bound;
+    if (!fast) r = add_double_rn_fp64(v, cd);
+    return r;
+}
+
+template <int I>
+__device__ __forceinline__ float plus_weight(float h) {  // float(double(h) + w_I)
+    constexpr double cd = wq_exact(I);
+    constexpr WSplit W = wsplit(cd);
+    return add_double_rn(h, W, cd);
+}
+template <int I>
+__device__ __forceinline__ float minus_weight(float f) {  // float(double(f) - w_I)
+    constexpr double cd = -wq_exact(I);
+    constexpr WSplit W = wsplit(cd);
+    return add_double_rn(f, W, cd);
+}
+
+// The 19 loads of a site are issued before any of its stores, so that they
+// are in flight together (the compiler may not move a load above a store to
+// a buffer it cannot tell apart).
+template <int I, int PREC>
+__device__ __forceinline__ float pull_load(const typename PopT<PREC>::T *A, uint32_t lm, int x, int y, int z, uint32_t s,
+                                           const Sim &S) {
+    if (lm & SOLID_BIT) return 0.0f;
+    const uint32_t ps = (uint32_t)S.ps;
+    const uint32_t idx = ((lm >> I) & 1u) ? (uint32_t)opp(I) * ps + s
+                                           : (uint32_t)I * ps + (uint32_t)(wrapi(x - cx(I), S.nx) +
+                                                                          S.nx * (wrapi(y - cy(I), S.ny) + S.ny * wrapi(z - cz(I), S.nz)));
+    return load_dev(A, idx);
+}
+
+template <int I>
+__device__ __forceinline__ float push_load(const float *f, uint32_t lm, int x, int y, int z, uint32_t s, const Sim &S) {
+    if (lm & SOLID_BIT) return 0.0f;
+    const bool bb = (lm >> opp(I)) & 1u;  // y + c_I is solid: the link comes back as opp(I)
+    const uint32_t src = bb ? s : (uint32_t)(wrapi(x + cx(I), S.nx) + S.nx * (wrapi(y + cy(I), S.ny) + S.ny * wrapi(z + cz(I), S.nz)));
+    return __ldg(f + (size_t)(bb ? opp(I) : I) * S.ns + src);
+}
+
+template <int PREC, bool DEV, int... I>
+__device__ __forceinline__ void pull_site(const typename PopT<PREC>::T *A, float *f, uint32_t lm, int x, int y, int z,
+                                          uint32_t s, const Sim &S, std::integer_sequence<int, I...>) {
+    float h[Q];
+    ((h[I] = pull_load<I, PREC>(A, lm, x, y, z, s, S)), ...);
+    const bool solid = lm & SOLID_BIT;
+    ((f[(size_t)I * S.ns + s] = solid ? 0.0f : (DEV ? h[I] : plus_weight<I>(h[I]))), ...);
+}
+template <int PREC, bool DEV, int... I>
+__device__ __forceinline__ void push_site(const float *f, typename PopT<PREC>::T *A, uint32_t lm, int x, int y, int z,
+                                          uint32_t s, const Sim &S, std::integer_sequence<int, I...>) {
+    float v[Q];
+    ((v[I] = push_load<I>(f, lm, x, y, z, s, S)), ...);
+    const bool solid = lm & SOLID_BIT;
+    (store_dev(A, (uint32_t)I * (uint32_t)S.ps + s, solid ? 0.0f : (DEV ? v[I] : minus_weight<I>(v[I]))), ...);
+}
+
+// pulled populations f^n (what the next step starts from) -> staging; one
+// thread per site, realization blockIdx.y
 template <int PREC, bool DEV>
-__global__ void k_pull_to_staging(const Sim S, const void *Av, float *stg) {
+__global__ void __launch_bounds__(256) k_pull_to_staging(const Sim S, const void *Av, float *stg) {
     using T = typename PopT<PREC>::T;
-    const size_t ns = (size_t)S.ns;
-    const size_t total = ns * S.n_real;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-        const size_t r = t / ns, s = t - r * ns;
-        const T *A = reinterpret_cast<const T *>(Av) + r * Q * (size_t)S.ps;
-        float *f = stg + r * Q * ns + s;
-        const uint32_t lm = S.link[s];
-        const int x = (int)(s % S.nx), y = (int)((s / S.nx) % S.ny), z = (int)(s / ((size_t)S.nx * S.ny));
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            float v = 0.0f;
-            if (!(lm & SOLID_BIT)) {
-                uint32_t idx;
-                if ((lm >> i) & 1u) idx = (uint32_t)(opp(i) * (size_t)S.ps + s);
-                else
-                    idx = (uint32_t)(i * (size_t)S.ps + wrapi(x - cx(i), S.nx) +
-                                     (size_t)S.nx * (wrapi(y - cy(i), S.ny) + (size_t)S.ny * wrapi(z - cz(i), S.nz)));
-                const float h = load_dev(A, idx);
-                v = DEV ? h : (float)(wq_exact(i) + (double)h);
-            }
-            f[i * ns] = v;
-        }
-    }
+    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= (uint32_t)S.ns) return;
+    const int r = blockIdx.y;
+    const uint32_t nxy = (uint32_t)S.nx * (uint32_t)S.ny;
+    const int z = (int)(s / nxy), rem = (int)(s - (uint32_t)z * nxy), y = rem / S.nx, x = rem - y * S.nx;
+    pull_site<PREC, DEV>(reinterpret_cast<const T *>(Av) + (size_t)r * Q * S.ps, stg + (size_t)r * Q * S.ns, S.link[s],
+                         x, y, z, s, S, std::make_integer_sequence<int, Q>{});
 }
 
 cudaError_t launch_pull_to_staging(const Sim &S, const void *A, float *staging, bool dev, cudaStream_t st) {
+    const dim3 grid((unsigned)((S.ns + 255) / 256), (unsigned)S.n_real);
     if (S.precision == LBMD_FP16DEV) {
-        if (dev) k_pull_to_staging<1, true><<<4 * 152, 256, 0, st>>>(S, A, staging);
-        else k_pull_to_staging<1, false><<<4 * 152, 256, 0, st>>>(S, A, staging);
+        if (dev) k_pull_to_staging<1, true><<<grid, 256, 0, st>>>(S, A, staging);
+        else k_pull_to_staging<1, false><<<grid, 256, 0, st>>>(S, A, staging);
     } else {
-        if (dev) k_pull_to_staging<0, true><<<4 * 152, 256, 0, st>>>(S, A, staging);
-        else k_pull_to_staging<0, false><<<4 * 152, 256, 0, st>>>(S, A, staging);
+        if (dev) k_pull_to_staging<0, true><<<grid, 256, 0, st>>>(S, A, staging);
+        else k_pull_to_staging<0, false><<<grid, 256, 0, st>>>(S, A, staging);
     }
     return cudaGetLastError();
 }
 
 // inverse of the pull: A_i(y) = f_i(y + c_i), or f_opp(i)(y) when y + c_i is solid
 template <int PREC, bool DEV>
-__global__ void k_push_from_staging(const Sim S, const float *stg, void *Av) {
+__global__ void __launch_bounds__(256) k_push_from_staging(const Sim S, const float *stg, void *Av) {
     using T = typename PopT<PREC>::T;
-    const size_t ns = (size_t)S.ns;
-    const size_t total = ns * S.n_real;
-    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-        const size_t r = t / ns, s = t - r * ns;
-        T *A = reinterpret_cast<T *>(Av) + r * Q * (size_t)S.ps;
-        const float *f = stg + r * Q * ns;
-        const uint32_t lm = S.link[s];
-        const int x = (int)(s % S.nx), y = (int)((s / S.nx) % S.ny), z = (int)(s / ((size_t)S.nx * S.ny));
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            float h = 0.0f;
-            if (!(lm & SOLID_BIT)) {
-                int k;
-                size_t src;
-                if ((lm >> opp(i)) & 1u) { k = opp(i); src = s; }
-                else {
-                    k = i;
-                    src = wrapi(x + cx(i), S.nx) + (size_t)S.nx * (wrapi(y + cy(i), S.ny) + (size_t)S.ny * wrapi(z + cz(i), S.nz));
-                }
-                const float v = f[k * ns + src];
-                h = DEV ? v : (float)((double)v - wq_exact(i));
-            }
-            store_dev(A, (uint32_t)(i * (size_t)S.ps + s), h);
-        }
-    }
+    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= (uint32_t)S.ns) return;
+    const int r = blockIdx.y;
+    const uint32_t nxy = (uint32_t)S.nx * (uint32_t)S.ny;
+    const int z = (int)(s / nxy), rem = (int)(s - (uint32_t)z * nxy), y = rem / S.nx, x = rem - y * S.nx;
+    push_site<PREC, DEV>(stg + (size_t)r * Q * S.ns, reinterpret_cast<T *>(Av) + (size_t)r * Q * S.ps, S.link[s],
+                         x, y, z, s, S, std::make_integer_sequence<int, Q>{});
 }
 
 cudaError_t launch_push_from_staging(const Sim &S, const float *staging, void *A, bool dev, cudaStream_t st) {
+    const dim3 grid((unsigned)((S.ns + 255) / 256), (unsigned)S.n_real);
     if (S.precision == LBMD_FP16DEV) {
-        if (dev) k_push_from_staging<1, true><<<4 * 152, 256, 0, st>>>(S, staging, A);
-        else k_push_from_staging<1, false><<<4 * 152, 256, 0, st>>>(S, staging, A);
+        if (dev) k_push_from_staging<1, true><<<grid, 256, 0, st>>>(S, staging, A);
+        else k_push_from_staging<1, false><<<grid, 256, 0, st>>>(S, staging, A);
     } else {
-        if (dev) k_push_from_staging<0, true><<<4 * 152, 256, 0, st>>>(S, staging, A);
-        else k_push_from_staging<0, false><<<4 * 152, 256, 0, st>>>(S, staging, A);
+        if (dev) k_push_from_staging<0, true><<<grid, 256, 0, st>>>(S, staging, A);
+        else k_push_from_staging<0, false><<<grid, 256, 0, st>>>(S, staging, A);
     }
     return cudaGetLastError();
 }
