@@ -585,6 +585,20 @@ def main():
     else:
         sim.step_loop(args.warmup + (args.warmup & 1))  # captures the loop graph
         units = [args.steps]
+    # the state (and step number) the timed steps start from: the end-to-end
+    # jobs below start from it too, so they compute the very same steps
+    L = sim._lib
+    nf = sim.n_real * 19 * sim.ns
+    nb3 = 3 * max(sim.total_beads, 1)
+    f_in = torch.empty(nf, dtype=torch.float32, pin_memory=True)
+    r_in = torch.empty(nb3, dtype=torch.float64, pin_memory=True)
+    v_in = torch.empty(nb3, dtype=torch.float64, pin_memory=True)
+    f_in.numpy()[:] = sim.get_populations().reshape(-1)
+    if sim.total_beads:
+        r0h, v0h = sim.get_beads()
+        r_in.numpy()[:] = r0h.reshape(-1)
+        v_in.numpy()[:] = v0h.reshape(-1)
+    step0 = sim.step_count
     barrier()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in units]
     launches0 = sim.launch_count()
@@ -664,36 +678,29 @@ def main():
     # End to end through the C ABI from pinned host buffers: upload the state
     # (populations and beads), K steps as one step-loop launch, read back the
     # K diagnostics rows, download the final state; host wall clock.
-    L = sim._lib
-    nf = sim.n_real * 19 * sim.ns
-    nb3 = 3 * max(sim.total_beads, 1)
-    f_in = torch.empty(nf, dtype=torch.float32, pin_memory=True)
     f_out = torch.empty(nf, dtype=torch.float32, pin_memory=True)
-    r_in = torch.empty(nb3, dtype=torch.float64, pin_memory=True)
-    v_in = torch.empty(nb3, dtype=torch.float64, pin_memory=True)
     r_out = torch.empty(nb3, dtype=torch.float64, pin_memory=True)
     v_out = torch.empty(nb3, dtype=torch.float64, pin_memory=True)
-    f_in.numpy()[:] = sim.get_populations().reshape(-1)
-    r0h, v0h = sim.get_beads()
-    if sim.total_beads:
-        r_in.numpy()[:] = r0h.reshape(-1)
-        v_in.numpy()[:] = v0h.reshape(-1)
     P = lambda t: ctypes.c_void_p(t.data_ptr())
     diag = (lbmd.Diag * (sim.n_real * args.steps))()
     rows = ctypes.c_int32()
     # the step-loop graph is captured once per configuration (the profiling
     # passes above dropped it); a caller's jobs reuse it, so capture it here
     sim.step_loop(2)
-    # three identical jobs (each uploads the same state); the median is
-    # reported, every job's time beside it: the copies share the host's
-    # memory with whatever else runs on it, and one job can catch a stall
+    # three identical jobs, each uploading the state and step number the
+    # timed steps started from (so each computes those same K steps: the
+    # particle kernel's cost follows the chain along its trajectory); the
+    # median is reported, every job's time beside it: the copies share the
+    # host's memory with whatever else runs on it, and one job can catch a
+    # stall
     walls = []
     for _ in range(3):
         if flush:
             flush_l2()
         barrier()
         t0 = time.perf_counter()
-        ok = [L.lbmd_set_populations(sim._h, P(f_in)), L.lbmd_set_beads(sim._h, P(r_in), P(v_in))]
+        ok = [L.lbmd_set_populations(sim._h, P(f_in)), L.lbmd_set_beads(sim._h, P(r_in), P(v_in)),
+              L.lbmd_set_step(sim._h, ctypes.c_int64(step0))]
         sim.step_loop(args.steps)
         ok += [L.lbmd_diagnostics(sim._h, diag, args.steps, ctypes.byref(rows)),
                L.lbmd_get_populations(sim._h, P(f_out)), L.lbmd_get_beads(sim._h, P(r_out), P(v_out))]
@@ -701,14 +708,15 @@ def main():
         assert all(x == 0 for x in ok) and rows.value == args.steps, (ok, rows.value)
     wall = statistics.median(walls)
     e2e_s = pdist.max_over_ranks(wall, world)
-    bi = f_in.numel() * 4 + 2 * 8 * 3 * sim.total_beads
+    bi = f_in.numel() * 4 + 2 * 8 * 3 * sim.total_beads + 8
     bo = sim.n_real * rows.value * ctypes.sizeof(lbmd.Diag) + f_out.numel() * 4 + 2 * 8 * 3 * sim.total_beads
     e2e = {"value": job_sites * args.steps / e2e_s / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": bi / args.steps, "d2h_bytes_per_step": bo / args.steps,
            "jobs_ms": [round(1e3 * x, 3) for x in walls],
            "note": ("K-step jobs through the C ABI from pinned host buffers: state upload, one step-loop launch "
                     "(its graph captured before, as a caller's later jobs reuse it), the K diagnostics rows and the "
-                    "final state read back; host wall clock, the median of three identical jobs")}
+                    "final state read back; host wall clock, the median of three identical jobs, each from the state and step "
+                    "the timed steps started from")}
 
     if rank == 0:
         clocks = clk.summary()
