@@ -209,7 +209,12 @@ lbmd_status lbmd_reset_translocation(lbmd_handle *h);
 lbmd_status lbmd_init_fluid(lbmd_handle *h, const double *rho, const double *u);
 
 /* Pre-collision populations f^n (the state the next step starts from).
- * f: host [n_real][19][ns]; solid sites read as 0. */
+ * f: host [n_real][19][ns]; solid sites read as 0.  The library stores the
+ * deviations h = f - w_i (Sec. II, w_i the D3Q19 weights); the conversions
+ * round exactly as the FP64 expressions f = (float)((double)h + w_i) and
+ * h = (float)((double)f - w_i) with w_i the double nearest the weight (then,
+ * with FP16 deviation storage, h 2^12 rounded to FP16).  Synchronous: both
+ * calls return once the copy is complete. */
 lbmd_status lbmd_get_populations(lbmd_handle *h, float *f);
 lbmd_status lbmd_set_populations(lbmd_handle *h, const float *f);
 /* The same state as deviations from rest, h = f - w_i (what the library
