@@ -590,7 +590,9 @@ lbmd_status capture_loop(lbmd_handle *h) {
         cudaGraphDestroy(g);
         return s != LBMD_OK ? s : cuda_fail(h, e, "cudaStreamEndCapture");
     }
-    e = cudaGraphInstantiate(&h->lexec, g, 0);
+    // the kernels keep the priorities of the streams they were captured on
+    // (particle kernel high, bead diagnostics low), as in eager launches
+    e = cudaGraphInstantiate(&h->lexec, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) { h->lexec = nullptr; return cuda_fail(h, e, "cudaGraphInstantiate(loop)"); }
     h->loop_A = A0;
@@ -622,7 +624,7 @@ lbmd_status capture_graph(lbmd_handle *h) {
     h->launches = l0;
     if (s != LBMD_OK) { if (g) cudaGraphDestroy(g); return s; }
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&h->gexec, g, 0);
+    e = cudaGraphInstantiate(&h->gexec, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) { h->gexec = nullptr; return cuda_fail(h, e, "cudaGraphInstantiate"); }
     h->graph_A = A0;
@@ -1684,10 +1686,15 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
         return LBMD_OK;
     }
     // Particle-kernel shape: time pseudo-steps (gather, then the particle
-    // kernel concurrent with the lattice pass, as in a step) for every
-    // admissible (lanes per bead, blocks per chain); the bead state is saved
-    // and restored and G cleared, so the state is unchanged.
+    // kernel concurrent with the lattice pass and the bead diagnostics, as in
+    // a step) for every admissible (lanes per bead, blocks per chain); the
+    // bead state and the translocation records are saved and restored and G
+    // cleared, so the state is unchanged.  (The diagnostics also rewrite the
+    // current step's row, which that step writes again.)
     const size_t bb16 = (size_t)h->total_beads * 16;
+    std::vector<lbmd_transloc> tl_saved((size_t)h->cfg.n_real);
+    CK(cudaMemcpyAsync(tl_saved.data(), h->S.tl, tl_saved.size() * sizeof(lbmd_transloc), cudaMemcpyDeviceToHost,
+                       h->st));
     char *snap = h->dbuf + h->L.snap;
     CK(cudaMemcpyAsync(snap, h->S.r_hi, bb16, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(snap + bb16, h->S.r_lo, bb16, cudaMemcpyDeviceToDevice, h->st));
@@ -1713,14 +1720,18 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
                 CKT(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
                 CKT(launch_particles(trial, h->popA, h->aux));
                 CKT(cudaEventRecord(h->ev_join, h->aux));
+                CKT(cudaStreamWaitEvent(h->aux2, h->ev_fork, 0));
+                CKT(launch_bead_diag(trial, h->aux2));
+                CKT(cudaEventRecord(h->ev_join2, h->aux2));
                 if (!h->overlap) CKT(cudaStreamWaitEvent(h->st, h->ev_join, 0));
                 CKT(lattice_pass(h, trial, h->by, h->zc, false));
                 CKT(cudaStreamWaitEvent(h->st, h->ev_join, 0));
+                CKT(cudaStreamWaitEvent(h->st, h->ev_join2, 0));
             }
             CKT(cudaEventRecord(b, h->st));
             CKT(cudaEventSynchronize(b));
             CKT(cudaEventElapsedTime(&ms, a, b));
-            h->launches += 4LL * reps;
+            h->launches += 5LL * reps;
         }
 #undef CKT
         return cudaSuccess;
@@ -1765,6 +1776,8 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
     CK(cudaMemcpyAsync(h->S.r_lo, snap + bb16, bb16, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(h->S.v, snap + 2 * bb16, bb16, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemsetAsync(h->S.G, 0, (size_t)h->cfg.n_real * 3 * h->S.ns * 8, h->st));
+    CK(cudaMemcpyAsync(h->S.tl, tl_saved.data(), tl_saved.size() * sizeof(lbmd_transloc), cudaMemcpyHostToDevice,
+                       h->st));
     CK(put_back());
     h->lists_ready = false;  // the candidates' lists are of their pseudo-steps' positions
     cudaEventDestroy(a);
