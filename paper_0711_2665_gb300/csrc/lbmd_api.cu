@@ -1688,13 +1688,20 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
     // Particle-kernel shape: time pseudo-steps (gather, then the particle
     // kernel concurrent with the lattice pass and the bead diagnostics, as in
     // a step) for every admissible (lanes per bead, blocks per chain); the
-    // bead state and the translocation records are saved and restored and G
-    // cleared, so the state is unchanged.  (The diagnostics also rewrite the
-    // current step's row, which that step writes again.)
+    // bead state, the translocation records and the diagnostics ring slot the
+    // pseudo-steps write (the current step's; once the ring has wrapped it
+    // holds the oldest row a caller can still read) are saved and restored,
+    // and G cleared, so the state is unchanged.
     const size_t bb16 = (size_t)h->total_beads * 16;
-    std::vector<lbmd_transloc> tl_saved((size_t)h->cfg.n_real);
+    const int R = h->cfg.n_real;
+    std::vector<lbmd_transloc> tl_saved((size_t)R);
     CK(cudaMemcpyAsync(tl_saved.data(), h->S.tl, tl_saved.size() * sizeof(lbmd_transloc), cudaMemcpyDeviceToHost,
                        h->st));
+    const size_t drow = sizeof(lbmd_diag);
+    lbmd_diag *slot = h->S.ring + (size_t)(h->host_step % LBMD_DIAG_RING);
+    std::vector<lbmd_diag> row_saved((size_t)R);
+    CK(cudaMemcpy2DAsync(row_saved.data(), drow, slot, (size_t)LBMD_DIAG_RING * drow, drow, R, cudaMemcpyDeviceToHost,
+                         h->st));
     char *snap = h->dbuf + h->L.snap;
     CK(cudaMemcpyAsync(snap, h->S.r_hi, bb16, cudaMemcpyDeviceToDevice, h->st));
     CK(cudaMemcpyAsync(snap + bb16, h->S.r_lo, bb16, cudaMemcpyDeviceToDevice, h->st));
@@ -1778,6 +1785,8 @@ lbmd_status lbmd_autotune(lbmd_handle *h, int32_t reps, int32_t *by_out, int32_t
     CK(cudaMemsetAsync(h->S.G, 0, (size_t)h->cfg.n_real * 3 * h->S.ns * 8, h->st));
     CK(cudaMemcpyAsync(h->S.tl, tl_saved.data(), tl_saved.size() * sizeof(lbmd_transloc), cudaMemcpyHostToDevice,
                        h->st));
+    CK(cudaMemcpy2DAsync(slot, (size_t)LBMD_DIAG_RING * drow, row_saved.data(), drow, drow, R, cudaMemcpyHostToDevice,
+                         h->st));
     CK(put_back());
     h->lists_ready = false;  // the candidates' lists are of their pseudo-steps' positions
     cudaEventDestroy(a);

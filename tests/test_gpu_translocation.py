@@ -160,12 +160,22 @@ def test_ensemble_records_graph_loop_and_reset():
 
 
 def test_autotune_keeps_the_records():
+    """The autotuner's pseudo-steps run the bead diagnostics as a step does;
+    the translocation records, and every diagnostics row a caller can read,
+    come out unchanged.  Past the ring's length the slot the pseudo-steps
+    write holds the oldest of those rows."""
     w, inp = _ensemble()
     sim = lbmd.Simulation(w, inp["solid"], inp["offsets"], inp["r0"])
     sim.step(40)
     before = sim.translocation()
     sim.autotune(2)
     assert sim.translocation().tobytes() == before.tobytes()
+    sim.step_loop(lbmd.DIAG_RING + 10)
+    rows, recs = sim.diagnostics(), sim.translocation()
+    assert rows.shape[1] == lbmd.DIAG_RING
+    sim.autotune(2)
+    assert sim.diagnostics().tobytes() == rows.tobytes()
+    assert sim.translocation().tobytes() == recs.tobytes()
 
 
 def _oracle_tx(w, inp, r, max_steps):
