@@ -359,7 +359,13 @@ __device__ __forceinline__ float wca_coef(float r2, float eps, float sig2) {
 }
 
 struct PSmem {
-    float4 *ph[2], *pl[2];  // replica of the whole chain: positions hi / lo, double buffered
+    // replica of the whole chain: positions hi / lo, double buffered.  Two
+    // members behind a select, not an array indexed by the buffer number: a
+    // runtime index into the struct would keep it in local memory, and every
+    // sub-step would load these pointers from there
+    float4 *ph0, *ph1, *pl0, *pl1;
+    __device__ __forceinline__ float4 *ph(int b) const { return b ? ph1 : ph0; }
+    __device__ __forceinline__ float4 *pl(int b) const { return b ? pl1 : pl0; }
     float4 *jbuf;           // [Nc] impulse J of the block's beads, for the spread
     uint16_t *nbr;          // [Nc][NBR_CAP] bead-pair lists of the block's beads
     uint32_t *wal;          // [Nc][WALL_CAP] packed solid-site coordinates
@@ -391,8 +397,8 @@ __host__ __device__ inline size_t psmem_layout(int nmax, int nc, int nzn, PSmem 
     char *halo = take(4 * (size_t)nmax), *mark = take((size_t)nmax);
     char *bnd = take(48 * ((size_t)nc + 2));
     if (p) {
-        p->ph[0] = (float4 *)ph0; p->ph[1] = (float4 *)ph1;
-        p->pl[0] = (float4 *)pl0; p->pl[1] = (float4 *)pl1;
+        p->ph0 = (float4 *)ph0; p->ph1 = (float4 *)ph1;
+        p->pl0 = (float4 *)pl0; p->pl1 = (float4 *)pl1;
         p->jbuf = (float4 *)jb;
         p->nbr = (uint16_t *)nbr; p->wal = (uint32_t *)wal;
         p->hkey = (int *)hkey; p->hhead = (int *)hhead; p->hnext = (int16_t *)hnext;
@@ -448,7 +454,7 @@ template <int T>
 __device__ __forceinline__ float3 bonded_part(const Sim &S, const PSmem &sm, int buf, bool own, int p, int N, float4 mh,
                                               float4 ml, int lt) {
     float3 F = make_float3(0.f, 0.f, 0.f);
-    const float4 *ph = sm.ph[buf], *plo = sm.pl[buf];
+    const float4 *ph = sm.ph(buf), *plo = sm.pl(buf);
     if constexpr (T >= 3) {
         // Lane lt (< 3) takes the angle whose beads are a = p+lt-2,
         // b = p+lt-1, c = p+lt, with u = r_b - r_a and w = r_c - r_b.  Its
@@ -540,7 +546,7 @@ __device__ __forceinline__ float3 bonded_part(const Sim &S, const PSmem &sm, int
 // one warp; the block's own beads need the centres first - 1 .. last + 1.
 __device__ __forceinline__ void bonded_stage(const Sim &S, const PSmem &sm, int buf, int N, int Nc, int first,
                                              int last) {
-    const float4 *ph = sm.ph[buf], *plo = sm.pl[buf];
+    const float4 *ph = sm.ph(buf), *plo = sm.pl(buf);
     const int nctr = last >= first ? last - first + 3 : 0;
     const int nbt = 32 * bonded_warps(Nc);  // the block's last nbt threads
     for (int sl = threadIdx.x - (blockDim.x - nbt); sl < nctr; sl += nbt) {
@@ -586,7 +592,7 @@ __device__ __forceinline__ float3 bonded_of(const PSmem &sm, int s) {
 template <int T>
 __device__ __forceinline__ float3 pair_part(const Sim &S, const PSmem &sm, int buf, bool own, int p, int pl, float4 mh,
                                             float4 ml, int lt, float3 F) {
-    const float4 *ph = sm.ph[buf], *plo = sm.pl[buf];
+    const float4 *ph = sm.ph(buf), *plo = sm.pl(buf);
     const int nn = own ? (int)sm.nn[pl] : 0, nw = own ? (int)sm.nw[pl] : 0;
     const int nn_w = __reduce_max_sync(0xffffffffu, nn), nw_w = __reduce_max_sync(0xffffffffu, nw);
     const float fnx = (float)S.bnx, fny = (float)S.ny, fnz = (float)S.nz;
@@ -820,7 +826,7 @@ __device__ __forceinline__ void build_lists_body(const Sim &S, const PSmem &sm, 
     const bool brute = N <= BRUTE_MAX;
     const bool hashed = !brute && S.ncell[0] >= 3 && S.ncell[1] >= 3 && S.ncell[2] >= 3;
     const float fnx = (float)S.bnx, fny = (float)S.ny, fnz = (float)S.nz;
-    const float4 *ph = sm.ph[buf], *plo = sm.pl[buf];
+    const float4 *ph = sm.ph(buf), *plo = sm.pl(buf);
     if (hashed)
         for (int k = threadIdx.x; k < HASH_SIZE; k += blockDim.x) { sm.hkey[k] = -1; sm.hhead[k] = -1; }
     __syncthreads();
@@ -962,7 +968,7 @@ cudaError_t launch_lists(const Sim &S, cudaStream_t st) {
 // Called by every thread of the block; ends with a block barrier.
 __device__ __forceinline__ void pull_beads(cg::cluster_group &cl, const PSmem &sm, int buf, int N, int Nc, int rank,
                                            int c0, bool all, int nhalo) {
-    float4 *ph = sm.ph[buf], *plo = sm.pl[buf];
+    float4 *ph = sm.ph(buf), *plo = sm.pl(buf);
     const int n = all ? N : nhalo;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
         const uint32_t e = all ? 0u : sm.halo[k];
@@ -996,15 +1002,20 @@ __device__ __forceinline__ void rebuild_body(const Sim &S, const PSmem &sm, int 
     build_lists_body<T>(S, sm, buf, N, p, pl, own, rank, Nc, pull, clear_flag, s_err, nhalo);
 }
 template <int T>
-__device__ __noinline__ void rebuild_call(const Sim &S, const PSmem &sm, int buf, int N, int p, int pl, bool own,
+__device__ __noinline__ void rebuild_call(const Sim &S, int nmax, int buf, int N, int p, int pl, bool own,
                                           int rank, int Nc, int c0, bool pull, int *clear_flag, int *s_err,
                                           int *nhalo) {
+    // the shared-memory map is laid out again here rather than passed: a
+    // PSmem whose address reached this call would live in local memory
+    extern __shared__ __align__(16) char smem_raw[];
+    PSmem sm;
+    psmem_layout(nmax, Nc, spv_noise_slots(S, Nc), &sm, smem_raw);
     rebuild_body<T>(S, sm, buf, N, p, pl, own, rank, Nc, c0, pull, clear_flag, s_err, nhalo);
 }
 template <int T, bool OUT_OF_LINE>
-__device__ __forceinline__ void rebuild(const Sim &S, const PSmem &sm, int buf, int N, int p, int pl, bool own,
+__device__ __forceinline__ void rebuild(const Sim &S, const PSmem &sm, int nmax, int buf, int N, int p, int pl, bool own,
                                         int rank, int Nc, int c0, bool pull, int *clear_flag, int *s_err, int *nhalo) {
-    if constexpr (OUT_OF_LINE) rebuild_call<T>(S, sm, buf, N, p, pl, own, rank, Nc, c0, pull, clear_flag, s_err, nhalo);
+    if constexpr (OUT_OF_LINE) rebuild_call<T>(S, nmax, buf, N, p, pl, own, rank, Nc, c0, pull, clear_flag, s_err, nhalo);
     else rebuild_body<T>(S, sm, buf, N, p, pl, own, rank, Nc, c0, pull, clear_flag, s_err, nhalo);
 }
 
@@ -1083,10 +1094,10 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
     // term might read holds a finite position) and the state of this lane's bead
     for (int q = threadIdx.x; q < N; q += blockDim.x) {
         const float4 a = S.r_hi[off + q], b = S.r_lo[off + q];
-        sm.ph[0][q] = a;
-        sm.pl[0][q] = b;
-        sm.ph[1][q] = a;
-        sm.pl[1][q] = b;
+        sm.ph(0)[q] = a;
+        sm.pl(0)[q] = b;
+        sm.ph(1)[q] = a;
+        sm.pl(1)[q] = b;
     }
     float4 mh = make_float4(0.f, 0.f, 0.f, 0.f), ml = mh;
     float3 v = make_float3(0.f, 0.f, 0.f), up = v;
@@ -1189,20 +1200,20 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
                 // rebuild request
                 if (pull) {
                     if (lt == 0) {
-                        sm.ph[nb][p] = mh;
-                        sm.pl[nb][p] = ml;
+                        sm.ph(nb)[p] = mh;
+                        sm.pl(nb)[p] = ml;
                     }
                     if (moved)
                         for (int c = c0 + lt; c < c0 + cc; c += T) *cl.map_shared_rank(&s_flag[t & 1], c) = 1;
                 } else if (cc > 1) {
                     for (int c = c0 + lt; c < c0 + cc; c += T) {
-                        *cl.map_shared_rank(sm.ph[nb] + p, c) = mh;
-                        *cl.map_shared_rank(sm.pl[nb] + p, c) = ml;
+                        *cl.map_shared_rank(sm.ph(nb) + p, c) = mh;
+                        *cl.map_shared_rank(sm.pl(nb) + p, c) = ml;
                         if (moved) *cl.map_shared_rank(&s_flag[t & 1], c) = 1;
                     }
                 } else if (lt == 0) {
-                    sm.ph[nb][p] = mh;
-                    sm.pl[nb][p] = ml;
+                    sm.ph(nb)[p] = mh;
+                    sm.pl(nb)[p] = ml;
                     if (moved) s_flag[t & 1] = 1;
                 }
             }
@@ -1210,7 +1221,7 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
             buf = nb;
             if (s_flag[t & 1]) {
                 const unsigned long long t0 = clock64();
-                rebuild<T, BWM>(S, sm, buf, N, p, pl, own, rank, Nc, c0, pull, &s_flag[t & 1], &s_err, &s_nhalo);
+                rebuild<T, BWM>(S, sm, Nmax, buf, N, p, pl, own, rank, Nc, c0, pull, &s_flag[t & 1], &s_err, &s_nhalo);
                 bh = mh;
                 bl = ml;
                 if (S.phase && blockIdx.x == 0 && threadIdx.x == 0) {
