@@ -1092,12 +1092,28 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
 
     // replica of the whole chain (both buffers, so that every entry a force
     // term might read holds a finite position) and the state of this lane's bead
-    for (int q = threadIdx.x; q < N; q += blockDim.x) {
-        const float4 a = S.r_hi[off + q], b = S.r_lo[off + q];
-        sm.ph(0)[q] = a;
-        sm.pl(0)[q] = b;
-        sm.ph(1)[q] = a;
-        sm.pl(1)[q] = b;
+    // (up to four of a thread's beads are loaded before any is stored, so
+    // that their global loads are in flight together)
+    for (int q0 = threadIdx.x; q0 < N; q0 += 4 * blockDim.x) {
+        float4 a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = q0 + u * (int)blockDim.x;
+            if (q < N) {
+                a[u] = S.r_hi[off + q];
+                b[u] = S.r_lo[off + q];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = q0 + u * (int)blockDim.x;
+            if (q < N) {
+                sm.ph(0)[q] = a[u];
+                sm.pl(0)[q] = b[u];
+                sm.ph(1)[q] = a[u];
+                sm.pl(1)[q] = b[u];
+            }
+        }
     }
     float4 mh = make_float4(0.f, 0.f, 0.f, 0.f), ml = mh;
     float3 v = make_float3(0.f, 0.f, 0.f), up = v;
@@ -1121,11 +1137,33 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
     sync_all(cl, C);
     phase_mark(S, 0, tclk);
     // the block's beads' starting lists, built by k_lists, and the halo
+    // A bead's lists are NBR_CAP 16-bit and WALL_CAP 32-bit slots, 16-byte
+    // aligned in both places: each lane copies its 16-byte chunks of both
+    // whole lists, loaded together with the lengths (one round trip to
+    // global memory; the slots past the lengths are never read)
+    static_assert(NBR_CAP % 8 == 0 && WALL_CAP % 4 == 0, "lists copy in 16-byte chunks");
     if (own) {
+        constexpr int NV = NBR_CAP / 8, WV = WALL_CAP / 4;
+        constexpr int NL = (NV + T - 1) / T, WL = (WV + T - 1) / T;
         const size_t g = (size_t)(off + p);
+        const uint4 *nsrc = reinterpret_cast<const uint4 *>(S.nbr_g + g * NBR_CAP);
+        const uint4 *wsrc = reinterpret_cast<const uint4 *>(S.wal_g + g * WALL_CAP);
+        uint4 nch[NL], wch[WL];
+#pragma unroll
+        for (int u = 0; u < NL; ++u)
+            if (lt + u * T < NV) nch[u] = nsrc[lt + u * T];
+#pragma unroll
+        for (int u = 0; u < WL; ++u)
+            if (lt + u * T < WV) wch[u] = wsrc[lt + u * T];
         const int n = S.nn_g[g], m = S.nw_g[g];
-        for (int k = lt; k < n; k += T) sm.nbr[pl * NBR_CAP + k] = S.nbr_g[g * NBR_CAP + k];
-        for (int k = lt; k < m; k += T) sm.wal[pl * WALL_CAP + k] = S.wal_g[g * WALL_CAP + k];
+        uint4 *ndst = reinterpret_cast<uint4 *>(sm.nbr + pl * NBR_CAP);
+        uint4 *wdst = reinterpret_cast<uint4 *>(sm.wal + pl * WALL_CAP);
+#pragma unroll
+        for (int u = 0; u < NL; ++u)
+            if (lt + u * T < NV) ndst[lt + u * T] = nch[u];
+#pragma unroll
+        for (int u = 0; u < WL; ++u)
+            if (lt + u * T < WV) wdst[lt + u * T] = wch[u];
         if (lt == 0) {
             sm.nn[pl] = (uint8_t)n;
             sm.nw[pl] = (uint8_t)m;
