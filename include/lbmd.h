@@ -337,14 +337,19 @@ lbmd_status lbmd_get_overlap(lbmd_handle *h, int32_t *overlap);
 /* Time every candidate tile shape of the stream-collide kernel on the
  * current state and keep the fastest; then, unless the caller fixed the
  * particle-kernel shape with lbmd_set_md_shape, time pseudo-steps (gather,
- * particle kernel concurrent with the lattice pass) for every admissible
+ * particle kernel concurrent with the lattice pass and the bead
+ * diagnostics, as in a step) for every admissible
  * shape and keep the fastest: lanes per bead in {1,2,4,8}; blocks per chain in
  * {1,2,4,8,16} (16 where the device can place such a cluster); push or pull
  * exchange for more than one block, unless the caller fixed it with
  * lbmd_set_md_exchange; both bonded modes, unless fixed with
  * lbmd_set_md_bonded; with and without reserving the SMs
- * (lbmd_get_md_reserve).  The state (populations, beads, G, step) is restored
- * afterwards.  Synchronises the stream. */
+ * (lbmd_get_md_reserve).  The state (populations, beads, G, step, the
+ * translocation records and every diagnostics row lbmd_diagnostics can
+ * return) is restored afterwards.  The choice is made on the state the call
+ * finds: a chain's cost changes along its path (a chain threading the pore
+ * carries long wall lists), and a later call may choose differently.
+ * Synchronises the stream. */
 lbmd_status lbmd_autotune(lbmd_handle *h, int32_t steps_per_candidate, int32_t *by, int32_t *zc);
 
 /* Per-kernel timing with CUDA events on the launching streams (eager launches
