@@ -1136,8 +1136,8 @@ __global__ void __launch_bounds__(512, 1) k_particles(const Sim S, const int C, 
     // block writes into another's shared memory
     sync_all(cl, C);
     phase_mark(S, 0, tclk);
-    // the block's beads' starting lists, built by k_lists, and the halo
-    // A bead's lists are NBR_CAP 16-bit and WALL_CAP 32-bit slots, 16-byte
+    // the block's beads' starting lists, built by k_lists, then the halo.  A
+    // bead's lists are NBR_CAP 16-bit and WALL_CAP 32-bit slots, 16-byte
     // aligned in both places: each lane copies its 16-byte chunks of both
     // whole lists, loaded together with the lengths (one round trip to
     // global memory; the slots past the lengths are never read)
